@@ -1,0 +1,287 @@
+"""CPU oracle for the LoD Gaussian render path (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may import
+this package.  The product library never calls it.  The arithmetic lives in
+`lodgs_oracle.c` (plain C, float64 values, float32 decisions); this module
+compiles it with gcc and marshals numpy arrays.
+
+Functions and the paper passage they follow:
+  build_scene      hierarchy merge (Sec. 3 "Gaussian Hierarchies"), HSPT
+                   construction (Sec. 4.3) and SPT layout (Sec. 4.1, Eq. 4, Eq. 6)
+  select           Algorithm 1 (upper BFS with frustum culling) + Algorithm 2
+  select_bruteforce  top-down descent inside each SPT (independent check)
+  project          EWA projection and SH colour (Sec. 3, Eq. 2)
+  sort_pairs       tile x depth ordering (3DGS sort reused by the paper)
+  blend            Eq. 1 front-to-back compositing
+  render_backward  exact derivative of blend + projection
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lodgs_oracle.c")
+_LIB = os.path.join(_HERE, "liblodgs_oracle.so")
+_lib = None
+
+KIND_INTERNAL, KIND_LEAF, KIND_SPT = 0, 1, 2
+TILE = 16
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (no fused multiply-add)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+               "-shared", "-fPIC", "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(_LIB)
+        _lib.or_morton_code.restype = C.c_uint64
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+    return C.c_void_p(a.ctypes.data)
+
+
+def stride(degree: int) -> int:
+    return int(lib().or_stride(C.c_int(degree)))
+
+
+def pack_camera(cam) -> np.ndarray:
+    """R[9], pos[3], fx, fy, cx, cy, W, H, tau, znear as float32."""
+    v = np.zeros(20, dtype=np.float32)
+    v[0:9] = np.asarray(cam.R, dtype=np.float32).reshape(9)
+    v[9:12] = np.asarray(cam.pos, dtype=np.float32)
+    v[12:20] = [cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height, cam.tau, cam.znear]
+    return v
+
+
+# ---------------------------------------------------------------------------
+# hierarchy
+# ---------------------------------------------------------------------------
+
+def morton_order(leaves: np.ndarray) -> np.ndarray:
+    leaves = np.ascontiguousarray(leaves, dtype=np.float32)
+    n = leaves.shape[0]
+    order = np.zeros(n, dtype=np.int64)
+    rc = lib().or_morton_order(C.c_int64(n), C.c_int(leaves.shape[1]), _p(leaves), _p(order))
+    assert rc == 0
+    return order
+
+
+def merge_hierarchy(leaves: np.ndarray, degree: int, order: np.ndarray | None = None) -> dict:
+    leaves = np.ascontiguousarray(leaves, dtype=np.float32)
+    n, st = leaves.shape
+    if order is None:
+        order = morton_order(leaves)
+    order = np.ascontiguousarray(order, dtype=np.int64)
+    M = 2 * n - 1
+    node = np.zeros((M, st), dtype=np.float32)
+    left = np.zeros(M, dtype=np.int64)
+    right = np.zeros(M, dtype=np.int64)
+    parent = np.zeros(M, dtype=np.int64)
+    rc = lib().or_merge(C.c_int64(n), C.c_int(st), C.c_int(degree), _p(leaves), _p(order), _p(node),
+                        _p(left), _p(right), _p(parent))
+    assert rc == 0
+    return {"n_leaves": n, "degree": degree, "stride": st, "node_rec": node, "left": left,
+            "right": right, "parent": parent, "root": M - 1, "order": order}
+
+
+def merge_pair(ra: np.ndarray, rb: np.ndarray, degree: int) -> np.ndarray:
+    ra = np.ascontiguousarray(ra, dtype=np.float32)
+    rb = np.ascontiguousarray(rb, dtype=np.float32)
+    out = np.zeros_like(ra)
+    lib().or_merge_pair(C.c_int(ra.shape[0]), C.c_int(degree), _p(ra), _p(rb), _p(out))
+    return out
+
+
+def cov_to_scale_rot(cov: np.ndarray):
+    A = np.ascontiguousarray(cov, dtype=np.float64).reshape(3, 3)
+    s = np.zeros(3)
+    q = np.zeros(4)
+    lib().or_cov_to_scale_rot(_p(A), _p(s), _p(q))
+    return s, q
+
+
+def hspt(h: dict, spt_volume: float, kappa: float) -> dict:
+    node = h["node_rec"]
+    M, st = node.shape
+    counts = np.zeros(3, dtype=np.int64)
+    up_node = np.zeros(M, dtype=np.int64)
+    up_kind = np.zeros(M, dtype=np.int32)
+    up_parent = np.zeros(M, dtype=np.int64)
+    up_child = np.zeros(2 * M, dtype=np.int64)
+    up_ref = np.zeros(M, dtype=np.int64)
+    spt_root = np.zeros(M, dtype=np.int64)
+    spt_base = np.zeros(M + 1, dtype=np.int64)
+    spt_count = np.zeros(M, dtype=np.int64)
+    node_of_row = np.zeros(M, dtype=np.int64)
+    row_of_node = np.zeros(M, dtype=np.int64)
+    lo_row = np.zeros(M, dtype=np.float32)
+    hi_row = np.zeros(M, dtype=np.float32)
+    lo_raw = np.zeros(M, dtype=np.float32)
+    rc = lib().or_hspt(C.c_int64(M), C.c_int(st), _p(node), _p(h["left"]), _p(h["right"]),
+                       C.c_int64(h["root"]), C.c_float(spt_volume), C.c_float(kappa), _p(counts),
+                       _p(up_node), _p(up_kind), _p(up_parent), _p(up_child), _p(up_ref),
+                       _p(spt_root), _p(spt_base), _p(spt_count), _p(node_of_row), _p(row_of_node),
+                       _p(lo_row), _p(hi_row), _p(lo_raw))
+    assert rc == 0, rc
+    nu, ns, nr = (int(x) for x in counts)
+    spt_base[ns] = M
+    out = dict(h)
+    out.update({
+        "spt_volume": float(np.float32(spt_volume)), "kappa": float(np.float32(kappa)),
+        "n_upper": nu, "n_spt": ns, "n_upper_rows": nr,
+        "up_node": up_node[:nu].copy(), "up_kind": up_kind[:nu].copy(), "up_parent": up_parent[:nu].copy(),
+        "up_child": up_child[:2 * nu].reshape(nu, 2).copy(), "up_ref": up_ref[:nu].copy(),
+        "spt_root": spt_root[:ns].copy(), "spt_base": spt_base[:ns + 1].copy(),
+        "spt_count": spt_count[:ns].copy(), "node_of_row": node_of_row, "row_of_node": row_of_node,
+        "lo_row": lo_row, "hi_row": hi_row, "lo_raw": lo_raw,
+        "row_rec": np.ascontiguousarray(node[node_of_row]),
+    })
+    return out
+
+
+def build_scene(leaves: np.ndarray, degree: int, spt_volume: float, kappa: float) -> dict:
+    """Leaves -> binary hierarchy -> HSPT with SPT layout (render-row order)."""
+    return hspt(merge_hierarchy(leaves, degree), spt_volume, kappa)
+
+
+# ---------------------------------------------------------------------------
+# selection
+# ---------------------------------------------------------------------------
+
+def select(scene: dict, cam, cull: bool = True):
+    M = scene["node_rec"].shape[0]
+    sel = np.zeros(M, dtype=np.int64)
+    n = np.zeros(1, dtype=np.int64)
+    stats = np.zeros(5, dtype=np.int64)
+    up_child = np.ascontiguousarray(scene["up_child"].reshape(-1))
+    camv = pack_camera(cam)
+    rc = lib().or_select(C.c_int64(scene["n_upper"]), _p(scene["up_node"]), _p(scene["up_kind"]), _p(up_child),
+                         _p(scene["up_ref"]), _p(scene["spt_base"]), _p(scene["lo_row"]), _p(scene["hi_row"]),
+                         C.c_int(scene["stride"]), _p(scene["node_rec"]), _p(camv), C.c_int(int(cull)),
+                         _p(sel), _p(n), _p(stats))
+    assert rc == 0
+    return sel[: int(n[0])].copy(), {"upper_visited": int(stats[0]), "upper_culled": int(stats[1]),
+                                     "spt_cut": int(stats[2]), "spt_scanned": int(stats[3]),
+                                     "selected": int(stats[4])}
+
+
+def select_bruteforce(scene: dict, cam, cull: bool = True) -> np.ndarray:
+    M = scene["node_rec"].shape[0]
+    sel = np.zeros(M, dtype=np.int64)
+    n = np.zeros(1, dtype=np.int64)
+    up_child = np.ascontiguousarray(scene["up_child"].reshape(-1))
+    camv = pack_camera(cam)
+    rc = lib().or_select_bruteforce(C.c_int64(scene["n_upper"]), _p(scene["up_node"]), _p(scene["up_kind"]),
+                                    _p(up_child), _p(scene["up_ref"]), _p(scene["spt_root"]), _p(scene["left"]),
+                                    _p(scene["right"]), _p(scene["lo_raw"]), _p(scene["row_of_node"]),
+                                    C.c_int(scene["stride"]), _p(scene["node_rec"]), _p(camv),
+                                    C.c_int(int(cull)), _p(sel), _p(n))
+    assert rc == 0
+    return sel[: int(n[0])].copy()
+
+
+# ---------------------------------------------------------------------------
+# projection, sort, blend, backward
+# ---------------------------------------------------------------------------
+
+def project(scene: dict, sel: np.ndarray, cam) -> dict:
+    sel = np.ascontiguousarray(sel, dtype=np.int64)
+    n = sel.shape[0]
+    vis = np.zeros(n, dtype=np.int32)
+    rect = np.zeros((n, 4), dtype=np.int32)
+    key = np.zeros(n, dtype=np.uint32)
+    f32 = np.zeros((n, 5), dtype=np.float32)
+    f64 = np.zeros((n, 12), dtype=np.float64)
+    camv = pack_camera(cam)
+    lib().or_project(C.c_int64(n), _p(sel), C.c_int(scene["stride"]), C.c_int(scene["degree"]),
+                     _p(scene["row_rec"]), _p(camv), _p(vis), _p(rect), _p(key), _p(f32), _p(f64))
+    return {"vis": vis, "rect": rect, "key": key, "f32": f32, "f64": f64, "n": n}
+
+
+def sort_pairs(proj: dict, width: int, height: int) -> dict:
+    TX, TY = (width + TILE - 1) // TILE, (height + TILE - 1) // TILE
+    r = proj["rect"].astype(np.int64)
+    cap = int(((r[:, 2] - r[:, 0]) * (r[:, 3] - r[:, 1]) * (proj["vis"] != 0)).sum())
+    pair_i = np.zeros(max(cap, 1), dtype=np.int64)
+    tile_start = np.zeros(TX * TY + 1, dtype=np.int64)
+    npairs = np.zeros(1, dtype=np.int64)
+    rc = lib().or_sort_pairs(C.c_int64(proj["n"]), _p(proj["vis"]), _p(proj["rect"]), _p(proj["key"]),
+                             C.c_int(TX), C.c_int(TY), C.c_int64(cap), _p(npairs), _p(pair_i), _p(tile_start))
+    assert rc == 0
+    return {"pair_i": pair_i[: int(npairs[0])].copy(), "tile_start": tile_start, "TX": TX, "TY": TY}
+
+
+def blend(proj: dict, pairs: dict, width: int, height: int, bg=(0.0, 0.0, 0.0)) -> dict:
+    img = np.zeros((height, width, 3), dtype=np.float64)
+    ncon = np.zeros((height, width), dtype=np.int32)
+    tfin = np.zeros((height, width), dtype=np.float64)
+    bgv = np.asarray(bg, dtype=np.float64)
+    pair_i = pairs["pair_i"] if pairs["pair_i"].size else np.zeros(1, dtype=np.int64)
+    lib().or_blend(C.c_int(width), C.c_int(height), _p(bgv), _p(pairs["tile_start"]), _p(pair_i),
+                   _p(proj["f32"]), _p(proj["f64"]), _p(img), _p(ncon), _p(tfin))
+    return {"image": img, "n_contrib": ncon, "T_final": tfin}
+
+
+def blend_backward(proj: dict, pairs: dict, width: int, height: int, dL_dimg: np.ndarray,
+                   bg=(0.0, 0.0, 0.0)) -> np.ndarray:
+    g = np.zeros((proj["n"], 9), dtype=np.float64)
+    bgv = np.asarray(bg, dtype=np.float64)
+    dL = np.ascontiguousarray(dL_dimg, dtype=np.float64)
+    pair_i = pairs["pair_i"] if pairs["pair_i"].size else np.zeros(1, dtype=np.int64)
+    lib().or_blend_backward(C.c_int(width), C.c_int(height), _p(bgv), _p(pairs["tile_start"]), _p(pair_i),
+                            _p(proj["f32"]), _p(proj["f64"]), _p(dL), C.c_int64(proj["n"]), _p(g))
+    return g
+
+
+def project_backward(scene: dict, sel: np.ndarray, cam, proj: dict, g2d: np.ndarray) -> np.ndarray:
+    sel = np.ascontiguousarray(sel, dtype=np.int64)
+    n = sel.shape[0]
+    out = np.zeros((n, scene["stride"]), dtype=np.float64)
+    camv = pack_camera(cam)
+    lib().or_project_backward(C.c_int64(n), _p(sel), C.c_int(scene["stride"]), C.c_int(scene["degree"]),
+                              _p(scene["row_rec"]), _p(camv), _p(proj["vis"]),
+                              _p(np.ascontiguousarray(g2d, dtype=np.float64)), _p(out))
+    return out
+
+
+def sh_eval(degree: int, v: np.ndarray):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    K = (degree + 1) ** 2 - 1
+    Y = np.zeros(max(K, 1))
+    dY = np.zeros(max(3 * K, 1))
+    lib().or_sh_eval(C.c_int(degree), _p(v), _p(Y), _p(dY))
+    return Y[:K], dY[: 3 * K].reshape(K, 3)
+
+
+def render(scene: dict, cam, bg=(0.0, 0.0, 0.0), cull: bool = True, sel: np.ndarray | None = None) -> dict:
+    """Full forward: select -> project -> sort -> blend."""
+    stats = None
+    if sel is None:
+        sel, stats = select(scene, cam, cull)
+    proj = project(scene, sel, cam)
+    pairs = sort_pairs(proj, cam.width, cam.height)
+    out = blend(proj, pairs, cam.width, cam.height, bg)
+    out.update({"sel": sel, "proj": proj, "pairs": pairs, "select_stats": stats})
+    return out
+
+
+def render_backward(scene: dict, cam, fwd: dict, dL_dimg: np.ndarray, bg=(0.0, 0.0, 0.0)) -> dict:
+    g2d = blend_backward(fwd["proj"], fwd["pairs"], cam.width, cam.height, dL_dimg, bg)
+    grec = project_backward(scene, fwd["sel"], cam, fwd["proj"], g2d)
+    return {"g2d": g2d, "g_rec": grec}

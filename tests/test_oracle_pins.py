@@ -1,0 +1,627 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant the paper states, a library routine (LAPACK eigh, scipy
+rotations and spherical harmonics, numpy lexsort), brute force on small
+inputs, or finite differences.  None of them needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2507_01110_b300 import synth
+
+REC_MU, REC_S, REC_Q, REC_OP, REC_B, REC_F = 0, 3, 6, 10, 11, 14
+
+
+def _rec(stride, mu, s, q=(1, 0, 0, 0), op=0.5, b=(0.5, 0.5, 0.5)):
+    r = np.zeros(stride, dtype=np.float32)
+    r[0:3], r[3:6], r[6:10], r[10], r[11:14] = mu, s, q, op, b
+    return r
+
+
+def _rot_from_quat(q):
+    from scipy.spatial.transform import Rotation
+    w, x, y, z = q
+    return Rotation.from_quat([x, y, z, w]).as_matrix()
+
+
+def _cov(rec):
+    R = _rot_from_quat(rec[6:10].astype(np.float64))
+    s = rec[3:6].astype(np.float64)
+    return R @ np.diag(s * s) @ R.T
+
+
+# ---------------------------------------------------------------------------
+# hierarchy: Morton order, eigen-decomposition, merges, topology
+# ---------------------------------------------------------------------------
+
+def test_morton_order_is_bitplane_lexicographic(oracle_lib):
+    """Z-order on a 4x4x4 grid = lexicographic order of (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo)."""
+    g = np.array([(x, y, z) for x in range(4) for y in range(4) for z in range(4)], dtype=np.float32)
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(len(g))
+    g = g[perm]
+    recs = np.zeros((len(g), 16), dtype=np.float32)
+    recs[:, 0:3] = g
+    order = oracle_lib.morton_order(recs)
+    xi, yi, zi = (g[:, a].astype(int) for a in range(3))
+    expect = np.lexsort((zi & 1, yi & 1, xi & 1, zi >> 1, yi >> 1, xi >> 1))
+    assert np.array_equal(order, expect)
+
+
+def test_morton_ties_broken_by_index(oracle_lib):
+    recs = np.zeros((5, 16), dtype=np.float32)
+    recs[:, 0] = [1.0, 0.0, 1.0, 0.0, 1.0]
+    assert list(oracle_lib.morton_order(recs)) == [1, 3, 0, 2, 4]
+
+
+def test_eigendecomposition_matches_lapack(oracle_lib):
+    rng = np.random.default_rng(1)
+    for trial in range(200):
+        A = rng.normal(size=(3, 3)) * rng.uniform(0.01, 100)
+        C = A @ A.T
+        if trial % 7 == 0:
+            C = np.diag(rng.uniform(0.1, 10, 3))                  # already diagonal
+        if trial % 11 == 0:
+            v = rng.normal(size=3)
+            C = np.outer(v, v) + 1e-6 * np.eye(3)                   # nearly rank one
+        s, q = oracle_lib.cov_to_scale_rot(C)
+        lam = np.linalg.eigh(C)[0][::-1]
+        assert np.allclose(s * s, lam, rtol=1e-10, atol=1e-12 * lam.max())
+        assert s[0] >= s[1] >= s[2]
+        assert abs(np.linalg.norm(q) - 1) < 1e-12 and q[0] >= 0
+        R = _rot_from_quat(q)
+        assert np.allclose(R @ np.diag(s * s) @ R.T, C, rtol=0, atol=1e-10 * np.abs(C).max())
+
+
+def test_merge_identical_children_returns_them(oracle_lib):
+    st = synth.record_stride(0)
+    q = np.array([0.9, 0.1, -0.3, 0.2]); q /= np.linalg.norm(q)
+    a = _rec(st, (1, 2, 3), (0.5, 0.2, 0.1), q, op=0.3, b=(0.1, 0.6, 0.9))
+    p = oracle_lib.merge_pair(a, a, 0)
+    assert np.allclose(p[0:3], a[0:3], atol=1e-6)
+    assert np.allclose(_cov(p), _cov(a), rtol=1e-5, atol=1e-7)
+    assert p[REC_OP] == pytest.approx(min(1.0, 2 * 0.3), rel=1e-6)
+    assert np.allclose(p[11:14], a[11:14], atol=1e-7)
+
+
+def test_merge_zero_weight_child_is_ignored(oracle_lib):
+    st = synth.record_stride(1)
+    q = np.array([0.5, 0.5, -0.5, 0.5])
+    a = _rec(st, (1, 2, 3), (0.5, 0.2, 0.1), q, op=0.7, b=(0.1, 0.6, 0.9))
+    a[14:23] = np.linspace(-0.3, 0.3, 9)
+    b = _rec(st, (9, -4, 7), (2.0, 1.0, 3.0), (1, 0, 0, 0), op=0.0, b=(1, 1, 1))
+    p = oracle_lib.merge_pair(a, b, 1)
+    assert np.allclose(p[0:3], a[0:3], atol=1e-6)
+    assert np.allclose(_cov(p), _cov(a), rtol=1e-5, atol=1e-7)
+    assert p[REC_OP] == pytest.approx(0.7, rel=1e-5)
+    assert np.allclose(p[11:23], a[11:23], atol=1e-7)
+
+
+def test_merge_point_like_children_closed_form(oracle_lib):
+    """Two equal, tiny, equal-opacity children at mu +- (d,0,0): the moment-matched
+    parent has mean mu and covariance diag(d^2, ~0, ~0) (+ the children's own)."""
+    st = synth.record_stride(0)
+    d, eps = 3.0, 1e-3
+    a = _rec(st, (10 + d, 5, -2), (eps, eps, eps), op=0.5)
+    b = _rec(st, (10 - d, 5, -2), (eps, eps, eps), op=0.5)
+    p = oracle_lib.merge_pair(a, b, 0)
+    assert np.allclose(p[0:3], (10, 5, -2), atol=1e-6)
+    assert p[3] == pytest.approx(math.sqrt(d * d + eps * eps), rel=1e-6)
+    assert p[4] == pytest.approx(eps, rel=1e-4) and p[5] == pytest.approx(eps, rel=1e-4)
+    R = _rot_from_quat(p[6:10].astype(np.float64))
+    assert abs(abs(R[0, 0]) - 1) < 1e-6                          # major axis along x
+    # opacity keeps sigma * area: 2 * 0.5 * 3 eps^2 / (2 d eps + eps^2)
+    assert p[REC_OP] == pytest.approx(3 * eps * eps / (2 * math.sqrt(d * d + eps * eps) * eps + eps * eps), rel=1e-4)
+
+
+def test_merge_weighted_mean(oracle_lib):
+    st = synth.record_stride(0)
+    a = _rec(st, (0, 0, 0), (1, 1, 1), op=0.2)
+    b = _rec(st, (4, 0, 0), (2, 2, 2), op=0.4)
+    wa, wb = 0.2 * 3, 0.4 * 12
+    p = oracle_lib.merge_pair(a, b, 0)
+    assert p[0] == pytest.approx(4 * wb / (wa + wb), rel=1e-6)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 13, 64])
+def test_hierarchy_topology(oracle_lib, n):
+    leaves = synth.leaves_uniform_cube(n, seed=5)
+    h = oracle_lib.merge_hierarchy(leaves, 0)
+    M = 2 * n - 1
+    left, right, parent = h["left"], h["right"], h["parent"]
+    assert h["root"] == M - 1 and parent[M - 1] == -1
+    assert np.all(left[:n] == -1) and np.all(right[:n] == -1)
+    assert np.all(left[n:] >= 0) and np.all(right[n:] >= 0)
+    seen = np.zeros(M, dtype=int)
+    stack = [M - 1]
+    while stack:
+        v = stack.pop()
+        seen[v] += 1
+        if left[v] >= 0:
+            assert parent[left[v]] == v and parent[right[v]] == v and left[v] < v and right[v] < v
+            stack += [left[v], right[v]]
+    assert np.all(seen == 1)
+
+
+def test_hierarchy_pairs_consecutive_morton_leaves(oracle_lib):
+    """Leaves sorted along x: level 1 pairs (0,1),(2,3); an odd last node is carried up."""
+    recs = np.zeros((5, 16), dtype=np.float32)
+    recs[:, 0] = [0, 1, 2, 3, 4]
+    recs[:, 3:6] = 0.1
+    recs[:, 6] = 1
+    recs[:, 10] = 0.5
+    h = oracle_lib.merge_hierarchy(recs, 0)
+    L, R = h["left"], h["right"]
+    assert (L[5], R[5]) == (0, 1) and (L[6], R[6]) == (2, 3)
+    assert (L[7], R[7]) == (5, 6) and (L[8], R[8]) == (7, 4)
+
+
+# ---------------------------------------------------------------------------
+# HSPT and SPT intervals
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def scene1(oracle_lib):
+    cfg = synth.config1_scene()
+    return cfg, oracle_lib.build_scene(cfg["leaves"], 0, cfg["spt_volume"], cfg["kappa"])
+
+
+def _subtree(left, right, r):
+    out, st = [], [r]
+    while st:
+        v = st.pop()
+        out.append(v)
+        if left[v] >= 0:
+            st += [left[v], right[v]]
+    return out
+
+
+def test_hspt_partitions_the_hierarchy(scene1):
+    cfg, sc = scene1
+    M = sc["node_rec"].shape[0]
+    rec, left, right = sc["node_rec"], sc["left"], sc["right"]
+    vol = (rec[:, 3] * rec[:, 4]) * rec[:, 5]
+    owner = np.full(M, -1)
+    for u in range(sc["n_upper"]):
+        node, kind = sc["up_node"][u], sc["up_kind"][u]
+        if kind == 2:
+            assert vol[node] < np.float32(cfg["spt_volume"])
+            for v in _subtree(left, right, node):
+                assert owner[v] == -1
+                owner[v] = 1
+        else:
+            assert vol[node] >= np.float32(cfg["spt_volume"])
+            assert owner[node] == -1
+            owner[node] = 0
+    assert np.all(owner >= 0)
+    assert np.array_equal(np.sort(sc["node_of_row"]), np.arange(M))
+    assert np.array_equal(sc["row_of_node"][sc["node_of_row"]], np.arange(M))
+    # SPT entries sorted by hi descending, root first with hi = +inf
+    for j in range(sc["n_spt"]):
+        b, c = sc["spt_base"][j], sc["spt_count"][j]
+        hi = sc["hi_row"][b:b + c]
+        assert np.isinf(hi[0]) and sc["node_of_row"][b] == sc["spt_root"][j]
+        assert np.all(np.diff(hi) <= 0)
+
+
+def _paths(left, right, r):
+    """All root-to-leaf paths of the subtree at r."""
+    out, st = [], [(r, [r])]
+    while st:
+        v, p = st.pop()
+        if left[v] < 0:
+            out.append(p)
+        else:
+            st += [(left[v], p + [left[v]]), (right[v], p + [right[v]])]
+    return out
+
+
+def test_spt_intervals_cut_every_path_exactly_once(scene1):
+    """Eq. 4 with clamped intervals: for any x >= 0 exactly one node per
+    root-to-leaf path satisfies lo <= x < hi, and it is the node the unclamped
+    top-down descent picks."""
+    _, sc = scene1
+    left, right = sc["left"], sc["right"]
+    rng = np.random.default_rng(3)
+    for j in rng.choice(sc["n_spt"], 6, replace=False):
+        b, c = sc["spt_base"][j], sc["spt_count"][j]
+        rows = np.arange(b, b + c)
+        nodes = sc["node_of_row"][rows]
+        lo = dict(zip(nodes, sc["lo_row"][rows]))
+        hi = dict(zip(nodes, sc["hi_row"][rows]))
+        paths = _paths(left, right, sc["spt_root"][j])
+        xs = np.concatenate([[0.0], rng.uniform(0, 1.5 * lo[sc["spt_root"][j]], 20),
+                             sc["lo_row"][rows][:10], [1e30]]).astype(np.float32)
+        for x in xs:
+            chosen = {v for v in nodes if lo[v] <= x < hi[v]}
+            for p in paths:
+                assert sum(v in chosen for v in p) == 1
+            # brute force: first node on the path with lo_raw <= x (leaves qualify)
+            bf = set()
+            for p in paths:
+                for v in p:
+                    if left[v] < 0 or sc["lo_raw"][v] <= x:
+                        bf.add(v)
+                        break
+            assert bf == chosen
+            if x == 0:
+                assert all(left[v] < 0 for v in chosen)
+            if x >= lo[sc["spt_root"][j]]:
+                assert chosen == {sc["spt_root"][j]}
+
+
+def test_unreachable_nodes_never_selected(scene1):
+    """Nodes whose own size term exceeds their parent's clamped bound get an
+    empty interval (lo == hi) and are never selected (appendix, Unreachable
+    Gaussians)."""
+    _, sc = scene1
+    M = sc["node_rec"].shape[0]
+    rows = np.arange(sc["n_upper_rows"], M)
+    empty = rows[sc["lo_row"][rows] >= sc["hi_row"][rows]]
+    assert empty.size > 0
+    lo, hi = sc["lo_row"], sc["hi_row"]
+    for x in np.linspace(0, 200, 101, dtype=np.float32):
+        assert not np.any((lo[empty] <= x) & (x < hi[empty]))
+
+
+def test_spt_conservative_distance(scene1):
+    """Sec. 4.1: selecting with M_d guarantees m_d(i) <= |mu_i - p| for every
+    selected SPT node (k = f/tau = kappa, triangle inequality)."""
+    cfg, sc = scene1
+    cam = cfg["cameras"][0]
+    sel, _ = __import__("oracle").select(sc, cam, cull=False)
+    rec = sc["row_rec"][sel].astype(np.float64)
+    in_spt = sel >= sc["n_upper_rows"]
+    s = rec[:, 3:6]
+    S = np.sqrt((s[:, 0] * s[:, 1] + s[:, 0] * s[:, 2] + s[:, 1] * s[:, 2]) / 3)
+    d = np.linalg.norm(rec[:, 0:3] - cam.pos.astype(np.float64), axis=1)
+    k = cam.fx / cam.tau
+    leaf = sc["left"][sc["node_of_row"][sel]] < 0
+    chk = in_spt & ~leaf
+    assert chk.sum() > 0
+    assert np.all(k * S[chk] <= d[chk] * (1 + 1e-5))
+
+
+def _covered_leaves(sc, sel):
+    left, right = sc["left"], sc["right"]
+    nodes = sc["node_of_row"][sel]
+    cover = np.zeros(sc["n_leaves"], dtype=int)
+    for v in nodes:
+        for w in _subtree(left, right, v):
+            if left[w] < 0:
+                cover[w] += 1
+    return cover
+
+
+def test_select_is_proper_cut_and_matches_bruteforce(oracle_lib, scene1):
+    cfg, sc = scene1
+    cams = [cfg["cameras"][0],
+            synth.camera_look([80.0, -60.0, 40.0], [-1.0, 0.7, -0.3], [0.0, 0.0, 1.0], 200, 120, tau=2.0),
+            synth.camera_look([0.0, 0.0, 0.0], [0.3, 0.2, 1.0], [1.0, 0.0, 0.0], 160, 160, tau=0.5)]
+    for cam in cams:
+        for cull in (True, False):
+            sel, st = oracle_lib.select(sc, cam, cull)
+            bf = oracle_lib.select_bruteforce(sc, cam, cull)
+            assert np.array_equal(sel, bf)
+            assert np.all(np.diff(sel) > 0)
+            cover = _covered_leaves(sc, sel)
+            assert cover.max() <= 1                       # proper: no node with its ancestor
+            if not cull:
+                assert np.all(cover == 1)                 # every root-to-leaf path crossed once
+        sel_c, _ = oracle_lib.select(sc, cam, True)
+        sel_n, _ = oracle_lib.select(sc, cam, False)
+        cov_c, cov_n = _covered_leaves(sc, sel_c), _covered_leaves(sc, sel_n)
+        assert np.all(cov_c <= cov_n)                     # culling only removes coverage
+
+
+def test_upper_bfs_matches_recursive_dfs(scene1):
+    """Algorithm 1 (queue) against a textbook recursion with the same predicates."""
+    import oracle
+    cfg, sc = scene1
+    cam = synth.camera_look([30.0, 20.0, -90.0], [-0.2, -0.1, 1.0], [1.0, 0.0, 0.0], 256, 200, tau=1.0)
+    sel, _ = oracle.select(sc, cam, True)
+    # recursion in float32 numpy with the documented expressions
+    f32 = np.float32
+    R, pos = cam.R.astype(f32), cam.pos.astype(f32)
+    fx, fy, cx, cy = f32(cam.fx), f32(cam.fy), f32(cam.cx), f32(cam.cy)
+    W, H = f32(cam.width), f32(cam.height)
+    planes = []
+    for (a, b_, c_) in ((fx, f32(0), cx), (-fx, f32(0), W - cx)):
+        l_ = np.sqrt(a * a + c_ * c_, dtype=f32)
+        planes.append((a / l_, f32(0), c_ / l_))
+    for (a, c_) in ((fy, cy), (-fy, H - cy)):
+        l_ = np.sqrt(a * a + c_ * c_, dtype=f32)
+        planes.append((f32(0), a / l_, c_ / l_))
+    inv_k = f32(cam.tau) / fx
+    rec = sc["node_rec"]
+    out = []
+
+    def view(v):
+        d = rec[v, 0:3] - pos
+        dist = np.sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2], dtype=f32)
+        t = [(R[a, 0] * d[0] + R[a, 1] * d[1]) + R[a, 2] * d[2] for a in range(3)]
+        return t, dist
+
+    def rec_dfs(u):
+        v = sc["up_node"][u]
+        t, dist = view(v)
+        r = f32(3) * max(rec[v, 3], rec[v, 4], rec[v, 5])
+        if t[2] + r < f32(cam.znear) or any((p[0] * t[0] + p[1] * t[1]) + p[2] * t[2] < -r for p in planes):
+            return
+        x = dist * inv_k
+        kind = sc["up_kind"][u]
+        s = rec[v, 3:6]
+        S = np.sqrt(((s[0] * s[1] + s[0] * s[2]) + s[1] * s[2]) / f32(3), dtype=f32)
+        if kind == 2:
+            j = sc["up_ref"][u]
+            b, c = sc["spt_base"][j], sc["spt_count"][j]
+            for e in range(b, b + c):
+                if sc["lo_row"][e] <= x < sc["hi_row"][e]:
+                    out.append(e)
+        elif kind == 1 or S <= x:
+            out.append(sc["up_ref"][u])
+        else:
+            rec_dfs(sc["up_child"][u][0])
+            rec_dfs(sc["up_child"][u][1])
+
+    rec_dfs(0)
+    assert np.array_equal(np.sort(np.array(out)), sel)
+
+
+# ---------------------------------------------------------------------------
+# projection and colour
+# ---------------------------------------------------------------------------
+
+def _one_gaussian_scene(recs, degree=0):
+    import oracle
+    recs = np.ascontiguousarray(np.atleast_2d(recs), dtype=np.float32)
+    st = recs.shape[1]
+    n = recs.shape[0]
+    return {"stride": st, "degree": degree, "row_rec": recs}, np.arange(n, dtype=np.int64)
+
+
+def test_projection_isotropic_on_axis_closed_form(oracle_lib):
+    """Sigma' = (f s / z)^2 I + 0.3 I for an isotropic Gaussian on the optical axis."""
+    st = synth.record_stride(0)
+    rng = np.random.default_rng(4)
+    for z, s in ((10.0, 0.5), (50.0, 2.0), (3.0, 0.05)):
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        cam = synth.camera_look([0.0, 0.0, -z], [0, 0, 1], [1, 0, 0], 128, 96)
+        scene, sel = _one_gaussian_scene(_rec(st, (0, 0, 0), (s, s, s), q))
+        pr = oracle_lib.project(scene, sel, cam)
+        f, s32 = float(cam.fx), float(np.float32(s))
+        var = (f * s32 / z) ** 2 + 0.3
+        u, v, A, B, Cc = pr["f64"][0, 0:5]
+        assert pr["vis"][0] == 1
+        assert u == pytest.approx(64.0) and v == pytest.approx(48.0)
+        assert A == pytest.approx(1 / var, rel=1e-9) and Cc == pytest.approx(1 / var, rel=1e-9)
+        assert abs(B) < 1e-12 / var
+        assert np.allclose(pr["f32"][0, 2:5], [1 / var, 0, 1 / var], rtol=1e-5, atol=1e-6 / var)
+        assert pr["key"][0] == np.float32(z).view(np.uint32)
+
+
+def test_projection_jacobian_matches_finite_differences(oracle_lib):
+    """EWA (Sec. 3): Sigma' = J W Sigma W^T J^T + 0.3 I with J the derivative of
+    the perspective map, here taken by central differences."""
+    st = synth.record_stride(0)
+    rng = np.random.default_rng(5)
+    cam = synth.camera_look([1.0, -2.0, -20.0], [0.05, 0.1, 1.0], [1, 0, 0], 320, 240)
+    R = cam.R.astype(np.float64)
+    for _ in range(10):
+        mu = rng.uniform(-3, 3, 3)
+        s = rng.uniform(0.1, 1.5, 3)
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        rec = _rec(st, mu, s, q)
+        scene, sel = _one_gaussian_scene(rec)
+        pr = oracle_lib.project(scene, sel, cam)
+        t = R @ (rec[0:3].astype(np.float64) - cam.pos.astype(np.float64))
+
+        def pi(t):
+            return np.array([cam.fx * t[0] / t[2] + cam.cx, cam.fy * t[1] / t[2] + cam.cy])
+        J = np.zeros((2, 3))
+        for a in range(3):
+            e = np.zeros(3); e[a] = 1e-5 * max(1.0, abs(t[a]))
+            J[:, a] = (pi(t + e) - pi(t - e)) / (2 * e[a])
+        S2 = J @ R @ _cov(rec) @ R.T @ J.T + 0.3 * np.eye(2)
+        Q = np.linalg.inv(S2)
+        A, B, Cc = pr["f64"][0, 2:5]
+        assert np.allclose([A, B, Cc], [Q[0, 0], Q[0, 1], Q[1, 1]], rtol=1e-6, atol=1e-9)
+        assert np.allclose(pr["f64"][0, 0:2], pi(t), rtol=1e-12)
+
+
+def test_projection_rotation_invariant_for_isotropic(oracle_lib):
+    st = synth.record_stride(0)
+    cam = synth.camera_look([2.0, 1.0, -15.0], [0.1, 0, 1], [1, 0, 0], 200, 200)
+    rng = np.random.default_rng(6)
+    ref = None
+    for _ in range(5):
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        scene, sel = _one_gaussian_scene(_rec(st, (0.5, -0.3, 1.0), (0.7, 0.7, 0.7), q))
+        v = oracle_lib.project(scene, sel, cam)["f64"][0, :5]
+        ref = v if ref is None else ref
+        assert np.allclose(v, ref, rtol=1e-6)
+
+
+def _real_sh_scipy(l, m, v):
+    from scipy.special import sph_harm_y
+    x, y, z = v
+    theta = math.acos(max(-1.0, min(1.0, z)))
+    phi = math.atan2(y, x)
+    if m == 0:
+        return sph_harm_y(l, 0, theta, phi).real
+    Y = sph_harm_y(l, abs(m), theta, phi)
+    sgn = (-1) ** abs(m)
+    return math.sqrt(2) * sgn * (Y.real if m > 0 else Y.imag)
+
+
+def test_sh_matches_scipy_and_derivative(oracle_lib):
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        v = rng.normal(size=3); v /= np.linalg.norm(v)
+        Y, dY = oracle_lib.sh_eval(3, v)
+        k = 0
+        for l in range(1, 4):
+            for m in range(-l, l + 1):
+                assert Y[k] == pytest.approx(_real_sh_scipy(l, m, v), abs=1e-12)
+                k += 1
+        # derivative of the polynomial form vs central differences, tangential part
+        for a in range(3):
+            e = np.zeros(3); e[a] = 1e-6
+            num = (oracle_lib.sh_eval(3, v + e)[0] - oracle_lib.sh_eval(3, v - e)[0]) / 2e-6
+            assert np.allclose(dY[:, a], num, atol=1e-7)
+
+
+def test_sh_orthonormal_by_quadrature(oracle_lib):
+    xg, wg = np.polynomial.legendre.leggauss(24)
+    nphi = 48
+    K = 15
+    G = np.zeros((K, K))
+    for z, w in zip(xg, wg):
+        for i in range(nphi):
+            phi = 2 * math.pi * i / nphi
+            r = math.sqrt(1 - z * z)
+            Y, _ = oracle_lib.sh_eval(3, np.array([r * math.cos(phi), r * math.sin(phi), z]))
+            G += w * (2 * math.pi / nphi) * np.outer(Y, Y)
+    assert np.allclose(G, np.eye(K), atol=1e-12)
+
+
+def test_colour_degree0_is_base_colour(oracle_lib):
+    st = synth.record_stride(0)
+    cam = synth.camera_look([0, 0, -10.0], [0, 0, 1], [1, 0, 0], 64, 64)
+    scene, sel = _one_gaussian_scene(_rec(st, (0.3, 0.2, 0), (0.2, 0.3, 0.4), b=(0.25, 0.5, 0.75)))
+    pr = oracle_lib.project(scene, sel, cam)
+    assert np.allclose(pr["f64"][0, 6:9], [0.25, 0.5, 0.75], rtol=0, atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# sort and blend
+# ---------------------------------------------------------------------------
+
+def test_sort_matches_lexsort(oracle_lib, scene1):
+    cfg, sc = scene1
+    cam = cfg["cameras"][0]
+    sel, _ = oracle_lib.select(sc, cam)
+    pr = oracle_lib.project(sc, sel, cam)
+    pairs = oracle_lib.sort_pairs(pr, cam.width, cam.height)
+    TX = pairs["TX"]
+    tiles, keys, idx = [], [], []
+    for i in np.nonzero(pr["vis"])[0]:
+        x0, y0, x1, y1 = pr["rect"][i]
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                tiles.append(ty * TX + tx); keys.append(pr["key"][i]); idx.append(i)
+    tiles, keys, idx = map(np.array, (tiles, keys, idx))
+    o = np.lexsort((idx, keys, tiles))
+    assert np.array_equal(pairs["pair_i"], idx[o])
+    assert np.array_equal(np.diff(pairs["tile_start"]), np.bincount(tiles, minlength=len(pairs["tile_start"]) - 1))
+
+
+def test_lone_gaussian_analytic_image(oracle_lib):
+    """Eq. 1-2 for one isotropic on-axis Gaussian: c * min(0.99, sigma exp(-r^2 / (2 var)))
+    inside the 3-sigma support, background outside."""
+    st = synth.record_stride(0)
+    z, s, op = 20.0, 0.4, 0.8
+    col = np.array([0.9, 0.4, 0.2])
+    cam = synth.camera_look([0, 0, -z], [0, 0, 1], [1, 0, 0], 64, 48)
+    scene, sel = _one_gaussian_scene(_rec(st, (0, 0, 0), (s, s, s), op=op, b=col))
+    out = oracle_lib.render(scene, cam, bg=(0.1, 0.2, 0.3), sel=sel)
+    s, op = float(np.float32(s)), float(np.float32(op))
+    col = col.astype(np.float32).astype(np.float64)
+    var = (float(cam.fx) * s / z) ** 2 + 0.3
+    py, px = np.mgrid[0:48, 0:64]
+    r2 = (px + 0.5 - 32.0) ** 2 + (py + 0.5 - 24.0) ** 2
+    p = -0.5 * r2 / var
+    alpha = np.minimum(0.99, op * np.exp(p)) * (p >= -4.5)
+    expect = col[None, None, :] * alpha[..., None] + (1 - alpha[..., None]) * np.array([0.1, 0.2, 0.3])
+    inner = np.abs(p + 4.5) > 1e-4                               # away from the float32 support edge
+    assert np.allclose(out["image"][inner], expect[inner], atol=1e-12)
+
+
+def test_two_gaussians_composite_front_to_back(oracle_lib):
+    st = synth.record_stride(0)
+    cam = synth.camera_look([0, 0, -10.0], [0, 0, 1], [1, 0, 0], 32, 32)
+    g1 = _rec(st, (0, 0, 0), (0.5, 0.5, 0.5), op=0.6, b=(1, 0, 0))
+    g2 = _rec(st, (0, 0, 5), (0.75, 0.75, 0.75), op=0.7, b=(0, 1, 0))
+    scene, sel = _one_gaussian_scene(np.stack([g2, g1]))         # order in input must not matter
+    out = oracle_lib.render(scene, cam, sel=sel)
+    f, f32 = float(cam.fx), lambda x: float(np.float32(x))
+    c = out["image"][16, 16]                                      # pixel centre (16.5, 16.5)
+    r2 = 0.5
+    a1 = f32(0.6) * math.exp(-0.5 * r2 / ((f * 0.5 / 10) ** 2 + 0.3))
+    a2 = f32(0.7) * math.exp(-0.5 * r2 / ((f * 0.75 / 15) ** 2 + 0.3))
+    assert c[0] == pytest.approx(a1, rel=1e-12)
+    assert c[1] == pytest.approx(a2 * (1 - a1), rel=1e-12)
+
+
+def test_blend_transmittance_and_transparent_scene(oracle_lib, scene1):
+    cfg, sc = scene1
+    cam = cfg["cameras"][0]
+    out = oracle_lib.render(sc, cam)
+    assert np.all(out["T_final"] <= 1.0) and np.all(out["T_final"] >= 1e-4)
+    assert np.all(out["image"] >= 0) and np.all(out["image"] <= 1.0 + 1e-12)
+    clear = dict(sc)
+    clear["row_rec"] = sc["row_rec"].copy()
+    clear["row_rec"][:, REC_OP] = 0.0
+    o2 = oracle_lib.render(clear, cam, bg=(0.2, 0.4, 0.6), sel=out["sel"])
+    assert np.allclose(o2["image"], np.array([0.2, 0.4, 0.6]), atol=0)
+
+
+# ---------------------------------------------------------------------------
+# backward: finite differences on the oracle's own forward
+# ---------------------------------------------------------------------------
+
+def _fd_scene(degree, rng, n=6, clamp_case=False):
+    st = synth.record_stride(degree)
+    recs = []
+    for i in range(n):
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        mu = (rng.uniform(-0.6, 0.6), rng.uniform(-0.6, 0.6), rng.uniform(-0.5, 2.0))
+        scales = rng.uniform(3.0, 4.5, 3)
+        if clamp_case and i == 0:
+            mu = (9.0, 0.2, 1.0)                                  # centre off-screen: clamped Jacobian
+            scales = np.array([8.0, 7.0, 9.0])
+        r = _rec(st, mu, scales, q, op=rng.uniform(0.1, 0.45), b=rng.uniform(0.3, 0.7, 3))
+        if degree:
+            r[14:14 + 3 * ((degree + 1) ** 2 - 1)] = rng.normal(0, 0.05, 3 * ((degree + 1) ** 2 - 1))
+        recs.append(r)
+    cam = synth.camera_look([0.1, -0.05, -6.0], [0.02, 0.01, 1.0], [1, 0, 0], 32, 24)
+    return np.stack(recs), cam
+
+
+@pytest.mark.parametrize("degree,clamp_case", [(0, False), (3, False), (1, True)])
+def test_backward_matches_finite_differences(oracle_lib, degree, clamp_case):
+    rng = np.random.default_rng(10 + degree)
+    recs, cam = _fd_scene(degree, rng, clamp_case=clamp_case)
+    scene, sel = _one_gaussian_scene(recs, degree)
+    bg = (0.05, 0.1, 0.15)
+    fwd = oracle_lib.render(scene, cam, bg=bg, sel=sel)
+    assert fwd["proj"]["vis"].all()
+    assert np.all(fwd["proj"]["rect"] == [0, 0, 2, 2])
+    f = fwd["proj"]["f64"]                                        # support edge outside the image:
+    py, px = np.mgrid[0:cam.height, 0:cam.width]                  # the float32 test never flips
+    for i in range(recs.shape[0]):
+        dx, dy = f[i, 0] - (px + 0.5), f[i, 1] - (py + 0.5)
+        p = -0.5 * (f[i, 2] * dx * dx + f[i, 4] * dy * dy) - f[i, 3] * dx * dy
+        assert p.min() > -4.3
+    if clamp_case:
+        assert f[0, 0] > cam.width                                # centre off-screen
+    wimg = np.random.default_rng(99).uniform(-1, 1, fwd["image"].shape)
+    g = oracle_lib.render_backward(scene, cam, fwd, wimg, bg=bg)["g_rec"]
+    K = (degree + 1) ** 2 - 1
+    cols = list(range(0, 14 + 3 * K))
+    for i in range(recs.shape[0]):
+        for c in cols:
+            base = recs[i, c]
+            h = np.float32(2e-3 * max(1.0, abs(float(base))))
+            vals = []
+            for sgn in (1, -1):
+                rr = recs.copy()
+                rr[i, c] = np.float32(base + sgn * h)
+                sc2, _ = _one_gaussian_scene(rr, degree)
+                vals.append((oracle_lib.render(sc2, cam, bg=bg, sel=sel)["image"] * wimg).sum())
+            hp = float(np.float32(base + h)) - float(np.float32(base - h))
+            num = (vals[0] - vals[1]) / hp
+            assert g[i, c] == pytest.approx(num, rel=2e-3, abs=2e-4 * (1 + abs(num))), (i, c)
