@@ -1,0 +1,191 @@
+/*
+ * lodgs.h -- C ABI of the B300-native LoD Gaussian render path.
+ *
+ * Method: "A LoD of Gaussians" (arxiv 2507.01110).  Given Gaussians and their
+ * hierarchy, a camera and an LoD threshold, select a proper cut of the
+ * hierarchical SPT (Sec. 4.3, Algorithms 1-2, Eq. 4/6), render it with the 3DGS
+ * tile rasterizer (Sec. 3, Eq. 1-2) and return gradients for the cut's
+ * parameters (Appendix "Implementation Details"; only cut-set nodes receive
+ * gradients).
+ *
+ * Conventions
+ *  - Every call returns a status code (LODGS_OK = 0, negative on error) and
+ *    never throws or aborts; lodgs_last_error() gives a message for the calling
+ *    thread.
+ *  - Pointers are plain host or device pointers; sizes are element counts.
+ *    Streams are cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Calls that take a stream only enqueue work; results are valid once that
+ *    stream has been synchronised.  They do not synchronise the device.
+ *  - Node records are float32 rows of `stride` floats (stride = 14 + 3K rounded
+ *    up to a multiple of 8, K = (D+1)^2 - 1 SH coefficients per channel):
+ *      [0:3] mean, [3:6] scales (linear), [6:10] quaternion (w,x,y,z, need not
+ *      be normalised), [10] opacity in [0,1], [11:14] base colour,
+ *      [14:14+3K] SH coefficients of degrees 1..D, coefficient-major, RGB-minor.
+ *  - Cameras: world->camera rotation R (row-major; rows = right, down,
+ *    forward), camera centre `pos` in world units, pinhole intrinsics in
+ *    pixels; pixel (x, y) covers [x, x+1) x [y, y+1), its centre is +0.5.
+ *  - Images are float32 H x W x 3 (row-major, RGB interleaved), device memory
+ *    owned by the caller.
+ */
+#ifndef LODGS_H
+#define LODGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LODGS_OK 0
+#define LODGS_E_INVALID (-1)   /* bad argument or size */
+#define LODGS_E_OOM (-2)       /* device or pinned allocation failed */
+#define LODGS_E_CUDA (-3)      /* a CUDA runtime call failed */
+#define LODGS_E_TIMEOUT (-4)   /* a bounded device wait ran out */
+#define LODGS_E_STATE (-5)     /* call out of order (e.g. backward before render) */
+#define LODGS_E_CAPACITY (-6)  /* a frame buffer was too small; grown, re-run the frame */
+
+typedef struct lodgs_scene lodgs_scene; /* opaque, library-owned */
+typedef struct lodgs_frame lodgs_frame; /* opaque per-view state and workspace, library-owned */
+
+typedef struct {
+    float R[9];        /* world->camera rotation, row-major */
+    float pos[3];      /* camera centre, world */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float tau;         /* LoD threshold in pixels (projected size of a node, Eq. 6 reading) */
+    float znear;       /* near plane, > 0 */
+} lodgs_camera;
+
+typedef struct {
+    float spt_volume;  /* HSPT volume threshold `size` of Sec. 4.3: s1*s2*s3 < size roots an SPT */
+    float kappa;       /* smallest focal/tau (pixels per world unit) the scene will be cut for;
+                          folds the focal normalisation of the appendix into the SPT intervals */
+} lodgs_build_params;
+
+typedef struct {
+    int64_t n_leaves, n_nodes;       /* n_nodes = 2 n_leaves - 1 */
+    int64_t n_upper;                 /* entries of the upper hierarchy (BFS order), SPT roots included */
+    int64_t n_upper_rows;            /* upper nodes that are not SPT roots (render rows 0..n_upper_rows-1) */
+    int64_t n_spt;                   /* number of SPTs */
+    int32_t sh_degree, stride;
+    float *d_rows;                   /* device, library-owned: n_nodes x stride records in render-row order */
+} lodgs_scene_info;
+
+typedef struct {
+    int64_t n_selected;              /* cut size (Algorithms 1-2) */
+    int64_t n_upper_selected;        /* of which upper-hierarchy nodes */
+    int64_t n_spt_cut;               /* SPTs handed to Algorithm 2 */
+    int64_t n_spt_scanned;           /* SPT entries tested, sum of the binary-search prefixes */
+    int64_t n_visible;               /* selected nodes in front of the near plane with a non-empty tile rect */
+    int64_t n_pairs;                 /* (Gaussian, tile) pairs sorted */
+    int32_t status;                  /* LODGS_OK, or LODGS_E_CAPACITY / LODGS_E_TIMEOUT from the device */
+    int32_t width, height;
+} lodgs_frame_stats;
+
+/* Thread-local message for the last failing call of this thread. */
+const char *lodgs_last_error(void);
+/* Library version string. */
+const char *lodgs_version(void);
+
+/*
+ * Build the scene from leaf Gaussians (Sec. 3 "Gaussian Hierarchies"; Sec. 4.3
+ * HSPT construction).  Leaves are merged pairwise, level by level, in Morton
+ * order (moment-matched mean and covariance, weights opacity x surface term);
+ * the hierarchy is cut by a BFS on the volume test into the upper hierarchy and
+ * SPT roots; each SPT's nodes are laid out by descending parent bound (Eq. 4)
+ * with the conservative spread term of Sec. 4.1 and top-down clamping
+ * (appendix "Unreachable Gaussians").
+ *   leaves: n x stride float32 records (layout above), host or device
+ *           (leaves_on_device != 0); read only during the call.
+ *   n >= 1, 0 <= sh_degree <= 3.  Synchronous.  *out is owned by the caller
+ *   and released with lodgs_scene_free.
+ */
+int lodgs_build_hierarchy(const float *leaves, int64_t n, int sh_degree, int leaves_on_device,
+                          const lodgs_build_params *params, lodgs_scene **out);
+void lodgs_scene_free(lodgs_scene *scene);
+int lodgs_scene_get_info(const lodgs_scene *scene, lodgs_scene_info *info);
+
+/*
+ * Copy the scene structure to host buffers (any pointer may be NULL to skip).
+ * Canonical node ids: leaves 0..n-1 in input order, internal nodes n.. in merge
+ * order, root n_nodes-1.
+ *   node_rec   n_nodes x stride   records by canonical id
+ *   left,right n_nodes            children (-1 for leaves)
+ *   up_node, up_kind (0 internal, 1 leaf, 2 SPT root), up_parent, up_ref
+ *              n_upper            upper hierarchy in BFS order; ref = render row or SPT index
+ *   spt_root, spt_base, spt_count n_spt
+ *   node_of_row n_nodes; lo_row, hi_row n_nodes (NaN for upper rows)
+ * Synchronous.
+ */
+int lodgs_scene_export(const lodgs_scene *scene, float *node_rec, int64_t *left, int64_t *right,
+                       int64_t *up_node, int32_t *up_kind, int64_t *up_parent, int64_t *up_ref,
+                       int64_t *spt_root, int64_t *spt_base, int64_t *spt_count,
+                       int64_t *node_of_row, float *lo_row, float *hi_row);
+
+/* Per-view state: selection, projected splats, sorted pairs and workspace.
+ * Buffers grow on demand; a frame may be reused for any camera and resolution
+ * of its scene.  A frame must not be used by two streams at once. */
+int lodgs_frame_create(lodgs_scene *scene, lodgs_frame **out);
+void lodgs_frame_free(lodgs_frame *frame);
+
+/*
+ * LoD cut for one camera (Algorithm 1 on the upper hierarchy with frustum
+ * culling, Sec. 4.3; Algorithm 2 per SPT at the shared root distance, Eq. 4).
+ * A node is fine enough when its projected size f*S/d <= tau.  The selected
+ * render rows (ascending) stay in the frame.  Asynchronous on `stream`.
+ */
+int lodgs_select_lod(lodgs_scene *scene, const lodgs_camera *cam, lodgs_frame *frame, void *stream);
+
+/* Device pointer to the frame's selected rows (uint32, ascending) and, after a
+ * stream sync, their count. */
+int lodgs_frame_selection(lodgs_frame *frame, const uint32_t **d_rows, int64_t *n_selected);
+
+/*
+ * Render the frame's selection (Eq. 1-2): EWA projection with SH colour, tile x
+ * depth sort, front-to-back blending per 16x16 tile with early stop at
+ * transmittance 1e-4.
+ *   rows:  device records in render-row order (NULL = the scene's own)
+ *   bg:    host RGB background (NULL = black)
+ *   image: device float32 H x W x 3, caller-owned
+ * Asynchronous.  If a workspace buffer was too small the frame records
+ * LODGS_E_CAPACITY in its status (lodgs_frame_get_stats), grows the buffer at
+ * the next call, and the image must be rendered again.
+ */
+int lodgs_render(lodgs_scene *scene, lodgs_frame *frame, const float *rows, const float *bg,
+                 float *image, void *stream);
+
+/*
+ * Backward of lodgs_render for the same frame, rows and bg: transmittance is
+ * recomputed per tile (nothing per pixel is stored by the forward).
+ *   dL_dimage: device H x W x 3
+ *   grad_rows: device, caller-owned.  dense == 0: n_selected x stride rows, row i
+ *              for the i-th selected node (lodgs_frame_selection order);
+ *              dense != 0: n_nodes x stride by render row, only selected rows
+ *              are written (the caller zeroes the rest).
+ * Gradients are w.r.t. the stored record values (quaternion normalisation
+ * included).  Asynchronous.
+ */
+int lodgs_render_backward(lodgs_scene *scene, lodgs_frame *frame, const float *rows, const float *bg,
+                          const float *dL_dimage, float *grad_rows, int dense, void *stream);
+
+/* Counters of the last select/render on this frame (blocks until `stream`,
+ * the stream the frame last ran on, is idle). */
+int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);
+
+/*
+ * Copy the frame's last render products to host buffers (inspection and
+ * tests; any pointer may be NULL to skip).  Blocks until the frame's stream is
+ * idle.
+ *   pair_index  n_pairs uint32: selected index of each (tile, depth)-sorted pair
+ *   ranges      2 x n_tiles uint32: [start, end) of each tile's pairs
+ *   splats      n_selected x 9 float32: u, v, A, B, C (conic of Eq. 2), opacity, r, g, b
+ *   depth_key   n_selected uint32: float32 bits of the view depth (0xffffffff if invisible)
+ *   cap_pairs   capacity of pair_index in elements (LODGS_E_INVALID if too small)
+ */
+int lodgs_frame_export(lodgs_frame *frame, uint32_t *pair_index, int64_t cap_pairs, uint32_t *ranges,
+                       float *splats, uint32_t *depth_key);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LODGS_H */

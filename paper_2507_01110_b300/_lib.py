@@ -1,0 +1,93 @@
+"""ctypes declarations of liblodgs.so (include/lodgs.h).  Marshalling only.
+
+The library is loaded from this package's folder; if it is missing or fails to
+load, every call raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblodgs.so")
+
+LODGS_OK = 0
+LODGS_E_INVALID = -1
+LODGS_E_OOM = -2
+LODGS_E_CUDA = -3
+LODGS_E_TIMEOUT = -4
+LODGS_E_STATE = -5
+LODGS_E_CAPACITY = -6
+_NAMES = {-1: "INVALID", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", -6: "CAPACITY"}
+
+
+class LodgsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lodgs error {code} ({_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("pos", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("tau", C.c_float), ("znear", C.c_float)]
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("spt_volume", C.c_float), ("kappa", C.c_float)]
+
+
+class SceneInfo(C.Structure):
+    _fields_ = [("n_leaves", C.c_int64), ("n_nodes", C.c_int64), ("n_upper", C.c_int64),
+                ("n_upper_rows", C.c_int64), ("n_spt", C.c_int64), ("sh_degree", C.c_int32),
+                ("stride", C.c_int32), ("d_rows", C.c_void_p)]
+
+
+class FrameStats(C.Structure):
+    _fields_ = [("n_selected", C.c_int64), ("n_upper_selected", C.c_int64), ("n_spt_cut", C.c_int64),
+                ("n_spt_scanned", C.c_int64), ("n_visible", C.c_int64), ("n_pairs", C.c_int64),
+                ("status", C.c_int32), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+_lib = None
+
+_P = C.c_void_p
+_SIGS = {
+    "lodgs_last_error": (C.c_char_p, []),
+    "lodgs_version": (C.c_char_p, []),
+    "lodgs_build_hierarchy": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.POINTER(BuildParams), C.POINTER(_P)]),
+    "lodgs_scene_free": (None, [_P]),
+    "lodgs_scene_get_info": (C.c_int, [_P, C.POINTER(SceneInfo)]),
+    "lodgs_scene_export": (C.c_int, [_P] + [_P] * 13),
+    "lodgs_frame_create": (C.c_int, [_P, C.POINTER(_P)]),
+    "lodgs_frame_free": (None, [_P]),
+    "lodgs_select_lod": (C.c_int, [_P, C.POINTER(Camera), _P, _P]),
+    "lodgs_frame_selection": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_int64)]),
+    "lodgs_render": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, _P]),
+    "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
+    "lodgs_frame_export": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
+}
+
+# every symbol include/lodgs.h declares
+EXPORTED = tuple(_SIGS.keys())
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LodgsError(LODGS_E_STATE, f"{LIB_PATH} is missing: build it with "
+                             "`python -m paper_2507_01110_b300.build` (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != LODGS_OK:
+        raise LodgsError(rc, lib().lodgs_last_error().decode(errors="replace"))

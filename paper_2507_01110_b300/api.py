@@ -1,0 +1,227 @@
+"""Python binding of the C ABI (include/lodgs.h), same names, torch for memory.
+
+Every step of the render path runs in liblodgs.so; this module only converts
+arguments (torch tensors -> device pointers, cameras -> structs) and retries a
+frame once its workspace has grown (LODGS_E_CAPACITY).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import Camera as _Cam, check, lib
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous() and t.dtype == torch.float32, "need a contiguous float32 CUDA tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class _DeviceArray:
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 3, "strides": None}
+
+
+def _device_view(ptr: int, shape, typestr: str) -> torch.Tensor:
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
+
+
+def camera_struct(cam) -> _Cam:
+    """Convert a synth.Camera-like object (R, pos, fx, fy, cx, cy, width, height, tau, znear)."""
+    c = _Cam()
+    R = np.asarray(cam.R, dtype=np.float32).reshape(9)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.pos[i] = float(np.float32(cam.pos[i]))
+    c.fx, c.fy, c.cx, c.cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.tau, c.znear = float(np.float32(cam.tau)), float(np.float32(cam.znear))
+    return c
+
+
+class Scene:
+    """A built scene (library-owned device memory)."""
+
+    def __init__(self, handle: C.c_void_p):
+        self._h = handle
+        info = _lib.SceneInfo()
+        check(lib().lodgs_scene_get_info(self._h, C.byref(info)))
+        self.n_leaves, self.n_nodes = info.n_leaves, info.n_nodes
+        self.n_upper, self.n_upper_rows, self.n_spt = info.n_upper, info.n_upper_rows, info.n_spt
+        self.sh_degree, self.stride = info.sh_degree, info.stride
+        self._rows_ptr = info.d_rows
+
+    @property
+    def handle(self):
+        return self._h
+
+    def rows(self) -> torch.Tensor:
+        """The scene's node records in render-row order (n_nodes x stride), a
+        zero-copy view of library-owned device memory valid while the scene lives."""
+        return _device_view(self._rows_ptr, (self.n_nodes, self.stride), "<f4")
+
+    def export(self) -> dict:
+        M, U, S, st = self.n_nodes, self.n_upper, self.n_spt, self.stride
+        a = {
+            "node_rec": np.zeros((M, st), np.float32), "left": np.zeros(M, np.int64), "right": np.zeros(M, np.int64),
+            "up_node": np.zeros(U, np.int64), "up_kind": np.zeros(U, np.int32), "up_parent": np.zeros(U, np.int64),
+            "up_ref": np.zeros(U, np.int64), "spt_root": np.zeros(max(S, 1), np.int64),
+            "spt_base": np.zeros(max(S, 1), np.int64), "spt_count": np.zeros(max(S, 1), np.int64),
+            "node_of_row": np.zeros(M, np.int64), "lo_row": np.zeros(M, np.float32), "hi_row": np.zeros(M, np.float32),
+        }
+        order = ["node_rec", "left", "right", "up_node", "up_kind", "up_parent", "up_ref", "spt_root", "spt_base",
+                 "spt_count", "node_of_row", "lo_row", "hi_row"]
+        check(lib().lodgs_scene_export(self._h, *[C.c_void_p(a[k].ctypes.data) for k in order]))
+        for k in ("spt_root", "spt_base", "spt_count"):
+            a[k] = a[k][:S]
+        a.update({"n_upper": U, "n_spt": S, "n_upper_rows": self.n_upper_rows, "stride": st,
+                  "degree": self.sh_degree, "n_leaves": self.n_leaves})
+        return a
+
+    def close(self):
+        if self._h:
+            lib().lodgs_scene_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Frame:
+    """Per-view state of a scene (selection, splats, sorted pairs)."""
+
+    def __init__(self, scene: Scene):
+        self.scene = scene
+        h = C.c_void_p()
+        check(lib().lodgs_frame_create(scene.handle, C.byref(h)))
+        self._h = h
+        self.camera = None
+        self.bg = (0.0, 0.0, 0.0)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        s = _lib.FrameStats()
+        check(lib().lodgs_frame_get_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _lib.FrameStats._fields_}
+
+    def selection(self) -> torch.Tensor:
+        """Selected render rows (int64, ascending) copied from the device."""
+        p = C.c_void_p()
+        n = C.c_int64()
+        check(lib().lodgs_frame_selection(self._h, C.byref(p), C.byref(n)))
+        if n.value == 0:
+            return torch.zeros(0, dtype=torch.int64, device="cuda")
+        return _device_view(p.value, (int(n.value),), "<u4").to(torch.int64)
+
+    def export(self) -> dict:
+        """Sorted pair order, tile ranges, splats and depth keys of the last render."""
+        st = self.stats()
+        cam = self.camera
+        n_tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+        pairs = np.zeros(max(st["n_pairs"], 1), np.uint32)
+        ranges = np.zeros((n_tiles, 2), np.uint32)
+        spl = np.zeros((max(st["n_selected"], 1), 9), np.float32)
+        keys = np.zeros(max(st["n_selected"], 1), np.uint32)
+        check(lib().lodgs_frame_export(self._h, C.c_void_p(pairs.ctypes.data), C.c_int64(pairs.size),
+                                       C.c_void_p(ranges.ctypes.data), C.c_void_p(spl.ctypes.data),
+                                       C.c_void_p(keys.ctypes.data)))
+        return {"pair_i": pairs[: st["n_pairs"]], "ranges": ranges, "splats": spl[: st["n_selected"]],
+                "depth_key": keys[: st["n_selected"]], "stats": st}
+
+    def close(self):
+        if self._h:
+            lib().lodgs_frame_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_hierarchy(leaves, sh_degree: int, spt_volume: float, kappa: float) -> Scene:
+    """Leaves (n x stride float32, numpy or torch) -> Scene.  See lodgs_build_hierarchy."""
+    lib()
+    if isinstance(leaves, torch.Tensor):
+        t = leaves.contiguous().to(torch.float32)
+        on_dev = int(t.is_cuda)
+        ptr = C.c_void_p(t.data_ptr())
+        keep = t
+        n = t.shape[0]
+    else:
+        a = np.ascontiguousarray(leaves, dtype=np.float32)
+        on_dev, ptr, keep, n = 0, C.c_void_p(a.ctypes.data), a, a.shape[0]
+    p = _lib.BuildParams(float(spt_volume), float(kappa))
+    h = C.c_void_p()
+    check(lib().lodgs_build_hierarchy(ptr, C.c_int64(n), C.c_int(sh_degree), C.c_int(on_dev), C.byref(p), C.byref(h)))
+    del keep
+    return Scene(h)
+
+
+def select_lod(scene: Scene, camera, frame: Frame | None = None, stream=None) -> Frame:
+    """LoD cut for one camera; the selection stays in the returned frame."""
+    fr = frame if frame is not None else Frame(scene)
+    cs = camera_struct(camera)
+    check(lib().lodgs_select_lod(scene.handle, C.byref(cs), fr.handle, _stream_ptr(stream)))
+    fr.camera = camera
+    return fr
+
+
+def render(scene: Scene, frame: Frame, rows: torch.Tensor | None = None, bg=(0.0, 0.0, 0.0),
+           image: torch.Tensor | None = None, stream=None, check_capacity: bool = True) -> torch.Tensor:
+    """Render the frame's selection into an H x W x 3 float32 CUDA tensor.
+
+    With check_capacity the call synchronises the stream, and if a workspace
+    buffer was too small (the buffers then grow) renders again."""
+    cam = frame.camera
+    if image is None:
+        image = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    bgv = (C.c_float * 3)(*[float(b) for b in bg])
+    frame.bg = tuple(float(b) for b in bg)
+    for _ in range(4):
+        check(lib().lodgs_render(scene.handle, frame.handle, _ptr(rows), bgv, _ptr(image), _stream_ptr(stream)))
+        if not check_capacity:
+            return image
+        st = frame.stats()
+        if st["status"] != _lib.LODGS_E_CAPACITY:
+            check(st["status"])
+            return image
+    raise _lib.LodgsError(_lib.LODGS_E_CAPACITY, "workspace did not converge")
+
+
+def render_backward(scene: Scene, frame: Frame, dL_dimage: torch.Tensor, rows: torch.Tensor | None = None,
+                    grad: torch.Tensor | None = None, dense: bool = False, n_selected: int | None = None,
+                    stream=None) -> torch.Tensor:
+    """Gradients of the frame's last render w.r.t. the records.  Sparse: one row per
+    selected node (selection order); dense: n_nodes x stride with selected rows written."""
+    if grad is None:
+        if dense:
+            grad = torch.zeros((scene.n_nodes, scene.stride), dtype=torch.float32, device="cuda")
+        else:
+            if n_selected is None:
+                n_selected = frame.stats()["n_selected"]
+            grad = torch.empty((max(n_selected, 1), scene.stride), dtype=torch.float32, device="cuda")
+    bgv = (C.c_float * 3)(*frame.bg)
+    dL = dL_dimage.contiguous()
+    check(lib().lodgs_render_backward(scene.handle, frame.handle, _ptr(rows), bgv, _ptr(dL), _ptr(grad),
+                                      C.c_int(int(dense)), _stream_ptr(stream)))
+    return grad

@@ -1,0 +1,385 @@
+// C ABI of liblodgs: argument checks, scene and frame lifetime, workspace
+// growth, and the order of the per-view stages.  No exception crosses the ABI.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lodgs_internal.cuh"
+
+namespace lodgs {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LODGS_E_OOM : LODGS_E_CUDA;
+}
+
+// Camera constants in float32 (host).  The LoD test compares tau*d/f with the
+// node size; culling uses the four side planes through the camera centre and
+// the near plane; the EWA Jacobian is clamped at 1.3x the half field of view.
+CamK make_camk(const lodgs_camera &c) {
+    CamK k;
+    memcpy(k.R, c.R, sizeof(k.R));
+    memcpy(k.pos, c.pos, sizeof(k.pos));
+    k.fx = c.fx; k.fy = c.fy; k.cx = c.cx; k.cy = c.cy;
+    k.W = c.width; k.H = c.height;
+    k.TX = (c.width + TILE - 1) / TILE;
+    k.TY = (c.height + TILE - 1) / TILE;
+    k.znear = c.znear;
+    k.inv_k = c.tau / c.fx;
+    float fW = (float)c.width, fH = (float)c.height;
+    k.limx = 1.3f * ((0.5f * fW) / c.fx);
+    k.limy = 1.3f * ((0.5f * fH) / c.fy);
+    float l = sqrtf(c.fx * c.fx + c.cx * c.cx);
+    k.plane[0][0] = c.fx / l; k.plane[0][1] = 0.0f; k.plane[0][2] = c.cx / l;
+    float wr = fW - c.cx;
+    l = sqrtf(c.fx * c.fx + wr * wr);
+    k.plane[1][0] = -c.fx / l; k.plane[1][1] = 0.0f; k.plane[1][2] = wr / l;
+    l = sqrtf(c.fy * c.fy + c.cy * c.cy);
+    k.plane[2][0] = 0.0f; k.plane[2][1] = c.fy / l; k.plane[2][2] = c.cy / l;
+    float hb = fH - c.cy;
+    l = sqrtf(c.fy * c.fy + hb * hb);
+    k.plane[3][0] = 0.0f; k.plane[3][1] = -c.fy / l; k.plane[3][2] = hb / l;
+    return k;
+}
+
+}  // namespace lodgs
+
+using namespace lodgs;
+
+struct lodgs_frame {
+    lodgs_scene *scene = nullptr;
+    FrameBufs f;
+    uint32_t *h_cnt = nullptr;          // pinned mirror of the device counters
+    cudaStream_t stream = 0;
+    CamK k{};
+    bool selected = false, rendered = false;
+    uint64_t want_sel = 0, want_pairs = 0;
+};
+
+namespace {
+
+bool camera_ok(const lodgs_camera *c) {
+    return c && c->width > 0 && c->height > 0 && c->width <= 65535 * TILE && c->height <= 65535 * TILE &&
+           c->fx > 0 && c->fy > 0 && c->tau > 0 && c->znear > 0 && isfinite(c->fx) && isfinite(c->fy) &&
+           isfinite(c->cx) && isfinite(c->cy) && isfinite(c->tau);
+}
+
+template <typename T>
+int grow(T *&p, uint64_t &cap, uint64_t want, size_t elem_per = 1) {
+    if (want <= cap && p) return LODGS_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    LODGS_CUDA(cudaMalloc((void **)&p, std::max<uint64_t>(want, 1) * elem_per * sizeof(T)));
+    cap = want;
+    return LODGS_OK;
+}
+
+int ensure_sel(lodgs_frame *fr, uint64_t want) {
+    FrameBufs &f = fr->f;
+    if (want <= f.cap_sel && f.sp_a) return LODGS_OK;
+    want = std::min<uint64_t>(std::max<uint64_t>(want, 1024), (uint64_t)fr->scene->n_nodes);
+    uint64_t c;
+#define G1(ptr, per)                                  \
+    c = f.cap_sel;                                    \
+    if (int r_ = grow(ptr, c, want, per)) return r_;
+    G1(f.sp_a, 1) G1(f.sp_b, 1) G1(f.sp_c, 1) G1(f.dkey, 1) G1(f.dval, 1) G1(f.dkey_alt, 1) G1(f.dval_alt, 1)
+    G1(f.rect, 1) G1(f.ntiles, 1) G1(f.nt_sorted, 1) G1(f.pair_off, 1) G1(f.g2d, 9)
+#undef G1
+    f.cap_sel = want;
+    return LODGS_OK;
+}
+
+int ensure_pairs(lodgs_frame *fr, uint64_t want) {
+    FrameBufs &f = fr->f;
+    if (want <= f.cap_pairs && f.pkey) return LODGS_OK;
+    want = std::max<uint64_t>(want, 1 << 16);
+    if (want > 0xffffffffull) { set_error("render: more than 2^32 (Gaussian, tile) pairs"); return LODGS_E_INVALID; }
+    uint64_t c;
+    c = f.cap_pairs; if (int r = grow(f.pkey, c, want)) return r;
+    c = f.cap_pairs; if (int r = grow(f.pval, c, want)) return r;
+    c = f.cap_pairs; if (int r = grow(f.pkey_alt, c, want)) return r;
+    c = f.cap_pairs; if (int r = grow(f.pval_alt, c, want)) return r;
+    f.cap_pairs = want;
+    return LODGS_OK;
+}
+
+void free_frame_bufs(FrameBufs &f) {
+    void *ps[] = {f.cnt, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
+                  f.sort_hist, f.sp_a, f.sp_b, f.sp_c, f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.rect, f.ntiles,
+                  f.nt_sorted, f.pair_off, f.g2d, f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.ranges};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    f = FrameBufs();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lodgs_last_error(void) { return g_err.c_str(); }
+const char *lodgs_version(void) { return "lodgs 0.1 (sm_103a)"; }
+
+int lodgs_build_hierarchy(const float *leaves, int64_t n, int sh_degree, int leaves_on_device,
+                          const lodgs_build_params *params, lodgs_scene **out) {
+    if (!out) { set_error("build_hierarchy: out is NULL"); return LODGS_E_INVALID; }
+    *out = nullptr;
+    if (!leaves || n < 1 || sh_degree < 0 || sh_degree > 3 || !params) {
+        set_error("build_hierarchy: need leaves, n >= 1, 0 <= sh_degree <= 3, params");
+        return LODGS_E_INVALID;
+    }
+    if (!(params->spt_volume > 0) || !(params->kappa > 0)) {
+        set_error("build_hierarchy: spt_volume and kappa must be > 0");
+        return LODGS_E_INVALID;
+    }
+    lodgs_scene *sc = new (std::nothrow) lodgs_scene();
+    if (!sc) { set_error("build_hierarchy: host allocation failed"); return LODGS_E_OOM; }
+    int rc = build_scene(leaves, n, sh_degree, leaves_on_device, *params, sc);
+    if (rc) {
+        free_scene(sc);
+        delete sc;
+        return rc;
+    }
+    *out = sc;
+    return LODGS_OK;
+}
+
+void lodgs_scene_free(lodgs_scene *scene) {
+    if (!scene) return;
+    free_scene(scene);
+    delete scene;
+}
+
+int lodgs_scene_get_info(const lodgs_scene *sc, lodgs_scene_info *info) {
+    if (!sc || !info) { set_error("scene_get_info: NULL argument"); return LODGS_E_INVALID; }
+    info->n_leaves = sc->n_leaves; info->n_nodes = sc->n_nodes; info->n_upper = sc->n_upper;
+    info->n_upper_rows = sc->n_upper_rows; info->n_spt = sc->n_spt;
+    info->sh_degree = sc->sh_degree; info->stride = sc->stride; info->d_rows = sc->d_rows;
+    return LODGS_OK;
+}
+
+int lodgs_scene_export(const lodgs_scene *sc, float *node_rec, int64_t *left, int64_t *right, int64_t *up_node,
+                       int32_t *up_kind, int64_t *up_parent, int64_t *up_ref, int64_t *spt_root, int64_t *spt_base,
+                       int64_t *spt_count, int64_t *node_of_row, float *lo_row, float *hi_row) {
+    if (!sc) { set_error("scene_export: NULL scene"); return LODGS_E_INVALID; }
+    const int64_t M = sc->n_nodes, U = sc->n_upper, S = sc->n_spt;
+    if (node_rec) LODGS_CUDA(cudaMemcpy(node_rec, sc->d_node_rec, (size_t)M * sc->stride * 4, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> t32(std::max<int64_t>(M, 1));
+    auto widen = [&](int64_t *dst, const int32_t *src, int64_t n) -> int {
+        if (!dst) return LODGS_OK;
+        LODGS_CUDA(cudaMemcpy(t32.data(), src, n * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) dst[i] = t32[i];
+        return LODGS_OK;
+    };
+    if (int r = widen(left, sc->d_left, M)) return r;
+    if (int r = widen(right, sc->d_right, M)) return r;
+    if (int r = widen(up_node, sc->d_up_node, U)) return r;
+    if (int r = widen(spt_root, sc->d_spt_root, S)) return r;
+    if (int r = widen(node_of_row, sc->d_node_of_row, M)) return r;
+    if (up_kind || up_parent || up_ref) {
+        std::vector<UpperEntry> ue(std::max<int64_t>(U, 1));
+        LODGS_CUDA(cudaMemcpy(ue.data(), sc->d_upper, U * sizeof(UpperEntry), cudaMemcpyDeviceToHost));
+        for (int64_t u = 0; u < U; ++u) {
+            if (up_kind) up_kind[u] = ue[u].kind;
+            if (up_parent) up_parent[u] = ue[u].parent;
+            if (up_ref) up_ref[u] = ue[u].ref;
+        }
+    }
+    if (spt_base || spt_count) {
+        std::vector<uint32_t> b(S + 1);
+        LODGS_CUDA(cudaMemcpy(b.data(), sc->d_spt_base, (S + 1) * 4, cudaMemcpyDeviceToHost));
+        for (int64_t j = 0; j < S; ++j) {
+            if (spt_base) spt_base[j] = b[j];
+            if (spt_count) spt_count[j] = (int64_t)b[j + 1] - b[j];
+        }
+    }
+    if (lo_row) LODGS_CUDA(cudaMemcpy(lo_row, sc->d_lo, M * 4, cudaMemcpyDeviceToHost));
+    if (hi_row) LODGS_CUDA(cudaMemcpy(hi_row, sc->d_hi, M * 4, cudaMemcpyDeviceToHost));
+    return LODGS_OK;
+}
+
+int lodgs_frame_create(lodgs_scene *sc, lodgs_frame **out) {
+    if (!sc || !out) { set_error("frame_create: NULL argument"); return LODGS_E_INVALID; }
+    *out = nullptr;
+    lodgs_frame *fr = new (std::nothrow) lodgs_frame();
+    if (!fr) { set_error("frame_create: host allocation failed"); return LODGS_E_OOM; }
+    fr->scene = sc;
+    FrameBufs &f = fr->f;
+    const int64_t M = sc->n_nodes, S = sc->n_spt;
+    cudaError_t e = cudaSuccess;
+#define AL(p, n)                                                                  \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p, std::max<size_t>((size_t)(n), 1) * sizeof(*p));
+    AL(f.cnt, C_COUNT) AL(f.sel_rows, M) AL(f.emit_j, S) AL(f.emit_x, S) AL(f.high, S + 1) AL(f.work_off, S + 1)
+    AL(f.block_counts, 1024) AL(f.scan_bsum, SCAN_GRID) AL(f.sort_hist, 256 * SORT_GRID)
+#undef AL
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&fr->h_cnt, C_COUNT * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        free_frame_bufs(f);
+        if (fr->h_cnt) cudaFreeHost(fr->h_cnt);
+        delete fr;
+        return cuda_fail(e, "frame_create");
+    }
+    memset(fr->h_cnt, 0, C_COUNT * sizeof(uint32_t));
+    int rc = ensure_sel(fr, std::min<int64_t>(M, 1 << 20));
+    if (!rc) rc = ensure_pairs(fr, 1 << 22);
+    if (rc) { lodgs_frame_free(fr); return rc; }
+    *out = fr;
+    return LODGS_OK;
+}
+
+void lodgs_frame_free(lodgs_frame *fr) {
+    if (!fr) return;
+    cudaStreamSynchronize(fr->stream);
+    free_frame_bufs(fr->f);
+    if (fr->h_cnt) cudaFreeHost(fr->h_cnt);
+    delete fr;
+}
+
+int lodgs_select_lod(lodgs_scene *sc, const lodgs_camera *cam, lodgs_frame *fr, void *stream) {
+    if (!sc || !fr || fr->scene != sc) { set_error("select_lod: frame does not belong to scene"); return LODGS_E_INVALID; }
+    if (!camera_ok(cam)) { set_error("select_lod: invalid camera"); return LODGS_E_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream;
+    fr->k = make_camk(*cam);
+    fr->stream = st;
+    LODGS_CUDA(cudaMemsetAsync(fr->f.cnt, 0, C_COUNT * sizeof(uint32_t), st));
+    int rc = launch_select(sc, fr->k, fr->f, st);
+    if (rc) return rc;
+    fr->selected = true;
+    fr->rendered = false;
+    return LODGS_OK;
+}
+
+int lodgs_frame_selection(lodgs_frame *fr, const uint32_t **d_rows, int64_t *n_selected) {
+    if (!fr || !fr->selected) { set_error("frame_selection: no selection"); return LODGS_E_STATE; }
+    if (d_rows) *d_rows = fr->f.sel_rows;
+    if (n_selected) {
+        LODGS_CUDA(cudaMemcpyAsync(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost, fr->stream));
+        LODGS_CUDA(cudaStreamSynchronize(fr->stream));
+        *n_selected = fr->h_cnt[C_NSEL];
+    }
+    return LODGS_OK;
+}
+
+int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const float *bg, float *image, void *stream) {
+    if (!sc || !fr || fr->scene != sc || !image) { set_error("render: NULL or mismatched argument"); return LODGS_E_INVALID; }
+    if (!fr->selected) { set_error("render: select_lod was not called on this frame"); return LODGS_E_STATE; }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (st != fr->stream) {       // order after the selection's stream
+        cudaEvent_t ev;
+        LODGS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaEventRecord(ev, fr->stream);
+        cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+        fr->stream = st;
+    }
+    if (int r = ensure_sel(fr, fr->want_sel)) return r;
+    if (int r = ensure_pairs(fr, fr->want_pairs)) return r;
+    uint64_t n_tiles = (uint64_t)fr->k.TX * fr->k.TY;
+    uint64_t c = fr->f.cap_tiles;
+    if (int r = grow(fr->f.ranges, c, n_tiles)) return r;
+    fr->f.cap_tiles = c;
+    float b[3] = {0.f, 0.f, 0.f};
+    if (bg) { b[0] = bg[0]; b[1] = bg[1]; b[2] = bg[2]; }
+    // reset the render's counters and status (the selection's counters stay)
+    LODGS_CUDA(cudaMemsetAsync(fr->f.cnt + C_NSEL_EFF, 0, (C_COUNT - C_NSEL_EFF) * sizeof(uint32_t), st));
+    int rc = launch_project(sc, rows ? rows : sc->d_rows, fr->k, fr->f, st);
+    if (!rc) rc = launch_raster(fr->k, fr->f, b, image, st);
+    if (rc) return rc;
+    LODGS_CUDA(cudaMemcpyAsync(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
+    fr->rendered = true;
+    return LODGS_OK;
+}
+
+int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const float *bg,
+                          const float *dL_dimage, float *grad_rows, int dense, void *stream) {
+    if (!sc || !fr || fr->scene != sc || !dL_dimage || !grad_rows) {
+        set_error("render_backward: NULL or mismatched argument");
+        return LODGS_E_INVALID;
+    }
+    if (!fr->rendered) { set_error("render_backward: render was not called on this frame"); return LODGS_E_STATE; }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (st != fr->stream) {
+        cudaEvent_t ev;
+        LODGS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaEventRecord(ev, fr->stream);
+        cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+        fr->stream = st;
+    }
+    float b[3] = {0.f, 0.f, 0.f};
+    if (bg) { b[0] = bg[0]; b[1] = bg[1]; b[2] = bg[2]; }
+    int rc = launch_raster_backward(fr->k, fr->f, b, dL_dimage, st);
+    if (!rc) rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->k, fr->f, grad_rows, dense, st);
+    return rc;
+}
+
+int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {
+    if (!fr || !s) { set_error("frame_get_stats: NULL argument"); return LODGS_E_INVALID; }
+    LODGS_CUDA(cudaStreamSynchronize(fr->stream));
+    if (!fr->rendered) LODGS_CUDA(cudaMemcpy(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost));
+    const uint32_t *h = fr->h_cnt;
+    s->n_selected = h[C_NSEL];
+    s->n_upper_selected = h[C_NUP];
+    s->n_spt_cut = h[C_NEMIT];
+    s->n_spt_scanned = h[C_WORK];
+    s->n_visible = h[C_NVIS];
+    s->n_pairs = h[C_NPAIR];
+    s->width = fr->k.W;
+    s->height = fr->k.H;
+    s->status = LODGS_OK;
+    if (h[C_STATUS] & ST_TIMEOUT) s->status = LODGS_E_TIMEOUT;
+    if (h[C_STATUS] & ST_CAPACITY) {
+        s->status = LODGS_E_CAPACITY;
+        uint64_t ns = h[C_NSEL], np = h[C_NPAIR];
+        if (ns > fr->f.cap_sel) fr->want_sel = std::max<uint64_t>(fr->want_sel, ns + ns / 4);
+        else if (np > fr->f.cap_pairs) fr->want_pairs = std::max<uint64_t>(fr->want_pairs, np + np / 4);
+    }
+    return LODGS_OK;
+}
+
+int lodgs_frame_export(lodgs_frame *fr, uint32_t *pair_index, int64_t cap_pairs, uint32_t *ranges, float *splats,
+                       uint32_t *depth_key) {
+    if (!fr || !fr->rendered) { set_error("frame_export: render was not called on this frame"); return LODGS_E_STATE; }
+    LODGS_CUDA(cudaStreamSynchronize(fr->stream));
+    LODGS_CUDA(cudaMemcpy(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost));
+    if (fr->h_cnt[C_STATUS] & ST_CAPACITY) { set_error("frame_export: last render overflowed"); return LODGS_E_CAPACITY; }
+    const uint64_t np = fr->h_cnt[C_NPAIR_EFF], ns = fr->h_cnt[C_NSEL_EFF];
+    const uint64_t nt = (uint64_t)fr->k.TX * fr->k.TY;
+    if (pair_index) {
+        if ((int64_t)np > cap_pairs) { set_error("frame_export: pair buffer too small"); return LODGS_E_INVALID; }
+        if (np) LODGS_CUDA(cudaMemcpy(pair_index, fr->f.sorted_pval, np * 4, cudaMemcpyDeviceToHost));
+    }
+    if (ranges) LODGS_CUDA(cudaMemcpy(ranges, fr->f.ranges, nt * 8, cudaMemcpyDeviceToHost));
+    if (splats && ns) {
+        std::vector<float4> a(ns), b(ns);
+        std::vector<float> c(ns);
+        LODGS_CUDA(cudaMemcpy(a.data(), fr->f.sp_a, ns * 16, cudaMemcpyDeviceToHost));
+        LODGS_CUDA(cudaMemcpy(b.data(), fr->f.sp_b, ns * 16, cudaMemcpyDeviceToHost));
+        LODGS_CUDA(cudaMemcpy(c.data(), fr->f.sp_c, ns * 4, cudaMemcpyDeviceToHost));
+        for (uint64_t i = 0; i < ns; ++i) {
+            float *o = splats + 9 * i;
+            o[0] = a[i].x; o[1] = a[i].y; o[2] = -2.0f * a[i].z; o[3] = -a[i].w; o[4] = -2.0f * b[i].x;
+            o[5] = b[i].y; o[6] = b[i].z; o[7] = b[i].w; o[8] = c[i];
+        }
+    }
+    if (depth_key && ns) {
+        // the depth sort permuted the keys: undo the permutation with the sorted order
+        const uint32_t *order = fr->f.order;
+        const uint32_t *skeys = order == fr->f.dval ? fr->f.dkey : fr->f.dkey_alt;
+        std::vector<uint32_t> o(ns), kk(ns);
+        LODGS_CUDA(cudaMemcpy(o.data(), order, ns * 4, cudaMemcpyDeviceToHost));
+        LODGS_CUDA(cudaMemcpy(kk.data(), skeys, ns * 4, cudaMemcpyDeviceToHost));
+        for (uint64_t r = 0; r < ns; ++r) depth_key[o[r]] = kk[r];
+    }
+    return LODGS_OK;
+}
+
+}  // extern "C"

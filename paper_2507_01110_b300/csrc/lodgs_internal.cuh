@@ -1,0 +1,168 @@
+// Internal declarations shared by the CUDA translation units of liblodgs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lodgs.h"
+
+namespace lodgs {
+
+// ---- record layout (see include/lodgs.h) ----------------------------------
+constexpr int REC_MU = 0, REC_S = 3, REC_Q = 6, REC_OP = 10, REC_B = 11, REC_F = 14;
+constexpr int KIND_INTERNAL = 0, KIND_LEAF = 1, KIND_SPT = 2;
+constexpr int TILE = 16;
+constexpr int TILE_PIX = TILE * TILE;
+
+inline int sh_count(int degree) { return (degree + 1) * (degree + 1) - 1; }
+inline int record_stride(int degree) { return (14 + 3 * sh_count(degree) + 7) / 8 * 8; }
+
+// ---- per-camera constants, float32 (same expressions as the decisions they feed)
+struct CamK {
+    float R[9];
+    float pos[3];
+    float fx, fy, cx, cy;
+    float inv_k;           // tau / fx
+    float limx, limy;      // 1.3 * tan(half fov)
+    float plane[4][3];     // unit inward normals of the 4 side planes (camera space)
+    float znear;
+    int W, H, TX, TY;
+};
+
+CamK make_camk(const lodgs_camera &c);
+
+// view-space position and camera distance of a world point (float32, evaluated
+// exactly as written; translation units using it are compiled without FMA
+// contraction)
+__device__ __forceinline__ void cam_view(const CamK &k, float mx, float my, float mz, float t[3], float *dist) {
+    float dx = mx - k.pos[0], dy = my - k.pos[1], dz = mz - k.pos[2];
+    *dist = sqrtf((dx * dx + dy * dy) + dz * dz);
+    t[0] = (k.R[0] * dx + k.R[1] * dy) + k.R[2] * dz;
+    t[1] = (k.R[3] * dx + k.R[4] * dy) + k.R[5] * dz;
+    t[2] = (k.R[6] * dx + k.R[7] * dy) + k.R[8] * dz;
+}
+
+// sphere (centre t, radius 3 * maxs) entirely outside the near plane or one of
+// the four side planes
+__device__ __forceinline__ bool cam_culled(const CamK &k, const float t[3], float maxs) {
+    float r = 3.0f * maxs;
+    if (t[2] + r < k.znear) return true;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        float s = (k.plane[p][0] * t[0] + k.plane[p][1] * t[1]) + k.plane[p][2] * t[2];
+        if (s < -r) return true;
+    }
+    return false;
+}
+
+// ---- device status words and counters --------------------------------------
+enum : uint32_t { ST_CAPACITY = 1u, ST_TIMEOUT = 2u };
+enum {
+    C_NSEL = 0,      // selected nodes (a1 + a2)
+    C_NUP = 1,       // of which upper-hierarchy nodes
+    C_NEMIT = 2,     // SPT roots handed to the SPT cut
+    C_WORK = 3,      // SPT entries scanned (sum of the prefixes)
+    C_NSPTSEL = 4,   // SPT entries selected
+    C_NSEL_EFF = 5,  // selected nodes processed by the render (0 on overflow)
+    C_NPAIR = 6,     // (Gaussian, tile) pairs
+    C_NPAIR_EFF = 7, // pairs processed (0 on overflow)
+    C_NVIS = 8,      // visible Gaussians
+    C_STATUS = 9,    // ST_* bits
+    C_COUNT = 16
+};
+
+// ---- scene -----------------------------------------------------------------
+struct UpperEntry {        // 32 bytes, one per upper-hierarchy BFS entry
+    float mu[3];
+    float S;               // size term S_i (float32 decision D3)
+    float maxs;            // max scale (culling sphere radius / 3)
+    int32_t parent;        // upper index of the parent, -1 for the root
+    int32_t kind;          // KIND_*
+    int32_t ref;           // render row (internal/leaf) or SPT index
+};
+
+}  // namespace lodgs
+
+struct lodgs_scene {
+    int64_t n_leaves = 0, n_nodes = 0, n_upper = 0, n_upper_rows = 0, n_spt = 0;
+    int sh_degree = 0, stride = 0;
+    float spt_volume = 0.f, kappa = 0.f;
+    int upper_depth = 0;                         // max depth of the upper hierarchy
+    // device
+    float *d_rows = nullptr;                     // n_nodes x stride, render-row order
+    lodgs::UpperEntry *d_upper = nullptr;        // n_upper
+    uint32_t *d_spt_base = nullptr;              // n_spt + 1
+    float *d_lo = nullptr, *d_hi = nullptr;      // n_nodes (render rows)
+    // canonical structure (device), kept for export and rebuilds
+    float *d_node_rec = nullptr;                 // n_nodes x stride, canonical id order
+    int32_t *d_left = nullptr, *d_right = nullptr;
+    int32_t *d_node_of_row = nullptr;
+    int32_t *d_up_node = nullptr;
+    int32_t *d_spt_root = nullptr;
+};
+
+namespace lodgs {
+
+// Device buffers of one frame (one view).  Capacities are element counts.
+struct FrameBufs {
+    uint32_t *cnt = nullptr;         // C_COUNT device counters
+    // selection (capacity n_nodes / n_spt)
+    uint32_t *sel_rows = nullptr, *emit_j = nullptr, *high = nullptr, *work_off = nullptr;
+    float *emit_x = nullptr;
+    uint32_t *block_counts = nullptr, *scan_bsum = nullptr, *sort_hist = nullptr;
+    // per selected node (capacity cap_sel)
+    float4 *sp_a = nullptr;          // u, v, -A/2, -B        (mean in pixels, scaled conic)
+    float4 *sp_b = nullptr;          // -C/2, opacity, r, g
+    float *sp_c = nullptr;           // b
+    uint32_t *dkey = nullptr, *dval = nullptr, *dkey_alt = nullptr, *dval_alt = nullptr;
+    uint2 *rect = nullptr;           // x0 | y0 << 16, x1 | y1 << 16
+    uint32_t *ntiles = nullptr, *nt_sorted = nullptr, *pair_off = nullptr;
+    float *g2d = nullptr;            // 9 per selected: d/d(u, v, A, B, C, opacity, r, g, b)
+    // pairs (capacity cap_pairs)
+    uint32_t *pkey = nullptr, *pval = nullptr, *pkey_alt = nullptr, *pval_alt = nullptr;
+    // tiles (capacity cap_tiles)
+    uint2 *ranges = nullptr;
+    uint64_t cap_sel = 0, cap_pairs = 0, cap_tiles = 0;
+    // where the last render left its sorted data
+    const uint32_t *order = nullptr;     // selected indices by depth
+    const uint32_t *sorted_pval = nullptr;
+};
+
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+#define LODGS_CUDA(call)                                       \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return lodgs::cuda_fail(_e, #call); \
+    } while (0)
+
+// hierarchy construction (scene.cu)
+int build_scene(const float *leaves, int64_t n, int degree, int on_device, const lodgs_build_params &p,
+                lodgs_scene *sc);
+void free_scene(lodgs_scene *sc);
+
+// radix sort and scans (sort.cu).  All take element counts from device memory so
+// that no host synchronisation is needed between stages.
+struct SortWork {
+    uint32_t *hist = nullptr;       // RADIX * grid
+    size_t hist_cap = 0;
+};
+constexpr int SORT_GRID = 296;      // 2 blocks per SM on 148 SMs
+int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                     const uint32_t *d_n, uint32_t max_n, int begin_bit, int end_bit, uint32_t *hist,
+                     cudaStream_t st, bool *result_in_alt);
+// exclusive scan of n (device count) uint32 values; total written to *d_total (may alias)
+constexpr int SCAN_GRID = 148;
+int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n,
+                   uint32_t *block_sums, uint32_t *d_total, cudaStream_t st);
+// per-view stages (select.cu, project.cu, raster.cu)
+int launch_select(const lodgs_scene *sc, const CamK &k, FrameBufs &f, cudaStream_t st);
+int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, cudaStream_t st);
+int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, cudaStream_t st);
+int launch_raster_backward(const CamK &k, FrameBufs &f, const float bg[3], const float *dL_dimage,
+                           cudaStream_t st);
+int launch_project_backward(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f,
+                            float *grad_rows, int dense, cudaStream_t st);
+}  // namespace lodgs

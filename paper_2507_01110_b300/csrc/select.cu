@@ -1,0 +1,250 @@
+// LoD cut selection (Sec. 4.3, Algorithms 1 and 2).
+//
+// a1  Upper hierarchy.  Algorithm 1 visits an entry iff every ancestor was
+//     visited and descended into (not culled, not fine enough, not an SPT
+//     root).  Each thread decides one entry by evaluating its own test and then
+//     walking its ancestor chain (the upper hierarchy is small: ~2 entries per
+//     SPT), so no level-by-level frontier or host round trip is needed.  An
+//     ordered two-pass compaction emits the selected upper rows and the SPT
+//     roots to cut, both ascending.
+// a2  SPTs.  Per SPT root, a binary search on the descending parent bounds `hi`
+//     gives the prefix [0, high) of possibly selected entries (Alg. 2); a flat,
+//     load-balanced pass over the concatenated prefixes keeps the entries with
+//     lo <= x (Eq. 4) and compacts them in order.
+//
+// Compiled with -fmad=false: the tests are evaluated exactly as written.
+#include "lodgs_internal.cuh"
+
+namespace lodgs {
+namespace {
+
+constexpr int SB = 256;
+constexpr int SEL_GRID = 296;
+
+enum { OUT_NONE = 0, OUT_SELECT = 1, OUT_SPT = 2 };
+
+// Algorithm 1 outcome for upper entry u; *x_out = tau * d / f of the entry.
+__device__ int upper_outcome(const UpperEntry *__restrict__ up, int u, const CamK &k, float *x_out) {
+    UpperEntry e = up[u];
+    float t[3], dist;
+    cam_view(k, e.mu[0], e.mu[1], e.mu[2], t, &dist);
+    if (cam_culled(k, t, e.maxs)) return OUT_NONE;
+    float x = dist * k.inv_k;
+    int out;
+    if (e.kind == KIND_SPT) out = OUT_SPT;
+    else if (e.kind == KIND_LEAF) out = OUT_SELECT;
+    else if (e.S <= x) out = OUT_SELECT;
+    else return OUT_NONE;
+    *x_out = x;
+    for (int a = e.parent; a >= 0; a = up[a].parent) {      // every ancestor must have descended
+        UpperEntry f = up[a];
+        cam_view(k, f.mu[0], f.mu[1], f.mu[2], t, &dist);
+        if (cam_culled(k, t, f.maxs)) return OUT_NONE;
+        if (f.S <= dist * k.inv_k) return OUT_NONE;          // an ancestor was selected
+    }
+    return out;
+}
+
+__device__ __forceinline__ void grid_chunk(uint32_t n, uint32_t &begin, uint32_t &end) {
+    uint32_t G = gridDim.x;
+    uint32_t per = (n + G - 1) / G;
+    per = (per + SB - 1) / SB * SB;
+    uint64_t b = (uint64_t)blockIdx.x * per;
+    begin = b < n ? (uint32_t)b : n;
+    uint64_t e2 = b + per;
+    end = e2 < n ? (uint32_t)e2 : n;
+}
+
+// inclusive block scan of one value per thread (SB threads); returns exclusive
+// prefix, *total gets the block total
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < SB / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < SB / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t excl = (warp ? s_warp[warp - 1] : 0u) + x - v;
+    *total = s_warp[SB / 32 - 1];
+    __syncthreads();
+    return excl;
+}
+
+__device__ __forceinline__ uint32_t block_prefix(const uint32_t *__restrict__ counts, uint32_t *s_warp) {
+    uint32_t s = 0;
+    for (uint32_t b = threadIdx.x; b < blockIdx.x; b += SB) s += counts[b];
+    uint32_t tot;
+    block_scan(s, s_warp, &tot);
+    return tot;
+}
+
+// ---- a1 --------------------------------------------------------------------
+__global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict__ up, uint32_t U, CamK k,
+                                                    uint32_t *__restrict__ bc) {
+    __shared__ uint32_t s_warp[32];
+    uint32_t begin, end;
+    grid_chunk(U, begin, end);
+    uint32_t packed = 0;
+    for (uint32_t u = begin + threadIdx.x; u < end; u += SB) {
+        float x;
+        int o = upper_outcome(up, (int)u, k, &x);
+        packed += o == OUT_SELECT ? 1u : (o == OUT_SPT ? 0x10000u : 0u);
+    }
+    uint32_t tot;
+    block_scan(packed, s_warp, &tot);   // counts per block < 65536 per field (U / grid)
+    if (threadIdx.x == 0) bc[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict__ up, uint32_t U, CamK k,
+                                                    const uint32_t *__restrict__ bc, uint32_t *__restrict__ sel_rows,
+                                                    uint32_t *__restrict__ emit_j, float *__restrict__ emit_x,
+                                                    uint32_t *__restrict__ cnt) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_off_sel, s_off_emit;
+    uint32_t sel_before = 0, emit_before = 0;
+    {
+        uint32_t s = 0, e = 0;
+        for (uint32_t b = threadIdx.x; b < blockIdx.x; b += SB) { s += bc[b] & 0xffffu; e += bc[b] >> 16; }
+        uint32_t ts, te;
+        block_scan(s, s_warp, &ts);
+        block_scan(e, s_warp, &te);
+        sel_before = ts; emit_before = te;
+    }
+    if (threadIdx.x == 0) { s_off_sel = sel_before; s_off_emit = emit_before; }
+    __syncthreads();
+    uint32_t begin, end;
+    grid_chunk(U, begin, end);
+    for (uint32_t t0 = begin; t0 < end; t0 += SB) {
+        uint32_t u = t0 + threadIdx.x;
+        float x = 0.f;
+        int o = u < end ? upper_outcome(up, (int)u, k, &x) : OUT_NONE;
+        uint32_t packed = o == OUT_SELECT ? 1u : (o == OUT_SPT ? 0x10000u : 0u);
+        uint32_t tot;
+        uint32_t ex = block_scan(packed, s_warp, &tot);
+        uint32_t os = s_off_sel, oe = s_off_emit;
+        if (o == OUT_SELECT) sel_rows[os + (ex & 0xffffu)] = (uint32_t)up[u].ref;
+        if (o == OUT_SPT) {
+            emit_j[oe + (ex >> 16)] = (uint32_t)up[u].ref;
+            emit_x[oe + (ex >> 16)] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) { s_off_sel = os + (tot & 0xffffu); s_off_emit = oe + (tot >> 16); }
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        cnt[C_NUP] = s_off_sel;
+        cnt[C_NEMIT] = s_off_emit;
+    }
+}
+
+// ---- a2 --------------------------------------------------------------------
+__global__ void __launch_bounds__(SB) k_spt_high(const uint32_t *__restrict__ cnt_in, const uint32_t *__restrict__ emit_j,
+                                                 const float *__restrict__ emit_x,
+                                                 const uint32_t *__restrict__ spt_base, const float *__restrict__ hi_row,
+                                                 uint32_t *__restrict__ high) {
+    uint32_t n = cnt_in[C_NEMIT];
+    for (uint32_t q = blockIdx.x * SB + threadIdx.x; q < n; q += gridDim.x * SB) {
+        uint32_t j = emit_j[q];
+        float x = emit_x[q];
+        uint32_t base = spt_base[j];
+        uint32_t a = 0, b = spt_base[j + 1] - base;
+        while (a < b) {                                     // first entry with hi <= x
+            uint32_t m = a + (b - a) / 2;
+            if (hi_row[base + m] > x) a = m + 1; else b = m;
+        }
+        high[q] = a;
+    }
+}
+
+__device__ __forceinline__ bool spt_item(uint32_t w, uint32_t n_emit, const uint32_t *__restrict__ work_off,
+                                         const uint32_t *__restrict__ emit_j, const float *__restrict__ emit_x,
+                                         const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
+                                         uint32_t *row) {
+    uint32_t a = 0, b = n_emit;                              // last q with work_off[q] <= w
+    while (b - a > 1) {
+        uint32_t m = a + (b - a) / 2;
+        if (work_off[m] <= w) a = m; else b = m;
+    }
+    uint32_t r = spt_base[emit_j[a]] + (w - work_off[a]);
+    *row = r;
+    return lo_row[r] <= emit_x[a];
+}
+
+__global__ void __launch_bounds__(SB) k_spt_count(const uint32_t *__restrict__ cnt_in, const uint32_t *__restrict__ work_off,
+                                                  const uint32_t *__restrict__ emit_j, const float *__restrict__ emit_x,
+                                                  const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
+                                                  uint32_t *__restrict__ bc) {
+    __shared__ uint32_t s_warp[32];
+    uint32_t W = cnt_in[C_WORK], n_emit = cnt_in[C_NEMIT];
+    uint32_t begin, end;
+    grid_chunk(W, begin, end);
+    uint32_t c = 0;
+    for (uint32_t w = begin + threadIdx.x; w < end; w += SB) {
+        uint32_t row;
+        c += spt_item(w, n_emit, work_off, emit_j, emit_x, spt_base, lo_row, &row) ? 1u : 0u;
+    }
+    uint32_t tot;
+    block_scan(c, s_warp, &tot);
+    if (threadIdx.x == 0) bc[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, const uint32_t *__restrict__ work_off,
+                                                  const uint32_t *__restrict__ emit_j, const float *__restrict__ emit_x,
+                                                  const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
+                                                  const uint32_t *__restrict__ bc, uint32_t *__restrict__ sel_rows) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_off;
+    uint32_t W = cnt[C_WORK], n_emit = cnt[C_NEMIT], n_up = cnt[C_NUP];
+    uint32_t before = block_prefix(bc, s_warp);
+    if (threadIdx.x == 0) s_off = n_up + before;
+    __syncthreads();
+    uint32_t begin, end;
+    grid_chunk(W, begin, end);
+    for (uint32_t t0 = begin; t0 < end; t0 += SB) {
+        uint32_t w = t0 + threadIdx.x, row = 0;
+        bool keep = w < end && spt_item(w, n_emit, work_off, emit_j, emit_x, spt_base, lo_row, &row);
+        uint32_t tot;
+        uint32_t ex = block_scan(keep ? 1u : 0u, s_warp, &tot);
+        uint32_t o = s_off;
+        if (keep) sel_rows[o + ex] = row;
+        __syncthreads();
+        if (threadIdx.x == 0) s_off = o + tot;
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        cnt[C_NSEL] = s_off;
+        cnt[C_NSPTSEL] = s_off - n_up;
+    }
+}
+
+}  // namespace
+
+int launch_select(const lodgs_scene *sc, const CamK &k, FrameBufs &f, cudaStream_t st) {
+    uint32_t U = (uint32_t)sc->n_upper;
+    k_upper_count<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, k, f.block_counts);
+    k_upper_write<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, k, f.block_counts, f.sel_rows, f.emit_j, f.emit_x, f.cnt);
+    k_spt_high<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_hi, f.high);
+    int rc = scan_exclusive(f.high, f.work_off, f.cnt + C_NEMIT, (uint32_t)sc->n_spt, f.scan_bsum, f.cnt + C_WORK, st);
+    if (rc) return rc;
+    k_spt_count<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
+                                         f.block_counts);
+    k_spt_write<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
+                                         f.block_counts, f.sel_rows);
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
+
+}  // namespace lodgs

@@ -1,0 +1,287 @@
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs and exclusive scans.
+//
+// Both run on a fixed grid and read the element count from device memory, so a
+// render needs no host round trip between its stages.  The sort is the
+// reduce-then-scan form: per pass an upsweep builds a digit histogram per block
+// (each block owns one contiguous chunk), a single block scans the
+// digit-major histogram table, and a downsweep ranks each tile of its chunk
+// with warp match/ballot ranking and scatters it.  No block waits on another.
+#include "lodgs_internal.cuh"
+
+namespace lodgs {
+
+namespace {
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int ST_THREADS = 256;                 // 8 warps
+constexpr int ST_WARPS = ST_THREADS / 32;
+constexpr int ST_ITEMS = 8;
+constexpr int ST_TILE = ST_THREADS * ST_ITEMS;  // 2048 keys per tile
+
+__device__ __forceinline__ void chunk_range(uint32_t n, uint32_t &begin, uint32_t &end) {
+    uint32_t G = gridDim.x;
+    uint32_t per = (n + G - 1) / G;
+    per = (per + ST_TILE - 1) / ST_TILE * ST_TILE;
+    uint64_t b = (uint64_t)blockIdx.x * per;
+    begin = b < n ? (uint32_t)b : n;
+    uint64_t e = b + per;
+    end = e < n ? (uint32_t)e : n;
+}
+
+__global__ void __launch_bounds__(ST_THREADS) k_radix_upsweep(const uint32_t *__restrict__ keys,
+                                                              const uint32_t *__restrict__ d_n, int shift,
+                                                              uint32_t mask, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_cnt[ST_WARPS][RADIX];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < ST_WARPS * RADIX; i += ST_THREADS) (&s_cnt[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t begin, end;
+    chunk_range(*d_n, begin, end);
+    for (uint32_t i = begin + tid; i < end; i += ST_THREADS) {
+        uint32_t d = (keys[i] >> shift) & mask;
+        atomicAdd(&s_cnt[warp][d], 1u);
+    }
+    __syncthreads();
+    for (int d = tid; d < RADIX; d += ST_THREADS) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < ST_WARPS; ++w) s += s_cnt[w][d];
+        hist[(size_t)d * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// exclusive scan in place of `len` uint32 values by one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_scan_single(uint32_t *__restrict__ a, int len) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < len; base += 1024) {
+        int i = base + tid;
+        uint32_t v = i < len ? a[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        uint32_t carry = s_carry;
+        uint32_t excl = carry + (warp ? s_warp[warp - 1] : 0u) + x - v;
+        if (i < len) a[i] = excl;
+        __syncthreads();
+        if (tid == 1023) s_carry = carry + s_warp[31];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(ST_THREADS) k_radix_downsweep(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+    uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ d_n, int shift, uint32_t mask,
+    const uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_off[RADIX];
+    __shared__ uint32_t s_tot[RADIX];
+    __shared__ uint32_t s_w[ST_WARPS][RADIX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int d = tid; d < RADIX; d += ST_THREADS) s_off[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+    uint32_t begin, end;
+    chunk_range(*d_n, begin, end);
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t t0 = begin; t0 < end; t0 += ST_TILE) {
+        for (int i = tid; i < ST_WARPS * RADIX; i += ST_THREADS) (&s_w[0][0])[i] = 0;
+        __syncthreads();
+        uint32_t key[ST_ITEMS], val[ST_ITEMS], rank[ST_ITEMS];
+#pragma unroll
+        for (int k = 0; k < ST_ITEMS; ++k) {
+            uint32_t idx = t0 + warp * (32 * ST_ITEMS) + k * 32 + lane;
+            bool ok = idx < end;
+            key[k] = ok ? keys_in[idx] : 0u;
+            val[k] = ok ? vals_in[idx] : 0u;
+            uint32_t d = ok ? ((key[k] >> shift) & mask) : 0xffffu;
+            uint32_t peers = __match_any_sync(0xffffffffu, d);
+            uint32_t prior = 0;
+            if (ok) prior = s_w[warp][d];
+            rank[k] = prior + __popc(peers & lt);
+            __syncwarp();
+            if (ok && (peers & lt) == 0) s_w[warp][d] = prior + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int d = tid; d < RADIX; d += ST_THREADS) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < ST_WARPS; ++w) {
+                uint32_t c = s_w[w][d];
+                s_w[w][d] = run;
+                run += c;
+            }
+            s_tot[d] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < ST_ITEMS; ++k) {
+            uint32_t idx = t0 + warp * (32 * ST_ITEMS) + k * 32 + lane;
+            if (idx < end) {
+                uint32_t d = (key[k] >> shift) & mask;
+                uint32_t pos = s_off[d] + s_w[warp][d] + rank[k];
+                keys_out[pos] = key[k];
+                vals_out[pos] = val[k];
+            }
+        }
+        __syncthreads();
+        for (int d = tid; d < RADIX; d += ST_THREADS) s_off[d] += s_tot[d];
+        __syncthreads();
+    }
+}
+
+// ---- exclusive scan ---------------------------------------------------------
+constexpr int SC_THREADS = 512;
+constexpr int SC_ITEMS = 8;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+__device__ __forceinline__ void scan_chunk(uint32_t n, uint32_t &begin, uint32_t &end) {
+    uint32_t G = gridDim.x;
+    uint32_t per = (n + G - 1) / G;
+    per = (per + SC_TILE - 1) / SC_TILE * SC_TILE;
+    uint64_t b = (uint64_t)blockIdx.x * per;
+    begin = b < n ? (uint32_t)b : n;
+    uint64_t e = b + per;
+    end = e < n ? (uint32_t)e : n;
+}
+
+__device__ __forceinline__ uint32_t block_reduce_add(uint32_t v, uint32_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;   // valid in warp 0
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ in,
+                                                            const uint32_t *__restrict__ d_n,
+                                                            uint32_t *__restrict__ block_sums) {
+    __shared__ uint32_t s_warp[32];
+    uint32_t begin, end;
+    scan_chunk(*d_n, begin, end);
+    uint32_t s = 0;
+    for (uint32_t i = begin + threadIdx.x; i < end; i += SC_THREADS) s += in[i];
+    s = block_reduce_add(s, s_warp);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *in, uint32_t *out,
+                                                          const uint32_t *__restrict__ d_n,
+                                                          const uint32_t *__restrict__ block_sums,
+                                                          uint32_t *d_total) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // offset of this block = sum of the sums of the blocks before it
+    uint32_t pre = 0;
+    for (uint32_t b = tid; b < blockIdx.x; b += SC_THREADS) pre += block_sums[b];
+    pre = block_reduce_add(pre, s_warp);
+    if (tid == 0) s_carry = pre;
+    __syncthreads();
+    uint32_t n = *d_n;
+    uint32_t begin, end;
+    scan_chunk(n, begin, end);
+    for (uint32_t t0 = begin; t0 < end; t0 += SC_TILE) {
+        // each thread owns SC_ITEMS consecutive elements
+        uint32_t v[SC_ITEMS];
+        uint32_t base = t0 + tid * SC_ITEMS;
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < SC_ITEMS; ++k) {
+            uint32_t i = base + k;
+            v[k] = i < end ? in[i] : 0u;
+            sum += v[k];
+        }
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < SC_THREADS / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < SC_THREADS / 32) s_warp[lane] = w;
+        }
+        __syncthreads();
+        uint32_t carry = s_carry;
+        uint32_t run = carry + (warp ? s_warp[warp - 1] : 0u) + x - sum;
+#pragma unroll
+        for (int k = 0; k < SC_ITEMS; ++k) {
+            uint32_t i = base + k;
+            if (i < end) out[i] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (tid == 0) s_carry = carry + s_warp[SC_THREADS / 32 - 1];
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && tid == 0 && d_total) *d_total = s_carry;
+}
+}  // namespace
+
+int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_n,
+                     uint32_t max_n, int begin_bit, int end_bit, uint32_t *hist, cudaStream_t st,
+                     bool *result_in_alt) {
+    bool alt = false;
+    if (max_n == 0 || end_bit <= begin_bit) {
+        *result_in_alt = false;
+        return LODGS_OK;
+    }
+    for (int shift = begin_bit; shift < end_bit; shift += RADIX_BITS) {
+        int bits = end_bit - shift < RADIX_BITS ? end_bit - shift : RADIX_BITS;
+        uint32_t mask = (1u << bits) - 1u;
+        const uint32_t *ki = alt ? keys_alt : keys;
+        const uint32_t *vi = alt ? vals_alt : vals;
+        uint32_t *ko = alt ? keys : keys_alt;
+        uint32_t *vo = alt ? vals : vals_alt;
+        k_radix_upsweep<<<SORT_GRID, ST_THREADS, 0, st>>>(ki, d_n, shift, mask, hist);
+        k_scan_single<<<1, 1024, 0, st>>>(hist, RADIX * SORT_GRID);
+        k_radix_downsweep<<<SORT_GRID, ST_THREADS, 0, st>>>(ki, vi, ko, vo, d_n, shift, mask, hist);
+        alt = !alt;
+    }
+    LODGS_CUDA(cudaGetLastError());
+    *result_in_alt = alt;
+    return LODGS_OK;
+}
+
+int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n, uint32_t *block_sums,
+                   uint32_t *d_total, cudaStream_t st) {
+    (void)max_n;
+    k_scan_reduce<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, d_n, block_sums);
+    k_scan_down<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, out, d_n, block_sums, d_total);
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
+
+}  // namespace lodgs
