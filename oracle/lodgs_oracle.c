@@ -815,8 +815,9 @@ int or_sort_pairs(int64_t n, const int32_t *vis, const int32_t *rect, const uint
 /* ------------------------------------------------------------------------- */
 /* Blend (Eq. 1 and Eq. 2): front-to-back per pixel over its tile's list.      */
 /* Support test D8 in float32; alpha = min(0.99, sigma exp(p)) in float64.    */
-/* A Gaussian whose blend would leave T below 1e-4 is not blended and ends the */
-/* pixel (the 3DGS rasterizer's early stop).                                  */
+/* Eq. 1 is truncated once the transmittance falls below 1e-4: the Gaussian   */
+/* that takes T below the bound is still blended and the pixel stops after    */
+/* it, so the neglected tail is at most 1e-4 times the largest colour.        */
 /* ------------------------------------------------------------------------- */
 static inline float support_p(float u, float v, float A, float B, float C, int px, int py) {
     float dx = u - ((float)px + 0.5f), dy = v - ((float)py + 0.5f);
@@ -841,11 +842,10 @@ int or_blend(int W, int H, const double *bg, const int64_t *tile_start, const in
                 double p = -0.5 * (q[2] * dx * dx + q[4] * dy * dy) - q[3] * dx * dy;
                 double alpha = q[5] * exp(p);
                 if (alpha > ALPHA_MAX) alpha = ALPHA_MAX;
-                double Tn = T * (1.0 - alpha);
-                if (Tn < T_MIN) break;
                 for (int ch = 0; ch < 3; ++ch) C[ch] += q[6 + ch] * alpha * T;
-                T = Tn;
+                T = T * (1.0 - alpha);
                 last = (int32_t)(e - tile_start[t] + 1);
+                if (T < T_MIN) break;
             }
             double *o = image + 3 * ((int64_t)py * W + px);
             for (int ch = 0; ch < 3; ++ch) o[ch] = C[ch] + T * bg[ch];
@@ -886,10 +886,9 @@ int or_blend_backward(int W, int H, const double *bg, const int64_t *tile_start,
                 double G = exp(p), alpha = q[5] * G;
                 int clamped = 0;
                 if (alpha > ALPHA_MAX) { alpha = ALPHA_MAX; clamped = 1; }
-                double Tn = T * (1.0 - alpha);
-                if (Tn < T_MIN) break;
                 li[cnt] = i; la[cnt] = alpha; lT[cnt] = T; lp[cnt] = p; lg[cnt] = G; lclamp[cnt] = clamped; ++cnt;
-                T = Tn;
+                T = T * (1.0 - alpha);
+                if (T < T_MIN) break;
             }
             const double *dC = dL_dimg + 3 * ((int64_t)py * W + px);
             double Rb[3] = {T * bg[0], T * bg[1], T * bg[2]};       /* colour behind, from the back */

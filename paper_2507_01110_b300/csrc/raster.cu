@@ -9,7 +9,9 @@
 // outnumber Gaussians.
 //
 // Blending runs one 256-thread CTA per 16x16 tile; batches of the tile's
-// Gaussians are staged in shared memory.  The support test p >= -4.5 uses
+// Gaussians are staged in shared memory.  Eq. 1 is truncated once a pixel's
+// transmittance falls below 1e-4 (the Gaussian that crosses the bound is still
+// blended), so the neglected tail is at most 1e-4 of the colour.  The support test p >= -4.5 uses
 // explicitly rounded float32 operations (it decides which pixels a Gaussian
 // touches); the alpha, transmittance and colour arithmetic are ordinary fp32.
 // The backward recomputes each pixel's final transmittance and last
@@ -111,11 +113,10 @@ __global__ void __launch_bounds__(RB) k_blend(const uint2 *__restrict__ ranges, 
                 float p = support_p(a, b.x, xc, yc, dx, dy);
                 if (p < SUPPORT_P) continue;
                 float alpha = fminf(ALPHA_MAX, b.y * __expf(p));
-                float Tn = T * (1.0f - alpha);
-                if (Tn < T_MIN) { done = true; break; }
                 float w = alpha * T;
                 c0 += b.z * w; c1 += b.w * w; c2 += s_c[j] * w;
-                T = Tn;
+                T = T * (1.0f - alpha);
+                if (T < T_MIN) { done = true; break; }
             }
         }
     }
@@ -164,10 +165,9 @@ __global__ void __launch_bounds__(RB) k_blend_bwd(const uint2 *__restrict__ rang
                 float p = support_p(a, b.x, xc, yc, dx, dy);
                 if (p < SUPPORT_P) continue;
                 float alpha = fminf(ALPHA_MAX, b.y * __expf(p));
-                float Tn = T * (1.0f - alpha);
-                if (Tn < T_MIN) { done = true; break; }
-                T = Tn;
+                T = T * (1.0f - alpha);
                 last = base - rg.x + j + 1;
+                if (T < T_MIN) { done = true; break; }
             }
         }
     }
