@@ -82,6 +82,9 @@ typedef struct {
     int32_t width, height;
 } lodgs_frame_stats;
 
+/* Number of kernels this library has launched in this process (all streams). */
+uint64_t lodgs_kernel_launches(void);
+
 /* Thread-local message for the last failing call of this thread. */
 const char *lodgs_last_error(void);
 /* Library version string. */
@@ -171,6 +174,24 @@ int lodgs_render_backward(lodgs_scene *scene, lodgs_frame *frame, const float *r
 /* Counters of the last select/render on this frame (blocks until `stream`,
  * the stream the frame last ran on, is idle). */
 int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);
+
+/* Stages timed by lodgs_frame_stage_ms, in order. */
+#define LODGS_STAGE_SELECT 0      /* upper-hierarchy BFS cut + SPT interval test and compaction */
+#define LODGS_STAGE_PROJECT 1     /* gather + EWA projection + SH colour */
+#define LODGS_STAGE_DEPTH_SORT 2  /* stable radix sort of the depth keys */
+#define LODGS_STAGE_EMIT 3        /* tile-count scan and (tile, Gaussian) pair emission */
+#define LODGS_STAGE_TILE_SORT 4   /* stable radix sort of the pairs by tile */
+#define LODGS_STAGE_BLEND 5       /* tile ranges + front-to-back blending */
+#define LODGS_STAGE_BLEND_BWD 6   /* backward of the blend (per-tile recomputation) */
+#define LODGS_STAGE_PROJECT_BWD 7 /* backward of the projection + gradient rows */
+#define LODGS_NUM_STAGES 8
+
+/* Record CUDA events around every stage of this frame (on = 1) or not (0). */
+int lodgs_frame_set_profiling(lodgs_frame *frame, int on);
+/* Device time in milliseconds of each stage of the last select/render/backward
+ * on this frame (LODGS_NUM_STAGES floats; 0 for stages that did not run since
+ * the last select).  Blocks until the frame's stream is idle. */
+int lodgs_frame_stage_ms(lodgs_frame *frame, float *ms);
 
 /*
  * Copy the frame's last render products to host buffers (inspection and

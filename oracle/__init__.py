@@ -227,25 +227,35 @@ def sort_pairs(proj: dict, width: int, height: int) -> dict:
     return {"pair_i": pair_i[: int(npairs[0])].copy(), "tile_start": tile_start, "TX": TX, "TY": TY}
 
 
-def blend(proj: dict, pairs: dict, width: int, height: int, bg=(0.0, 0.0, 0.0)) -> dict:
+def _win(window):
+    if window is None:
+        return None
+    w = np.ascontiguousarray(window, dtype=np.int32)
+    return w
+
+
+def blend(proj: dict, pairs: dict, width: int, height: int, bg=(0.0, 0.0, 0.0), window=None) -> dict:
     img = np.zeros((height, width, 3), dtype=np.float64)
     ncon = np.zeros((height, width), dtype=np.int32)
     tfin = np.zeros((height, width), dtype=np.float64)
     bgv = np.asarray(bg, dtype=np.float64)
     pair_i = pairs["pair_i"] if pairs["pair_i"].size else np.zeros(1, dtype=np.int64)
+    w = _win(window)
     lib().or_blend(C.c_int(width), C.c_int(height), _p(bgv), _p(pairs["tile_start"]), _p(pair_i),
-                   _p(proj["f32"]), _p(proj["f64"]), _p(img), _p(ncon), _p(tfin))
+                   _p(proj["f32"]), _p(proj["f64"]), _p(img), _p(ncon), _p(tfin), _p(w) if w is not None else None)
     return {"image": img, "n_contrib": ncon, "T_final": tfin}
 
 
 def blend_backward(proj: dict, pairs: dict, width: int, height: int, dL_dimg: np.ndarray,
-                   bg=(0.0, 0.0, 0.0)) -> np.ndarray:
+                   bg=(0.0, 0.0, 0.0), window=None) -> np.ndarray:
     g = np.zeros((proj["n"], 9), dtype=np.float64)
     bgv = np.asarray(bg, dtype=np.float64)
     dL = np.ascontiguousarray(dL_dimg, dtype=np.float64)
     pair_i = pairs["pair_i"] if pairs["pair_i"].size else np.zeros(1, dtype=np.int64)
+    w = _win(window)
     lib().or_blend_backward(C.c_int(width), C.c_int(height), _p(bgv), _p(pairs["tile_start"]), _p(pair_i),
-                            _p(proj["f32"]), _p(proj["f64"]), _p(dL), C.c_int64(proj["n"]), _p(g))
+                            _p(proj["f32"]), _p(proj["f64"]), _p(dL), C.c_int64(proj["n"]), _p(g),
+                            _p(w) if w is not None else None)
     return g
 
 
@@ -269,19 +279,20 @@ def sh_eval(degree: int, v: np.ndarray):
     return Y[:K], dY[: 3 * K].reshape(K, 3)
 
 
-def render(scene: dict, cam, bg=(0.0, 0.0, 0.0), cull: bool = True, sel: np.ndarray | None = None) -> dict:
-    """Full forward: select -> project -> sort -> blend."""
+def render(scene: dict, cam, bg=(0.0, 0.0, 0.0), cull: bool = True, sel: np.ndarray | None = None,
+           window=None) -> dict:
+    """Full forward: select -> project -> sort -> blend (blend limited to `window` if given)."""
     stats = None
     if sel is None:
         sel, stats = select(scene, cam, cull)
     proj = project(scene, sel, cam)
     pairs = sort_pairs(proj, cam.width, cam.height)
-    out = blend(proj, pairs, cam.width, cam.height, bg)
+    out = blend(proj, pairs, cam.width, cam.height, bg, window)
     out.update({"sel": sel, "proj": proj, "pairs": pairs, "select_stats": stats})
     return out
 
 
-def render_backward(scene: dict, cam, fwd: dict, dL_dimg: np.ndarray, bg=(0.0, 0.0, 0.0)) -> dict:
-    g2d = blend_backward(fwd["proj"], fwd["pairs"], cam.width, cam.height, dL_dimg, bg)
+def render_backward(scene: dict, cam, fwd: dict, dL_dimg: np.ndarray, bg=(0.0, 0.0, 0.0), window=None) -> dict:
+    g2d = blend_backward(fwd["proj"], fwd["pairs"], cam.width, cam.height, dL_dimg, bg, window)
     grec = project_backward(scene, fwd["sel"], cam, fwd["proj"], g2d)
     return {"g2d": g2d, "g_rec": grec}

@@ -825,11 +825,14 @@ static inline float support_p(float u, float v, float A, float B, float C, int p
     return fmaf(nb * dx, dy, fmaf(nhc * dy, dy, (nha * dx) * dx));
 }
 
+/* win (x0, y0, x1, y1) restricts the work to a pixel window (NULL: all). */
 int or_blend(int W, int H, const double *bg, const int64_t *tile_start, const int64_t *pair_i,
-             const float *f32, const double *f64, double *image, int32_t *n_contrib, double *T_final) {
+             const float *f32, const double *f64, double *image, int32_t *n_contrib, double *T_final,
+             const int32_t *win) {
     int TX = (W + TILE - 1) / TILE;
-    for (int py = 0; py < H; ++py)
-        for (int px = 0; px < W; ++px) {
+    int wx0 = win ? win[0] : 0, wy0 = win ? win[1] : 0, wx1 = win ? win[2] : W, wy1 = win ? win[3] : H;
+    for (int py = wy0; py < wy1; ++py)
+        for (int px = wx0; px < wx1; ++px) {
             int64_t t = (int64_t)(py / TILE) * TX + px / TILE;
             double T = 1.0, C[3] = {0, 0, 0};
             int32_t last = 0;
@@ -861,7 +864,9 @@ int or_blend(int W, int H, const double *bg, const int64_t *tile_start, const in
  *   dC/dc_i = alpha_i T_i,  dC/dalpha_i = c_i T_i - R_i / (1 - alpha_i).
  * Outputs per selected Gaussian: g2d[9i..] = dL/d(u, v, A, B, C, opacity, r, g, b). */
 int or_blend_backward(int W, int H, const double *bg, const int64_t *tile_start, const int64_t *pair_i,
-                      const float *f32, const double *f64, const double *dL_dimg, int64_t n, double *g2d) {
+                      const float *f32, const double *f64, const double *dL_dimg, int64_t n, double *g2d,
+                      const int32_t *win) {
+    int wx0 = win ? win[0] : 0, wy0 = win ? win[1] : 0, wx1 = win ? win[2] : W, wy1 = win ? win[3] : H;
     int TX = (W + TILE - 1) / TILE;
     memset(g2d, 0, sizeof(double) * 9 * (size_t)n);
     int64_t maxlen = 0;
@@ -871,8 +876,8 @@ int or_blend_backward(int W, int H, const double *bg, const int64_t *tile_start,
     double *la = malloc(sizeof(double) * (size_t)(maxlen + 1)), *lT = malloc(sizeof(double) * (size_t)(maxlen + 1));
     double *lp = malloc(sizeof(double) * (size_t)(maxlen + 1)), *lg = malloc(sizeof(double) * (size_t)(maxlen + 1));
     int *lclamp = malloc(sizeof(int) * (size_t)(maxlen + 1));
-    for (int py = 0; py < H; ++py)
-        for (int px = 0; px < W; ++px) {
+    for (int py = wy0; py < wy1; ++py)
+        for (int px = wx0; px < wx1; ++px) {
             int64_t t = (int64_t)(py / TILE) * TX + px / TILE;
             double T = 1.0;
             int64_t cnt = 0;

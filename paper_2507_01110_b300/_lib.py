@@ -18,6 +18,7 @@ LODGS_E_CUDA = -3
 LODGS_E_TIMEOUT = -4
 LODGS_E_STATE = -5
 LODGS_E_CAPACITY = -6
+STAGES = ("select", "project", "depth_sort", "emit", "tile_sort", "blend", "blend_bwd", "project_bwd")
 _NAMES = {-1: "INVALID", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", -6: "CAPACITY"}
 
 
@@ -55,6 +56,7 @@ _P = C.c_void_p
 _SIGS = {
     "lodgs_last_error": (C.c_char_p, []),
     "lodgs_version": (C.c_char_p, []),
+    "lodgs_kernel_launches": (C.c_uint64, []),
     "lodgs_build_hierarchy": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.POINTER(BuildParams), C.POINTER(_P)]),
     "lodgs_scene_free": (None, [_P]),
     "lodgs_scene_get_info": (C.c_int, [_P, C.POINTER(SceneInfo)]),
@@ -67,6 +69,8 @@ _SIGS = {
     "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, _P]),
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
     "lodgs_frame_export": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
+    "lodgs_frame_set_profiling": (C.c_int, [_P, C.c_int]),
+    "lodgs_frame_stage_ms": (C.c_int, [_P, _P]),
 }
 
 # every symbol include/lodgs.h declares

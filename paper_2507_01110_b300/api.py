@@ -131,6 +131,15 @@ class Frame:
             return torch.zeros(0, dtype=torch.int64, device="cuda")
         return _device_view(p.value, (int(n.value),), "<u4").to(torch.int64)
 
+    def set_profiling(self, on: bool = True) -> None:
+        check(lib().lodgs_frame_set_profiling(self._h, C.c_int(int(on))))
+
+    def stage_ms(self) -> dict:
+        """Device milliseconds per stage of the last select/render/backward."""
+        ms = (C.c_float * len(_lib.STAGES))()
+        check(lib().lodgs_frame_stage_ms(self._h, ms))
+        return dict(zip(_lib.STAGES, [float(v) for v in ms]))
+
     def export(self) -> dict:
         """Sorted pair order, tile ranges, splats and depth keys of the last render."""
         st = self.stats()

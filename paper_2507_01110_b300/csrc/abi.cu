@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -13,6 +14,9 @@
 namespace lodgs {
 
 static thread_local std::string g_err;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_err = msg; }
 
@@ -62,6 +66,15 @@ struct lodgs_frame {
     CamK k{};
     bool selected = false, rendered = false;
     uint64_t want_sel = 0, want_pairs = 0;
+    // stage timing: ev[2s] / ev[2s+1] bracket stage s
+    bool prof = false;
+    cudaEvent_t ev[2 * LODGS_NUM_STAGES] = {};
+    bool ran[LODGS_NUM_STAGES] = {};
+    void mark(int stage, int end, cudaStream_t st) {
+        if (!prof) return;
+        cudaEventRecord(ev[2 * stage + end], st);
+        if (end) ran[stage] = true;
+    }
 };
 
 namespace {
@@ -127,6 +140,7 @@ extern "C" {
 
 const char *lodgs_last_error(void) { return g_err.c_str(); }
 const char *lodgs_version(void) { return "lodgs 0.1 (sm_103a)"; }
+uint64_t lodgs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int lodgs_build_hierarchy(const float *leaves, int64_t n, int sh_degree, int leaves_on_device,
                           const lodgs_build_params *params, lodgs_scene **out) {
@@ -238,6 +252,8 @@ int lodgs_frame_create(lodgs_scene *sc, lodgs_frame **out) {
 void lodgs_frame_free(lodgs_frame *fr) {
     if (!fr) return;
     cudaStreamSynchronize(fr->stream);
+    for (cudaEvent_t &e : fr->ev)
+        if (e) cudaEventDestroy(e);
     free_frame_bufs(fr->f);
     if (fr->h_cnt) cudaFreeHost(fr->h_cnt);
     delete fr;
@@ -249,9 +265,12 @@ int lodgs_select_lod(lodgs_scene *sc, const lodgs_camera *cam, lodgs_frame *fr, 
     cudaStream_t st = (cudaStream_t)stream;
     fr->k = make_camk(*cam);
     fr->stream = st;
+    for (bool &r : fr->ran) r = false;
+    fr->mark(LODGS_STAGE_SELECT, 0, st);
     LODGS_CUDA(cudaMemsetAsync(fr->f.cnt, 0, C_COUNT * sizeof(uint32_t), st));
     int rc = launch_select(sc, fr->k, fr->f, st);
     if (rc) return rc;
+    fr->mark(LODGS_STAGE_SELECT, 1, st);
     fr->selected = true;
     fr->rendered = false;
     return LODGS_OK;
@@ -290,9 +309,15 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     if (bg) { b[0] = bg[0]; b[1] = bg[1]; b[2] = bg[2]; }
     // reset the render's counters and status (the selection's counters stay)
     LODGS_CUDA(cudaMemsetAsync(fr->f.cnt + C_NSEL_EFF, 0, (C_COUNT - C_NSEL_EFF) * sizeof(uint32_t), st));
+    fr->mark(LODGS_STAGE_PROJECT, 0, st);
     int rc = launch_project(sc, rows ? rows : sc->d_rows, fr->k, fr->f, st);
-    if (!rc) rc = launch_raster(fr->k, fr->f, b, image, st);
     if (rc) return rc;
+    fr->mark(LODGS_STAGE_PROJECT, 1, st);
+    StageMarks sm{fr->prof ? fr->ev : nullptr};
+    rc = launch_raster(fr->k, fr->f, b, image, st, sm);
+    if (rc) return rc;
+    if (fr->prof)
+        for (int s2 = LODGS_STAGE_DEPTH_SORT; s2 <= LODGS_STAGE_BLEND; ++s2) fr->ran[s2] = true;
     LODGS_CUDA(cudaMemcpyAsync(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
     fr->rendered = true;
     return LODGS_OK;
@@ -316,9 +341,15 @@ int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, c
     }
     float b[3] = {0.f, 0.f, 0.f};
     if (bg) { b[0] = bg[0]; b[1] = bg[1]; b[2] = bg[2]; }
+    fr->mark(LODGS_STAGE_BLEND_BWD, 0, st);
     int rc = launch_raster_backward(fr->k, fr->f, b, dL_dimage, st);
-    if (!rc) rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->k, fr->f, grad_rows, dense, st);
-    return rc;
+    if (rc) return rc;
+    fr->mark(LODGS_STAGE_BLEND_BWD, 1, st);
+    fr->mark(LODGS_STAGE_PROJECT_BWD, 0, st);
+    rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->k, fr->f, grad_rows, dense, st);
+    if (rc) return rc;
+    fr->mark(LODGS_STAGE_PROJECT_BWD, 1, st);
+    return LODGS_OK;
 }
 
 int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {
@@ -341,6 +372,26 @@ int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {
         uint64_t ns = h[C_NSEL], np = h[C_NPAIR];
         if (ns > fr->f.cap_sel) fr->want_sel = std::max<uint64_t>(fr->want_sel, ns + ns / 4);
         else if (np > fr->f.cap_pairs) fr->want_pairs = std::max<uint64_t>(fr->want_pairs, np + np / 4);
+    }
+    return LODGS_OK;
+}
+
+int lodgs_frame_set_profiling(lodgs_frame *fr, int on) {
+    if (!fr) { set_error("frame_set_profiling: NULL frame"); return LODGS_E_INVALID; }
+    if (on)
+        for (cudaEvent_t &e : fr->ev)
+            if (!e) LODGS_CUDA(cudaEventCreate(&e));
+    fr->prof = on != 0;
+    return LODGS_OK;
+}
+
+int lodgs_frame_stage_ms(lodgs_frame *fr, float *ms) {
+    if (!fr || !ms) { set_error("frame_stage_ms: NULL argument"); return LODGS_E_INVALID; }
+    if (!fr->prof) { set_error("frame_stage_ms: profiling is off"); return LODGS_E_STATE; }
+    LODGS_CUDA(cudaStreamSynchronize(fr->stream));
+    for (int s2 = 0; s2 < LODGS_NUM_STAGES; ++s2) {
+        ms[s2] = 0.f;
+        if (fr->ran[s2]) LODGS_CUDA(cudaEventElapsedTime(&ms[s2], fr->ev[2 * s2], fr->ev[2 * s2 + 1]));
     }
     return LODGS_OK;
 }

@@ -131,6 +131,7 @@ struct FrameBufs {
 };
 
 void set_error(const std::string &msg);
+void count_launches(int n);     // process-wide tally of this library's kernel launches
 int cuda_fail(cudaError_t e, const char *what);
 #define LODGS_CUDA(call)                                       \
     do {                                                       \
@@ -157,10 +158,19 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
 constexpr int SCAN_GRID = 148;
 int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n,
                    uint32_t *block_sums, uint32_t *d_total, cudaStream_t st);
+// optional CUDA events bracketing stages (ev[2s], ev[2s+1]); null = off
+struct StageMarks {
+    cudaEvent_t *ev = nullptr;
+    void mark(int stage, int end, cudaStream_t st) const {
+        if (ev) cudaEventRecord(ev[2 * stage + end], st);
+    }
+};
+
 // per-view stages (select.cu, project.cu, raster.cu)
 int launch_select(const lodgs_scene *sc, const CamK &k, FrameBufs &f, cudaStream_t st);
 int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, cudaStream_t st);
-int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, cudaStream_t st);
+int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, cudaStream_t st,
+                  const StageMarks &sm);
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float bg[3], const float *dL_dimage,
                            cudaStream_t st);
 int launch_project_backward(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f,

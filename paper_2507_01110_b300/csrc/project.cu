@@ -340,8 +340,10 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
 
 int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, cudaStream_t st) {
     k_clamp_sel<<<1, 1, 0, st>>>(f.cnt, f.cap_sel);
+    count_launches(1);
     k_project<<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, sc->sh_degree, f.sel_rows, k, f.cnt, f.sp_a, f.sp_b,
                                         f.sp_c, f.dkey, f.dval, f.rect, f.ntiles);
+    count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
 }
@@ -350,6 +352,7 @@ int launch_project_backward(const lodgs_scene *sc, const float *rows, const CamK
                             int dense, cudaStream_t st) {
     k_project_bwd<<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, sc->sh_degree, f.sel_rows, k, f.cnt, f.ntiles, f.g2d,
                                             grad_rows, dense);
+    count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
 }

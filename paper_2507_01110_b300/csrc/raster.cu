@@ -264,29 +264,43 @@ int ceil_log2(uint64_t x) {
 
 }  // namespace
 
-int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, cudaStream_t st) {
+int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, cudaStream_t st,
+                  const StageMarks &sm) {
     bool alt;
+    sm.mark(LODGS_STAGE_DEPTH_SORT, 0, st);
     int rc = radix_sort_pairs(f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, 0, 32,
                               f.sort_hist, st, &alt);
     if (rc) return rc;
     const uint32_t *order = alt ? f.dval_alt : f.dval;
     f.order = order;
+    sm.mark(LODGS_STAGE_DEPTH_SORT, 1, st);
+    sm.mark(LODGS_STAGE_EMIT, 0, st);
     k_gather_nt<<<RGRID, RB, 0, st>>>(order, f.ntiles, f.cnt, f.nt_sorted);
+    count_launches(1);
     rc = scan_exclusive(f.nt_sorted, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
                         f.cnt + C_NPAIR, st);
     if (rc) return rc;
     k_clamp_pairs<<<1, 1, 0, st>>>(f.cnt, f.cap_pairs);
+    count_launches(1);
     k_emit<<<RGRID, RB, 0, st>>>(order, f.ntiles, f.rect, f.pair_off, f.cnt, k.TX, f.pkey, f.pval);
+    count_launches(1);
+    sm.mark(LODGS_STAGE_EMIT, 1, st);
+    sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     rc = radix_sort_pairs(f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.cnt + C_NPAIR_EFF, (uint32_t)f.cap_pairs, 0,
                           ceil_log2(n_tiles), f.sort_hist, st, &alt);
     if (rc) return rc;
     const uint32_t *skey = alt ? f.pkey_alt : f.pkey;
     f.sorted_pval = alt ? f.pval_alt : f.pval;
+    sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
+    sm.mark(LODGS_STAGE_BLEND, 0, st);
     LODGS_CUDA(cudaMemsetAsync(f.ranges, 0, n_tiles * sizeof(uint2), st));
     k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, f.ranges);
+    count_launches(1);
     k_blend<<<(unsigned)n_tiles, RB, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX,
                                               bg[0], bg[1], bg[2], image);
+    count_launches(1);
+    sm.mark(LODGS_STAGE_BLEND, 1, st);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
 }
@@ -296,6 +310,7 @@ int launch_raster_backward(const CamK &k, FrameBufs &f, const float bg[3], const
     LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * 9 * sizeof(float), st));
     k_blend_bwd<<<(unsigned)n_tiles, RB, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H,
                                                   k.TX, bg[0], bg[1], bg[2], dL_dimage, f.g2d);
+    count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
 }

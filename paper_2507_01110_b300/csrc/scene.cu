@@ -466,7 +466,9 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
         CK(cudaMemcpy(box.p, init, sizeof(init), cudaMemcpyHostToDevice));
     }
     k_aabb<<<std::min(nblk(n), 1184), BT, 0, st>>>(node_rec.p, stride, n, box.p);
+    count_launches(1);
     k_morton<<<nblk(n), BT, 0, st>>>(node_rec.p, stride, n, box.p, k0.p, hi_g.p, v0.p);
+    count_launches(1);
     uint32_t n32 = (uint32_t)n;
     CK(cudaMemcpy(dn.p, &n32, 4, cudaMemcpyHostToDevice));
     bool alt;
@@ -475,6 +477,7 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
     uint32_t *ord = alt ? v1.p : v0.p;
     uint32_t *kk = alt ? k0.p : k1.p, *kalt = alt ? k1.p : k0.p, *valt = alt ? v0.p : v1.p;
     k_gather_u32<<<nblk(n), BT, 0, st>>>(hi_g.p, ord, n, kk);
+    count_launches(1);
     rc = radix_sort_pairs(kk, ord, kalt, valt, dn.p, n32, 0, 31, hist.p, st, &alt);          // high word
     if (rc) return rc;
     uint32_t *order = alt ? valt : ord;
@@ -490,6 +493,7 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
         int64_t npair = len / 2;
         k_merge_level<<<nblk(npair + 1, 128), 128, 0, st>>>(node_rec.p, stride, ncol, cur, len, next_id, nxt,
                                                             left.p, right.p, parent.p);
+        count_launches(1);
         next_id += npair;
         len = npair + (len & 1);
         std::swap(cur, nxt);
@@ -513,6 +517,7 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
         CK(cudaMemcpyAsync(up_parent.p + U, frp_a.p, F * 4, cudaMemcpyDeviceToDevice, st));
         k_hspt_classify<<<nblk(F), BT, 0, st>>>(node_rec.p, stride, left.p, fr_a.p, F, p.spt_volume,
                                                 up_kind.p + U, flag.p);
+        count_launches(1);
         uint32_t F32 = (uint32_t)F;
         CK(cudaMemcpyAsync(dn.p, &F32, 4, cudaMemcpyHostToDevice, st));
         rc = scan_exclusive(flag.p, pos.p, dn.p, F32, bsum.p, total.p, st);
@@ -521,6 +526,7 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
         CK(cudaMemcpyAsync(&n_int, total.p, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         k_hspt_expand<<<nblk(F), BT, 0, st>>>(fr_a.p, F, U, up_kind.p + U, pos.p, left.p, right.p, fr_b.p, frp_b.p);
+        count_launches(1);
         U += F;
         F = 2 * (int64_t)n_int;
         std::swap(fr_a.p, fr_b.p);
@@ -536,10 +542,12 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
     uint32_t U32 = (uint32_t)U, n_spt = 0, n_rows_up = 0;
     CK(cudaMemcpy(dn.p, &U32, 4, cudaMemcpyHostToDevice));
     k_flag_eq<<<nblk(U), BT, 0, st>>>(up_kind.p, U, KIND_SPT, 0, flag.p);
+    count_launches(1);
     rc = scan_exclusive(flag.p, spt_idx.p, dn.p, U32, bsum.p, total.p, st);
     if (rc) return rc;
     CK(cudaMemcpy(&n_spt, total.p, 4, cudaMemcpyDeviceToHost));
     k_flag_eq<<<nblk(U), BT, 0, st>>>(up_kind.p, U, KIND_SPT, 1, flag.p);
+    count_launches(1);
     rc = scan_exclusive(flag.p, row_idx.p, dn.p, U32, bsum.p, total.p, st);
     if (rc) return rc;
     CK(cudaMemcpy(&n_rows_up, total.p, 4, cudaMemcpyDeviceToHost));
@@ -551,11 +559,13 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
     CK(cudaMemset(node_spt_root.p, 0xff, M * 4)); CK(cudaMemset(node_upper_row.p, 0xff, M * 4));
     k_mark_upper<<<nblk(U), BT, 0, st>>>(up_node.p, up_kind.p, U, spt_idx.p, row_idx.p, node_spt_root.p,
                                          node_upper_row.p, spt_root.p, up_ref.p);
+    count_launches(1);
 
     // ---- SPT intervals and layout ----
     CK(lo_node.alloc(M)); CK(hi_node.alloc(M));
     k_spt_intervals<<<nblk(M), BT, 0, st>>>(node_rec.p, stride, M, parent.p, left.p, node_spt_root.p,
                                             node_upper_row.p, n_spt, p.kappa, lo_node.p, hi_node.p, k0.p, hi_g.p, v0.p);
+    count_launches(1);
     uint32_t M32 = (uint32_t)M;
     CK(cudaMemcpy(dn.p, &M32, 4, cudaMemcpyHostToDevice));
     rc = radix_sort_pairs(k0.p, v0.p, k1.p, v1.p, dn.p, M32, 0, 32, hist.p, st, &alt);     // hi descending
@@ -563,6 +573,7 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
     ord = alt ? v1.p : v0.p;
     kk = alt ? k0.p : k1.p; kalt = alt ? k1.p : k0.p; valt = alt ? v0.p : v1.p;
     k_gather_u32<<<nblk(M), BT, 0, st>>>(hi_g.p, ord, M, kk);
+    count_launches(1);
     int jbits = 1;
     while ((1ull << jbits) <= (uint64_t)n_spt) ++jbits;
     rc = radix_sort_pairs(kk, ord, kalt, valt, dn.p, M32, 0, jbits, hist.p, st, &alt);      // SPT index
@@ -577,13 +588,17 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
     }
     k_spt_rows<<<nblk(M), BT, 0, st>>>(sorted_node, sorted_j, M, n_spt, n_rows_up, node_of_row.p, spt_base.p,
                                        lo_node.p, hi_node.p, lo_row.p, hi_row.p);
+    count_launches(1);
     k_upper_rows<<<nblk(U), BT, 0, st>>>(up_node.p, up_kind.p, up_ref.p, U, node_of_row.p, lo_row.p, hi_row.p);
+    count_launches(1);
     CK(rows.alloc((size_t)M * stride));
     k_permute_rows<<<nblk(M * (stride / 4)), BT, 0, st>>>(node_rec.p, node_of_row.p, M, stride, rows.p);
+    count_launches(1);
     DevBuf<UpperEntry> upper;
     CK(upper.alloc(U));
     k_upper_entries<<<nblk(U), BT, 0, st>>>(node_rec.p, stride, up_node.p, up_kind.p, up_parent.p, up_ref.p, U,
                                             upper.p);
+    count_launches(1);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
 

@@ -235,14 +235,19 @@ __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, co
 int launch_select(const lodgs_scene *sc, const CamK &k, FrameBufs &f, cudaStream_t st) {
     uint32_t U = (uint32_t)sc->n_upper;
     k_upper_count<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, k, f.block_counts);
+    count_launches(1);
     k_upper_write<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, k, f.block_counts, f.sel_rows, f.emit_j, f.emit_x, f.cnt);
+    count_launches(1);
     k_spt_high<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_hi, f.high);
+    count_launches(1);
     int rc = scan_exclusive(f.high, f.work_off, f.cnt + C_NEMIT, (uint32_t)sc->n_spt, f.scan_bsum, f.cnt + C_WORK, st);
     if (rc) return rc;
     k_spt_count<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
                                          f.block_counts);
+    count_launches(1);
     k_spt_write<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
                                          f.block_counts, f.sel_rows);
+    count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
 }

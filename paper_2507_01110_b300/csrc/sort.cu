@@ -266,8 +266,11 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
         uint32_t *ko = alt ? keys : keys_alt;
         uint32_t *vo = alt ? vals : vals_alt;
         k_radix_upsweep<<<SORT_GRID, ST_THREADS, 0, st>>>(ki, d_n, shift, mask, hist);
+        count_launches(1);
         k_scan_single<<<1, 1024, 0, st>>>(hist, RADIX * SORT_GRID);
+        count_launches(1);
         k_radix_downsweep<<<SORT_GRID, ST_THREADS, 0, st>>>(ki, vi, ko, vo, d_n, shift, mask, hist);
+        count_launches(1);
         alt = !alt;
     }
     LODGS_CUDA(cudaGetLastError());
@@ -279,7 +282,9 @@ int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint3
                    uint32_t *d_total, cudaStream_t st) {
     (void)max_n;
     k_scan_reduce<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, d_n, block_sums);
+    count_launches(1);
     k_scan_down<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, out, d_n, block_sums, d_total);
+    count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
 }

@@ -148,9 +148,12 @@ def test_backward_matches_oracle_config1(api, c1):
         grad = api.render_backward(sc_g, fr, torch.from_numpy(w).cuda()).cpu().numpy()
         ref = oracle.render_backward(sc_o, cam, out, w.astype(np.float64), bg=(0.05, 0.1, 0.0))["g_rec"]
         _check_grads(grad[: len(out["sel"])], ref, 0)
-        # dense layout writes the same values at the selected rows
+        # dense layout writes the same values at the selected rows (up to the
+        # order in which float atomics summed the per-tile contributions)
         dense = api.render_backward(sc_g, fr, torch.from_numpy(w).cuda(), dense=True).cpu().numpy()
-        assert np.allclose(dense[out["sel"]], grad[: len(out["sel"])], rtol=1e-5, atol=1e-7)
+        assert _rel(dense[out["sel"]], grad[: len(out["sel"])]) < 1e-5
+        others = np.setdiff1d(np.arange(dense.shape[0]), out["sel"])
+        assert not np.any(dense[others])
 
 
 @pytest.fixture(scope="module")
