@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark of the LoD Gaussian render path on B300.
+
+One step = one view of the 2M-leaf SH3 scene (70% ground, 30% boxes) on the
+32-view aerial-to-street trajectory at 1920x1080: LoD select (upper BFS + SPT
+cut), projection with SH colour, tile x depth sort, front-to-back blending,
+mean-L1 loss against a seeded target, and the backward to sparse gradient rows
+of the selected nodes.  The metric is views per second (fwd+bwd frames/s); the
+forward-only rate and the per-stage device times are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lodgs|reference]
+
+N > 1 runs under torchrun, one process per GPU; views are independent, so each
+rank takes every N-th view (no collective on the data path).  --impl reference
+times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "frames/s & fwd+bwd step ms at 1080p (LoD splat); serving p50/p99 ms"
+WORKLOAD = ("2,097,152-leaf SH3 scene (70% ground plane, 30% in 256 boxes), 32-view aerial-to-street path at "
+            "1920x1080, tau 1 px; per view: LoD select + render + mean-L1 loss + backward to sparse node gradients")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=32)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="lodgs", choices=["lodgs", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--leaves", type=int, default=2_097_152)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6400.0), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+def stage_bytes(stage: str, st: dict, record_bytes: int, n_upper: int, tile_passes: int) -> float:
+    """Algorithmic bytes one launch of a stage must move (what the method reads
+    and writes at least once), from the frame's counters."""
+    ns, nv, npair, scanned = st["n_selected"], st["n_visible"], st["n_pairs"], st["n_spt_scanned"]
+    if stage == "select":
+        return 32.0 * n_upper + 8.0 * scanned + 4.0 * ns
+    if stage == "project":
+        return (record_bytes + 56.0) * ns
+    if stage == "depth_sort":
+        return 4 * 20.0 * ns
+    if stage == "emit":
+        return 40.0 * ns + 8.0 * npair
+    if stage == "tile_sort":
+        return tile_passes * 20.0 * npair
+    if stage == "project_bwd":
+        return (record_bytes + 36.0 + record_bytes) * ns
+    return 0.0
+
+
+# ---------------------------------------------------------------------------
+# CUDA arm
+# ---------------------------------------------------------------------------
+def run_lodgs(args, rank: int, world: int):
+    import torch
+
+    from paper_2507_01110_b300 import _lib, api, build, synth
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    cfg = synth.config2_scene(n=args.leaves)
+    cams = cfg["cameras"]
+    nv = len(cams)
+    scene = api.build_hierarchy(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
+    leaves_host = cfg.pop("leaves")
+    del leaves_host
+    H, W = cams[0].height, cams[0].width
+    # views of this rank (independent units: no exchange between ranks)
+    my_views = [v for v in range(nv) if v % world == rank] or [rank % nv]
+    frames = {v: api.Frame(scene) for v in my_views}
+    for fr in frames.values():
+        fr.set_profiling(True)
+    gen = torch.Generator().manual_seed(1234)
+    targets_h = {v: torch.rand((H, W, 3), generator=gen).pin_memory() for v in my_views}
+    targets_d = {v: t.cuda() for v, t in targets_h.items()}
+    image = torch.empty((H, W, 3), device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # grow every frame's workspace once (capacity-checked renders), size gradient rows
+    max_sel = 1
+    fwd_stats = {}
+    for v in my_views:
+        fr = api.select_lod(scene, cams[v], frames[v])
+        api.render(scene, fr, image=image, check_capacity=True)
+        st = fr.stats()
+        fwd_stats[v] = st
+        max_sel = max(max_sel, st["n_selected"])
+    grad = torch.empty((max_sel, scene.stride), device="cuda")
+    inv_n = 1.0 / (H * W * 3)
+
+    def step(v, target):
+        fr = api.select_lod(scene, cams[v], frames[v])
+        api.render(scene, fr, image=image, check_capacity=False)
+        diff = image - target
+        loss = diff.abs().mean()
+        dL = torch.sign(diff).mul_(inv_n)
+        api.render_backward(scene, fr, dL, grad=grad)
+        return loss
+
+    order = [my_views[i % len(my_views)] for i in range(args.steps)]
+    for i in range(args.warmup):
+        step(my_views[i % len(my_views)], targets_d[my_views[i % len(my_views)]])
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs ----
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = _lib.lib().lodgs_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for v in order:
+        step(v, targets_d[v])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = _lib.lib().lodgs_kernel_launches() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    # per-stage device times of the timed region (each frame keeps its last step)
+    stage_ms = {s: [] for s in _lib.STAGES}
+    stats_ok = True
+    for v in set(order):
+        fr = frames[v]
+        t = fr.stage_ms()
+        for s in _lib.STAGES:
+            stage_ms[s].append(t[s])
+        stats_ok &= fr.stats()["status"] == 0
+    stage_mean = {s: float(np.mean(x)) for s, x in stage_ms.items()}
+
+    # ---- forward only (same frames) ----
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for v in order:
+        fr = api.select_lod(scene, cams[v], frames[v])
+        api.render(scene, fr, image=image, check_capacity=False)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1)
+
+    # ---- end to end: targets from pinned host, loss read back every step ----
+    loss_h = torch.empty(len(order), dtype=torch.float32).pin_memory()
+    tgt_dev = torch.empty((H, W, 3), device="cuda")
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for i, v in enumerate(order):
+        tgt_dev.copy_(targets_h[v], non_blocking=True)
+        loss = step(v, tgt_dev)
+        loss_h[i:i + 1].copy_(loss.reshape(1), non_blocking=True)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    e2e_wall = time.perf_counter() - t0
+    e2e_ms = g0.elapsed_time(g1)
+    if world > 1:
+        torch.distributed.barrier()
+
+    # max over ranks
+    def maxr(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    ms, fwd_ms, e2e_ms, e2e_wall = maxr(ms), maxr(fwd_ms), maxr(e2e_ms), maxr(max(e2e_wall * 1e3, e2e_ms)) / 1e3
+    total_views = args.steps * world
+    res = {
+        "ms": ms, "fwd_ms": fwd_ms, "e2e_ms": max(e2e_ms, e2e_wall * 1e3), "views": total_views,
+        "stage_ms": stage_mean, "clocks": clk, "launches": launches, "stats_ok": stats_ok,
+        "fwd_stats": fwd_stats, "scene": {"n_nodes": scene.n_nodes, "n_upper": scene.n_upper, "n_spt": scene.n_spt,
+                                          "stride": scene.stride},
+        "h2d_bytes": H * W * 3 * 4 + 64, "d2h_bytes": 4, "order": order,
+    }
+    return res, cfg
+
+
+def roofline(res: dict, peaks: dict) -> dict:
+    from paper_2507_01110_b300 import _lib
+    st_mean = res["stage_ms"]
+    # mean counters over the views of the timed region
+    fs = [res["fwd_stats"][v] for v in set(res["order"])]
+    mean = {k: float(np.mean([s[k] for s in fs])) for k in ("n_selected", "n_visible", "n_pairs", "n_spt_scanned")}
+    rb = 236
+    tile_passes = 2
+    hbm = {s: stage_bytes(s, mean, rb, res["scene"]["n_upper"], tile_passes) for s in _lib.STAGES}
+    dom = max(st_mean, key=lambda s: st_mean[s])
+    per_stage = {}
+    for s in _lib.STAGES:
+        t = st_mean[s] * 1e-3
+        if hbm[s] > 0 and t > 0:
+            per_stage[s] = {"ms": st_mean[s], "gbs": hbm[s] / t / 1e9, "frac_hbm": hbm[s] / t / 1e9 / peaks["hbm_gbs"]}
+        else:
+            per_stage[s] = {"ms": st_mean[s]}
+    return {"dominant": dom, "stages": per_stage, "bytes": hbm, "mean_counts": mean}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_view_seconds(sc_o, cam, window_rows: int, target_seed: int) -> tuple[float, str]:
+    """Time select + project + sort on the full view and the blend + backward on
+    a band of `window_rows` pixel rows; scale the band to the full image."""
+    import oracle
+    from paper_2507_01110_b300 import synth
+    t0 = time.perf_counter()
+    sel, _ = oracle.select(sc_o, cam)
+    proj = oracle.project(sc_o, sel, cam)
+    pairs = oracle.sort_pairs(proj, cam.width, cam.height)
+    t_common = time.perf_counter() - t0
+    y0 = (cam.height - window_rows) // 2
+    win = (0, y0, cam.width, y0 + window_rows)
+    t1 = time.perf_counter()
+    out = oracle.blend(proj, pairs, cam.width, cam.height, window=win)
+    tgt = synth.target_image(target_seed, cam.height, cam.width)
+    dL = np.sign(out["image"] - tgt) / out["image"].size
+    g2d = oracle.blend_backward(proj, pairs, cam.width, cam.height, dL, window=win)
+    oracle.project_backward(sc_o, sel, cam, proj, g2d)
+    t_band = time.perf_counter() - t1
+    scale = cam.height / window_rows
+    return t_common + t_band * scale, f"rows {win[1]}-{win[3]} of {cam.height}"
+
+
+def cpu_baseline(cfg_leaves_fn, budget_s: float = 20.0) -> dict:
+    import oracle
+    from paper_2507_01110_b300 import synth
+    cfg = cfg_leaves_fn()
+    sc_o = oracle.build_scene(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
+    cams = cfg["cameras"]
+    secs, views, desc = [], [0, 31], []
+    for v in views:
+        s, d = oracle_view_seconds(sc_o, cams[v], 68, 1000 + v)
+        secs.append(s)
+        desc.append(f"view {v}: {d}")
+    per_view = float(np.mean(secs))
+    return {"value": 1.0 / per_view, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": "float64 C oracle, one thread: select+project+sort on the full view, blend+backward on a "
+                      "68-row band scaled to 1080 rows; " + "; ".join(desc)}
+
+
+def run_reference(args, rank: int, world: int):
+    """The oracle as the reference arm: each step one view, bounded sample."""
+    import oracle
+    from paper_2507_01110_b300 import synth
+    if rank != 0:
+        return None
+    cfg = synth.config2_scene(n=args.leaves)
+    sc_o = oracle.build_scene(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
+    cams = cfg["cameras"]
+    for i in range(args.warmup):
+        oracle_view_seconds(sc_o, cams[(i * 7) % len(cams)], 16, 1000 + i)
+    total = 0.0
+    for i in range(args.steps):
+        v = (i * 7) % len(cams)
+        s, _ = oracle_view_seconds(sc_o, cams[v], 16, 1000 + v)
+        total += s
+    value = args.steps / total
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step one view (views 0,7,14,..): select+project+sort full, "
+                                       "blend+backward on a 16-row band scaled to 1080 rows"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    res, cfg = run_lodgs(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    rf = roofline(res, peaks)
+    dom = rf["dominant"]
+    ds = rf["stages"][dom]
+    value = res["views"] / (res["ms"] * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "leaves": args.leaves, "nodes": res["scene"]["n_nodes"],
+                   "spt": res["scene"]["n_spt"], "views": 32, "resolution": "1920x1080", "tau_px": 1.0,
+                   "l2": "inputs larger than L2 (node records 1.07 GB; per-view reads 100-400 MB)",
+                   "parallelism": f"replicas x{world} (views split across ranks)"},
+        "fwd_bwd_step_ms": res["ms"] / args.steps,
+        "fwd_only": {"value": res["views"] / (res["fwd_ms"] * 1e-3), "unit": "frames/s",
+                     "ms_per_frame": res["fwd_ms"] / args.steps},
+        "e2e": {"value": res["views"] / (res["e2e_ms"] * 1e-3), "unit": "frames/s",
+                "h2d_bytes_per_step": res["h2d_bytes"], "d2h_bytes_per_step": res["d2h_bytes"]},
+        "gpu_launches": int(res["launches"]),
+        "stages_ms": {k: round(v, 4) for k, v in res["stage_ms"].items()},
+        "clocks": res["clocks"],
+        "status_ok": res["stats_ok"],
+    }
+    if "gbs" in ds:
+        line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": ds["gbs"], "peak": peaks["hbm_gbs"],
+                            "unit": "GB/s", "frac": ds["frac_hbm"], "traffic": None,
+                            "peak_source": peaks["source"]}
+    else:
+        line["roofline"] = {"bound": "alu", "kernel": dom, "ms": ds["ms"], "achieved": None, "peak": None,
+                            "unit": "inst/s", "frac": None, "traffic": None}
+    line["roofline_stages"] = {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in rf["stages"].items()}
+    if not args.no_cpu_baseline and world == 1:
+        from paper_2507_01110_b300 import synth
+        line["cpu_baseline"] = cpu_baseline(lambda: synth.config2_scene(n=args.leaves))
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()
