@@ -20,7 +20,6 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -49,55 +48,84 @@ def parse():
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
-class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+class _Nvml:
+    """Minimal read-only NVML access through ctypes (libnvidia-ml.so.1)."""
+    # clock-event reason bits of the public NVML API
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40, "hw_power_brake": 0x80}
 
     def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.lines = []
+        import ctypes as C
+        self.C = C
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = C.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(self.h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByIndex failed")
+        self._reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sm_mhz(self) -> float:
+        v = self.C.c_uint()
+        self.lib.nvmlDeviceGetClockInfo(self.h, self.C.c_int(1), self.C.byref(v))     # NVML_CLOCK_SM
+        return float(v.value)
+
+    def max_sm_mhz(self) -> float:
+        v = self.C.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.C.c_int(1), self.C.byref(v))
+        return float(v.value)
+
+    def reasons(self) -> int:
+        v = self.C.c_ulonglong()
+        self._reasons(self.h, self.C.byref(v))
+        return int(v.value)
+
+
+class ClockSampler:
+    """Samples the SM clock and the clock-event reasons through NVML every 2 ms
+    while the timed region runs (reads only; nothing is set)."""
+
+    def __init__(self, index: int):
+        self.samples = []
+        self.reasons = set()
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self.ok = False
+        self.err = ""
+        try:
+            self.nv = _Nvml(index)
+            self.max_mhz = self.nv.max_sm_mhz()
+            self.ok = True
+        except Exception as e:  # noqa: BLE001
+            self.err = str(e)
+
+    def _poll(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self.nv.sm_mhz())
+                mask = self.nv.reasons()
+                for name, bit in _Nvml.BITS.items():
+                    if mask & bit:
+                        self.reasons.add(name)
+            except Exception:  # noqa: BLE001
+                pass
+            time.sleep(0.002)
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
+        if self.ok:
+            self.t = threading.Thread(target=self._poll, daemon=True)
             self.t.start()
-        except OSError:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            while not self.samples and self.t.is_alive():
+                time.sleep(0.001)
 
     def stop(self) -> dict:
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 8:
-                continue
-            try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        if not self.ok:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvml unavailable: " + self.err]}
+        self._stop.set()
+        self.t.join(timeout=1)
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples)}
 
 
 # ---------------------------------------------------------------------------
@@ -210,8 +238,10 @@ def run_lodgs(args, rank: int, world: int):
     # per-stage device times of the timed region (each frame keeps its last step)
     stage_ms = {s: [] for s in _lib.STAGES}
     stats_ok = True
+    work = {}
     for v in set(order):
         fr = frames[v]
+        work[v] = fr.work()
         t = fr.stage_ms()
         for s in _lib.STAGES:
             stage_ms[s].append(t[s])
@@ -261,12 +291,29 @@ def run_lodgs(args, rank: int, world: int):
     total_views = args.steps * world
     res = {
         "ms": ms, "fwd_ms": fwd_ms, "e2e_ms": max(e2e_ms, e2e_wall * 1e3), "views": total_views,
-        "stage_ms": stage_mean, "clocks": clk, "launches": launches, "stats_ok": stats_ok,
+        "stage_ms": stage_mean, "clocks": clk, "launches": launches, "stats_ok": stats_ok, "work": work,
         "fwd_stats": fwd_stats, "scene": {"n_nodes": scene.n_nodes, "n_upper": scene.n_upper, "n_spt": scene.n_spt,
                                           "stride": scene.stride},
         "h2d_bytes": H * W * 3 * 4 + 64, "d2h_bytes": 4, "order": order,
     }
     return res, cfg
+
+
+# FP32-pipe instructions per unit of blend work, counted from the kernel source
+# (support test: 2 sub/mul + 2 fma + compare; blend: exp, alpha, T, 3 colour fma;
+# backward contribution: exp, alpha, division, colour/alpha/conic/mean terms,
+# running sums).  Used only to express blend throughput against the FP32 peak.
+OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB, OPS_BWD_PASS1_BLEND = 5, 11, 45, 8
+FP32_LANES_PER_SM, N_SM = 128, 148
+
+
+def alu_ops(stage: str, work: dict) -> float:
+    if stage == "blend":
+        return OPS_EVAL * work["fwd_eval"] + OPS_BLEND * work["fwd_blend"]
+    if stage == "blend_bwd":
+        return OPS_EVAL * work["bwd_eval"] + OPS_BWD_CONTRIB * work["bwd_contrib"] + \
+            OPS_BWD_PASS1_BLEND * work["fwd_blend"]
+    return 0.0
 
 
 def roofline(res: dict, peaks: dict) -> dict:
@@ -279,14 +326,22 @@ def roofline(res: dict, peaks: dict) -> dict:
     tile_passes = 2
     hbm = {s: stage_bytes(s, mean, rb, res["scene"]["n_upper"], tile_passes) for s in _lib.STAGES}
     dom = max(st_mean, key=lambda s: st_mean[s])
+    wk = {k: float(np.mean([w[k] for w in res["work"].values()])) for k in ("fwd_eval", "fwd_blend", "bwd_eval",
+                                                                           "bwd_contrib")}
+    mhz = res["clocks"].get("sm_mhz") or 2032.0
+    alu_peak = N_SM * FP32_LANES_PER_SM * mhz * 1e6 / 1e12      # T FP32 instructions / s
     per_stage = {}
     for s in _lib.STAGES:
         t = st_mean[s] * 1e-3
         if hbm[s] > 0 and t > 0:
             per_stage[s] = {"ms": st_mean[s], "gbs": hbm[s] / t / 1e9, "frac_hbm": hbm[s] / t / 1e9 / peaks["hbm_gbs"]}
+        elif s in ("blend", "blend_bwd") and t > 0:
+            a = alu_ops(s, wk) / t / 1e12
+            per_stage[s] = {"ms": st_mean[s], "tinst_s": a, "frac_alu": a / alu_peak}
         else:
             per_stage[s] = {"ms": st_mean[s]}
-    return {"dominant": dom, "stages": per_stage, "bytes": hbm, "mean_counts": mean}
+    return {"dominant": dom, "stages": per_stage, "bytes": hbm, "mean_counts": mean, "work": wk,
+            "alu_peak": alu_peak, "mhz": mhz}
 
 
 # ---------------------------------------------------------------------------
@@ -404,10 +459,12 @@ def main():
     if "gbs" in ds:
         line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": ds["gbs"], "peak": peaks["hbm_gbs"],
                             "unit": "GB/s", "frac": ds["frac_hbm"], "traffic": None,
-                            "peak_source": peaks["source"]}
+                            "peak_source": peaks["source"] + " (MEASURED_PEAKS hbm_gbs)"}
     else:
-        line["roofline"] = {"bound": "alu", "kernel": dom, "ms": ds["ms"], "achieved": None, "peak": None,
-                            "unit": "inst/s", "frac": None, "traffic": None}
+        line["roofline"] = {"bound": "alu", "kernel": dom, "achieved": ds.get("tinst_s"), "peak": rf["alu_peak"],
+                            "unit": "T FP32 inst/s", "frac": ds.get("frac_alu"), "traffic": None,
+                            "peak_source": f"148 SMs x 128 FP32 lanes x {rf['mhz']:.0f} MHz (median SM clock "
+                                           "in the timed region)", "work_per_view": rf["work"]}
     line["roofline_stages"] = {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in rf["stages"].items()}
     if not args.no_cpu_baseline and world == 1:
         from paper_2507_01110_b300 import synth

@@ -193,6 +193,12 @@ int lodgs_frame_set_profiling(lodgs_frame *frame, int on);
  * the last select).  Blocks until the frame's stream is idle. */
 int lodgs_frame_stage_ms(lodgs_frame *frame, float *ms);
 
+/* Pixel-Gaussian work of the last render/backward on this frame (4 uint64):
+ * [0] forward support tests evaluated, [1] forward blends (alpha composited),
+ * [2] backward support tests (both passes), [3] backward contributions.
+ * Blocks until the frame's stream is idle. */
+int lodgs_frame_work(lodgs_frame *frame, uint64_t *work);
+
 /*
  * Copy the frame's last render products to host buffers (inspection and
  * tests; any pointer may be NULL to skip).  Blocks until the frame's stream is

@@ -9,7 +9,7 @@ import ctypes as C
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblodgs.so")
+LIB_PATH = os.environ.get("LODGS_LIBRARY", os.path.join(_HERE, "liblodgs.so"))
 
 LODGS_OK = 0
 LODGS_E_INVALID = -1
@@ -70,6 +70,7 @@ _SIGS = {
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
     "lodgs_frame_export": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "lodgs_frame_set_profiling": (C.c_int, [_P, C.c_int]),
+    "lodgs_frame_work": (C.c_int, [_P, _P]),
     "lodgs_frame_stage_ms": (C.c_int, [_P, _P]),
 }
 

@@ -140,6 +140,12 @@ class Frame:
         check(lib().lodgs_frame_stage_ms(self._h, ms))
         return dict(zip(_lib.STAGES, [float(v) for v in ms]))
 
+    def work(self) -> dict:
+        """Pixel-Gaussian work counters of the last render/backward."""
+        w = (C.c_uint64 * 4)()
+        check(lib().lodgs_frame_work(self._h, w))
+        return {"fwd_eval": w[0], "fwd_blend": w[1], "bwd_eval": w[2], "bwd_contrib": w[3]}
+
     def export(self) -> dict:
         """Sorted pair order, tile ranges, splats and depth keys of the last render."""
         st = self.stats()

@@ -128,7 +128,7 @@ int ensure_pairs(lodgs_frame *fr, uint64_t want) {
 void free_frame_bufs(FrameBufs &f) {
     void *ps[] = {f.cnt, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
                   f.sort_hist, f.sp_a, f.sp_b, f.sp_c, f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.rect, f.ntiles,
-                  f.nt_sorted, f.pair_off, f.g2d, f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.ranges};
+                  f.nt_sorted, f.pair_off, f.g2d, f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.ranges, f.work};
     for (void *p : ps)
         if (p) cudaFree(p);
     f = FrameBufs();
@@ -232,7 +232,7 @@ int lodgs_frame_create(lodgs_scene *sc, lodgs_frame **out) {
 #define AL(p, n)                                                                  \
     if (e == cudaSuccess) e = cudaMalloc((void **)&p, std::max<size_t>((size_t)(n), 1) * sizeof(*p));
     AL(f.cnt, C_COUNT) AL(f.sel_rows, M) AL(f.emit_j, S) AL(f.emit_x, S) AL(f.high, S + 1) AL(f.work_off, S + 1)
-    AL(f.block_counts, 1024) AL(f.scan_bsum, SCAN_GRID) AL(f.sort_hist, 256 * SORT_GRID)
+    AL(f.block_counts, 1024) AL(f.scan_bsum, SCAN_GRID) AL(f.sort_hist, SORT_HIST) AL(f.work, 4)
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void **)&fr->h_cnt, C_COUNT * sizeof(uint32_t));
     if (e != cudaSuccess) {
@@ -393,6 +393,15 @@ int lodgs_frame_stage_ms(lodgs_frame *fr, float *ms) {
         ms[s2] = 0.f;
         if (fr->ran[s2]) LODGS_CUDA(cudaEventElapsedTime(&ms[s2], fr->ev[2 * s2], fr->ev[2 * s2 + 1]));
     }
+    return LODGS_OK;
+}
+
+int lodgs_frame_work(lodgs_frame *fr, uint64_t *work) {
+    if (!fr || !work) { set_error("frame_work: NULL argument"); return LODGS_E_INVALID; }
+    LODGS_CUDA(cudaStreamSynchronize(fr->stream));
+    unsigned long long w[4];
+    LODGS_CUDA(cudaMemcpy(w, fr->f.work, sizeof(w), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i) work[i] = w[i];
     return LODGS_OK;
 }
 

@@ -124,6 +124,7 @@ struct FrameBufs {
     uint32_t *pkey = nullptr, *pval = nullptr, *pkey_alt = nullptr, *pval_alt = nullptr;
     // tiles (capacity cap_tiles)
     uint2 *ranges = nullptr;
+    unsigned long long *work = nullptr;   // 4 counters, see lodgs_frame_work
     uint64_t cap_sel = 0, cap_pairs = 0, cap_tiles = 0;
     // where the last render left its sorted data
     const uint32_t *order = nullptr;     // selected indices by depth
@@ -151,6 +152,7 @@ struct SortWork {
     size_t hist_cap = 0;
 };
 constexpr int SORT_GRID = 296;      // 2 blocks per SM on 148 SMs
+constexpr int SORT_HIST = 256 * (SORT_GRID + 1);   // histogram table + digit totals
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                      const uint32_t *d_n, uint32_t max_n, int begin_bit, int end_bit, uint32_t *hist,
                      cudaStream_t st, bool *result_in_alt);

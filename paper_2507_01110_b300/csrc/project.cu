@@ -130,14 +130,16 @@ __device__ __forceinline__ void geometry(const CamK &k, const float *mu, const f
     g.det = g.a * g.c - g.b * g.b;
 }
 
-__global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, int stride, int degree,
+template <int DEG>
+__global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, int stride,
                                                  const uint32_t *__restrict__ sel_rows, CamK k,
                                                  uint32_t *__restrict__ cnt, float4 *__restrict__ sp_a,
                                                  float4 *__restrict__ sp_b, float *__restrict__ sp_c,
                                                  uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
                                                  uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles) {
     const uint32_t n = cnt[C_NSEL_EFF];
-    const int K = (degree + 1) * (degree + 1) - 1;
+    constexpr int degree = DEG;
+    constexpr int K = (DEG + 1) * (DEG + 1) - 1;
     uint32_t nvis = 0;
     for (uint32_t i = blockIdx.x * PB + threadIdx.x; i < n; i += gridDim.x * PB) {
         const float *r = rows + (size_t)sel_rows[i] * stride;
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
                             float Y[15];
                             sh_basis(degree, dx, dy, dz, Y);
                             const float *f = r + REC_F;
+#pragma unroll
                             for (int kk = 0; kk < K; ++kk) {
                                 col[0] += Y[kk] * f[3 * kk];
                                 col[1] += Y[kk] * f[3 * kk + 1];
@@ -219,14 +222,16 @@ __global__ void k_clamp_sel(uint32_t *cnt, uint64_t cap_sel) {
     cnt[C_NVIS] = 0;
 }
 
-__global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ rows, int stride, int degree,
+template <int DEG>
+__global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ rows, int stride,
                                                      const uint32_t *__restrict__ sel_rows, CamK k,
                                                      const uint32_t *__restrict__ cnt,
                                                      const uint32_t *__restrict__ ntiles,
                                                      const float *__restrict__ g2d, float *__restrict__ out,
                                                      int dense) {
     const uint32_t n = cnt[C_NSEL_EFF];
-    const int K = (degree + 1) * (degree + 1) - 1;
+    constexpr int degree = DEG;
+    constexpr int K = (DEG + 1) * (DEG + 1) - 1;
     for (uint32_t i = blockIdx.x * PB + threadIdx.x; i < n; i += gridDim.x * PB) {
         const uint32_t row = sel_rows[i];
         float *o = out + (size_t)(dense ? row : i) * stride;
@@ -251,11 +256,14 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
         if (K > 0) { sh_basis(degree, dir[0], dir[1], dir[2], Y); sh_basis_grad(degree, dir[0], dir[1], dir[2], dY); }
         float gdir[3] = {0.f, 0.f, 0.f};
         float grow_b[3] = {0.f, 0.f, 0.f};
+#pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             float raw = r[REC_B + ch];
+#pragma unroll
             for (int kk = 0; kk < K; ++kk) raw += Y[kk] * r[REC_F + 3 * kk + ch];
             float gc = raw < 0.0f ? 0.0f : g[6 + ch];
             grow_b[ch] = gc;
+#pragma unroll
             for (int kk = 0; kk < K; ++kk) {
                 o[REC_F + 3 * kk + ch] = gc * Y[kk];
                 float f = r[REC_F + 3 * kk + ch];
@@ -277,22 +285,32 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
         gS2[1][0] = -(t10 * Qm00 + t11 * Qm01);
         gS2[1][1] = -(t10 * Qm01 + t11 * Qm11);
         float gS[3][3], gT[2][3];
+#pragma unroll
         for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
             for (int j = 0; j < 3; ++j) {
                 float acc = 0.f;
+#pragma unroll
                 for (int a = 0; a < 2; ++a)
+#pragma unroll
                     for (int c = 0; c < 2; ++c) acc += G.T[a][i2] * gS2[a][c] * G.T[c][j];
                 gS[i2][j] = acc;
             }
+#pragma unroll
         for (int a = 0; a < 2; ++a)
+#pragma unroll
             for (int b = 0; b < 3; ++b) {
                 float acc = 0.f;
+#pragma unroll
                 for (int c = 0; c < 2; ++c)
+#pragma unroll
                     for (int m = 0; m < 3; ++m) acc += 2.0f * gS2[a][c] * G.T[c][m] * G.S[m][b];
                 gT[a][b] = acc;
             }
         float gJ[2][3];
+#pragma unroll
         for (int a = 0; a < 2; ++a)
+#pragma unroll
             for (int m = 0; m < 3; ++m)
                 gJ[a][m] = gT[a][0] * k.R[m * 3 + 0] + gT[a][1] * k.R[m * 3 + 1] + gT[a][2] * k.R[m * 3 + 2];
         float tz2 = tz * tz, tz3 = tz2 * tz;
@@ -306,12 +324,15 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
         gt[2] += -k.fx * tx / tz2 * g[0];
         gt[1] += k.fy / tz * g[1];
         gt[2] += -k.fy * ty / tz2 * g[1];
+#pragma unroll
         for (int a = 0; a < 3; ++a)
             o[REC_MU + a] = gd[a] + k.R[0 * 3 + a] * gt[0] + k.R[1 * 3 + a] * gt[1] + k.R[2 * 3 + a] * gt[2];
         // ---- Sigma = M M^T, M = R diag(s) ----
         float gR[3][3];
+#pragma unroll
         for (int j = 0; j < 3; ++j) {
             float acc = 0.f;
+#pragma unroll
             for (int i2 = 0; i2 < 3; ++i2) {
                 float gM = 2.0f * (gS[i2][0] * G.M[0][j] + gS[i2][1] * G.M[1][j] + gS[i2][2] * G.M[2][j]);
                 acc += gM * G.R[i2][j];
@@ -329,8 +350,10 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
         gq[3] = 2.0f * (-w * gR[0][1] + x * gR[0][2] + w * gR[1][0] + y * gR[1][2] + x * gR[2][0] + y * gR[2][1])
               - 4.0f * z * (gR[0][0] + gR[1][1]);
         float qd = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+#pragma unroll
         for (int a = 0; a < 4; ++a) o[REC_Q + a] = (gq[a] - G.qh[a] * qd) / G.qn;
         o[REC_OP] = g[5];
+#pragma unroll
         for (int ch = 0; ch < 3; ++ch) o[REC_B + ch] = grow_b[ch];
         for (int c = 14 + 3 * K; c < stride; ++c) o[c] = 0.f;
     }
@@ -341,8 +364,16 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
 int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, cudaStream_t st) {
     k_clamp_sel<<<1, 1, 0, st>>>(f.cnt, f.cap_sel);
     count_launches(1);
-    k_project<<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, sc->sh_degree, f.sel_rows, k, f.cnt, f.sp_a, f.sp_b,
-                                        f.sp_c, f.dkey, f.dval, f.rect, f.ntiles);
+#define LAUNCH_PROJ(D)                                                                                     \
+    k_project<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.sel_rows, k, f.cnt, f.sp_a, f.sp_b, f.sp_c, f.dkey, \
+                                           f.dval, f.rect, f.ntiles)
+    switch (sc->sh_degree) {
+        case 0: LAUNCH_PROJ(0); break;
+        case 1: LAUNCH_PROJ(1); break;
+        case 2: LAUNCH_PROJ(2); break;
+        default: LAUNCH_PROJ(3); break;
+    }
+#undef LAUNCH_PROJ
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
@@ -350,8 +381,15 @@ int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, Fram
 
 int launch_project_backward(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, float *grad_rows,
                             int dense, cudaStream_t st) {
-    k_project_bwd<<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, sc->sh_degree, f.sel_rows, k, f.cnt, f.ntiles, f.g2d,
-                                            grad_rows, dense);
+#define LAUNCH_PBWD(D)                                                                                     \
+    k_project_bwd<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.sel_rows, k, f.cnt, f.ntiles, f.g2d, grad_rows, dense)
+    switch (sc->sh_degree) {
+        case 0: LAUNCH_PBWD(0); break;
+        case 1: LAUNCH_PBWD(1); break;
+        case 2: LAUNCH_PBWD(2); break;
+        default: LAUNCH_PBWD(3); break;
+    }
+#undef LAUNCH_PBWD
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;

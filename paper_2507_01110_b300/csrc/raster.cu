@@ -37,24 +37,26 @@ __global__ void k_clamp_pairs(uint32_t *cnt, uint64_t cap_pairs) {
     cnt[C_NPAIR_EFF] = n;
 }
 
-__global__ void k_emit(const uint32_t *__restrict__ order, const uint32_t *__restrict__ ntiles,
-                       const uint2 *__restrict__ rect, const uint32_t *__restrict__ pair_off,
-                       const uint32_t *__restrict__ cnt, int TX, uint32_t *__restrict__ pkey,
-                       uint32_t *__restrict__ pval) {
-    if (cnt[C_NPAIR_EFF] == 0) return;
-    uint32_t n = cnt[C_NSEL_EFF];
-    for (uint32_t r = blockIdx.x * RB + threadIdx.x; r < n; r += gridDim.x * RB) {
-        uint32_t g = order[r];
-        if (ntiles[g] == 0) continue;
+// One thread per (tile, Gaussian) pair: pair p belongs to the last depth rank r
+// with pair_off[r] <= p (binary search), and is the k-th tile of its rectangle
+// in row-major order.  Every thread writes one pair, whatever the footprints.
+__global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restrict__ rect,
+                       const uint32_t *__restrict__ pair_off, const uint32_t *__restrict__ cnt, int TX,
+                       uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    const uint32_t P = cnt[C_NPAIR_EFF], n = cnt[C_NSEL_EFF];
+    for (uint32_t p = blockIdx.x * RB + threadIdx.x; p < P; p += gridDim.x * RB) {
+        uint32_t a = 0, b = n;
+        while (b - a > 1) {
+            uint32_t m = (a + b) >> 1;
+            if (pair_off[m] <= p) a = m; else b = m;
+        }
+        uint32_t g = order[a];
         uint2 rc = rect[g];
-        uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu, y1 = rc.y >> 16;
-        uint32_t o = pair_off[r];
-        for (uint32_t ty = y0; ty < y1; ++ty)
-            for (uint32_t tx = x0; tx < x1; ++tx) {
-                pkey[o] = ty * (uint32_t)TX + tx;
-                pval[o] = g;
-                ++o;
-            }
+        uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+        uint32_t w = x1 - x0, k = p - pair_off[a];
+        uint32_t ty = y0 + k / w, tx = x0 + k % w;
+        pkey[p] = ty * (uint32_t)TX + tx;
+        pval[p] = g;
     }
 }
 
@@ -67,194 +69,323 @@ __global__ void k_ranges(const uint32_t *__restrict__ pkey, const uint32_t *__re
     }
 }
 
-// support exponent p = -1/2 d^T Q d with d = mean - pixel centre; float32,
-// explicitly rounded (no contraction beyond the written fmaf)
-__device__ __forceinline__ float support_p(float4 a, float nhc, float xc, float yc, float &dx, float &dy) {
-    dx = __fsub_rn(a.x, xc);
-    dy = __fsub_rn(a.y, yc);
-    return __fmaf_rn(__fmul_rn(a.w, dx), dy, __fmaf_rn(__fmul_rn(nhc, dy), dy, __fmul_rn(__fmul_rn(a.z, dx), dx)));
-}
-
+// The support exponent p = -1/2 d^T Q d (d = mean - pixel centre) decides which
+// pixels a Gaussian touches, so it is evaluated with explicitly rounded float32
+// operations: p = fma(-B dx, dy, fma(-C/2 dy, dy, (-A/2 dx) dx)).
 constexpr float SUPPORT_P = -4.5f;
 constexpr float ALPHA_MAX = 0.99f;
 constexpr float T_MIN = 1e-4f;
+constexpr int BATCH = 256;            // Gaussians staged in shared memory per round
 
-__global__ void __launch_bounds__(RB) k_blend(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
-                                              const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
-                                              const float *__restrict__ sp_c, const uint32_t *__restrict__ cnt,
-                                              int W, int H, int TX, float bg0, float bg1, float bg2,
-                                              float *__restrict__ image) {
-    __shared__ float4 s_a[RB], s_b[RB];
-    __shared__ float s_c[RB];
-    if (cnt[C_STATUS] & ST_CAPACITY) return;
-    const int tile = blockIdx.x, tid = threadIdx.x;
-    const int px = (tile % TX) * TILE + (tid & 15), py = (tile / TX) * TILE + (tid >> 4);
-    const bool inside = px < W && py < H;
-    const float xc = (float)px + 0.5f, yc = (float)py + 0.5f;
-    const uint2 rg = ranges[tile];
-    float T = 1.0f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    bool done = !inside;
-    for (uint32_t base = rg.x; base < rg.y; base += RB) {
-        if (__syncthreads_count(done) == RB) break;
-        uint32_t idx = base + tid;
-        if (idx < rg.y) {
-            uint32_t g = pval[idx];
-            s_a[tid] = sp_a[g];
-            s_b[tid] = sp_b[g];
-            s_c[tid] = sp_c[g];
-        }
-        __syncthreads();
-        int n = min((uint32_t)RB, rg.y - base);
-        if (!done) {
-            for (int j = 0; j < n; ++j) {
-                float4 a = s_a[j];
-                float4 b = s_b[j];
-                float dx, dy;
-                float p = support_p(a, b.x, xc, yc, dx, dy);
-                if (p < SUPPORT_P) continue;
-                float alpha = fminf(ALPHA_MAX, b.y * __expf(p));
-                float w = alpha * T;
-                c0 += b.z * w; c1 += b.w * w; c2 += s_c[j] * w;
-                T = T * (1.0f - alpha);
-                if (T < T_MIN) { done = true; break; }
-            }
-        }
+// Sum 9 per-lane values over the warp and add the totals to dst[0..8] in shared
+// memory.  Values 0..7 use a transposed butterfly: at each exchange a lane keeps
+// half of its values and receives its partner's share of that half, so the
+// eight sums take 4+2+1+1+1 = 9 shuffles instead of 8 x 5; afterwards lane
+// 4*i holds the total of value i.  Value 8 uses a plain butterfly.
+// per-warp sums of two per-thread counters, one 64-bit atomic each per warp
+__device__ __forceinline__ void add_work(unsigned long long *work, uint32_t a, uint32_t b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    if (inside) {
-        float *o = image + ((size_t)py * W + px) * 3;
-        o[0] = c0 + T * bg0; o[1] = c1 + T * bg1; o[2] = c2 + T * bg2;
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(work, (unsigned long long)a);
+        atomicAdd(work + 1, (unsigned long long)b);
     }
 }
 
-__global__ void __launch_bounds__(RB) k_blend_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
-                                                  const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
-                                                  const float *__restrict__ sp_c, const uint32_t *__restrict__ cnt,
-                                                  int W, int H, int TX, float bg0, float bg1, float bg2,
-                                                  const float *__restrict__ dL_dimg, float *__restrict__ g2d) {
-    __shared__ float4 s_a[RB], s_b[RB];
-    __shared__ float s_c[RB];
-    __shared__ uint32_t s_g[RB];
-    __shared__ float s_grad[RB][9];
+__device__ __forceinline__ void warp_sum9_to_smem(float v[9], int lane, float *dst) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float w4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float send = h16 ? v[i] : v[i + 4];
+        float keep = h16 ? v[i + 4] : v[i];
+        w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float w2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float send = h8 ? w4[i] : w4[i + 2];
+        float keep = h8 ? w4[i + 2] : w4[i];
+        w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float w1;
+    {
+        float send = h4 ? w2[0] : w2[1];
+        float keep = h4 ? w2[1] : w2[0];
+        w1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    w1 += __shfl_xor_sync(0xffffffffu, w1, 2);
+    w1 += __shfl_xor_sync(0xffffffffu, w1, 1);
+    float s8 = v[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
+    if ((lane & 3) == 0) {
+        const int idx = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
+        atomicAdd(dst + idx, w1);
+    }
+    if (lane == 1) atomicAdd(dst + 8, s8);
+}
+
+// Each thread owns PIX pixels of one column of the 16x16 tile (rows r, r + 16/PIX, ...),
+// so per staged Gaussian it reuses dx and the shared shared-memory loads PIX times.
+template <int PIX>
+__global__ void __launch_bounds__(TILE_PIX / PIX) k_blend(const uint2 *__restrict__ ranges,
+                                                          const uint32_t *__restrict__ pval,
+                                                          const float4 *__restrict__ sp_a,
+                                                          const float4 *__restrict__ sp_b,
+                                                          const float *__restrict__ sp_c,
+                                                          const uint32_t *__restrict__ cnt, int W, int H, int TX,
+                                                          float bg0, float bg1, float bg2, float *__restrict__ image,
+                                                          unsigned long long *__restrict__ work) {
+    constexpr int NT = TILE_PIX / PIX, RS = TILE / PIX;
+    uint32_t n_eval = 0, n_blend = 0;
+    __shared__ float4 s_a[BATCH], s_b[BATCH];
+    __shared__ float s_c[BATCH];
+    if (cnt[C_STATUS] & ST_CAPACITY) return;
+    const int tile = blockIdx.x, tid = threadIdx.x;
+    const int px = (tile % TX) * TILE + (tid & 15), py0 = (tile / TX) * TILE + (tid >> 4);
+    const float xc = (float)px + 0.5f;
+    float yc[PIX], T[PIX], c0[PIX], c1[PIX], c2[PIX];
+    bool live[PIX];
+    bool done = true;
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        int py = py0 + k * RS;
+        yc[k] = (float)py + 0.5f;
+        T[k] = 1.0f; c0[k] = c1[k] = c2[k] = 0.f;
+        live[k] = px < W && py < H;
+        done &= !live[k];
+    }
+    const uint2 rg = ranges[tile];
+    for (uint32_t base = rg.x; base < rg.y; base += BATCH) {
+        if (__syncthreads_count(done) == NT) break;
+        for (int q = tid; q < BATCH; q += NT) {
+            uint32_t idx = base + q;
+            if (idx < rg.y) {
+                uint32_t g = pval[idx];
+                s_a[q] = sp_a[g];
+                s_b[q] = sp_b[g];
+                s_c[q] = sp_c[g];
+            }
+        }
+        __syncthreads();
+        const int n = min((uint32_t)BATCH, rg.y - base);
+        for (int j = 0; j < n && !done; ++j) {
+            const float4 a = s_a[j];
+            const float4 b = s_b[j];
+            const float cb = s_c[j];
+            const float dx = __fsub_rn(a.x, xc);
+            const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
+            done = true;
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                if (live[k]) {
+                    const float dy = __fsub_rn(a.y, yc[k]);
+                    const float p = __fmaf_rn(bx, dy, __fmaf_rn(__fmul_rn(b.x, dy), dy, hxx));
+                    ++n_eval;
+                    if (p >= SUPPORT_P) {
+                        ++n_blend;
+                        const float alpha = fminf(ALPHA_MAX, b.y * __expf(p));
+                        const float w = alpha * T[k];
+                        c0[k] += b.z * w; c1[k] += b.w * w; c2[k] += cb * w;
+                        T[k] = T[k] * (1.0f - alpha);
+                        if (T[k] < T_MIN) live[k] = false;
+                    }
+                }
+                done &= !live[k];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        int py = py0 + k * RS;
+        if (px < W && py < H) {
+            float *o = image + ((size_t)py * W + px) * 3;
+            o[0] = c0[k] + T[k] * bg0; o[1] = c1[k] + T[k] * bg1; o[2] = c2[k] + T[k] * bg2;
+        }
+    }
+    add_work(work, n_eval, n_blend);
+}
+
+template <int PIX>
+__global__ void __launch_bounds__(TILE_PIX / PIX) k_blend_bwd(const uint2 *__restrict__ ranges,
+                                                              const uint32_t *__restrict__ pval,
+                                                              const float4 *__restrict__ sp_a,
+                                                              const float4 *__restrict__ sp_b,
+                                                              const float *__restrict__ sp_c,
+                                                              const uint32_t *__restrict__ cnt, int W, int H, int TX,
+                                                              float bg0, float bg1, float bg2,
+                                                              const float *__restrict__ dL_dimg,
+                                                              float *__restrict__ g2d,
+                                                              unsigned long long *__restrict__ work) {
+    constexpr int NT = TILE_PIX / PIX, RS = TILE / PIX;
+    uint32_t n_eval = 0, n_contrib = 0;
+    __shared__ float4 s_a[BATCH], s_b[BATCH];
+    __shared__ float s_c[BATCH];
+    __shared__ uint32_t s_g[BATCH];
+    __shared__ float s_grad[BATCH][9];
     __shared__ uint32_t s_maxlast;
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
-    const int px = (tile % TX) * TILE + (tid & 15), py = (tile / TX) * TILE + (tid >> 4);
-    const bool inside = px < W && py < H;
-    const float xc = (float)px + 0.5f, yc = (float)py + 0.5f;
+    const int px = (tile % TX) * TILE + (tid & 15), py0 = (tile / TX) * TILE + (tid >> 4);
+    const float xc = (float)px + 0.5f;
+    float yc[PIX], T[PIX];
+    uint32_t last[PIX];
+    bool live[PIX];
+    bool done = true;
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        int py = py0 + k * RS;
+        yc[k] = (float)py + 0.5f;
+        T[k] = 1.0f; last[k] = 0;
+        live[k] = px < W && py < H;
+        done &= !live[k];
+    }
     const uint2 rg = ranges[tile];
     if (tid == 0) s_maxlast = 0;
-    // ---- pass 1: final transmittance and last contributor of each pixel ----
-    float T = 1.0f;
-    uint32_t last = 0;
-    bool done = !inside;
-    for (uint32_t base = rg.x; base < rg.y; base += RB) {
-        if (__syncthreads_count(done) == RB) break;
-        uint32_t idx = base + tid;
-        if (idx < rg.y) {
-            uint32_t g = pval[idx];
-            s_a[tid] = sp_a[g];
-            s_b[tid] = sp_b[g];
+    // ---- pass 1: each pixel's final transmittance and last contributor ----
+    for (uint32_t base = rg.x; base < rg.y; base += BATCH) {
+        if (__syncthreads_count(done) == NT) break;
+        for (int q = tid; q < BATCH; q += NT) {
+            uint32_t idx = base + q;
+            if (idx < rg.y) {
+                uint32_t g = pval[idx];
+                s_a[q] = sp_a[g];
+                s_b[q] = sp_b[g];
+            }
         }
         __syncthreads();
-        int n = min((uint32_t)RB, rg.y - base);
-        if (!done) {
-            for (int j = 0; j < n; ++j) {
-                float4 a = s_a[j];
-                float4 b = s_b[j];
-                float dx, dy;
-                float p = support_p(a, b.x, xc, yc, dx, dy);
-                if (p < SUPPORT_P) continue;
-                float alpha = fminf(ALPHA_MAX, b.y * __expf(p));
-                T = T * (1.0f - alpha);
-                last = base - rg.x + j + 1;
-                if (T < T_MIN) { done = true; break; }
+        const int n = min((uint32_t)BATCH, rg.y - base);
+        for (int j = 0; j < n && !done; ++j) {
+            const float4 a = s_a[j];
+            const float4 b = s_b[j];
+            const float dx = __fsub_rn(a.x, xc);
+            const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
+            done = true;
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                if (live[k]) {
+                    const float dy = __fsub_rn(a.y, yc[k]);
+                    const float p = __fmaf_rn(bx, dy, __fmaf_rn(__fmul_rn(b.x, dy), dy, hxx));
+                    ++n_eval;
+                    if (p >= SUPPORT_P) {
+                        const float alpha = fminf(ALPHA_MAX, b.y * __expf(p));
+                        T[k] = T[k] * (1.0f - alpha);
+                        last[k] = base - rg.x + j + 1;
+                        if (T[k] < T_MIN) live[k] = false;
+                    }
+                }
+                done &= !live[k];
             }
         }
     }
     __syncthreads();
-    if (inside && last) atomicMax(&s_maxlast, last);
+    {
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < PIX; ++k) m = max(m, last[k]);
+        if (m) atomicMax(&s_maxlast, m);
+    }
     __syncthreads();
     const uint32_t end = rg.x + s_maxlast;
     // ---- pass 2: back to front ----
-    float G0 = 0.f, G1 = 0.f, G2 = 0.f;
-    if (inside) {
-        const float *gi = dL_dimg + ((size_t)py * W + px) * 3;
-        G0 = gi[0]; G1 = gi[1]; G2 = gi[2];
-    }
-    float Q0 = bg0, Q1 = bg1, Q2 = bg2;   // colour behind, divided by the transmittance in front of it
-    for (uint32_t bend = end; bend > rg.x;) {
-        uint32_t bstart = bend - rg.x > (uint32_t)RB ? bend - RB : rg.x;
-        int n = (int)(bend - bstart);
-        __syncthreads();
-        if (tid < n) {
-            uint32_t g = pval[bstart + tid];
-            s_g[tid] = g;
-            s_a[tid] = sp_a[g];
-            s_b[tid] = sp_b[g];
-            s_c[tid] = sp_c[g];
+    float G[PIX][3], Q[PIX][3];
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        int py = py0 + k * RS;
+        G[k][0] = G[k][1] = G[k][2] = 0.f;
+        if (px < W && py < H) {
+            const float *gi = dL_dimg + ((size_t)py * W + px) * 3;
+            G[k][0] = gi[0]; G[k][1] = gi[1]; G[k][2] = gi[2];
         }
-        for (int c = 0; c < 9; ++c) s_grad[tid][c] = 0.f;
+        Q[k][0] = bg0; Q[k][1] = bg1; Q[k][2] = bg2;   // colour behind / transmittance in front of it
+    }
+    for (uint32_t bend = end; bend > rg.x;) {
+        const uint32_t bstart = bend - rg.x > (uint32_t)BATCH ? bend - BATCH : rg.x;
+        const int n = (int)(bend - bstart);
+        __syncthreads();
+        for (int q = tid; q < BATCH; q += NT) {
+            if (q < n) {
+                uint32_t g = pval[bstart + q];
+                s_g[q] = g;
+                s_a[q] = sp_a[g];
+                s_b[q] = sp_b[g];
+                s_c[q] = sp_c[g];
+            }
+#pragma unroll
+            for (int c = 0; c < 9; ++c) s_grad[q][c] = 0.f;
+        }
         __syncthreads();
         for (int j = n - 1; j >= 0; --j) {
-            uint32_t pos = bstart - rg.x + (uint32_t)j;
-            float4 a = s_a[j];
-            float4 b = s_b[j];
-            float dx, dy;
-            float p = support_p(a, b.x, xc, yc, dx, dy);
-            bool contrib = inside && pos < last && p >= SUPPORT_P;
+            const uint32_t pos = bstart - rg.x + (uint32_t)j;
+            const float4 a = s_a[j];
+            const float4 b = s_b[j];
+            const float cb = s_c[j];
+            const float dx = __fsub_rn(a.x, xc);
+            const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
             float gv[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) gv[c] = 0.f;
-            if (contrib) {
-                float e = __expf(p);
-                float raw = b.y * e;
-                float alpha = fminf(ALPHA_MAX, raw);
-                float Tb = T / (1.0f - alpha);
-                float cb = s_c[j];
-                float dA = G0 * (b.z - Q0) + G1 * (b.w - Q1) + G2 * (cb - Q2);
-                dA *= Tb;
-                float wgt = alpha * Tb;
-                gv[6] = G0 * wgt; gv[7] = G1 * wgt; gv[8] = G2 * wgt;
-                Q0 = alpha * b.z + (1.0f - alpha) * Q0;
-                Q1 = alpha * b.w + (1.0f - alpha) * Q1;
-                Q2 = alpha * cb + (1.0f - alpha) * Q2;
-                T = Tb;
-                if (raw <= ALPHA_MAX) {
-                    float dp = dA * alpha;
-                    gv[5] = dA * e;
-                    gv[0] = dp * (2.0f * a.z * dx + a.w * dy);
-                    gv[1] = dp * (2.0f * b.x * dy + a.w * dx);
-                    gv[2] = -0.5f * dp * dx * dx;
-                    gv[3] = -dp * dx * dy;
-                    gv[4] = -0.5f * dp * dy * dy;
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                const float dy = __fsub_rn(a.y, yc[k]);
+                const float p = __fmaf_rn(bx, dy, __fmaf_rn(__fmul_rn(b.x, dy), dy, hxx));
+                n_eval += pos < last[k];
+                if (pos < last[k] && p >= SUPPORT_P) {
+                    any = true;
+                    ++n_contrib;
+                    const float e = __expf(p);
+                    const float raw = b.y * e;
+                    const float alpha = fminf(ALPHA_MAX, raw);
+                    const float Tb = __fdividef(T[k], 1.0f - alpha);
+                    float dA = G[k][0] * (b.z - Q[k][0]) + G[k][1] * (b.w - Q[k][1]) + G[k][2] * (cb - Q[k][2]);
+                    dA *= Tb;
+                    const float wgt = alpha * Tb;
+                    gv[6] += G[k][0] * wgt; gv[7] += G[k][1] * wgt; gv[8] += G[k][2] * wgt;
+                    Q[k][0] = alpha * b.z + (1.0f - alpha) * Q[k][0];
+                    Q[k][1] = alpha * b.w + (1.0f - alpha) * Q[k][1];
+                    Q[k][2] = alpha * cb + (1.0f - alpha) * Q[k][2];
+                    T[k] = Tb;
+                    if (raw <= ALPHA_MAX) {
+                        const float dp = dA * alpha;
+                        gv[5] += dA * e;
+                        gv[0] += dp * (2.0f * a.z * dx + a.w * dy);
+                        gv[1] += dp * (2.0f * b.x * dy + a.w * dx);
+                        gv[2] += -0.5f * dp * dx * dx;
+                        gv[3] += -dp * dx * dy;
+                        gv[4] += -0.5f * dp * dy * dy;
+                    }
                 }
             }
-            if (__ballot_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int c = 0; c < 9; ++c) {
-                    float v = gv[c];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    gv[c] = v;
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) atomicAdd(&s_grad[j][c], gv[c]);
-                }
-            }
+            if (__ballot_sync(0xffffffffu, any)) warp_sum9_to_smem(gv, lane, s_grad[j]);
         }
         __syncthreads();
-        if (tid < n) {
-            float *o = g2d + (size_t)s_g[tid] * 9;
+        for (int q = tid; q < n; q += NT) {
+            float *o = g2d + (size_t)s_g[q] * 9;
 #pragma unroll
             for (int c = 0; c < 9; ++c) {
-                float v = s_grad[tid][c];
+                const float v = s_grad[q][c];
                 if (v != 0.f) atomicAdd(o + c, v);
             }
         }
         bend = bstart;
     }
+    add_work(work + 2, n_eval, n_contrib);
 }
+
+// pixels per thread of the forward and backward blends (compile-time tuning)
+#ifndef LODGS_FWD_PIX
+#define LODGS_FWD_PIX 2
+#endif
+#ifndef LODGS_BWD_PIX
+#define LODGS_BWD_PIX 2
+#endif
+constexpr int FWD_PIX = LODGS_FWD_PIX;
+constexpr int BWD_PIX = LODGS_BWD_PIX;
 
 int ceil_log2(uint64_t x) {
     int b = 0;
@@ -282,7 +413,7 @@ int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, 
     if (rc) return rc;
     k_clamp_pairs<<<1, 1, 0, st>>>(f.cnt, f.cap_pairs);
     count_launches(1);
-    k_emit<<<RGRID, RB, 0, st>>>(order, f.ntiles, f.rect, f.pair_off, f.cnt, k.TX, f.pkey, f.pval);
+    k_emit<<<RGRID, RB, 0, st>>>(order, f.rect, f.pair_off, f.cnt, k.TX, f.pkey, f.pval);
     count_launches(1);
     sm.mark(LODGS_STAGE_EMIT, 1, st);
     sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
@@ -295,10 +426,11 @@ int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, 
     sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
     sm.mark(LODGS_STAGE_BLEND, 0, st);
     LODGS_CUDA(cudaMemsetAsync(f.ranges, 0, n_tiles * sizeof(uint2), st));
+    LODGS_CUDA(cudaMemsetAsync(f.work, 0, 2 * sizeof(unsigned long long), st));
     k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, f.ranges);
     count_launches(1);
-    k_blend<<<(unsigned)n_tiles, RB, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX,
-                                              bg[0], bg[1], bg[2], image);
+    k_blend<FWD_PIX><<<(unsigned)n_tiles, TILE_PIX / FWD_PIX, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX,
+                                              bg[0], bg[1], bg[2], image, f.work);
     count_launches(1);
     sm.mark(LODGS_STAGE_BLEND, 1, st);
     LODGS_CUDA(cudaGetLastError());
@@ -308,8 +440,9 @@ int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, 
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float bg[3], const float *dL_dimage, cudaStream_t st) {
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * 9 * sizeof(float), st));
-    k_blend_bwd<<<(unsigned)n_tiles, RB, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H,
-                                                  k.TX, bg[0], bg[1], bg[2], dL_dimage, f.g2d);
+    LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
+    k_blend_bwd<BWD_PIX><<<(unsigned)n_tiles, TILE_PIX / BWD_PIX, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H,
+                                                  k.TX, bg[0], bg[1], bg[2], dL_dimage, f.g2d, f.work);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;

@@ -459,7 +459,7 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
     // ---- Morton order ----
     DevBuf<uint32_t> k0, k1, v0, v1, hist, dn, hi_g;
     CK(k0.alloc(M)); CK(k1.alloc(M)); CK(v0.alloc(M)); CK(v1.alloc(M)); CK(hi_g.alloc(M));
-    CK(hist.alloc(256 * SORT_GRID)); CK(dn.alloc(1));
+    CK(hist.alloc(SORT_HIST)); CK(dn.alloc(1));
     CK(box.alloc(6));
     {
         float init[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};

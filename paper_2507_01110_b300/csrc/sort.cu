@@ -3,9 +3,10 @@
 // Both run on a fixed grid and read the element count from device memory, so a
 // render needs no host round trip between its stages.  The sort is the
 // reduce-then-scan form: per pass an upsweep builds a digit histogram per block
-// (each block owns one contiguous chunk), a single block scans the
-// digit-major histogram table, and a downsweep ranks each tile of its chunk
-// with warp match/ballot ranking and scatters it.  No block waits on another.
+// (each block owns one contiguous chunk), one warp per digit scans that digit's
+// block counts, and a downsweep (which scans the 256 digit totals itself) ranks
+// each tile of its chunk with warp match/ballot ranking and scatters it.  No
+// block waits on another.
 #include "lodgs_internal.cuh"
 
 namespace lodgs {
@@ -50,52 +51,51 @@ __global__ void __launch_bounds__(ST_THREADS) k_radix_upsweep(const uint32_t *__
     }
 }
 
-// exclusive scan in place of `len` uint32 values by one block of 1024 threads
-__global__ void __launch_bounds__(1024) k_scan_single(uint32_t *__restrict__ a, int len) {
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < len; base += 1024) {
-        int i = base + tid;
-        uint32_t v = i < len ? a[i] : 0u;
+// Per digit d (one warp each): exclusive scan in place of the per-block counts
+// hist[d*G .. d*G+G) and the digit total in totals[d].
+__global__ void __launch_bounds__(256) k_digit_scan(uint32_t *__restrict__ hist, int G, uint32_t *__restrict__ totals) {
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
+    uint32_t carry = 0;
+    uint32_t *h = hist + (size_t)d * G;
+    for (int base = 0; base < G; base += 32) {
+        int i = base + lane;
+        uint32_t v = i < G ? h[i] : 0u;
         uint32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t w = s_warp[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            s_warp[lane] = w;
-        }
-        __syncthreads();
-        uint32_t carry = s_carry;
-        uint32_t excl = carry + (warp ? s_warp[warp - 1] : 0u) + x - v;
-        if (i < len) a[i] = excl;
-        __syncthreads();
-        if (tid == 1023) s_carry = carry + s_warp[31];
-        __syncthreads();
+        if (i < G) h[i] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
     }
+    if (lane == 0) totals[d] = carry;
 }
 
 __global__ void __launch_bounds__(ST_THREADS) k_radix_downsweep(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ d_n, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist) {
+    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals) {
     __shared__ uint32_t s_off[RADIX];
     __shared__ uint32_t s_tot[RADIX];
     __shared__ uint32_t s_w[ST_WARPS][RADIX];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int d = tid; d < RADIX; d += ST_THREADS) s_off[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+    {   // digit bases: exclusive scan of the digit totals (RADIX == ST_THREADS)
+        uint32_t t = totals[tid];
+        uint32_t x = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_tot[warp] = x;
+        __syncthreads();
+        uint32_t wb = 0;
+        for (int w = 0; w < warp; ++w) wb += s_tot[w];
+        s_off[tid] = wb + x - t + hist[(size_t)tid * gridDim.x + blockIdx.x];
+        __syncthreads();
+    }
     uint32_t begin, end;
     chunk_range(*d_n, begin, end);
     const uint32_t lt = (1u << lane) - 1u;
@@ -265,11 +265,12 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
         const uint32_t *vi = alt ? vals_alt : vals;
         uint32_t *ko = alt ? keys : keys_alt;
         uint32_t *vo = alt ? vals : vals_alt;
+        uint32_t *totals = hist + RADIX * SORT_GRID;
         k_radix_upsweep<<<SORT_GRID, ST_THREADS, 0, st>>>(ki, d_n, shift, mask, hist);
         count_launches(1);
-        k_scan_single<<<1, 1024, 0, st>>>(hist, RADIX * SORT_GRID);
+        k_digit_scan<<<RADIX / 8, 256, 0, st>>>(hist, SORT_GRID, totals);
         count_launches(1);
-        k_radix_downsweep<<<SORT_GRID, ST_THREADS, 0, st>>>(ki, vi, ko, vo, d_n, shift, mask, hist);
+        k_radix_downsweep<<<SORT_GRID, ST_THREADS, 0, st>>>(ki, vi, ko, vo, d_n, shift, mask, hist, totals);
         count_launches(1);
         alt = !alt;
     }
