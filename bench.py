@@ -225,10 +225,12 @@ def run_lodgs(args, rank: int, world: int):
     torch.cuda.synchronize()
     launches0 = _lib.lib().lodgs_kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for v in order:
         step(v, targets_d[v])
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     launches = _lib.lib().lodgs_kernel_launches() - launches0
     if world > 1:

@@ -77,7 +77,7 @@ typedef struct {
     int64_t n_spt_cut;               /* SPTs handed to Algorithm 2 */
     int64_t n_spt_scanned;           /* SPT entries tested, sum of the binary-search prefixes */
     int64_t n_visible;               /* selected nodes in front of the near plane with a non-empty tile rect */
-    int64_t n_pairs;                 /* (Gaussian, tile) pairs sorted */
+    int64_t n_pairs;                 /* (Gaussian, tile) pairs whose support reaches the tile (blended) */
     int32_t status;                  /* LODGS_OK, or LODGS_E_CAPACITY / LODGS_E_TIMEOUT from the device */
     int32_t width, height;
 } lodgs_frame_stats;

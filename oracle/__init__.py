@@ -222,7 +222,8 @@ def sort_pairs(proj: dict, width: int, height: int) -> dict:
     tile_start = np.zeros(TX * TY + 1, dtype=np.int64)
     npairs = np.zeros(1, dtype=np.int64)
     rc = lib().or_sort_pairs(C.c_int64(proj["n"]), _p(proj["vis"]), _p(proj["rect"]), _p(proj["key"]),
-                             C.c_int(TX), C.c_int(TY), C.c_int64(cap), _p(npairs), _p(pair_i), _p(tile_start))
+                             _p(proj["f32"]), C.c_int(TX), C.c_int(TY), C.c_int64(cap), _p(npairs), _p(pair_i),
+                             _p(tile_start))
     assert rc == 0
     return {"pair_i": pair_i[: int(npairs[0])].copy(), "tile_start": tile_start, "TX": TX, "TY": TY}
 
@@ -232,6 +233,12 @@ def _win(window):
         return None
     w = np.ascontiguousarray(window, dtype=np.int32)
     return w
+
+
+def tile_keep(u, v, ca, cb, cc, tx, ty) -> bool:
+    """Tile support test D9 for one (Gaussian, tile); (ca, cb, cc) is the conic."""
+    f = C.c_float
+    return bool(lib().or_tile_keep(f(u), f(v), f(ca), f(cb), f(cc), C.c_int(int(tx)), C.c_int(int(ty))))
 
 
 def blend(proj: dict, pairs: dict, width: int, height: int, bg=(0.0, 0.0, 0.0), window=None) -> dict:

@@ -33,6 +33,8 @@
  *   D8 support  dx = u - (px + 0.5f), dy = v - (py + 0.5f)
  *               p = fmaf(nb*dx, dy, fmaf(nhc*dy, dy, (nha*dx)*dx))
  *               nha = -0.5f*A, nhc = -0.5f*C, nb = -B ; support iff p >= -4.5f
+ *   D9 tile     a (tile, Gaussian) pair is kept iff the support ellipse can
+ *               reach a pixel centre of the tile: see tile_keep() below
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC
  */
@@ -787,22 +789,53 @@ static int cmp_pair(const void *a, const void *b) {
     return (x->i > y->i) - (x->i < y->i);
 }
 
-int or_sort_pairs(int64_t n, const int32_t *vis, const int32_t *rect, const uint32_t *key, int TX, int TY,
-                  int64_t cap, int64_t *n_pairs, int64_t *pair_i, int64_t *tile_start) {
+/* Tile support test D9 (float32, evaluated as written).  The support exponent
+ * p(x, y) = -1/2 (A dx^2 + 2 B dx dy + C dy^2), dx = u - x, dy = v - y, is a
+ * concave quadratic; its maximum over the rectangle spanned by the tile's pixel
+ * centres is 0 if (u, v) lies inside, else it lies on an edge, where it is the
+ * 1-D maximum clamped to the edge.  The pair is kept iff that maximum is at
+ * least -4.5 - 0.01; the margin makes the test conservative against rounding,
+ * so a dropped pair never had a pixel passing D8 and the image is unchanged. */
+static float edge_p(float A, float B, float C, float dx, float dy) {
+    return -0.5f * (A * dx * dx + C * dy * dy) - B * dx * dy;
+}
+
+int or_tile_keep(float u, float v, float A, float B, float C, int tx, int ty) {
+    float X0 = (float)(TILE * tx) + 0.5f, X1 = X0 + 15.0f;
+    float Y0 = (float)(TILE * ty) + 0.5f, Y1 = Y0 + 15.0f;
+    if (u >= X0 && u <= X1 && v >= Y0 && v <= Y1) return 1;
+    float best = -INFINITY;
+    float xs[2] = {X0, X1}, ys[2] = {Y0, Y1};
+    for (int k = 0; k < 2; ++k) {
+        float dx = u - xs[k];                       /* vertical edge x = xs[k] */
+        float y = fminf(fmaxf(v + (B * dx) / C, Y0), Y1);
+        best = fmaxf(best, edge_p(A, B, C, dx, v - y));
+        float dy = v - ys[k];                       /* horizontal edge y = ys[k] */
+        float x = fminf(fmaxf(u + (B * dy) / A, X0), X1);
+        best = fmaxf(best, edge_p(A, B, C, u - x, dy));
+    }
+    return best >= -4.51f;
+}
+
+int or_sort_pairs(int64_t n, const int32_t *vis, const int32_t *rect, const uint32_t *key, const float *f32,
+                  int TX, int TY, int64_t cap, int64_t *n_pairs, int64_t *pair_i, int64_t *tile_start) {
     int64_t np = 0;
     for (int64_t i = 0; i < n; ++i)
         if (vis[i]) np += (int64_t)(rect[4 * i + 2] - rect[4 * i]) * (rect[4 * i + 3] - rect[4 * i + 1]);
-    *n_pairs = np;
-    if (np > cap) return -1;
+    if (np > cap) { *n_pairs = np; return -1; }
     pair_t *p = malloc(sizeof(pair_t) * (size_t)(np + 1));
     int64_t w = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (!vis[i]) continue;
+        const float *g = f32 + 5 * i;
         for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ++ty)
             for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; ++tx) {
+                if (!or_tile_keep(g[0], g[1], g[2], g[3], g[4], tx, ty)) continue;
                 p[w].tile = (int64_t)ty * TX + tx; p[w].key = key[i]; p[w].i = i; ++w;
             }
     }
+    np = w;
+    *n_pairs = np;
     qsort(p, (size_t)np, sizeof(pair_t), cmp_pair);
     int64_t nt = (int64_t)TX * TY;
     for (int64_t t = 0; t <= nt; ++t) tile_start[t] = 0;

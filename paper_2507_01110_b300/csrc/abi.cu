@@ -362,7 +362,7 @@ int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {
     s->n_spt_cut = h[C_NEMIT];
     s->n_spt_scanned = h[C_WORK];
     s->n_visible = h[C_NVIS];
-    s->n_pairs = h[C_NPAIR];
+    s->n_pairs = h[C_NKEPT];
     s->width = fr->k.W;
     s->height = fr->k.H;
     s->status = LODGS_OK;
@@ -411,7 +411,7 @@ int lodgs_frame_export(lodgs_frame *fr, uint32_t *pair_index, int64_t cap_pairs,
     LODGS_CUDA(cudaStreamSynchronize(fr->stream));
     LODGS_CUDA(cudaMemcpy(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost));
     if (fr->h_cnt[C_STATUS] & ST_CAPACITY) { set_error("frame_export: last render overflowed"); return LODGS_E_CAPACITY; }
-    const uint64_t np = fr->h_cnt[C_NPAIR_EFF], ns = fr->h_cnt[C_NSEL_EFF];
+    const uint64_t np = fr->h_cnt[C_NKEPT], ns = fr->h_cnt[C_NSEL_EFF];
     const uint64_t nt = (uint64_t)fr->k.TX * fr->k.TY;
     if (pair_index) {
         if ((int64_t)np > cap_pairs) { set_error("frame_export: pair buffer too small"); return LODGS_E_INVALID; }

@@ -70,6 +70,7 @@ enum {
     C_NPAIR_EFF = 7, // pairs processed (0 on overflow)
     C_NVIS = 8,      // visible Gaussians
     C_STATUS = 9,    // ST_* bits
+    C_NKEPT = 10,    // pairs kept by the tile support test (sorted first)
     C_COUNT = 16
 };
 

@@ -37,12 +37,43 @@ __global__ void k_clamp_pairs(uint32_t *cnt, uint64_t cap_pairs) {
     cnt[C_NPAIR_EFF] = n;
 }
 
-// One thread per (tile, Gaussian) pair: pair p belongs to the last depth rank r
-// with pair_off[r] <= p (binary search), and is the k-th tile of its rectangle
-// in row-major order.  Every thread writes one pair, whatever the footprints.
+// Tile support test (float32, explicitly rounded).  The support exponent is a
+// concave quadratic; its maximum over the rectangle of the tile's pixel centres
+// is 0 when the mean lies inside, otherwise it lies on an edge at the clamped
+// 1-D maximum.  The pair is kept iff that maximum is >= -4.5 - 0.01, a
+// conservative margin: a dropped pair has no pixel passing the support test, so
+// the image is unchanged while the blend skips tiles the ellipse never reaches.
+__device__ __forceinline__ float edge_p(float A, float B, float C, float dx, float dy) {
+    const float s = __fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(C, dy), dy));
+    return __fsub_rn(__fmul_rn(-0.5f, s), __fmul_rn(__fmul_rn(B, dx), dy));
+}
+
+__device__ __forceinline__ bool tile_keep(float u, float v, float A, float B, float C, uint32_t tx, uint32_t ty) {
+    const float X0 = __fadd_rn((float)(TILE * tx), 0.5f), X1 = __fadd_rn(X0, 15.0f);
+    const float Y0 = __fadd_rn((float)(TILE * ty), 0.5f), Y1 = __fadd_rn(Y0, 15.0f);
+    if (u >= X0 && u <= X1 && v >= Y0 && v <= Y1) return true;
+    float best = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float xe = k ? X1 : X0, ye = k ? Y1 : Y0;
+        const float dx = __fsub_rn(u, xe);
+        const float y = fminf(fmaxf(__fadd_rn(v, __fdiv_rn(__fmul_rn(B, dx), C)), Y0), Y1);
+        best = fmaxf(best, edge_p(A, B, C, dx, __fsub_rn(v, y)));
+        const float dy = __fsub_rn(v, ye);
+        const float x = fminf(fmaxf(__fadd_rn(u, __fdiv_rn(__fmul_rn(B, dy), A)), X0), X1);
+        best = fmaxf(best, edge_p(A, B, C, __fsub_rn(u, x), dy));
+    }
+    return best >= -4.51f;
+}
+
+// One thread per rectangle pair: pair p belongs to the last depth rank r with
+// pair_off[r] <= p (binary search) and is the k-th tile of its rectangle in
+// row-major order.  Pairs whose tile the support ellipse cannot reach get the
+// key n_tiles, which the tile sort moves behind every real tile.
 __global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restrict__ rect,
+                       const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
                        const uint32_t *__restrict__ pair_off, const uint32_t *__restrict__ cnt, int TX,
-                       uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+                       uint32_t n_tiles, uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
     const uint32_t P = cnt[C_NPAIR_EFF], n = cnt[C_NSEL_EFF];
     for (uint32_t p = blockIdx.x * RB + threadIdx.x; p < P; p += gridDim.x * RB) {
         uint32_t a = 0, b = n;
@@ -50,22 +81,30 @@ __global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restri
             uint32_t m = (a + b) >> 1;
             if (pair_off[m] <= p) a = m; else b = m;
         }
-        uint32_t g = order[a];
-        uint2 rc = rect[g];
-        uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
-        uint32_t w = x1 - x0, k = p - pair_off[a];
-        uint32_t ty = y0 + k / w, tx = x0 + k % w;
-        pkey[p] = ty * (uint32_t)TX + tx;
+        const uint32_t g = order[a];
+        const uint2 rc = rect[g];
+        const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+        const uint32_t w = x1 - x0, k = p - pair_off[a];
+        const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+        const float4 sa = sp_a[g];
+        const float nhc = sp_b[g].x;
+        const bool keep = tile_keep(sa.x, sa.y, -2.0f * sa.z, -sa.w, -2.0f * nhc, tx, ty);
+        pkey[p] = keep ? ty * (uint32_t)TX + tx : n_tiles;
         pval[p] = g;
     }
 }
 
-__global__ void k_ranges(const uint32_t *__restrict__ pkey, const uint32_t *__restrict__ cnt, uint2 *__restrict__ ranges) {
+__global__ void k_ranges(const uint32_t *__restrict__ pkey, uint32_t *__restrict__ cnt, uint32_t n_tiles,
+                         uint2 *__restrict__ ranges) {
     uint32_t n = cnt[C_NPAIR_EFF];
     for (uint32_t p = blockIdx.x * RB + threadIdx.x; p < n; p += gridDim.x * RB) {
         uint32_t t = pkey[p];
+        if (t >= n_tiles) continue;                       // dropped pairs sort behind every tile
         if (p == 0 || pkey[p - 1] != t) ranges[t].x = p;
-        if (p + 1 == n || pkey[p + 1] != t) ranges[t].y = p + 1;
+        if (p + 1 == n || pkey[p + 1] != t) {
+            ranges[t].y = p + 1;
+            if (p + 1 == n || pkey[p + 1] >= n_tiles) cnt[C_NKEPT] = p + 1;
+        }
     }
 }
 
@@ -413,13 +452,14 @@ int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, 
     if (rc) return rc;
     k_clamp_pairs<<<1, 1, 0, st>>>(f.cnt, f.cap_pairs);
     count_launches(1);
-    k_emit<<<RGRID, RB, 0, st>>>(order, f.rect, f.pair_off, f.cnt, k.TX, f.pkey, f.pval);
+    const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
+    k_emit<<<RGRID, RB, 0, st>>>(order, f.rect, f.sp_a, f.sp_b, f.pair_off, f.cnt, k.TX, (uint32_t)n_tiles, f.pkey,
+                                 f.pval);
     count_launches(1);
     sm.mark(LODGS_STAGE_EMIT, 1, st);
     sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
-    const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     rc = radix_sort_pairs(f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.cnt + C_NPAIR_EFF, (uint32_t)f.cap_pairs, 0,
-                          ceil_log2(n_tiles), f.sort_hist, st, &alt);
+                          ceil_log2(n_tiles + 1), f.sort_hist, st, &alt);
     if (rc) return rc;
     const uint32_t *skey = alt ? f.pkey_alt : f.pkey;
     f.sorted_pval = alt ? f.pval_alt : f.pval;
@@ -427,7 +467,7 @@ int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, 
     sm.mark(LODGS_STAGE_BLEND, 0, st);
     LODGS_CUDA(cudaMemsetAsync(f.ranges, 0, n_tiles * sizeof(uint2), st));
     LODGS_CUDA(cudaMemsetAsync(f.work, 0, 2 * sizeof(unsigned long long), st));
-    k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, f.ranges);
+    k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, (uint32_t)n_tiles, f.ranges);
     count_launches(1);
     k_blend<FWD_PIX><<<(unsigned)n_tiles, TILE_PIX / FWD_PIX, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX,
                                               bg[0], bg[1], bg[2], image, f.work);

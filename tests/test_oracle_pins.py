@@ -500,23 +500,86 @@ def test_colour_degree0_is_base_colour(oracle_lib):
 # sort and blend
 # ---------------------------------------------------------------------------
 
-def test_sort_matches_lexsort(oracle_lib, scene1):
-    cfg, sc = scene1
-    cam = cfg["cameras"][0]
-    sel, _ = oracle_lib.select(sc, cam)
-    pr = oracle_lib.project(sc, sel, cam)
-    pairs = oracle_lib.sort_pairs(pr, cam.width, cam.height)
-    TX = pairs["TX"]
+def _rect_pairs(pr, TX):
     tiles, keys, idx = [], [], []
     for i in np.nonzero(pr["vis"])[0]:
         x0, y0, x1, y1 = pr["rect"][i]
         for ty in range(y0, y1):
             for tx in range(x0, x1):
                 tiles.append(ty * TX + tx); keys.append(pr["key"][i]); idx.append(i)
-    tiles, keys, idx = map(np.array, (tiles, keys, idx))
+    return map(np.array, (tiles, keys, idx))
+
+
+def test_sort_matches_lexsort_of_kept_pairs(oracle_lib, scene1):
+    """The pair list is the (tile, depth, index) lexsort of the rectangle pairs
+    that pass the tile support test D9."""
+    cfg, sc = scene1
+    cam = cfg["cameras"][0]
+    sel, _ = oracle_lib.select(sc, cam)
+    pr = oracle_lib.project(sc, sel, cam)
+    pairs = oracle_lib.sort_pairs(pr, cam.width, cam.height)
+    TX = pairs["TX"]
+    tiles, keys, idx = _rect_pairs(pr, TX)
+    f = pr["f32"]
+    keep = np.array([oracle_lib.tile_keep(*f[i], t % TX, t // TX) for t, i in zip(tiles, idx)])
+    assert 0 < keep.sum() < len(keep)
+    tiles, keys, idx = tiles[keep], keys[keep], idx[keep]
     o = np.lexsort((idx, keys, tiles))
     assert np.array_equal(pairs["pair_i"], idx[o])
     assert np.array_equal(np.diff(pairs["tile_start"]), np.bincount(tiles, minlength=len(pairs["tile_start"]) - 1))
+
+
+def _support_f32(u, v, A, B, C, px, py):
+    f32 = np.float32
+    dx = f32(u) - (f32(px) + f32(0.5))
+    dy = f32(v) - (f32(py) + f32(0.5))
+    nha, nhc, nb = f32(-0.5) * f32(A), f32(-0.5) * f32(C), -f32(B)
+    # fmaf(nb*dx, dy, fmaf(nhc*dy, dy, (nha*dx)*dx)) with exact fused steps in float64
+    inner = f32(np.float64(nhc * dy) * np.float64(dy) + np.float64((nha * dx) * dx))
+    return f32(np.float64(nb * dx) * np.float64(dy) + np.float64(inner))
+
+
+def test_tile_support_test_is_conservative(oracle_lib):
+    """Brute force over every pixel centre: a tile that D9 drops has no pixel
+    passing the float32 support test D8, for random anisotropic Gaussians."""
+    rng = np.random.default_rng(21)
+    kept = dropped = 0
+    for _ in range(300):
+        ang = rng.uniform(0, np.pi)
+        s1, s2 = rng.uniform(0.5, 40.0), rng.uniform(0.5, 6.0)
+        Rm = np.array([[np.cos(ang), -np.sin(ang)], [np.sin(ang), np.cos(ang)]])
+        S = Rm @ np.diag([s1 * s1, s2 * s2]) @ Rm.T + 0.3 * np.eye(2)
+        Q = np.linalg.inv(S)
+        A, B, C = (np.float32(Q[0, 0]), np.float32(Q[0, 1]), np.float32(Q[1, 1]))
+        u, v = np.float32(rng.uniform(-40, 104)), np.float32(rng.uniform(-40, 104))
+        for tx in range(4):
+            for ty in range(4):
+                k = oracle_lib.tile_keep(u, v, A, B, C, tx, ty)
+                kept += k
+                if not k:
+                    dropped += 1
+                    for py in range(16 * ty, 16 * ty + 16):
+                        for px in range(16 * tx, 16 * tx + 16):
+                            assert _support_f32(u, v, A, B, C, px, py) < np.float32(-4.5)
+    assert kept > 100 and dropped > 100
+
+
+def test_tile_culling_leaves_the_image_unchanged(oracle_lib, scene1):
+    """Blending the full rectangle pair list gives the same image, bit for bit."""
+    cfg, sc = scene1
+    cam = cfg["cameras"][0]
+    sel, _ = oracle_lib.select(sc, cam)
+    pr = oracle_lib.project(sc, sel, cam)
+    culled = oracle_lib.sort_pairs(pr, cam.width, cam.height)
+    TX = culled["TX"]
+    tiles, keys, idx = _rect_pairs(pr, TX)
+    o = np.lexsort((idx, keys, tiles))
+    full = {"pair_i": idx[o].astype(np.int64), "TX": TX, "TY": culled["TY"],
+            "tile_start": np.concatenate([[0], np.cumsum(np.bincount(tiles, minlength=TX * culled["TY"]))]).astype(np.int64)}
+    assert len(full["pair_i"]) > len(culled["pair_i"])
+    a = oracle_lib.blend(pr, culled, cam.width, cam.height)
+    b = oracle_lib.blend(pr, full, cam.width, cam.height)
+    assert np.array_equal(a["image"], b["image"]) and np.array_equal(a["T_final"], b["T_final"])
 
 
 def test_lone_gaussian_analytic_image(oracle_lib):
