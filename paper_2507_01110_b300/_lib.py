@@ -64,6 +64,7 @@ _SIGS = {
     "lodgs_frame_create": (C.c_int, [_P, C.POINTER(_P)]),
     "lodgs_frame_free": (None, [_P]),
     "lodgs_select_lod": (C.c_int, [_P, C.POINTER(Camera), _P, _P]),
+    "lodgs_select_lod_noalloc": (C.c_int, [_P, C.POINTER(Camera), _P, C.c_int64, _P, _P]),
     "lodgs_frame_selection": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_int64)]),
     "lodgs_render": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, _P]),
