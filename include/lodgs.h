@@ -160,6 +160,51 @@ int lodgs_select_lod(lodgs_scene *scene, const lodgs_camera *cam, lodgs_frame *f
 int lodgs_select_lod_noalloc(lodgs_scene *scene, const lodgs_camera *cam, uint32_t *d_rows, int64_t capacity,
                              uint32_t *d_count, void *stream);
 
+/*
+ * Out-of-core mode (Sec. 4.4 "Caching on the GPU", Eq. 7, Algorithm 3): all
+ * records in pinned host memory, the scene structure and the upper
+ * hierarchy's records on the device, and a device slab of SPT records managed
+ * LRU.  A miss streams the contiguous prefix of the SPT's records that the cut
+ * can select (one cudaMemcpyAsync per SPT on a copy stream).
+ */
+typedef struct lodgs_cache lodgs_cache; /* opaque, library-owned */
+
+typedef struct {
+    int64_t capacity_bytes;  /* device slab for SPT records (the upper rows are extra) */
+    float d_min, d_max;      /* reuse window of Eq. 7 on x_now / x_cached, x = tau d / f; [1,1] = exact */
+    int32_t release_scene_rows; /* free the scene's device copy of the records after copying them to host */
+} lodgs_cache_params;
+
+typedef struct {
+    int64_t spt_hits;        /* SPTs whose cached cut was reused (inside the Eq. 7 window) */
+    int64_t spt_resident;    /* SPTs cut at the current distance from records already on the device */
+    int64_t spt_loaded;      /* SPTs whose record prefix was copied from host memory */
+    int64_t bytes_streamed;  /* host-to-device bytes issued for this view */
+    int64_t evictions;       /* cached SPTs evicted (least recently used) for this view */
+    int64_t cached_spts, cached_records;  /* cache contents after this view */
+} lodgs_stream_stats;
+
+/* Create the cache: copies the scene's records to pinned host memory (the
+ * scene's device copy is freed if release_scene_rows), allocates the device
+ * slab and copies the upper hierarchy's records.  Synchronous. */
+int lodgs_cache_create(lodgs_scene *scene, const lodgs_cache_params *params, lodgs_cache **out);
+void lodgs_cache_free(lodgs_cache *cache);
+/* Device records to pass as `rows` to lodgs_render / lodgs_render_backward for
+ * frames selected with lodgs_stream_nodes (upper rows, then the slab). */
+int lodgs_cache_records(lodgs_cache *cache, float **d_records);
+
+/*
+ * LoD cut of one camera through the cache, replacing lodgs_select_lod for
+ * out-of-core scenes: upper cut on `stream`, one host synchronisation to take
+ * the per-SPT cache decisions (hit / resident / load), copies of missing
+ * prefixes on `copy_stream`, then the SPT cut on `stream`, which is made to
+ * wait for the copies.  Renders that read the cache must run on `stream` (or
+ * be complete) before the next call, because evicted slab ranges are reused.
+ * Returns LODGS_E_CAPACITY if one view's SPT records do not fit the slab.
+ */
+int lodgs_stream_nodes(lodgs_scene *scene, lodgs_cache *cache, const lodgs_camera *cam, lodgs_frame *frame,
+                       void *stream, void *copy_stream, lodgs_stream_stats *stats);
+
 /* Device pointer to the frame's selected rows (uint32, ascending) and, after a
  * stream sync, their count. */
 int lodgs_frame_selection(lodgs_frame *frame, const uint32_t **d_rows, int64_t *n_selected);

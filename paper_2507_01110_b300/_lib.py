@@ -44,6 +44,17 @@ class SceneInfo(C.Structure):
                 ("stride", C.c_int32), ("d_rows", C.c_void_p)]
 
 
+class CacheParams(C.Structure):
+    _fields_ = [("capacity_bytes", C.c_int64), ("d_min", C.c_float), ("d_max", C.c_float),
+                ("release_scene_rows", C.c_int32)]
+
+
+class StreamStats(C.Structure):
+    _fields_ = [("spt_hits", C.c_int64), ("spt_resident", C.c_int64), ("spt_loaded", C.c_int64),
+                ("bytes_streamed", C.c_int64), ("evictions", C.c_int64), ("cached_spts", C.c_int64),
+                ("cached_records", C.c_int64)]
+
+
 class FrameStats(C.Structure):
     _fields_ = [("n_selected", C.c_int64), ("n_upper_selected", C.c_int64), ("n_spt_cut", C.c_int64),
                 ("n_spt_scanned", C.c_int64), ("n_visible", C.c_int64), ("n_pairs", C.c_int64),
@@ -66,6 +77,10 @@ _SIGS = {
     "lodgs_select_lod": (C.c_int, [_P, C.POINTER(Camera), _P, _P]),
     "lodgs_select_lod_noalloc": (C.c_int, [_P, C.POINTER(Camera), _P, C.c_int64, _P, _P]),
     "lodgs_frame_selection": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_int64)]),
+    "lodgs_cache_create": (C.c_int, [_P, C.POINTER(CacheParams), C.POINTER(_P)]),
+    "lodgs_cache_free": (None, [_P]),
+    "lodgs_cache_records": (C.c_int, [_P, C.POINTER(_P)]),
+    "lodgs_stream_nodes": (C.c_int, [_P, _P, C.POINTER(Camera), _P, _P, _P, C.POINTER(StreamStats)]),
     "lodgs_render": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, _P]),
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),

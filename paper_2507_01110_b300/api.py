@@ -173,6 +173,52 @@ class Frame:
             pass
 
 
+class Cache:
+    """Out-of-core node cache of a scene (records in pinned host memory)."""
+
+    def __init__(self, scene: Scene, capacity_bytes: int, d_min: float = 0.9, d_max: float = 1.1,
+                 release_scene_rows: bool = False):
+        self.scene = scene
+        p = _lib.CacheParams(int(capacity_bytes), float(d_min), float(d_max), int(release_scene_rows))
+        h = C.c_void_p()
+        check(lib().lodgs_cache_create(scene.handle, C.byref(p), C.byref(h)))
+        self._h = h
+        ptr = C.c_void_p()
+        check(lib().lodgs_cache_records(self._h, C.byref(ptr)))
+        rec = scene.stride * 4
+        n = scene.n_upper_rows + int(capacity_bytes) // rec
+        self.records = _device_view(ptr.value, (n, scene.stride), "<f4")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().lodgs_cache_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stream_nodes(scene: Scene, cache: Cache, camera, frame: Frame | None = None, stream=None,
+                 copy_stream=None) -> tuple[Frame, dict]:
+    """LoD cut through the out-of-core cache; returns the frame and the view's
+    streaming statistics.  Render it with rows=cache.records."""
+    fr = frame if frame is not None else Frame(scene)
+    cs = camera_struct(camera)
+    st = _lib.StreamStats()
+    cpy = copy_stream if copy_stream is not None else (stream or torch.cuda.current_stream())
+    check(lib().lodgs_stream_nodes(scene.handle, cache.handle, C.byref(cs), fr.handle, _stream_ptr(stream),
+                                   C.c_void_p(cpy.cuda_stream), C.byref(st)))
+    fr.camera = camera
+    return fr, {k: getattr(st, k) for k, _ in _lib.StreamStats._fields_}
+
+
 def build_hierarchy(leaves, sh_degree: int, spt_volume: float, kappa: float) -> Scene:
     """Leaves (n x stride float32, numpy or torch) -> Scene.  See lodgs_build_hierarchy."""
     lib()

@@ -58,24 +58,6 @@ CamK make_camk(const lodgs_camera &c) {
 
 using namespace lodgs;
 
-struct lodgs_frame {
-    lodgs_scene *scene = nullptr;
-    FrameBufs f;
-    uint32_t *h_cnt = nullptr;          // pinned mirror of the device counters
-    cudaStream_t stream = 0;
-    CamK k{};
-    bool selected = false, rendered = false;
-    uint64_t want_sel = 0, want_pairs = 0;
-    // stage timing: ev[2s] / ev[2s+1] bracket stage s
-    bool prof = false;
-    cudaEvent_t ev[2 * LODGS_NUM_STAGES] = {};
-    bool ran[LODGS_NUM_STAGES] = {};
-    void mark(int stage, int end, cudaStream_t st) {
-        if (!prof) return;
-        cudaEventRecord(ev[2 * stage + end], st);
-        if (end) ran[stage] = true;
-    }
-};
 
 namespace {
 
@@ -128,7 +110,8 @@ int ensure_pairs(lodgs_frame *fr, uint64_t want) {
 void free_frame_bufs(FrameBufs &f) {
     void *ps[] = {f.cnt, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
                   f.sort_hist, f.sp_a, f.sp_b, f.sp_c, f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.rect, f.ntiles,
-                  f.nt_sorted, f.pair_off, f.g2d, f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.ranges, f.work};
+                  f.nt_sorted, f.pair_off, f.g2d, f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.ranges, f.work,
+                  f.sel_src, f.emit_src};
     for (void *p : ps)
         if (p) cudaFree(p);
     f = FrameBufs();
@@ -265,6 +248,7 @@ int lodgs_select_lod(lodgs_scene *sc, const lodgs_camera *cam, lodgs_frame *fr, 
     cudaStream_t st = (cudaStream_t)stream;
     fr->k = make_camk(*cam);
     fr->stream = st;
+    fr->f.use_src = false;
     for (bool &r : fr->ran) r = false;
     fr->mark(LODGS_STAGE_SELECT, 0, st);
     LODGS_CUDA(cudaMemsetAsync(fr->f.cnt, 0, C_COUNT * sizeof(uint32_t), st));
@@ -310,6 +294,10 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     // reset the render's counters and status (the selection's counters stay)
     LODGS_CUDA(cudaMemsetAsync(fr->f.cnt + C_NSEL_EFF, 0, (C_COUNT - C_NSEL_EFF) * sizeof(uint32_t), st));
     fr->mark(LODGS_STAGE_PROJECT, 0, st);
+    if (!rows && !sc->d_rows) {
+        set_error("render: the scene's records live in host memory; pass the cache's device records");
+        return LODGS_E_INVALID;
+    }
     int rc = launch_project(sc, rows ? rows : sc->d_rows, fr->k, fr->f, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_PROJECT, 1, st);
@@ -346,6 +334,10 @@ int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, c
     if (rc) return rc;
     fr->mark(LODGS_STAGE_BLEND_BWD, 1, st);
     fr->mark(LODGS_STAGE_PROJECT_BWD, 0, st);
+    if (!rows && !sc->d_rows) {
+        set_error("render_backward: the scene's records live in host memory; pass the cache's device records");
+        return LODGS_E_INVALID;
+    }
     rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->k, fr->f, grad_rows, dense, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_PROJECT_BWD, 1, st);

@@ -111,6 +111,9 @@ struct FrameBufs {
     uint32_t *cnt = nullptr;         // C_COUNT device counters
     // selection (capacity n_nodes / n_spt)
     uint32_t *sel_rows = nullptr, *emit_j = nullptr, *high = nullptr, *work_off = nullptr;
+    uint32_t *sel_src = nullptr;      // record slot of each selected node (out-of-core renders)
+    uint32_t *emit_src = nullptr;     // slot of entry 0 of each emitted SPT (out-of-core renders)
+    bool use_src = false;             // project through sel_src instead of sel_rows
     float *emit_x = nullptr;
     uint32_t *block_counts = nullptr, *scan_bsum = nullptr, *sort_hist = nullptr;
     // per selected node (capacity cap_sel)
@@ -171,6 +174,9 @@ struct StageMarks {
 
 // per-view stages (select.cu, project.cu, raster.cu)
 int launch_select(const lodgs_scene *sc, const CamK &k, FrameBufs &f, cudaStream_t st);
+int launch_select_upper(const lodgs_scene *sc, const CamK &k, FrameBufs &f, bool with_src, cudaStream_t st);
+int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st);
+int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st);
 int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, cudaStream_t st);
 int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, cudaStream_t st,
                   const StageMarks &sm);
@@ -179,3 +185,23 @@ int launch_raster_backward(const CamK &k, FrameBufs &f, const float bg[3], const
 int launch_project_backward(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f,
                             float *grad_rows, int dense, cudaStream_t st);
 }  // namespace lodgs
+
+struct lodgs_frame {
+    lodgs_scene *scene = nullptr;
+    lodgs::FrameBufs f;
+    uint32_t *h_cnt = nullptr;          // pinned mirror of the device counters
+    cudaStream_t stream = 0;
+    lodgs::CamK k{};
+    bool selected = false, rendered = false;
+    uint64_t want_sel = 0, want_pairs = 0;
+    // stage timing: ev[2s] / ev[2s+1] bracket stage s
+    bool prof = false;
+    cudaEvent_t ev[2 * LODGS_NUM_STAGES] = {};
+    bool ran[LODGS_NUM_STAGES] = {};
+    void mark(int stage, int end, cudaStream_t st) {
+        if (!prof) return;
+        cudaEventRecord(ev[2 * stage + end], st);
+        if (end) ran[stage] = true;
+    }
+};
+

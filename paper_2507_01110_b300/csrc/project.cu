@@ -224,6 +224,7 @@ __global__ void k_clamp_sel(uint32_t *cnt, uint64_t cap_sel) {
 
 template <int DEG>
 __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ rows, int stride,
+                                                     const uint32_t *__restrict__ sel_src,
                                                      const uint32_t *__restrict__ sel_rows, CamK k,
                                                      const uint32_t *__restrict__ cnt,
                                                      const uint32_t *__restrict__ ntiles,
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
             for (int c = 0; c < stride; c += 4) *reinterpret_cast<float4 *>(o + c) = make_float4(0, 0, 0, 0);
             continue;
         }
-        const float *r = rows + (size_t)row * stride;
+        const float *r = rows + (size_t)sel_src[i] * stride;
         const float *gg = g2d + (size_t)i * 9;
         float g[9];
 #pragma unroll
@@ -365,8 +366,8 @@ int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, Fram
     k_clamp_sel<<<1, 1, 0, st>>>(f.cnt, f.cap_sel);
     count_launches(1);
 #define LAUNCH_PROJ(D)                                                                                     \
-    k_project<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.sel_rows, k, f.cnt, f.sp_a, f.sp_b, f.sp_c, f.dkey, \
-                                           f.dval, f.rect, f.ntiles)
+    k_project<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, k, f.cnt, f.sp_a,  \
+                                           f.sp_b, f.sp_c, f.dkey, f.dval, f.rect, f.ntiles)
     switch (sc->sh_degree) {
         case 0: LAUNCH_PROJ(0); break;
         case 1: LAUNCH_PROJ(1); break;
@@ -382,7 +383,8 @@ int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, Fram
 int launch_project_backward(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, float *grad_rows,
                             int dense, cudaStream_t st) {
 #define LAUNCH_PBWD(D)                                                                                     \
-    k_project_bwd<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.sel_rows, k, f.cnt, f.ntiles, f.g2d, grad_rows, dense)
+    k_project_bwd<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.sel_rows, k, \
+                                               f.cnt, f.ntiles, f.g2d, grad_rows, dense)
     switch (sc->sh_degree) {
         case 0: LAUNCH_PBWD(0); break;
         case 1: LAUNCH_PBWD(1); break;

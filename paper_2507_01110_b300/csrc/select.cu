@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict
 
 __global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict__ up, uint32_t U, CamK k,
                                                     const uint32_t *__restrict__ bc, uint32_t *__restrict__ sel_rows,
-                                                    uint32_t *__restrict__ emit_j, float *__restrict__ emit_x,
-                                                    uint32_t *__restrict__ cnt) {
+                                                    uint32_t *__restrict__ sel_src, uint32_t *__restrict__ emit_j,
+                                                    float *__restrict__ emit_x, uint32_t *__restrict__ cnt) {
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_off_sel, s_off_emit;
     uint32_t sel_before = 0, emit_before = 0;
@@ -135,7 +135,10 @@ __global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict
         uint32_t tot;
         uint32_t ex = block_scan(packed, s_warp, &tot);
         uint32_t os = s_off_sel, oe = s_off_emit;
-        if (o == OUT_SELECT) sel_rows[os + (ex & 0xffffu)] = (uint32_t)up[u].ref;
+        if (o == OUT_SELECT) {
+            sel_rows[os + (ex & 0xffffu)] = (uint32_t)up[u].ref;
+            if (sel_src) sel_src[os + (ex & 0xffffu)] = (uint32_t)up[u].ref;   // upper rows are resident
+        }
         if (o == OUT_SPT) {
             emit_j[oe + (ex >> 16)] = (uint32_t)up[u].ref;
             emit_x[oe + (ex >> 16)] = x;
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(SB) k_spt_high(const uint32_t *__restrict__ cn
 __device__ __forceinline__ bool spt_item(uint32_t w, uint32_t n_emit, const uint32_t *__restrict__ work_off,
                                          const uint32_t *__restrict__ emit_j, const float *__restrict__ emit_x,
                                          const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
-                                         uint32_t *row) {
+                                         uint32_t *row, uint32_t *q = nullptr, uint32_t *e = nullptr) {
     uint32_t a = 0, b = n_emit;                              // last q with work_off[q] <= w
     while (b - a > 1) {
         uint32_t m = a + (b - a) / 2;
@@ -180,6 +183,7 @@ __device__ __forceinline__ bool spt_item(uint32_t w, uint32_t n_emit, const uint
     }
     uint32_t r = spt_base[emit_j[a]] + (w - work_off[a]);
     *row = r;
+    if (q) { *q = a; *e = w - work_off[a]; }
     return lo_row[r] <= emit_x[a];
 }
 
@@ -204,7 +208,9 @@ __global__ void __launch_bounds__(SB) k_spt_count(const uint32_t *__restrict__ c
 __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, const uint32_t *__restrict__ work_off,
                                                   const uint32_t *__restrict__ emit_j, const float *__restrict__ emit_x,
                                                   const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
-                                                  const uint32_t *__restrict__ bc, uint32_t *__restrict__ sel_rows) {
+                                                  const uint32_t *__restrict__ bc, uint32_t *__restrict__ sel_rows,
+                                                  uint32_t *__restrict__ sel_src,
+                                                  const uint32_t *__restrict__ emit_src) {
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_off;
     uint32_t W = cnt[C_WORK], n_emit = cnt[C_NEMIT], n_up = cnt[C_NUP];
@@ -214,12 +220,15 @@ __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, co
     uint32_t begin, end;
     grid_chunk(W, begin, end);
     for (uint32_t t0 = begin; t0 < end; t0 += SB) {
-        uint32_t w = t0 + threadIdx.x, row = 0;
-        bool keep = w < end && spt_item(w, n_emit, work_off, emit_j, emit_x, spt_base, lo_row, &row);
+        uint32_t w = t0 + threadIdx.x, row = 0, q = 0, e = 0;
+        bool keep = w < end && spt_item(w, n_emit, work_off, emit_j, emit_x, spt_base, lo_row, &row, &q, &e);
         uint32_t tot;
         uint32_t ex = block_scan(keep ? 1u : 0u, s_warp, &tot);
         uint32_t o = s_off;
-        if (keep) sel_rows[o + ex] = row;
+        if (keep) {
+            sel_rows[o + ex] = row;
+            if (sel_src) sel_src[o + ex] = emit_src[q] + e;    // record slot of entry e of this SPT
+        }
         __syncthreads();
         if (threadIdx.x == 0) s_off = o + tot;
         __syncthreads();
@@ -232,24 +241,43 @@ __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, co
 
 }  // namespace
 
-int launch_select(const lodgs_scene *sc, const CamK &k, FrameBufs &f, cudaStream_t st) {
+int launch_select_upper(const lodgs_scene *sc, const CamK &k, FrameBufs &f, bool with_src, cudaStream_t st) {
     uint32_t U = (uint32_t)sc->n_upper;
     k_upper_count<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, k, f.block_counts);
     count_launches(1);
-    k_upper_write<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, k, f.block_counts, f.sel_rows, f.emit_j, f.emit_x, f.cnt);
+    k_upper_write<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, k, f.block_counts, f.sel_rows, with_src ? f.sel_src : nullptr,
+                                           f.emit_j, f.emit_x, f.cnt);
     count_launches(1);
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
+
+int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st) {
     k_spt_high<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_hi, f.high);
     count_launches(1);
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
+
+int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st) {
     int rc = scan_exclusive(f.high, f.work_off, f.cnt + C_NEMIT, (uint32_t)sc->n_spt, f.scan_bsum, f.cnt + C_WORK, st);
     if (rc) return rc;
     k_spt_count<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
                                          f.block_counts);
     count_launches(1);
     k_spt_write<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
-                                         f.block_counts, f.sel_rows);
+                                         f.block_counts, f.sel_rows, with_src ? f.sel_src : nullptr,
+                                         with_src ? f.emit_src : nullptr);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
+}
+
+int launch_select(const lodgs_scene *sc, const CamK &k, FrameBufs &f, cudaStream_t st) {
+    int rc = launch_select_upper(sc, k, f, false, st);
+    if (!rc) rc = launch_spt_high(sc, f, st);
+    if (!rc) rc = launch_select_spt(sc, f, false, st);
+    return rc;
 }
 
 }  // namespace lodgs
