@@ -42,6 +42,12 @@ def parse():
     p.add_argument("--impl", default="lodgs", choices=["lodgs", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--leaves", type=int, default=2_097_152)
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-out-of-core", action="store_true")
+    p.add_argument("--serving-leaves", type=int, default=50_000_000)
+    p.add_argument("--serving-requests", type=int, default=400)
+    p.add_argument("--ooc-leaves", type=int, default=20_000_000)
+    p.add_argument("--ooc-views", type=int, default=200)
     return p.parse_args()
 
 
@@ -416,6 +422,82 @@ def run_reference(args, rank: int, world: int):
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------------------
+# serving (50M-leaf city, Poisson arrivals) and out-of-core (20M-leaf city)
+# ---------------------------------------------------------------------------
+SERVING_SPT_VOLUME = 150.0      # ~N/1024 SPT roots on the 50M-leaf city
+OOC_SPT_VOLUME = 300.0          # ~N/1024 SPT roots on the 20M-leaf city
+
+
+def run_serving(args) -> dict:
+    import torch
+    from paper_2507_01110_b300 import api, serving, synth
+    t0 = time.perf_counter()
+    leaves = synth.city_leaves_t(args.serving_leaves, seed=4, degree=3, device="cuda")
+    cams = synth.serving_cameras(256, seed=4)
+    kappa = min(float(c.fx / c.tau) for c in cams)
+    scene = api.build_hierarchy(leaves, 3, SERVING_SPT_VOLUME, kappa)
+    del leaves
+    torch.cuda.empty_cache()
+    t_build = time.perf_counter() - t0
+    rate = 200.0
+    mix = serving.RenderServer(scene, n_slots=8, mem_budget_bytes=8 << 30)
+    mix.warm(cams[:32])
+    r_mix = mix.run(serving.poisson_requests(cams, rate, args.serving_requests, seed=4))
+    fifo = serving.RenderServer(scene, n_slots=1, mem_budget_bytes=8 << 30)
+    fifo.warm(cams[:32])
+    r_fifo = fifo.run(serving.poisson_requests(cams, rate, args.serving_requests, seed=4))
+    return {"workload": f"{args.serving_leaves:,}-leaf SH3 city (2 km), Poisson {rate:.0f} req/s, "
+                        f"{args.serving_requests} requests, resolution in {{360p,720p,1080p,2160p}}, "
+                        "tau in {0.5,1,2,4} px, half aerial half street",
+            "nodes": scene.n_nodes, "spt": scene.n_spt, "build_s": round(t_build, 2),
+            "continuous_batching": {k: round(v, 3) if isinstance(v, float) else v for k, v in r_mix.items()},
+            "one_at_a_time": {k: round(v, 3) if isinstance(v, float) else v for k, v in r_fifo.items()},
+            "unit": "ms"}
+
+
+def run_out_of_core(args) -> dict:
+    import torch
+    from paper_2507_01110_b300 import api, synth
+    leaves = synth.city_leaves_t(args.ooc_leaves, seed=3, degree=3, device="cuda")
+    cams = synth.flythrough_path(args.ooc_views)
+    kappa = float(cams[0].fx / cams[0].tau)
+    scene = api.build_hierarchy(leaves, 3, OOC_SPT_VOLUME, kappa)
+    del leaves
+    cap = 8 << 30
+    cache = api.Cache(scene, capacity_bytes=cap, d_min=0.9, d_max=1.1, release_scene_rows=True)
+    torch.cuda.empty_cache()
+    fr = api.Frame(scene)
+    H, W = cams[0].height, cams[0].width
+    image = torch.empty((H, W, 3), device="cuda")
+    copy_stream = torch.cuda.Stream()
+    # size the frame's workspace on the path (first pass), then time a fresh cache pass
+    for cam in cams[:: max(1, len(cams) // 16)]:
+        api.stream_nodes(scene, cache, cam, fr, copy_stream=copy_stream)
+        api.render(scene, fr, rows=cache.records, image=image, check_capacity=True)
+    cache.close()
+    cache = api.Cache(scene, capacity_bytes=cap, d_min=0.9, d_max=1.1)
+    torch.cuda.synchronize()
+    tot = {"spt_hits": 0, "spt_resident": 0, "spt_loaded": 0, "bytes_streamed": 0, "evictions": 0}
+    t0 = time.perf_counter()
+    for cam in cams:
+        _, st = api.stream_nodes(scene, cache, cam, fr, copy_stream=copy_stream)
+        api.render(scene, fr, rows=cache.records, image=image, check_capacity=False)
+        for k in tot:
+            tot[k] += st[k]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    n_spt_views = tot["spt_hits"] + tot["spt_resident"] + tot["spt_loaded"]
+    return {"workload": f"{args.ooc_leaves:,}-leaf SH3 city, records in pinned host memory, 8 GiB device "
+                        f"cache, {len(cams)}-view flythrough 300 m -> 20 m at 1920x1080, forward only",
+            "frames_per_s": round(len(cams) / wall, 2), "ms_per_frame": round(1e3 * wall / len(cams), 3),
+            "bytes_streamed_per_frame": int(tot["bytes_streamed"] / len(cams)),
+            "spt_hit_rate": round(tot["spt_hits"] / max(1, n_spt_views), 4),
+            "spt_device_resident_rate": round((tot["spt_hits"] + tot["spt_resident"]) / max(1, n_spt_views), 4),
+            "evictions": tot["evictions"], "host_record_gb": round(scene.n_nodes * scene.stride * 4 / 1e9, 2),
+            "reuse_window": [0.9, 1.1]}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -468,6 +550,10 @@ def main():
                             "peak_source": f"148 SMs x 128 FP32 lanes x {rf['mhz']:.0f} MHz (median SM clock "
                                            "in the timed region)", "work_per_view": rf["work"]}
     line["roofline_stages"] = {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in rf["stages"].items()}
+    if world == 1 and not args.no_out_of_core:
+        line["out_of_core"] = run_out_of_core(args)
+    if world == 1 and not args.no_serving:
+        line["serving"] = run_serving(args)
     if not args.no_cpu_baseline and world == 1:
         from paper_2507_01110_b300 import synth
         line["cpu_baseline"] = cpu_baseline(lambda: synth.config2_scene(n=args.leaves))

@@ -217,3 +217,148 @@ def config2_scene(n: int = 2_097_152, n_views: int = 32, width: int = 1920, heig
     cams = aerial_to_street_path(n_views, width, height)
     return {"leaves": leaves, "degree": 3, "cameras": cams, "spt_volume": 400.0,
             "kappa": float(cams[0].fx / cams[0].tau)}
+
+
+# ---------------------------------------------------------------------------
+# device-side generation for the large scenes (same hash, torch int64 lanes)
+# ---------------------------------------------------------------------------
+
+def _to_i64(u: int) -> int:
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+_GOLDEN_I = _to_i64(0x9E3779B97F4A7C15)
+_M1_I = _to_i64(0xBF58476D1CE4E5B9)
+_M2_I = _to_i64(0x94D049BB133111EB)
+
+
+def _srl(z, k: int):
+    """Logical right shift of int64 lanes holding uint64 bit patterns."""
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def _mix_t(z):
+    z = (z ^ _srl(z, 30)) * _M1_I
+    z = (z ^ _srl(z, 27)) * _M2_I
+    return z ^ _srl(z, 31)
+
+
+def hash_u64_t(seed: int, stream: int, idx):
+    """Torch version of hash_u64 (bit-identical), idx an int64 tensor."""
+    key = int(_mix(np.array([(seed << 32) + stream], dtype=np.uint64))[0])
+    return _mix_t(_to_i64(key) + (idx + 1) * _GOLDEN_I)
+
+
+def uniform_t(seed: int, stream: int, idx):
+    import torch
+    return _srl(hash_u64_t(seed, stream, idx), 40).to(torch.float64) * (1.0 / 16777216.0)
+
+
+def normal_t(seed: int, stream: int, idx):
+    import torch
+    u1 = (_srl(hash_u64_t(seed, 1_000_000 + 2 * stream, idx), 40).to(torch.float64) + 0.5) * (1.0 / 16777216.0)
+    u2 = uniform_t(seed, 1_000_000 + 2 * stream + 1, idx)
+    return torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+
+
+def city_leaves_t(n: int, seed: int, degree: int = 3, extent: float = 2000.0, block: float = 100.0,
+                  ground_frac: float = 0.4, device: str = "cuda", chunk: int = 1 << 22,
+                  log_scale_mu: float = -1.0, log_scale_sigma: float = 0.5, sh_sigma: float = 0.2):
+    """City-like leaves generated on the device: a square street grid of
+    `block`-metre blocks, one box building per block (footprint U[30,70] m,
+    height U[10,120] m); `ground_frac` of the leaves on the ground (z jitter
+    N(0, 0.05^2)), the rest uniform on building walls and roofs (face chosen by
+    area).  Attributes as in leaves_uniform_cube.  Returns an n x stride
+    float32 tensor on `device`."""
+    import torch
+    st = record_stride(degree)
+    out = torch.zeros((n, st), dtype=torch.float32, device=device)
+    nb = int(extent // block)
+    bidx = torch.arange(nb * nb, dtype=torch.int64, device=device)
+    bw = 30.0 + 40.0 * uniform_t(seed, 200, bidx)
+    bd = 30.0 + 40.0 * uniform_t(seed, 201, bidx)
+    bh = 10.0 + 110.0 * uniform_t(seed, 202, bidx)
+    bcx = -0.5 * extent + block * (torch.remainder(bidx, nb).to(torch.float64) + 0.5)
+    bcy = -0.5 * extent + block * (torch.div(bidx, nb, rounding_mode="floor").to(torch.float64) + 0.5)
+    areas = torch.stack([bw * bh, bw * bh, bd * bh, bd * bh, bw * bd], dim=1)
+    cum = torch.cumsum(areas, dim=1)
+    cum = cum / cum[:, -1:]
+    n_ground = int(round(ground_frac * n))
+    K = sh_coeff_count(degree)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        i = torch.arange(s, e, dtype=torch.int64, device=device)
+        pos = torch.zeros((e - s, 3), dtype=torch.float64, device=device)
+        g = i < n_ground
+        ux, uy = uniform_t(seed, 0, i), uniform_t(seed, 1, i)
+        pos[:, 0] = -0.5 * extent + extent * ux
+        pos[:, 1] = -0.5 * extent + extent * uy
+        pos[:, 2] = 0.05 * normal_t(seed, 2, i)
+        b = torch.clamp((uniform_t(seed, 3, i) * (nb * nb)).to(torch.int64), max=nb * nb - 1)
+        f = torch.searchsorted(cum[b], uniform_t(seed, 4, i).unsqueeze(1)).squeeze(1).clamp(max=4)
+        a, c = uniform_t(seed, 5, i) - 0.5, uniform_t(seed, 6, i)
+        hx, hy = 0.5 * bw[b], 0.5 * bd[b]
+        wx = torch.where(f <= 1, a * bw[b], torch.where(f == 2, -hx, torch.where(f == 3, hx, a * bw[b])))
+        wy = torch.where(f == 0, -hy, torch.where(f == 1, hy, torch.where(f <= 3, a * bd[b], (c - 0.5) * bd[b])))
+        wz = torch.where(f == 4, bh[b], c * bh[b])
+        bpos = torch.stack([bcx[b] + wx, bcy[b] + wy, wz], dim=1)
+        pos = torch.where(g.unsqueeze(1), pos, bpos)
+        rec = out[s:e]
+        rec[:, 0:3] = pos.to(torch.float32)
+        for k in range(3):
+            rec[:, REC_S + k] = torch.exp(log_scale_mu + log_scale_sigma * normal_t(seed, 10 + k, i)).float()
+        q = torch.stack([normal_t(seed, 20 + k, i) for k in range(4)], dim=1)
+        q = q / torch.linalg.norm(q, dim=1, keepdim=True)
+        rec[:, REC_Q:REC_Q + 4] = q.float()
+        rec[:, REC_OP] = (0.1 + 0.8 * uniform_t(seed, 30, i)).float()
+        for c3 in range(3):
+            rec[:, REC_B + c3] = uniform_t(seed, 31 + c3, i).float()
+        for k in range(3 * K):
+            rec[:, REC_F + k] = (sh_sigma * normal_t(seed, 40 + k, i)).float()
+    return out
+
+
+def flythrough_path(n_views: int = 200, width: int = 1920, height: int = 1080, alt_hi: float = 300.0,
+                    alt_lo: float = 20.0, tau: float = 1.0) -> list[Camera]:
+    """Smooth flythrough: altitude geometric alt_hi -> alt_lo, pitch -60 deg ->
+    -15 deg, heading turning through 90 degrees along a spiral; consecutive
+    views move by well under 1% of the viewing distance."""
+    cams = []
+    for v in range(n_views):
+        t = v / max(1, n_views - 1)
+        alt = alt_hi * (alt_lo / alt_hi) ** t
+        pitch = math.radians(-60.0 + 45.0 * t)
+        head = math.radians(90.0 * t)
+        r = 400.0 * (1.0 - 0.8 * t)
+        pos = np.array([r * math.cos(head + math.pi), r * math.sin(head + math.pi), alt])
+        fwd = np.array([math.cos(head) * math.cos(pitch), math.sin(head) * math.cos(pitch), math.sin(pitch)])
+        right = np.array([math.sin(head), -math.cos(head), 0.0])
+        cams.append(camera_look(pos, fwd, right, width, height, tau=tau))
+    return cams
+
+
+SERVING_RESOLUTIONS = ((640, 360), (1280, 720), (1920, 1080), (3840, 2160))
+SERVING_TAUS = (0.5, 1.0, 2.0, 4.0)
+
+
+def serving_cameras(n: int, seed: int, extent: float = 2000.0) -> list[Camera]:
+    """Request cameras: resolution and LoD threshold uniform over the serving
+    sets; half aerial (50-500 m, pitch -45..-90 deg), half street level
+    (1.5-3 m, pitch -5..+5 deg), positions and headings uniform."""
+    idx = np.arange(n, dtype=np.uint64)
+    u = [uniform(seed, 600 + k, idx) for k in range(8)]
+    cams = []
+    for i in range(n):
+        w, h = SERVING_RESOLUTIONS[int(u[0][i] * 4) % 4]
+        tau = SERVING_TAUS[int(u[1][i] * 4) % 4]
+        aerial = u[2][i] < 0.5
+        x, y = (u[3][i] - 0.5) * 0.8 * extent, (u[4][i] - 0.5) * 0.8 * extent
+        head = 2.0 * math.pi * u[5][i]
+        if aerial:
+            alt, pitch = 50.0 + 450.0 * u[6][i], math.radians(-45.0 - 44.0 * u[7][i])
+        else:
+            alt, pitch = 1.5 + 1.5 * u[6][i], math.radians(-5.0 + 10.0 * u[7][i])
+        fwd = np.array([math.cos(head) * math.cos(pitch), math.sin(head) * math.cos(pitch), math.sin(pitch)])
+        right = np.array([math.sin(head), -math.cos(head), 0.0])
+        cams.append(camera_look([x, y, alt], fwd, right, w, h, tau=tau))
+    return cams

@@ -38,9 +38,15 @@ def _proper_cut(ex, sel):
 def test_exact_window_matches_resident_render_under_eviction(world):
     api, scene, cams = world
     rec_bytes = scene.stride * 4
-    # a slab too small for the whole trajectory forces LRU evictions
-    cache = api.Cache(scene, capacity_bytes=60_000 * rec_bytes, d_min=1.0, d_max=1.0)
     fr_c, fr_r = api.Frame(scene), api.Frame(scene)
+    need = []
+    for cam in cams:
+        api.select_lod(scene, cam, fr_r)
+        need.append(fr_r.stats()["n_spt_scanned"])
+    # a slab that holds any one view but not the whole trajectory forces LRU evictions
+    cap = int(1.3 * max(need))
+    assert cap < sum(need)
+    cache = api.Cache(scene, capacity_bytes=cap * rec_bytes, d_min=1.0, d_max=1.0)
     copy_stream = torch.cuda.Stream()
     total_evict = 0
     for i, cam in enumerate(cams + cams[::-1]):
