@@ -189,6 +189,9 @@ typedef struct {
  * slab and copies the upper hierarchy's records.  Synchronous. */
 int lodgs_cache_create(lodgs_scene *scene, const lodgs_cache_params *params, lodgs_cache **out);
 void lodgs_cache_free(lodgs_cache *cache);
+/* Drop every cached SPT (Sec. 4.4: the paper flushes the whole cache
+ * periodically during training).  Host-side only; no data moves. */
+int lodgs_cache_flush(lodgs_cache *cache);
 /* Device records to pass as `rows` to lodgs_render / lodgs_render_backward for
  * frames selected with lodgs_stream_nodes (upper rows, then the slab). */
 int lodgs_cache_records(lodgs_cache *cache, float **d_records);

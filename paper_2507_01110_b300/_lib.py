@@ -80,6 +80,7 @@ _SIGS = {
     "lodgs_cache_create": (C.c_int, [_P, C.POINTER(CacheParams), C.POINTER(_P)]),
     "lodgs_cache_free": (None, [_P]),
     "lodgs_cache_records": (C.c_int, [_P, C.POINTER(_P)]),
+    "lodgs_cache_flush": (C.c_int, [_P]),
     "lodgs_stream_nodes": (C.c_int, [_P, _P, C.POINTER(Camera), _P, _P, _P, C.POINTER(StreamStats)]),
     "lodgs_render": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, _P]),

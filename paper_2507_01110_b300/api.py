@@ -193,6 +193,10 @@ class Cache:
     def handle(self):
         return self._h
 
+    def flush(self):
+        """Drop every cached SPT (the paper's periodic cache flush)."""
+        check(lib().lodgs_cache_flush(self._h))
+
     def close(self):
         if self._h:
             lib().lodgs_cache_free(self._h)

@@ -168,6 +168,17 @@ void lodgs_cache_free(lodgs_cache *c) {
     delete c;
 }
 
+int lodgs_cache_flush(lodgs_cache *c) {
+    if (!c) { set_error("cache_flush: NULL cache"); return LODGS_E_INVALID; }
+    for (Entry &e : c->entry) e.valid = false;
+    c->lru.clear();
+    c->free_ranges.clear();
+    c->free_ranges.emplace(0, c->slab_records);
+    c->cached_records = 0;
+    c->cached_spts = 0;
+    return LODGS_OK;
+}
+
 int lodgs_cache_records(lodgs_cache *c, float **d_records) {
     if (!c || !d_records) { set_error("cache_records: NULL argument"); return LODGS_E_INVALID; }
     *d_records = c->d_records;
