@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--serving-requests", type=int, default=400)
     p.add_argument("--ooc-leaves", type=int, default=20_000_000)
     p.add_argument("--ooc-views", type=int, default=200)
+    p.add_argument("--train-leaves", type=int, default=150_000_000)
+    p.add_argument("--no-train-batch", action="store_true")
     return p.parse_args()
 
 
@@ -497,6 +499,63 @@ def run_out_of_core(args) -> dict:
             "reuse_window": [0.9, 1.1]}
 
 
+TRAIN_SPT_VOLUME = 150.0      # per-scene HSPT size for the 150M-leaf city
+
+
+def run_train_batch(args) -> dict:
+    """Training-scale step: 150M-leaf SH3 city, a batch of 8 views (4 aerial, 4
+    street) at 1600x1200; LoD select + render + mean-L1 + backward per view on
+    its own stream, then the batch gradient summed over the union of the cuts."""
+    import torch
+    from paper_2507_01110_b300 import api, synth
+    t0 = time.perf_counter()
+    leaves = synth.city_leaves_t(args.train_leaves, seed=5, degree=3, device="cuda")
+    aerial = synth.serving_cameras(64, seed=5)
+    views = [c for c in aerial if c.pos[2] > 40.0][:4] + [c for c in aerial if c.pos[2] < 5.0][:4]
+    views = [synth.camera_look(c.pos, c.R[2], c.R[0], 1600, 1200, tau=1.0) for c in views]
+    kappa = float(views[0].fx)
+    scene = api.build_hierarchy(leaves, 3, TRAIN_SPT_VOLUME, kappa)
+    del leaves
+    torch.cuda.empty_cache()
+    t_build = time.perf_counter() - t0
+    streams = [torch.cuda.Stream() for _ in views]
+    frames = [api.Frame(scene) for _ in views]
+    imgs = [torch.empty((1200, 1600, 3), device="cuda") for _ in views]
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    targets = [torch.rand((1200, 1600, 3), device="cuda", generator=gen) for _ in views]
+    for v, cam in enumerate(views):                 # size the workspaces
+        api.select_lod(scene, cam, frames[v])
+        api.render(scene, frames[v], image=imgs[v], check_capacity=True)
+    sizes = [fr.stats()["n_selected"] for fr in frames]
+    grads = [torch.empty((max(n, 1), scene.stride), device="cuda") for n in sizes]
+    inv_n = 1.0 / (1200 * 1600 * 3)
+
+    def step():
+        for v, cam in enumerate(views):
+            with torch.cuda.stream(streams[v]):
+                fr = api.select_lod(scene, cam, frames[v], stream=streams[v])
+                api.render(scene, fr, image=imgs[v], stream=streams[v], check_capacity=False)
+                dL = torch.sign(imgs[v] - targets[v]).mul_(inv_n)
+                api.render_backward(scene, fr, dL, grad=grads[v], stream=streams[v])
+        return api.accumulate_grads(scene, frames, grads)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    reps = 5
+    t1 = time.perf_counter()
+    for _ in range(reps):
+        rows, _g = step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t1) / reps
+    return {"workload": f"{args.train_leaves:,}-leaf SH3 city (2 km), batch of 8 views (4 aerial, 4 street) at "
+                        "1600x1200: select + render + mean-L1 + backward, batch gradient on the union of the cuts",
+            "nodes": scene.n_nodes, "spt": scene.n_spt, "build_s": round(t_build, 2),
+            "step_ms": round(dt * 1e3, 3), "views_per_s": round(8 / dt, 1),
+            "selected_per_view": sizes, "union_rows": int(rows.numel()),
+            "device_gb_peak": round(torch.cuda.max_memory_allocated() / 1e9, 1)}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -553,6 +612,8 @@ def main():
         line["out_of_core"] = run_out_of_core(args)
     if world == 1 and not args.no_serving:
         line["serving"] = run_serving(args)
+    if world == 1 and not args.no_train_batch:
+        line["train_batch"] = run_train_batch(args)
     if not args.no_cpu_baseline and world == 1:
         from paper_2507_01110_b300 import synth
         line["cpu_baseline"] = cpu_baseline(lambda: synth.config2_scene(n=args.leaves))

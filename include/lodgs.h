@@ -240,6 +240,21 @@ int lodgs_render(lodgs_scene *scene, lodgs_frame *frame, const float *rows, cons
 int lodgs_render_backward(lodgs_scene *scene, lodgs_frame *frame, const float *rows, const float *bg,
                           const float *dL_dimage, float *grad_rows, int dense, void *stream);
 
+/*
+ * Gradient of a multi-view batch loss: sums the per-view sparse gradient rows
+ * (lodgs_render_backward with dense = 0) into one row per node of the union of
+ * the views' cuts; only cut-set nodes receive gradients (appendix,
+ * Implementation Details).  Deterministic: rows of a node are summed in view
+ * order, without atomics.
+ *   frames[v], grads[v]  the n_views rendered frames and their device gradient rows
+ *   out_rows   device uint32, capacity >= sum of the views' selections: union rows, ascending
+ *   out_grads  device float32, capacity x stride: the summed rows, in out_rows order
+ *   d_count    device uint32: the union size
+ * Synchronises the frames' streams, then runs asynchronously on `stream`.
+ */
+int lodgs_accumulate_grads(lodgs_scene *scene, lodgs_frame *const *frames, const float *const *grads, int n_views,
+                           uint32_t *out_rows, float *out_grads, int64_t capacity, uint32_t *d_count, void *stream);
+
 /* Counters of the last select/render on this frame (blocks until `stream`,
  * the stream the frame last ran on, is idle). */
 int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);

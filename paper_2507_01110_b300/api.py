@@ -223,6 +223,23 @@ def stream_nodes(scene: Scene, cache: Cache, camera, frame: Frame | None = None,
     return fr, {k: getattr(st, k) for k, _ in _lib.StreamStats._fields_}
 
 
+def accumulate_grads(scene: Scene, frames: list, grads: list, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+    """Sum per-view sparse gradient rows over the union of the views' cuts.
+    Returns (rows int64 ascending, summed gradient rows)."""
+    n = len(frames)
+    total = sum(int(g.shape[0]) for g in grads)
+    out_rows = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+    out_grads = torch.empty((max(total, 1), scene.stride), dtype=torch.float32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    fr_arr = (C.c_void_p * n)(*[f.handle.value for f in frames])
+    g_arr = (C.c_void_p * n)(*[g.data_ptr() for g in grads])
+    check(lib().lodgs_accumulate_grads(scene.handle, fr_arr, g_arr, C.c_int(n), C.c_void_p(out_rows.data_ptr()),
+                                       C.c_void_p(out_grads.data_ptr()), C.c_int64(max(total, 1)),
+                                       C.c_void_p(count.data_ptr()), _stream_ptr(stream)))
+    k = int(count.item())
+    return out_rows[:k].to(torch.int64), out_grads[:k]
+
+
 def build_hierarchy(leaves, sh_degree: int, spt_volume: float, kappa: float) -> Scene:
     """Leaves (n x stride float32, numpy or torch) -> Scene.  See lodgs_build_hierarchy."""
     lib()

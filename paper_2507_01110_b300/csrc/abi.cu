@@ -168,8 +168,15 @@ int lodgs_scene_export(const lodgs_scene *sc, float *node_rec, int64_t *left, in
                        int64_t *spt_count, int64_t *node_of_row, float *lo_row, float *hi_row) {
     if (!sc) { set_error("scene_export: NULL scene"); return LODGS_E_INVALID; }
     const int64_t M = sc->n_nodes, U = sc->n_upper, S = sc->n_spt;
-    if (node_rec) LODGS_CUDA(cudaMemcpy(node_rec, sc->d_node_rec, (size_t)M * sc->stride * 4, cudaMemcpyDeviceToHost));
     std::vector<int32_t> t32(std::max<int64_t>(M, 1));
+    if (node_rec) {      // canonical order = render rows scattered through node_of_row
+        if (!sc->d_rows) { set_error("scene_export: the scene's records are not on the device"); return LODGS_E_STATE; }
+        const size_t st = (size_t)sc->stride;
+        std::vector<float> rows((size_t)M * st);
+        LODGS_CUDA(cudaMemcpy(rows.data(), sc->d_rows, rows.size() * 4, cudaMemcpyDeviceToHost));
+        LODGS_CUDA(cudaMemcpy(t32.data(), sc->d_node_of_row, M * 4, cudaMemcpyDeviceToHost));
+        for (int64_t r = 0; r < M; ++r) memcpy(node_rec + (size_t)t32[r] * st, rows.data() + (size_t)r * st, st * 4);
+    }
     auto widen = [&](int64_t *dst, const int32_t *src, int64_t n) -> int {
         if (!dst) return LODGS_OK;
         LODGS_CUDA(cudaMemcpy(t32.data(), src, n * 4, cudaMemcpyDeviceToHost));

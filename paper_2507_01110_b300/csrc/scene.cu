@@ -607,7 +607,7 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
     sc->d_spt_base = spt_base.release();
     sc->d_lo = lo_row.release();
     sc->d_hi = hi_row.release();
-    sc->d_node_rec = node_rec.release();
+    // the canonical-order copy is not kept: export rebuilds it from the rows
     sc->d_left = left.release();
     sc->d_right = right.release();
     sc->d_node_of_row = node_of_row.release();

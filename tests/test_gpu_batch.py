@@ -1,0 +1,37 @@
+"""Batch gradient over several views: the union of the cuts, summed rows."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2507_01110_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_accumulate_grads_equals_scatter_add():
+    from paper_2507_01110_b300 import api, build
+    build.build()
+    leaves = synth.leaves_uniform_cube(20000, seed=61, half_extent=20.0, degree=1)
+    cams = [synth.camera_look([0.0, 0.0, -70.0], [0, 0, 1], [1, 0, 0], 96, 80),
+            synth.camera_look([10.0, 2.0, -60.0], [-0.1, 0.0, 1.0], [1, 0, 0], 96, 80, tau=2.0),
+            synth.camera_look([60.0, 0.0, 0.0], [-1, 0, 0], [0, 0, 1], 120, 64)]
+    scene = api.build_hierarchy(leaves, 1, 2.0, float(cams[0].fx))
+    frames, grads, sels = [], [], []
+    rng = np.random.default_rng(3)
+    for cam in cams:
+        fr = api.select_lod(scene, cam)
+        img = api.render(scene, fr)
+        w = torch.from_numpy(rng.uniform(-1, 1, img.shape).astype(np.float32)).cuda()
+        g = api.render_backward(scene, fr, w)
+        sel = fr.selection()
+        frames.append(fr)
+        grads.append(g[: sel.numel()].contiguous())
+        sels.append(sel.cpu().numpy())
+    rows, summed = api.accumulate_grads(scene, frames, grads)
+    rows, summed = rows.cpu().numpy(), summed.cpu().numpy()
+    union = np.unique(np.concatenate(sels))
+    assert np.array_equal(rows, union)
+    ref = np.zeros((scene.n_nodes, scene.stride))
+    for s, g in zip(sels, grads):
+        np.add.at(ref, s, g.cpu().numpy().astype(np.float64))
+    assert np.allclose(summed, ref[union], rtol=1e-6, atol=1e-9)
