@@ -608,12 +608,20 @@ def main():
                             "peak_source": f"148 SMs x 128 FP32 lanes x {rf['mhz']:.0f} MHz (median SM clock "
                                            "in the timed region)", "work_per_view": rf["work"]}
     line["roofline_stages"] = {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in rf["stages"].items()}
+    def section(name, fn):
+        try:
+            line[name] = fn(args)
+        except Exception as e:  # noqa: BLE001  (a failed side workload must not lose the main line)
+            line[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        import torch
+        torch.cuda.empty_cache()
+
     if world == 1 and not args.no_out_of_core:
-        line["out_of_core"] = run_out_of_core(args)
+        section("out_of_core", run_out_of_core)
     if world == 1 and not args.no_serving:
-        line["serving"] = run_serving(args)
+        section("serving", run_serving)
     if world == 1 and not args.no_train_batch:
-        line["train_batch"] = run_train_batch(args)
+        section("train_batch", run_train_batch)
     if not args.no_cpu_baseline and world == 1:
         from paper_2507_01110_b300 import synth
         line["cpu_baseline"] = cpu_baseline(lambda: synth.config2_scene(n=args.leaves))
