@@ -209,16 +209,15 @@ def run_lodgs(args, rank: int, world: int):
         fwd_stats[v] = st
         max_sel = max(max_sel, st["n_selected"])
     grad = torch.empty((max_sel, scene.stride), device="cuda")
-    inv_n = 1.0 / (H * W * 3)
+    dL = torch.empty_like(image)
+    loss_sum = torch.empty(1, device="cuda")
 
     def step(v, target):
         fr = api.select_lod(scene, cams[v], frames[v])
         api.render(scene, fr, image=image, check_capacity=False)
-        diff = image - target
-        loss = diff.abs().mean()
-        dL = torch.sign(diff).mul_(inv_n)
+        api.l1_loss_grad(image, target, dL=dL, loss_sum=loss_sum)     # fused mean-L1 loss + gradient
         api.render_backward(scene, fr, dL, grad=grad)
-        return loss
+        return loss_sum
 
     order = [my_views[i % len(my_views)] for i in range(args.steps)]
     for i in range(args.warmup):

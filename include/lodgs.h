@@ -255,6 +255,17 @@ int lodgs_render_backward(lodgs_scene *scene, lodgs_frame *frame, const float *r
 int lodgs_accumulate_grads(lodgs_scene *scene, lodgs_frame *const *frames, const float *const *grads, int n_views,
                            uint32_t *out_rows, float *out_grads, int64_t capacity, uint32_t *d_count, void *stream);
 
+/*
+ * Photometric L1 loss of a rendered image against a target (the training loss
+ * of the benchmark step) fused with its gradient, in one pass over device
+ * buffers of n floats (16-byte aligned): dL[i] = grad_scale * sign(image[i] -
+ * target[i]) and *loss_sum = sum |image[i] - target[i]| (device float,
+ * overwritten).  For the mean loss pass grad_scale = 1/n and divide the sum by n.
+ * Not part of the paper's method: its loss is the training objective around it.
+ */
+int lodgs_l1_loss_grad(const float *image, const float *target, int64_t n, float grad_scale, float *dL,
+                       float *loss_sum, void *stream);
+
 /* Counters of the last select/render on this frame (blocks until `stream`,
  * the stream the frame last ran on, is idle). */
 int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);

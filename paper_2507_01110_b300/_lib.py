@@ -86,6 +86,7 @@ _SIGS = {
     "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, _P]),
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
     "lodgs_accumulate_grads": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, C.c_int64, _P, _P]),
+    "lodgs_l1_loss_grad": (C.c_int, [_P, _P, C.c_int64, C.c_float, _P, _P, _P]),
     "lodgs_frame_export": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "lodgs_frame_set_profiling": (C.c_int, [_P, C.c_int]),
     "lodgs_frame_work": (C.c_int, [_P, _P]),

@@ -240,6 +240,20 @@ def accumulate_grads(scene: Scene, frames: list, grads: list, stream=None) -> tu
     return out_rows[:k].to(torch.int64), out_grads[:k]
 
 
+def l1_loss_grad(image: torch.Tensor, target: torch.Tensor, dL: torch.Tensor | None = None,
+                 loss_sum: torch.Tensor | None = None, stream=None):
+    """Mean L1 loss and its gradient in one pass; returns (dL, loss_sum) where
+    loss_sum / image.numel() is the mean (a device scalar, not synchronised)."""
+    n = image.numel()
+    if dL is None:
+        dL = torch.empty_like(image)
+    if loss_sum is None:
+        loss_sum = torch.empty(1, dtype=torch.float32, device=image.device)
+    check(lib().lodgs_l1_loss_grad(_ptr(image), _ptr(target), C.c_int64(n), C.c_float(1.0 / max(n, 1)),
+                                   _ptr(dL), _ptr(loss_sum), _stream_ptr(stream)))
+    return dL, loss_sum
+
+
 def build_hierarchy(leaves, sh_degree: int, spt_volume: float, kappa: float) -> Scene:
     """Leaves (n x stride float32, numpy or torch) -> Scene.  See lodgs_build_hierarchy."""
     lib()

@@ -160,10 +160,11 @@ constexpr int SORT_HIST = 256 * (SORT_GRID + 1);   // histogram table + digit to
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                      const uint32_t *d_n, uint32_t max_n, int begin_bit, int end_bit, uint32_t *hist,
                      cudaStream_t st, bool *result_in_alt);
-// exclusive scan of n (device count) uint32 values; total written to *d_total (may alias)
+// exclusive scan of n (device count) uint32 values in[idx[i]] (idx null: in[i]);
+// total written to *d_total
 constexpr int SCAN_GRID = 148;
 int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n,
-                   uint32_t *block_sums, uint32_t *d_total, cudaStream_t st);
+                   uint32_t *block_sums, uint32_t *d_total, cudaStream_t st, const uint32_t *idx = nullptr);
 // optional CUDA events bracketing stages (ev[2s], ev[2s+1]); null = off
 struct StageMarks {
     cudaEvent_t *ev = nullptr;

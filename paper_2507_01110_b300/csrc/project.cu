@@ -133,11 +133,17 @@ __device__ __forceinline__ void geometry(const CamK &k, const float *mu, const f
 template <int DEG>
 __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, int stride,
                                                  const uint32_t *__restrict__ sel_rows, CamK k,
-                                                 uint32_t *__restrict__ cnt, float4 *__restrict__ sp_a,
+                                                 uint32_t *__restrict__ cnt, uint64_t cap_sel, float4 *__restrict__ sp_a,
                                                  float4 *__restrict__ sp_b, float *__restrict__ sp_c,
                                                  uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
                                                  uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles) {
-    const uint32_t n = cnt[C_NSEL_EFF];
+    // selections beyond the workspace are not rendered: the frame reports a capacity error
+    uint32_t n = cnt[C_NSEL];
+    if (n > cap_sel) n = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cnt[C_NSEL_EFF] = n;
+        if (cnt[C_NSEL] > cap_sel) atomicOr(&cnt[C_STATUS], ST_CAPACITY);
+    }
     constexpr int degree = DEG;
     constexpr int K = (DEG + 1) * (DEG + 1) - 1;
     uint32_t nvis = 0;
@@ -213,13 +219,6 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nvis += __shfl_xor_sync(0xffffffffu, nvis, o);
     if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(&cnt[C_NVIS], nvis);
-}
-
-__global__ void k_clamp_sel(uint32_t *cnt, uint64_t cap_sel) {
-    uint32_t n = cnt[C_NSEL];
-    if (n > cap_sel) { cnt[C_STATUS] |= ST_CAPACITY; n = 0; }
-    cnt[C_NSEL_EFF] = n;
-    cnt[C_NVIS] = 0;
 }
 
 template <int DEG>
@@ -363,10 +362,8 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
 }  // namespace
 
 int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, cudaStream_t st) {
-    k_clamp_sel<<<1, 1, 0, st>>>(f.cnt, f.cap_sel);
-    count_launches(1);
 #define LAUNCH_PROJ(D)                                                                                     \
-    k_project<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, k, f.cnt, f.sp_a,  \
+    k_project<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, k, f.cnt, f.cap_sel, f.sp_a, \
                                            f.sp_b, f.sp_c, f.dkey, f.dval, f.rect, f.ntiles)
     switch (sc->sh_degree) {
         case 0: LAUNCH_PROJ(0); break;

@@ -25,18 +25,6 @@ namespace {
 constexpr int RB = 256;
 constexpr int RGRID = 148 * 8;
 
-__global__ void k_gather_nt(const uint32_t *__restrict__ order, const uint32_t *__restrict__ ntiles,
-                            const uint32_t *__restrict__ cnt, uint32_t *__restrict__ nt_sorted) {
-    uint32_t n = cnt[C_NSEL_EFF];
-    for (uint32_t r = blockIdx.x * RB + threadIdx.x; r < n; r += gridDim.x * RB) nt_sorted[r] = ntiles[order[r]];
-}
-
-__global__ void k_clamp_pairs(uint32_t *cnt, uint64_t cap_pairs) {
-    uint32_t n = cnt[C_NPAIR];
-    if (n > cap_pairs || (cnt[C_STATUS] & ST_CAPACITY)) { cnt[C_STATUS] |= ST_CAPACITY; n = 0; }
-    cnt[C_NPAIR_EFF] = n;
-}
-
 // Tile support test (float32, explicitly rounded).  The support exponent is a
 // concave quadratic; its maximum over the rectangle of the tile's pixel centres
 // is 0 when the mean lies inside, otherwise it lies on an edge at the clamped
@@ -72,9 +60,17 @@ __device__ __forceinline__ bool tile_keep(float u, float v, float A, float B, fl
 // key n_tiles, which the tile sort moves behind every real tile.
 __global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restrict__ rect,
                        const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
-                       const uint32_t *__restrict__ pair_off, const uint32_t *__restrict__ cnt, int TX,
-                       uint32_t n_tiles, uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
-    const uint32_t P = cnt[C_NPAIR_EFF], n = cnt[C_NSEL_EFF];
+                       const uint32_t *__restrict__ pair_off, uint32_t *__restrict__ cnt, uint64_t cap_pairs,
+                       int TX, uint32_t n_tiles, uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    // pairs beyond the workspace (or an earlier overflow) are not emitted: capacity error
+    uint32_t P = cnt[C_NPAIR];
+    const bool over = P > cap_pairs || (cnt[C_STATUS] & ST_CAPACITY);
+    if (over) P = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cnt[C_NPAIR_EFF] = P;
+        if (over) atomicOr(&cnt[C_STATUS], ST_CAPACITY);
+    }
+    const uint32_t n = cnt[C_NSEL_EFF];
     for (uint32_t p = blockIdx.x * RB + threadIdx.x; p < P; p += gridDim.x * RB) {
         uint32_t a = 0, b = n;
         while (b - a > 1) {
@@ -445,16 +441,12 @@ int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, 
     f.order = order;
     sm.mark(LODGS_STAGE_DEPTH_SORT, 1, st);
     sm.mark(LODGS_STAGE_EMIT, 0, st);
-    k_gather_nt<<<RGRID, RB, 0, st>>>(order, f.ntiles, f.cnt, f.nt_sorted);
-    count_launches(1);
-    rc = scan_exclusive(f.nt_sorted, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
-                        f.cnt + C_NPAIR, st);
+    rc = scan_exclusive(f.ntiles, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
+                        f.cnt + C_NPAIR, st, order);      // tile counts in depth order
     if (rc) return rc;
-    k_clamp_pairs<<<1, 1, 0, st>>>(f.cnt, f.cap_pairs);
-    count_launches(1);
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
-    k_emit<<<RGRID, RB, 0, st>>>(order, f.rect, f.sp_a, f.sp_b, f.pair_off, f.cnt, k.TX, (uint32_t)n_tiles, f.pkey,
-                                 f.pval);
+    k_emit<<<RGRID, RB, 0, st>>>(order, f.rect, f.sp_a, f.sp_b, f.pair_off, f.cnt, f.cap_pairs, k.TX,
+                                 (uint32_t)n_tiles, f.pkey, f.pval);
     count_launches(1);
     sm.mark(LODGS_STAGE_EMIT, 1, st);
     sm.mark(LODGS_STAGE_TILE_SORT, 0, st);

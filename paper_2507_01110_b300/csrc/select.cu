@@ -172,19 +172,58 @@ __global__ void __launch_bounds__(SB) k_spt_high(const uint32_t *__restrict__ cn
     }
 }
 
-__device__ __forceinline__ bool spt_item(uint32_t w, uint32_t n_emit, const uint32_t *__restrict__ work_off,
-                                         const uint32_t *__restrict__ emit_j, const float *__restrict__ emit_x,
-                                         const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
-                                         uint32_t *row, uint32_t *q = nullptr, uint32_t *e = nullptr) {
-    uint32_t a = 0, b = n_emit;                              // last q with work_off[q] <= w
+// The work items (SPT entries to test) of a tile of SB consecutive items belong
+// to at most SB consecutive emitted SPTs (each SPT has at least one item, its
+// root), starting at the SPT of the tile's first item.  A tile stages those
+// SPTs' item offsets, row bases, query values (and record slots) in shared
+// memory, so each item's SPT is found by a short shared-memory search instead
+// of a dependent chain of global loads.
+struct SptTile {
+    uint32_t off[SB], base[SB], src[SB];
+    float x[SB];
+    uint32_t count;
+};
+
+// last emitted SPT whose first item is <= w (global binary search)
+__device__ __forceinline__ uint32_t spt_of_item(uint32_t w, uint32_t n_emit, const uint32_t *__restrict__ work_off) {
+    uint32_t a = 0, b = n_emit;
     while (b - a > 1) {
         uint32_t m = a + (b - a) / 2;
         if (work_off[m] <= w) a = m; else b = m;
     }
-    uint32_t r = spt_base[emit_j[a]] + (w - work_off[a]);
-    *row = r;
-    if (q) { *q = a; *e = w - work_off[a]; }
-    return lo_row[r] <= emit_x[a];
+    return a;
+}
+
+__device__ __forceinline__ void stage_tile(SptTile &T, uint32_t q0, uint32_t t_last, uint32_t n_emit,
+                                           const uint32_t *__restrict__ work_off, const uint32_t *__restrict__ emit_j,
+                                           const float *__restrict__ emit_x, const uint32_t *__restrict__ spt_base,
+                                           const uint32_t *__restrict__ emit_src) {
+    const uint32_t q = q0 + threadIdx.x;
+    const uint32_t wo = q < n_emit ? work_off[q] : 0xffffffffu;
+    const int in_tile = q < n_emit && wo <= t_last;            // a prefix of the candidates
+    const int count = __syncthreads_count(in_tile);
+    if (in_tile) {
+        T.off[threadIdx.x] = wo;
+        T.base[threadIdx.x] = spt_base[emit_j[q]];
+        T.x[threadIdx.x] = emit_x[q];
+        if (emit_src) T.src[threadIdx.x] = emit_src[q];
+    }
+    if (threadIdx.x == 0) T.count = (uint32_t)count;
+    __syncthreads();
+}
+
+// SPT entry w of the tile: row, slot offset within its SPT, and the interval test lo <= x
+__device__ __forceinline__ bool tile_item(const SptTile &T, uint32_t w, const float *__restrict__ lo_row,
+                                          uint32_t *row, uint32_t *lq, uint32_t *e) {
+    uint32_t a = 0, b = T.count;
+    while (b - a > 1) {
+        uint32_t m = (a + b) >> 1;
+        if (T.off[m] <= w) a = m; else b = m;
+    }
+    *lq = a;
+    *e = w - T.off[a];
+    *row = T.base[a] + *e;
+    return lo_row[*row] <= T.x[a];
 }
 
 __global__ void __launch_bounds__(SB) k_spt_count(const uint32_t *__restrict__ cnt_in, const uint32_t *__restrict__ work_off,
@@ -192,13 +231,24 @@ __global__ void __launch_bounds__(SB) k_spt_count(const uint32_t *__restrict__ c
                                                   const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
                                                   uint32_t *__restrict__ bc) {
     __shared__ uint32_t s_warp[32];
-    uint32_t W = cnt_in[C_WORK], n_emit = cnt_in[C_NEMIT];
+    __shared__ SptTile T;
+    __shared__ uint32_t s_q;
+    const uint32_t W = cnt_in[C_WORK], n_emit = cnt_in[C_NEMIT];
     uint32_t begin, end;
     grid_chunk(W, begin, end);
+    if (threadIdx.x == 0 && begin < end) s_q = spt_of_item(begin, n_emit, work_off);
+    __syncthreads();
     uint32_t c = 0;
-    for (uint32_t w = begin + threadIdx.x; w < end; w += SB) {
-        uint32_t row;
-        c += spt_item(w, n_emit, work_off, emit_j, emit_x, spt_base, lo_row, &row) ? 1u : 0u;
+    for (uint32_t t0 = begin; t0 < end; t0 += SB) {
+        const uint32_t t_last = min(t0 + SB, end) - 1;
+        const uint32_t q0 = s_q;
+        stage_tile(T, q0, t_last, n_emit, work_off, emit_j, emit_x, spt_base, nullptr);
+        const uint32_t w = t0 + threadIdx.x;
+        uint32_t row, lq, e;
+        if (w <= t_last && tile_item(T, w, lo_row, &row, &lq, &e)) ++c;
+        __syncthreads();
+        if (threadIdx.x == 0) s_q = q0 + T.count - 1;           // the next tile starts in the last SPT or later
+        __syncthreads();
     }
     uint32_t tot;
     block_scan(c, s_warp, &tot);
@@ -212,25 +262,33 @@ __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, co
                                                   uint32_t *__restrict__ sel_src,
                                                   const uint32_t *__restrict__ emit_src) {
     __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_off;
+    __shared__ SptTile T;
+    __shared__ uint32_t s_off, s_q;
     uint32_t W = cnt[C_WORK], n_emit = cnt[C_NEMIT], n_up = cnt[C_NUP];
     uint32_t before = block_prefix(bc, s_warp);
-    if (threadIdx.x == 0) s_off = n_up + before;
-    __syncthreads();
     uint32_t begin, end;
     grid_chunk(W, begin, end);
+    if (threadIdx.x == 0) {
+        s_off = n_up + before;
+        if (begin < end) s_q = spt_of_item(begin, n_emit, work_off);
+    }
+    __syncthreads();
     for (uint32_t t0 = begin; t0 < end; t0 += SB) {
-        uint32_t w = t0 + threadIdx.x, row = 0, q = 0, e = 0;
-        bool keep = w < end && spt_item(w, n_emit, work_off, emit_j, emit_x, spt_base, lo_row, &row, &q, &e);
+        const uint32_t t_last = min(t0 + SB, end) - 1;
+        const uint32_t q0 = s_q;
+        stage_tile(T, q0, t_last, n_emit, work_off, emit_j, emit_x, spt_base, emit_src);
+        const uint32_t w = t0 + threadIdx.x;
+        uint32_t row = 0, lq = 0, e = 0;
+        const bool keep = w <= t_last && tile_item(T, w, lo_row, &row, &lq, &e);
         uint32_t tot;
         uint32_t ex = block_scan(keep ? 1u : 0u, s_warp, &tot);
         uint32_t o = s_off;
         if (keep) {
             sel_rows[o + ex] = row;
-            if (sel_src) sel_src[o + ex] = emit_src[q] + e;    // record slot of entry e of this SPT
+            if (sel_src) sel_src[o + ex] = T.src[lq] + e;      // record slot of entry e of this SPT
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_off = o + tot;
+        if (threadIdx.x == 0) { s_off = o + tot; s_q = q0 + T.count - 1; }
         __syncthreads();
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {

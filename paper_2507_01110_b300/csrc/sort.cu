@@ -178,19 +178,20 @@ __device__ __forceinline__ uint32_t block_reduce_add(uint32_t v, uint32_t *s_war
 }
 
 __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ in,
+                                                            const uint32_t *__restrict__ idx,
                                                             const uint32_t *__restrict__ d_n,
                                                             uint32_t *__restrict__ block_sums) {
     __shared__ uint32_t s_warp[32];
     uint32_t begin, end;
     scan_chunk(*d_n, begin, end);
     uint32_t s = 0;
-    for (uint32_t i = begin + threadIdx.x; i < end; i += SC_THREADS) s += in[i];
+    for (uint32_t i = begin + threadIdx.x; i < end; i += SC_THREADS) s += in[idx ? idx[i] : i];
     s = block_reduce_add(s, s_warp);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *in, uint32_t *out,
-                                                          const uint32_t *__restrict__ d_n,
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *in, const uint32_t *__restrict__ idx,
+                                                          uint32_t *out, const uint32_t *__restrict__ d_n,
                                                           const uint32_t *__restrict__ block_sums,
                                                           uint32_t *d_total) {
     __shared__ uint32_t s_warp[32];
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *in, ui
 #pragma unroll
         for (int k = 0; k < SC_ITEMS; ++k) {
             uint32_t i = base + k;
-            v[k] = i < end ? in[i] : 0u;
+            v[k] = i < end ? in[idx ? idx[i] : i] : 0u;
             sum += v[k];
         }
         uint32_t x = sum;
@@ -280,11 +281,11 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
 }
 
 int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n, uint32_t *block_sums,
-                   uint32_t *d_total, cudaStream_t st) {
+                   uint32_t *d_total, cudaStream_t st, const uint32_t *idx) {
     (void)max_n;
-    k_scan_reduce<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, d_n, block_sums);
+    k_scan_reduce<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, idx, d_n, block_sums);
     count_launches(1);
-    k_scan_down<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, out, d_n, block_sums, d_total);
+    k_scan_down<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, idx, out, d_n, block_sums, d_total);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;

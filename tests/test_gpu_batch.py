@@ -35,3 +35,17 @@ def test_accumulate_grads_equals_scatter_add():
     for s, g in zip(sels, grads):
         np.add.at(ref, s, g.cpu().numpy().astype(np.float64))
     assert np.allclose(summed, ref[union], rtol=1e-6, atol=1e-9)
+
+
+def test_fused_l1_loss_grad_matches_torch():
+    from paper_2507_01110_b300 import api, build
+    build.build()
+    g = torch.Generator(device="cuda").manual_seed(7)
+    for shape in ((1080, 1920, 3), (37, 41, 3)):
+        img = torch.rand(shape, device="cuda", generator=g)
+        tgt = torch.rand(shape, device="cuda", generator=g)
+        tgt.view(-1)[:5] = img.view(-1)[:5]                      # sign(0) = 0
+        dL, s = api.l1_loss_grad(img, tgt)
+        n = img.numel()
+        assert torch.equal(dL, torch.sign(img - tgt) * (1.0 / n))
+        assert abs(s.item() / n - (img - tgt).abs().mean().item()) < 1e-6
