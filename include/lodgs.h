@@ -132,10 +132,21 @@ int lodgs_frame_create(lodgs_scene *scene, lodgs_frame **out);
 void lodgs_frame_free(lodgs_frame *frame);
 
 /*
+ * Set the frame's view: the camera (if cam != NULL) and the background (if
+ * bg != NULL, host RGB).  The view is uploaded on `stream` and read by the
+ * kernels from device memory, so a CUDA graph captured from
+ * lodgs_select_lod(scene, NULL, ...) + lodgs_render(..., bg = NULL, ...) +
+ * lodgs_render_backward can be replayed for any camera of the same resolution
+ * after a lodgs_frame_set_view outside the graph.  Asynchronous.
+ */
+int lodgs_frame_set_view(lodgs_frame *frame, const lodgs_camera *cam, const float *bg, void *stream);
+
+/*
  * LoD cut for one camera (Algorithm 1 on the upper hierarchy with frustum
  * culling, Sec. 4.3; Algorithm 2 per SPT at the shared root distance, Eq. 4).
  * A node is fine enough when its projected size f*S/d <= tau.  The selected
- * render rows (ascending) stay in the frame.  Asynchronous on `stream`.
+ * render rows (ascending) stay in the frame.  cam == NULL uses the view set on
+ * the frame (lodgs_frame_set_view).  Asynchronous on `stream`.
  */
 int lodgs_select_lod(lodgs_scene *scene, const lodgs_camera *cam, lodgs_frame *frame, void *stream);
 
@@ -217,7 +228,8 @@ int lodgs_frame_selection(lodgs_frame *frame, const uint32_t **d_rows, int64_t *
  * depth sort, front-to-back blending per 16x16 tile with early stop at
  * transmittance 1e-4.
  *   rows:  device records in render-row order (NULL = the scene's own)
- *   bg:    host RGB background (NULL = black)
+ *   bg:    host RGB background (NULL = the frame's current background, black
+ *          unless set)
  *   image: device float32 H x W x 3, caller-owned
  * Asynchronous.  If a workspace buffer was too small the frame records
  * LODGS_E_CAPACITY in its status (lodgs_frame_get_stats), grows the buffer at

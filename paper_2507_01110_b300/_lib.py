@@ -75,6 +75,7 @@ _SIGS = {
     "lodgs_frame_create": (C.c_int, [_P, C.POINTER(_P)]),
     "lodgs_frame_free": (None, [_P]),
     "lodgs_select_lod": (C.c_int, [_P, C.POINTER(Camera), _P, _P]),
+    "lodgs_frame_set_view": (C.c_int, [_P, C.POINTER(Camera), _P, _P]),
     "lodgs_select_lod_noalloc": (C.c_int, [_P, C.POINTER(Camera), _P, C.c_int64, _P, _P]),
     "lodgs_frame_selection": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_int64)]),
     "lodgs_cache_create": (C.c_int, [_P, C.POINTER(CacheParams), C.POINTER(_P)]),

@@ -273,12 +273,26 @@ def build_hierarchy(leaves, sh_degree: int, spt_volume: float, kappa: float) -> 
     return Scene(h)
 
 
+def set_view(frame: Frame, camera=None, bg=None, stream=None) -> None:
+    """Set the frame's camera and/or background on the device (outside any
+    captured graph); later select_lod(scene, None, frame) and render(...) use it."""
+    cs = C.byref(camera_struct(camera)) if camera is not None else None
+    bgv = (C.c_float * 3)(*[float(b) for b in bg]) if bg is not None else None
+    check(lib().lodgs_frame_set_view(frame.handle, cs, bgv, _stream_ptr(stream)))
+    if camera is not None:
+        frame.camera = camera
+    if bg is not None:
+        frame.bg = tuple(float(b) for b in bg)
+
+
 def select_lod(scene: Scene, camera, frame: Frame | None = None, stream=None) -> Frame:
-    """LoD cut for one camera; the selection stays in the returned frame."""
+    """LoD cut for one camera; the selection stays in the returned frame.
+    camera=None uses the view set on the frame (graph-capturable form)."""
     fr = frame if frame is not None else Frame(scene)
-    cs = camera_struct(camera)
-    check(lib().lodgs_select_lod(scene.handle, C.byref(cs), fr.handle, _stream_ptr(stream)))
-    fr.camera = camera
+    cs = C.byref(camera_struct(camera)) if camera is not None else None
+    check(lib().lodgs_select_lod(scene.handle, cs, fr.handle, _stream_ptr(stream)))
+    if camera is not None:
+        fr.camera = camera
     return fr
 
 
@@ -291,8 +305,11 @@ def render(scene: Scene, frame: Frame, rows: torch.Tensor | None = None, bg=(0.0
     cam = frame.camera
     if image is None:
         image = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
-    bgv = (C.c_float * 3)(*[float(b) for b in bg])
-    frame.bg = tuple(float(b) for b in bg)
+    if bg is None:
+        bgv = None
+    else:
+        bgv = (C.c_float * 3)(*[float(b) for b in bg])
+        frame.bg = tuple(float(b) for b in bg)
     for _ in range(4):
         check(lib().lodgs_render(scene.handle, frame.handle, _ptr(rows), bgv, _ptr(image), _stream_ptr(stream)))
         if not check_capacity:

@@ -108,13 +108,29 @@ int ensure_pairs(lodgs_frame *fr, uint64_t want) {
 }
 
 void free_frame_bufs(FrameBufs &f) {
-    void *ps[] = {f.cnt, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
+    void *ps[] = {f.cnt, f.d_view, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
                   f.sort_hist, f.sp_a, f.sp_b, f.sp_c, f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.rect, f.ntiles,
                   f.nt_sorted, f.pair_off, f.g2d, f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.ranges, f.work,
                   f.sel_src, f.emit_src};
     for (void *p : ps)
         if (p) cudaFree(p);
     f = FrameBufs();
+}
+
+}  // namespace
+
+namespace {
+
+// Upload the frame's view (camera constants and background) on `st`.
+int set_view(lodgs_frame *fr, const lodgs_camera *cam, const float *bg, cudaStream_t st) {
+    if (cam) fr->k = make_camk(*cam);
+    if (bg) { fr->bg[0] = bg[0]; fr->bg[1] = bg[1]; fr->bg[2] = bg[2]; }
+    View v;
+    v.k = fr->k;
+    v.bg[0] = fr->bg[0]; v.bg[1] = fr->bg[1]; v.bg[2] = fr->bg[2]; v.bg[3] = 0.f;
+    int rc = launch_set_view(v, fr->f.d_view, st);
+    if (!rc) fr->have_view = true;
+    return rc;
 }
 
 }  // namespace
@@ -221,7 +237,7 @@ int lodgs_frame_create(lodgs_scene *sc, lodgs_frame **out) {
     cudaError_t e = cudaSuccess;
 #define AL(p, n)                                                                  \
     if (e == cudaSuccess) e = cudaMalloc((void **)&p, std::max<size_t>((size_t)(n), 1) * sizeof(*p));
-    AL(f.cnt, C_COUNT) AL(f.sel_rows, M) AL(f.emit_j, S) AL(f.emit_x, S) AL(f.high, S + 1) AL(f.work_off, S + 1)
+    AL(f.cnt, C_COUNT) AL(f.d_view, 1) AL(f.sel_rows, M) AL(f.emit_j, S) AL(f.emit_x, S) AL(f.high, S + 1) AL(f.work_off, S + 1)
     AL(f.block_counts, 1024) AL(f.scan_bsum, SCAN_GRID) AL(f.sort_hist, SORT_HIST) AL(f.work, 4)
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void **)&fr->h_cnt, C_COUNT * sizeof(uint32_t));
@@ -249,17 +265,27 @@ void lodgs_frame_free(lodgs_frame *fr) {
     delete fr;
 }
 
+int lodgs_frame_set_view(lodgs_frame *fr, const lodgs_camera *cam, const float *bg, void *stream) {
+    if (!fr) { set_error("frame_set_view: NULL frame"); return LODGS_E_INVALID; }
+    if (cam && !camera_ok(cam)) { set_error("frame_set_view: invalid camera"); return LODGS_E_INVALID; }
+    return set_view(fr, cam, bg, (cudaStream_t)stream);
+}
+
 int lodgs_select_lod(lodgs_scene *sc, const lodgs_camera *cam, lodgs_frame *fr, void *stream) {
     if (!sc || !fr || fr->scene != sc) { set_error("select_lod: frame does not belong to scene"); return LODGS_E_INVALID; }
-    if (!camera_ok(cam)) { set_error("select_lod: invalid camera"); return LODGS_E_INVALID; }
+    if (cam ? !camera_ok(cam) : !fr->have_view) {
+        set_error(cam ? "select_lod: invalid camera" : "select_lod: no camera given and none set on the frame");
+        return LODGS_E_INVALID;
+    }
     cudaStream_t st = (cudaStream_t)stream;
-    fr->k = make_camk(*cam);
     fr->stream = st;
     fr->f.use_src = false;
     for (bool &r : fr->ran) r = false;
     fr->mark(LODGS_STAGE_SELECT, 0, st);
+    if (cam)
+        if (int rc = set_view(fr, cam, nullptr, st)) return rc;
     LODGS_CUDA(cudaMemsetAsync(fr->f.cnt, 0, C_COUNT * sizeof(uint32_t), st));
-    int rc = launch_select(sc, fr->k, fr->f, st);
+    int rc = launch_select(sc, fr->f, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_SELECT, 1, st);
     fr->selected = true;
@@ -296,8 +322,8 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     uint64_t c = fr->f.cap_tiles;
     if (int r = grow(fr->f.ranges, c, n_tiles)) return r;
     fr->f.cap_tiles = c;
-    float b[3] = {0.f, 0.f, 0.f};
-    if (bg) { b[0] = bg[0]; b[1] = bg[1]; b[2] = bg[2]; }
+    if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2]))
+        if (int r = set_view(fr, nullptr, bg, st)) return r;
     // reset the render's counters and status (the selection's counters stay)
     LODGS_CUDA(cudaMemsetAsync(fr->f.cnt + C_NSEL_EFF, 0, (C_COUNT - C_NSEL_EFF) * sizeof(uint32_t), st));
     fr->mark(LODGS_STAGE_PROJECT, 0, st);
@@ -305,11 +331,11 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
         set_error("render: the scene's records live in host memory; pass the cache's device records");
         return LODGS_E_INVALID;
     }
-    int rc = launch_project(sc, rows ? rows : sc->d_rows, fr->k, fr->f, st);
+    int rc = launch_project(sc, rows ? rows : sc->d_rows, fr->f, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_PROJECT, 1, st);
     StageMarks sm{fr->prof ? fr->ev : nullptr};
-    rc = launch_raster(fr->k, fr->f, b, image, st, sm);
+    rc = launch_raster(fr->k, fr->f, image, st, sm);
     if (rc) return rc;
     if (fr->prof)
         for (int s2 = LODGS_STAGE_DEPTH_SORT; s2 <= LODGS_STAGE_BLEND; ++s2) fr->ran[s2] = true;
@@ -334,10 +360,12 @@ int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, c
         cudaEventDestroy(ev);
         fr->stream = st;
     }
-    float b[3] = {0.f, 0.f, 0.f};
-    if (bg) { b[0] = bg[0]; b[1] = bg[1]; b[2] = bg[2]; }
+    if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2])) {
+        set_error("render_backward: background differs from the one the frame was rendered with");
+        return LODGS_E_STATE;
+    }
     fr->mark(LODGS_STAGE_BLEND_BWD, 0, st);
-    int rc = launch_raster_backward(fr->k, fr->f, b, dL_dimage, st);
+    int rc = launch_raster_backward(fr->k, fr->f, dL_dimage, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_BLEND_BWD, 1, st);
     fr->mark(LODGS_STAGE_PROJECT_BWD, 0, st);
@@ -345,7 +373,7 @@ int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, c
         set_error("render_backward: the scene's records live in host memory; pass the cache's device records");
         return LODGS_E_INVALID;
     }
-    rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->k, fr->f, grad_rows, dense, st);
+    rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->f, grad_rows, dense, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_PROJECT_BWD, 1, st);
     return LODGS_OK;

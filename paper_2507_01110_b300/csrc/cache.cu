@@ -200,13 +200,13 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
     const int64_t M = sc->n_nodes, S = sc->n_spt;
     if (!f.sel_src) LODGS_CUDA(cudaMalloc((void **)&f.sel_src, (size_t)std::max<int64_t>(M, 1) * 4));
     if (!f.emit_src) LODGS_CUDA(cudaMalloc((void **)&f.emit_src, (size_t)std::max<int64_t>(S, 1) * 4));
-    fr->k = make_camk(*cam);
     fr->stream = st;
     for (bool &r : fr->ran) r = false;
     fr->mark(LODGS_STAGE_SELECT, 0, st);
+    if (int rc = lodgs_frame_set_view(fr, cam, nullptr, stream)) return rc;
     LODGS_CUDA(cudaMemsetAsync(f.cnt, 0, C_COUNT * sizeof(uint32_t), st));
     // 1. upper cut and, per SPT root, the prefix needed at the current distance
-    if (int rc = launch_select_upper(sc, fr->k, f, true, st)) return rc;
+    if (int rc = launch_select_upper(sc, f, true, st)) return rc;
     if (int rc = launch_spt_high(sc, f, st)) return rc;
     const size_t n = (size_t)std::max<int64_t>(S, 1);
     LODGS_CUDA(cudaMemcpyAsync(c->h_cnt, f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost, st));

@@ -33,6 +33,14 @@ struct CamK {
 
 CamK make_camk(const lodgs_camera &c);
 
+// Per-view parameters read by the kernels from device memory, so that a
+// captured CUDA graph of a view's step can be replayed for any camera of the
+// same resolution (the view is uploaded outside the graph).
+struct View {
+    CamK k;
+    float bg[4];
+};
+
 // view-space position and camera distance of a world point (float32, evaluated
 // exactly as written; translation units using it are compiled without FMA
 // contraction)
@@ -109,6 +117,7 @@ namespace lodgs {
 // Device buffers of one frame (one view).  Capacities are element counts.
 struct FrameBufs {
     uint32_t *cnt = nullptr;         // C_COUNT device counters
+    View *d_view = nullptr;          // camera constants and background of the current view
     // selection (capacity n_nodes / n_spt)
     uint32_t *sel_rows = nullptr, *emit_j = nullptr, *high = nullptr, *work_off = nullptr;
     uint32_t *sel_src = nullptr;      // record slot of each selected node (out-of-core renders)
@@ -174,17 +183,17 @@ struct StageMarks {
 };
 
 // per-view stages (select.cu, project.cu, raster.cu)
-int launch_select(const lodgs_scene *sc, const CamK &k, FrameBufs &f, cudaStream_t st);
-int launch_select_upper(const lodgs_scene *sc, const CamK &k, FrameBufs &f, bool with_src, cudaStream_t st);
+int launch_set_view(const View &v, View *dst, cudaStream_t st);
+int launch_select(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st);
+int launch_select_upper(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st);
 int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st);
 int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st);
-int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, cudaStream_t st);
-int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, cudaStream_t st,
-                  const StageMarks &sm);
-int launch_raster_backward(const CamK &k, FrameBufs &f, const float bg[3], const float *dL_dimage,
-                           cudaStream_t st);
-int launch_project_backward(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f,
-                            float *grad_rows, int dense, cudaStream_t st);
+// `k` is the host copy of the view (resolution, grid sizes); kernels read f.d_view
+int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaStream_t st);
+int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, const StageMarks &sm);
+int launch_raster_backward(const CamK &k, FrameBufs &f, const float *dL_dimage, cudaStream_t st);
+int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows, int dense,
+                            cudaStream_t st);
 }  // namespace lodgs
 
 struct lodgs_frame {
@@ -193,7 +202,8 @@ struct lodgs_frame {
     uint32_t *h_cnt = nullptr;          // pinned mirror of the device counters
     cudaStream_t stream = 0;
     lodgs::CamK k{};
-    bool selected = false, rendered = false;
+    bool selected = false, rendered = false, have_view = false;
+    float bg[3] = {0.f, 0.f, 0.f};
     uint64_t want_sel = 0, want_pairs = 0;
     // stage timing: ev[2s] / ev[2s+1] bracket stage s
     bool prof = false;

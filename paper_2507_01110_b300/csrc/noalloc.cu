@@ -21,7 +21,9 @@ namespace {
 constexpr int64_t NA_MAX_SPT = LODGS_NOALLOC_MAX_SPT;
 // word offsets inside the scratch array
 constexpr size_t NA_CNT = 0;                                  // C_COUNT counters
+constexpr size_t NA_VIEW = 64;                                // the view (camera constants)
 constexpr size_t NA_BLOCK = 256;                              // 1024 block counts
+static_assert(sizeof(View) <= (NA_BLOCK - NA_VIEW) * 4, "the view must fit its slot");
 constexpr size_t NA_BSUM = NA_BLOCK + 1024;                   // scan block sums
 constexpr size_t NA_EMIT_J = NA_BSUM + 256;                   // n_spt SPT indices
 constexpr size_t NA_EMIT_X = NA_EMIT_J + NA_MAX_SPT;          // n_spt query values
@@ -82,6 +84,7 @@ extern "C" int lodgs_select_lod_noalloc(lodgs_scene *scene, const lodgs_camera *
     cudaStream_t st = (cudaStream_t)stream;
     FrameBufs f;
     f.cnt = s + NA_CNT;
+    f.d_view = reinterpret_cast<View *>(s + NA_VIEW);
     f.block_counts = s + NA_BLOCK;
     f.scan_bsum = s + NA_BSUM;
     f.emit_j = s + NA_EMIT_J;
@@ -90,8 +93,10 @@ extern "C" int lodgs_select_lod_noalloc(lodgs_scene *scene, const lodgs_camera *
     f.work_off = s + NA_WORK;
     f.sel_rows = d_rows;
     LODGS_CUDA(cudaMemsetAsync(f.cnt, 0, C_COUNT * sizeof(uint32_t), st));
-    const CamK k = make_camk(*cam);
-    if (int rc = launch_select(scene, k, f, st)) return rc;
+    View v{};
+    v.k = make_camk(*cam);
+    if (int rc = launch_set_view(v, f.d_view, st)) return rc;   // a kernel argument: no staging buffer
+    if (int rc = launch_select(scene, f, st)) return rc;
     LODGS_CUDA(cudaMemcpyAsync(d_count, f.cnt + C_NSEL, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
     return LODGS_OK;
 }

@@ -132,11 +132,12 @@ __device__ __forceinline__ void geometry(const CamK &k, const float *mu, const f
 
 template <int DEG>
 __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, int stride,
-                                                 const uint32_t *__restrict__ sel_rows, CamK k,
+                                                 const uint32_t *__restrict__ sel_rows, const View *__restrict__ view,
                                                  uint32_t *__restrict__ cnt, uint64_t cap_sel, float4 *__restrict__ sp_a,
                                                  float4 *__restrict__ sp_b, float *__restrict__ sp_c,
                                                  uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
                                                  uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles) {
+    const CamK &k = view->k;
     // selections beyond the workspace are not rendered: the frame reports a capacity error
     uint32_t n = cnt[C_NSEL];
     if (n > cap_sel) n = 0;
@@ -224,11 +225,12 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
 template <int DEG>
 __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ rows, int stride,
                                                      const uint32_t *__restrict__ sel_src,
-                                                     const uint32_t *__restrict__ sel_rows, CamK k,
-                                                     const uint32_t *__restrict__ cnt,
+                                                     const uint32_t *__restrict__ sel_rows,
+                                                     const View *__restrict__ view, const uint32_t *__restrict__ cnt,
                                                      const uint32_t *__restrict__ ntiles,
                                                      const float *__restrict__ g2d, float *__restrict__ out,
                                                      int dense) {
+    const CamK &k = view->k;
     const uint32_t n = cnt[C_NSEL_EFF];
     constexpr int degree = DEG;
     constexpr int K = (DEG + 1) * (DEG + 1) - 1;
@@ -361,9 +363,9 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
 
 }  // namespace
 
-int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, cudaStream_t st) {
+int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaStream_t st) {
 #define LAUNCH_PROJ(D)                                                                                     \
-    k_project<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, k, f.cnt, f.cap_sel, f.sp_a, \
+    k_project<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.d_view, f.cnt, f.cap_sel, f.sp_a, \
                                            f.sp_b, f.sp_c, f.dkey, f.dval, f.rect, f.ntiles)
     switch (sc->sh_degree) {
         case 0: LAUNCH_PROJ(0); break;
@@ -377,10 +379,10 @@ int launch_project(const lodgs_scene *sc, const float *rows, const CamK &k, Fram
     return LODGS_OK;
 }
 
-int launch_project_backward(const lodgs_scene *sc, const float *rows, const CamK &k, FrameBufs &f, float *grad_rows,
-                            int dense, cudaStream_t st) {
+int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows, int dense,
+                            cudaStream_t st) {
 #define LAUNCH_PBWD(D)                                                                                     \
-    k_project_bwd<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.sel_rows, k, \
+    k_project_bwd<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.sel_rows, f.d_view, \
                                                f.cnt, f.ntiles, f.g2d, grad_rows, dense)
     switch (sc->sh_degree) {
         case 0: LAUNCH_PBWD(0); break;

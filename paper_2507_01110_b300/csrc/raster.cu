@@ -173,8 +173,9 @@ __global__ void __launch_bounds__(TILE_PIX / PIX) k_blend(const uint2 *__restric
                                                           const float4 *__restrict__ sp_b,
                                                           const float *__restrict__ sp_c,
                                                           const uint32_t *__restrict__ cnt, int W, int H, int TX,
-                                                          float bg0, float bg1, float bg2, float *__restrict__ image,
+                                                          const View *__restrict__ view, float *__restrict__ image,
                                                           unsigned long long *__restrict__ work) {
+    const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
     constexpr int NT = TILE_PIX / PIX, RS = TILE / PIX;
     uint32_t n_eval = 0, n_blend = 0;
     __shared__ float4 s_a[BATCH], s_b[BATCH];
@@ -252,11 +253,12 @@ __global__ void __launch_bounds__(TILE_PIX / PIX) k_blend_bwd(const uint2 *__res
                                                               const float4 *__restrict__ sp_b,
                                                               const float *__restrict__ sp_c,
                                                               const uint32_t *__restrict__ cnt, int W, int H, int TX,
-                                                              float bg0, float bg1, float bg2,
+                                                              const View *__restrict__ view,
                                                               const float *__restrict__ dL_dimg,
                                                               float *__restrict__ g2d,
                                                               unsigned long long *__restrict__ work) {
     constexpr int NT = TILE_PIX / PIX, RS = TILE / PIX;
+    const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
     uint32_t n_eval = 0, n_contrib = 0;
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
@@ -430,8 +432,7 @@ int ceil_log2(uint64_t x) {
 
 }  // namespace
 
-int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, cudaStream_t st,
-                  const StageMarks &sm) {
+int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, const StageMarks &sm) {
     bool alt;
     sm.mark(LODGS_STAGE_DEPTH_SORT, 0, st);
     int rc = radix_sort_pairs(f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, 0, 32,
@@ -462,19 +463,19 @@ int launch_raster(const CamK &k, FrameBufs &f, const float bg[3], float *image, 
     k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, (uint32_t)n_tiles, f.ranges);
     count_launches(1);
     k_blend<FWD_PIX><<<(unsigned)n_tiles, TILE_PIX / FWD_PIX, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX,
-                                              bg[0], bg[1], bg[2], image, f.work);
+                                              f.d_view, image, f.work);
     count_launches(1);
     sm.mark(LODGS_STAGE_BLEND, 1, st);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
 }
 
-int launch_raster_backward(const CamK &k, FrameBufs &f, const float bg[3], const float *dL_dimage, cudaStream_t st) {
+int launch_raster_backward(const CamK &k, FrameBufs &f, const float *dL_dimage, cudaStream_t st) {
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * 9 * sizeof(float), st));
     LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
     k_blend_bwd<BWD_PIX><<<(unsigned)n_tiles, TILE_PIX / BWD_PIX, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H,
-                                                  k.TX, bg[0], bg[1], bg[2], dL_dimage, f.g2d, f.work);
+                                                  k.TX, f.d_view, dL_dimage, f.g2d, f.work);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;

@@ -92,8 +92,9 @@ __device__ __forceinline__ uint32_t block_prefix(const uint32_t *__restrict__ co
 }
 
 // ---- a1 --------------------------------------------------------------------
-__global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict__ up, uint32_t U, CamK k,
-                                                    uint32_t *__restrict__ bc) {
+__global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict__ up, uint32_t U,
+                                                    const View *__restrict__ view, uint32_t *__restrict__ bc) {
+    const CamK &k = view->k;
     __shared__ uint32_t s_warp[32];
     uint32_t begin, end;
     grid_chunk(U, begin, end);
@@ -108,10 +109,12 @@ __global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict
     if (threadIdx.x == 0) bc[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict__ up, uint32_t U, CamK k,
+__global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict__ up, uint32_t U,
+                                                    const View *__restrict__ view,
                                                     const uint32_t *__restrict__ bc, uint32_t *__restrict__ sel_rows,
                                                     uint32_t *__restrict__ sel_src, uint32_t *__restrict__ emit_j,
                                                     float *__restrict__ emit_x, uint32_t *__restrict__ cnt) {
+    const CamK &k = view->k;
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_off_sel, s_off_emit;
     uint32_t sel_before = 0, emit_before = 0;
@@ -297,13 +300,28 @@ __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, co
     }
 }
 
+__global__ void k_set_view(View v, View *__restrict__ dst) {
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(&v);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t i = threadIdx.x; i < sizeof(View) / 4; i += blockDim.x) d[i] = s[i];
+}
+
 }  // namespace
 
-int launch_select_upper(const lodgs_scene *sc, const CamK &k, FrameBufs &f, bool with_src, cudaStream_t st) {
-    uint32_t U = (uint32_t)sc->n_upper;
-    k_upper_count<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, k, f.block_counts);
+// The view goes to the device as a kernel argument: the copy is asynchronous,
+// needs no host staging buffer, and is ordered on the stream like the kernels.
+int launch_set_view(const View &v, View *dst, cudaStream_t st) {
+    k_set_view<<<1, 32, 0, st>>>(v, dst);
     count_launches(1);
-    k_upper_write<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, k, f.block_counts, f.sel_rows, with_src ? f.sel_src : nullptr,
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
+
+int launch_select_upper(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st) {
+    uint32_t U = (uint32_t)sc->n_upper;
+    k_upper_count<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, f.d_view, f.block_counts);
+    count_launches(1);
+    k_upper_write<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, f.d_view, f.block_counts, f.sel_rows, with_src ? f.sel_src : nullptr,
                                            f.emit_j, f.emit_x, f.cnt);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
@@ -331,8 +349,8 @@ int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaSt
     return LODGS_OK;
 }
 
-int launch_select(const lodgs_scene *sc, const CamK &k, FrameBufs &f, cudaStream_t st) {
-    int rc = launch_select_upper(sc, k, f, false, st);
+int launch_select(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st) {
+    int rc = launch_select_upper(sc, f, false, st);
     if (!rc) rc = launch_spt_high(sc, f, st);
     if (!rc) rc = launch_select_spt(sc, f, false, st);
     return rc;
