@@ -293,7 +293,8 @@ int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);
 #define LODGS_STAGE_PROJECT_BWD 7 /* backward of the projection + gradient rows */
 #define LODGS_NUM_STAGES 8
 
-/* Record CUDA events around every stage of this frame (on = 1) or not (0). */
+/* Record CUDA events around the stages of this frame: on < 0 all stages, 0
+ * none, > 0 a bit mask of LODGS_STAGE_* bits (1 << stage). */
 int lodgs_frame_set_profiling(lodgs_frame *frame, int on);
 /* Device time in milliseconds of each stage of the last select/render/backward
  * on this frame (LODGS_NUM_STAGES floats; 0 for stages that did not run since

@@ -131,8 +131,15 @@ class Frame:
             return torch.zeros(0, dtype=torch.int64, device="cuda")
         return _device_view(p.value, (int(n.value),), "<u4").to(torch.int64)
 
-    def set_profiling(self, on: bool = True) -> None:
-        check(lib().lodgs_frame_set_profiling(self._h, C.c_int(int(on))))
+    def set_profiling(self, on=True) -> None:
+        """True: time every stage; False: none; a list of stage names: those."""
+        if on is True:
+            mask = -1
+        elif not on:
+            mask = 0
+        else:
+            mask = sum(1 << _lib.STAGES.index(s) for s in on)
+        check(lib().lodgs_frame_set_profiling(self._h, C.c_int(mask)))
 
     def stage_ms(self) -> dict:
         """Device milliseconds per stage of the last select/render/backward."""

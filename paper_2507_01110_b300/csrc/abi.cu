@@ -334,11 +334,11 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     int rc = launch_project(sc, rows ? rows : sc->d_rows, fr->f, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_PROJECT, 1, st);
-    StageMarks sm{fr->prof ? fr->ev : nullptr};
+    StageMarks sm{fr->prof_mask ? fr->ev : nullptr, fr->prof_mask};
     rc = launch_raster(fr->k, fr->f, image, st, sm);
     if (rc) return rc;
-    if (fr->prof)
-        for (int s2 = LODGS_STAGE_DEPTH_SORT; s2 <= LODGS_STAGE_BLEND; ++s2) fr->ran[s2] = true;
+    for (int s2 = LODGS_STAGE_DEPTH_SORT; s2 <= LODGS_STAGE_BLEND; ++s2)
+        if (fr->prof_mask >> s2 & 1u) fr->ran[s2] = true;
     LODGS_CUDA(cudaMemcpyAsync(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
     fr->rendered = true;
     return LODGS_OK;
@@ -408,13 +408,13 @@ int lodgs_frame_set_profiling(lodgs_frame *fr, int on) {
     if (on)
         for (cudaEvent_t &e : fr->ev)
             if (!e) LODGS_CUDA(cudaEventCreate(&e));
-    fr->prof = on != 0;
+    fr->prof_mask = on < 0 ? (1u << LODGS_NUM_STAGES) - 1u : (uint32_t)on;
     return LODGS_OK;
 }
 
 int lodgs_frame_stage_ms(lodgs_frame *fr, float *ms) {
     if (!fr || !ms) { set_error("frame_stage_ms: NULL argument"); return LODGS_E_INVALID; }
-    if (!fr->prof) { set_error("frame_stage_ms: profiling is off"); return LODGS_E_STATE; }
+    if (!fr->prof_mask) { set_error("frame_stage_ms: profiling is off"); return LODGS_E_STATE; }
     LODGS_CUDA(cudaStreamSynchronize(fr->stream));
     for (int s2 = 0; s2 < LODGS_NUM_STAGES; ++s2) {
         ms[s2] = 0.f;

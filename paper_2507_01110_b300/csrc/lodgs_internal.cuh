@@ -174,11 +174,12 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
 constexpr int SCAN_GRID = 148;
 int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n,
                    uint32_t *block_sums, uint32_t *d_total, cudaStream_t st, const uint32_t *idx = nullptr);
-// optional CUDA events bracketing stages (ev[2s], ev[2s+1]); null = off
+// optional CUDA events bracketing stages (ev[2s], ev[2s+1]) of the stages in `mask`
 struct StageMarks {
     cudaEvent_t *ev = nullptr;
+    uint32_t mask = 0;
     void mark(int stage, int end, cudaStream_t st) const {
-        if (ev) cudaEventRecord(ev[2 * stage + end], st);
+        if (ev && (mask >> stage & 1u)) cudaEventRecord(ev[2 * stage + end], st);
     }
 };
 
@@ -205,12 +206,12 @@ struct lodgs_frame {
     bool selected = false, rendered = false, have_view = false;
     float bg[3] = {0.f, 0.f, 0.f};
     uint64_t want_sel = 0, want_pairs = 0;
-    // stage timing: ev[2s] / ev[2s+1] bracket stage s
-    bool prof = false;
+    // stage timing: ev[2s] / ev[2s+1] bracket stage s, for the stages in prof_mask
+    uint32_t prof_mask = 0;
     cudaEvent_t ev[2 * LODGS_NUM_STAGES] = {};
     bool ran[LODGS_NUM_STAGES] = {};
     void mark(int stage, int end, cudaStream_t st) {
-        if (!prof) return;
+        if (!(prof_mask >> stage & 1u)) return;
         cudaEventRecord(ev[2 * stage + end], st);
         if (end) ran[stage] = true;
     }
