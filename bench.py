@@ -212,11 +212,21 @@ def run_lodgs(args, rank: int, world: int):
     dL = torch.empty_like(image)
     loss_sum = torch.empty(1, device="cuda")
 
-    def step(v, target, camera):
+    def step_fwd(v, target, camera):
         fr = api.select_lod(scene, camera, frames[v])                  # camera=None: the frame's view
         api.render(scene, fr, image=image, bg=None, check_capacity=False)
         api.l1_loss_grad(image, target, dL=dL, loss_sum=loss_sum)     # fused mean-L1 loss + gradient
-        api.render_backward(scene, fr, dL, grad=grad)
+
+    def step_bwd_blend(v):
+        api.render_backward_blend(scene, frames[v], dL)
+
+    def step_bwd_project(v):
+        api.render_backward_project(scene, frames[v], grad)
+
+    def step(v, target, camera):
+        step_fwd(v, target, camera)
+        step_bwd_blend(v)
+        step_bwd_project(v)
         return loss_sum
 
     order = [my_views[i % len(my_views)] for i in range(args.steps)]
@@ -225,24 +235,41 @@ def run_lodgs(args, rank: int, world: int):
         step(v, targets_d[v], cams[v])
     torch.cuda.synchronize()
 
-    # One CUDA graph per frame of the whole step (select, render, loss,
-    # backward); the camera is uploaded before each replay, outside the graph.
+    # CUDA graphs per frame: [select, render, loss], [blend backward],
+    # [projection backward]; the camera is uploaded before each replay, outside
+    # the graphs, and events between the graph launches time the blend backward
+    # (the dominant kernel) inside the timed region.
     for v in my_views:
         api.set_view(frames[v], cams[v])
-        frames[v].set_profiling(["blend_bwd"])       # the dominant kernel, timed inside the timed region
     torch.cuda.synchronize()
     cap = torch.cuda.Stream()
     graphs = {}
     with torch.cuda.stream(cap):
         for v in my_views:
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=cap):
-                step(v, targets_d[v], None)
-            graphs[v] = g
+            gs = [torch.cuda.CUDAGraph() for _ in range(3)]
+            with torch.cuda.graph(gs[0], stream=cap):
+                step_fwd(v, targets_d[v], None)
+            with torch.cuda.graph(gs[1], stream=cap):
+                step_bwd_blend(v)
+            with torch.cuda.graph(gs[2], stream=cap):
+                step_bwd_project(v)
+            graphs[v] = gs
     torch.cuda.synchronize()
-    for v in my_views:                               # one untimed replay each
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    def replay(v, i=None):
         api.set_view(frames[v], cams[v])
-        graphs[v].replay()
+        graphs[v][0].replay()
+        if i is not None:
+            ev_a[i].record(stream)
+        graphs[v][1].replay()
+        if i is not None:
+            ev_b[i].record(stream)
+        graphs[v][2].replay()
+
+    for v in my_views:                               # one untimed replay each
+        replay(v)
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident inputs ----
@@ -255,9 +282,8 @@ def run_lodgs(args, rank: int, world: int):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
-    for v in order:
-        api.set_view(frames[v], cams[v])
-        graphs[v].replay()
+    for i, v in enumerate(order):
+        replay(v, i)
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
@@ -266,13 +292,12 @@ def run_lodgs(args, rank: int, world: int):
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    bwd_ms = []
+    bwd_ms = [a.elapsed_time(b2) for a, b2 in zip(ev_a, ev_b)]
     stats_ok = True
     work = {}
     for v in set(order):
         fr = frames[v]
         work[v] = fr.work()
-        bwd_ms.append(fr.stage_ms()["blend_bwd"])
         stats_ok &= fr.stats()["status"] == 0
     # kernels per step: counted on an eager step (graph replays launch the same kernels)
     l0 = _lib.lib().lodgs_kernel_launches()
@@ -317,8 +342,7 @@ def run_lodgs(args, rank: int, world: int):
     g0.record(stream)
     for i, v in enumerate(order):
         targets_d[v].copy_(targets_h[v], non_blocking=True)
-        api.set_view(frames[v], cams[v])
-        graphs[v].replay()
+        replay(v)
         loss_h[i:i + 1].copy_(loss_sum, non_blocking=True)
     g1.record(stream)
     torch.cuda.synchronize()

@@ -278,6 +278,14 @@ int lodgs_accumulate_grads(lodgs_scene *scene, lodgs_frame *const *frames, const
 int lodgs_l1_loss_grad(const float *image, const float *target, int64_t n, float grad_scale, float *dL,
                        float *loss_sum, void *stream);
 
+/* The two halves of lodgs_render_backward, for callers that schedule them
+ * separately (e.g. as separate CUDA graphs): the blend backward (per-pixel
+ * recomputation, 2D gradients kept in the frame), then the projection backward
+ * into gradient rows (same meaning of rows, grad_rows, dense). */
+int lodgs_render_backward_blend(lodgs_scene *scene, lodgs_frame *frame, const float *dL_dimage, void *stream);
+int lodgs_render_backward_project(lodgs_scene *scene, lodgs_frame *frame, const float *rows, float *grad_rows,
+                                  int dense, void *stream);
+
 /* Counters of the last select/render on this frame (blocks until `stream`,
  * the stream the frame last ran on, is idle). */
 int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);

@@ -280,6 +280,20 @@ def build_hierarchy(leaves, sh_degree: int, spt_volume: float, kappa: float) -> 
     return Scene(h)
 
 
+def render_backward_blend(scene: Scene, frame: Frame, dL_dimage: torch.Tensor, stream=None) -> None:
+    """First half of render_backward: the blend backward (2D gradients stay in the frame)."""
+    check(lib().lodgs_render_backward_blend(scene.handle, frame.handle, _ptr(dL_dimage.contiguous()),
+                                            _stream_ptr(stream)))
+
+
+def render_backward_project(scene: Scene, frame: Frame, grad: torch.Tensor, rows: torch.Tensor | None = None,
+                            dense: bool = False, stream=None) -> torch.Tensor:
+    """Second half of render_backward: the projection backward into `grad`."""
+    check(lib().lodgs_render_backward_project(scene.handle, frame.handle, _ptr(rows), _ptr(grad),
+                                              C.c_int(int(dense)), _stream_ptr(stream)))
+    return grad
+
+
 def set_view(frame: Frame, camera=None, bg=None, stream=None) -> None:
     """Set the frame's camera and/or background on the device (outside any
     captured graph); later select_lod(scene, None, frame) and render(...) use it."""

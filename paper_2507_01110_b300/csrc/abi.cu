@@ -290,6 +290,7 @@ int lodgs_select_lod(lodgs_scene *sc, const lodgs_camera *cam, lodgs_frame *fr, 
     fr->mark(LODGS_STAGE_SELECT, 1, st);
     fr->selected = true;
     fr->rendered = false;
+    fr->blend_bwd_done = false;
     return LODGS_OK;
 }
 
@@ -341,13 +342,13 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
         if (fr->prof_mask >> s2 & 1u) fr->ran[s2] = true;
     LODGS_CUDA(cudaMemcpyAsync(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
     fr->rendered = true;
+    fr->blend_bwd_done = false;
     return LODGS_OK;
 }
 
-int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const float *bg,
-                          const float *dL_dimage, float *grad_rows, int dense, void *stream) {
-    if (!sc || !fr || fr->scene != sc || !dL_dimage || !grad_rows) {
-        set_error("render_backward: NULL or mismatched argument");
+int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *dL_dimage, void *stream) {
+    if (!sc || !fr || fr->scene != sc || !dL_dimage) {
+        set_error("render_backward_blend: NULL or mismatched argument");
         return LODGS_E_INVALID;
     }
     if (!fr->rendered) { set_error("render_backward: render was not called on this frame"); return LODGS_E_STATE; }
@@ -360,23 +361,54 @@ int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, c
         cudaEventDestroy(ev);
         fr->stream = st;
     }
-    if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2])) {
-        set_error("render_backward: background differs from the one the frame was rendered with");
-        return LODGS_E_STATE;
-    }
     fr->mark(LODGS_STAGE_BLEND_BWD, 0, st);
     int rc = launch_raster_backward(fr->k, fr->f, dL_dimage, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_BLEND_BWD, 1, st);
-    fr->mark(LODGS_STAGE_PROJECT_BWD, 0, st);
+    fr->blend_bwd_done = true;
+    return LODGS_OK;
+}
+
+int lodgs_render_backward_project(lodgs_scene *sc, lodgs_frame *fr, const float *rows, float *grad_rows, int dense,
+                                  void *stream) {
+    if (!sc || !fr || fr->scene != sc || !grad_rows) {
+        set_error("render_backward_project: NULL or mismatched argument");
+        return LODGS_E_INVALID;
+    }
+    if (!fr->blend_bwd_done) { set_error("render_backward_project: the blend backward has not run"); return LODGS_E_STATE; }
     if (!rows && !sc->d_rows) {
         set_error("render_backward: the scene's records live in host memory; pass the cache's device records");
         return LODGS_E_INVALID;
     }
-    rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->f, grad_rows, dense, st);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (st != fr->stream) {
+        cudaEvent_t ev;
+        LODGS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaEventRecord(ev, fr->stream);
+        cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+        fr->stream = st;
+    }
+    fr->mark(LODGS_STAGE_PROJECT_BWD, 0, st);
+    int rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->f, grad_rows, dense, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_PROJECT_BWD, 1, st);
     return LODGS_OK;
+}
+
+int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const float *bg,
+                          const float *dL_dimage, float *grad_rows, int dense, void *stream) {
+    if (!sc || !fr || fr->scene != sc || !dL_dimage || !grad_rows) {
+        set_error("render_backward: NULL or mismatched argument");
+        return LODGS_E_INVALID;
+    }
+    if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2])) {
+        set_error("render_backward: background differs from the one the frame was rendered with");
+        return LODGS_E_STATE;
+    }
+    int rc = lodgs_render_backward_blend(sc, fr, dL_dimage, stream);
+    if (!rc) rc = lodgs_render_backward_project(sc, fr, rows, grad_rows, dense, stream);
+    return rc;
 }
 
 int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {

@@ -203,7 +203,7 @@ struct lodgs_frame {
     uint32_t *h_cnt = nullptr;          // pinned mirror of the device counters
     cudaStream_t stream = 0;
     lodgs::CamK k{};
-    bool selected = false, rendered = false, have_view = false;
+    bool selected = false, rendered = false, have_view = false, blend_bwd_done = false;
     float bg[3] = {0.f, 0.f, 0.f};
     uint64_t want_sel = 0, want_pairs = 0;
     // stage timing: ev[2s] / ev[2s+1] bracket stage s, for the stages in prof_mask

@@ -52,3 +52,29 @@ def test_captured_step_replays_for_a_new_camera():
         torch.cuda.synchronize()
         assert fr.stats()["status"] == 0
         assert torch.equal(img, ref[name]), name
+
+
+def test_split_backward_matches_the_combined_call():
+    from paper_2507_01110_b300 import api, build
+    build.build()
+    leaves = synth.leaves_uniform_cube(20000, seed=72, half_extent=15.0, degree=2)
+    cam = synth.camera_look([0.0, 0.0, -50.0], [0, 0, 1], [1, 0, 0], 160, 96)
+    scene = api.build_hierarchy(leaves, 2, 2.0, float(cam.fx))
+    fr = api.select_lod(scene, cam)
+    img = api.render(scene, fr)
+    dL = torch.rand_like(img) - 0.5
+    n = fr.stats()["n_selected"]
+    g1 = torch.zeros((n, scene.stride), device="cuda")
+    api.render_backward(scene, fr, dL, grad=g1)
+    g2 = torch.zeros_like(g1)
+    api.render_backward_blend(scene, fr, dL)
+    api.render_backward_project(scene, fr, g2)
+    torch.cuda.synchronize()
+    # per-Gaussian 2D gradients are summed across tiles with float atomics, so
+    # two backward passes agree up to summation order
+    scale = g1.abs().amax(dim=0, keepdim=True).clamp_min(1e-12)
+    assert ((g1 - g2).abs() / scale).max().item() < 1e-4
+    # the projection half refuses to run before a blend backward on a new render
+    api.render(scene, fr)
+    with pytest.raises(Exception):
+        api.render_backward_project(scene, fr, g2)
