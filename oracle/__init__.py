@@ -206,7 +206,7 @@ def project(scene: dict, sel: np.ndarray, cam) -> dict:
     vis = np.zeros(n, dtype=np.int32)
     rect = np.zeros((n, 4), dtype=np.int32)
     key = np.zeros(n, dtype=np.uint32)
-    f32 = np.zeros((n, 5), dtype=np.float32)
+    f32 = np.zeros((n, 7), dtype=np.float32)       # u, v, A, B, C, rx, ry
     f64 = np.zeros((n, 12), dtype=np.float64)
     camv = pack_camera(cam)
     lib().or_project(C.c_int64(n), _p(sel), C.c_int(scene["stride"]), C.c_int(scene["degree"]),
@@ -239,6 +239,24 @@ def tile_keep(u, v, ca, cb, cc, tx, ty) -> bool:
     """Tile support test D9 for one (Gaussian, tile); (ca, cb, cc) is the conic."""
     f = C.c_float
     return bool(lib().or_tile_keep(f(u), f(v), f(ca), f(cb), f(cc), C.c_int(int(tx)), C.c_int(int(ty))))
+
+
+def block_keep(g, px: int, py: int) -> bool:
+    """Block support test D10 for one (Gaussian, pixel); g = (u, v, A, B, C, rx, ry)."""
+    gv = np.ascontiguousarray(g, dtype=np.float32)
+    return bool(lib().or_block_keep(_p(gv), C.c_int(int(px)), C.c_int(int(py))))
+
+
+def support_extents(a: float, c: float, det: float) -> tuple:
+    """Float32 support half extents (rx, ry) of D10 from a 2D covariance (a, c) and its determinant."""
+    rx, ry = C.c_float(), C.c_float()
+    lib().or_support_extents(C.c_float(a), C.c_float(c), C.c_float(det), C.byref(rx), C.byref(ry))
+    return rx.value, ry.value
+
+
+def set_block_cull(on: bool) -> None:
+    """Switch the block test D10 of blend / blend_backward on (default) or off."""
+    lib().or_set_block_cull(C.c_int(int(bool(on))))
 
 
 def blend(proj: dict, pairs: dict, width: int, height: int, bg=(0.0, 0.0, 0.0), window=None) -> dict:

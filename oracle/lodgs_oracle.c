@@ -35,6 +35,9 @@
  *               nha = -0.5f*A, nhc = -0.5f*C, nb = -B ; support iff p >= -4.5f
  *   D9 tile     a (tile, Gaussian) pair is kept iff the support ellipse can
  *               reach a pixel centre of the tile: see tile_keep() below
+ *   D10 block   a pixel tests a Gaussian only if the Gaussian's support box
+ *               (half extents rx, ry from the 2D covariance, D7) reaches the
+ *               8x8 pixel block holding the pixel: see block_keep() below
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC
  */
@@ -50,6 +53,7 @@ enum { TILE = 16 };
 #define ALPHA_MAX 0.99
 #define DILATION 0.3
 #define SUPPORT_P (-4.5f)
+#define F32_N 7          /* float32 decision values per Gaussian: u, v, A, B, C, rx, ry */
 
 int or_stride(int degree) {
     int k = 14 + 3 * ((degree + 1) * (degree + 1) - 1);
@@ -625,7 +629,27 @@ typedef struct {
     int rect[4];          /* x0, y0, x1, y1 tile rectangle, exclusive max */
     uint32_t depth_key;
     float u, v, A, B, C;  /* float32 mean and conic (support test) */
+    float rx, ry;         /* float32 support half extents (block test D10) */
 } proj32_t;
+
+/* Support half extents (D10).  For the 2D covariance (a, b; b, c) the ellipse
+ * d^T Sigma^-1 d <= 2L reaches |dx| <= sqrt(2L a), |dy| <= sqrt(2L c).  The
+ * support test D8 is p >= -4.5, i.e. L = 4.5; L is raised to 4.51 plus 1e-5
+ * times kap = (a + c)^2 / det, an upper bound of the covariance's condition
+ * number, which covers the float32 rounding of the conic and of p (both grow
+ * with the conditioning).  Above kap = 1e5 the extents are infinite (no block
+ * is skipped). */
+void or_support_extents(float a, float c, float det, float *rx, float *ry) {
+    float tr = a + c;
+    float kap = (tr * tr) / det;
+    *rx = INFINITY;
+    *ry = INFINITY;
+    if (kap <= 1e5f) {
+        float l2 = 9.02f + 2e-5f * kap;
+        *rx = sqrtf(l2 * a);
+        *ry = sqrtf(l2 * c);
+    }
+}
 
 static void project_fp32(const cam_t *k, const float *r, proj32_t *o) {
     memset(o, 0, sizeof(*o));
@@ -685,6 +709,7 @@ static void project_fp32(const cam_t *k, const float *r, proj32_t *o) {
     o->rect[0] = (int)fx0; o->rect[1] = (int)fy0; o->rect[2] = (int)fx1; o->rect[3] = (int)fy1;
     if ((o->rect[2] - o->rect[0]) * (o->rect[3] - o->rect[1]) <= 0) return;
     o->u = u; o->v = v;
+    or_support_extents(a, c, det, &o->rx, &o->ry);
     uint32_t bits;
     memcpy(&bits, &tz, 4);
     o->depth_key = bits;
@@ -752,7 +777,7 @@ static void project_fp64(const cam_t *k, int degree, const float *r, proj64_t *o
 
 /* Per selected Gaussian i (rows sel[i] of row_rec): decisions (float32) and
  * values (float64).  vis/rect/key/u32.. are outputs of length n, rect 4n,
- * f32 5n (u, v, A, B, C), f64 12n (u, v, A, B, C, opacity, rgb[3], depth, -, -). */
+ * f32 7n (u, v, A, B, C, rx, ry), f64 12n (u, v, A, B, C, opacity, rgb[3], depth, -, -). */
 int or_project(int64_t n, const int64_t *sel, int stride, int degree, const float *row_rec, const float *cam,
                int32_t *vis, int32_t *rect, uint32_t *key, float *f32, double *f64) {
     cam_t k;
@@ -764,7 +789,8 @@ int or_project(int64_t n, const int64_t *sel, int stride, int degree, const floa
         vis[i] = p.visible;
         for (int a = 0; a < 4; ++a) rect[4 * i + a] = p.rect[a];
         key[i] = p.depth_key;
-        f32[5 * i + 0] = p.u; f32[5 * i + 1] = p.v; f32[5 * i + 2] = p.A; f32[5 * i + 3] = p.B; f32[5 * i + 4] = p.C;
+        float *o32 = f32 + F32_N * i;
+        o32[0] = p.u; o32[1] = p.v; o32[2] = p.A; o32[3] = p.B; o32[4] = p.C; o32[5] = p.rx; o32[6] = p.ry;
         double *o = f64 + 12 * i;
         memset(o, 0, sizeof(double) * 12);
         if (p.visible) {
@@ -827,7 +853,7 @@ int or_sort_pairs(int64_t n, const int32_t *vis, const int32_t *rect, const uint
     int64_t w = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (!vis[i]) continue;
-        const float *g = f32 + 5 * i;
+        const float *g = f32 + F32_N * i;
         for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ++ty)
             for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; ++tx) {
                 if (!or_tile_keep(g[0], g[1], g[2], g[3], g[4], tx, ty)) continue;
@@ -852,6 +878,21 @@ int or_sort_pairs(int64_t n, const int32_t *vis, const int32_t *rect, const uint
 /* that takes T below the bound is still blended and the pixel stops after    */
 /* it, so the neglected tail is at most 1e-4 times the largest colour.        */
 /* ------------------------------------------------------------------------- */
+/* Block support test D10 (float32, evaluated as written).  The image is cut
+ * into 8x8 pixel blocks (four per tile); block (bx0, by0) has pixel centres
+ * bx0 + 0.5 .. bx0 + 7.5 (same in y), centre bx0 + 4 and half span 3.5.  A
+ * pixel tests Gaussian g (u, v, rx, ry = g[0], g[1], g[5], g[6]) only if the
+ * support box |u - x| <= rx, |v - y| <= ry can reach a centre of its block. */
+static int g_block_cull = 1;
+
+void or_set_block_cull(int on) { g_block_cull = on; }
+
+int or_block_keep(const float *g, int px, int py) {
+    if (!g_block_cull) return 1;
+    float wcx = (float)(px & ~7) + 4.0f, wcy = (float)(py & ~7) + 4.0f;
+    return !(fabsf(g[0] - wcx) > g[5] + 3.5f || fabsf(g[1] - wcy) > g[6] + 3.5f);
+}
+
 static inline float support_p(float u, float v, float A, float B, float C, int px, int py) {
     float dx = u - ((float)px + 0.5f), dy = v - ((float)py + 0.5f);
     float nha = -0.5f * A, nhc = -0.5f * C, nb = -B;
@@ -871,7 +912,8 @@ int or_blend(int W, int H, const double *bg, const int64_t *tile_start, const in
             int32_t last = 0;
             for (int64_t e = tile_start[t]; e < tile_start[t + 1]; ++e) {
                 int64_t i = pair_i[e];
-                const float *g = f32 + 5 * i;
+                const float *g = f32 + F32_N * i;
+                if (!or_block_keep(g, px, py)) continue;
                 if (support_p(g[0], g[1], g[2], g[3], g[4], px, py) < SUPPORT_P) continue;
                 const double *q = f64 + 12 * i;
                 double dx = q[0] - (px + 0.5), dy = q[1] - (py + 0.5);
@@ -916,7 +958,8 @@ int or_blend_backward(int W, int H, const double *bg, const int64_t *tile_start,
             int64_t cnt = 0;
             for (int64_t e = tile_start[t]; e < tile_start[t + 1]; ++e) {
                 int64_t i = pair_i[e];
-                const float *g = f32 + 5 * i;
+                const float *g = f32 + F32_N * i;
+                if (!or_block_keep(g, px, py)) continue;
                 if (support_p(g[0], g[1], g[2], g[3], g[4], px, py) < SUPPORT_P) continue;
                 const double *q = f64 + 12 * i;
                 double dx = q[0] - (px + 0.5), dy = q[1] - (py + 0.5);

@@ -521,7 +521,7 @@ def test_sort_matches_lexsort_of_kept_pairs(oracle_lib, scene1):
     TX = pairs["TX"]
     tiles, keys, idx = _rect_pairs(pr, TX)
     f = pr["f32"]
-    keep = np.array([oracle_lib.tile_keep(*f[i], t % TX, t // TX) for t, i in zip(tiles, idx)])
+    keep = np.array([oracle_lib.tile_keep(*f[i][:5], t % TX, t // TX) for t, i in zip(tiles, idx)])
     assert 0 < keep.sum() < len(keep)
     tiles, keys, idx = tiles[keep], keys[keep], idx[keep]
     o = np.lexsort((idx, keys, tiles))
@@ -562,6 +562,93 @@ def test_tile_support_test_is_conservative(oracle_lib):
                         for px in range(16 * tx, 16 * tx + 16):
                             assert _support_f32(u, v, A, B, C, px, py) < np.float32(-4.5)
     assert kept > 100 and dropped > 100
+
+
+def _support_f32_grid(u, v, A, B, C, px, py):
+    """_support_f32 over integer pixel arrays (numpy float32 steps, fused steps in float64)."""
+    f32 = np.float32
+    dx = f32(u) - (px.astype(f32) + f32(0.5))
+    dy = f32(v) - (py.astype(f32) + f32(0.5))
+    nha, nhc, nb = f32(-0.5) * f32(A), f32(-0.5) * f32(C), -f32(B)
+    inner = ((nhc * dy).astype(np.float64) * dy.astype(np.float64) + ((nha * dx) * dx).astype(np.float64)).astype(f32)
+    return ((nb * dx).astype(np.float64) * dy.astype(np.float64) + inner.astype(np.float64)).astype(f32)
+
+
+def test_block_support_test_is_conservative(oracle_lib):
+    """Brute force over every pixel centre near the Gaussian: an 8x8 block that
+    D10 skips has no pixel passing the float32 support test D8, for random
+    anisotropic covariances up to condition numbers past the cut-off (1e5)."""
+    rng = np.random.default_rng(22)
+    f32 = np.float32
+    kept = skipped = 0
+    kaps = []
+    for it in range(160):
+        ang = rng.uniform(0, np.pi)
+        s1 = rng.choice([rng.uniform(0.3, 5.0), rng.uniform(5.0, 60.0), rng.uniform(60.0, 400.0)])
+        s2 = rng.uniform(0.05, 3.0)
+        c_, s_ = f32(np.cos(ang)), f32(np.sin(ang))
+        # covariance in float32 as the projection forms it: entries + 0.3 dilation
+        l1, l2 = f32(s1 * s1), f32(s2 * s2)
+        a = (c_ * c_) * l1 + (s_ * s_) * l2 + f32(0.3)
+        b = (c_ * s_) * l1 - (c_ * s_) * l2
+        c = (s_ * s_) * l1 + (c_ * c_) * l2 + f32(0.3)
+        det = a * c - b * b
+        if not det > 0:
+            continue
+        A, B, C = c / det, -b / det, a / det
+        rx, ry = oracle_lib.support_extents(a, c, det)
+        kaps.append(float((a + c) * (a + c) / det))
+        u, v = f32(rng.uniform(100, 108)), f32(rng.uniform(100, 108))
+        g = np.array([u, v, A, B, C, rx, ry], np.float32)
+        R = int(min(3.2 * s1 + 12, 700))
+        ys, xs = np.mgrid[max(0, 104 - R) & ~7:(104 + R) | 7, max(0, 104 - R) & ~7:(104 + R) | 7]
+        p = _support_f32_grid(u, v, A, B, C, xs, ys)
+        inside = p >= f32(-4.5)
+        assert inside.any()
+        for by in range(ys[0, 0], ys[-1, 0] + 1, 8):
+            for bx in range(xs[0, 0], xs[0, -1] + 1, 8):
+                k = oracle_lib.block_keep(g, bx, by)
+                kept += k
+                if not k:
+                    skipped += 1
+                    blk = inside[by - ys[0, 0]:by - ys[0, 0] + 8, bx - xs[0, 0]:bx - xs[0, 0] + 8]
+                    assert not blk.any(), (it, bx, by, s1, s2)
+    assert kept > 500 and skipped > 5000
+    assert max(kaps) > 1e5 and sum(1e3 < k < 1e5 for k in kaps) > 20
+
+
+def test_block_culling_leaves_image_and_gradients_unchanged(oracle_lib, scene1):
+    """Blend and its backward with and without D10 give the same image and
+    2D gradients, bit for bit, on a real view."""
+    cfg, sc = scene1
+    cam = cfg["cameras"][0]
+    sel, _ = oracle_lib.select(sc, cam)
+    pr = oracle_lib.project(sc, sel, cam)
+    pairs = oracle_lib.sort_pairs(pr, cam.width, cam.height)
+    rng = np.random.default_rng(5)
+    dL = rng.standard_normal((cam.height, cam.width, 3))
+    win = (0, 0, cam.width, min(cam.height, 48))
+    try:
+        oracle_lib.set_block_cull(False)
+        a = oracle_lib.blend(pr, pairs, cam.width, cam.height, bg=(0.2, 0.1, 0.3), window=win)
+        ga = oracle_lib.blend_backward(pr, pairs, cam.width, cam.height, dL, bg=(0.2, 0.1, 0.3), window=win)
+    finally:
+        oracle_lib.set_block_cull(True)
+    b = oracle_lib.blend(pr, pairs, cam.width, cam.height, bg=(0.2, 0.1, 0.3), window=win)
+    gb = oracle_lib.blend_backward(pr, pairs, cam.width, cam.height, dL, bg=(0.2, 0.1, 0.3), window=win)
+    assert np.array_equal(a["image"], b["image"]) and np.array_equal(a["n_contrib"], b["n_contrib"])
+    assert np.array_equal(ga, gb) and np.abs(ga).max() > 0
+    # the test is not vacuous: some (pixel, Gaussian) evaluations of the view are skipped
+    f = pr["f32"]
+    ts = pairs["tile_start"]
+    TX = pairs["TX"]
+    skips = 0
+    for t in range(0, min(len(ts) - 1, 3 * TX)):
+        for e in range(ts[t], ts[t + 1]):
+            gi = f[pairs["pair_i"][e]]
+            x0, y0 = (t % TX) * 16, (t // TX) * 16
+            skips += sum(not oracle_lib.block_keep(gi, x0 + 8 * i, y0 + 8 * j) for i in range(2) for j in range(2))
+    assert skips > 0
 
 
 def test_tile_culling_leaves_the_image_unchanged(oracle_lib, scene1):
