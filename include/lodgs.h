@@ -311,7 +311,9 @@ int lodgs_frame_stage_ms(lodgs_frame *frame, float *ms);
 
 /* Pixel-Gaussian work of the last render/backward on this frame (4 uint64):
  * [0] forward support tests evaluated, [1] forward blends (alpha composited),
- * [2] backward support tests (both passes), [3] backward contributions.
+ * [2] backward support tests, [3] backward contributions.  Tests skipped by
+ * the 8x8-block support test are not counted; [2] and [3] are 0 after a render
+ * until the backward runs.
  * Blocks until the frame's stream is idle. */
 int lodgs_frame_work(lodgs_frame *frame, uint64_t *work);
 
@@ -321,10 +323,12 @@ int lodgs_frame_work(lodgs_frame *frame, uint64_t *work);
  * idle.
  *   pair_index  n_pairs uint32: selected index of each (tile, depth)-sorted pair
  *   ranges      2 x n_tiles uint32: [start, end) of each tile's pairs
- *   splats      n_selected x 9 float32: u, v, A, B, C (conic of Eq. 2), opacity, r, g, b
+ *   splats      n_selected x LODGS_SPLAT_FLOATS float32: u, v, A, B, C (conic of Eq. 2),
+ *               opacity, r, g, b, rx, ry (support half extents of the 8x8-block test)
  *   depth_key   n_selected uint32: float32 bits of the view depth (0xffffffff if invisible)
  *   cap_pairs   capacity of pair_index in elements (LODGS_E_INVALID if too small)
  */
+#define LODGS_SPLAT_FLOATS 11
 int lodgs_frame_export(lodgs_frame *frame, uint32_t *pair_index, int64_t cap_pairs, uint32_t *ranges,
                        float *splats, uint32_t *depth_key);
 

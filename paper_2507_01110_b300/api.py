@@ -160,7 +160,7 @@ class Frame:
         n_tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
         pairs = np.zeros(max(st["n_pairs"], 1), np.uint32)
         ranges = np.zeros((n_tiles, 2), np.uint32)
-        spl = np.zeros((max(st["n_selected"], 1), 9), np.float32)
+        spl = np.zeros((max(st["n_selected"], 1), 11), np.float32)   # u v A B C opacity r g b rx ry
         keys = np.zeros(max(st["n_selected"], 1), np.uint32)
         check(lib().lodgs_frame_export(self._h, C.c_void_p(pairs.ctypes.data), C.c_int64(pairs.size),
                                        C.c_void_p(ranges.ctypes.data), C.c_void_p(spl.ctypes.data),

@@ -111,7 +111,7 @@ void free_frame_bufs(FrameBufs &f) {
     void *ps[] = {f.cnt, f.d_view, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
                   f.sort_hist, f.sp_a, f.sp_b, f.sp_c, f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.rect, f.ntiles,
                   f.nt_sorted, f.pair_off, f.g2d, f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.ranges, f.work,
-                  f.sel_src, f.emit_src};
+                  f.sel_src, f.emit_src, f.px_state};
     for (void *p : ps)
         if (p) cudaFree(p);
     f = FrameBufs();
@@ -268,6 +268,7 @@ void lodgs_frame_free(lodgs_frame *fr) {
 int lodgs_frame_set_view(lodgs_frame *fr, const lodgs_camera *cam, const float *bg, void *stream) {
     if (!fr) { set_error("frame_set_view: NULL frame"); return LODGS_E_INVALID; }
     if (cam && !camera_ok(cam)) { set_error("frame_set_view: invalid camera"); return LODGS_E_INVALID; }
+    if (cam) fr->rendered = fr->blend_bwd_done = false;   // the last render belongs to the old camera
     return set_view(fr, cam, bg, (cudaStream_t)stream);
 }
 
@@ -323,6 +324,9 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     uint64_t c = fr->f.cap_tiles;
     if (int r = grow(fr->f.ranges, c, n_tiles)) return r;
     fr->f.cap_tiles = c;
+    c = fr->f.cap_px;
+    if (int r = grow(fr->f.px_state, c, (uint64_t)fr->k.W * fr->k.H)) return r;
+    fr->f.cap_px = c;
     if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2]))
         if (int r = set_view(fr, nullptr, bg, st)) return r;
     // reset the render's counters and status (the selection's counters stay)
@@ -352,6 +356,10 @@ int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *d
         return LODGS_E_INVALID;
     }
     if (!fr->rendered) { set_error("render_backward: render was not called on this frame"); return LODGS_E_STATE; }
+    if ((uint64_t)fr->k.TX * fr->k.TY > fr->f.cap_tiles || (uint64_t)fr->k.W * fr->k.H > fr->f.cap_px) {
+        set_error("render_backward: the frame's camera is larger than the one it was rendered with");
+        return LODGS_E_STATE;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     if (st != fr->stream) {
         cudaEvent_t ev;
@@ -478,15 +486,14 @@ int lodgs_frame_export(lodgs_frame *fr, uint32_t *pair_index, int64_t cap_pairs,
     }
     if (ranges) LODGS_CUDA(cudaMemcpy(ranges, fr->f.ranges, nt * 8, cudaMemcpyDeviceToHost));
     if (splats && ns) {
-        std::vector<float4> a(ns), b(ns);
-        std::vector<float> c(ns);
+        std::vector<float4> a(ns), b(ns), c(ns);
         LODGS_CUDA(cudaMemcpy(a.data(), fr->f.sp_a, ns * 16, cudaMemcpyDeviceToHost));
         LODGS_CUDA(cudaMemcpy(b.data(), fr->f.sp_b, ns * 16, cudaMemcpyDeviceToHost));
-        LODGS_CUDA(cudaMemcpy(c.data(), fr->f.sp_c, ns * 4, cudaMemcpyDeviceToHost));
+        LODGS_CUDA(cudaMemcpy(c.data(), fr->f.sp_c, ns * 16, cudaMemcpyDeviceToHost));
         for (uint64_t i = 0; i < ns; ++i) {
-            float *o = splats + 9 * i;
+            float *o = splats + LODGS_SPLAT_FLOATS * i;
             o[0] = a[i].x; o[1] = a[i].y; o[2] = -2.0f * a[i].z; o[3] = -a[i].w; o[4] = -2.0f * b[i].x;
-            o[5] = b[i].y; o[6] = b[i].z; o[7] = b[i].w; o[8] = c[i];
+            o[5] = b[i].y; o[6] = b[i].z; o[7] = b[i].w; o[8] = c[i].x; o[9] = c[i].y; o[10] = c[i].z;
         }
     }
     if (depth_key && ns) {

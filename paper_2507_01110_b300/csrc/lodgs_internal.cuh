@@ -128,7 +128,7 @@ struct FrameBufs {
     // per selected node (capacity cap_sel)
     float4 *sp_a = nullptr;          // u, v, -A/2, -B        (mean in pixels, scaled conic)
     float4 *sp_b = nullptr;          // -C/2, opacity, r, g
-    float *sp_c = nullptr;           // b
+    float4 *sp_c = nullptr;          // b, rx, ry, 0   (rx, ry: support half extents, block test)
     uint32_t *dkey = nullptr, *dval = nullptr, *dkey_alt = nullptr, *dval_alt = nullptr;
     uint2 *rect = nullptr;           // x0 | y0 << 16, x1 | y1 << 16
     uint32_t *ntiles = nullptr, *nt_sorted = nullptr, *pair_off = nullptr;
@@ -137,8 +137,10 @@ struct FrameBufs {
     uint32_t *pkey = nullptr, *pval = nullptr, *pkey_alt = nullptr, *pval_alt = nullptr;
     // tiles (capacity cap_tiles)
     uint2 *ranges = nullptr;
+    // pixels (capacity cap_px): final transmittance bits and last contributor of the last render
+    uint2 *px_state = nullptr;
     unsigned long long *work = nullptr;   // 4 counters, see lodgs_frame_work
-    uint64_t cap_sel = 0, cap_pairs = 0, cap_tiles = 0;
+    uint64_t cap_sel = 0, cap_pairs = 0, cap_tiles = 0, cap_px = 0;
     // where the last render left its sorted data
     const uint32_t *order = nullptr;     // selected indices by depth
     const uint32_t *sorted_pval = nullptr;

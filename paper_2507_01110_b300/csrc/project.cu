@@ -130,11 +130,29 @@ __device__ __forceinline__ void geometry(const CamK &k, const float *mu, const f
     g.det = g.a * g.c - g.b * g.b;
 }
 
+// Support half extents for the 8x8-block test of the blend.  The ellipse
+// d^T Sigma^-1 d <= 2L of the 2D covariance (a, b; b, c) spans |dx| <= sqrt(2L a),
+// |dy| <= sqrt(2L c); the support test p >= -4.5 is L = 4.5, raised to 4.51 +
+// 1e-5 kap, kap = (a + c)^2 / det >= the condition number, to cover the float32
+// rounding of the conic and of p, which grows with the conditioning.  Beyond
+// kap = 1e5 the extents are infinite (no block is ever skipped).
+__device__ __forceinline__ void support_extents(float a, float c, float det, float &rx, float &ry) {
+    const float tr = a + c;
+    const float kap = (tr * tr) / det;
+    rx = INFINITY;
+    ry = INFINITY;
+    if (kap <= 1e5f) {
+        const float l2 = 9.02f + 2e-5f * kap;
+        rx = sqrtf(l2 * a);
+        ry = sqrtf(l2 * c);
+    }
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, int stride,
                                                  const uint32_t *__restrict__ sel_rows, const View *__restrict__ view,
                                                  uint32_t *__restrict__ cnt, uint64_t cap_sel, float4 *__restrict__ sp_a,
-                                                 float4 *__restrict__ sp_b, float *__restrict__ sp_c,
+                                                 float4 *__restrict__ sp_b, float4 *__restrict__ sp_c,
                                                  uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
                                                  uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles) {
     const CamK &k = view->k;
@@ -159,8 +177,7 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
         bool vis = false;
         uint32_t key = 0xffffffffu, nt = 0;
         uint2 rc = make_uint2(0, 0);
-        float4 a = make_float4(0, 0, 0, 0), b = make_float4(0, 0, 0, 0);
-        float cb = 0.f;
+        float4 a = make_float4(0, 0, 0, 0), b = make_float4(0, 0, 0, 0), c4 = make_float4(0, 0, 0, 0);
         float tz;
         {
             float t[3], dist;
@@ -207,12 +224,14 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
                         }
                         a = make_float4(u, v, -0.5f * A, -B);
                         b = make_float4(-0.5f * C, op, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
-                        cb = fmaxf(col[2], 0.f);
+                        float rx, ry;
+                        support_extents(g.a, g.c, g.det, rx, ry);
+                        c4 = make_float4(fmaxf(col[2], 0.f), rx, ry, 0.f);
                     }
                 }
             }
         }
-        sp_a[i] = a; sp_b[i] = b; sp_c[i] = cb;
+        sp_a[i] = a; sp_b[i] = b; sp_c[i] = c4;
         dkey[i] = key; dval[i] = i;
         rect[i] = rc; ntiles[i] = nt;
         nvis += vis ? 1u : 0u;

@@ -8,15 +8,16 @@
 // index) order of a full-key sort at a fraction of its passes, because pairs
 // outnumber Gaussians.
 //
-// Blending runs one 256-thread CTA per 16x16 tile; batches of the tile's
+// Blending runs one 128-thread CTA per 16x16 tile; batches of the tile's
 // Gaussians are staged in shared memory.  Eq. 1 is truncated once a pixel's
 // transmittance falls below 1e-4 (the Gaussian that crosses the bound is still
 // blended), so the neglected tail is at most 1e-4 of the colour.  The support test p >= -4.5 uses
 // explicitly rounded float32 operations (it decides which pixels a Gaussian
 // touches); the alpha, transmittance and colour arithmetic are ordinary fp32.
-// The backward recomputes each pixel's final transmittance and last
-// contributor from the sorted list (nothing per pixel is stored by the forward)
-// and then walks the list back to front.
+// The forward saves each pixel's final transmittance and last contributor;
+// the backward walks the list back to front from them.  Within a tile each
+// warp owns an 8x8 pixel block and skips the Gaussians whose support box
+// misses it (block test, conservative like the tile test).
 #include "lodgs_internal.cuh"
 
 namespace lodgs {
@@ -164,244 +165,250 @@ __device__ __forceinline__ void warp_sum9_to_smem(float v[9], int lane, float *d
     if (lane == 1) atomicAdd(dst + 8, s8);
 }
 
-// Each thread owns PIX pixels of one column of the 16x16 tile (rows r, r + 16/PIX, ...),
-// so per staged Gaussian it reuses dx and the shared shared-memory loads PIX times.
-template <int PIX>
-__global__ void __launch_bounds__(TILE_PIX / PIX) k_blend(const uint2 *__restrict__ ranges,
-                                                          const uint32_t *__restrict__ pval,
-                                                          const float4 *__restrict__ sp_a,
-                                                          const float4 *__restrict__ sp_b,
-                                                          const float *__restrict__ sp_c,
-                                                          const uint32_t *__restrict__ cnt, int W, int H, int TX,
-                                                          const View *__restrict__ view, float *__restrict__ image,
-                                                          unsigned long long *__restrict__ work) {
-    const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
-    constexpr int NT = TILE_PIX / PIX, RS = TILE / PIX;
-    uint32_t n_eval = 0, n_blend = 0;
-    __shared__ float4 s_a[BATCH], s_b[BATCH];
-    __shared__ float s_c[BATCH];
-    if (cnt[C_STATUS] & ST_CAPACITY) return;
-    const int tile = blockIdx.x, tid = threadIdx.x;
-    const int px = (tile % TX) * TILE + (tid & 15), py0 = (tile / TX) * TILE + (tid >> 4);
-    const float xc = (float)px + 0.5f;
-    float yc[PIX], T[PIX], c0[PIX], c1[PIX], c2[PIX];
-    bool live[PIX];
-    bool done = true;
-#pragma unroll
-    for (int k = 0; k < PIX; ++k) {
-        int py = py0 + k * RS;
-        yc[k] = (float)py + 0.5f;
-        T[k] = 1.0f; c0[k] = c1[k] = c2[k] = 0.f;
-        live[k] = px < W && py < H;
-        done &= !live[k];
-    }
-    const uint2 rg = ranges[tile];
-    for (uint32_t base = rg.x; base < rg.y; base += BATCH) {
-        if (__syncthreads_count(done) == NT) break;
-        for (int q = tid; q < BATCH; q += NT) {
-            uint32_t idx = base + q;
-            if (idx < rg.y) {
-                uint32_t g = pval[idx];
-                s_a[q] = sp_a[g];
-                s_b[q] = sp_b[g];
-                s_c[q] = sp_c[g];
-            }
-        }
-        __syncthreads();
-        const int n = min((uint32_t)BATCH, rg.y - base);
-        for (int j = 0; j < n && !done; ++j) {
-            const float4 a = s_a[j];
-            const float4 b = s_b[j];
-            const float cb = s_c[j];
-            const float dx = __fsub_rn(a.x, xc);
-            const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
-            done = true;
-#pragma unroll
-            for (int k = 0; k < PIX; ++k) {
-                if (live[k]) {
-                    const float dy = __fsub_rn(a.y, yc[k]);
-                    const float p = __fmaf_rn(bx, dy, __fmaf_rn(__fmul_rn(b.x, dy), dy, hxx));
-                    ++n_eval;
-                    if (p >= SUPPORT_P) {
-                        ++n_blend;
-                        const float alpha = fminf(ALPHA_MAX, b.y * __expf(p));
-                        const float w = alpha * T[k];
-                        c0[k] += b.z * w; c1[k] += b.w * w; c2[k] += cb * w;
-                        T[k] = T[k] * (1.0f - alpha);
-                        if (T[k] < T_MIN) live[k] = false;
-                    }
-                }
-                done &= !live[k];
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < PIX; ++k) {
-        int py = py0 + k * RS;
-        if (px < W && py < H) {
-            float *o = image + ((size_t)py * W + px) * 3;
-            o[0] = c0[k] + T[k] * bg0; o[1] = c1[k] + T[k] * bg1; o[2] = c2[k] + T[k] * bg2;
-        }
-    }
-    add_work(work, n_eval, n_blend);
+// Warp-block layout of a 16x16 tile (128 threads, 2 pixels each): warp w owns
+// the 8x8 pixel block at ((w & 1) * 8, (w >> 1) * 8) of the tile, lane l the
+// pixels (l & 7, (l >> 3) + 4k), k = 0, 1.  Each warp skips a staged Gaussian
+// whose support box (half extents rx, ry) misses its block's pixel centres
+// (the block test is warp-uniform, so the warp branches as a whole), and
+// skips the blend body when no lane's pixel passes the support test.
+constexpr int PIX = 2;
+constexpr int BNT = TILE_PIX / PIX;
+constexpr float BLOCK_HALF = 3.5f;     // half span of an 8x8 block's pixel centres
+
+struct BlockPix {
+    int px, py0;          // this lane's column and first row
+    float xc, wcx, wcy;   // pixel-centre x, block centre
+};
+
+__device__ __forceinline__ BlockPix block_pix(int tile, int TX, int tid) {
+    const int w = tid >> 5, lane = tid & 31;
+    const int bx0 = (tile % TX) * TILE + (w & 1) * 8, by0 = (tile / TX) * TILE + (w >> 1) * 8;
+    BlockPix b;
+    b.px = bx0 + (lane & 7);
+    b.py0 = by0 + (lane >> 3);
+    b.xc = (float)b.px + 0.5f;
+    b.wcx = (float)bx0 + 4.0f;
+    b.wcy = (float)by0 + 4.0f;
+    return b;
 }
 
-template <int PIX>
-__global__ void __launch_bounds__(TILE_PIX / PIX) k_blend_bwd(const uint2 *__restrict__ ranges,
-                                                              const uint32_t *__restrict__ pval,
-                                                              const float4 *__restrict__ sp_a,
-                                                              const float4 *__restrict__ sp_b,
-                                                              const float *__restrict__ sp_c,
-                                                              const uint32_t *__restrict__ cnt, int W, int H, int TX,
-                                                              const View *__restrict__ view,
-                                                              const float *__restrict__ dL_dimg,
-                                                              float *__restrict__ g2d,
-                                                              unsigned long long *__restrict__ work) {
-    constexpr int NT = TILE_PIX / PIX, RS = TILE / PIX;
-    const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
-    uint32_t n_eval = 0, n_contrib = 0;
-    __shared__ float4 s_a[BATCH], s_b[BATCH];
-    __shared__ float s_c[BATCH];
-    __shared__ uint32_t s_g[BATCH];
-    __shared__ float s_grad[BATCH][9];
-    __shared__ uint32_t s_maxlast;
+// True when the support box of a staged Gaussian (mean a.x, a.y; half extents
+// c.y, c.z) cannot reach this warp's block.
+__device__ __forceinline__ bool block_skip(const BlockPix &bp, const float4 &a, const float4 &c) {
+    return fabsf(__fsub_rn(a.x, bp.wcx)) > __fadd_rn(c.y, BLOCK_HALF) ||
+           fabsf(__fsub_rn(a.y, bp.wcy)) > __fadd_rn(c.z, BLOCK_HALF);
+}
+
+__global__ void __launch_bounds__(BNT) k_blend(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
+                                               const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
+                                               const float4 *__restrict__ sp_c, const uint32_t *__restrict__ cnt,
+                                               int W, int H, int TX, const View *__restrict__ view,
+                                               float *__restrict__ image, uint2 *__restrict__ px_state,
+                                               unsigned long long *__restrict__ work) {
+    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
     if (cnt[C_STATUS] & ST_CAPACITY) return;
-    const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
-    const int px = (tile % TX) * TILE + (tid & 15), py0 = (tile / TX) * TILE + (tid >> 4);
-    const float xc = (float)px + 0.5f;
-    float yc[PIX], T[PIX];
+    const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
+    const int tile = blockIdx.x, tid = threadIdx.x;
+    const BlockPix bp = block_pix(tile, TX, tid);
+    float yc[PIX], T[PIX], c0[PIX], c1[PIX], c2[PIX];
     uint32_t last[PIX];
     bool live[PIX];
     bool done = true;
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
-        int py = py0 + k * RS;
+        const int py = bp.py0 + 4 * k;
         yc[k] = (float)py + 0.5f;
-        T[k] = 1.0f; last[k] = 0;
-        live[k] = px < W && py < H;
+        T[k] = 1.0f; c0[k] = c1[k] = c2[k] = 0.f; last[k] = 0;
+        live[k] = bp.px < W && py < H;
         done &= !live[k];
     }
+    uint32_t n_eval = 0, n_blend = 0;
     const uint2 rg = ranges[tile];
-    if (tid == 0) s_maxlast = 0;
-    // ---- pass 1: each pixel's final transmittance and last contributor ----
     for (uint32_t base = rg.x; base < rg.y; base += BATCH) {
-        if (__syncthreads_count(done) == NT) break;
-        for (int q = tid; q < BATCH; q += NT) {
-            uint32_t idx = base + q;
+        if (__syncthreads_count(done) == BNT) break;
+        for (int q = tid; q < BATCH; q += BNT) {
+            const uint32_t idx = base + q;
             if (idx < rg.y) {
-                uint32_t g = pval[idx];
-                s_a[q] = sp_a[g];
-                s_b[q] = sp_b[g];
-            }
-        }
-        __syncthreads();
-        const int n = min((uint32_t)BATCH, rg.y - base);
-        for (int j = 0; j < n && !done; ++j) {
-            const float4 a = s_a[j];
-            const float4 b = s_b[j];
-            const float dx = __fsub_rn(a.x, xc);
-            const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
-            done = true;
-#pragma unroll
-            for (int k = 0; k < PIX; ++k) {
-                if (live[k]) {
-                    const float dy = __fsub_rn(a.y, yc[k]);
-                    const float p = __fmaf_rn(bx, dy, __fmaf_rn(__fmul_rn(b.x, dy), dy, hxx));
-                    ++n_eval;
-                    if (p >= SUPPORT_P) {
-                        const float alpha = fminf(ALPHA_MAX, b.y * __expf(p));
-                        T[k] = T[k] * (1.0f - alpha);
-                        last[k] = base - rg.x + j + 1;
-                        if (T[k] < T_MIN) live[k] = false;
-                    }
-                }
-                done &= !live[k];
-            }
-        }
-    }
-    __syncthreads();
-    {
-        uint32_t m = 0;
-#pragma unroll
-        for (int k = 0; k < PIX; ++k) m = max(m, last[k]);
-        if (m) atomicMax(&s_maxlast, m);
-    }
-    __syncthreads();
-    const uint32_t end = rg.x + s_maxlast;
-    // ---- pass 2: back to front ----
-    float G[PIX][3], Q[PIX][3];
-#pragma unroll
-    for (int k = 0; k < PIX; ++k) {
-        int py = py0 + k * RS;
-        G[k][0] = G[k][1] = G[k][2] = 0.f;
-        if (px < W && py < H) {
-            const float *gi = dL_dimg + ((size_t)py * W + px) * 3;
-            G[k][0] = gi[0]; G[k][1] = gi[1]; G[k][2] = gi[2];
-        }
-        Q[k][0] = bg0; Q[k][1] = bg1; Q[k][2] = bg2;   // colour behind / transmittance in front of it
-    }
-    for (uint32_t bend = end; bend > rg.x;) {
-        const uint32_t bstart = bend - rg.x > (uint32_t)BATCH ? bend - BATCH : rg.x;
-        const int n = (int)(bend - bstart);
-        __syncthreads();
-        for (int q = tid; q < BATCH; q += NT) {
-            if (q < n) {
-                uint32_t g = pval[bstart + q];
-                s_g[q] = g;
+                const uint32_t g = pval[idx];
                 s_a[q] = sp_a[g];
                 s_b[q] = sp_b[g];
                 s_c[q] = sp_c[g];
             }
+        }
+        __syncthreads();
+        const int n = min((uint32_t)BATCH, rg.y - base);
+        if (__all_sync(0xffffffffu, done)) continue;
+        for (int j = 0; j < n; ++j) {
+            const float4 a = s_a[j];
+            const float4 c = s_c[j];
+            if (block_skip(bp, a, c)) continue;
+            const float4 b = s_b[j];
+            const float dx = __fsub_rn(a.x, bp.xc);
+            const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
+            float p[PIX];
+            bool hit[PIX], any = false;
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                const float dy = __fsub_rn(a.y, yc[k]);
+                p[k] = __fmaf_rn(bx, dy, __fmaf_rn(__fmul_rn(b.x, dy), dy, hxx));
+                hit[k] = live[k] && p[k] >= SUPPORT_P;
+                any |= hit[k];
+            }
+            n_eval += PIX;
+            if (!__any_sync(0xffffffffu, any)) continue;
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                if (hit[k]) {
+                    ++n_blend;
+                    const float alpha = fminf(ALPHA_MAX, b.y * __expf(p[k]));
+                    const float w = alpha * T[k];
+                    c0[k] += b.z * w; c1[k] += b.w * w; c2[k] += c.x * w;
+                    T[k] = T[k] * (1.0f - alpha);
+                    last[k] = base - rg.x + j + 1;
+                    if (T[k] < T_MIN) live[k] = false;
+                }
+            }
+            done = true;
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) done &= !live[k];
+            if (__all_sync(0xffffffffu, done)) break;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        const int py = bp.py0 + 4 * k;
+        if (bp.px < W && py < H) {
+            const size_t o = (size_t)py * W + bp.px;
+            float *img = image + o * 3;
+            img[0] = c0[k] + T[k] * bg0; img[1] = c1[k] + T[k] * bg1; img[2] = c2[k] + T[k] * bg2;
+            px_state[o] = make_uint2(__float_as_uint(T[k]), last[k]);
+        }
+    }
+    add_work(work, n_eval, n_blend);
+}
+
+// Backward of the blend, one pass back to front over each tile's list, from the
+// final transmittance and last contributor the forward saved per pixel.  Per
+// pixel and contributing Gaussian i (front-to-back transmittance T_i, colour Q
+// composited behind it, background included, dL/dC = G):
+//   dL/dc_i = G alpha_i T_i,   dL/dalpha_i = T_i G . (c_i - Q),
+// then Q <- Q + alpha_i (c_i - Q) and T_i = T_{i+1} / (1 - alpha_i).  The nine
+// per-Gaussian sums of a warp are reduced in registers and added to shared
+// memory; each batch's sums go to global memory with one atomic per value.
+__global__ void __launch_bounds__(BNT) k_blend_bwd(const uint2 *__restrict__ ranges,
+                                                   const uint32_t *__restrict__ pval,
+                                                   const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
+                                                   const float4 *__restrict__ sp_c,
+                                                   const uint32_t *__restrict__ cnt, int W, int H, int TX,
+                                                   const View *__restrict__ view,
+                                                   const uint2 *__restrict__ px_state,
+                                                   const float *__restrict__ dL_dimg, float *__restrict__ g2d,
+                                                   unsigned long long *__restrict__ work) {
+    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    __shared__ uint32_t s_g[BATCH];
+    __shared__ float s_grad[BATCH][9];
+    __shared__ uint32_t s_end;
+    if (cnt[C_STATUS] & ST_CAPACITY) return;
+    const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
+    const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const BlockPix bp = block_pix(tile, TX, tid);
+    float yc[PIX], T[PIX], G[PIX][3], Q[PIX][3];
+    uint32_t last[PIX];
+    uint32_t wend = 0;
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        const int py = bp.py0 + 4 * k;
+        yc[k] = (float)py + 0.5f;
+        T[k] = 1.0f; last[k] = 0;
+        G[k][0] = G[k][1] = G[k][2] = 0.f;
+        if (bp.px < W && py < H) {
+            const size_t o = (size_t)py * W + bp.px;
+            const uint2 st = px_state[o];
+            T[k] = __uint_as_float(st.x);
+            last[k] = st.y;
+            const float *gi = dL_dimg + o * 3;
+            G[k][0] = gi[0]; G[k][1] = gi[1]; G[k][2] = gi[2];
+        }
+        Q[k][0] = bg0; Q[k][1] = bg1; Q[k][2] = bg2;
+        wend = max(wend, last[k]);
+    }
+    wend = __reduce_max_sync(0xffffffffu, wend);        // this warp's list end
+    if (tid == 0) s_end = 0;
+    __syncthreads();
+    if (lane == 0 && wend) atomicMax(&s_end, wend);
+    __syncthreads();
+    const uint2 rg = ranges[tile];
+    const uint32_t end = rg.x + s_end;
+    uint32_t n_eval = 0, n_contrib = 0;
+    for (uint32_t bend = end; bend > rg.x;) {
+        const uint32_t bstart = bend - rg.x > (uint32_t)BATCH ? bend - BATCH : rg.x;
+        const int n = (int)(bend - bstart);
+        __syncthreads();
+        for (int q = tid; q < n; q += BNT) {
+            const uint32_t g = pval[bstart + q];
+            s_g[q] = g;
+            s_a[q] = sp_a[g];
+            s_b[q] = sp_b[g];
+            s_c[q] = sp_c[g];
 #pragma unroll
             for (int c = 0; c < 9; ++c) s_grad[q][c] = 0.f;
         }
         __syncthreads();
-        for (int j = n - 1; j >= 0; --j) {
-            const uint32_t pos = bstart - rg.x + (uint32_t)j;
+        const uint32_t rel = bstart - rg.x;
+        const int jtop = min(n, (int)wend - (int)rel);
+        for (int j = jtop - 1; j >= 0; --j) {
             const float4 a = s_a[j];
+            const float4 c = s_c[j];
+            if (block_skip(bp, a, c)) continue;
             const float4 b = s_b[j];
-            const float cb = s_c[j];
-            const float dx = __fsub_rn(a.x, xc);
+            const uint32_t pos = rel + (uint32_t)j;
+            const float dx = __fsub_rn(a.x, bp.xc);
             const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
-            float gv[9];
-#pragma unroll
-            for (int c = 0; c < 9; ++c) gv[c] = 0.f;
-            bool any = false;
+            float p[PIX], dyk[PIX];
+            bool hit[PIX], any = false;
 #pragma unroll
             for (int k = 0; k < PIX; ++k) {
-                const float dy = __fsub_rn(a.y, yc[k]);
-                const float p = __fmaf_rn(bx, dy, __fmaf_rn(__fmul_rn(b.x, dy), dy, hxx));
-                n_eval += pos < last[k];
-                if (pos < last[k] && p >= SUPPORT_P) {
-                    any = true;
+                dyk[k] = __fsub_rn(a.y, yc[k]);
+                p[k] = __fmaf_rn(bx, dyk[k], __fmaf_rn(__fmul_rn(b.x, dyk[k]), dyk[k], hxx));
+                hit[k] = pos < last[k] && p[k] >= SUPPORT_P;
+                any |= hit[k];
+            }
+            n_eval += PIX;
+            if (!__any_sync(0xffffffffu, any)) continue;
+            const float ax2 = 2.0f * a.z * dx, cy2 = 2.0f * b.x, hdx2 = -0.5f * dx * dx;
+            float gv[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) gv[q] = 0.f;
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                if (hit[k]) {
                     ++n_contrib;
-                    const float e = __expf(p);
+                    const float dy = dyk[k];
+                    const float e = __expf(p[k]);
                     const float raw = b.y * e;
                     const float alpha = fminf(ALPHA_MAX, raw);
                     const float Tb = __fdividef(T[k], 1.0f - alpha);
-                    float dA = G[k][0] * (b.z - Q[k][0]) + G[k][1] * (b.w - Q[k][1]) + G[k][2] * (cb - Q[k][2]);
-                    dA *= Tb;
+                    const float d0 = b.z - Q[k][0], d1 = b.w - Q[k][1], d2 = c.x - Q[k][2];
+                    const float dA = (G[k][0] * d0 + G[k][1] * d1 + G[k][2] * d2) * Tb;
                     const float wgt = alpha * Tb;
                     gv[6] += G[k][0] * wgt; gv[7] += G[k][1] * wgt; gv[8] += G[k][2] * wgt;
-                    Q[k][0] = alpha * b.z + (1.0f - alpha) * Q[k][0];
-                    Q[k][1] = alpha * b.w + (1.0f - alpha) * Q[k][1];
-                    Q[k][2] = alpha * cb + (1.0f - alpha) * Q[k][2];
+                    Q[k][0] += alpha * d0; Q[k][1] += alpha * d1; Q[k][2] += alpha * d2;
                     T[k] = Tb;
                     if (raw <= ALPHA_MAX) {
                         const float dp = dA * alpha;
                         gv[5] += dA * e;
-                        gv[0] += dp * (2.0f * a.z * dx + a.w * dy);
-                        gv[1] += dp * (2.0f * b.x * dy + a.w * dx);
-                        gv[2] += -0.5f * dp * dx * dx;
-                        gv[3] += -dp * dx * dy;
+                        gv[0] += dp * (ax2 + a.w * dy);
+                        gv[1] += dp * (cy2 * dy + bx);
+                        gv[2] += dp * hdx2;
+                        gv[3] -= dp * dx * dy;
                         gv[4] += -0.5f * dp * dy * dy;
                     }
                 }
             }
-            if (__ballot_sync(0xffffffffu, any)) warp_sum9_to_smem(gv, lane, s_grad[j]);
+            warp_sum9_to_smem(gv, lane, s_grad[j]);
         }
         __syncthreads();
-        for (int q = tid; q < n; q += NT) {
+        for (int q = tid; q < n; q += BNT) {
             float *o = g2d + (size_t)s_g[q] * 9;
 #pragma unroll
             for (int c = 0; c < 9; ++c) {
@@ -413,16 +420,6 @@ __global__ void __launch_bounds__(TILE_PIX / PIX) k_blend_bwd(const uint2 *__res
     }
     add_work(work + 2, n_eval, n_contrib);
 }
-
-// pixels per thread of the forward and backward blends (compile-time tuning)
-#ifndef LODGS_FWD_PIX
-#define LODGS_FWD_PIX 2
-#endif
-#ifndef LODGS_BWD_PIX
-#define LODGS_BWD_PIX 2
-#endif
-constexpr int FWD_PIX = LODGS_FWD_PIX;
-constexpr int BWD_PIX = LODGS_BWD_PIX;
 
 int ceil_log2(uint64_t x) {
     int b = 0;
@@ -459,11 +456,11 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
     sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
     sm.mark(LODGS_STAGE_BLEND, 0, st);
     LODGS_CUDA(cudaMemsetAsync(f.ranges, 0, n_tiles * sizeof(uint2), st));
-    LODGS_CUDA(cudaMemsetAsync(f.work, 0, 2 * sizeof(unsigned long long), st));
+    LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));
     k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, (uint32_t)n_tiles, f.ranges);
     count_launches(1);
-    k_blend<FWD_PIX><<<(unsigned)n_tiles, TILE_PIX / FWD_PIX, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX,
-                                              f.d_view, image, f.work);
+    k_blend<<<(unsigned)n_tiles, BNT, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H,
+                                               k.TX, f.d_view, image, f.px_state, f.work);
     count_launches(1);
     sm.mark(LODGS_STAGE_BLEND, 1, st);
     LODGS_CUDA(cudaGetLastError());
@@ -474,8 +471,8 @@ int launch_raster_backward(const CamK &k, FrameBufs &f, const float *dL_dimage, 
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * 9 * sizeof(float), st));
     LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
-    k_blend_bwd<BWD_PIX><<<(unsigned)n_tiles, TILE_PIX / BWD_PIX, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H,
-                                                  k.TX, f.d_view, dL_dimage, f.g2d, f.work);
+    k_blend_bwd<<<(unsigned)n_tiles, BNT, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W,
+                                                   k.H, k.TX, f.d_view, f.px_state, dL_dimage, f.g2d, f.work);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
