@@ -190,9 +190,7 @@ def run_lodgs(args, rank: int, world: int):
     H, W = cams[0].height, cams[0].width
     # views of this rank (independent units: no exchange between ranks)
     my_views = [v for v in range(nv) if v % world == rank] or [rank % nv]
-    frames = {v: api.Frame(scene) for v in my_views}
-    for fr in frames.values():
-        fr.set_profiling(True)
+    frames = {v: api.Frame(scene) for v in my_views}     # profiling off: nothing extra in the timed graphs
     gen = torch.Generator().manual_seed(1234)
     targets_h = {v: torch.rand((H, W, 3), generator=gen).pin_memory() for v in my_views}
     targets_d = {v: t.cuda() for v, t in targets_h.items()}
@@ -293,12 +291,7 @@ def run_lodgs(args, rank: int, world: int):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     bwd_ms = [a.elapsed_time(b2) for a, b2 in zip(ev_a, ev_b)]
-    stats_ok = True
-    work = {}
-    for v in set(order):
-        fr = frames[v]
-        work[v] = fr.work()
-        stats_ok &= fr.stats()["status"] == 0
+    stats_ok = all(frames[v].stats()["status"] == 0 for v in set(order))
     # kernels per step: counted on an eager step (graph replays launch the same kernels)
     l0 = _lib.lib().lodgs_kernel_launches()
     step(order[0], targets_d[order[0]], cams[order[0]])
@@ -313,10 +306,12 @@ def run_lodgs(args, rank: int, world: int):
     for v in order:
         step(v, targets_d[v], cams[v])
     torch.cuda.synchronize()
+    work = {}
     for v in set(order):
         t = frames[v].stage_ms()
         for s in _lib.STAGES:
             stage_ms[s].append(t[s])
+        work[v] = frames[v].work()          # pixel-Gaussian work, tallied by the profiling launches
     stage_mean = {s: float(np.mean(x)) for s, x in stage_ms.items()}
     stage_mean_live = dict(stage_mean)
     stage_mean_live["blend_bwd"] = float(np.mean(bwd_ms))
@@ -372,20 +367,25 @@ def run_lodgs(args, rank: int, world: int):
     return res, cfg
 
 
-# FP32-pipe instructions per unit of blend work, counted from the kernel source
-# (support test: 2 sub/mul + 2 fma + compare; blend: exp, alpha, T, 3 colour fma;
-# backward contribution: exp, alpha, division, colour/alpha/conic/mean terms,
-# running sums).  Used only to express blend throughput against the FP32 peak.
-OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB, OPS_BWD_PASS1_BLEND = 5, 11, 45, 8
+# Algorithmic instructions per (pixel, Gaussian) contribution, counted from the
+# method's arithmetic: the support test (2 sub, mul, 2 fma, compare) plus, for
+# the forward, exp (2), opacity product, clamp, weight, 3 colour fma, 1 - alpha,
+# transmittance product, stop test (11); for the backward, exp (2), opacity
+# product, clamp, division (2), 1 - alpha, 3 colour differences, dot product (3),
+# T scale, weight, 3 colour-gradient fma, 3 Q updates, clamp test, dL/dp,
+# opacity fma, mean (4), conic (6) = 34.  Support tests of pixels a Gaussian does
+# not reach and the per-Gaussian warp sums are not counted: they are the
+# implementation's, not the method's.  Counts are issue slots: 128 per SM and
+# clock is the issue peak for any instruction type.
+OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB = 6, 11, 34
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 
 def alu_ops(stage: str, work: dict) -> float:
     if stage == "blend":
-        return OPS_EVAL * work["fwd_eval"] + OPS_BLEND * work["fwd_blend"]
+        return (OPS_EVAL + OPS_BLEND) * work["fwd_blend"]
     if stage == "blend_bwd":
-        return OPS_EVAL * work["bwd_eval"] + OPS_BWD_CONTRIB * work["bwd_contrib"] + \
-            OPS_BWD_PASS1_BLEND * work["fwd_blend"]
+        return (OPS_EVAL + OPS_BWD_CONTRIB) * work["bwd_contrib"]
     return 0.0
 
 
@@ -402,7 +402,7 @@ def roofline(res: dict, peaks: dict) -> dict:
     wk = {k: float(np.mean([w[k] for w in res["work"].values()])) for k in ("fwd_eval", "fwd_blend", "bwd_eval",
                                                                            "bwd_contrib")}
     mhz = res["clocks"].get("sm_mhz") or 2032.0
-    alu_peak = N_SM * FP32_LANES_PER_SM * mhz * 1e6 / 1e12      # T FP32 instructions / s
+    alu_peak = N_SM * FP32_LANES_PER_SM * mhz * 1e6 / 1e12      # T thread-instructions / s (issue peak)
     per_stage = {}
     for s in _lib.STAGES:
         t = st_mean[s] * 1e-3
@@ -669,9 +669,12 @@ def main():
                             "peak_source": peaks["source"] + " (MEASURED_PEAKS hbm_gbs)"}
     else:
         line["roofline"] = {"bound": "alu", "kernel": dom, "achieved": ds.get("tinst_s"), "peak": rf["alu_peak"],
-                            "unit": "T FP32 inst/s", "frac": ds.get("frac_alu"), "traffic": None,
-                            "peak_source": f"148 SMs x 128 FP32 lanes x {rf['mhz']:.0f} MHz (median SM clock "
-                                           "in the timed region)", "work_per_view": rf["work"]}
+                            "unit": "T inst/s", "frac": ds.get("frac_alu"), "traffic": None,
+                            "peak_source": f"148 SMs x 128 issue lanes x {rf['mhz']:.0f} MHz (median SM clock "
+                                           "in the timed region)",
+                            "work": f"algorithmic instructions = {OPS_EVAL + OPS_BWD_CONTRIB} per backward "
+                                    f"contribution ({OPS_EVAL + OPS_BLEND} per forward blend)",
+                            "work_per_view": rf["work"]}
     line["roofline_stages"] = {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in rf["stages"].items()}
     def section(name, fn):
         try:

@@ -313,7 +313,8 @@ int lodgs_frame_stage_ms(lodgs_frame *frame, float *ms);
  * [0] forward support tests evaluated, [1] forward blends (alpha composited),
  * [2] backward support tests, [3] backward contributions.  Tests skipped by
  * the 8x8-block support test are not counted; [2] and [3] are 0 after a render
- * until the backward runs.
+ * until the backward runs.  The counters are tallied only while the frame's
+ * profiling is on (lodgs_frame_set_profiling); otherwise they read 0.
  * Blocks until the frame's stream is idle. */
 int lodgs_frame_work(lodgs_frame *frame, uint64_t *work);
 

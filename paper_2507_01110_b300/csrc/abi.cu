@@ -329,6 +329,7 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     fr->f.cap_px = c;
     if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2]))
         if (int r = set_view(fr, nullptr, bg, st)) return r;
+    fr->f.count_work = fr->prof_mask != 0;
     // reset the render's counters and status (the selection's counters stay)
     LODGS_CUDA(cudaMemsetAsync(fr->f.cnt + C_NSEL_EFF, 0, (C_COUNT - C_NSEL_EFF) * sizeof(uint32_t), st));
     fr->mark(LODGS_STAGE_PROJECT, 0, st);

@@ -140,6 +140,7 @@ struct FrameBufs {
     // pixels (capacity cap_px): final transmittance bits and last contributor of the last render
     uint2 *px_state = nullptr;
     unsigned long long *work = nullptr;   // 4 counters, see lodgs_frame_work
+    bool count_work = false;              // blends tally the work counters (profiling frames)
     uint64_t cap_sel = 0, cap_pairs = 0, cap_tiles = 0, cap_px = 0;
     // where the last render left its sorted data
     const uint32_t *order = nullptr;     // selected indices by depth

@@ -167,48 +167,98 @@ __device__ __forceinline__ void warp_sum9_to_smem(float v[9], int lane, float *d
 
 // Warp-block layout of a 16x16 tile (128 threads, 2 pixels each): warp w owns
 // the 8x8 pixel block at ((w & 1) * 8, (w >> 1) * 8) of the tile, lane l the
-// pixels (l & 7, (l >> 3) + 4k), k = 0, 1.  Each warp skips a staged Gaussian
-// whose support box (half extents rx, ry) misses its block's pixel centres
-// (the block test is warp-uniform, so the warp branches as a whole), and
-// skips the blend body when no lane's pixel passes the support test.
+// pixels (l & 7, (l >> 3) + 4k), k = 0, 1.  When a batch of the tile's
+// Gaussians is staged, each Gaussian gets a 4-bit mask of the blocks its
+// support box reaches (the block test), and each warp compacts the batch to
+// the Gaussians whose mask holds its block; it then runs over that list only,
+// skipping the blend body of a Gaussian no lane's pixel passes the support
+// test for.
 constexpr int PIX = 2;
 constexpr int BNT = TILE_PIX / PIX;
+constexpr int NWARP = BNT / 32;
+// resident CTAs per SM the register allocation is held to (occupancy)
+#ifndef LODGS_FWD_MINB
+#define LODGS_FWD_MINB 8
+#endif
+#ifndef LODGS_BWD_MINB
+#define LODGS_BWD_MINB 8
+#endif
 constexpr float BLOCK_HALF = 3.5f;     // half span of an 8x8 block's pixel centres
+constexpr float LOG2E = 1.44269504088896341f;
+
+// 2^x and 1/x on the special function unit, denormals flushed: the blend only
+// takes 2^x for x >= -4.5 log2(e) and 1/x for x >= 0.01, where neither an input
+// nor a result is denormal.  exp(p) = 2^(p log2 e).
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 struct BlockPix {
-    int px, py0;          // this lane's column and first row
-    float xc, wcx, wcy;   // pixel-centre x, block centre
+    int w, px, py0;       // warp (block), this lane's column and first row
+    float xc;             // pixel-centre x
 };
 
 __device__ __forceinline__ BlockPix block_pix(int tile, int TX, int tid) {
     const int w = tid >> 5, lane = tid & 31;
-    const int bx0 = (tile % TX) * TILE + (w & 1) * 8, by0 = (tile / TX) * TILE + (w >> 1) * 8;
     BlockPix b;
-    b.px = bx0 + (lane & 7);
-    b.py0 = by0 + (lane >> 3);
+    b.w = w;
+    b.px = (tile % TX) * TILE + (w & 1) * 8 + (lane & 7);
+    b.py0 = (tile / TX) * TILE + (w >> 1) * 8 + (lane >> 3);
     b.xc = (float)b.px + 0.5f;
-    b.wcx = (float)bx0 + 4.0f;
-    b.wcy = (float)by0 + 4.0f;
     return b;
 }
 
-// True when the support box of a staged Gaussian (mean a.x, a.y; half extents
-// c.y, c.z) cannot reach this warp's block.
-__device__ __forceinline__ bool block_skip(const BlockPix &bp, const float4 &a, const float4 &c) {
-    return fabsf(__fsub_rn(a.x, bp.wcx)) > __fadd_rn(c.y, BLOCK_HALF) ||
-           fabsf(__fsub_rn(a.y, bp.wcy)) > __fadd_rn(c.z, BLOCK_HALF);
+// Blocks of tile (tx0, ty0) that the support box of a Gaussian (mean a.x,
+// a.y; half extents c.y, c.z) can reach: bit 2 * by + bx for the block at
+// (tx0 + 8 bx, ty0 + 8 by), whose pixel centres have centre (+4, +4) and half
+// span 3.5.  Float32, evaluated as written (the block test).
+__device__ __forceinline__ uint32_t block_mask(const float4 &a, const float4 &c, int tx0, int ty0) {
+    const float hx = __fadd_rn(c.y, BLOCK_HALF), hy = __fadd_rn(c.z, BLOCK_HALF);
+    const bool x0 = !(fabsf(__fsub_rn(a.x, __fadd_rn((float)tx0, 4.0f))) > hx);
+    const bool x1 = !(fabsf(__fsub_rn(a.x, __fadd_rn((float)(tx0 + 8), 4.0f))) > hx);
+    const bool y0 = !(fabsf(__fsub_rn(a.y, __fadd_rn((float)ty0, 4.0f))) > hy);
+    const bool y1 = !(fabsf(__fsub_rn(a.y, __fadd_rn((float)(ty0 + 8), 4.0f))) > hy);
+    return (uint32_t)(x0 && y0) | (uint32_t)(x1 && y0) << 1 | (uint32_t)(x0 && y1) << 2 |
+           (uint32_t)(x1 && y1) << 3;
 }
 
-__global__ void __launch_bounds__(BNT) k_blend(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
-                                               const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
-                                               const float4 *__restrict__ sp_c, const uint32_t *__restrict__ cnt,
-                                               int W, int H, int TX, const View *__restrict__ view,
-                                               float *__restrict__ image, uint2 *__restrict__ px_state,
-                                               unsigned long long *__restrict__ work) {
-    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+// This warp's list of the staged entries [0, n) whose mask holds block w, in
+// ascending order; returns its length.
+__device__ __forceinline__ int warp_list(const uint8_t *s_m, int n, int w, int lane, uint8_t *list) {
+    int len = 0;
+    for (int q0 = 0; q0 < n; q0 += 32) {
+        const int q = q0 + lane;
+        const bool mine = q < n && (s_m[q] >> w & 1u);
+        const unsigned bal = __ballot_sync(0xffffffffu, mine);
+        if (mine) list[len + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)q;
+        len += __popc(bal);
+    }
+    __syncwarp();
+    return len;
+}
+
+// COUNT: tally the work counters (profiling launches only).
+template <bool COUNT>
+__global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
+    k_blend(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval, const float4 *__restrict__ sp_a,
+            const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c, const uint32_t *__restrict__ cnt, int W,
+            int H, int TX, const View *__restrict__ view, float *__restrict__ image, uint2 *__restrict__ px_state,
+            unsigned long long *__restrict__ work) {
+    __shared__ float4 s_a[BATCH], s_b[BATCH];
+    __shared__ float s_c[BATCH];
+    __shared__ uint8_t s_m[BATCH];
+    __shared__ uint8_t s_list[NWARP][BATCH];
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
-    const int tile = blockIdx.x, tid = threadIdx.x;
+    const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int tx0 = (tile % TX) * TILE, ty0 = (tile / TX) * TILE;
     const BlockPix bp = block_pix(tile, TX, tid);
     float yc[PIX], T[PIX], c0[PIX], c1[PIX], c2[PIX];
     uint32_t last[PIX];
@@ -226,22 +276,22 @@ __global__ void __launch_bounds__(BNT) k_blend(const uint2 *__restrict__ ranges,
     const uint2 rg = ranges[tile];
     for (uint32_t base = rg.x; base < rg.y; base += BATCH) {
         if (__syncthreads_count(done) == BNT) break;
-        for (int q = tid; q < BATCH; q += BNT) {
-            const uint32_t idx = base + q;
-            if (idx < rg.y) {
-                const uint32_t g = pval[idx];
-                s_a[q] = sp_a[g];
-                s_b[q] = sp_b[g];
-                s_c[q] = sp_c[g];
-            }
+        const int n = min((uint32_t)BATCH, rg.y - base);
+        for (int q = tid; q < n; q += BNT) {
+            const uint32_t g = pval[base + q];
+            const float4 a = sp_a[g], c = sp_c[g];
+            s_a[q] = a;
+            s_b[q] = sp_b[g];
+            s_c[q] = c.x;
+            s_m[q] = (uint8_t)block_mask(a, c, tx0, ty0);
         }
         __syncthreads();
-        const int n = min((uint32_t)BATCH, rg.y - base);
         if (__all_sync(0xffffffffu, done)) continue;
-        for (int j = 0; j < n; ++j) {
+        const int len = warp_list(s_m, n, bp.w, lane, s_list[bp.w]);
+        const uint32_t rel1 = base - rg.x + 1;
+        for (int i = 0; i < len; ++i) {
+            const int j = s_list[bp.w][i];
             const float4 a = s_a[j];
-            const float4 c = s_c[j];
-            if (block_skip(bp, a, c)) continue;
             const float4 b = s_b[j];
             const float dx = __fsub_rn(a.x, bp.xc);
             const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
@@ -254,24 +304,28 @@ __global__ void __launch_bounds__(BNT) k_blend(const uint2 *__restrict__ ranges,
                 hit[k] = live[k] && p[k] >= SUPPORT_P;
                 any |= hit[k];
             }
-            n_eval += PIX;
+            if (COUNT) n_eval += PIX;
             if (!__any_sync(0xffffffffu, any)) continue;
+            const float cb = s_c[j];
+            bool died = false;
 #pragma unroll
-            for (int k = 0; k < PIX; ++k) {
-                if (hit[k]) {
-                    ++n_blend;
-                    const float alpha = fminf(ALPHA_MAX, b.y * __expf(p[k]));
-                    const float w = alpha * T[k];
-                    c0[k] += b.z * w; c1[k] += b.w * w; c2[k] += c.x * w;
-                    T[k] = T[k] * (1.0f - alpha);
-                    last[k] = base - rg.x + j + 1;
-                    if (T[k] < T_MIN) live[k] = false;
-                }
+            for (int k = 0; k < PIX; ++k) {     // predicated: alpha = 0 leaves T and the colour unchanged
+                if (COUNT) n_blend += hit[k];
+                const float alpha = hit[k] ? fminf(ALPHA_MAX, b.y * ex2_ftz(p[k] * LOG2E)) : 0.f;
+                const float w = alpha * T[k];
+                c0[k] += b.z * w; c1[k] += b.w * w; c2[k] += cb * w;
+                T[k] = T[k] * (1.0f - alpha);
+                last[k] = hit[k] ? rel1 + j : last[k];
+                const bool stop = hit[k] && T[k] < T_MIN;
+                live[k] = live[k] && !stop;
+                died |= stop;
             }
-            done = true;
+            if (__any_sync(0xffffffffu, died)) {
+                done = true;
 #pragma unroll
-            for (int k = 0; k < PIX; ++k) done &= !live[k];
-            if (__all_sync(0xffffffffu, done)) break;
+                for (int k = 0; k < PIX; ++k) done &= !live[k];
+                if (__all_sync(0xffffffffu, done)) break;
+            }
         }
     }
 #pragma unroll
@@ -284,7 +338,7 @@ __global__ void __launch_bounds__(BNT) k_blend(const uint2 *__restrict__ ranges,
             px_state[o] = make_uint2(__float_as_uint(T[k]), last[k]);
         }
     }
-    add_work(work, n_eval, n_blend);
+    if (COUNT) add_work(work, n_eval, n_blend);
 }
 
 // Backward of the blend, one pass back to front over each tile's list, from the
@@ -295,22 +349,24 @@ __global__ void __launch_bounds__(BNT) k_blend(const uint2 *__restrict__ ranges,
 // then Q <- Q + alpha_i (c_i - Q) and T_i = T_{i+1} / (1 - alpha_i).  The nine
 // per-Gaussian sums of a warp are reduced in registers and added to shared
 // memory; each batch's sums go to global memory with one atomic per value.
-__global__ void __launch_bounds__(BNT) k_blend_bwd(const uint2 *__restrict__ ranges,
-                                                   const uint32_t *__restrict__ pval,
-                                                   const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
-                                                   const float4 *__restrict__ sp_c,
-                                                   const uint32_t *__restrict__ cnt, int W, int H, int TX,
-                                                   const View *__restrict__ view,
-                                                   const uint2 *__restrict__ px_state,
-                                                   const float *__restrict__ dL_dimg, float *__restrict__ g2d,
-                                                   unsigned long long *__restrict__ work) {
-    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+template <bool COUNT>
+__global__ void __launch_bounds__(BNT, LODGS_BWD_MINB)
+    k_blend_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
+                const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c,
+                const uint32_t *__restrict__ cnt, int W, int H, int TX, const View *__restrict__ view,
+                const uint2 *__restrict__ px_state, const float *__restrict__ dL_dimg, float *__restrict__ g2d,
+                unsigned long long *__restrict__ work) {
+    __shared__ float4 s_a[BATCH], s_b[BATCH];
+    __shared__ float s_c[BATCH];
     __shared__ uint32_t s_g[BATCH];
     __shared__ float s_grad[BATCH][9];
+    __shared__ uint8_t s_m[BATCH];
+    __shared__ uint8_t s_list[NWARP][BATCH];
     __shared__ uint32_t s_end;
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
     const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int tx0 = (tile % TX) * TILE, ty0 = (tile / TX) * TILE;
     const BlockPix bp = block_pix(tile, TX, tid);
     float yc[PIX], T[PIX], G[PIX][3], Q[PIX][3];
     uint32_t last[PIX];
@@ -346,20 +402,22 @@ __global__ void __launch_bounds__(BNT) k_blend_bwd(const uint2 *__restrict__ ran
         __syncthreads();
         for (int q = tid; q < n; q += BNT) {
             const uint32_t g = pval[bstart + q];
+            const float4 a = sp_a[g], c = sp_c[g];
             s_g[q] = g;
-            s_a[q] = sp_a[g];
+            s_a[q] = a;
             s_b[q] = sp_b[g];
-            s_c[q] = sp_c[g];
+            s_c[q] = c.x;
+            s_m[q] = (uint8_t)block_mask(a, c, tx0, ty0);
 #pragma unroll
-            for (int c = 0; c < 9; ++c) s_grad[q][c] = 0.f;
+            for (int v = 0; v < 9; ++v) s_grad[q][v] = 0.f;
         }
         __syncthreads();
         const uint32_t rel = bstart - rg.x;
-        const int jtop = min(n, (int)wend - (int)rel);
-        for (int j = jtop - 1; j >= 0; --j) {
+        const int jtop = min(n, (int)wend - (int)rel);     // entries at or past this warp's end are skipped
+        const int len = jtop > 0 ? warp_list(s_m, jtop, bp.w, lane, s_list[bp.w]) : 0;
+        for (int i = len - 1; i >= 0; --i) {
+            const int j = s_list[bp.w][i];
             const float4 a = s_a[j];
-            const float4 c = s_c[j];
-            if (block_skip(bp, a, c)) continue;
             const float4 b = s_b[j];
             const uint32_t pos = rel + (uint32_t)j;
             const float dx = __fsub_rn(a.x, bp.xc);
@@ -373,8 +431,9 @@ __global__ void __launch_bounds__(BNT) k_blend_bwd(const uint2 *__restrict__ ran
                 hit[k] = pos < last[k] && p[k] >= SUPPORT_P;
                 any |= hit[k];
             }
-            n_eval += PIX;
+            if (COUNT) n_eval += PIX;
             if (!__any_sync(0xffffffffu, any)) continue;
+            const float cb = s_c[j];
             const float ax2 = 2.0f * a.z * dx, cy2 = 2.0f * b.x, hdx2 = -0.5f * dx * dx;
             float gv[9];
 #pragma unroll
@@ -382,13 +441,13 @@ __global__ void __launch_bounds__(BNT) k_blend_bwd(const uint2 *__restrict__ ran
 #pragma unroll
             for (int k = 0; k < PIX; ++k) {
                 if (hit[k]) {
-                    ++n_contrib;
+                    if (COUNT) ++n_contrib;
                     const float dy = dyk[k];
-                    const float e = __expf(p[k]);
+                    const float e = ex2_ftz(p[k] * LOG2E);
                     const float raw = b.y * e;
                     const float alpha = fminf(ALPHA_MAX, raw);
-                    const float Tb = __fdividef(T[k], 1.0f - alpha);
-                    const float d0 = b.z - Q[k][0], d1 = b.w - Q[k][1], d2 = c.x - Q[k][2];
+                    const float Tb = T[k] * rcp_ftz(1.0f - alpha);
+                    const float d0 = b.z - Q[k][0], d1 = b.w - Q[k][1], d2 = cb - Q[k][2];
                     const float dA = (G[k][0] * d0 + G[k][1] * d1 + G[k][2] * d2) * Tb;
                     const float wgt = alpha * Tb;
                     gv[6] += G[k][0] * wgt; gv[7] += G[k][1] * wgt; gv[8] += G[k][2] * wgt;
@@ -411,14 +470,14 @@ __global__ void __launch_bounds__(BNT) k_blend_bwd(const uint2 *__restrict__ ran
         for (int q = tid; q < n; q += BNT) {
             float *o = g2d + (size_t)s_g[q] * 9;
 #pragma unroll
-            for (int c = 0; c < 9; ++c) {
-                const float v = s_grad[q][c];
-                if (v != 0.f) atomicAdd(o + c, v);
+            for (int v = 0; v < 9; ++v) {
+                const float x = s_grad[q][v];
+                if (x != 0.f) atomicAdd(o + v, x);
             }
         }
         bend = bstart;
     }
-    add_work(work + 2, n_eval, n_contrib);
+    if (COUNT) add_work(work + 2, n_eval, n_contrib);
 }
 
 int ceil_log2(uint64_t x) {
@@ -459,8 +518,8 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
     LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));
     k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, (uint32_t)n_tiles, f.ranges);
     count_launches(1);
-    k_blend<<<(unsigned)n_tiles, BNT, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H,
-                                               k.TX, f.d_view, image, f.px_state, f.work);
+    (f.count_work ? k_blend<true> : k_blend<false>)<<<(unsigned)n_tiles, BNT, 0, st>>>(
+        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.px_state, f.work);
     count_launches(1);
     sm.mark(LODGS_STAGE_BLEND, 1, st);
     LODGS_CUDA(cudaGetLastError());
@@ -471,8 +530,9 @@ int launch_raster_backward(const CamK &k, FrameBufs &f, const float *dL_dimage, 
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * 9 * sizeof(float), st));
     LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
-    k_blend_bwd<<<(unsigned)n_tiles, BNT, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W,
-                                                   k.H, k.TX, f.d_view, f.px_state, dL_dimage, f.g2d, f.work);
+    (f.count_work ? k_blend_bwd<true> : k_blend_bwd<false>)<<<(unsigned)n_tiles, BNT, 0, st>>>(
+        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, f.px_state, dL_dimage,
+        f.g2d, f.work);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
