@@ -241,6 +241,16 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
     if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(&cnt[C_NVIS], nvis);
 }
 
+// Floats per record of SH degree DEG (14 base values + 3 per SH coefficient,
+// padded to a multiple of 8).
+__host__ __device__ constexpr int rec_stride(int deg) { return (14 + 3 * ((deg + 1) * (deg + 1) - 1) + 7) / 8 * 8; }
+
+// Each warp handles 32 selected Gaussians at a time: the records of the
+// visible ones are staged in shared memory row by row (whole-warp, coalesced
+// reads), each lane computes the gradient of its own Gaussian in place of its
+// record there, and the warp writes the 32 gradient rows back row by row.
+// Rows are padded to RS + 1 floats so that lanes reading the same field of
+// their own rows hit distinct banks.
 template <int DEG>
 __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ rows, int stride,
                                                      const uint32_t *__restrict__ sel_src,
@@ -249,18 +259,37 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
                                                      const uint32_t *__restrict__ ntiles,
                                                      const float *__restrict__ g2d, float *__restrict__ out,
                                                      int dense) {
+    constexpr int RS = rec_stride(DEG), SP = RS + 1;
+    __shared__ float s_rows[PB / 32][32 * SP];
     const CamK &k = view->k;
     const uint32_t n = cnt[C_NSEL_EFF];
     constexpr int degree = DEG;
     constexpr int K = (DEG + 1) * (DEG + 1) - 1;
-    for (uint32_t i = blockIdx.x * PB + threadIdx.x; i < n; i += gridDim.x * PB) {
-        const uint32_t row = sel_rows[i];
-        float *o = out + (size_t)(dense ? row : i) * stride;
-        if (ntiles[i] == 0) {
-            for (int c = 0; c < stride; c += 4) *reinterpret_cast<float4 *>(o + c) = make_float4(0, 0, 0, 0);
-            continue;
+    (void)stride;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *sw = s_rows[wib];
+    float *r = sw + lane * SP;              // this lane's record, then its gradient row
+    for (uint32_t t0 = (blockIdx.x * (PB / 32) + wib) * 32u; t0 < n; t0 += gridDim.x * PB) {
+        const int m = (int)min(32u, n - t0);
+        const uint32_t i = t0 + lane;
+        const bool mine = lane < m;
+        const bool vis = mine && ntiles[i] != 0;
+        const uint32_t src = vis ? sel_src[i] : 0u;
+        const unsigned vmask = __ballot_sync(0xffffffffu, vis);
+#pragma unroll 4
+        for (int e = 0; e < m; ++e) {
+            if (!(vmask >> e & 1u)) continue;
+            const float2 *g = reinterpret_cast<const float2 *>(rows + (size_t)__shfl_sync(0xffffffffu, src, e) * RS);
+            for (int c = lane; c < RS / 2; c += 32) {
+                const float2 v = g[c];
+                sw[e * SP + 2 * c] = v.x;
+                sw[e * SP + 2 * c + 1] = v.y;
+            }
         }
-        const float *r = rows + (size_t)sel_src[i] * stride;
+        __syncwarp();
+        if (mine && !vis) {
+            for (int c = 0; c < RS; ++c) r[c] = 0.f;
+        } else if (vis) {
         const float *gg = g2d + (size_t)i * 9;
         float g[9];
 #pragma unroll
@@ -286,11 +315,11 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
             grow_b[ch] = gc;
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) {
-                o[REC_F + 3 * kk + ch] = gc * Y[kk];
-                float f = r[REC_F + 3 * kk + ch];
+                const float f = r[REC_F + 3 * kk + ch];      // read before the slot is overwritten
                 gdir[0] += gc * f * dY[kk][0];
                 gdir[1] += gc * f * dY[kk][1];
                 gdir[2] += gc * f * dY[kk][2];
+                r[REC_F + 3 * kk + ch] = gc * Y[kk];
             }
         }
         float dotv = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
@@ -347,7 +376,7 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
         gt[2] += -k.fy * ty / tz2 * g[1];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            o[REC_MU + a] = gd[a] + k.R[0 * 3 + a] * gt[0] + k.R[1 * 3 + a] * gt[1] + k.R[2 * 3 + a] * gt[2];
+            r[REC_MU + a] = gd[a] + k.R[0 * 3 + a] * gt[0] + k.R[1 * 3 + a] * gt[1] + k.R[2 * 3 + a] * gt[2];
         // ---- Sigma = M M^T, M = R diag(s) ----
         float gR[3][3];
 #pragma unroll
@@ -359,7 +388,7 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
                 acc += gM * G.R[i2][j];
                 gR[i2][j] = gM * s[j];
             }
-            o[REC_S + j] = acc;
+            r[REC_S + j] = acc;
         }
         float w = G.qh[0], x = G.qh[1], y = G.qh[2], z = G.qh[3];
         float gq[4];
@@ -372,11 +401,20 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
               - 4.0f * z * (gR[0][0] + gR[1][1]);
         float qd = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) o[REC_Q + a] = (gq[a] - G.qh[a] * qd) / G.qn;
-        o[REC_OP] = g[5];
+        for (int a = 0; a < 4; ++a) r[REC_Q + a] = (gq[a] - G.qh[a] * qd) / G.qn;
+        r[REC_OP] = g[5];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) o[REC_B + ch] = grow_b[ch];
-        for (int c = 14 + 3 * K; c < stride; ++c) o[c] = 0.f;
+        for (int ch = 0; ch < 3; ++ch) r[REC_B + ch] = grow_b[ch];
+        for (int c = 14 + 3 * K; c < RS; ++c) r[c] = 0.f;
+        }
+        __syncwarp();
+        const uint32_t dst_row = mine ? (dense ? sel_rows[i] : i) : 0u;
+#pragma unroll 4
+        for (int e = 0; e < m; ++e) {
+            float2 *d = reinterpret_cast<float2 *>(out + (size_t)__shfl_sync(0xffffffffu, dst_row, e) * RS);
+            for (int c = lane; c < RS / 2; c += 32) d[c] = make_float2(sw[e * SP + 2 * c], sw[e * SP + 2 * c + 1]);
+        }
+        __syncwarp();
     }
 }
 
@@ -400,6 +438,10 @@ int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaS
 
 int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows, int dense,
                             cudaStream_t st) {
+    if (sc->sh_degree < 0 || sc->sh_degree > 3 || sc->stride != rec_stride(sc->sh_degree)) {
+        set_error("render_backward: record stride does not match the SH degree");
+        return LODGS_E_INVALID;
+    }
 #define LAUNCH_PBWD(D)                                                                                     \
     k_project_bwd<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.sel_rows, f.d_view, \
                                                f.cnt, f.ntiles, f.g2d, grad_rows, dense)
