@@ -54,4 +54,7 @@ def test_autograd_two_views_accumulate():
     rows.grad = None
     autograd.render(rows, scene, c2).sum().backward()
     g2 = rows.grad.clone()
-    assert torch.allclose(g_both, g1 + g2, rtol=1e-5, atol=1e-7)
+    # the blend backward sums per-Gaussian gradients across tiles with float
+    # atomics, so separate backward passes agree to the rounding of those sums
+    scale = (g1.abs() + g2.abs()).amax(dim=0, keepdim=True).clamp_min(1e-12)
+    assert ((g_both - g1 - g2).abs() / scale).max().item() < 1e-5
