@@ -87,7 +87,7 @@ int ensure_sel(lodgs_frame *fr, uint64_t want) {
     c = f.cap_sel;                                    \
     if (int r_ = grow(ptr, c, want, per)) return r_;
     G1(f.sp_a, 1) G1(f.sp_b, 1) G1(f.sp_c, 1) G1(f.dkey, 1) G1(f.dval, 1) G1(f.dkey_alt, 1) G1(f.dval_alt, 1)
-    G1(f.rect, 1) G1(f.ntiles, 1) G1(f.nt_sorted, 1) G1(f.pair_off, 1) G1(f.g2d, 9)
+    G1(f.rect, 1) G1(f.ntiles, 1) G1(f.nt_sorted, 1) G1(f.pair_off, 1) G1(f.g2d, G2D_STRIDE)
 #undef G1
     f.cap_sel = want;
     return LODGS_OK;

@@ -115,6 +115,9 @@ struct lodgs_scene {
 namespace lodgs {
 
 // Device buffers of one frame (one view).  Capacities are element counts.
+// floats per Gaussian of the 2D gradient rows (9 used; 16-byte aligned rows)
+constexpr int G2D_STRIDE = 12;
+
 struct FrameBufs {
     uint32_t *cnt = nullptr;         // C_COUNT device counters
     View *d_view = nullptr;          // camera constants and background of the current view
@@ -132,7 +135,7 @@ struct FrameBufs {
     uint32_t *dkey = nullptr, *dval = nullptr, *dkey_alt = nullptr, *dval_alt = nullptr;
     uint2 *rect = nullptr;           // x0 | y0 << 16, x1 | y1 << 16
     uint32_t *ntiles = nullptr, *nt_sorted = nullptr, *pair_off = nullptr;
-    float *g2d = nullptr;            // 9 per selected: d/d(u, v, A, B, C, opacity, r, g, b)
+    float *g2d = nullptr;            // G2D_STRIDE per selected: d/d(u, v, A, B, C, opacity, r, g, b), 3 unused
     // pairs (capacity cap_pairs)
     uint32_t *pkey = nullptr, *pval = nullptr, *pkey_alt = nullptr, *pval_alt = nullptr;
     // tiles (capacity cap_tiles)

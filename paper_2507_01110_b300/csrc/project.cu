@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
         if (mine && !vis) {
             for (int c = 0; c < RS; ++c) r[c] = 0.f;
         } else if (vis) {
-        const float *gg = g2d + (size_t)i * 9;
+        const float *gg = g2d + (size_t)i * G2D_STRIDE;
         float g[9];
 #pragma unroll
         for (int c = 0; c < 9; ++c) g[c] = gg[c];

@@ -180,8 +180,12 @@ constexpr int NWARP = BNT / 32;
 #ifndef LODGS_FWD_MINB
 #define LODGS_FWD_MINB 8
 #endif
-#ifndef LODGS_BWD_MINB
-#define LODGS_BWD_MINB 8
+#ifndef LODGS_BWD_PIX
+#define LODGS_BWD_PIX 2      // pixels per lane of the backward blend (2 or 4)
+#endif
+constexpr int BWD_PIX = LODGS_BWD_PIX;
+#ifndef LODGS_G2D_VEC
+#define LODGS_G2D_VEC 1      // 16-byte vector atomics for the per-batch gradient flush
 #endif
 constexpr float BLOCK_HALF = 3.5f;     // half span of an 8x8 block's pixel centres
 constexpr float LOG2E = 1.44269504088896341f;
@@ -229,13 +233,13 @@ __device__ __forceinline__ uint32_t block_mask(const float4 &a, const float4 &c,
            (uint32_t)(x1 && y1) << 3;
 }
 
-// This warp's list of the staged entries [0, n) whose mask holds block w, in
-// ascending order; returns its length.
-__device__ __forceinline__ int warp_list(const uint8_t *s_m, int n, int w, int lane, uint8_t *list) {
+// This warp's list of the staged entries [0, n) whose mask meets the warp's
+// blocks (wmask), in ascending order; returns its length.
+__device__ __forceinline__ int warp_list(const uint8_t *s_m, int n, uint32_t wmask, int lane, uint8_t *list) {
     int len = 0;
     for (int q0 = 0; q0 < n; q0 += 32) {
         const int q = q0 + lane;
-        const bool mine = q < n && (s_m[q] >> w & 1u);
+        const bool mine = q < n && (s_m[q] & wmask);
         const unsigned bal = __ballot_sync(0xffffffffu, mine);
         if (mine) list[len + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)q;
         len += __popc(bal);
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
         }
         __syncthreads();
         if (__all_sync(0xffffffffu, done)) continue;
-        const int len = warp_list(s_m, n, bp.w, lane, s_list[bp.w]);
+        const int len = warp_list(s_m, n, 1u << bp.w, lane, s_list[bp.w]);
         const uint32_t rel1 = base - rg.x + 1;
         for (int i = 0; i < len; ++i) {
             const int j = s_list[bp.w][i];
@@ -349,8 +353,11 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
 // then Q <- Q + alpha_i (c_i - Q) and T_i = T_{i+1} / (1 - alpha_i).  The nine
 // per-Gaussian sums of a warp are reduced in registers and added to shared
 // memory; each batch's sums go to global memory with one atomic per value.
-template <bool COUNT>
-__global__ void __launch_bounds__(BNT, LODGS_BWD_MINB)
+// BP pixels per lane: 2 (a warp per 8x8 block, 128 threads per tile) or 4 (a
+// warp per 8x16 column of two blocks, 64 threads per tile; the per-Gaussian
+// warp sums and list overhead are shared by twice the pixels).
+template <bool COUNT, int BP>
+__global__ void __launch_bounds__(TILE_PIX / BP)
     k_blend_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
                 const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c,
                 const uint32_t *__restrict__ cnt, int W, int H, int TX, const View *__restrict__ view,
@@ -361,18 +368,23 @@ __global__ void __launch_bounds__(BNT, LODGS_BWD_MINB)
     __shared__ uint32_t s_g[BATCH];
     __shared__ float s_grad[BATCH][9];
     __shared__ uint8_t s_m[BATCH];
-    __shared__ uint8_t s_list[NWARP][BATCH];
+    constexpr int NT = TILE_PIX / BP, NW = NT / 32;
+    __shared__ uint8_t s_list[NW][BATCH];
     __shared__ uint32_t s_end;
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
     const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     const int tx0 = (tile % TX) * TILE, ty0 = (tile / TX) * TILE;
     const BlockPix bp = block_pix(tile, TX, tid);
-    float yc[PIX], T[PIX], G[PIX][3], Q[PIX][3];
-    uint32_t last[PIX];
+    // blocks this warp covers: (w & 1, (w >> 1) + k / 2) for its pixel rows k
+    uint32_t wmask = 0;
+#pragma unroll
+    for (int k = 0; k < BP; k += 2) wmask |= 1u << (((bp.w >> 1) + k / 2) * 2 + (bp.w & 1));
+    float yc[BP], T[BP], G[BP][3], Q[BP][3];
+    uint32_t last[BP];
     uint32_t wend = 0;
 #pragma unroll
-    for (int k = 0; k < PIX; ++k) {
+    for (int k = 0; k < BP; ++k) {
         const int py = bp.py0 + 4 * k;
         yc[k] = (float)py + 0.5f;
         T[k] = 1.0f; last[k] = 0;
@@ -400,7 +412,7 @@ __global__ void __launch_bounds__(BNT, LODGS_BWD_MINB)
         const uint32_t bstart = bend - rg.x > (uint32_t)BATCH ? bend - BATCH : rg.x;
         const int n = (int)(bend - bstart);
         __syncthreads();
-        for (int q = tid; q < n; q += BNT) {
+        for (int q = tid; q < n; q += NT) {
             const uint32_t g = pval[bstart + q];
             const float4 a = sp_a[g], c = sp_c[g];
             s_g[q] = g;
@@ -414,7 +426,7 @@ __global__ void __launch_bounds__(BNT, LODGS_BWD_MINB)
         __syncthreads();
         const uint32_t rel = bstart - rg.x;
         const int jtop = min(n, (int)wend - (int)rel);     // entries at or past this warp's end are skipped
-        const int len = jtop > 0 ? warp_list(s_m, jtop, bp.w, lane, s_list[bp.w]) : 0;
+        const int len = jtop > 0 ? warp_list(s_m, jtop, wmask, lane, s_list[bp.w]) : 0;
         for (int i = len - 1; i >= 0; --i) {
             const int j = s_list[bp.w][i];
             const float4 a = s_a[j];
@@ -422,16 +434,16 @@ __global__ void __launch_bounds__(BNT, LODGS_BWD_MINB)
             const uint32_t pos = rel + (uint32_t)j;
             const float dx = __fsub_rn(a.x, bp.xc);
             const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
-            float p[PIX], dyk[PIX];
-            bool hit[PIX], any = false;
+            float p[BP], dyk[BP];
+            bool hit[BP], any = false;
 #pragma unroll
-            for (int k = 0; k < PIX; ++k) {
+            for (int k = 0; k < BP; ++k) {
                 dyk[k] = __fsub_rn(a.y, yc[k]);
                 p[k] = __fmaf_rn(bx, dyk[k], __fmaf_rn(__fmul_rn(b.x, dyk[k]), dyk[k], hxx));
                 hit[k] = pos < last[k] && p[k] >= SUPPORT_P;
                 any |= hit[k];
             }
-            if (COUNT) n_eval += PIX;
+            if (COUNT) n_eval += BP;
             if (!__any_sync(0xffffffffu, any)) continue;
             const float cb = s_c[j];
             const float ax2 = 2.0f * a.z * dx, cy2 = 2.0f * b.x, hdx2 = -0.5f * dx * dx;
@@ -439,7 +451,7 @@ __global__ void __launch_bounds__(BNT, LODGS_BWD_MINB)
 #pragma unroll
             for (int q = 0; q < 9; ++q) gv[q] = 0.f;
 #pragma unroll
-            for (int k = 0; k < PIX; ++k) {
+            for (int k = 0; k < BP; ++k) {
                 if (hit[k]) {
                     if (COUNT) ++n_contrib;
                     const float dy = dyk[k];
@@ -467,13 +479,23 @@ __global__ void __launch_bounds__(BNT, LODGS_BWD_MINB)
             warp_sum9_to_smem(gv, lane, s_grad[j]);
         }
         __syncthreads();
-        for (int q = tid; q < n; q += BNT) {
-            float *o = g2d + (size_t)s_g[q] * 9;
+        for (int q = tid; q < n; q += NT) {
+            float *o = g2d + (size_t)s_g[q] * G2D_STRIDE;
+#if LODGS_G2D_VEC
+            const float4 x0 = make_float4(s_grad[q][0], s_grad[q][1], s_grad[q][2], s_grad[q][3]);
+            const float4 x1 = make_float4(s_grad[q][4], s_grad[q][5], s_grad[q][6], s_grad[q][7]);
+            if (x0.x != 0.f || x0.y != 0.f || x0.z != 0.f || x0.w != 0.f)
+                atomicAdd(reinterpret_cast<float4 *>(o), x0);
+            if (x1.x != 0.f || x1.y != 0.f || x1.z != 0.f || x1.w != 0.f)
+                atomicAdd(reinterpret_cast<float4 *>(o + 4), x1);
+            if (s_grad[q][8] != 0.f) atomicAdd(o + 8, s_grad[q][8]);
+#else
 #pragma unroll
             for (int v = 0; v < 9; ++v) {
                 const float x = s_grad[q][v];
                 if (x != 0.f) atomicAdd(o + v, x);
             }
+#endif
         }
         bend = bstart;
     }
@@ -528,9 +550,9 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
 
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float *dL_dimage, cudaStream_t st) {
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
-    LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * 9 * sizeof(float), st));
+    LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * G2D_STRIDE * sizeof(float), st));
     LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
-    (f.count_work ? k_blend_bwd<true> : k_blend_bwd<false>)<<<(unsigned)n_tiles, BNT, 0, st>>>(
+    (f.count_work ? k_blend_bwd<true, BWD_PIX> : k_blend_bwd<false, BWD_PIX>)<<<(unsigned)n_tiles, TILE_PIX / BWD_PIX, 0, st>>>(
         f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, f.px_state, dL_dimage,
         f.g2d, f.work);
     count_launches(1);
