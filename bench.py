@@ -378,6 +378,9 @@ def run_lodgs(args, rank: int, world: int):
 # implementation's, not the method's.  Counts are issue slots: 128 per SM and
 # clock is the issue peak for any instruction type.
 OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB = 6, 11, 34
+# DRAM bytes (read + write) per k_blend_bwd launch, mean over the 32 views of
+# this workload, from one ncu capture (profiles/launches_fwd_bwd_1080p_2Mleaves.md)
+BLEND_BWD_DRAM_BYTES = 49.5e6
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 
@@ -669,7 +672,8 @@ def main():
                             "peak_source": peaks["source"] + " (MEASURED_PEAKS hbm_gbs)"}
     else:
         line["roofline"] = {"bound": "alu", "kernel": dom, "achieved": ds.get("tinst_s"), "peak": rf["alu_peak"],
-                            "unit": "T inst/s", "frac": ds.get("frac_alu"), "traffic": None,
+                            "unit": "T inst/s", "frac": ds.get("frac_alu"),
+                            "traffic": BLEND_BWD_DRAM_BYTES if dom == "blend_bwd" else None,
                             "peak_source": f"148 SMs x 128 issue lanes x {rf['mhz']:.0f} MHz (median SM clock "
                                            "in the timed region)",
                             "work": f"algorithmic instructions = {OPS_EVAL + OPS_BWD_CONTRIB} per backward "

@@ -239,8 +239,13 @@ int lodgs_render(lodgs_scene *scene, lodgs_frame *frame, const float *rows, cons
                  float *image, void *stream);
 
 /*
- * Backward of lodgs_render for the same frame, rows and bg: transmittance is
- * recomputed per tile (nothing per pixel is stored by the forward).
+ * Backward of lodgs_render for the same frame, rows and bg (Eq. 1-2
+ * differentiated): each tile's list is walked front to back again,
+ * recomputing transmittance per tile (nothing per pixel is stored by the
+ * forward); the colour behind each Gaussian is the forward's output minus the
+ * colour composited in front of it.
+ *   image:     device H x W x 3, the image the frame's last lodgs_render wrote,
+ *              unchanged since
  *   dL_dimage: device H x W x 3
  *   grad_rows: device, caller-owned.  dense == 0: n_selected x stride rows, row i
  *              for the i-th selected node (lodgs_frame_selection order);
@@ -250,7 +255,7 @@ int lodgs_render(lodgs_scene *scene, lodgs_frame *frame, const float *rows, cons
  * included).  Asynchronous.
  */
 int lodgs_render_backward(lodgs_scene *scene, lodgs_frame *frame, const float *rows, const float *bg,
-                          const float *dL_dimage, float *grad_rows, int dense, void *stream);
+                          const float *image, const float *dL_dimage, float *grad_rows, int dense, void *stream);
 
 /*
  * Gradient of a multi-view batch loss: sums the per-view sparse gradient rows
@@ -282,7 +287,8 @@ int lodgs_l1_loss_grad(const float *image, const float *target, int64_t n, float
  * separately (e.g. as separate CUDA graphs): the blend backward (per-pixel
  * recomputation, 2D gradients kept in the frame), then the projection backward
  * into gradient rows (same meaning of rows, grad_rows, dense). */
-int lodgs_render_backward_blend(lodgs_scene *scene, lodgs_frame *frame, const float *dL_dimage, void *stream);
+int lodgs_render_backward_blend(lodgs_scene *scene, lodgs_frame *frame, const float *image, const float *dL_dimage,
+                                void *stream);
 int lodgs_render_backward_project(lodgs_scene *scene, lodgs_frame *frame, const float *rows, float *grad_rows,
                                   int dense, void *stream);
 

@@ -84,8 +84,8 @@ _SIGS = {
     "lodgs_cache_flush": (C.c_int, [_P]),
     "lodgs_stream_nodes": (C.c_int, [_P, _P, C.POINTER(Camera), _P, _P, _P, C.POINTER(StreamStats)]),
     "lodgs_render": (C.c_int, [_P, _P, _P, _P, _P, _P]),
-    "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, _P]),
-    "lodgs_render_backward_blend": (C.c_int, [_P, _P, _P, _P]),
+    "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, _P]),
+    "lodgs_render_backward_blend": (C.c_int, [_P, _P, _P, _P, _P]),
     "lodgs_render_backward_project": (C.c_int, [_P, _P, _P, _P, C.c_int, _P]),
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
     "lodgs_accumulate_grads": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, C.c_int64, _P, _P]),

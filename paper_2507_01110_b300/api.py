@@ -112,6 +112,7 @@ class Frame:
         self._h = h
         self.camera = None
         self.bg = (0.0, 0.0, 0.0)
+        self.image = None           # tensor the last render wrote (read by render_backward)
 
     @property
     def handle(self):
@@ -280,10 +281,11 @@ def build_hierarchy(leaves, sh_degree: int, spt_volume: float, kappa: float) -> 
     return Scene(h)
 
 
-def render_backward_blend(scene: Scene, frame: Frame, dL_dimage: torch.Tensor, stream=None) -> None:
+def render_backward_blend(scene: Scene, frame: Frame, dL_dimage: torch.Tensor, stream=None,
+                          image: torch.Tensor | None = None) -> None:
     """First half of render_backward: the blend backward (2D gradients stay in the frame)."""
-    check(lib().lodgs_render_backward_blend(scene.handle, frame.handle, _ptr(dL_dimage.contiguous()),
-                                            _stream_ptr(stream)))
+    check(lib().lodgs_render_backward_blend(scene.handle, frame.handle, _ptr(_rendered_image(frame, image)),
+                                            _ptr(dL_dimage.contiguous()), _stream_ptr(stream)))
 
 
 def render_backward_project(scene: Scene, frame: Frame, grad: torch.Tensor, rows: torch.Tensor | None = None,
@@ -331,6 +333,7 @@ def render(scene: Scene, frame: Frame, rows: torch.Tensor | None = None, bg=(0.0
     else:
         bgv = (C.c_float * 3)(*[float(b) for b in bg])
         frame.bg = tuple(float(b) for b in bg)
+    frame.image = image             # what render_backward reads by default
     for _ in range(4):
         check(lib().lodgs_render(scene.handle, frame.handle, _ptr(rows), bgv, _ptr(image), _stream_ptr(stream)))
         if not check_capacity:
@@ -342,11 +345,19 @@ def render(scene: Scene, frame: Frame, rows: torch.Tensor | None = None, bg=(0.0
     raise _lib.LodgsError(_lib.LODGS_E_CAPACITY, "workspace did not converge")
 
 
+def _rendered_image(frame: Frame, image: torch.Tensor | None) -> torch.Tensor:
+    img = image if image is not None else getattr(frame, "image", None)
+    if img is None:
+        raise _lib.LodgsError(_lib.LODGS_E_STATE, "render_backward: no image rendered on this frame")
+    return img.contiguous()
+
+
 def render_backward(scene: Scene, frame: Frame, dL_dimage: torch.Tensor, rows: torch.Tensor | None = None,
                     grad: torch.Tensor | None = None, dense: bool = False, n_selected: int | None = None,
-                    stream=None) -> torch.Tensor:
+                    stream=None, image: torch.Tensor | None = None) -> torch.Tensor:
     """Gradients of the frame's last render w.r.t. the records.  Sparse: one row per
-    selected node (selection order); dense: n_nodes x stride with selected rows written."""
+    selected node (selection order); dense: n_nodes x stride with selected rows written.
+    `image` is the frame's last rendered image (default: the tensor render wrote)."""
     if grad is None:
         if dense:
             grad = torch.zeros((scene.n_nodes, scene.stride), dtype=torch.float32, device="cuda")
@@ -356,6 +367,7 @@ def render_backward(scene: Scene, frame: Frame, dL_dimage: torch.Tensor, rows: t
             grad = torch.empty((max(n_selected, 1), scene.stride), dtype=torch.float32, device="cuda")
     bgv = (C.c_float * 3)(*frame.bg)
     dL = dL_dimage.contiguous()
-    check(lib().lodgs_render_backward(scene.handle, frame.handle, _ptr(rows), bgv, _ptr(dL), _ptr(grad),
+    img = _rendered_image(frame, image)
+    check(lib().lodgs_render_backward(scene.handle, frame.handle, _ptr(rows), bgv, _ptr(img), _ptr(dL), _ptr(grad),
                                       C.c_int(int(dense)), _stream_ptr(stream)))
     return grad

@@ -4,7 +4,9 @@ The differentiable input is the scene's record tensor (n_nodes x stride,
 render-row order); only the rows of the view's LoD cut receive gradients, as in
 the paper's training, where optimisation touches the cut set only (appendix,
 Implementation Details).  The backward recomputes each pixel's transmittance
-from the sorted per-tile lists; nothing per pixel is stored by the forward.
+from the sorted per-tile lists, front to back, and takes the colour behind
+each Gaussian from the rendered image (saved for backward); nothing else per
+pixel is stored by the forward.
 """
 from __future__ import annotations
 
@@ -19,14 +21,15 @@ class LodRender(torch.autograd.Function):
         rows_c = rows.detach().contiguous()
         img = api.render(scene, frame, rows=rows_c, bg=bg)
         ctx.scene, ctx.frame = scene, frame
-        ctx.save_for_backward(rows_c)
+        ctx.save_for_backward(rows_c, img)
         return img
 
     @staticmethod
     def backward(ctx, grad_img: torch.Tensor):
-        (rows_c,) = ctx.saved_tensors
+        rows_c, img = ctx.saved_tensors
         grad = torch.zeros_like(rows_c)
-        api.render_backward(ctx.scene, ctx.frame, grad_img.contiguous(), rows=rows_c, grad=grad, dense=True)
+        api.render_backward(ctx.scene, ctx.frame, grad_img.contiguous(), rows=rows_c, grad=grad, dense=True,
+                            image=img)
         return grad, None, None, None
 
 

@@ -111,7 +111,7 @@ void free_frame_bufs(FrameBufs &f) {
     void *ps[] = {f.cnt, f.d_view, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
                   f.sort_hist, f.sp_a, f.sp_b, f.sp_c, f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.rect, f.ntiles,
                   f.nt_sorted, f.pair_off, f.g2d, f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.ranges, f.work,
-                  f.sel_src, f.emit_src, f.px_state};
+                  f.sel_src, f.emit_src};
     for (void *p : ps)
         if (p) cudaFree(p);
     f = FrameBufs();
@@ -324,9 +324,6 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     uint64_t c = fr->f.cap_tiles;
     if (int r = grow(fr->f.ranges, c, n_tiles)) return r;
     fr->f.cap_tiles = c;
-    c = fr->f.cap_px;
-    if (int r = grow(fr->f.px_state, c, (uint64_t)fr->k.W * fr->k.H)) return r;
-    fr->f.cap_px = c;
     if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2]))
         if (int r = set_view(fr, nullptr, bg, st)) return r;
     fr->f.count_work = fr->prof_mask != 0;
@@ -351,13 +348,14 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     return LODGS_OK;
 }
 
-int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *dL_dimage, void *stream) {
-    if (!sc || !fr || fr->scene != sc || !dL_dimage) {
+int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const float *dL_dimage,
+                                void *stream) {
+    if (!sc || !fr || fr->scene != sc || !image || !dL_dimage) {
         set_error("render_backward_blend: NULL or mismatched argument");
         return LODGS_E_INVALID;
     }
     if (!fr->rendered) { set_error("render_backward: render was not called on this frame"); return LODGS_E_STATE; }
-    if ((uint64_t)fr->k.TX * fr->k.TY > fr->f.cap_tiles || (uint64_t)fr->k.W * fr->k.H > fr->f.cap_px) {
+    if ((uint64_t)fr->k.TX * fr->k.TY > fr->f.cap_tiles) {
         set_error("render_backward: the frame's camera is larger than the one it was rendered with");
         return LODGS_E_STATE;
     }
@@ -371,7 +369,7 @@ int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *d
         fr->stream = st;
     }
     fr->mark(LODGS_STAGE_BLEND_BWD, 0, st);
-    int rc = launch_raster_backward(fr->k, fr->f, dL_dimage, st);
+    int rc = launch_raster_backward(fr->k, fr->f, image, dL_dimage, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_BLEND_BWD, 1, st);
     fr->blend_bwd_done = true;
@@ -406,8 +404,8 @@ int lodgs_render_backward_project(lodgs_scene *sc, lodgs_frame *fr, const float 
 }
 
 int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const float *bg,
-                          const float *dL_dimage, float *grad_rows, int dense, void *stream) {
-    if (!sc || !fr || fr->scene != sc || !dL_dimage || !grad_rows) {
+                          const float *image, const float *dL_dimage, float *grad_rows, int dense, void *stream) {
+    if (!sc || !fr || fr->scene != sc || !image || !dL_dimage || !grad_rows) {
         set_error("render_backward: NULL or mismatched argument");
         return LODGS_E_INVALID;
     }
@@ -415,7 +413,7 @@ int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, c
         set_error("render_backward: background differs from the one the frame was rendered with");
         return LODGS_E_STATE;
     }
-    int rc = lodgs_render_backward_blend(sc, fr, dL_dimage, stream);
+    int rc = lodgs_render_backward_blend(sc, fr, image, dL_dimage, stream);
     if (!rc) rc = lodgs_render_backward_project(sc, fr, rows, grad_rows, dense, stream);
     return rc;
 }

@@ -140,11 +140,9 @@ struct FrameBufs {
     uint32_t *pkey = nullptr, *pval = nullptr, *pkey_alt = nullptr, *pval_alt = nullptr;
     // tiles (capacity cap_tiles)
     uint2 *ranges = nullptr;
-    // pixels (capacity cap_px): final transmittance bits and last contributor of the last render
-    uint2 *px_state = nullptr;
     unsigned long long *work = nullptr;   // 4 counters, see lodgs_frame_work
     bool count_work = false;              // blends tally the work counters (profiling frames)
-    uint64_t cap_sel = 0, cap_pairs = 0, cap_tiles = 0, cap_px = 0;
+    uint64_t cap_sel = 0, cap_pairs = 0, cap_tiles = 0;
     // where the last render left its sorted data
     const uint32_t *order = nullptr;     // selected indices by depth
     const uint32_t *sorted_pval = nullptr;
@@ -198,7 +196,8 @@ int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaSt
 // `k` is the host copy of the view (resolution, grid sizes); kernels read f.d_view
 int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaStream_t st);
 int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, const StageMarks &sm);
-int launch_raster_backward(const CamK &k, FrameBufs &f, const float *dL_dimage, cudaStream_t st);
+int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, const float *dL_dimage,
+                           cudaStream_t st);
 int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows, int dense,
                             cudaStream_t st);
 }  // namespace lodgs

@@ -14,10 +14,11 @@
 // blended), so the neglected tail is at most 1e-4 of the colour.  The support test p >= -4.5 uses
 // explicitly rounded float32 operations (it decides which pixels a Gaussian
 // touches); the alpha, transmittance and colour arithmetic are ordinary fp32.
-// The forward saves each pixel's final transmittance and last contributor;
-// the backward walks the list back to front from them.  Within a tile each
-// warp owns an 8x8 pixel block and skips the Gaussians whose support box
-// misses it (block test, conservative like the tile test).
+// The backward walks each tile's list front to back like the forward,
+// recomputing transmittance per tile (nothing per pixel is stored), and takes
+// the colour behind each Gaussian from the forward's output image.  Within a
+// tile each warp owns an 8x8 pixel block and skips the Gaussians whose support
+// box misses it (block test, conservative like the tile test).
 #include "lodgs_internal.cuh"
 
 namespace lodgs {
@@ -184,9 +185,6 @@ constexpr int NWARP = BNT / 32;
 #define LODGS_BWD_PIX 2      // pixels per lane of the backward blend (2 or 4)
 #endif
 constexpr int BWD_PIX = LODGS_BWD_PIX;
-#ifndef LODGS_G2D_VEC
-#define LODGS_G2D_VEC 1      // 16-byte vector atomics for the per-batch gradient flush
-#endif
 constexpr float BLOCK_HALF = 3.5f;     // half span of an 8x8 block's pixel centres
 constexpr float LOG2E = 1.44269504088896341f;
 
@@ -253,7 +251,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
     k_blend(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval, const float4 *__restrict__ sp_a,
             const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c, const uint32_t *__restrict__ cnt, int W,
-            int H, int TX, const View *__restrict__ view, float *__restrict__ image, uint2 *__restrict__ px_state,
+            int H, int TX, const View *__restrict__ view, float *__restrict__ image,
             unsigned long long *__restrict__ work) {
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
@@ -265,14 +263,13 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
     const int tx0 = (tile % TX) * TILE, ty0 = (tile / TX) * TILE;
     const BlockPix bp = block_pix(tile, TX, tid);
     float yc[PIX], T[PIX], c0[PIX], c1[PIX], c2[PIX];
-    uint32_t last[PIX];
     bool live[PIX];
     bool done = true;
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
         const int py = bp.py0 + 4 * k;
         yc[k] = (float)py + 0.5f;
-        T[k] = 1.0f; c0[k] = c1[k] = c2[k] = 0.f; last[k] = 0;
+        T[k] = 1.0f; c0[k] = c1[k] = c2[k] = 0.f;
         live[k] = bp.px < W && py < H;
         done &= !live[k];
     }
@@ -292,7 +289,6 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
         __syncthreads();
         if (__all_sync(0xffffffffu, done)) continue;
         const int len = warp_list(s_m, n, 1u << bp.w, lane, s_list[bp.w]);
-        const uint32_t rel1 = base - rg.x + 1;
         for (int i = 0; i < len; ++i) {
             const int j = s_list[bp.w][i];
             const float4 a = s_a[j];
@@ -319,7 +315,6 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
                 const float w = alpha * T[k];
                 c0[k] += b.z * w; c1[k] += b.w * w; c2[k] += cb * w;
                 T[k] = T[k] * (1.0f - alpha);
-                last[k] = hit[k] ? rel1 + j : last[k];
                 const bool stop = hit[k] && T[k] < T_MIN;
                 live[k] = live[k] && !stop;
                 died |= stop;
@@ -339,40 +334,39 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
             const size_t o = (size_t)py * W + bp.px;
             float *img = image + o * 3;
             img[0] = c0[k] + T[k] * bg0; img[1] = c1[k] + T[k] * bg1; img[2] = c2[k] + T[k] * bg2;
-            px_state[o] = make_uint2(__float_as_uint(T[k]), last[k]);
         }
     }
     if (COUNT) add_work(work, n_eval, n_blend);
 }
 
-// Backward of the blend, one pass back to front over each tile's list, from the
-// final transmittance and last contributor the forward saved per pixel.  Per
-// pixel and contributing Gaussian i (front-to-back transmittance T_i, colour Q
-// composited behind it, background included, dL/dC = G):
-//   dL/dc_i = G alpha_i T_i,   dL/dalpha_i = T_i G . (c_i - Q),
-// then Q <- Q + alpha_i (c_i - Q) and T_i = T_{i+1} / (1 - alpha_i).  The nine
-// per-Gaussian sums of a warp are reduced in registers and added to shared
-// memory; each batch's sums go to global memory with one atomic per value.
+// Backward of the blend, front to back over each tile's list like the forward,
+// recomputing each pixel's transmittance per tile (nothing per pixel is stored
+// by the forward).  With T_i the transmittance in front of Gaussian i, A_i the
+// colour composited in front of it and C the forward's output (background
+// included), the colour behind i is S_i = C - A_i - c_i alpha_i T_i, and
+//   dL/dc_i = G alpha_i T_i,   dL/dalpha_i = T_i G.c_i - G.S_i / (1 - alpha_i),
+// with G = dL/dC.  Each pixel carries the scalar g = G.(C - A), which drops by
+// alpha_i T_i G.c_i at every contribution, so G.S_i needs no colour sums.  T is
+// rebuilt with the forward's own float operations, so the backward visits
+// exactly the contributions the forward blended and stops where it stopped.  The nine per-Gaussian sums of a warp are reduced in
+// registers and added to shared memory; each batch's sums go to global memory
+// with 16-byte atomics.
 // BP pixels per lane: 2 (a warp per 8x8 block, 128 threads per tile) or 4 (a
-// warp per 8x16 column of two blocks, 64 threads per tile; the per-Gaussian
-// warp sums and list overhead are shared by twice the pixels).
+// warp per 8x16 column of two blocks, 64 threads per tile).
 template <bool COUNT, int BP>
 __global__ void __launch_bounds__(TILE_PIX / BP)
     k_blend_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
                 const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c,
-                const uint32_t *__restrict__ cnt, int W, int H, int TX, const View *__restrict__ view,
-                const uint2 *__restrict__ px_state, const float *__restrict__ dL_dimg, float *__restrict__ g2d,
-                unsigned long long *__restrict__ work) {
+                const uint32_t *__restrict__ cnt, int W, int H, int TX, const float *__restrict__ image,
+                const float *__restrict__ dL_dimg, float *__restrict__ g2d, unsigned long long *__restrict__ work) {
+    constexpr int NT = TILE_PIX / BP, NW = NT / 32;
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
     __shared__ uint32_t s_g[BATCH];
     __shared__ float s_grad[BATCH][9];
     __shared__ uint8_t s_m[BATCH];
-    constexpr int NT = TILE_PIX / BP, NW = NT / 32;
     __shared__ uint8_t s_list[NW][BATCH];
-    __shared__ uint32_t s_end;
     if (cnt[C_STATUS] & ST_CAPACITY) return;
-    const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
     const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     const int tx0 = (tile % TX) * TILE, ty0 = (tile / TX) * TILE;
     const BlockPix bp = block_pix(tile, TX, tid);
@@ -380,40 +374,31 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
     uint32_t wmask = 0;
 #pragma unroll
     for (int k = 0; k < BP; k += 2) wmask |= 1u << (((bp.w >> 1) + k / 2) * 2 + (bp.w & 1));
-    float yc[BP], T[BP], G[BP][3], Q[BP][3];
-    uint32_t last[BP];
-    uint32_t wend = 0;
+    float yc[BP], T[BP], gS[BP], G[BP][3];
+    bool live[BP];
+    bool done = true;
 #pragma unroll
     for (int k = 0; k < BP; ++k) {
         const int py = bp.py0 + 4 * k;
         yc[k] = (float)py + 0.5f;
-        T[k] = 1.0f; last[k] = 0;
-        G[k][0] = G[k][1] = G[k][2] = 0.f;
-        if (bp.px < W && py < H) {
-            const size_t o = (size_t)py * W + bp.px;
-            const uint2 st = px_state[o];
-            T[k] = __uint_as_float(st.x);
-            last[k] = st.y;
-            const float *gi = dL_dimg + o * 3;
-            G[k][0] = gi[0]; G[k][1] = gi[1]; G[k][2] = gi[2];
+        T[k] = 1.0f;
+        live[k] = bp.px < W && py < H;
+        G[k][0] = G[k][1] = G[k][2] = gS[k] = 0.f;
+        if (live[k]) {
+            const size_t o = ((size_t)py * W + bp.px) * 3;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) G[k][ch] = dL_dimg[o + ch];
+            gS[k] = G[k][0] * image[o] + G[k][1] * image[o + 1] + G[k][2] * image[o + 2];   // G.C
         }
-        Q[k][0] = bg0; Q[k][1] = bg1; Q[k][2] = bg2;
-        wend = max(wend, last[k]);
+        done &= !live[k];
     }
-    wend = __reduce_max_sync(0xffffffffu, wend);        // this warp's list end
-    if (tid == 0) s_end = 0;
-    __syncthreads();
-    if (lane == 0 && wend) atomicMax(&s_end, wend);
-    __syncthreads();
-    const uint2 rg = ranges[tile];
-    const uint32_t end = rg.x + s_end;
     uint32_t n_eval = 0, n_contrib = 0;
-    for (uint32_t bend = end; bend > rg.x;) {
-        const uint32_t bstart = bend - rg.x > (uint32_t)BATCH ? bend - BATCH : rg.x;
-        const int n = (int)(bend - bstart);
-        __syncthreads();
+    const uint2 rg = ranges[tile];
+    for (uint32_t base = rg.x; base < rg.y; base += BATCH) {
+        if (__syncthreads_count(done) == NT) break;
+        const int n = min((uint32_t)BATCH, rg.y - base);
         for (int q = tid; q < n; q += NT) {
-            const uint32_t g = pval[bstart + q];
+            const uint32_t g = pval[base + q];
             const float4 a = sp_a[g], c = sp_c[g];
             s_g[q] = g;
             s_a[q] = a;
@@ -424,64 +409,69 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
             for (int v = 0; v < 9; ++v) s_grad[q][v] = 0.f;
         }
         __syncthreads();
-        const uint32_t rel = bstart - rg.x;
-        const int jtop = min(n, (int)wend - (int)rel);     // entries at or past this warp's end are skipped
-        const int len = jtop > 0 ? warp_list(s_m, jtop, wmask, lane, s_list[bp.w]) : 0;
-        for (int i = len - 1; i >= 0; --i) {
-            const int j = s_list[bp.w][i];
-            const float4 a = s_a[j];
-            const float4 b = s_b[j];
-            const uint32_t pos = rel + (uint32_t)j;
-            const float dx = __fsub_rn(a.x, bp.xc);
-            const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
-            float p[BP], dyk[BP];
-            bool hit[BP], any = false;
+        if (!__all_sync(0xffffffffu, done)) {
+            const int len = warp_list(s_m, n, wmask, lane, s_list[bp.w]);
+            for (int i = 0; i < len; ++i) {
+                const int j = s_list[bp.w][i];
+                const float4 a = s_a[j];
+                const float4 b = s_b[j];
+                const float dx = __fsub_rn(a.x, bp.xc);
+                const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
+                float p[BP], dyk[BP];
+                bool hit[BP], any = false;
 #pragma unroll
-            for (int k = 0; k < BP; ++k) {
-                dyk[k] = __fsub_rn(a.y, yc[k]);
-                p[k] = __fmaf_rn(bx, dyk[k], __fmaf_rn(__fmul_rn(b.x, dyk[k]), dyk[k], hxx));
-                hit[k] = pos < last[k] && p[k] >= SUPPORT_P;
-                any |= hit[k];
-            }
-            if (COUNT) n_eval += BP;
-            if (!__any_sync(0xffffffffu, any)) continue;
-            const float cb = s_c[j];
-            const float ax2 = 2.0f * a.z * dx, cy2 = 2.0f * b.x, hdx2 = -0.5f * dx * dx;
-            float gv[9];
+                for (int k = 0; k < BP; ++k) {
+                    dyk[k] = __fsub_rn(a.y, yc[k]);
+                    p[k] = __fmaf_rn(bx, dyk[k], __fmaf_rn(__fmul_rn(b.x, dyk[k]), dyk[k], hxx));
+                    hit[k] = live[k] && p[k] >= SUPPORT_P;
+                    any |= hit[k];
+                }
+                if (COUNT) n_eval += BP;
+                if (!__any_sync(0xffffffffu, any)) continue;
+                const float cb = s_c[j];
+                const float ax2 = 2.0f * a.z * dx, cy2 = 2.0f * b.x, hdx2 = -0.5f * dx * dx;
+                float gv[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) gv[q] = 0.f;
+                for (int q = 0; q < 9; ++q) gv[q] = 0.f;
+                bool died = false;
 #pragma unroll
-            for (int k = 0; k < BP; ++k) {
-                if (hit[k]) {
-                    if (COUNT) ++n_contrib;
-                    const float dy = dyk[k];
-                    const float e = ex2_ftz(p[k] * LOG2E);
-                    const float raw = b.y * e;
-                    const float alpha = fminf(ALPHA_MAX, raw);
-                    const float Tb = T[k] * rcp_ftz(1.0f - alpha);
-                    const float d0 = b.z - Q[k][0], d1 = b.w - Q[k][1], d2 = cb - Q[k][2];
-                    const float dA = (G[k][0] * d0 + G[k][1] * d1 + G[k][2] * d2) * Tb;
-                    const float wgt = alpha * Tb;
-                    gv[6] += G[k][0] * wgt; gv[7] += G[k][1] * wgt; gv[8] += G[k][2] * wgt;
-                    Q[k][0] += alpha * d0; Q[k][1] += alpha * d1; Q[k][2] += alpha * d2;
-                    T[k] = Tb;
-                    if (raw <= ALPHA_MAX) {
-                        const float dp = dA * alpha;
-                        gv[5] += dA * e;
-                        gv[0] += dp * (ax2 + a.w * dy);
-                        gv[1] += dp * (cy2 * dy + bx);
-                        gv[2] += dp * hdx2;
-                        gv[3] -= dp * dx * dy;
-                        gv[4] += -0.5f * dp * dy * dy;
+                for (int k = 0; k < BP; ++k) {
+                    if (hit[k]) {
+                        if (COUNT) ++n_contrib;
+                        const float dy = dyk[k];
+                        const float e = ex2_ftz(p[k] * LOG2E);
+                        const float raw = b.y * e;
+                        const float alpha = fminf(ALPHA_MAX, raw);
+                        const float w = alpha * T[k];
+                        const float gc = G[k][0] * b.z + G[k][1] * b.w + G[k][2] * cb;
+                        gS[k] -= w * gc;                                                  // G.S_i
+                        const float dA = T[k] * gc - rcp_ftz(1.0f - alpha) * gS[k];
+                        gv[6] += G[k][0] * w; gv[7] += G[k][1] * w; gv[8] += G[k][2] * w;
+                        T[k] = T[k] * (1.0f - alpha);                                     // as the forward
+                        if (T[k] < T_MIN) { live[k] = false; died = true; }
+                        if (raw <= ALPHA_MAX) {
+                            const float dp = dA * alpha;
+                            gv[5] += dA * e;
+                            gv[0] += dp * (ax2 + a.w * dy);
+                            gv[1] += dp * (cy2 * dy + bx);
+                            gv[2] += dp * hdx2;
+                            gv[3] -= dp * dx * dy;
+                            gv[4] += -0.5f * dp * dy * dy;
+                        }
                     }
                 }
+                warp_sum9_to_smem(gv, lane, s_grad[j]);
+                if (__any_sync(0xffffffffu, died)) {
+                    done = true;
+#pragma unroll
+                    for (int k = 0; k < BP; ++k) done &= !live[k];
+                    if (__all_sync(0xffffffffu, done)) break;
+                }
             }
-            warp_sum9_to_smem(gv, lane, s_grad[j]);
         }
         __syncthreads();
         for (int q = tid; q < n; q += NT) {
             float *o = g2d + (size_t)s_g[q] * G2D_STRIDE;
-#if LODGS_G2D_VEC
             const float4 x0 = make_float4(s_grad[q][0], s_grad[q][1], s_grad[q][2], s_grad[q][3]);
             const float4 x1 = make_float4(s_grad[q][4], s_grad[q][5], s_grad[q][6], s_grad[q][7]);
             if (x0.x != 0.f || x0.y != 0.f || x0.z != 0.f || x0.w != 0.f)
@@ -489,15 +479,7 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
             if (x1.x != 0.f || x1.y != 0.f || x1.z != 0.f || x1.w != 0.f)
                 atomicAdd(reinterpret_cast<float4 *>(o + 4), x1);
             if (s_grad[q][8] != 0.f) atomicAdd(o + 8, s_grad[q][8]);
-#else
-#pragma unroll
-            for (int v = 0; v < 9; ++v) {
-                const float x = s_grad[q][v];
-                if (x != 0.f) atomicAdd(o + v, x);
-            }
-#endif
         }
-        bend = bstart;
     }
     if (COUNT) add_work(work + 2, n_eval, n_contrib);
 }
@@ -541,20 +523,20 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
     k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, (uint32_t)n_tiles, f.ranges);
     count_launches(1);
     (f.count_work ? k_blend<true> : k_blend<false>)<<<(unsigned)n_tiles, BNT, 0, st>>>(
-        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.px_state, f.work);
+        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work);
     count_launches(1);
     sm.mark(LODGS_STAGE_BLEND, 1, st);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
 }
 
-int launch_raster_backward(const CamK &k, FrameBufs &f, const float *dL_dimage, cudaStream_t st) {
+int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, const float *dL_dimage,
+                           cudaStream_t st) {
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * G2D_STRIDE * sizeof(float), st));
     LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
     (f.count_work ? k_blend_bwd<true, BWD_PIX> : k_blend_bwd<false, BWD_PIX>)<<<(unsigned)n_tiles, TILE_PIX / BWD_PIX, 0, st>>>(
-        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, f.px_state, dL_dimage,
-        f.g2d, f.work);
+        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, dL_dimage, f.g2d, f.work);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
