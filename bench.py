@@ -380,7 +380,7 @@ def run_lodgs(args, rank: int, world: int):
 OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB = 6, 11, 34
 # DRAM bytes (read + write) per k_blend_bwd launch, mean over the 32 views of
 # this workload, from one ncu capture (profiles/launches_fwd_bwd_1080p_2Mleaves.md)
-BLEND_BWD_DRAM_BYTES = 49.5e6
+BLEND_BWD_DRAM_BYTES = 57.9e6
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 
