@@ -156,12 +156,12 @@ def stage_bytes(stage: str, st: dict, record_bytes: int, n_upper: int, tile_pass
         return 32.0 * n_upper + 8.0 * scanned + 4.0 * ns
     if stage == "project":
         return (record_bytes + 56.0) * ns
-    if stage == "depth_sort":
-        return 4 * 20.0 * ns
-    if stage == "emit":
-        return 40.0 * ns + 8.0 * npair
-    if stage == "tile_sort":
-        return tile_passes * 20.0 * npair
+    if stage == "count":          # area scan (4 B read, 4 B written, twice), rect reads, tile counters
+        return 16.0 * ns + 40.0 * nv + 4.0 * npair
+    if stage == "emit":           # rect reads again + 8 B written per kept pair
+        return 40.0 * nv + 8.0 * npair
+    if stage == "tile_sort":      # kept pairs read (key + index) and indices written back
+        return 12.0 * npair
     if stage == "project_bwd":
         return (record_bytes + 36.0 + record_bytes) * ns
     return 0.0

@@ -299,10 +299,10 @@ int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);
 /* Stages timed by lodgs_frame_stage_ms, in order. */
 #define LODGS_STAGE_SELECT 0      /* upper-hierarchy BFS cut + SPT interval test and compaction */
 #define LODGS_STAGE_PROJECT 1     /* gather + EWA projection + SH colour */
-#define LODGS_STAGE_DEPTH_SORT 2  /* stable radix sort of the depth keys */
-#define LODGS_STAGE_EMIT 3        /* tile-count scan and (tile, Gaussian) pair emission */
-#define LODGS_STAGE_TILE_SORT 4   /* stable radix sort of the pairs by tile */
-#define LODGS_STAGE_BLEND 5       /* tile ranges + front-to-back blending */
+#define LODGS_STAGE_COUNT 2       /* per tile: pair scan, tile test, counts, ranges; global: depth sort */
+#define LODGS_STAGE_EMIT 3        /* per tile: scatter into tiles; global: pair emission in depth order */
+#define LODGS_STAGE_TILE_SORT 4   /* per tile: sort of each tile's list; global: radix sort by tile + ranges */
+#define LODGS_STAGE_BLEND 5       /* front-to-back blending */
 #define LODGS_STAGE_BLEND_BWD 6   /* backward of the blend (per-tile recomputation) */
 #define LODGS_STAGE_PROJECT_BWD 7 /* backward of the projection + gradient rows */
 #define LODGS_NUM_STAGES 8
@@ -314,6 +314,22 @@ int lodgs_frame_set_profiling(lodgs_frame *frame, int on);
  * on this frame (LODGS_NUM_STAGES floats; 0 for stages that did not run since
  * the last select).  Blocks until the frame's stream is idle. */
 int lodgs_frame_stage_ms(lodgs_frame *frame, float *ms);
+
+/*
+ * How lodgs_render puts the (tile, Gaussian) pairs in (tile, depth key,
+ * selected index) order -- the result is the same either way:
+ *   LODGS_ORDER_PER_TILE  pairs counted and scattered per tile, each tile's list
+ *                         sorted by one block (few launches; best for short lists)
+ *   LODGS_ORDER_GLOBAL    stable radix sort of the selection by depth, pairs
+ *                         emitted in that order, stable radix sort by tile
+ *                         (best for long tile lists)
+ *   LODGS_ORDER_AUTO      per tile while the frame's pair workspace averages at
+ *                         most 1024 pairs per tile, global beyond (default)
+ */
+#define LODGS_ORDER_AUTO 0
+#define LODGS_ORDER_PER_TILE 1
+#define LODGS_ORDER_GLOBAL 2
+int lodgs_frame_set_ordering(lodgs_frame *frame, int mode);
 
 /* Pixel-Gaussian work of the last render/backward on this frame (4 uint64):
  * [0] forward support tests evaluated, [1] forward blends (alpha composited),

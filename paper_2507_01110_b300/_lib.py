@@ -18,7 +18,7 @@ LODGS_E_CUDA = -3
 LODGS_E_TIMEOUT = -4
 LODGS_E_STATE = -5
 LODGS_E_CAPACITY = -6
-STAGES = ("select", "project", "depth_sort", "emit", "tile_sort", "blend", "blend_bwd", "project_bwd")
+STAGES = ("select", "project", "count", "emit", "tile_sort", "blend", "blend_bwd", "project_bwd")
 _NAMES = {-1: "INVALID", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", -6: "CAPACITY"}
 
 
@@ -88,6 +88,7 @@ _SIGS = {
     "lodgs_render_backward_blend": (C.c_int, [_P, _P, _P, _P, _P]),
     "lodgs_render_backward_project": (C.c_int, [_P, _P, _P, _P, C.c_int, _P]),
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
+    "lodgs_frame_set_ordering": (C.c_int, [_P, C.c_int]),
     "lodgs_accumulate_grads": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, C.c_int64, _P, _P]),
     "lodgs_l1_loss_grad": (C.c_int, [_P, _P, C.c_int64, C.c_float, _P, _P, _P]),
     "lodgs_frame_export": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),

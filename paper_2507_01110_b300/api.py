@@ -132,6 +132,12 @@ class Frame:
             return torch.zeros(0, dtype=torch.int64, device="cuda")
         return _device_view(p.value, (int(n.value),), "<u4").to(torch.int64)
 
+    ORDER_AUTO, ORDER_PER_TILE, ORDER_GLOBAL = 0, 1, 2
+
+    def set_ordering(self, mode: int) -> None:
+        """How renders order the (tile, Gaussian) pairs: Frame.ORDER_* (same result)."""
+        check(lib().lodgs_frame_set_ordering(self._h, C.c_int(int(mode))))
+
     def set_profiling(self, on=True) -> None:
         """True: time every stage; False: none; a list of stage names: those."""
         if on is True:

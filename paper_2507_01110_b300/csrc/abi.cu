@@ -87,7 +87,7 @@ int ensure_sel(lodgs_frame *fr, uint64_t want) {
     c = f.cap_sel;                                    \
     if (int r_ = grow(ptr, c, want, per)) return r_;
     G1(f.sp_a, 1) G1(f.sp_b, 1) G1(f.sp_c, 1) G1(f.dkey, 1) G1(f.dval, 1) G1(f.dkey_alt, 1) G1(f.dval_alt, 1)
-    G1(f.rect, 1) G1(f.ntiles, 1) G1(f.nt_sorted, 1) G1(f.pair_off, 1) G1(f.g2d, G2D_STRIDE)
+    G1(f.rect, 1) G1(f.ntiles, 1) G1(f.pair_off, 1) G1(f.g2d, G2D_STRIDE)
 #undef G1
     f.cap_sel = want;
     return LODGS_OK;
@@ -101,6 +101,7 @@ int ensure_pairs(lodgs_frame *fr, uint64_t want) {
     uint64_t c;
     c = f.cap_pairs; if (int r = grow(f.pkey, c, want)) return r;
     c = f.cap_pairs; if (int r = grow(f.pval, c, want)) return r;
+    c = f.cap_pairs; if (int r = grow(f.pscratch, c, want)) return r;
     c = f.cap_pairs; if (int r = grow(f.pkey_alt, c, want)) return r;
     c = f.cap_pairs; if (int r = grow(f.pval_alt, c, want)) return r;
     f.cap_pairs = want;
@@ -110,7 +111,8 @@ int ensure_pairs(lodgs_frame *fr, uint64_t want) {
 void free_frame_bufs(FrameBufs &f) {
     void *ps[] = {f.cnt, f.d_view, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
                   f.sort_hist, f.sp_a, f.sp_b, f.sp_c, f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.rect, f.ntiles,
-                  f.nt_sorted, f.pair_off, f.g2d, f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.ranges, f.work,
+                  f.pair_off, f.g2d, f.pkey, f.pval, f.pscratch, f.pkey_alt, f.pval_alt, f.ranges, f.tile_cnt,
+                  f.work,
                   f.sel_src, f.emit_src};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -321,9 +323,13 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     if (int r = ensure_sel(fr, fr->want_sel)) return r;
     if (int r = ensure_pairs(fr, fr->want_pairs)) return r;
     uint64_t n_tiles = (uint64_t)fr->k.TX * fr->k.TY;
-    uint64_t c = fr->f.cap_tiles;
-    if (int r = grow(fr->f.ranges, c, n_tiles)) return r;
-    fr->f.cap_tiles = c;
+    if (n_tiles > fr->f.cap_tiles || !fr->f.ranges) {
+        uint64_t c = fr->f.cap_tiles, c2 = fr->f.cap_tiles;
+        if (int r = grow(fr->f.ranges, c, n_tiles)) return r;
+        if (int r = grow(fr->f.tile_cnt, c2, n_tiles)) return r;
+        LODGS_CUDA(cudaMemsetAsync(fr->f.tile_cnt, 0, n_tiles * sizeof(uint32_t), st));   // zero between renders
+        fr->f.cap_tiles = c;
+    }
     if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2]))
         if (int r = set_view(fr, nullptr, bg, st)) return r;
     fr->f.count_work = fr->prof_mask != 0;
@@ -340,7 +346,7 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     StageMarks sm{fr->prof_mask ? fr->ev : nullptr, fr->prof_mask};
     rc = launch_raster(fr->k, fr->f, image, st, sm);
     if (rc) return rc;
-    for (int s2 = LODGS_STAGE_DEPTH_SORT; s2 <= LODGS_STAGE_BLEND; ++s2)
+    for (int s2 = LODGS_STAGE_COUNT; s2 <= LODGS_STAGE_BLEND; ++s2)
         if (fr->prof_mask >> s2 & 1u) fr->ran[s2] = true;
     LODGS_CUDA(cudaMemcpyAsync(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost, st));
     fr->rendered = true;
@@ -435,10 +441,19 @@ int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {
     if (h[C_STATUS] & ST_TIMEOUT) s->status = LODGS_E_TIMEOUT;
     if (h[C_STATUS] & ST_CAPACITY) {
         s->status = LODGS_E_CAPACITY;
-        uint64_t ns = h[C_NSEL], np = h[C_NPAIR];
+        uint64_t ns = h[C_NSEL], np = h[C_NKEPT_WANT];
         if (ns > fr->f.cap_sel) fr->want_sel = std::max<uint64_t>(fr->want_sel, ns + ns / 4);
         else if (np > fr->f.cap_pairs) fr->want_pairs = std::max<uint64_t>(fr->want_pairs, np + np / 4);
     }
+    return LODGS_OK;
+}
+
+int lodgs_frame_set_ordering(lodgs_frame *fr, int mode) {
+    if (!fr || mode < ORDER_AUTO || mode > ORDER_GLOBAL) {
+        set_error("frame_set_ordering: NULL frame or mode not in 0..2");
+        return LODGS_E_INVALID;
+    }
+    fr->f.ordering = mode;
     return LODGS_OK;
 }
 
@@ -496,13 +511,15 @@ int lodgs_frame_export(lodgs_frame *fr, uint32_t *pair_index, int64_t cap_pairs,
         }
     }
     if (depth_key && ns) {
-        // the depth sort permuted the keys: undo the permutation with the sorted order
-        const uint32_t *order = fr->f.order;
-        const uint32_t *skeys = order == fr->f.dval ? fr->f.dkey : fr->f.dkey_alt;
-        std::vector<uint32_t> o(ns), kk(ns);
-        LODGS_CUDA(cudaMemcpy(o.data(), order, ns * 4, cudaMemcpyDeviceToHost));
-        LODGS_CUDA(cudaMemcpy(kk.data(), skeys, ns * 4, cudaMemcpyDeviceToHost));
-        for (uint64_t r = 0; r < ns; ++r) depth_key[o[r]] = kk[r];
+        if (!fr->f.order) {
+            LODGS_CUDA(cudaMemcpy(depth_key, fr->f.dkey, ns * 4, cudaMemcpyDeviceToHost));
+        } else {     // the global ordering's depth sort permuted the keys: undo it with the sorted order
+            const uint32_t *skeys = fr->f.order == fr->f.dval ? fr->f.dkey : fr->f.dkey_alt;
+            std::vector<uint32_t> o(ns), kk(ns);
+            LODGS_CUDA(cudaMemcpy(o.data(), fr->f.order, ns * 4, cudaMemcpyDeviceToHost));
+            LODGS_CUDA(cudaMemcpy(kk.data(), skeys, ns * 4, cudaMemcpyDeviceToHost));
+            for (uint64_t r = 0; r < ns; ++r) depth_key[o[r]] = kk[r];
+        }
     }
     return LODGS_OK;
 }

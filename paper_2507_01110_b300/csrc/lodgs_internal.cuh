@@ -74,11 +74,13 @@ enum {
     C_WORK = 3,      // SPT entries scanned (sum of the prefixes)
     C_NSPTSEL = 4,   // SPT entries selected
     C_NSEL_EFF = 5,  // selected nodes processed by the render (0 on overflow)
-    C_NPAIR = 6,     // (Gaussian, tile) pairs
-    C_NPAIR_EFF = 7, // pairs processed (0 on overflow)
+    C_NPAIR = 6,     // (Gaussian, tile) rectangle pairs
+    C_NPAIR_EFF = 7, // rectangle pairs emitted by the global ordering (0 on overflow)
     C_NVIS = 8,      // visible Gaussians
     C_STATUS = 9,    // ST_* bits
-    C_NKEPT = 10,    // pairs kept by the tile support test (sorted first)
+    C_NKEPT = 10,    // pairs kept by the tile support test
+    C_NKEPT_WANT = 11, // kept pairs counted before the capacity check (workspace growth)
+    C_NPAIR64 = 12,  // words 12-13: rectangle pairs as a 64-bit sum (32-bit index guard)
     C_COUNT = 16
 };
 
@@ -115,6 +117,8 @@ struct lodgs_scene {
 namespace lodgs {
 
 // Device buffers of one frame (one view).  Capacities are element counts.
+enum : int { ORDER_AUTO = 0, ORDER_PER_TILE = 1, ORDER_GLOBAL = 2 };
+
 // floats per Gaussian of the 2D gradient rows (9 used; 16-byte aligned rows)
 constexpr int G2D_STRIDE = 12;
 
@@ -132,20 +136,24 @@ struct FrameBufs {
     float4 *sp_a = nullptr;          // u, v, -A/2, -B        (mean in pixels, scaled conic)
     float4 *sp_b = nullptr;          // -C/2, opacity, r, g
     float4 *sp_c = nullptr;          // b, rx, ry, 0   (rx, ry: support half extents, block test)
-    uint32_t *dkey = nullptr, *dval = nullptr, *dkey_alt = nullptr, *dval_alt = nullptr;
+    uint32_t *dkey = nullptr;        // float32 bits of the view depth (0xffffffff if invisible)
+    uint32_t *dval = nullptr, *dkey_alt = nullptr, *dval_alt = nullptr;   // global ordering: depth sort
     uint2 *rect = nullptr;           // x0 | y0 << 16, x1 | y1 << 16
-    uint32_t *ntiles = nullptr, *nt_sorted = nullptr, *pair_off = nullptr;
+    uint32_t *ntiles = nullptr, *pair_off = nullptr;
     float *g2d = nullptr;            // G2D_STRIDE per selected: d/d(u, v, A, B, C, opacity, r, g, b), 3 unused
     // pairs (capacity cap_pairs)
-    uint32_t *pkey = nullptr, *pval = nullptr, *pkey_alt = nullptr, *pval_alt = nullptr;
+    uint32_t *pkey = nullptr, *pval = nullptr;   // pairs: depth key / tile key, selected index
+    uint32_t *pkey_alt = nullptr, *pval_alt = nullptr;   // global ordering: tile sort
+    unsigned long long *pscratch = nullptr;      // merge scratch of the per-tile sort (long lists)
     // tiles (capacity cap_tiles)
     uint2 *ranges = nullptr;
+    uint32_t *tile_cnt = nullptr;     // kept pairs per tile, then scatter cursors; zero between renders
     unsigned long long *work = nullptr;   // 4 counters, see lodgs_frame_work
     bool count_work = false;              // blends tally the work counters (profiling frames)
+    int ordering = 0;                     // ORDER_*: how pairs are put in (tile, depth, index) order
+    const uint32_t *order = nullptr;      // global ordering: selected indices by depth
+    const uint32_t *sorted_pval = nullptr;   // selected index of each ordered pair
     uint64_t cap_sel = 0, cap_pairs = 0, cap_tiles = 0;
-    // where the last render left its sorted data
-    const uint32_t *order = nullptr;     // selected indices by depth
-    const uint32_t *sorted_pval = nullptr;
 };
 
 void set_error(const std::string &msg);
@@ -168,7 +176,10 @@ struct SortWork {
     uint32_t *hist = nullptr;       // RADIX * grid
     size_t hist_cap = 0;
 };
-constexpr int SORT_GRID = 296;      // 2 blocks per SM on 148 SMs
+#ifndef LODGS_SORT_GRID
+#define LODGS_SORT_GRID 296
+#endif
+constexpr int SORT_GRID = LODGS_SORT_GRID;   // radix sort blocks (2 per SM on 148 SMs)
 constexpr int SORT_HIST = 256 * (SORT_GRID + 1);   // histogram table + digit totals
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                      const uint32_t *d_n, uint32_t max_n, int begin_bit, int end_bit, uint32_t *hist,

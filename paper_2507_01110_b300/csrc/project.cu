@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
     constexpr int degree = DEG;
     constexpr int K = (DEG + 1) * (DEG + 1) - 1;
     uint32_t nvis = 0;
+    unsigned long long npairs = 0;
     for (uint32_t i = blockIdx.x * PB + threadIdx.x; i < n; i += gridDim.x * PB) {
         const float *r = rows + (size_t)sel_rows[i] * stride;
         float4 r0 = *reinterpret_cast<const float4 *>(r);        // mu, s0
@@ -235,10 +236,15 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
         dkey[i] = key; dval[i] = i;
         rect[i] = rc; ntiles[i] = nt;
         nvis += vis ? 1u : 0u;
+        npairs += nt;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nvis += __shfl_xor_sync(0xffffffffu, nvis, o);
     if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(&cnt[C_NVIS], nvis);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    if ((threadIdx.x & 31) == 0 && npairs)     // rectangle pairs as a 64-bit sum (32-bit index guard)
+        atomicAdd(reinterpret_cast<unsigned long long *>(cnt + C_NPAIR64), npairs);
 }
 
 // Floats per record of SH degree DEG (14 base values + 3 per SH coefficient,

@@ -1,12 +1,17 @@
 // a5-a8: tile x depth ordering and per-tile front-to-back compositing (Eq. 1-2)
 // with its backward.
 //
-// Ordering is done depth-first: the selected Gaussians are stably sorted once
-// by their float32 depth key (ties keep ascending selection order), the
-// (tile, Gaussian) pairs are emitted in that order, and a stable radix sort on
-// the tile id alone groups them by tile.  The result is the (tile, depth,
-// index) order of a full-key sort at a fraction of its passes, because pairs
-// outnumber Gaussians.
+// Ordering is done per tile: the (Gaussian, tile) pairs of the selection's tile
+// rectangles are enumerated flat, the tile support test drops pairs whose tile
+// the ellipse cannot reach, the kept pairs are counted per tile, the counts are
+// scanned into tile ranges, the pairs are scattered into their tiles, and one
+// block per tile sorts its short list by (depth key, selected index).  The
+// result is the (tile, depth, index) order of a full-key sort, in six launches
+// instead of a global multi-pass radix sort.  Frames dense enough to have long
+// tile lists (a pair workspace of more than 1024 pairs per tile on average)
+// take the global route instead: the selected Gaussians are stably sorted by
+// depth key, the pairs are emitted in that order, and a stable radix sort on the
+// tile id groups them by tile -- the same order.
 //
 // Blending runs one 128-thread CTA per 16x16 tile; batches of the tile's
 // Gaussians are staged in shared memory.  Eq. 1 is truncated once a pixel's
@@ -56,6 +61,7 @@ __device__ __forceinline__ bool tile_keep(float u, float v, float A, float B, fl
     return best >= -4.51f;
 }
 
+// ---- global ordering (large frames): depth sort, emission, tile sort ----
 // One thread per rectangle pair: pair p belongs to the last depth rank r with
 // pair_off[r] <= p (binary search) and is the k-th tile of its rectangle in
 // row-major order.  Pairs whose tile the support ellipse cannot reach get the
@@ -70,6 +76,7 @@ __global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restri
     if (over) P = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         cnt[C_NPAIR_EFF] = P;
+        cnt[C_NKEPT_WANT] = cnt[C_NPAIR];           // all rectangle pairs are stored on this path
         if (over) atomicOr(&cnt[C_STATUS], ST_CAPACITY);
     }
     const uint32_t n = cnt[C_NSEL_EFF];
@@ -104,6 +111,263 @@ __global__ void k_ranges(const uint32_t *__restrict__ pkey, uint32_t *__restrict
             if (p + 1 == n || pkey[p + 1] >= n_tiles) cnt[C_NKEPT] = p + 1;
         }
     }
+}
+
+// ---- per-tile ordering ----
+// Rectangle pairs are enumerated flat: pair p belongs to the last selected
+// Gaussian g with pair_off[g] <= p (binary search over the scan of the
+// rectangle areas, selection order) and is the k-th tile of its rectangle in
+// row-major order.  Returns the tile of the pair, or -1 when the tile support
+// test drops it.
+__device__ __forceinline__ int64_t rect_pair(uint32_t p, uint32_t n, const uint32_t *__restrict__ pair_off,
+                                             const uint2 *__restrict__ rect, const float4 *__restrict__ sp_a,
+                                             const float4 *__restrict__ sp_b, int TX, uint32_t &g) {
+    uint32_t a = 0, b = n;
+    while (b - a > 1) {
+        const uint32_t m = (a + b) >> 1;
+        if (pair_off[m] <= p) a = m; else b = m;
+    }
+    g = a;
+    const uint2 rc = rect[g];
+    const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+    const uint32_t w = x1 - x0, k = p - pair_off[g];
+    const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+    const float4 sa = sp_a[g];
+    const float nhc = sp_b[g].x;
+    if (!tile_keep(sa.x, sa.y, -2.0f * sa.z, -sa.w, -2.0f * nhc, tx, ty)) return -1;
+    return (int64_t)ty * TX + tx;
+}
+
+// Count the kept pairs of every tile (one atomic per group of equal tiles in a warp).
+__global__ void __launch_bounds__(RB) k_emit_count(const uint32_t *__restrict__ pair_off,
+                                                   const uint2 *__restrict__ rect, const float4 *__restrict__ sp_a,
+                                                   const float4 *__restrict__ sp_b, uint32_t *__restrict__ cnt,
+                                                   int TX, uint32_t *__restrict__ tile_cnt) {
+    if (cnt[C_STATUS] & ST_CAPACITY) return;
+    if (*reinterpret_cast<const unsigned long long *>(cnt + C_NPAIR64) > 0xffffffffull) {   // 32-bit pair indices
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr((uint32_t *)&cnt[C_STATUS], ST_CAPACITY);
+        return;
+    }
+    const uint32_t P = cnt[C_NPAIR], n = cnt[C_NSEL_EFF];
+    const int lane = threadIdx.x & 31;
+    // whole warps step together so that the match below sees every lane
+    for (uint32_t p0 = (blockIdx.x * RB + threadIdx.x) & ~31u; p0 < P; p0 += gridDim.x * RB) {
+        const uint32_t p = p0 + lane;
+        uint32_t g;
+        const int64_t t = p < P ? rect_pair(p, n, pair_off, rect, sp_a, sp_b, TX, g) : -1;
+        const uint32_t key = t < 0 ? 0xffffffffu : (uint32_t)t;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        if (t >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&tile_cnt[t], (uint32_t)__popc(peers));
+    }
+}
+
+// One block: exclusive scan of the tile counts.  Writes the tile ranges, turns
+// the counts into scatter cursors (the tile's first slot) and records the kept
+// pair total, flagging a capacity error when it exceeds the pair buffers.
+constexpr int TO_THREADS = 1024;
+__global__ void __launch_bounds__(TO_THREADS) k_tile_offsets(uint32_t *__restrict__ tile_cnt, uint32_t n_tiles,
+                                                             uint64_t cap_pairs, uint32_t *__restrict__ cnt,
+                                                             uint2 *__restrict__ ranges) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < n_tiles; base += TO_THREADS) {
+        const uint32_t t = base + tid;
+        const uint32_t v = t < n_tiles ? tile_cnt[t] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const unsigned long long off = s_carry + (warp ? s_warp[warp - 1] : 0u) + x - v;
+        if (t < n_tiles) {
+            const uint32_t o32 = off > 0xffffffffull ? 0xffffffffu : (uint32_t)off;
+            ranges[t] = make_uint2(o32, o32 + v);
+            tile_cnt[t] = o32;
+        }
+        __syncthreads();
+        if (tid == 0) s_carry += s_warp[31];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const unsigned long long total = s_carry;
+        cnt[C_NKEPT_WANT] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+        if (total > cap_pairs) {                     // kept pairs beyond the workspace: capacity error
+            atomicOr(&cnt[C_STATUS], ST_CAPACITY);
+            cnt[C_NKEPT] = 0;
+        } else {
+            cnt[C_NKEPT] = (uint32_t)total;
+        }
+    }
+}
+
+// Scatter the kept pairs into their tiles' slots (in any order within a tile:
+// the per-tile sort fixes it): depth key and selected index.
+__global__ void __launch_bounds__(RB) k_emit_scatter(const uint32_t *__restrict__ pair_off,
+                                                     const uint2 *__restrict__ rect, const float4 *__restrict__ sp_a,
+                                                     const float4 *__restrict__ sp_b,
+                                                     const uint32_t *__restrict__ dkey, const uint32_t *__restrict__ cnt,
+                                                     int TX, uint32_t *__restrict__ cursor, uint32_t *__restrict__ pkey,
+                                                     uint32_t *__restrict__ pval) {
+    if (cnt[C_STATUS] & ST_CAPACITY) return;
+    const uint32_t P = cnt[C_NPAIR], n = cnt[C_NSEL_EFF];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t p0 = (blockIdx.x * RB + threadIdx.x) & ~31u; p0 < P; p0 += gridDim.x * RB) {
+        const uint32_t p = p0 + lane;
+        uint32_t g = 0;
+        const int64_t t = p < P ? rect_pair(p, n, pair_off, rect, sp_a, sp_b, TX, g) : -1;
+        const uint32_t key = t < 0 ? 0xffffffffu : (uint32_t)t;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t slot = 0;
+        if (t >= 0 && lane == leader) slot = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
+        slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(peers & ((1u << lane) - 1u));
+        if (t >= 0) {
+            pkey[slot] = dkey[g];
+            pval[slot] = g;
+        }
+    }
+}
+
+// One block per tile: sort the tile's pairs by (depth key, selected index) --
+// the order of the (tile, depth, index) sort -- and leave the indices in pval.
+// Up to TS_RANK pairs: rank by counting (one pass, no barriers); up to TS_SMEM:
+// a bitonic network in shared memory, whose comparators always put the
+// smaller key at the lower index (a flip stage, then half-cleaners), so
+// positions past the list end act as +infinity and need no storage.  Longer
+// lists: TS_SMEM-sized chunks sorted that way, then merged pairwise (each merge
+// split evenly over the block's threads along its merge path), alternating
+// between the pair arrays and a 64-bit scratch array.  The block also clears
+// the tile's counter for the next render.
+constexpr int TS_THREADS = 256, TS_RANK = 256, TS_SMEM = 2048;
+
+// a tile's keys, held either as 64-bit words or split over the pair arrays
+struct TileKeys {
+    uint32_t *K, *V;                  // split: depth key (high word), selected index (low word)
+    unsigned long long *S;            // or whole keys
+    __device__ __forceinline__ unsigned long long get(uint32_t i) const {
+        return S ? S[i] : ((unsigned long long)K[i] << 32 | V[i]);
+    }
+    __device__ __forceinline__ void put(uint32_t i, unsigned long long v) const {
+        if (S) S[i] = v;
+        else { K[i] = (uint32_t)(v >> 32); V[i] = (uint32_t)v; }
+    }
+};
+
+template <typename Load, typename Store>
+__device__ __forceinline__ void bitonic_sort(uint32_t L, Load load, Store store) {
+    uint32_t N = 1;
+    while (N < L) N <<= 1;
+    for (uint32_t k = 2; k <= N; k <<= 1) {
+        for (uint32_t c = threadIdx.x; c < N / 2; c += TS_THREADS) {      // flip: i against its mirror in the block
+            const uint32_t h = k >> 1, i = (c / h) * k + (c % h), j = (c / h) * k + (k - 1 - (c % h));
+            if (j < L) {
+                const unsigned long long a = load(i), b = load(j);
+                if (a > b) { store(i, b); store(j, a); }
+            }
+        }
+        __syncthreads();
+        for (uint32_t st = k >> 2; st >= 1; st >>= 1) {                    // half-cleaners
+            for (uint32_t c = threadIdx.x; c < N / 2; c += TS_THREADS) {
+                const uint32_t i = (c / st) * 2 * st + (c % st), j = i + st;
+                if (j < L) {
+                    const unsigned long long a = load(i), b = load(j);
+                    if (a > b) { store(i, b); store(j, a); }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Merge the sorted runs src[a0, a1) and src[a1, a2) into dst[a0, a2) with the
+// whole block: thread t writes outputs [t n / T, (t + 1) n / T) after locating
+// its start on the merge path by binary search (keys are distinct).
+__device__ void merge_runs(const TileKeys &src, const TileKeys &dst, uint32_t a0, uint32_t a1, uint32_t a2) {
+    const uint32_t na = a1 - a0, nb = a2 - a1, n = na + nb;
+    const uint32_t d0 = (uint32_t)((uint64_t)n * threadIdx.x / TS_THREADS);
+    const uint32_t d1 = (uint32_t)((uint64_t)n * (threadIdx.x + 1) / TS_THREADS);
+    if (d0 == d1) return;
+    // i = number of A elements among the first d0 outputs
+    uint32_t lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
+    while (lo < hi) {
+        const uint32_t i = (lo + hi) >> 1;                      // is A[i] before B[d0 - i - 1]?
+        if (src.get(a0 + i) < src.get(a1 + d0 - i - 1)) lo = i + 1; else hi = i;
+    }
+    uint32_t i = lo, j = d0 - lo;
+    for (uint32_t d = d0; d < d1; ++d) {
+        const bool takeA = j >= nb || (i < na && src.get(a0 + i) < src.get(a1 + j));
+        dst.put(a0 + d, takeA ? src.get(a0 + i++) : src.get(a1 + j++));
+    }
+}
+
+__global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint2 *__restrict__ ranges,
+                                                          uint32_t *__restrict__ tile_cnt,
+                                                          const uint32_t *__restrict__ cnt, uint32_t *pkey,
+                                                          uint32_t *pval, unsigned long long *scratch) {
+    __shared__ unsigned long long s_k[TS_SMEM];
+    const uint32_t t = blockIdx.x;
+    if (threadIdx.x == 0) tile_cnt[t] = 0;               // counters start at zero for the next render
+    if (cnt[C_STATUS] & ST_CAPACITY) return;
+    const uint2 rg = ranges[t];
+    const uint32_t L = rg.y - rg.x;
+    if (L <= 1) return;
+    uint32_t *K = pkey + rg.x, *V = pval + rg.x;
+    const TileKeys split{K, V, nullptr}, whole{nullptr, nullptr, scratch + rg.x};
+    if (L <= TS_SMEM) {
+        for (uint32_t i = threadIdx.x; i < L; i += TS_THREADS) s_k[i] = split.get(i);
+        __syncthreads();
+        if (L <= TS_RANK) {                              // keys are distinct (indices are)
+            if (threadIdx.x < L) {
+                const unsigned long long me = s_k[threadIdx.x];
+                uint32_t r = 0;
+                for (uint32_t j = 0; j < L; ++j) r += s_k[j] < me;
+                V[r] = (uint32_t)me;
+            }
+            return;
+        }
+        bitonic_sort(L, [&](uint32_t i) { return s_k[i]; },
+                     [&](uint32_t i, unsigned long long v) { s_k[i] = v; });
+        for (uint32_t i = threadIdx.x; i < L; i += TS_THREADS) V[i] = (uint32_t)s_k[i];
+        return;
+    }
+    // long list: sorted chunks into the scratch array, then merge passes
+    for (uint32_t c0 = 0; c0 < L; c0 += TS_SMEM) {
+        const uint32_t Lc = min((uint32_t)TS_SMEM, L - c0);
+        for (uint32_t i = threadIdx.x; i < Lc; i += TS_THREADS) s_k[i] = split.get(c0 + i);
+        __syncthreads();
+        bitonic_sort(Lc, [&](uint32_t i) { return s_k[i]; },
+                     [&](uint32_t i, unsigned long long v) { s_k[i] = v; });
+        for (uint32_t i = threadIdx.x; i < Lc; i += TS_THREADS) whole.put(c0 + i, s_k[i]);
+        __syncthreads();
+    }
+    bool in_whole = true;
+    for (uint32_t w = TS_SMEM; w < L; w <<= 1) {
+        const TileKeys &src = in_whole ? whole : split, &dst = in_whole ? split : whole;
+        for (uint32_t a0 = 0; a0 < L; a0 += 2 * w) {
+            const uint32_t a1 = min(a0 + w, L), a2 = min(a0 + 2 * w, L);
+            merge_runs(src, dst, a0, a1, a2);           // a lone last run is copied
+        }
+        __syncthreads();
+        in_whole = !in_whole;
+    }
+    if (in_whole)
+        for (uint32_t i = threadIdx.x; i < L; i += TS_THREADS) V[i] = (uint32_t)whole.get(i);
 }
 
 // The support exponent p = -1/2 d^T Q d (d = mean - pixel centre) decides which
@@ -484,44 +748,75 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
     if (COUNT) add_work(work + 2, n_eval, n_contrib);
 }
 
+
+}  // namespace
+
 int ceil_log2(uint64_t x) {
     int b = 0;
     while ((1ull << b) < x) ++b;
     return b;
 }
 
-}  // namespace
+// Per-tile ordering for frames whose pair workspace averages at most this many
+// pairs per tile; the global sorts for denser frames (long tile lists).
+constexpr uint64_t PER_TILE_MAX_MEAN = 1024;
 
 int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, const StageMarks &sm) {
-    bool alt;
-    sm.mark(LODGS_STAGE_DEPTH_SORT, 0, st);
-    int rc = radix_sort_pairs(f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, 0, 32,
-                              f.sort_hist, st, &alt);
-    if (rc) return rc;
-    const uint32_t *order = alt ? f.dval_alt : f.dval;
-    f.order = order;
-    sm.mark(LODGS_STAGE_DEPTH_SORT, 1, st);
-    sm.mark(LODGS_STAGE_EMIT, 0, st);
-    rc = scan_exclusive(f.ntiles, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
-                        f.cnt + C_NPAIR, st, order);      // tile counts in depth order
-    if (rc) return rc;
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
-    k_emit<<<RGRID, RB, 0, st>>>(order, f.rect, f.sp_a, f.sp_b, f.pair_off, f.cnt, f.cap_pairs, k.TX,
-                                 (uint32_t)n_tiles, f.pkey, f.pval);
-    count_launches(1);
-    sm.mark(LODGS_STAGE_EMIT, 1, st);
-    sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
-    rc = radix_sort_pairs(f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.cnt + C_NPAIR_EFF, (uint32_t)f.cap_pairs, 0,
-                          ceil_log2(n_tiles + 1), f.sort_hist, st, &alt);
-    if (rc) return rc;
-    const uint32_t *skey = alt ? f.pkey_alt : f.pkey;
-    f.sorted_pval = alt ? f.pval_alt : f.pval;
-    sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
-    sm.mark(LODGS_STAGE_BLEND, 0, st);
-    LODGS_CUDA(cudaMemsetAsync(f.ranges, 0, n_tiles * sizeof(uint2), st));
+    const bool per_tile = f.ordering == ORDER_PER_TILE ||
+                          (f.ordering == ORDER_AUTO && f.cap_pairs <= PER_TILE_MAX_MEAN * n_tiles);
+    if (per_tile) {
+        f.order = nullptr;
+        sm.mark(LODGS_STAGE_COUNT, 0, st);
+        int rc = scan_exclusive(f.ntiles, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
+                                f.cnt + C_NPAIR, st);     // rectangle pairs per selected Gaussian
+        if (rc) return rc;
+        k_emit_count<<<RGRID, RB, 0, st>>>(f.pair_off, f.rect, f.sp_a, f.sp_b, f.cnt, k.TX, f.tile_cnt);
+        k_tile_offsets<<<1, TO_THREADS, 0, st>>>(f.tile_cnt, (uint32_t)n_tiles, f.cap_pairs, f.cnt, f.ranges);
+        count_launches(2);
+        sm.mark(LODGS_STAGE_COUNT, 1, st);
+        sm.mark(LODGS_STAGE_EMIT, 0, st);
+        k_emit_scatter<<<RGRID, RB, 0, st>>>(f.pair_off, f.rect, f.sp_a, f.sp_b, f.dkey, f.cnt, k.TX, f.tile_cnt,
+                                             f.pkey, f.pval);
+        count_launches(1);
+        sm.mark(LODGS_STAGE_EMIT, 1, st);
+        sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
+        k_tile_sort<<<(unsigned)n_tiles, TS_THREADS, 0, st>>>(f.ranges, f.tile_cnt, f.cnt, f.pkey, f.pval,
+                                                              f.pscratch);
+        count_launches(1);
+        sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
+        f.sorted_pval = f.pval;
+        sm.mark(LODGS_STAGE_BLEND, 0, st);
+    } else {
+        bool alt;
+        sm.mark(LODGS_STAGE_COUNT, 0, st);        // depth sort of the selected Gaussians
+        int rc = radix_sort_pairs(f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel,
+                                  0, 32, f.sort_hist, st, &alt);
+        if (rc) return rc;
+        const uint32_t *order = alt ? f.dval_alt : f.dval;
+        f.order = order;
+        sm.mark(LODGS_STAGE_COUNT, 1, st);
+        sm.mark(LODGS_STAGE_EMIT, 0, st);
+        rc = scan_exclusive(f.ntiles, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
+                            f.cnt + C_NPAIR, st, order);  // tile counts in depth order
+        if (rc) return rc;
+        k_emit<<<RGRID, RB, 0, st>>>(order, f.rect, f.sp_a, f.sp_b, f.pair_off, f.cnt, f.cap_pairs, k.TX,
+                                     (uint32_t)n_tiles, f.pkey, f.pval);
+        count_launches(1);
+        sm.mark(LODGS_STAGE_EMIT, 1, st);
+        sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
+        rc = radix_sort_pairs(f.pkey, f.pval, f.pkey_alt, f.pval_alt, f.cnt + C_NPAIR_EFF, (uint32_t)f.cap_pairs, 0,
+                              ceil_log2(n_tiles + 1), f.sort_hist, st, &alt);
+        if (rc) return rc;
+        const uint32_t *skey = alt ? f.pkey_alt : f.pkey;
+        f.sorted_pval = alt ? f.pval_alt : f.pval;
+        LODGS_CUDA(cudaMemsetAsync(f.ranges, 0, n_tiles * sizeof(uint2), st));
+        k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, (uint32_t)n_tiles, f.ranges);
+        count_launches(1);
+        sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
+        sm.mark(LODGS_STAGE_BLEND, 0, st);
+    }
     LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));
-    k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, (uint32_t)n_tiles, f.ranges);
-    count_launches(1);
     (f.count_work ? k_blend<true> : k_blend<false>)<<<(unsigned)n_tiles, BNT, 0, st>>>(
         f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work);
     count_launches(1);

@@ -52,22 +52,30 @@ __global__ void __launch_bounds__(ST_THREADS) k_radix_upsweep(const uint32_t *__
 }
 
 // Per digit d (one warp each): exclusive scan in place of the per-block counts
-// hist[d*G .. d*G+G) and the digit total in totals[d].
+// hist[d*G .. d*G+G) and the digit total in totals[d].  All of a digit's counts
+// are loaded before any is written back, so the loads overlap.
+constexpr int DS_CHUNKS = (SORT_GRID + 31) / 32;
 __global__ void __launch_bounds__(256) k_digit_scan(uint32_t *__restrict__ hist, int G, uint32_t *__restrict__ totals) {
     const int lane = threadIdx.x & 31;
     const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
-    uint32_t carry = 0;
     uint32_t *h = hist + (size_t)d * G;
-    for (int base = 0; base < G; base += 32) {
-        int i = base + lane;
-        uint32_t v = i < G ? h[i] : 0u;
-        uint32_t x = v;
+    uint32_t v[DS_CHUNKS];
+#pragma unroll
+    for (int c = 0; c < DS_CHUNKS; ++c) {
+        const int i = c * 32 + lane;
+        v[c] = i < G ? h[i] : 0u;
+    }
+    uint32_t carry = 0;
+#pragma unroll
+    for (int c = 0; c < DS_CHUNKS; ++c) {
+        uint32_t x = v[c];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (i < G) h[i] = carry + x - v;
+        const int i = c * 32 + lane;
+        if (i < G) h[i] = carry + x - v[c];
         carry += __shfl_sync(0xffffffffu, x, 31);
     }
     if (lane == 0) totals[d] = carry;

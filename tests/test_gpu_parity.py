@@ -110,9 +110,12 @@ def _compare_render(api, sc_o, sc_g, cam, bg=(0.0, 0.0, 0.0), fr=None):
     return fr, out, img
 
 
-def test_render_matches_oracle_config1(api, c1):
+@pytest.mark.parametrize("ordering", [1, 2])
+def test_render_matches_oracle_config1(api, c1, ordering):
+    """Both pair orderings (per tile, global radix) against the oracle."""
     _, sc_o, sc_g = c1
     fr = api.Frame(sc_g)
+    fr.set_ordering(ordering)
     for cam in _cams_c1():
         _compare_render(api, sc_o, sc_g, cam, bg=(0.1, 0.0, 0.25), fr=fr)
 
@@ -190,3 +193,43 @@ def test_config2_view_forward_backward(api, c2, view):
     grad = api.render_backward(sc_g, fr, torch.from_numpy(dL).cuda()).cpu().numpy()
     ref = oracle.render_backward(sc_o, cam, out, dL.astype(np.float64))["g_rec"]
     _check_grads(grad[: len(out["sel"])], ref, 3)
+
+
+@pytest.mark.parametrize("n,ordering", [(200, 1), (1000, 1), (6000, 1), (20000, 1), (6000, 2), (20000, 0)])
+def test_long_tile_lists_match_oracle(api, n, ordering):
+    """A dense cluster puts hundreds to tens of thousands of pairs in a few
+    tiles: the per-tile sort's rank, shared-memory bitonic and chunk-and-merge
+    paths give the oracle's (tile, depth, index) order bit for bit, and the image."""
+    leaves = synth.leaves_uniform_cube(n, seed=900 + n, half_extent=0.05, degree=0, log_scale_mu=-6.0)
+    cam = synth.camera_look([0.013, -0.021, -10.0], [0, 0, 1], [1, 0, 0], 64, 48, tau=0.01)
+    kappa = float(cam.fx / cam.tau)
+    sc_o = oracle.build_scene(leaves, 0, 1e-9, kappa)
+    sc_g = api.build_hierarchy(leaves, 0, 1e-9, kappa)
+    fr = api.Frame(sc_g)
+    fr.set_ordering(ordering)
+    fr, out, _ = _compare_render(api, sc_o, sc_g, cam, bg=(0.2, 0.3, 0.1), fr=fr)
+    lens = np.diff(out["pairs"]["tile_start"])
+    assert lens.max() >= {200: 150, 1000: 700, 6000: 4000, 20000: 12000}[n], lens.max()
+
+
+def test_orderings_agree_on_a_1080p_view(api):
+    """Per-tile and global ordering give the same pairs, image and gradients on
+    a dense 1080p view of the 2M-leaf scene."""
+    cfg = synth.config2_scene()
+    cam = cfg["cameras"][2]
+    sc = api.build_hierarchy(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
+    res = []
+    for ordering in (1, 2):
+        fr = api.Frame(sc)
+        fr.set_ordering(ordering)
+        api.select_lod(sc, cam, fr)
+        img = api.render(sc, fr, bg=(0.1, 0.1, 0.1))
+        dL = torch.full_like(img, 1e-3)
+        g = api.render_backward(sc, fr, dL)
+        ex = fr.export()
+        res.append((ex["pair_i"], ex["ranges"], img.cpu().numpy(), g.cpu().numpy(), fr.stats()))
+    assert res[0][4]["n_pairs"] == res[1][4]["n_pairs"] > 100000
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[0][2], res[1][2])
+    scale = np.abs(res[1][3]).max(axis=0, keepdims=True) + 1e-12
+    assert (np.abs(res[0][3] - res[1][3]) / scale).max() < 1e-4
