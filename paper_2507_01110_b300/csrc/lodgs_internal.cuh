@@ -128,6 +128,8 @@ struct FrameBufs {
     // selection (capacity n_nodes / n_spt)
     uint32_t *sel_rows = nullptr, *emit_j = nullptr, *high = nullptr, *work_off = nullptr;
     uint32_t *sel_src = nullptr;      // record slot of each selected node (out-of-core renders)
+    uint8_t *up_out = nullptr;        // per upper entry: its Algorithm 1 outcome (optional cache)
+    float *up_x = nullptr;            // per upper entry: tau * d / f (with up_out)
     uint32_t *emit_src = nullptr;     // slot of entry 0 of each emitted SPT (out-of-core renders)
     bool use_src = false;             // project through sel_src instead of sel_rows
     float *emit_x = nullptr;

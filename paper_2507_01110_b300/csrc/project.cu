@@ -247,13 +247,18 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
         atomicAdd(reinterpret_cast<unsigned long long *>(cnt + C_NPAIR64), npairs);
 }
 
+__device__ __forceinline__ void cp_async4(float *dst_smem, const float *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 // Floats per record of SH degree DEG (14 base values + 3 per SH coefficient,
 // padded to a multiple of 8).
 __host__ __device__ constexpr int rec_stride(int deg) { return (14 + 3 * ((deg + 1) * (deg + 1) - 1) + 7) / 8 * 8; }
 
 // Each warp handles 32 selected Gaussians at a time: the records of the
 // visible ones are staged in shared memory row by row (whole-warp, coalesced
-// reads), each lane computes the gradient of its own Gaussian in place of its
+// asynchronous copies), each lane computes the gradient of its own Gaussian in place of its
 // record there, and the warp writes the 32 gradient rows back row by row.
 // Rows are padded to RS + 1 floats so that lanes reading the same field of
 // their own rows hit distinct banks.
@@ -282,16 +287,16 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
         const bool vis = mine && ntiles[i] != 0;
         const uint32_t src = vis ? sel_src[i] : 0u;
         const unsigned vmask = __ballot_sync(0xffffffffu, vis);
-#pragma unroll 4
+        // asynchronous 4-byte copies straight into the padded rows: all of the
+        // warp's row reads are in flight at once, without registers
         for (int e = 0; e < m; ++e) {
             if (!(vmask >> e & 1u)) continue;
-            const float2 *g = reinterpret_cast<const float2 *>(rows + (size_t)__shfl_sync(0xffffffffu, src, e) * RS);
-            for (int c = lane; c < RS / 2; c += 32) {
-                const float2 v = g[c];
-                sw[e * SP + 2 * c] = v.x;
-                sw[e * SP + 2 * c + 1] = v.y;
-            }
+            const float *g = rows + (size_t)__shfl_sync(0xffffffffu, src, e) * RS;
+#pragma unroll
+            for (int c = lane; c < RS; c += 32) cp_async4(sw + e * SP + c, g + c);
         }
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncwarp();
         if (mine && !vis) {
             for (int c = 0; c < RS; ++c) r[c] = 0.f;

@@ -92,17 +92,21 @@ __device__ __forceinline__ uint32_t block_prefix(const uint32_t *__restrict__ co
 }
 
 // ---- a1 --------------------------------------------------------------------
+// Counts per block; with a cache (up_out, up_x) the outcomes are kept for the
+// write pass, which then skips the ancestor walks.
 __global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict__ up, uint32_t U,
-                                                    const View *__restrict__ view, uint32_t *__restrict__ bc) {
+                                                    const View *__restrict__ view, uint32_t *__restrict__ bc,
+                                                    uint8_t *__restrict__ up_out, float *__restrict__ up_x) {
     const CamK &k = view->k;
     __shared__ uint32_t s_warp[32];
     uint32_t begin, end;
     grid_chunk(U, begin, end);
     uint32_t packed = 0;
     for (uint32_t u = begin + threadIdx.x; u < end; u += SB) {
-        float x;
+        float x = 0.f;
         int o = upper_outcome(up, (int)u, k, &x);
         packed += o == OUT_SELECT ? 1u : (o == OUT_SPT ? 0x10000u : 0u);
+        if (up_out) { up_out[u] = (uint8_t)o; up_x[u] = x; }
     }
     uint32_t tot;
     block_scan(packed, s_warp, &tot);   // counts per block < 65536 per field (U / grid)
@@ -111,7 +115,8 @@ __global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict
 
 __global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict__ up, uint32_t U,
                                                     const View *__restrict__ view,
-                                                    const uint32_t *__restrict__ bc, uint32_t *__restrict__ sel_rows,
+                                                    const uint32_t *__restrict__ bc, const uint8_t *__restrict__ up_out,
+                                                    const float *__restrict__ up_x, uint32_t *__restrict__ sel_rows,
                                                     uint32_t *__restrict__ sel_src, uint32_t *__restrict__ emit_j,
                                                     float *__restrict__ emit_x, uint32_t *__restrict__ cnt) {
     const CamK &k = view->k;
@@ -133,7 +138,11 @@ __global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict
     for (uint32_t t0 = begin; t0 < end; t0 += SB) {
         uint32_t u = t0 + threadIdx.x;
         float x = 0.f;
-        int o = u < end ? upper_outcome(up, (int)u, k, &x) : OUT_NONE;
+        int o = OUT_NONE;
+        if (u < end) {
+            if (up_out) { o = up_out[u]; x = up_x[u]; }
+            else o = upper_outcome(up, (int)u, k, &x);
+        }
         uint32_t packed = o == OUT_SELECT ? 1u : (o == OUT_SPT ? 0x10000u : 0u);
         uint32_t tot;
         uint32_t ex = block_scan(packed, s_warp, &tot);
@@ -319,10 +328,10 @@ int launch_set_view(const View &v, View *dst, cudaStream_t st) {
 
 int launch_select_upper(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st) {
     uint32_t U = (uint32_t)sc->n_upper;
-    k_upper_count<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, f.d_view, f.block_counts);
+    k_upper_count<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, f.d_view, f.block_counts, f.up_out, f.up_x);
     count_launches(1);
-    k_upper_write<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, f.d_view, f.block_counts, f.sel_rows, with_src ? f.sel_src : nullptr,
-                                           f.emit_j, f.emit_x, f.cnt);
+    k_upper_write<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, f.d_view, f.block_counts, f.up_out, f.up_x, f.sel_rows,
+                                           with_src ? f.sel_src : nullptr, f.emit_j, f.emit_x, f.cnt);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
