@@ -72,7 +72,8 @@ __global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restri
                        int TX, uint32_t n_tiles, uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
     // pairs beyond the workspace (or an earlier overflow) are not emitted: capacity error
     uint32_t P = cnt[C_NPAIR];
-    const bool over = P > cap_pairs || (cnt[C_STATUS] & ST_CAPACITY);
+    const bool over = P > cap_pairs || (cnt[C_STATUS] & ST_CAPACITY) ||
+                      *reinterpret_cast<const unsigned long long *>(cnt + C_NPAIR64) > 0xffffffffull;
     if (over) P = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         cnt[C_NPAIR_EFF] = P;
