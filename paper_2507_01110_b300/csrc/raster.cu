@@ -695,35 +695,32 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
                 if (!__any_sync(0xffffffffu, any)) continue;
                 const float cb = s_c[j];
                 const float ax2 = 2.0f * a.z * dx, cy2 = 2.0f * b.x, hdx2 = -0.5f * dx * dx;
+                // predicated: a lane whose pixel misses gets alpha = e = 0, which
+                // leaves T and G.S unchanged and makes every term below zero
                 float gv[9];
-#pragma unroll
-                for (int q = 0; q < 9; ++q) gv[q] = 0.f;
                 bool died = false;
 #pragma unroll
                 for (int k = 0; k < BP; ++k) {
-                    if (hit[k]) {
-                        if (COUNT) ++n_contrib;
-                        const float dy = dyk[k];
-                        const float e = ex2_ftz(p[k] * LOG2E);
-                        const float raw = b.y * e;
-                        const float alpha = fminf(ALPHA_MAX, raw);
-                        const float w = alpha * T[k];
-                        const float gc = G[k][0] * b.z + G[k][1] * b.w + G[k][2] * cb;
-                        gS[k] -= w * gc;                                                  // G.S_i
-                        const float dA = T[k] * gc - rcp_ftz(1.0f - alpha) * gS[k];
-                        gv[6] += G[k][0] * w; gv[7] += G[k][1] * w; gv[8] += G[k][2] * w;
-                        T[k] = T[k] * (1.0f - alpha);                                     // as the forward
-                        if (T[k] < T_MIN) { live[k] = false; died = true; }
-                        if (raw <= ALPHA_MAX) {
-                            const float dp = dA * alpha;
-                            gv[5] += dA * e;
-                            gv[0] += dp * (ax2 + a.w * dy);
-                            gv[1] += dp * (cy2 * dy + bx);
-                            gv[2] += dp * hdx2;
-                            gv[3] -= dp * dx * dy;
-                            gv[4] += -0.5f * dp * dy * dy;
-                        }
-                    }
+                    if (COUNT) n_contrib += hit[k];
+                    const float dy = dyk[k];
+                    const float e = hit[k] ? ex2_ftz(p[k] * LOG2E) : 0.f;
+                    const float raw = b.y * e;
+                    const float alpha = fminf(ALPHA_MAX, raw);
+                    const float w = alpha * T[k];
+                    const float gc = G[k][0] * b.z + G[k][1] * b.w + G[k][2] * cb;
+                    gS[k] -= w * gc;                                                      // G.S_i
+                    const float dA = T[k] * gc - rcp_ftz(1.0f - alpha) * gS[k];
+                    const bool free_ = raw <= ALPHA_MAX;                                  // alpha not clamped
+                    const float dp = free_ ? dA * alpha : 0.f;
+                    const float c[9] = {dp * (ax2 + a.w * dy), dp * (cy2 * dy + bx), dp * hdx2, -(dp * dx) * dy,
+                                        -0.5f * dp * dy * dy, free_ ? dA * e : 0.f, G[k][0] * w, G[k][1] * w,
+                                        G[k][2] * w};
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) gv[q] = k == 0 ? c[q] : gv[q] + c[q];
+                    T[k] = T[k] * (1.0f - alpha);                                         // as the forward
+                    const bool stop = hit[k] && T[k] < T_MIN;
+                    live[k] = live[k] && !stop;
+                    died |= stop;
                 }
                 warp_sum9_to_smem(gv, lane, s_grad[j]);
                 if (__any_sync(0xffffffffu, died)) {
