@@ -317,6 +317,30 @@ def render(scene: dict, cam, bg=(0.0, 0.0, 0.0), cull: bool = True, sel: np.ndar
     return out
 
 
+def adam_sparse(params: np.ndarray, m: np.ndarray, v: np.ndarray, t: np.ndarray, rows, grads: np.ndarray,
+                lr, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-15, used: int | None = None) -> None:
+    """Sparse Adam step in place (float64 params/m/v of shape n x stride, uint32 t):
+    only `rows` move, each with its own step count; lr is per column."""
+    assert params.dtype == m.dtype == v.dtype == np.float64 and t.dtype == np.uint32
+    stride = params.shape[1]
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    g = np.ascontiguousarray(grads, dtype=np.float64).reshape(len(rows), -1)
+    if g.shape[1] != stride:
+        g = np.ascontiguousarray(np.pad(g, ((0, 0), (0, stride - g.shape[1]))))
+    lrv = np.ascontiguousarray(np.broadcast_to(np.asarray(lr, dtype=np.float64), (stride,)))
+    lib().or_adam_sparse(C.c_int64(len(rows)), _p(rows), _p(g), C.c_int(stride), C.c_int(used or stride), _p(lrv),
+                         C.c_double(b1), C.c_double(b2), C.c_double(eps), _p(params), _p(m), _p(v), _p(t))
+
+
+def screen_grad_max(n_nodes: int, views) -> np.ndarray:
+    """Per node, the largest norm of the screen-space mean gradient dL/d(u, v) over
+    the views (the densification criterion); views = [(selected rows, g2d)]."""
+    out = np.zeros(n_nodes, dtype=np.float64)
+    for sel, g2d in views:
+        np.maximum.at(out, np.asarray(sel, dtype=np.int64), np.hypot(g2d[:, 0], g2d[:, 1]))
+    return out
+
+
 def render_backward(scene: dict, cam, fwd: dict, dL_dimg: np.ndarray, bg=(0.0, 0.0, 0.0), window=None) -> dict:
     g2d = blend_backward(fwd["proj"], fwd["pairs"], cam.width, cam.height, dL_dimg, bg, window)
     grec = project_backward(scene, fwd["sel"], cam, fwd["proj"], g2d)

@@ -1138,3 +1138,32 @@ int or_project_backward(int64_t n, const int64_t *sel, int stride, int degree, c
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Sparse Adam over the cut (appendix "Implementation Details": only the      */
+/* nodes of the cut set are optimised; Adam after Kingma and Ba).  For every  */
+/* listed row r with gradient row g (its first `used` columns) and per-column */
+/* learning rates lr[c]:                                                       */
+/*   t_r <- t_r + 1                                                            */
+/*   m <- b1 m + (1 - b1) g ;  v <- b2 v + (1 - b2) g^2                        */
+/*   p <- p - lr_c (m / (1 - b1^t_r)) / (sqrt(v / (1 - b2^t_r)) + eps)        */
+/* Each row counts its own steps, so its bias correction covers the steps it  */
+/* took part in.  Rows not listed are untouched.  float64 throughout.         */
+/* ------------------------------------------------------------------------- */
+int or_adam_sparse(int64_t n_rows, const int64_t *rows, const double *grads, int stride, int used,
+                   const double *lr, double b1, double b2, double eps, double *params, double *m, double *v,
+                   uint32_t *t) {
+    for (int64_t i = 0; i < n_rows; ++i) {
+        const int64_t r = rows[i];
+        t[r] += 1;
+        const double bc1 = 1.0 - pow(b1, (double)t[r]), bc2 = 1.0 - pow(b2, (double)t[r]);
+        for (int c = 0; c < used; ++c) {
+            const double g = grads[i * stride + c];
+            double *mm = m + r * stride + c, *vv = v + r * stride + c;
+            *mm = b1 * *mm + (1.0 - b1) * g;
+            *vv = b2 * *vv + (1.0 - b2) * g * g;
+            params[r * stride + c] -= lr[c] * (*mm / bc1) / (sqrt(*vv / bc2) + eps);
+        }
+    }
+    return 0;
+}

@@ -31,6 +31,10 @@ namespace {
 
 constexpr int RB = 256;
 constexpr int RGRID = 148 * 8;
+#ifndef LODGS_EMIT_GRID
+#define LODGS_EMIT_GRID (148 * 16)
+#endif
+constexpr int EGRID = LODGS_EMIT_GRID;     // blocks of the pair enumeration kernels
 
 // Tile support test (float32, explicitly rounded).  The support exponent is a
 // concave quadratic; its maximum over the rectangle of the tile's pixel centres
@@ -769,12 +773,12 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         int rc = scan_exclusive(f.ntiles, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
                                 f.cnt + C_NPAIR, st);     // rectangle pairs per selected Gaussian
         if (rc) return rc;
-        k_emit_count<<<RGRID, RB, 0, st>>>(f.pair_off, f.rect, f.sp_a, f.sp_b, f.cnt, k.TX, f.tile_cnt);
+        k_emit_count<<<EGRID, RB, 0, st>>>(f.pair_off, f.rect, f.sp_a, f.sp_b, f.cnt, k.TX, f.tile_cnt);
         k_tile_offsets<<<1, TO_THREADS, 0, st>>>(f.tile_cnt, (uint32_t)n_tiles, f.cap_pairs, f.cnt, f.ranges);
         count_launches(2);
         sm.mark(LODGS_STAGE_COUNT, 1, st);
         sm.mark(LODGS_STAGE_EMIT, 0, st);
-        k_emit_scatter<<<RGRID, RB, 0, st>>>(f.pair_off, f.rect, f.sp_a, f.sp_b, f.dkey, f.cnt, k.TX, f.tile_cnt,
+        k_emit_scatter<<<EGRID, RB, 0, st>>>(f.pair_off, f.rect, f.sp_a, f.sp_b, f.dkey, f.cnt, k.TX, f.tile_cnt,
                                              f.pkey, f.pval);
         count_launches(1);
         sm.mark(LODGS_STAGE_EMIT, 1, st);

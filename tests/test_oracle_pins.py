@@ -8,6 +8,7 @@ inputs, or finite differences.  None of them needs a GPU.
 import math
 
 import numpy as np
+import torch
 import pytest
 
 from paper_2507_01110_b300 import synth
@@ -776,3 +777,65 @@ def test_backward_matches_finite_differences(oracle_lib, degree, clamp_case):
             hp = float(np.float32(base + h)) - float(np.float32(base - h))
             num = (vals[0] - vals[1]) / hp
             assert g[i, c] == pytest.approx(num, rel=2e-3, abs=2e-4 * (1 + abs(num))), (i, c)
+
+
+# ---------------------------------------------------------------------------
+# sparse Adam over the cut set
+# ---------------------------------------------------------------------------
+
+def test_adam_every_row_every_step_equals_torch(oracle_lib):
+    """With every row selected at every step the sparse Adam is torch.optim.Adam."""
+    rng = np.random.default_rng(40)
+    n, stride, lr = 6, 8, 3e-3
+    p0 = rng.standard_normal((n, stride))
+    params, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    t = np.zeros(n, np.uint32)
+    tp = torch.tensor(p0.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=lr, betas=(0.9, 0.999), eps=1e-8)
+    for _ in range(7):
+        g = rng.standard_normal((n, stride))
+        oracle_lib.adam_sparse(params, m, v, t, np.arange(n), g, lr, eps=1e-8)
+        tp.grad = torch.tensor(g)
+        opt.step()
+    assert np.allclose(params, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+    assert np.all(t == 7)
+
+
+def test_adam_rows_count_their_own_steps(oracle_lib):
+    """A row selected at some steps only moves then, with the bias correction of
+    its own step count: it matches a torch Adam that steps only at those steps;
+    rows never selected are untouched, bit for bit."""
+    rng = np.random.default_rng(41)
+    n, stride, lr = 5, 4, 1e-2
+    p0 = rng.standard_normal((n, stride))
+    params, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    t = np.zeros(n, np.uint32)
+    sel_by_step = [[0, 2], [2], [0, 1, 2], [1], [0, 2]]
+    ref = {}
+    for r in range(n):
+        tp = torch.tensor(p0[r].copy(), dtype=torch.float64, requires_grad=True)
+        ref[r] = (tp, torch.optim.Adam([tp], lr=lr, eps=1e-15))
+    for sel in sel_by_step:
+        g = rng.standard_normal((len(sel), stride))
+        oracle_lib.adam_sparse(params, m, v, t, sel, g, lr)
+        for i, r in enumerate(sel):
+            tp, opt = ref[r]
+            tp.grad = torch.tensor(g[i])
+            opt.step()
+    for r in range(n):
+        assert np.allclose(params[r], ref[r][0].detach().numpy(), rtol=1e-12, atol=1e-14)
+    assert list(t) == [3, 2, 4, 0, 0]
+    assert np.array_equal(params[3:], p0[3:])
+
+
+def test_adam_constant_gradient_closed_form(oracle_lib):
+    """A constant gradient makes both bias-corrected moments exact (m = g, v = g^2),
+    so every step moves a column by lr_c g / (|g| + eps)."""
+    stride, steps, eps = 6, 9, 1e-8
+    lr = np.array([1e-3, 2e-3, 5e-4, 1e-2, 3e-3, 0.0])
+    g = np.array([[0.5, -2.0, 1e-3, 4.0, -0.25, 1.0]])
+    params = np.ones((1, stride))
+    m, v, t = np.zeros_like(params), np.zeros_like(params), np.zeros(1, np.uint32)
+    for _ in range(steps):
+        oracle_lib.adam_sparse(params, m, v, t, [0], g, lr, eps=eps)
+    assert np.allclose(params[0], 1.0 - steps * lr * g[0] / (np.abs(g[0]) + eps), rtol=1e-12, atol=1e-15)
