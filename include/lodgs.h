@@ -273,6 +273,44 @@ int lodgs_accumulate_grads(lodgs_scene *scene, lodgs_frame *const *frames, const
                            uint32_t *out_rows, float *out_grads, int64_t capacity, uint32_t *d_count, void *stream);
 
 /*
+ * Sparse Adam step over the cut set (appendix "Implementation Details": only
+ * the nodes of the cut are optimised; Adam after Kingma and Ba).  For each of
+ * the n listed rows r = rows[i] (unique) with gradient row grads[i] (stride
+ * floats, the layout of lodgs_render_backward's sparse rows or of
+ * lodgs_accumulate_grads' output), t[r] += 1 and for every record column c that
+ * the SH degree uses:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *   p -= lr[c] (m / (1 - b1^t[r])) / (sqrt(v / (1 - b2^t[r])) + eps)
+ * so each row's bias correction counts the steps it took part in.
+ *   params, m, v: device float32 n_nodes x stride (render-row order, e.g. the
+ *                 scene's own records); m, v, t zeroed by the caller before the
+ *                 first step
+ *   t:            device uint32 n_nodes
+ *   d_n:          device uint32 count of rows (NULL: exactly max_n rows);
+ *                 max_n bounds it (grid sizing)
+ *   lr:           host float[stride] per-column learning rates
+ * Asynchronous.  The update is w.r.t. the stored values (activations are the
+ * caller's, as for the gradients).
+ */
+int lodgs_adam_step(lodgs_scene *scene, float *params, float *m, float *v, uint32_t *t, const uint32_t *rows,
+                    const float *grads, const uint32_t *d_n, int64_t max_n, const float *lr, float b1, float b2,
+                    float eps, void *stream);
+
+/*
+ * Densification criterion (Sec. 3: nodes are split where the screen-space
+ * gradient is largest): after lodgs_render_backward on `frame`, for every
+ * selected node max_per_node[row] = max(max_per_node[row], |dL/d(u, v)|), the
+ * norm of the gradient w.r.t. the projected mean.  max_per_node: device float
+ * n_nodes, zeroed by the caller.  Asynchronous on `stream`.
+ */
+int lodgs_frame_screen_grad_max(lodgs_frame *frame, float *max_per_node, void *stream);
+
+/* Device pointer to the frame's count of selected nodes as its last render
+ * processed them (uint32, valid while the frame lives): the row count of its
+ * sparse gradient rows, for lodgs_adam_step without a host synchronisation. */
+int lodgs_frame_device_count(lodgs_frame *frame, const uint32_t **d_n_selected);
+
+/*
  * Photometric L1 loss of a rendered image against a target (the training loss
  * of the benchmark step) fused with its gradient, in one pass over device
  * buffers of n floats (16-byte aligned): dL[i] = grad_scale * sign(image[i] -

@@ -89,6 +89,10 @@ _SIGS = {
     "lodgs_render_backward_project": (C.c_int, [_P, _P, _P, _P, C.c_int, _P]),
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
     "lodgs_frame_set_ordering": (C.c_int, [_P, C.c_int]),
+    "lodgs_adam_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, C.c_float, C.c_float, C.c_float,
+                                  _P]),
+    "lodgs_frame_screen_grad_max": (C.c_int, [_P, _P, _P]),
+    "lodgs_frame_device_count": (C.c_int, [_P, C.POINTER(_P)]),
     "lodgs_accumulate_grads": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, C.c_int64, _P, _P]),
     "lodgs_l1_loss_grad": (C.c_int, [_P, _P, C.c_int64, C.c_float, _P, _P, _P]),
     "lodgs_frame_export": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),

@@ -254,6 +254,49 @@ def accumulate_grads(scene: Scene, frames: list, grads: list, stream=None) -> tu
     return out_rows[:k].to(torch.int64), out_grads[:k]
 
 
+class AdamState:
+    """Sparse Adam state of a scene's records (device float32 m, v; uint32 step counts)."""
+
+    def __init__(self, scene: Scene):
+        self.m = torch.zeros((scene.n_nodes, scene.stride), dtype=torch.float32, device="cuda")
+        self.v = torch.zeros_like(self.m)
+        self.t = torch.zeros(scene.n_nodes, dtype=torch.int32, device="cuda")
+
+
+def adam_step(scene: Scene, params: torch.Tensor, state: AdamState, rows: torch.Tensor, grads: torch.Tensor, lr,
+              b1: float = 0.9, b2: float = 0.999, eps: float = 1e-15, d_n=None, stream=None) -> None:
+    """Sparse Adam step of the listed rows (uint32/int32 device tensor or a raw device
+    pointer with d_n): params -= lr m_hat / (sqrt(v_hat) + eps), per-row step counts.
+    lr: a float or a per-column sequence of `stride` floats."""
+    lrv = np.broadcast_to(np.asarray(lr, dtype=np.float32), (scene.stride,)).copy()
+    if isinstance(rows, torch.Tensor):
+        n = rows.numel()
+        rows = rows.to(torch.int32).contiguous()
+        assert rows.is_cuda, "rows must be a CUDA tensor"
+        rows_p = C.c_void_p(rows.data_ptr())
+    else:
+        rows_p, n = rows
+    assert state.t.is_cuda and state.t.dtype == torch.int32
+    check(lib().lodgs_adam_step(scene.handle, _ptr(params), _ptr(state.m), _ptr(state.v),
+                                C.c_void_p(state.t.data_ptr()), rows_p,
+                                _ptr(grads), C.c_void_p(d_n) if d_n else None, C.c_int64(int(n)),
+                                lrv.ctypes.data_as(C.c_void_p), C.c_float(b1), C.c_float(b2), C.c_float(eps),
+                                _stream_ptr(stream)))
+
+
+def screen_grad_max(frame: Frame, max_per_node: torch.Tensor, stream=None) -> torch.Tensor:
+    """max_per_node[row] = max(.., |dL/d(u, v)|) over the frame's selected nodes (after render_backward)."""
+    check(lib().lodgs_frame_screen_grad_max(frame.handle, _ptr(max_per_node), _stream_ptr(stream)))
+    return max_per_node
+
+
+def frame_device_count(frame: Frame) -> int:
+    """Device address of the frame's selected-node count (uint32)."""
+    p = C.c_void_p()
+    check(lib().lodgs_frame_device_count(frame.handle, C.byref(p)))
+    return p.value
+
+
 def l1_loss_grad(image: torch.Tensor, target: torch.Tensor, dL: torch.Tensor | None = None,
                  loss_sum: torch.Tensor | None = None, stream=None):
     """Mean L1 loss and its gradient in one pass; returns (dL, loss_sum) where

@@ -21,7 +21,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                  "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
 EXACT = {"scene.cu", "select.cu", "project.cu", "abi.cu"}     # no FMA contraction
-SOURCES = ["abi.cu", "scene.cu", "select.cu", "project.cu", "raster.cu", "sort.cu", "noalloc.cu", "cache.cu", "batch.cu", "loss.cu"]
+SOURCES = ["abi.cu", "scene.cu", "select.cu", "project.cu", "raster.cu", "sort.cu", "noalloc.cu", "cache.cu", "batch.cu",
+           "loss.cu", "adam.cu"]
 
 
 def _newer(src_paths, out):
