@@ -132,6 +132,14 @@ class Frame:
             return torch.zeros(0, dtype=torch.int64, device="cuda")
         return _device_view(p.value, (int(n.value),), "<u4").to(torch.int64)
 
+    def selection_device(self) -> tuple:
+        """(device address of the selected rows (uint32), device address of their count)
+        -- the rows of the frame's sparse gradient rows, for adam_step without a copy."""
+        p = C.c_void_p()
+        n = C.c_int64()
+        check(lib().lodgs_frame_selection(self._h, C.byref(p), C.byref(n)))
+        return p.value, frame_device_count(self)
+
     ORDER_AUTO, ORDER_PER_TILE, ORDER_GLOBAL = 0, 1, 2
 
     def set_ordering(self, mode: int) -> None:

@@ -3,8 +3,8 @@
 // Training optimises only the nodes of the view's LoD cut (appendix
 // "Implementation Details"): after the backward, each listed node row takes an
 // Adam step (Kingma and Ba) with its own step count, so its bias correction
-// covers the steps it took part in.  One warp per row, the row's columns spread
-// over the lanes (coalesced).  The screen-space mean gradient dL/d(u, v) of
+// covers the steps it took part in.  Sixteen-byte quarters of a row are spread
+// over threads (coalesced).  The screen-space mean gradient dL/d(u, v) of
 // every selected Gaussian is also reduced to a per-node maximum over views, the
 // quantity densification ranks nodes by.
 #include <algorithm>
@@ -22,35 +22,43 @@ struct ColumnRates {
     float lr[MAX_STRIDE];
 };
 
-__global__ void __launch_bounds__(AB) k_adam(float *__restrict__ params, float *__restrict__ m, float *__restrict__ v,
-                                             uint32_t *__restrict__ t, const uint32_t *__restrict__ rows,
-                                             const float *__restrict__ grads, const uint32_t *__restrict__ d_n,
-                                             uint32_t n_host, int stride, int used, ColumnRates rates, float b1,
-                                             float b2, float eps) {
+// One thread per 16-byte quarter of a row: every access of a row (its step
+// count, the gradient, m, v and the parameters) is issued at once, so a row
+// costs one memory round trip; the quarter holding column 0 writes the new
+// step count.  Columns at or past `used` keep their bits.
+__global__ void __launch_bounds__(AB) k_adam(float4 *__restrict__ params, float4 *__restrict__ m,
+                                             float4 *__restrict__ v, uint32_t *__restrict__ t,
+                                             const uint32_t *__restrict__ rows, const float4 *__restrict__ grads,
+                                             const uint32_t *__restrict__ d_n, uint32_t n_host, int quads, int used,
+                                             ColumnRates rates, float b1, float b2, float eps) {
     const uint32_t n = d_n ? *d_n : n_host;
-    const int lane = threadIdx.x & 31;
     const float omb1 = 1.0f - b1, omb2 = 1.0f - b2;
-    const uint32_t warps = gridDim.x * (AB / 32);
-    for (uint32_t i = blockIdx.x * (AB / 32) + (threadIdx.x >> 5); i < n; i += warps) {
+    const uint64_t total = (uint64_t)n * quads;
+    for (uint64_t e = (uint64_t)blockIdx.x * AB + threadIdx.x; e < total; e += (uint64_t)gridDim.x * AB) {
+        const uint32_t i = (uint32_t)(e / quads);
+        const int q = (int)(e % quads);
         const uint32_t r = rows[i];
-        uint32_t step = 0;
-        if (lane == 0) {
-            step = t[r] + 1;
-            t[r] = step;
-        }
-        step = __shfl_sync(0xffffffffu, step, 0);
+        const size_t at = (size_t)r * quads + q;
+        const uint32_t step = t[r] + 1;
+        const float4 g = grads[(size_t)i * quads + q];
+        float4 mm = m[at], vv = v[at], pp = params[at];
+        if (q == 0) t[r] = step;
         // 1 - b^t as -expm1(t log1p(-(1 - b))): 1 - b is exact in float32 and nothing cancels
         const float bc1 = -expm1f((float)step * log1pf(-omb1)), bc2 = -expm1f((float)step * log1pf(-omb2));
-        const float *g = grads + (size_t)i * stride;
-        const size_t base = (size_t)r * stride;
-        for (int c = lane; c < used; c += 32) {
-            const float gc = g[c];
-            const float mm = b1 * m[base + c] + omb1 * gc;
-            const float vv = b2 * v[base + c] + omb2 * gc * gc;
-            m[base + c] = mm;
-            v[base + c] = vv;
-            params[base + c] -= rates.lr[c] * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+        float *mp = &mm.x, *vp = &vv.x, *pq = &pp.x;
+        const float *gp = &g.x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int col = 4 * q + c;
+            if (col < used) {
+                mp[c] = b1 * mp[c] + omb1 * gp[c];
+                vp[c] = b2 * vp[c] + omb2 * gp[c] * gp[c];
+                pq[c] -= rates.lr[col] * (mp[c] / bc1) / (sqrtf(vp[c] / bc2) + eps);
+            }
         }
+        m[at] = mm;
+        v[at] = vv;
+        params[at] = pp;
     }
 }
 
@@ -85,9 +93,15 @@ extern "C" int lodgs_adam_step(lodgs_scene *sc, float *params, float *m, float *
     ColumnRates rates{};
     for (int c = 0; c < sc->stride; ++c) rates.lr[c] = lr[c];
     const int used = 14 + 3 * ((sc->sh_degree + 1) * (sc->sh_degree + 1) - 1);
-    const int64_t blocks = std::min<int64_t>((max_n + AB / 32 - 1) / (AB / 32), 148 * 16);
+    if (sc->stride % 4 || (uintptr_t)params % 16 || (uintptr_t)m % 16 || (uintptr_t)v % 16 || (uintptr_t)grads % 16) {
+        set_error("adam_step: params, m, v and grads must be 16-byte aligned");
+        return LODGS_E_INVALID;
+    }
+    const int quads = sc->stride / 4;
+    const int64_t blocks = std::min<int64_t>((max_n * quads + AB - 1) / AB, 148 * 64);
     k_adam<<<(unsigned)std::max<int64_t>(blocks, 1), AB, 0, (cudaStream_t)stream>>>(
-        params, m, v, t, rows, grads, d_n, (uint32_t)max_n, sc->stride, used, rates, b1, b2, eps);
+        reinterpret_cast<float4 *>(params), reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), t, rows,
+        reinterpret_cast<const float4 *>(grads), d_n, (uint32_t)max_n, quads, used, rates, b1, b2, eps);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
