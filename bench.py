@@ -17,6 +17,7 @@ times the CPU oracle on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -43,6 +44,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--leaves", type=int, default=2_097_152)
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-lod-sweep", action="store_true")
     p.add_argument("--no-out-of-core", action="store_true")
     p.add_argument("--serving-leaves", type=int, default=50_000_000)
     p.add_argument("--serving-requests", type=int, default=400)
@@ -554,6 +556,43 @@ def run_serving(args) -> dict:
             "unit": "ms"}
 
 
+def run_lod_sweep(args) -> dict:
+    """LoD effectiveness: forward frames/s against the number of selected nodes over
+    50 LoD thresholds tau (log-spaced 0.25..64 px) on the 2M-leaf scene, three views
+    of the path (aerial, middle, street); the scene is built for the largest tau."""
+    import torch
+    from paper_2507_01110_b300 import api, synth
+    cfg = synth.config2_scene(n=args.leaves)
+    base = [cfg["cameras"][i] for i in (0, 16, 31)]
+    taus = np.geomspace(0.25, 64.0, 50)
+    scene = api.build_hierarchy(cfg["leaves"], 3, cfg["spt_volume"], float(base[0].fx / taus[-1]))
+    frames = [api.Frame(scene) for _ in base]
+    image = torch.empty((base[0].height, base[0].width, 3), device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out_tau, out_sel, out_fps = [], [], []
+    for tau in taus:
+        cams = [dataclasses.replace(c, tau=np.float32(tau)) for c in base]
+        for fr, cam in zip(frames, cams):          # size the workspaces for this tau
+            api.select_lod(scene, cam, fr)
+            api.render(scene, fr, image=image, check_capacity=True)
+        sel = float(np.mean([fr.stats()["n_selected"] for fr in frames]))
+        reps = 4
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            for fr, cam in zip(frames, cams):
+                api.select_lod(scene, cam, fr)
+                api.render(scene, fr, image=image, check_capacity=False)
+        e1.record()
+        torch.cuda.synchronize()
+        out_tau.append(round(float(tau), 3))
+        out_sel.append(int(sel))
+        out_fps.append(round(reps * len(cams) / (e0.elapsed_time(e1) * 1e-3), 1))
+    return {"workload": f"{args.leaves:,}-leaf SH3 scene, views 0/16/31 of the path at 1920x1080, forward "
+                        "(select + render), tau log-spaced 0.25..64 px", "tau_px": out_tau,
+            "selected_mean": out_sel, "frames_per_s": out_fps}
+
+
 def run_out_of_core(args) -> dict:
     import torch
     from paper_2507_01110_b300 import api, synth
@@ -724,6 +763,8 @@ def main():
 
     if world == 1 and not args.no_out_of_core:
         section("out_of_core", run_out_of_core)
+    if world == 1 and not args.no_lod_sweep:
+        section("lod_sweep", run_lod_sweep)
     if world == 1 and not args.no_serving:
         section("serving", run_serving)
     if world == 1 and not args.no_train_batch:

@@ -54,6 +54,8 @@ typedef struct {
     int32_t width, height;
     float tau;         /* LoD threshold in pixels (projected size of a node, Eq. 6 reading) */
     float znear;       /* near plane, > 0 */
+    float spt_scale;   /* factor on the distances to the SPT roots (training LoD noise, 1 + 5 r^4 with
+                          r ~ U(0, 1), appendix "Varying level of detail"); 1 = none, 0 is read as 1 */
 } lodgs_camera;
 
 typedef struct {

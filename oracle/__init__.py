@@ -61,11 +61,12 @@ def stride(degree: int) -> int:
 
 
 def pack_camera(cam) -> np.ndarray:
-    """R[9], pos[3], fx, fy, cx, cy, W, H, tau, znear as float32."""
-    v = np.zeros(20, dtype=np.float32)
+    """R[9], pos[3], fx, fy, cx, cy, W, H, tau, znear, spt_scale as float32."""
+    v = np.zeros(21, dtype=np.float32)
     v[0:9] = np.asarray(cam.R, dtype=np.float32).reshape(9)
     v[9:12] = np.asarray(cam.pos, dtype=np.float32)
     v[12:20] = [cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height, cam.tau, cam.znear]
+    v[20] = getattr(cam, "spt_scale", 1.0)
     return v
 
 

@@ -422,6 +422,7 @@ int or_hspt(int64_t M, int stride, const float *rec, const int64_t *left, const 
 /* ------------------------------------------------------------------------- */
 typedef struct {
     float R[3][3], pos[3], fx, fy, cx, cy, tau, znear, inv_k, limx, limy;
+    float spt_scale;      /* factor on the SPT root distances (training LoD noise; 1 = none) */
     float plane[4][3];
     int W, H, TX, TY;
 } cam_t;
@@ -434,6 +435,7 @@ static void cam_setup(const float *c, cam_t *k) {
     k->W = (int)c[16]; k->H = (int)c[17]; k->tau = c[18]; k->znear = c[19];
     k->TX = (k->W + TILE - 1) / TILE; k->TY = (k->H + TILE - 1) / TILE;
     k->inv_k = k->tau / k->fx;
+    k->spt_scale = c[20] > 0.0f ? c[20] : 1.0f;
     float fW = (float)k->W, fH = (float)k->H;
     k->limx = 1.3f * ((0.5f * fW) / k->fx);
     k->limy = 1.3f * ((0.5f * fH) / k->fy);
@@ -494,7 +496,9 @@ static int64_t upper_bfs(int64_t n_upper, const int64_t *up_node, const int32_t 
         stats[0]++;
         if (cull && cam_culled(k, t, max_scale(r))) { stats[1]++; continue; }
         float x = dist * k->inv_k;
-        if (up_kind[u] == KIND_SPT) { sq[*nsq].j = up_ref[u]; sq[*nsq].x = x; (*nsq)++; }
+        /* LoD noise of training (appendix "Varying level of detail"): the distances to
+         * the SPT roots are multiplied by a factor (1 + 5 r^4, drawn by the caller) */
+        if (up_kind[u] == KIND_SPT) { sq[*nsq].j = up_ref[u]; sq[*nsq].x = x * k->spt_scale; (*nsq)++; }
         else if (up_kind[u] == KIND_LEAF) sel[(*nsel)++] = up_ref[u];
         else if (size_S(r) <= x) sel[(*nsel)++] = up_ref[u];
         else { queue[tail++] = up_child[2 * u]; queue[tail++] = up_child[2 * u + 1]; }

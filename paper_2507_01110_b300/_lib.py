@@ -31,7 +31,7 @@ class LodgsError(RuntimeError):
 class Camera(C.Structure):
     _fields_ = [("R", C.c_float * 9), ("pos", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
                 ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
-                ("tau", C.c_float), ("znear", C.c_float)]
+                ("tau", C.c_float), ("znear", C.c_float), ("spt_scale", C.c_float)]
 
 
 class BuildParams(C.Structure):

@@ -38,7 +38,7 @@ def _device_view(ptr: int, shape, typestr: str) -> torch.Tensor:
 
 
 def camera_struct(cam) -> _Cam:
-    """Convert a synth.Camera-like object (R, pos, fx, fy, cx, cy, width, height, tau, znear)."""
+    """Convert a synth.Camera-like object (R, pos, fx, fy, cx, cy, width, height, tau, znear[, spt_scale])."""
     c = _Cam()
     R = np.asarray(cam.R, dtype=np.float32).reshape(9)
     for i in range(9):
@@ -48,6 +48,7 @@ def camera_struct(cam) -> _Cam:
     c.fx, c.fy, c.cx, c.cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
     c.width, c.height = int(cam.width), int(cam.height)
     c.tau, c.znear = float(np.float32(cam.tau)), float(np.float32(cam.znear))
+    c.spt_scale = float(np.float32(getattr(cam, "spt_scale", 1.0)))
     return c
 
 

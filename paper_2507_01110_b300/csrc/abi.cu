@@ -38,6 +38,7 @@ CamK make_camk(const lodgs_camera &c) {
     k.TY = (c.height + TILE - 1) / TILE;
     k.znear = c.znear;
     k.inv_k = c.tau / c.fx;
+    k.spt_scale = c.spt_scale > 0.0f ? c.spt_scale : 1.0f;
     float fW = (float)c.width, fH = (float)c.height;
     k.limx = 1.3f * ((0.5f * fW) / c.fx);
     k.limy = 1.3f * ((0.5f * fH) / c.fy);
@@ -64,7 +65,7 @@ namespace {
 bool camera_ok(const lodgs_camera *c) {
     return c && c->width > 0 && c->height > 0 && c->width <= 65535 * TILE && c->height <= 65535 * TILE &&
            c->fx > 0 && c->fy > 0 && c->tau > 0 && c->znear > 0 && isfinite(c->fx) && isfinite(c->fy) &&
-           isfinite(c->cx) && isfinite(c->cy) && isfinite(c->tau);
+           isfinite(c->cx) && isfinite(c->cy) && isfinite(c->tau) && isfinite(c->spt_scale) && c->spt_scale >= 0;
 }
 
 template <typename T>

@@ -25,6 +25,7 @@ struct CamK {
     float pos[3];
     float fx, fy, cx, cy;
     float inv_k;           // tau / fx
+    float spt_scale;       // factor on the SPT root distances (training LoD noise; 1 = none)
     float limx, limy;      // 1.3 * tan(half fov)
     float plane[4][3];     // unit inward normals of the 4 side planes (camera space)
     float znear;

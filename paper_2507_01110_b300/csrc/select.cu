@@ -31,7 +31,7 @@ __device__ int upper_outcome(const UpperEntry *__restrict__ up, int u, const Cam
     if (cam_culled(k, t, e.maxs)) return OUT_NONE;
     float x = dist * k.inv_k;
     int out;
-    if (e.kind == KIND_SPT) out = OUT_SPT;
+    if (e.kind == KIND_SPT) { out = OUT_SPT; x = x * k.spt_scale; }   // LoD noise on the SPT distances
     else if (e.kind == KIND_LEAF) out = OUT_SELECT;
     else if (e.S <= x) out = OUT_SELECT;
     else return OUT_NONE;

@@ -158,7 +158,14 @@ class Camera:
     height: int
     tau: float = 1.0
     znear: float = 0.2
+    spt_scale: float = 1.0        # factor on the SPT root distances (training LoD noise)
     extra: dict = field(default_factory=dict)
+
+
+def lod_noise_factor(r: float) -> float:
+    """LoD noise of training: distances to the SPT roots are multiplied by 1 + 5 r^4,
+    r ~ U(0, 1) drawn once per iteration (appendix "Varying level of detail")."""
+    return 1.0 + 5.0 * float(r) ** 4
 
 
 def camera_look(pos, forward, right, width: int, height: int, fovx_deg: float = 60.0,

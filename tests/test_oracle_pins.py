@@ -839,3 +839,25 @@ def test_adam_constant_gradient_closed_form(oracle_lib):
     for _ in range(steps):
         oracle_lib.adam_sparse(params, m, v, t, [0], g, lr, eps=eps)
     assert np.allclose(params[0], 1.0 - steps * lr * g[0] / (np.abs(g[0]) + eps), rtol=1e-12, atol=1e-15)
+
+
+def test_lod_noise_keeps_proper_cuts_and_coarsens(oracle_lib, scene1):
+    """Training LoD noise multiplies the distances to the SPT roots by 1 + 5 r^4:
+    every scaled cut is still proper (each root-to-leaf path crossed once), equals
+    the brute-force descent at the scaled distances, and coarsens as the factor grows;
+    a factor of 1 is the plain cut."""
+    import dataclasses
+    cfg, sc = scene1
+    cam = cfg["cameras"][0]
+    plain, _ = oracle_lib.select(sc, cam, False)
+    counts = []
+    for r in (0.0, 0.3, 0.7, 1.0):
+        s = synth.lod_noise_factor(r)
+        cam_s = dataclasses.replace(cam, spt_scale=s)
+        sel, _ = oracle_lib.select(sc, cam_s, False)
+        assert np.array_equal(sel, oracle_lib.select_bruteforce(sc, cam_s, False))
+        assert np.all(_covered_leaves(sc, sel) == 1)
+        counts.append(len(sel))
+        if r == 0.0:
+            assert np.array_equal(sel, plain)
+    assert counts == sorted(counts, reverse=True) and counts[-1] < counts[0]
