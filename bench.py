@@ -594,44 +594,99 @@ def run_lod_sweep(args) -> dict:
 
 
 def run_out_of_core(args) -> dict:
+    """Out-of-core rendering: records in pinned host memory, a device cache of SPT
+    prefixes.  The flythrough with an 8 GiB cache (the headline of this section),
+    the same flythrough with smaller caches, and the loads of a training view order
+    drawn uniformly against one drawn by the kNN view scheduler."""
     import torch
-    from paper_2507_01110_b300 import api, synth
+    from paper_2507_01110_b300 import api, schedule, synth
     leaves = synth.city_leaves_t(args.ooc_leaves, seed=3, degree=3, device="cuda")
     cams = synth.flythrough_path(args.ooc_views)
     kappa = float(cams[0].fx / cams[0].tau)
     scene = api.build_hierarchy(leaves, 3, OOC_SPT_VOLUME, kappa)
     del leaves
-    cap = 8 << 30
-    cache = api.Cache(scene, capacity_bytes=cap, d_min=0.9, d_max=1.1, release_scene_rows=True)
-    torch.cuda.empty_cache()
+    rec_bytes = scene.stride * 4
     fr = api.Frame(scene)
     H, W = cams[0].height, cams[0].width
     image = torch.empty((H, W, 3), device="cuda")
     copy_stream = torch.cuda.Stream()
-    # size the frame's workspace on the path (first pass), then time a fresh cache pass
-    for cam in cams[:: max(1, len(cams) // 16)]:
-        api.stream_nodes(scene, cache, cam, fr, copy_stream=copy_stream)
-        api.render(scene, fr, rows=cache.records, image=image, check_capacity=True)
-    cache.flush()                                   # timed pass starts from an empty cache
-    torch.cuda.synchronize()
-    tot = {"spt_hits": 0, "spt_resident": 0, "spt_loaded": 0, "bytes_streamed": 0, "evictions": 0}
-    t0 = time.perf_counter()
-    for cam in cams:
-        _, st = api.stream_nodes(scene, cache, cam, fr, copy_stream=copy_stream)
-        api.render(scene, fr, rows=cache.records, image=image, check_capacity=False)
-        for k in tot:
-            tot[k] += st[k]
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    n_spt_views = tot["spt_hits"] + tot["spt_resident"] + tot["spt_loaded"]
+    keys = ("spt_hits", "spt_resident", "spt_loaded", "bytes_streamed", "evictions")
+
+    def flythrough(cache) -> dict:
+        # size the frame's workspace on the path (first pass), then time a fresh cache pass
+        for cam in cams[:: max(1, len(cams) // 16)]:
+            api.stream_nodes(scene, cache, cam, fr, copy_stream=copy_stream)
+            api.render(scene, fr, rows=cache.records, image=image, check_capacity=True)
+        cache.flush()                               # timed pass starts from an empty cache
+        torch.cuda.synchronize()
+        tot = dict.fromkeys(keys, 0)
+        t0 = time.perf_counter()
+        for cam in cams:
+            _, st = api.stream_nodes(scene, cache, cam, fr, copy_stream=copy_stream)
+            api.render(scene, fr, rows=cache.records, image=image, check_capacity=False)
+            for k in tot:
+                tot[k] += st[k]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        n_spt_views = tot["spt_hits"] + tot["spt_resident"] + tot["spt_loaded"]
+        return {"frames_per_s": round(len(cams) / wall, 2), "ms_per_frame": round(1e3 * wall / len(cams), 3),
+                "bytes_streamed_per_frame": int(tot["bytes_streamed"] / len(cams)),
+                "spt_hit_rate": round(tot["spt_hits"] / max(1, n_spt_views), 4),
+                "spt_device_resident_rate": round((tot["spt_hits"] + tot["spt_resident"]) / max(1, n_spt_views), 4),
+                "evictions": tot["evictions"]}
+
+    # cache size against frame rate (smaller caches first: they keep the scene's device rows)
+    sweep = []
+    for gib in (1, 2, 4):
+        c = api.Cache(scene, capacity_bytes=gib << 30, d_min=0.9, d_max=1.1, release_scene_rows=False)
+        try:
+            r = flythrough(c)
+            sweep.append({"cache_gib": gib, "frames_per_s": r["frames_per_s"],
+                          "bytes_streamed_per_frame": r["bytes_streamed_per_frame"],
+                          "spt_hit_rate": r["spt_hit_rate"], "evictions": r["evictions"]})
+        except Exception as e:  # noqa: BLE001  (a view whose SPT records exceed the slab)
+            torch.cuda.synchronize()
+            sweep.append({"cache_gib": gib, "error": f"{type(e).__name__}: {e}"[:160]})
+        c.close()
+        del c
+        torch.cuda.empty_cache()
+    cache = api.Cache(scene, capacity_bytes=8 << 30, d_min=0.9, d_max=1.1, release_scene_rows=True)
+    torch.cuda.empty_cache()
+    main = flythrough(cache)
+    sweep.append({"cache_gib": 8, "frames_per_s": main["frames_per_s"],
+                  "bytes_streamed_per_frame": main["bytes_streamed_per_frame"],
+                  "spt_hit_rate": main["spt_hit_rate"], "evictions": main["evictions"]})
+
+    # training view order: uniform against the kNN scheduler (LoD cut and loads only)
+    pool = [synth.camera_look(c.pos, c.R[2], c.R[0], 1920, 1080, tau=1.0)
+            for c in synth.serving_cameras(512, seed=33)]
+    iters = 256
+
+    def loads(order) -> dict:
+        cache.flush()
+        tot, cut = dict.fromkeys(keys, 0), 0
+        for v in order:
+            _, st = api.stream_nodes(scene, cache, pool[v], fr, copy_stream=copy_stream)
+            cut += fr.stats()["n_selected"]
+            for k in tot:
+                tot[k] += st[k]
+        n_spt_views = tot["spt_hits"] + tot["spt_resident"] + tot["spt_loaded"]
+        return {"nodes_loaded_per_iter": int(tot["bytes_streamed"] / rec_bytes / len(order)),
+                "cut_nodes_per_iter": int(cut / len(order)),
+                "spt_hit_rate": round(tot["spt_hits"] / max(1, n_spt_views), 4)}
+
+    uniform = loads(np.random.default_rng(34).integers(len(pool), size=iters).tolist())
+    sched = schedule.ViewScheduler(np.array([c.pos for c in pool]), k=10, seed=35)
+    knn = loads([sched.next() for _ in range(iters)])
     return {"workload": f"{args.ooc_leaves:,}-leaf SH3 city, records in pinned host memory, 8 GiB device "
                         f"cache, {len(cams)}-view flythrough 300 m -> 20 m at 1920x1080, forward only",
-            "frames_per_s": round(len(cams) / wall, 2), "ms_per_frame": round(1e3 * wall / len(cams), 3),
-            "bytes_streamed_per_frame": int(tot["bytes_streamed"] / len(cams)),
-            "spt_hit_rate": round(tot["spt_hits"] / max(1, n_spt_views), 4),
-            "spt_device_resident_rate": round((tot["spt_hits"] + tot["spt_resident"]) / max(1, n_spt_views), 4),
-            "evictions": tot["evictions"], "host_record_gb": round(scene.n_nodes * scene.stride * 4 / 1e9, 2),
-            "reuse_window": [0.9, 1.1]}
+            **main, "host_record_gb": round(scene.n_nodes * scene.stride * 4 / 1e9, 2), "reuse_window": [0.9, 1.1],
+            "cache_size_sweep": sweep,
+            "view_selection": {"pool_views": len(pool), "iterations": iters,
+                               "note": "nodes loaded from host per training iteration; a cache-less run loads "
+                                       "the whole cut (cut_nodes_per_iter)",
+                               "uniform_views": uniform, "knn_scheduler": knn,
+                               "knn": {"k": 10, "W": round(sched.W, 2), "random_every": 128}}}
 
 
 TRAIN_SPT_VOLUME = 150.0      # per-scene HSPT size for the 150M-leaf city

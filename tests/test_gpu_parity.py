@@ -233,3 +233,17 @@ def test_orderings_agree_on_a_1080p_view(api):
     assert np.array_equal(res[0][2], res[1][2])
     scale = np.abs(res[1][3]).max(axis=0, keepdims=True) + 1e-12
     assert (np.abs(res[0][3] - res[1][3]) / scale).max() < 1e-4
+
+
+def test_select_with_lod_noise_matches_oracle(api, c1):
+    """LoD noise (distances to the SPT roots times 1 + 5 r^4): bit-exact cut."""
+    import dataclasses
+    _, sc_o, sc_g = c1
+    fr = api.Frame(sc_g)
+    for cam in _cams_c1()[:3]:
+        for r in (0.35, 0.8, 1.0):
+            cam_s = dataclasses.replace(cam, spt_scale=synth.lod_noise_factor(r))
+            sel_o, st_o = oracle.select(sc_o, cam_s)
+            api.select_lod(sc_g, cam_s, fr)
+            assert np.array_equal(fr.selection().cpu().numpy(), sel_o)
+            assert fr.stats()["n_spt_scanned"] == st_o["spt_scanned"]
