@@ -65,12 +65,14 @@ typedef struct {
 } lodgs_build_params;
 
 typedef struct {
-    int64_t n_leaves, n_nodes;       /* n_nodes = 2 n_leaves - 1 */
+    int64_t n_leaves, n_nodes;       /* n_nodes = 2 n_leaves - 1 (every internal node has two children) */
     int64_t n_upper;                 /* entries of the upper hierarchy (BFS order), SPT roots included */
     int64_t n_upper_rows;            /* upper nodes that are not SPT roots (render rows 0..n_upper_rows-1) */
     int64_t n_spt;                   /* number of SPTs */
     int32_t sh_degree, stride;
     float *d_rows;                   /* device, library-owned: n_nodes x stride records in render-row order */
+    int64_t root;                    /* canonical id of the root (n_nodes-1 until a densification moves it) */
+    int64_t layout_version;          /* 0 after the build, +1 per lodgs_scene_densify */
 } lodgs_scene_info;
 
 typedef struct {
@@ -113,7 +115,7 @@ int lodgs_scene_get_info(const lodgs_scene *scene, lodgs_scene_info *info);
 /*
  * Copy the scene structure to host buffers (any pointer may be NULL to skip).
  * Canonical node ids: leaves 0..n-1 in input order, internal nodes n.. in merge
- * order, root n_nodes-1.
+ * order, root n_nodes-1; after lodgs_scene_densify the ids it documents.
  *   node_rec   n_nodes x stride   records by canonical id
  *   left,right n_nodes            children (-1 for leaves)
  *   up_node, up_kind (0 internal, 1 leaf, 2 SPT root), up_parent, up_ref
@@ -126,6 +128,45 @@ int lodgs_scene_export(const lodgs_scene *scene, float *node_rec, int64_t *left,
                        int64_t *up_node, int32_t *up_kind, int64_t *up_parent, int64_t *up_ref,
                        int64_t *spt_root, int64_t *spt_base, int64_t *spt_count,
                        int64_t *node_of_row, float *lo_row, float *hi_row);
+
+/*
+ * Densification by moving Gaussians (Sec. 3 "Densification"): a batch of
+ * operations on leaves, after which the HSPT and SPT layout are rebuilt
+ * (Sec. 4.3, Algorithm 1 split and Sec. 4.1 intervals) with the scene's
+ * build parameters.
+ *   LODGS_DENSIFY_SPAWN    leaf `target` becomes an internal node with two new
+ *                          leaf children (canonical ids n_nodes, n_nodes+1 in
+ *                          operation order); n_nodes grows by 2.
+ *   LODGS_DENSIFY_RESPAWN  leaf `dead` and its parent P leave their places: the
+ *                          sibling of `dead` takes P's place under P's parent
+ *                          (or becomes the root), and P and `dead` become the
+ *                          two children of leaf `target`; n_nodes is unchanged.
+ * In both, the two children carry the split of the target's record: its mean,
+ * rotation and colour; opacity o' = 1 - sqrt(1 - o); scales times
+ * sqrt(o / (2 o' - o'^2 / 2)) (float32, as written); the target keeps its own
+ * record and becomes their parent.  `target` and `dead` are render rows of the
+ * layout before the call and must be leaves of it; a node made by an earlier
+ * operation of the same batch cannot be a target or dead, and `dead` != `target`.
+ * ops[i].dead is ignored for SPAWN.
+ *   old_row_of_new_row  host, capacity >= the new n_nodes: for each render row of
+ *                       the new layout, the row the node held before the call,
+ *                       or -1 for a node whose record is new (the children).
+ *                       Per-row state follows it through lodgs_gather_rows.
+ * Render rows are renumbered: frames and caches created before the call are
+ * rejected afterwards (LODGS_E_STATE) and must be recreated.  Requires the
+ * scene's records on the device (LODGS_E_STATE after a cache released them).
+ * Invalid operations leave the scene unchanged (LODGS_E_INVALID).  Synchronous.
+ */
+#define LODGS_DENSIFY_SPAWN 0
+#define LODGS_DENSIFY_RESPAWN 1
+typedef struct {
+    int32_t kind;      /* LODGS_DENSIFY_SPAWN or LODGS_DENSIFY_RESPAWN */
+    int32_t pad_;
+    int64_t target;    /* render row of a leaf to split */
+    int64_t dead;      /* RESPAWN: render row of the leaf that is moved */
+} lodgs_densify_op;
+int lodgs_scene_densify(lodgs_scene *scene, const lodgs_densify_op *ops, int64_t n_ops,
+                        int32_t *old_row_of_new_row, int64_t capacity);
 
 /* Per-view state: selection, projected splats, sorted pairs and workspace.
  * Buffers grow on demand; a frame may be reused for any camera and resolution
@@ -273,6 +314,17 @@ int lodgs_render_backward(lodgs_scene *scene, lodgs_frame *frame, const float *r
  */
 int lodgs_accumulate_grads(lodgs_scene *scene, lodgs_frame *const *frames, const float *const *grads, int n_views,
                            uint32_t *out_rows, float *out_grads, int64_t capacity, uint32_t *d_count, void *stream);
+
+/*
+ * Row gather for per-row state across a densification (its old_row_of_new_row):
+ * dst[r] = src[src_row[r]] for r < n_rows, each row `row_words` 32-bit words
+ * (floats or step counts alike); rows whose src_row is -1 (or >= n_src) are
+ * zero, the fresh state of a new node.  src (n_src rows), dst (n_rows rows) and
+ * src_row (n_rows int32) are device pointers; src and dst must not overlap.
+ * Asynchronous on `stream`.
+ */
+int lodgs_gather_rows(const void *src, int64_t n_src, void *dst, const int32_t *src_row, int64_t n_rows,
+                      int32_t row_words, void *stream);
 
 /*
  * Sparse Adam step over the cut set (appendix "Implementation Details": only

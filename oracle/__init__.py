@@ -14,6 +14,9 @@ Functions and the paper passage they follow:
   sort_pairs       tile x depth ordering (3DGS sort reused by the paper)
   blend            Eq. 1 front-to-back compositing
   render_backward  exact derivative of blend + projection
+  split_record, densify
+                   densification by moving Gaussians (Sec. 3 "Densification",
+                   the 3DGS-MCMC split) and the HSPT rebuild after it
 """
 from __future__ import annotations
 
@@ -159,6 +162,103 @@ def hspt(h: dict, spt_volume: float, kappa: float) -> dict:
 def build_scene(leaves: np.ndarray, degree: int, spt_volume: float, kappa: float) -> dict:
     """Leaves -> binary hierarchy -> HSPT with SPT layout (render-row order)."""
     return hspt(merge_hierarchy(leaves, degree), spt_volume, kappa)
+
+
+# ---------------------------------------------------------------------------
+# densification (Sec. 3 "Densification")
+# ---------------------------------------------------------------------------
+DENSIFY_SPAWN, DENSIFY_RESPAWN = 0, 1
+REC_S, REC_OP = 3, 10
+
+
+def split_record(rec: np.ndarray) -> np.ndarray:
+    """The record each of the two children of a split leaf carries: the same
+    mean, rotation and colour; opacity o' with 1 - (1 - o')^2 = o (the centre's
+    composited opacity is kept) and scales times f, f^2 = o / (2 o' - o'^2 / 2)
+    (the opacity integrated over the image plane is kept).  Records are float32
+    and both sides evaluate these five operations in float32, in this order,
+    because the HSPT volume test and the SPT bounds are float32 decisions on
+    the result."""
+    f32 = np.float32
+    out = np.array(rec, dtype=np.float32, copy=True)
+    sg = f32(rec[REC_OP])
+    if not sg > 0:
+        return out
+    sp = f32(1) - np.sqrt(f32(1) - sg)
+    f = np.sqrt(sg / (f32(2) * sp - (sp * sp) / f32(2)))
+    out[REC_OP] = sp
+    out[REC_S:REC_S + 3] = (np.asarray(rec[REC_S:REC_S + 3], np.float32) * f).astype(np.float32)
+    return out
+
+
+def densify(scene: dict, ops) -> tuple[dict, np.ndarray]:
+    """Apply spawn / respawn operations (kind, target row, dead row) given in
+    the scene's render rows, in order, then rebuild the HSPT and SPT layout with
+    the scene's own spt_volume and kappa.
+
+    spawn:   leaf T gets two new leaf children with the next free canonical ids.
+    respawn: dead leaf D and its parent P leave; D's sibling takes P's place
+             (the root's place if P was the root); P and D become T's children.
+    Both children carry split_record(T); T keeps its record and is their parent.
+    Returns the new scene and, per new render row, the row the node had before
+    (-1 for a node whose record is new)."""
+    node = scene["node_rec"]
+    M0, st = node.shape
+    nor0 = np.asarray(scene["node_of_row"], np.int64)
+    row_of_node0 = np.empty(M0, np.int64)
+    row_of_node0[nor0] = np.arange(M0)
+    n_spawn = sum(1 for k, _, _ in ops if k == DENSIFY_SPAWN)
+    M = M0 + 2 * n_spawn
+    left = np.full(M, -1, np.int64)
+    right = np.full(M, -1, np.int64)
+    left[:M0], right[:M0] = scene["left"], scene["right"]
+    parent = np.full(M, -1, np.int64)
+    for u in range(M0):
+        for c in (left[u], right[u]):
+            if c >= 0:
+                parent[c] = u
+    root = int(scene["root"])
+    rec = np.zeros((M, st), np.float32)
+    rec[:M0] = node
+    fresh = np.zeros(M, bool)
+    nxt = M0
+    for kind, t_row, d_row in ops:
+        T = int(nor0[t_row])
+        if left[T] >= 0 or fresh[T]:
+            raise ValueError("densify: the target is not an original leaf")
+        if kind == DENSIFY_SPAWN:
+            a, b = nxt, nxt + 1
+            nxt += 2
+        elif kind == DENSIFY_RESPAWN:
+            D = int(nor0[d_row])
+            P = int(parent[D])
+            if left[D] >= 0 or fresh[D] or D == T or P < 0:
+                raise ValueError("densify: the dead node must be an original leaf with a parent, not the target")
+            S = int(right[P]) if left[P] == D else int(left[P])
+            G = int(parent[P])
+            if G >= 0:
+                if left[G] == P:
+                    left[G] = S
+                else:
+                    right[G] = S
+            else:
+                root = S
+            parent[S] = G
+            a, b = P, D
+        else:
+            raise ValueError("densify: unknown operation")
+        child = split_record(rec[T])
+        left[T], right[T] = a, b
+        parent[a] = parent[b] = T
+        left[a] = right[a] = left[b] = right[b] = -1
+        rec[a] = rec[b] = child
+        fresh[a] = fresh[b] = True
+    h = {"n_leaves": (M + 1) // 2, "degree": scene["degree"], "stride": st, "node_rec": rec, "left": left,
+         "right": right, "parent": parent, "root": root}
+    out = hspt(h, scene["spt_volume"], scene["kappa"])
+    nor = out["node_of_row"]
+    old = np.where((nor < M0) & ~fresh[nor], row_of_node0[np.minimum(nor, M0 - 1)], -1)
+    return out, old
 
 
 # ---------------------------------------------------------------------------

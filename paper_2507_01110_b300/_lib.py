@@ -41,7 +41,14 @@ class BuildParams(C.Structure):
 class SceneInfo(C.Structure):
     _fields_ = [("n_leaves", C.c_int64), ("n_nodes", C.c_int64), ("n_upper", C.c_int64),
                 ("n_upper_rows", C.c_int64), ("n_spt", C.c_int64), ("sh_degree", C.c_int32),
-                ("stride", C.c_int32), ("d_rows", C.c_void_p)]
+                ("stride", C.c_int32), ("d_rows", C.c_void_p), ("root", C.c_int64), ("layout_version", C.c_int64)]
+
+
+class DensifyOp(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("target", C.c_int64), ("dead", C.c_int64)]
+
+
+DENSIFY_SPAWN, DENSIFY_RESPAWN = 0, 1
 
 
 class CacheParams(C.Structure):
@@ -72,6 +79,8 @@ _SIGS = {
     "lodgs_scene_free": (None, [_P]),
     "lodgs_scene_get_info": (C.c_int, [_P, C.POINTER(SceneInfo)]),
     "lodgs_scene_export": (C.c_int, [_P] + [_P] * 13),
+    "lodgs_scene_densify": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64]),
+    "lodgs_gather_rows": (C.c_int, [_P, C.c_int64, _P, _P, C.c_int64, C.c_int32, _P]),
     "lodgs_frame_create": (C.c_int, [_P, C.POINTER(_P)]),
     "lodgs_frame_free": (None, [_P]),
     "lodgs_select_lod": (C.c_int, [_P, C.POINTER(Camera), _P, _P]),

@@ -57,12 +57,37 @@ class Scene:
 
     def __init__(self, handle: C.c_void_p):
         self._h = handle
+        self._refresh()
+
+    def _refresh(self):
         info = _lib.SceneInfo()
         check(lib().lodgs_scene_get_info(self._h, C.byref(info)))
         self.n_leaves, self.n_nodes = info.n_leaves, info.n_nodes
         self.n_upper, self.n_upper_rows, self.n_spt = info.n_upper, info.n_upper_rows, info.n_spt
         self.sh_degree, self.stride = info.sh_degree, info.stride
+        self.root, self.layout_version = info.root, info.layout_version
         self._rows_ptr = info.d_rows
+
+    def densify(self, spawn=(), respawn=()) -> np.ndarray:
+        """Densification by moving Gaussians (Sec. 3): `spawn` lists render rows of
+        leaves that each get two new children; `respawn` lists (target, dead)
+        pairs of leaf rows, where the dead leaf and its parent become the target's
+        children.  Both carry the split of the target's record.  Operations run
+        spawn first, then respawn, in list order.  Rebuilds the HSPT/SPT layout;
+        frames and caches made earlier must be recreated.  Returns, per new
+        render row, the row the node held before (-1 for the new children), to
+        carry per-row state such as Adam moments across."""
+        ops = [(_lib.DENSIFY_SPAWN, int(t), -1) for t in spawn] + \
+              [(_lib.DENSIFY_RESPAWN, int(t), int(d)) for t, d in respawn]
+        arr = (_lib.DensifyOp * max(len(ops), 1))()
+        for i, (k, t, d) in enumerate(ops):
+            arr[i].kind, arr[i].target, arr[i].dead = k, t, d
+        cap = self.n_nodes + 2 * len(spawn)
+        out = np.zeros(cap, np.int32)
+        rc = lib().lodgs_scene_densify(self._h, C.cast(arr, C.c_void_p), len(ops), C.c_void_p(out.ctypes.data), cap)
+        self._refresh()
+        check(rc)
+        return out[:self.n_nodes]
 
     @property
     def handle(self):
@@ -72,6 +97,17 @@ class Scene:
         """The scene's node records in render-row order (n_nodes x stride), a
         zero-copy view of library-owned device memory valid while the scene lives."""
         return _device_view(self._rows_ptr, (self.n_nodes, self.stride), "<f4")
+
+    def topology(self) -> dict:
+        """Children (canonical ids, -1 for leaves), node_of_row and the root, copied
+        to the host; what densification planning needs without the records."""
+        M = self.n_nodes
+        a = {"left": np.zeros(M, np.int64), "right": np.zeros(M, np.int64), "node_of_row": np.zeros(M, np.int64)}
+        ptr = {k: C.c_void_p(v.ctypes.data) for k, v in a.items()}
+        check(lib().lodgs_scene_export(self._h, None, ptr["left"], ptr["right"], None, None, None, None, None, None,
+                                       None, ptr["node_of_row"], None, None))
+        a["root"] = self.root
+        return a
 
     def export(self) -> dict:
         M, U, S, st = self.n_nodes, self.n_upper, self.n_spt, self.stride
@@ -88,7 +124,7 @@ class Scene:
         for k in ("spt_root", "spt_base", "spt_count"):
             a[k] = a[k][:S]
         a.update({"n_upper": U, "n_spt": S, "n_upper_rows": self.n_upper_rows, "stride": st,
-                  "degree": self.sh_degree, "n_leaves": self.n_leaves})
+                  "degree": self.sh_degree, "n_leaves": self.n_leaves, "root": self.root})
         return a
 
     def close(self):
@@ -263,6 +299,22 @@ def accumulate_grads(scene: Scene, frames: list, grads: list, stream=None) -> tu
     return out_rows[:k].to(torch.int64), out_grads[:k]
 
 
+def gather_rows(src: torch.Tensor, src_row, stream=None) -> torch.Tensor:
+    """New tensor whose row r is src[src_row[r]], zeros where src_row[r] is -1
+    (a densification's old_row_of_new_row; the gather runs in the library's
+    kernel).  src: CUDA tensor of a 4-byte dtype, rows along dim 0."""
+    assert src.is_cuda and src.element_size() == 4 and src.is_contiguous()
+    idx = torch.as_tensor(np.ascontiguousarray(src_row, dtype=np.int32)).to("cuda", non_blocking=False)
+    n = idx.numel()
+    words = int(np.prod(src.shape[1:])) if src.dim() > 1 else 1
+    out = torch.empty((n,) + tuple(src.shape[1:]), dtype=src.dtype, device="cuda")
+    check(lib().lodgs_gather_rows(C.c_void_p(src.data_ptr()), C.c_int64(src.shape[0]), C.c_void_p(out.data_ptr()),
+                                  C.c_void_p(idx.data_ptr()), C.c_int64(n), C.c_int32(words), _stream_ptr(stream)))
+    if stream is not None:
+        idx.record_stream(stream)        # freed on return: keep it until `stream` is done with it
+    return out
+
+
 class AdamState:
     """Sparse Adam state of a scene's records (device float32 m, v; uint32 step counts)."""
 
@@ -270,6 +322,14 @@ class AdamState:
         self.m = torch.zeros((scene.n_nodes, scene.stride), dtype=torch.float32, device="cuda")
         self.v = torch.zeros_like(self.m)
         self.t = torch.zeros(scene.n_nodes, dtype=torch.int32, device="cuda")
+
+    def remap(self, old_row_of_new_row) -> None:
+        """Carry the state across a densification: each node keeps its moments
+        and step count, new nodes start from zero (as 3DGS-MCMC resets the
+        state of relocated Gaussians)."""
+        self.m = gather_rows(self.m, old_row_of_new_row)
+        self.v = gather_rows(self.v, old_row_of_new_row)
+        self.t = gather_rows(self.t, old_row_of_new_row)
 
 
 def adam_step(scene: Scene, params: torch.Tensor, state: AdamState, rows: torch.Tensor, grads: torch.Tensor, lr,

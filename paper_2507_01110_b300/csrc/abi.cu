@@ -138,6 +138,20 @@ int set_view(lodgs_frame *fr, const lodgs_camera *cam, const float *bg, cudaStre
 
 }  // namespace
 
+namespace lodgs {
+int check_frame(const lodgs_scene *sc, const lodgs_frame *fr, const char *who) {
+    if (!sc || !fr || fr->scene != sc) {
+        set_error(std::string(who) + ": frame does not belong to scene");
+        return LODGS_E_INVALID;
+    }
+    if (fr->layout_version != sc->layout_version) {
+        set_error(std::string(who) + ": the frame was created before the scene was densified; create a new frame");
+        return LODGS_E_STATE;
+    }
+    return LODGS_OK;
+}
+}  // namespace lodgs
+
 extern "C" {
 
 const char *lodgs_last_error(void) { return g_err.c_str(); }
@@ -179,8 +193,19 @@ int lodgs_scene_get_info(const lodgs_scene *sc, lodgs_scene_info *info) {
     info->n_leaves = sc->n_leaves; info->n_nodes = sc->n_nodes; info->n_upper = sc->n_upper;
     info->n_upper_rows = sc->n_upper_rows; info->n_spt = sc->n_spt;
     info->sh_degree = sc->sh_degree; info->stride = sc->stride; info->d_rows = sc->d_rows;
+    info->root = sc->root; info->layout_version = sc->layout_version;
     return LODGS_OK;
 }
+
+int lodgs_scene_densify(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, int32_t *old_row_of_new_row,
+                        int64_t capacity) {
+    if (!sc || (n_ops > 0 && !ops) || n_ops < 0 || !old_row_of_new_row) {
+        set_error("scene_densify: NULL or negative argument");
+        return LODGS_E_INVALID;
+    }
+    return densify_scene(sc, ops, n_ops, old_row_of_new_row, capacity);
+}
+
 
 int lodgs_scene_export(const lodgs_scene *sc, float *node_rec, int64_t *left, int64_t *right, int64_t *up_node,
                        int32_t *up_kind, int64_t *up_parent, int64_t *up_ref, int64_t *spt_root, int64_t *spt_base,
@@ -235,6 +260,7 @@ int lodgs_frame_create(lodgs_scene *sc, lodgs_frame **out) {
     lodgs_frame *fr = new (std::nothrow) lodgs_frame();
     if (!fr) { set_error("frame_create: host allocation failed"); return LODGS_E_OOM; }
     fr->scene = sc;
+    fr->layout_version = sc->layout_version;
     FrameBufs &f = fr->f;
     const int64_t M = sc->n_nodes, S = sc->n_spt;
     cudaError_t e = cudaSuccess;
@@ -277,7 +303,7 @@ int lodgs_frame_set_view(lodgs_frame *fr, const lodgs_camera *cam, const float *
 }
 
 int lodgs_select_lod(lodgs_scene *sc, const lodgs_camera *cam, lodgs_frame *fr, void *stream) {
-    if (!sc || !fr || fr->scene != sc) { set_error("select_lod: frame does not belong to scene"); return LODGS_E_INVALID; }
+    if (int rc = check_frame(sc, fr, "select_lod")) return rc;
     if (cam ? !camera_ok(cam) : !fr->have_view) {
         set_error(cam ? "select_lod: invalid camera" : "select_lod: no camera given and none set on the frame");
         return LODGS_E_INVALID;
@@ -311,7 +337,8 @@ int lodgs_frame_selection(lodgs_frame *fr, const uint32_t **d_rows, int64_t *n_s
 }
 
 int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const float *bg, float *image, void *stream) {
-    if (!sc || !fr || fr->scene != sc || !image) { set_error("render: NULL or mismatched argument"); return LODGS_E_INVALID; }
+    if (int rc = check_frame(sc, fr, "render")) return rc;
+    if (!image) { set_error("render: NULL image"); return LODGS_E_INVALID; }
     if (!fr->selected) { set_error("render: select_lod was not called on this frame"); return LODGS_E_STATE; }
     cudaStream_t st = (cudaStream_t)stream;
     if (st != fr->stream) {       // order after the selection's stream
@@ -358,8 +385,9 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
 
 int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const float *dL_dimage,
                                 void *stream) {
-    if (!sc || !fr || fr->scene != sc || !image || !dL_dimage) {
-        set_error("render_backward_blend: NULL or mismatched argument");
+    if (int rc = check_frame(sc, fr, "render_backward_blend")) return rc;
+    if (!image || !dL_dimage) {
+        set_error("render_backward_blend: NULL argument");
         return LODGS_E_INVALID;
     }
     if (!fr->rendered) { set_error("render_backward: render was not called on this frame"); return LODGS_E_STATE; }
@@ -386,8 +414,9 @@ int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *i
 
 int lodgs_render_backward_project(lodgs_scene *sc, lodgs_frame *fr, const float *rows, float *grad_rows, int dense,
                                   void *stream) {
-    if (!sc || !fr || fr->scene != sc || !grad_rows) {
-        set_error("render_backward_project: NULL or mismatched argument");
+    if (int rc = check_frame(sc, fr, "render_backward_project")) return rc;
+    if (!grad_rows) {
+        set_error("render_backward_project: NULL argument");
         return LODGS_E_INVALID;
     }
     if (!fr->blend_bwd_done) { set_error("render_backward_project: the blend backward has not run"); return LODGS_E_STATE; }
@@ -413,8 +442,9 @@ int lodgs_render_backward_project(lodgs_scene *sc, lodgs_frame *fr, const float 
 
 int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const float *bg,
                           const float *image, const float *dL_dimage, float *grad_rows, int dense, void *stream) {
-    if (!sc || !fr || fr->scene != sc || !image || !dL_dimage || !grad_rows) {
-        set_error("render_backward: NULL or mismatched argument");
+    if (int rc = check_frame(sc, fr, "render_backward")) return rc;
+    if (!image || !dL_dimage || !grad_rows) {
+        set_error("render_backward: NULL argument");
         return LODGS_E_INVALID;
     }
     if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2])) {

@@ -6,7 +6,9 @@
 // covers the steps it took part in.  Sixteen-byte quarters of a row are spread
 // over threads (coalesced).  The screen-space mean gradient dL/d(u, v) of
 // every selected Gaussian is also reduced to a per-node maximum over views, the
-// quantity densification ranks nodes by.
+// quantity densification ranks nodes by.  After a densification renumbers the
+// rows, per-row state (parameters' moments, step counts, gradient statistics)
+// follows its node through a row gather.
 #include <algorithm>
 
 #include "lodgs_internal.cuh"
@@ -75,7 +77,38 @@ __global__ void __launch_bounds__(AB) k_screen_grad_max(const uint32_t *__restri
     }
 }
 
+// dst[r] = src[src_row[r]] (row_words 32-bit words), zeros where src_row[r] is
+// -1 or not below n_src.  One thread per word: consecutive threads read
+// consecutive words of a row.
+__global__ void __launch_bounds__(AB) k_gather_rows(const uint32_t *__restrict__ src, int64_t n_src,
+                                                    uint32_t *__restrict__ dst, const int32_t *__restrict__ src_row,
+                                                    int64_t n_rows, int row_words) {
+    const int64_t total = n_rows * row_words;
+    for (int64_t e = (int64_t)blockIdx.x * AB + threadIdx.x; e < total; e += (int64_t)gridDim.x * AB) {
+        const int64_t r = e / row_words;
+        const int c = (int)(e % row_words);
+        const int32_t s = src_row[r];
+        dst[e] = (s >= 0 && s < n_src) ? src[(int64_t)s * row_words + c] : 0u;
+    }
+}
+
 }  // namespace
+
+extern "C" int lodgs_gather_rows(const void *src, int64_t n_src, void *dst, const int32_t *src_row, int64_t n_rows,
+                                 int32_t row_words, void *stream) {
+    if (n_rows < 0 || n_src < 0 || row_words <= 0 || (n_rows > 0 && (!src_row || !dst || (n_src > 0 && !src)))) {
+        set_error("gather_rows: NULL argument or bad size");
+        return LODGS_E_INVALID;
+    }
+    if (src && dst && src == dst) { set_error("gather_rows: src and dst must not alias"); return LODGS_E_INVALID; }
+    if (n_rows == 0) return LODGS_OK;
+    const int64_t blocks = std::min<int64_t>((n_rows * row_words + AB - 1) / AB, 148 * 32);
+    k_gather_rows<<<(unsigned)blocks, AB, 0, (cudaStream_t)stream>>>(
+        static_cast<const uint32_t *>(src), n_src, static_cast<uint32_t *>(dst), src_row, n_rows, row_words);
+    count_launches(1);
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
 
 extern "C" int lodgs_adam_step(lodgs_scene *sc, float *params, float *m, float *v, uint32_t *t, const uint32_t *rows,
                                const float *grads, const uint32_t *d_n, int64_t max_n, const float *lr, float b1,
@@ -109,6 +142,7 @@ extern "C" int lodgs_adam_step(lodgs_scene *sc, float *params, float *m, float *
 
 extern "C" int lodgs_frame_screen_grad_max(lodgs_frame *fr, float *max_per_node, void *stream) {
     if (!fr || !max_per_node) { set_error("frame_screen_grad_max: NULL argument"); return LODGS_E_INVALID; }
+    if (int rc = check_frame(fr->scene, fr, "frame_screen_grad_max")) return rc;
     if (!fr->blend_bwd_done) { set_error("frame_screen_grad_max: no backward on this frame's last render"); return LODGS_E_STATE; }
     k_screen_grad_max<<<148 * 4, AB, 0, (cudaStream_t)stream>>>(fr->f.sel_rows, fr->f.g2d, fr->f.cnt,
                                                                reinterpret_cast<unsigned int *>(max_per_node));

@@ -79,8 +79,9 @@ extern "C" int lodgs_accumulate_grads(lodgs_scene *sc, lodgs_frame *const *frame
     std::vector<uint64_t> gp(n_views);
     for (int v = 0; v < n_views; ++v) {
         lodgs_frame *fr = frames[v];
-        if (!fr || fr->scene != sc || !fr->rendered || !grads[v]) {
-            set_error("accumulate_grads: every view needs a rendered frame of this scene and its gradient rows");
+        if (!fr || fr->scene != sc || fr->layout_version != sc->layout_version || !fr->rendered || !grads[v]) {
+            set_error("accumulate_grads: every view needs a rendered frame of this scene's current layout and its "
+                      "gradient rows");
             return LODGS_E_STATE;
         }
         LODGS_CUDA(cudaStreamSynchronize(fr->stream));

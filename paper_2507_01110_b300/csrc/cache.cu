@@ -45,6 +45,7 @@ struct Entry {
 
 struct lodgs_cache {
     lodgs_scene *scene = nullptr;
+    uint32_t layout_version = 0;      // the scene layout the host copy and slab follow
     float d_min = 1.f, d_max = 1.f;
     uint64_t slab_records = 0;
     float *h_rows = nullptr;          // pinned, n_nodes x stride
@@ -119,6 +120,7 @@ int lodgs_cache_create(lodgs_scene *sc, const lodgs_cache_params *p, lodgs_cache
     lodgs_cache *c = new (std::nothrow) lodgs_cache();
     if (!c) { set_error("cache_create: host allocation failed"); return LODGS_E_OOM; }
     c->scene = sc;
+    c->layout_version = sc->layout_version;
     c->d_min = p->d_min;
     c->d_max = p->d_max;
     const size_t rec = (size_t)sc->stride * sizeof(float);
@@ -187,9 +189,14 @@ int lodgs_cache_records(lodgs_cache *c, float **d_records) {
 
 int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam, lodgs_frame *fr, void *stream,
                        void *copy_stream, lodgs_stream_stats *stats) {
-    if (!sc || !c || !cam || !fr || c->scene != sc || fr->scene != sc) {
+    if (!c || !cam || c->scene != sc) {
         set_error("stream_nodes: NULL or mismatched argument");
         return LODGS_E_INVALID;
+    }
+    if (int rc = check_frame(sc, fr, "stream_nodes")) return rc;
+    if (c->layout_version != sc->layout_version) {
+        set_error("stream_nodes: the cache was created before the scene was densified; create a new cache");
+        return LODGS_E_STATE;
     }
     if (!(cam->width > 0 && cam->height > 0 && cam->fx > 0 && cam->fy > 0 && cam->tau > 0 && cam->znear > 0)) {
         set_error("stream_nodes: invalid camera");

@@ -102,6 +102,8 @@ struct lodgs_scene {
     int sh_degree = 0, stride = 0;
     float spt_volume = 0.f, kappa = 0.f;
     int upper_depth = 0;                         // max depth of the upper hierarchy
+    uint32_t layout_version = 0;                 // bumped by each densification (rows renumbered)
+    int32_t root = -1;                           // canonical id of the root
     // device
     float *d_rows = nullptr;                     // n_nodes x stride, render-row order
     lodgs::UpperEntry *d_upper = nullptr;        // n_upper
@@ -172,6 +174,11 @@ int cuda_fail(cudaError_t e, const char *what);
 int build_scene(const float *leaves, int64_t n, int degree, int on_device, const lodgs_build_params &p,
                 lodgs_scene *sc);
 void free_scene(lodgs_scene *sc);
+int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, int32_t *old_row_of_new_row,
+                  int64_t capacity);
+// 0 if `fr` belongs to `sc` and was created for its current layout, else an
+// error code (with the message set, prefixed by `who`)
+int check_frame(const lodgs_scene *sc, const lodgs_frame *fr, const char *who);
 
 // radix sort and scans (sort.cu).  All take element counts from device memory so
 // that no host synchronisation is needed between stages.
@@ -218,6 +225,7 @@ int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs 
 
 struct lodgs_frame {
     lodgs_scene *scene = nullptr;
+    uint32_t layout_version = 0;        // the scene layout the buffers were sized for
     lodgs::FrameBufs f;
     uint32_t *h_cnt = nullptr;          // pinned mirror of the device counters
     cudaStream_t stream = 0;

@@ -384,6 +384,49 @@ __global__ void k_upper_rows(const int32_t *__restrict__ up_node, const int32_t 
     hi_row[up_ref[u]] = NAN;
 }
 
+// The two children of a densified leaf (Sec. 3 "Densification", after the
+// split of 3DGS-MCMC): both keep the target's mean, rotation and colour.  Their
+// opacity o' satisfies 1 - (1 - o')^2 = o, so the composited opacity at the
+// centre is unchanged; their scales are the target's times f with
+// f^2 = o / (2 o' - o'^2 / 2), so that the opacity the pair integrates over
+// the image plane, (2 o' - o'^2 / 2) f^2 A, equals the target's o A (A the
+// target's footprint area).  float32 with IEEE sqrt and division, evaluated as
+// written.  trip[3i..3i+2] = (target, child a, child b), canonical ids.
+__global__ void k_split_children(float *__restrict__ node_rec, int stride, const int32_t *__restrict__ trip,
+                                 int64_t n_ops) {
+    int64_t t = blockIdx.x * (int64_t)BT + threadIdx.x;
+    if (t >= n_ops * stride) return;
+    const int64_t i = t / stride;
+    const int c = (int)(t % stride);
+    const int32_t T = trip[3 * i], a = trip[3 * i + 1], b = trip[3 * i + 2];
+    const float *rec = node_rec + (int64_t)T * stride;
+    float v = rec[c];
+    const float sg = rec[REC_OP];
+    if (sg > 0.0f && (c == REC_OP || (c >= REC_S && c < REC_S + 3))) {
+        const float sp = 1.0f - sqrtf(1.0f - sg);
+        if (c == REC_OP) {
+            v = sp;
+        } else {
+            const float f = sqrtf(sg / (2.0f * sp - (sp * sp) / 2.0f));
+            v = v * f;
+        }
+    }
+    node_rec[(int64_t)a * stride + c] = v;
+    node_rec[(int64_t)b * stride + c] = v;
+}
+
+// canonical records from render rows: node_rec[node_of_row[r]] = rows[r]
+__global__ void k_unpermute_rows(const float *__restrict__ rows, const int32_t *__restrict__ node_of_row, int64_t M,
+                                 int stride, float *__restrict__ node_rec) {
+    int64_t t = blockIdx.x * (int64_t)BT + threadIdx.x;
+    int q = stride / 4;
+    if (t >= M * q) return;
+    int64_t row = t / q;
+    int c = (int)(t % q);
+    reinterpret_cast<float4 *>(node_rec)[(int64_t)node_of_row[row] * q + c] =
+        reinterpret_cast<const float4 *>(rows)[row * q + c];
+}
+
 __global__ void k_permute_rows(const float *__restrict__ node_rec, const int32_t *__restrict__ node_of_row,
                                int64_t M, int stride, float *__restrict__ rows) {
     int64_t t = blockIdx.x * (int64_t)BT + threadIdx.x;
@@ -437,6 +480,150 @@ void free_scene(lodgs_scene *sc) {
 }
 
 #define CK(x) LODGS_CUDA(x)
+
+// HSPT and SPT layout of a hierarchy (canonical records node_rec, children
+// left/right, parent, root): the level-synchronous BFS of Algorithm 1 (SPT roots
+// where the volume drops below spt_volume), the clamped SPT intervals, the SPT
+// row layout (per SPT by descending hi) and the render-row records.  Used by the
+// build and by the rebuild after densification; the scene's previous layout is
+// replaced only once the new one is complete.
+int build_layout(lodgs_scene *sc, const float *node_rec_p, const int32_t *left_p, const int32_t *right_p,
+                 const int32_t *parent_p, int64_t M, int32_t root, const lodgs_build_params &p, cudaStream_t st) {
+    const int stride = sc->stride;
+    struct { const float *p; } node_rec{node_rec_p};
+    struct { const int32_t *p; } left{left_p}, right{right_p}, parent{parent_p};
+    DevBuf<float> lo_node, hi_node, lo_row, hi_row, rows;
+    DevBuf<int32_t> node_spt_root, node_upper_row, node_of_row;
+    DevBuf<uint32_t> k0, k1, v0, v1, hist, dn, hi_g;
+    CK(k0.alloc(M)); CK(k1.alloc(M)); CK(v0.alloc(M)); CK(v1.alloc(M)); CK(hi_g.alloc(M));
+    CK(hist.alloc(SORT_HIST)); CK(dn.alloc(1));
+    bool alt;
+    int rc;
+    uint32_t *ord, *kk, *kalt, *valt;
+    // ---- HSPT BFS (level synchronous) ----
+    DevBuf<int32_t> up_node, up_kind, up_parent, up_ref, fr_a, fr_b, frp_a, frp_b;
+    DevBuf<uint32_t> flag, pos, bsum, total;
+    CK(up_node.alloc(M)); CK(up_kind.alloc(M)); CK(up_parent.alloc(M)); CK(up_ref.alloc(M));
+    CK(fr_a.alloc(M)); CK(fr_b.alloc(M)); CK(frp_a.alloc(M)); CK(frp_b.alloc(M));
+    CK(flag.alloc(M)); CK(pos.alloc(M)); CK(bsum.alloc(SCAN_GRID)); CK(total.alloc(1));
+    int32_t minus1 = -1;
+    CK(cudaMemcpy(fr_a.p, &root, 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(frp_a.p, &minus1, 4, cudaMemcpyHostToDevice));
+    int64_t F = 1, U = 0;
+    int depth = 0;
+    while (F > 0) {
+        CK(cudaMemcpyAsync(up_node.p + U, fr_a.p, F * 4, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(up_parent.p + U, frp_a.p, F * 4, cudaMemcpyDeviceToDevice, st));
+        k_hspt_classify<<<nblk(F), BT, 0, st>>>(node_rec.p, stride, left.p, fr_a.p, F, p.spt_volume,
+                                                up_kind.p + U, flag.p);
+        count_launches(1);
+        uint32_t F32 = (uint32_t)F;
+        CK(cudaMemcpyAsync(dn.p, &F32, 4, cudaMemcpyHostToDevice, st));
+        rc = scan_exclusive(flag.p, pos.p, dn.p, F32, bsum.p, total.p, st);
+        if (rc) return rc;
+        uint32_t n_int = 0;
+        CK(cudaMemcpyAsync(&n_int, total.p, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        k_hspt_expand<<<nblk(F), BT, 0, st>>>(fr_a.p, F, U, up_kind.p + U, pos.p, left.p, right.p, fr_b.p, frp_b.p);
+        count_launches(1);
+        U += F;
+        F = 2 * (int64_t)n_int;
+        std::swap(fr_a.p, fr_b.p);
+        std::swap(frp_a.p, frp_b.p);
+        ++depth;
+    }
+    CK(cudaGetLastError());
+    // SPT indices and upper rows in BFS order
+    DevBuf<uint32_t> spt_idx, row_idx;
+    CK(spt_idx.alloc(U)); CK(row_idx.alloc(U));
+    uint32_t U32 = (uint32_t)U, n_spt = 0, n_rows_up = 0;
+    CK(cudaMemcpy(dn.p, &U32, 4, cudaMemcpyHostToDevice));
+    k_flag_eq<<<nblk(U), BT, 0, st>>>(up_kind.p, U, KIND_SPT, 0, flag.p);
+    count_launches(1);
+    rc = scan_exclusive(flag.p, spt_idx.p, dn.p, U32, bsum.p, total.p, st);
+    if (rc) return rc;
+    CK(cudaMemcpy(&n_spt, total.p, 4, cudaMemcpyDeviceToHost));
+    k_flag_eq<<<nblk(U), BT, 0, st>>>(up_kind.p, U, KIND_SPT, 1, flag.p);
+    count_launches(1);
+    rc = scan_exclusive(flag.p, row_idx.p, dn.p, U32, bsum.p, total.p, st);
+    if (rc) return rc;
+    CK(cudaMemcpy(&n_rows_up, total.p, 4, cudaMemcpyDeviceToHost));
+    DevBuf<int32_t> spt_root;
+    CK(spt_root.alloc(n_spt));
+    CK(node_spt_root.alloc(M)); CK(node_upper_row.alloc(M));
+    CK(cudaMemset(node_spt_root.p, 0xff, M * 4)); CK(cudaMemset(node_upper_row.p, 0xff, M * 4));
+    k_mark_upper<<<nblk(U), BT, 0, st>>>(up_node.p, up_kind.p, U, spt_idx.p, row_idx.p, node_spt_root.p,
+                                         node_upper_row.p, spt_root.p, up_ref.p);
+    count_launches(1);
+
+    // ---- SPT intervals and layout ----
+    CK(lo_node.alloc(M)); CK(hi_node.alloc(M));
+    k_spt_intervals<<<nblk(M), BT, 0, st>>>(node_rec.p, stride, M, parent.p, left.p, node_spt_root.p,
+                                            node_upper_row.p, n_spt, p.kappa, lo_node.p, hi_node.p, k0.p, hi_g.p, v0.p);
+    count_launches(1);
+    uint32_t M32 = (uint32_t)M;
+    CK(cudaMemcpy(dn.p, &M32, 4, cudaMemcpyHostToDevice));
+    rc = radix_sort_pairs(k0.p, v0.p, k1.p, v1.p, dn.p, M32, 0, 32, hist.p, st, &alt);     // hi descending
+    if (rc) return rc;
+    ord = alt ? v1.p : v0.p;
+    kk = alt ? k0.p : k1.p; kalt = alt ? k1.p : k0.p; valt = alt ? v0.p : v1.p;
+    k_gather_u32<<<nblk(M), BT, 0, st>>>(hi_g.p, ord, M, kk);
+    count_launches(1);
+    int jbits = 1;
+    while ((1ull << jbits) <= (uint64_t)n_spt) ++jbits;
+    rc = radix_sort_pairs(kk, ord, kalt, valt, dn.p, M32, 0, jbits, hist.p, st, &alt);      // SPT index
+    if (rc) return rc;
+    uint32_t *sorted_node = alt ? valt : ord, *sorted_j = alt ? kalt : kk;
+    CK(node_of_row.alloc(M)); CK(lo_row.alloc(M)); CK(hi_row.alloc(M));
+    DevBuf<uint32_t> spt_base;
+    CK(spt_base.alloc(n_spt + 1));
+    {
+        uint32_t M32b = (uint32_t)M;
+        CK(cudaMemcpy(spt_base.p + n_spt, &M32b, 4, cudaMemcpyHostToDevice));
+    }
+    k_spt_rows<<<nblk(M), BT, 0, st>>>(sorted_node, sorted_j, M, n_spt, n_rows_up, node_of_row.p, spt_base.p,
+                                       lo_node.p, hi_node.p, lo_row.p, hi_row.p);
+    count_launches(1);
+    k_upper_rows<<<nblk(U), BT, 0, st>>>(up_node.p, up_kind.p, up_ref.p, U, node_of_row.p, lo_row.p, hi_row.p);
+    count_launches(1);
+    CK(rows.alloc((size_t)M * stride));
+    k_permute_rows<<<nblk(M * (stride / 4)), BT, 0, st>>>(node_rec.p, node_of_row.p, M, stride, rows.p);
+    count_launches(1);
+    DevBuf<UpperEntry> upper;
+    CK(upper.alloc(U));
+    k_upper_entries<<<nblk(U), BT, 0, st>>>(node_rec.p, stride, up_node.p, up_kind.p, up_parent.p, up_ref.p, U,
+                                            upper.p);
+    count_launches(1);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+
+    DevBuf<int32_t> left_keep, right_keep;
+    CK(left_keep.alloc(M)); CK(right_keep.alloc(M));
+    CK(cudaMemcpy(left_keep.p, left.p, M * 4, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(right_keep.p, right.p, M * 4, cudaMemcpyDeviceToDevice));
+    free_scene(sc);                                  // the previous layout, if any
+    sc->n_nodes = M;
+    sc->n_leaves = (M + 1) / 2;
+    sc->n_upper = U;
+    sc->upper_depth = depth;
+    sc->n_spt = n_spt;
+    sc->n_upper_rows = n_rows_up;
+    sc->spt_volume = p.spt_volume;
+    sc->kappa = p.kappa;
+    sc->d_rows = rows.release();
+    sc->d_upper = upper.release();
+    sc->d_spt_base = spt_base.release();
+    sc->d_lo = lo_row.release();
+    sc->d_hi = hi_row.release();
+    sc->d_node_rec = nullptr;                        // the canonical copy is not kept: export rebuilds it
+    sc->d_left = left_keep.release();
+    sc->d_right = right_keep.release();
+    sc->d_node_of_row = node_of_row.release();
+    sc->d_up_node = up_node.release();
+    sc->d_spt_root = spt_root.release();
+    sc->root = root;
+    return LODGS_OK;
+}
 
 int build_scene(const float *leaves, int64_t n, int degree, int on_device, const lodgs_build_params &p,
                 lodgs_scene *sc) {
@@ -501,119 +688,107 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
 
-    // ---- HSPT BFS (level synchronous) ----
-    DevBuf<int32_t> up_node, up_kind, up_parent, up_ref, fr_a, fr_b, frp_a, frp_b;
-    DevBuf<uint32_t> flag, pos, bsum, total;
-    CK(up_node.alloc(M)); CK(up_kind.alloc(M)); CK(up_parent.alloc(M)); CK(up_ref.alloc(M));
-    CK(fr_a.alloc(M)); CK(fr_b.alloc(M)); CK(frp_a.alloc(M)); CK(frp_b.alloc(M));
-    CK(flag.alloc(M)); CK(pos.alloc(M)); CK(bsum.alloc(SCAN_GRID)); CK(total.alloc(1));
-    int32_t root = (int32_t)(M - 1), minus1 = -1;
-    CK(cudaMemcpy(fr_a.p, &root, 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(frp_a.p, &minus1, 4, cudaMemcpyHostToDevice));
-    int64_t F = 1, U = 0;
-    int depth = 0;
-    while (F > 0) {
-        CK(cudaMemcpyAsync(up_node.p + U, fr_a.p, F * 4, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(up_parent.p + U, frp_a.p, F * 4, cudaMemcpyDeviceToDevice, st));
-        k_hspt_classify<<<nblk(F), BT, 0, st>>>(node_rec.p, stride, left.p, fr_a.p, F, p.spt_volume,
-                                                up_kind.p + U, flag.p);
+    return build_layout(sc, node_rec.p, left.p, right.p, parent.p, M, (int32_t)(M - 1), p, st);
+}
+
+int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, int32_t *old_row_of_new_row,
+                  int64_t capacity) {
+    if (!sc->d_rows) {
+        set_error("scene_densify: the scene's records are not on the device (released to a cache)");
+        return LODGS_E_STATE;
+    }
+    const int stride = sc->stride;
+    const int64_t M0 = sc->n_nodes;
+    int64_t n_spawn = 0;
+    for (int64_t i = 0; i < n_ops; ++i) {
+        if (ops[i].kind == LODGS_DENSIFY_SPAWN) ++n_spawn;
+        else if (ops[i].kind != LODGS_DENSIFY_RESPAWN) { set_error("scene_densify: unknown operation"); return LODGS_E_INVALID; }
+        if (ops[i].target < 0 || ops[i].target >= M0 ||
+            (ops[i].kind == LODGS_DENSIFY_RESPAWN && (ops[i].dead < 0 || ops[i].dead >= M0))) {
+            set_error("scene_densify: row out of range");
+            return LODGS_E_INVALID;
+        }
+    }
+    const int64_t M = M0 + 2 * n_spawn;
+    if (M >= (int64_t)1 << 31) { set_error("scene_densify: more than 2^31 nodes"); return LODGS_E_INVALID; }
+    if (capacity < M) { set_error("scene_densify: old_row_of_new_row holds fewer than the new node count"); return LODGS_E_INVALID; }
+    // host topology
+    std::vector<int32_t> left(M, -1), right(M, -1), parent(M, -1), node_of_row(M0), row_of_node(M0);
+    CK(cudaMemcpy(left.data(), sc->d_left, M0 * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(right.data(), sc->d_right, M0 * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(node_of_row.data(), sc->d_node_of_row, M0 * 4, cudaMemcpyDeviceToHost));
+    for (int64_t r = 0; r < M0; ++r) row_of_node[node_of_row[r]] = (int32_t)r;
+    for (int64_t u = 0; u < M0; ++u) {
+        if (left[u] >= 0) parent[left[u]] = (int32_t)u;
+        if (right[u] >= 0) parent[right[u]] = (int32_t)u;
+    }
+    int32_t root = sc->root;
+    std::vector<uint8_t> fresh(M, 0);                // nodes whose record is new
+    std::vector<int32_t> trip;                       // (target, child a, child b) per operation
+    trip.reserve(3 * n_ops);
+    int32_t next = (int32_t)M0;
+    for (int64_t i = 0; i < n_ops; ++i) {
+        const int32_t T = node_of_row[ops[i].target];
+        if (left[T] >= 0 || fresh[T]) {
+            set_error("scene_densify: operation " + std::to_string(i) + ": the target is not an original leaf");
+            return LODGS_E_INVALID;
+        }
+        int32_t a, b;
+        if (ops[i].kind == LODGS_DENSIFY_SPAWN) {
+            a = next++;
+            b = next++;
+        } else {
+            const int32_t D = node_of_row[ops[i].dead], P = parent[D];
+            if (left[D] >= 0 || fresh[D] || D == T || P < 0) {
+                set_error("scene_densify: operation " + std::to_string(i) +
+                          ": the dead node must be an original leaf with a parent, other than the target");
+                return LODGS_E_INVALID;
+            }
+            const int32_t S = left[P] == D ? right[P] : left[P], G = parent[P];
+            if (G >= 0) {                            // the sibling takes the parent's place
+                if (left[G] == P) left[G] = S; else right[G] = S;
+            } else {
+                root = S;
+            }
+            parent[S] = G;
+            a = P;
+            b = D;
+        }
+        left[T] = a; right[T] = b;
+        parent[a] = parent[b] = T;
+        left[a] = right[a] = left[b] = right[b] = -1;
+        fresh[a] = fresh[b] = 1;
+        trip.push_back(T); trip.push_back(a); trip.push_back(b);
+    }
+    // the records: canonical order on the device, children written by one kernel
+    // (targets are original leaves, never rewritten within a batch, so the
+    // operations' splits are independent)
+    DevBuf<float> node_rec;
+    DevBuf<int32_t> d_trip;
+    CK(node_rec.alloc((size_t)M * stride));
+    CK(d_trip.alloc(trip.size()));
+    CK(cudaMemcpy(d_trip.p, trip.data(), trip.size() * 4, cudaMemcpyHostToDevice));
+    k_unpermute_rows<<<nblk(M0 * (stride / 4)), BT>>>(sc->d_rows, sc->d_node_of_row, M0, stride, node_rec.p);
+    count_launches(1);
+    if (n_ops > 0) {
+        k_split_children<<<nblk(n_ops * stride), BT>>>(node_rec.p, stride, d_trip.p, n_ops);
         count_launches(1);
-        uint32_t F32 = (uint32_t)F;
-        CK(cudaMemcpyAsync(dn.p, &F32, 4, cudaMemcpyHostToDevice, st));
-        rc = scan_exclusive(flag.p, pos.p, dn.p, F32, bsum.p, total.p, st);
-        if (rc) return rc;
-        uint32_t n_int = 0;
-        CK(cudaMemcpyAsync(&n_int, total.p, 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        k_hspt_expand<<<nblk(F), BT, 0, st>>>(fr_a.p, F, U, up_kind.p + U, pos.p, left.p, right.p, fr_b.p, frp_b.p);
-        count_launches(1);
-        U += F;
-        F = 2 * (int64_t)n_int;
-        std::swap(fr_a.p, fr_b.p);
-        std::swap(frp_a.p, frp_b.p);
-        ++depth;
     }
     CK(cudaGetLastError());
-    sc->n_upper = U;
-    sc->upper_depth = depth;
-    // SPT indices and upper rows in BFS order
-    DevBuf<uint32_t> spt_idx, row_idx;
-    CK(spt_idx.alloc(U)); CK(row_idx.alloc(U));
-    uint32_t U32 = (uint32_t)U, n_spt = 0, n_rows_up = 0;
-    CK(cudaMemcpy(dn.p, &U32, 4, cudaMemcpyHostToDevice));
-    k_flag_eq<<<nblk(U), BT, 0, st>>>(up_kind.p, U, KIND_SPT, 0, flag.p);
-    count_launches(1);
-    rc = scan_exclusive(flag.p, spt_idx.p, dn.p, U32, bsum.p, total.p, st);
-    if (rc) return rc;
-    CK(cudaMemcpy(&n_spt, total.p, 4, cudaMemcpyDeviceToHost));
-    k_flag_eq<<<nblk(U), BT, 0, st>>>(up_kind.p, U, KIND_SPT, 1, flag.p);
-    count_launches(1);
-    rc = scan_exclusive(flag.p, row_idx.p, dn.p, U32, bsum.p, total.p, st);
-    if (rc) return rc;
-    CK(cudaMemcpy(&n_rows_up, total.p, 4, cudaMemcpyDeviceToHost));
-    sc->n_spt = n_spt;
-    sc->n_upper_rows = n_rows_up;
-    DevBuf<int32_t> spt_root;
-    CK(spt_root.alloc(n_spt));
-    CK(node_spt_root.alloc(M)); CK(node_upper_row.alloc(M));
-    CK(cudaMemset(node_spt_root.p, 0xff, M * 4)); CK(cudaMemset(node_upper_row.p, 0xff, M * 4));
-    k_mark_upper<<<nblk(U), BT, 0, st>>>(up_node.p, up_kind.p, U, spt_idx.p, row_idx.p, node_spt_root.p,
-                                         node_upper_row.p, spt_root.p, up_ref.p);
-    count_launches(1);
-
-    // ---- SPT intervals and layout ----
-    CK(lo_node.alloc(M)); CK(hi_node.alloc(M));
-    k_spt_intervals<<<nblk(M), BT, 0, st>>>(node_rec.p, stride, M, parent.p, left.p, node_spt_root.p,
-                                            node_upper_row.p, n_spt, p.kappa, lo_node.p, hi_node.p, k0.p, hi_g.p, v0.p);
-    count_launches(1);
-    uint32_t M32 = (uint32_t)M;
-    CK(cudaMemcpy(dn.p, &M32, 4, cudaMemcpyHostToDevice));
-    rc = radix_sort_pairs(k0.p, v0.p, k1.p, v1.p, dn.p, M32, 0, 32, hist.p, st, &alt);     // hi descending
-    if (rc) return rc;
-    ord = alt ? v1.p : v0.p;
-    kk = alt ? k0.p : k1.p; kalt = alt ? k1.p : k0.p; valt = alt ? v0.p : v1.p;
-    k_gather_u32<<<nblk(M), BT, 0, st>>>(hi_g.p, ord, M, kk);
-    count_launches(1);
-    int jbits = 1;
-    while ((1ull << jbits) <= (uint64_t)n_spt) ++jbits;
-    rc = radix_sort_pairs(kk, ord, kalt, valt, dn.p, M32, 0, jbits, hist.p, st, &alt);      // SPT index
-    if (rc) return rc;
-    uint32_t *sorted_node = alt ? valt : ord, *sorted_j = alt ? kalt : kk;
-    CK(node_of_row.alloc(M)); CK(lo_row.alloc(M)); CK(hi_row.alloc(M));
-    DevBuf<uint32_t> spt_base;
-    CK(spt_base.alloc(n_spt + 1));
-    {
-        uint32_t M32b = (uint32_t)M;
-        CK(cudaMemcpy(spt_base.p + n_spt, &M32b, 4, cudaMemcpyHostToDevice));
+    DevBuf<int32_t> d_left, d_right, d_parent;
+    CK(d_left.alloc(M)); CK(d_right.alloc(M)); CK(d_parent.alloc(M));
+    CK(cudaMemcpy(d_left.p, left.data(), M * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_right.p, right.data(), M * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_parent.p, parent.data(), M * 4, cudaMemcpyHostToDevice));
+    lodgs_build_params p{sc->spt_volume, sc->kappa};
+    if (int rc = build_layout(sc, node_rec.p, d_left.p, d_right.p, d_parent.p, M, root, p, 0)) return rc;
+    sc->layout_version++;
+    std::vector<int32_t> nor(M);
+    CK(cudaMemcpy(nor.data(), sc->d_node_of_row, M * 4, cudaMemcpyDeviceToHost));
+    for (int64_t r = 0; r < M; ++r) {
+        const int32_t u = nor[r];
+        old_row_of_new_row[r] = (u < M0 && !fresh[u]) ? row_of_node[u] : -1;
     }
-    k_spt_rows<<<nblk(M), BT, 0, st>>>(sorted_node, sorted_j, M, n_spt, n_rows_up, node_of_row.p, spt_base.p,
-                                       lo_node.p, hi_node.p, lo_row.p, hi_row.p);
-    count_launches(1);
-    k_upper_rows<<<nblk(U), BT, 0, st>>>(up_node.p, up_kind.p, up_ref.p, U, node_of_row.p, lo_row.p, hi_row.p);
-    count_launches(1);
-    CK(rows.alloc((size_t)M * stride));
-    k_permute_rows<<<nblk(M * (stride / 4)), BT, 0, st>>>(node_rec.p, node_of_row.p, M, stride, rows.p);
-    count_launches(1);
-    DevBuf<UpperEntry> upper;
-    CK(upper.alloc(U));
-    k_upper_entries<<<nblk(U), BT, 0, st>>>(node_rec.p, stride, up_node.p, up_kind.p, up_parent.p, up_ref.p, U,
-                                            upper.p);
-    count_launches(1);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(st));
-
-    sc->d_rows = rows.release();
-    sc->d_upper = upper.release();
-    sc->d_spt_base = spt_base.release();
-    sc->d_lo = lo_row.release();
-    sc->d_hi = hi_row.release();
-    // the canonical-order copy is not kept: export rebuilds it from the rows
-    sc->d_left = left.release();
-    sc->d_right = right.release();
-    sc->d_node_of_row = node_of_row.release();
-    sc->d_up_node = up_node.release();
-    sc->d_spt_root = spt_root.release();
-    // keep the upper hierarchy's kind/parent/ref for export inside d_upper
     return LODGS_OK;
 }
 
