@@ -141,10 +141,11 @@ int lodgs_scene_export(const lodgs_scene *scene, float *node_rec, int64_t *left,
  *                          sibling of `dead` takes P's place under P's parent
  *                          (or becomes the root), and P and `dead` become the
  *                          two children of leaf `target`; n_nodes is unchanged.
- * In both, the two children carry the split of the target's record: its mean,
- * rotation and colour; opacity o' = 1 - sqrt(1 - o); scales times
- * sqrt(o / (2 o' - o'^2 / 2)) (float32, as written); the target keeps its own
- * record and becomes their parent.  `target` and `dead` are render rows of the
+ * In both, the two children carry the split of the target's record (the
+ * 3DGS-MCMC split with two copies): its mean, rotation and colour; opacity
+ * o' = 1 - sqrt(1 - o); scales times o / (2 o' - o'^2 / sqrt 2) (float32 as
+ * written, sqrt 2 rounded to float32); the target keeps its own record and
+ * becomes their parent.  `target` and `dead` are render rows of the
  * layout before the call and must be leaves of it; a node made by an earlier
  * operation of the same batch cannot be a target or dead, and `dead` != `target`.
  * ops[i].dead is ignored for SPAWN.

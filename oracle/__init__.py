@@ -172,20 +172,23 @@ REC_S, REC_OP = 3, 10
 
 
 def split_record(rec: np.ndarray) -> np.ndarray:
-    """The record each of the two children of a split leaf carries: the same
-    mean, rotation and colour; opacity o' with 1 - (1 - o')^2 = o (the centre's
-    composited opacity is kept) and scales times f, f^2 = o / (2 o' - o'^2 / 2)
-    (the opacity integrated over the image plane is kept).  Records are float32
-    and both sides evaluate these five operations in float32, in this order,
-    because the HSPT volume test and the SPT bounds are float32 decisions on
-    the result."""
+    """The record each of the two children of a split leaf carries (Sec. 3
+    "Densification", the split of 3DGS-MCMC with N = 2 copies): the same mean,
+    rotation and colour; opacity o' = 1 - (1 - o)^(1/2), so the centre's
+    composited opacity is kept; scales times o / (2 o' - o'^2 / sqrt 2), the
+    MCMC factor for N = 2 (sum over the copies i and the terms k of
+    C(i-1, k) (-1)^k o'^(k+1) / sqrt(k+1)).  Records are float32 and both sides
+    evaluate these operations in float32, in this order (sqrt 2 as the float32
+    constant), because the HSPT volume test and the SPT bounds are float32
+    decisions on the result."""
     f32 = np.float32
     out = np.array(rec, dtype=np.float32, copy=True)
     sg = f32(rec[REC_OP])
     if not sg > 0:
         return out
     sp = f32(1) - np.sqrt(f32(1) - sg)
-    f = np.sqrt(sg / (f32(2) * sp - (sp * sp) / f32(2)))
+    den = f32(2) * sp - (sp * sp) / f32(np.sqrt(2.0))
+    f = sg / den
     out[REC_OP] = sp
     out[REC_S:REC_S + 3] = (np.asarray(rec[REC_S:REC_S + 3], np.float32) * f).astype(np.float32)
     return out

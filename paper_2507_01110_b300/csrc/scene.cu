@@ -384,14 +384,19 @@ __global__ void k_upper_rows(const int32_t *__restrict__ up_node, const int32_t 
     hi_row[up_ref[u]] = NAN;
 }
 
-// The two children of a densified leaf (Sec. 3 "Densification", after the
-// split of 3DGS-MCMC): both keep the target's mean, rotation and colour.  Their
-// opacity o' satisfies 1 - (1 - o')^2 = o, so the composited opacity at the
-// centre is unchanged; their scales are the target's times f with
-// f^2 = o / (2 o' - o'^2 / 2), so that the opacity the pair integrates over
-// the image plane, (2 o' - o'^2 / 2) f^2 A, equals the target's o A (A the
-// target's footprint area).  float32 with IEEE sqrt and division, evaluated as
-// written.  trip[3i..3i+2] = (target, child a, child b), canonical ids.
+// The two children of a densified leaf (Sec. 3 "Densification": the split of
+// 3DGS-MCMC, whose implementation the paper reuses, with N = 2): both keep the
+// target's mean, rotation and colour.  Their opacity o' = 1 - sqrt(1 - o)
+// keeps the composited opacity at the centre, 1 - (1 - o')^2 = o; their scales
+// are the target's times f = o / (2 o' - o'^2 / sqrt 2), the factor with which
+// the pair, composited front to back, integrates along any line through the
+// centre to the target's o * integral(g) (the second child adds
+// o' g (1 - o' g), and the square of a unit-peak Gaussian integrates in one
+// dimension to 1/sqrt 2 of the Gaussian).  float32 with IEEE sqrt and
+// division, evaluated as written.  trip[3i..3i+2] = (target, child a, child b),
+// canonical ids.
+constexpr float SQRT2_F = 1.41421356f;   // sqrt(2) rounded to float32
+
 __global__ void k_split_children(float *__restrict__ node_rec, int stride, const int32_t *__restrict__ trip,
                                  int64_t n_ops) {
     int64_t t = blockIdx.x * (int64_t)BT + threadIdx.x;
@@ -407,7 +412,7 @@ __global__ void k_split_children(float *__restrict__ node_rec, int stride, const
         if (c == REC_OP) {
             v = sp;
         } else {
-            const float f = sqrtf(sg / (2.0f * sp - (sp * sp) / 2.0f));
+            const float f = sg / (2.0f * sp - (sp * sp) / SQRT2_F);
             v = v * f;
         }
     }
