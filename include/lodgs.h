@@ -228,6 +228,8 @@ typedef struct {
     int64_t capacity_bytes;  /* device slab for SPT records (the upper rows are extra) */
     float d_min, d_max;      /* reuse window of Eq. 7 on x_now / x_cached, x = tau d / f; [1,1] = exact */
     int32_t release_scene_rows; /* free the scene's device copy of the records after copying them to host */
+    int32_t train;           /* keep Adam state (m, v, step counts) beside the records: pinned host arrays
+                                and device slabs mirroring the record slab (3x the slab plus 4 B a record) */
 } lodgs_cache_params;
 
 typedef struct {
@@ -237,6 +239,7 @@ typedef struct {
     int64_t bytes_streamed;  /* host-to-device bytes issued for this view */
     int64_t evictions;       /* cached SPTs evicted (least recently used) for this view */
     int64_t cached_spts, cached_records;  /* cache contents after this view */
+    int64_t bytes_written_back;  /* device-to-host bytes of evicted trained prefixes (training caches) */
 } lodgs_stream_stats;
 
 /* Create the cache: copies the scene's records to pinned host memory (the
@@ -245,8 +248,36 @@ typedef struct {
 int lodgs_cache_create(lodgs_scene *scene, const lodgs_cache_params *params, lodgs_cache **out);
 void lodgs_cache_free(lodgs_cache *cache);
 /* Drop every cached SPT (Sec. 4.4: the paper flushes the whole cache
- * periodically during training).  Host-side only; no data moves. */
+ * periodically during training).  A training cache first writes its trained
+ * rows and Adam state back to host memory (synchronous, after a device
+ * synchronisation); otherwise host-side only. */
 int lodgs_cache_flush(lodgs_cache *cache);
+
+/*
+ * Out-of-core training (Algorithm 3: optimise the cached nodes, write them back
+ * when the LRU evicts them; Adam state in host memory beside the records).
+ * lodgs_cache_adam_step: sparse Adam (lodgs_adam_step's update, hyper-parameters
+ * and per-column lr[stride]) over the frame's selected rows in the cache's
+ * device slabs.  `frame` must hold this cache's latest lodgs_stream_nodes view,
+ * rendered with the cache's records and back-propagated (lodgs_render_backward,
+ * sparse gradient rows `grads` in selection order).  Marks the view's SPTs
+ * and the upper rows as trained.  Asynchronous on `stream`; the next
+ * lodgs_stream_nodes orders its write-backs after it.  LODGS_E_STATE for a
+ * cache created without `train`.
+ * A trained SPT prefix is copied back to host memory (records, m, v, step
+ * counts) when it is evicted, on the copy stream, ahead of any load into its
+ * range.
+ * lodgs_cache_writeback: copies every trained SPT prefix and the upper rows
+ * back to host memory on `stream` (the cache keeps them); the host arrays are
+ * current once `stream` has completed.
+ * lodgs_cache_host_state: the pinned host arrays in render-row order: records
+ * (n_nodes x stride), m, v (n_nodes x stride; NULL unless training), step
+ * counts (n_nodes; NULL unless training).  Library-owned.
+ */
+int lodgs_cache_adam_step(lodgs_cache *cache, lodgs_frame *frame, const float *grads, const float *lr, float b1,
+                          float b2, float eps, void *stream);
+int lodgs_cache_writeback(lodgs_cache *cache, void *stream);
+int lodgs_cache_host_state(lodgs_cache *cache, float **h_rows, float **h_m, float **h_v, uint32_t **h_t);
 /* Device records to pass as `rows` to lodgs_render / lodgs_render_backward for
  * frames selected with lodgs_stream_nodes (upper rows, then the slab). */
 int lodgs_cache_records(lodgs_cache *cache, float **d_records);

@@ -53,13 +53,13 @@ DENSIFY_SPAWN, DENSIFY_RESPAWN = 0, 1
 
 class CacheParams(C.Structure):
     _fields_ = [("capacity_bytes", C.c_int64), ("d_min", C.c_float), ("d_max", C.c_float),
-                ("release_scene_rows", C.c_int32)]
+                ("release_scene_rows", C.c_int32), ("train", C.c_int32)]
 
 
 class StreamStats(C.Structure):
     _fields_ = [("spt_hits", C.c_int64), ("spt_resident", C.c_int64), ("spt_loaded", C.c_int64),
                 ("bytes_streamed", C.c_int64), ("evictions", C.c_int64), ("cached_spts", C.c_int64),
-                ("cached_records", C.c_int64)]
+                ("cached_records", C.c_int64), ("bytes_written_back", C.c_int64)]
 
 
 class FrameStats(C.Structure):
@@ -91,6 +91,9 @@ _SIGS = {
     "lodgs_cache_free": (None, [_P]),
     "lodgs_cache_records": (C.c_int, [_P, C.POINTER(_P)]),
     "lodgs_cache_flush": (C.c_int, [_P]),
+    "lodgs_cache_adam_step": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_float, C.c_float, _P]),
+    "lodgs_cache_writeback": (C.c_int, [_P, _P]),
+    "lodgs_cache_host_state": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P)]),
     "lodgs_stream_nodes": (C.c_int, [_P, _P, C.POINTER(Camera), _P, _P, _P, C.POINTER(StreamStats)]),
     "lodgs_render": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, _P]),

@@ -236,9 +236,10 @@ class Cache:
     """Out-of-core node cache of a scene (records in pinned host memory)."""
 
     def __init__(self, scene: Scene, capacity_bytes: int, d_min: float = 0.9, d_max: float = 1.1,
-                 release_scene_rows: bool = False):
+                 release_scene_rows: bool = False, train: bool = False):
         self.scene = scene
-        p = _lib.CacheParams(int(capacity_bytes), float(d_min), float(d_max), int(release_scene_rows))
+        self.train = bool(train)
+        p = _lib.CacheParams(int(capacity_bytes), float(d_min), float(d_max), int(release_scene_rows), int(train))
         h = C.c_void_p()
         check(lib().lodgs_cache_create(scene.handle, C.byref(p), C.byref(h)))
         self._h = h
@@ -253,8 +254,35 @@ class Cache:
         return self._h
 
     def flush(self):
-        """Drop every cached SPT (the paper's periodic cache flush)."""
+        """Drop every cached SPT (the paper's periodic cache flush); a training
+        cache writes its trained rows and Adam state back first."""
         check(lib().lodgs_cache_flush(self._h))
+
+    def adam_step(self, frame: Frame, grads: torch.Tensor, lr, b1: float = 0.9, b2: float = 0.999,
+                  eps: float = 1e-15, stream=None) -> None:
+        """Sparse Adam on the cached rows of the frame's view (after
+        render_backward with rows=cache.records); lr: float or per-column."""
+        lrv = np.broadcast_to(np.asarray(lr, dtype=np.float32), (self.scene.stride,)).copy()
+        check(lib().lodgs_cache_adam_step(self._h, frame.handle, _ptr(grads), lrv.ctypes.data_as(C.c_void_p),
+                                          C.c_float(b1), C.c_float(b2), C.c_float(eps), _stream_ptr(stream)))
+
+    def writeback(self, stream=None) -> None:
+        """Copy every trained row (records and Adam state) back to host memory."""
+        check(lib().lodgs_cache_writeback(self._h, _stream_ptr(stream)))
+
+    def host_state(self) -> dict:
+        """numpy views of the pinned host arrays (render-row order): rows, and
+        for training caches m, v, t.  Current after writeback() and a sync."""
+        ptrs = [C.c_void_p() for _ in range(4)]
+        check(lib().lodgs_cache_host_state(self._h, *[C.byref(p) for p in ptrs]))
+        M, st = self.scene.n_nodes, self.scene.stride
+        out = {}
+        for name, p, shape, ct in (("rows", ptrs[0], (M, st), C.c_float), ("m", ptrs[1], (M, st), C.c_float),
+                                   ("v", ptrs[2], (M, st), C.c_float), ("t", ptrs[3], (M,), C.c_uint32)):
+            if p.value:
+                n = int(np.prod(shape))
+                out[name] = np.ctypeslib.as_array((ct * n).from_address(p.value)).reshape(shape)
+        return out
 
     def close(self):
         if self._h:

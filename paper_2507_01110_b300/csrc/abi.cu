@@ -311,6 +311,7 @@ int lodgs_select_lod(lodgs_scene *sc, const lodgs_camera *cam, lodgs_frame *fr, 
     cudaStream_t st = (cudaStream_t)stream;
     fr->stream = st;
     fr->f.use_src = false;
+    fr->cache = nullptr;                 // no longer a cache view
     for (bool &r : fr->ran) r = false;
     fr->mark(LODGS_STAGE_SELECT, 0, st);
     if (cam)

@@ -26,8 +26,10 @@ struct ColumnRates {
 
 // One thread per 16-byte quarter of a row: every access of a row (its step
 // count, the gradient, m, v and the parameters) is issued at once, so a row
-// costs one memory round trip; the quarter holding column 0 writes the new
-// step count.  Columns at or past `used` keep their bits.
+// costs one memory round trip.  Whole rows go to one warp (32 / quads rows per
+// warp, the remaining lanes idle): the quarter holding column 0 writes the new
+// step count only after every quarter of its row has read the old one, which
+// a __syncwarp orders.  Columns at or past `used` keep their bits.
 __global__ void __launch_bounds__(AB) k_adam(float4 *__restrict__ params, float4 *__restrict__ m,
                                              float4 *__restrict__ v, uint32_t *__restrict__ t,
                                              const uint32_t *__restrict__ rows, const float4 *__restrict__ grads,
@@ -35,15 +37,28 @@ __global__ void __launch_bounds__(AB) k_adam(float4 *__restrict__ params, float4
                                              ColumnRates rates, float b1, float b2, float eps) {
     const uint32_t n = d_n ? *d_n : n_host;
     const float omb1 = 1.0f - b1, omb2 = 1.0f - b2;
-    const uint64_t total = (uint64_t)n * quads;
-    for (uint64_t e = (uint64_t)blockIdx.x * AB + threadIdx.x; e < total; e += (uint64_t)gridDim.x * AB) {
-        const uint32_t i = (uint32_t)(e / quads);
-        const int q = (int)(e % quads);
-        const uint32_t r = rows[i];
-        const size_t at = (size_t)r * quads + q;
-        const uint32_t step = t[r] + 1;
-        const float4 g = grads[(size_t)i * quads + q];
-        float4 mm = m[at], vv = v[at], pp = params[at];
+    const int lane = threadIdx.x & 31;
+    const int rpw = 32 / quads;                              // rows per warp (quads <= 16)
+    const int slot = lane / quads, q = lane % quads;
+    const uint64_t n_warps = ((uint64_t)n + rpw - 1) / rpw;
+    const uint64_t grid_warps = (uint64_t)gridDim.x * (AB / 32);
+    for (uint64_t w = (uint64_t)blockIdx.x * (AB / 32) + (threadIdx.x >> 5); w < n_warps; w += grid_warps) {
+        const uint64_t i = w * rpw + slot;
+        const bool act = slot < rpw && i < n;
+        uint32_t r = 0, step = 0;
+        size_t at = 0;
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f), mm = g, vv = g, pp = g;
+        if (act) {
+            r = rows[i];
+            at = (size_t)r * quads + q;
+            step = t[r] + 1;
+            g = grads[(size_t)i * quads + q];
+            mm = m[at];
+            vv = v[at];
+            pp = params[at];
+        }
+        __syncwarp();                                        // every quarter has read t[r]
+        if (!act) continue;
         if (q == 0) t[r] = step;
         // 1 - b^t as -expm1(t log1p(-(1 - b))): 1 - b is exact in float32 and nothing cancels
         const float bc1 = -expm1f((float)step * log1pf(-omb1)), bc2 = -expm1f((float)step * log1pf(-omb2));
@@ -110,9 +125,10 @@ extern "C" int lodgs_gather_rows(const void *src, int64_t n_src, void *dst, cons
     return LODGS_OK;
 }
 
-extern "C" int lodgs_adam_step(lodgs_scene *sc, float *params, float *m, float *v, uint32_t *t, const uint32_t *rows,
-                               const float *grads, const uint32_t *d_n, int64_t max_n, const float *lr, float b1,
-                               float b2, float eps, void *stream) {
+namespace lodgs {
+int launch_adam(const lodgs_scene *sc, float *params, float *m, float *v, uint32_t *t, const uint32_t *rows,
+                const float *grads, const uint32_t *d_n, int64_t max_n, const float *lr, float b1, float b2,
+                float eps, cudaStream_t st) {
     if (!sc || !params || !m || !v || !t || !rows || !grads || !lr || max_n < 0) {
         set_error("adam_step: NULL argument or negative count");
         return LODGS_E_INVALID;
@@ -131,13 +147,21 @@ extern "C" int lodgs_adam_step(lodgs_scene *sc, float *params, float *m, float *
         return LODGS_E_INVALID;
     }
     const int quads = sc->stride / 4;
-    const int64_t blocks = std::min<int64_t>((max_n * quads + AB - 1) / AB, 148 * 64);
-    k_adam<<<(unsigned)std::max<int64_t>(blocks, 1), AB, 0, (cudaStream_t)stream>>>(
+    const int64_t rpw = 32 / quads, warps = (max_n + rpw - 1) / rpw;
+    const int64_t blocks = std::min<int64_t>((warps + AB / 32 - 1) / (AB / 32), 148 * 64);
+    k_adam<<<(unsigned)std::max<int64_t>(blocks, 1), AB, 0, st>>>(
         reinterpret_cast<float4 *>(params), reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), t, rows,
         reinterpret_cast<const float4 *>(grads), d_n, (uint32_t)max_n, quads, used, rates, b1, b2, eps);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
+}
+}  // namespace lodgs
+
+extern "C" int lodgs_adam_step(lodgs_scene *sc, float *params, float *m, float *v, uint32_t *t, const uint32_t *rows,
+                               const float *grads, const uint32_t *d_n, int64_t max_n, const float *lr, float b1,
+                               float b2, float eps, void *stream) {
+    return launch_adam(sc, params, m, v, t, rows, grads, d_n, max_n, lr, b1, b2, eps, (cudaStream_t)stream);
 }
 
 extern "C" int lodgs_frame_screen_grad_max(lodgs_frame *fr, float *max_per_node, void *stream) {

@@ -18,6 +18,16 @@
 //             least-recently-used SPTs not used by this view) and cut at x_j.
 // The reuse ratio is taken on x = tau d / f, i.e. on the focal-normalised
 // distance, so cameras with different focal lengths share cached cuts.
+//
+// Training (Algorithm 3: optimise the cached nodes, write them back to host
+// memory when the LRU evicts them, flush periodically; Adam state kept in host
+// memory beside the records): a training cache mirrors the record slab with
+// slabs of the Adam moments and step counts.  A load streams the prefix of all
+// four arrays; a sparse Adam step updates the view's cached rows in place and
+// marks the view's SPTs dirty; evicting a dirty SPT copies its prefix of the
+// four arrays back to host memory on the copy stream, ahead of any load that
+// reuses the range (same stream, in order).  Upper rows stay resident and are
+// written back by lodgs_cache_writeback and lodgs_cache_flush.
 #include <string.h>
 
 #include <list>
@@ -38,6 +48,7 @@ struct Entry {
     uint32_t h = 0;           // cached prefix length (records)
     uint64_t off = 0;         // slab offset (records)
     uint64_t used = 0;        // last view that used the entry
+    bool dirty = false;       // trained since it was loaded (training caches)
     std::list<uint32_t>::iterator lru;
 };
 
@@ -50,6 +61,11 @@ struct lodgs_cache {
     uint64_t slab_records = 0;
     float *h_rows = nullptr;          // pinned, n_nodes x stride
     float *d_records = nullptr;       // device: upper rows then the slab
+    // training: Adam moments and step counts, same layouts as h_rows / d_records
+    bool train = false, upper_dirty = false;
+    float *h_m = nullptr, *h_v = nullptr, *d_m = nullptr, *d_v = nullptr;
+    uint32_t *h_t = nullptr, *d_t = nullptr;
+    cudaEvent_t adam_done = nullptr;  // after the last Adam step (its stream is the caller's)
     std::vector<uint32_t> spt_base;   // host copy (n_spt + 1)
     std::vector<Entry> entry;
     std::list<uint32_t> lru;          // front = most recently used
@@ -88,13 +104,40 @@ bool range_alloc(lodgs_cache *c, uint64_t len, uint64_t *off) {
     return false;
 }
 
-void evict(lodgs_cache *c, uint32_t j) {
+// copies n records from slab/host slot `dev` to/from host row `host` for the
+// four arrays of a training cache (records only otherwise)
+cudaError_t copy_rows(lodgs_cache *c, uint64_t dev, uint64_t host, uint64_t n, bool to_host, cudaStream_t st) {
+    const size_t w = (size_t)c->scene->stride;
+    const cudaMemcpyKind k = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+    auto cp = [&](float *d, float *h) {
+        return to_host ? cudaMemcpyAsync(h + host * w, d + dev * w, n * w * 4, k, st)
+                       : cudaMemcpyAsync(d + dev * w, h + host * w, n * w * 4, k, st);
+    };
+    cudaError_t e = cp(c->d_records, c->h_rows);
+    if (e != cudaSuccess || !c->train) return e;
+    if ((e = cp(c->d_m, c->h_m)) != cudaSuccess) return e;
+    if ((e = cp(c->d_v, c->h_v)) != cudaSuccess) return e;
+    return to_host ? cudaMemcpyAsync(c->h_t + host, c->d_t + dev, n * 4, k, st)
+                   : cudaMemcpyAsync(c->d_t + dev, c->h_t + host, n * 4, k, st);
+}
+
+// drop SPT j from the cache; a dirty prefix is first copied back to host
+// memory on `st` (the copy stream), before any later copy into the range
+cudaError_t evict(lodgs_cache *c, uint32_t j, cudaStream_t st, int64_t *written) {
     Entry &e = c->entry[j];
+    if (e.dirty) {
+        const uint64_t U = (uint64_t)c->scene->n_upper_rows;
+        cudaError_t err = copy_rows(c, U + e.off, c->spt_base[j], e.h, true, st);
+        if (err != cudaSuccess) return err;
+        if (written) *written += (int64_t)e.h * c->scene->stride * 4 * (c->train ? 3 : 1) + (c->train ? e.h * 4 : 0);
+        e.dirty = false;
+    }
     range_free(c, e.off, e.h);
     c->lru.erase(e.lru);
     c->cached_records -= e.h;
     c->cached_spts -= 1;
     e.valid = false;
+    return cudaSuccess;
 }
 
 void touch(lodgs_cache *c, uint32_t j) {
@@ -151,6 +194,26 @@ int lodgs_cache_create(lodgs_scene *sc, const lodgs_cache_params *p, lodgs_cache
         (e = cudaMallocHost((void **)&c->h_src, n * 4)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->copies_done, cudaEventDisableTiming)) != cudaSuccess)
         return fail(cuda_fail(e, "cache_create: staging"));
+    if (p->train) {
+        const size_t slots = (size_t)(U + c->slab_records);
+        c->train = true;
+        if ((e = cudaMallocHost((void **)&c->h_m, (size_t)M * rec)) != cudaSuccess ||
+            (e = cudaMallocHost((void **)&c->h_v, (size_t)M * rec)) != cudaSuccess ||
+            (e = cudaMallocHost((void **)&c->h_t, (size_t)std::max<int64_t>(M, 1) * 4)) != cudaSuccess)
+            return fail(cuda_fail(e, "cache_create: pinned Adam state"));
+        memset(c->h_m, 0, (size_t)M * rec);
+        memset(c->h_v, 0, (size_t)M * rec);
+        memset(c->h_t, 0, (size_t)M * 4);
+        if ((e = cudaMalloc((void **)&c->d_m, slots * rec)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c->d_v, slots * rec)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c->d_t, std::max<size_t>(slots, 1) * 4)) != cudaSuccess)
+            return fail(cuda_fail(e, "cache_create: device Adam state"));
+        if ((e = cudaMemset(c->d_m, 0, (size_t)U * rec)) != cudaSuccess ||
+            (e = cudaMemset(c->d_v, 0, (size_t)U * rec)) != cudaSuccess ||
+            (e = cudaMemset(c->d_t, 0, (size_t)U * 4)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c->adam_done, cudaEventDisableTiming)) != cudaSuccess)
+            return fail(cuda_fail(e, "cache_create: upper Adam state"));
+    }
     if (p->release_scene_rows) {
         cudaFree(sc->d_rows);
         sc->d_rows = nullptr;
@@ -166,12 +229,77 @@ void lodgs_cache_free(lodgs_cache *c) {
     cudaFree(c->d_records);
     cudaFreeHost(c->h_cnt); cudaFreeHost(c->h_emit_j); cudaFreeHost(c->h_emit_x); cudaFreeHost(c->h_high);
     cudaFreeHost(c->h_x_used); cudaFreeHost(c->h_src);
+    cudaFreeHost(c->h_m); cudaFreeHost(c->h_v); cudaFreeHost(c->h_t);
+    cudaFree(c->d_m); cudaFree(c->d_v); cudaFree(c->d_t);
     if (c->copies_done) cudaEventDestroy(c->copies_done);
+    if (c->adam_done) cudaEventDestroy(c->adam_done);
     delete c;
+}
+
+namespace {
+// write every dirty SPT prefix and the upper rows back to host memory on `st`
+int writeback_all(lodgs_cache *c, cudaStream_t st) {
+    if (!c->train) return LODGS_OK;
+    LODGS_CUDA(cudaStreamWaitEvent(st, c->adam_done, 0));
+    const uint64_t U = (uint64_t)c->scene->n_upper_rows;
+    const uint64_t M = (uint64_t)c->scene->n_nodes;
+    for (uint32_t j = 0; j < (uint32_t)c->entry.size(); ++j) {
+        Entry &e = c->entry[j];
+        if (!e.valid || !e.dirty) continue;
+        LODGS_CUDA(copy_rows(c, U + e.off, c->spt_base[j], e.h, true, st));
+        e.dirty = false;
+    }
+    if (U && c->upper_dirty) {
+        LODGS_CUDA(copy_rows(c, 0, 0, U, true, st));
+        c->upper_dirty = false;
+    }
+    (void)M;
+    return LODGS_OK;
+}
+}  // namespace
+
+int lodgs_cache_writeback(lodgs_cache *c, void *stream) {
+    if (!c) { set_error("cache_writeback: NULL cache"); return LODGS_E_INVALID; }
+    return writeback_all(c, (cudaStream_t)stream);
+}
+
+int lodgs_cache_host_state(lodgs_cache *c, float **h_rows, float **h_m, float **h_v, uint32_t **h_t) {
+    if (!c) { set_error("cache_host_state: NULL cache"); return LODGS_E_INVALID; }
+    if (h_rows) *h_rows = c->h_rows;
+    if (h_m) *h_m = c->h_m;
+    if (h_v) *h_v = c->h_v;
+    if (h_t) *h_t = c->h_t;
+    return LODGS_OK;
+}
+
+int lodgs_cache_adam_step(lodgs_cache *c, lodgs_frame *fr, const float *grads, const float *lr, float b1, float b2,
+                          float eps, void *stream) {
+    if (!c || !fr || !grads || !lr) { set_error("cache_adam_step: NULL argument"); return LODGS_E_INVALID; }
+    if (!c->train) { set_error("cache_adam_step: the cache was not created for training"); return LODGS_E_STATE; }
+    if (int rc = check_frame(c->scene, fr, "cache_adam_step")) return rc;
+    if (fr->cache != c || fr->cache_view != c->view || !fr->blend_bwd_done) {
+        set_error("cache_adam_step: the frame must hold this cache's latest view, rendered and back-propagated");
+        return LODGS_E_STATE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const FrameBufs &f = fr->f;
+    if (int rc = launch_adam(c->scene, c->d_records, c->d_m, c->d_v, c->d_t, f.sel_src, grads, f.cnt + C_NSEL_EFF,
+                             (int64_t)f.cap_sel, lr, b1, b2, eps, st))
+        return rc;
+    LODGS_CUDA(cudaEventRecord(c->adam_done, st));
+    for (Entry &e : c->entry)
+        if (e.valid && e.used == c->view) e.dirty = true;
+    c->upper_dirty = true;
+    return LODGS_OK;
 }
 
 int lodgs_cache_flush(lodgs_cache *c) {
     if (!c) { set_error("cache_flush: NULL cache"); return LODGS_E_INVALID; }
+    if (c->train) {                                  // trained rows and state go home first
+        LODGS_CUDA(cudaDeviceSynchronize());
+        if (int rc = writeback_all(c, 0)) return rc;
+        LODGS_CUDA(cudaStreamSynchronize(0));
+    }
     for (Entry &e : c->entry) e.valid = false;
     c->lru.clear();
     c->free_ranges.clear();
@@ -222,7 +350,8 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
     LODGS_CUDA(cudaMemcpyAsync(c->h_high, f.high, n * 4, cudaMemcpyDeviceToHost, st));
     // this also waits for earlier renders on `st`, which may read slab ranges evicted below
     LODGS_CUDA(cudaStreamSynchronize(st));
-    // 2. cache decisions (host)
+    // 2. cache decisions (host); write-backs read rows the last Adam step wrote
+    if (c->train) LODGS_CUDA(cudaStreamWaitEvent(cs, c->adam_done, 0));
     c->view += 1;
     lodgs_stream_stats s{};
     const uint32_t n_emit = c->h_cnt[C_NEMIT];
@@ -250,7 +379,7 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
                 s.spt_resident += 1;
                 continue;
             }
-            evict(c, j);
+            LODGS_CUDA(evict(c, j, cs, &s.bytes_written_back));
         }
         uint64_t off = 0;
         while (!range_alloc(c, need, &off)) {                 // evict least recently used, never this view's
@@ -258,7 +387,7 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
                 set_error("stream_nodes: the view's SPT records exceed the cache capacity");
                 return LODGS_E_CAPACITY;
             }
-            evict(c, c->lru.back());
+            LODGS_CUDA(evict(c, c->lru.back(), cs, &s.bytes_written_back));
             s.evictions += 1;
         }
         e.valid = true;
@@ -270,9 +399,8 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
         e.used = c->view;
         c->cached_records += need;
         c->cached_spts += 1;
-        const size_t bytes = (size_t)need * rec;
-        LODGS_CUDA(cudaMemcpyAsync(c->d_records + (U + off) * sc->stride, c->h_rows + (size_t)c->spt_base[j] * sc->stride,
-                                   bytes, cudaMemcpyHostToDevice, cs));
+        const size_t bytes = (size_t)need * (c->train ? 3 * rec + 4 : rec);
+        LODGS_CUDA(copy_rows(c, U + off, c->spt_base[j], need, false, cs));
         s.bytes_streamed += (int64_t)bytes;
         s.spt_loaded += 1;
         c->h_x_used[q] = x;
@@ -289,6 +417,8 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
     LODGS_CUDA(cudaStreamWaitEvent(st, c->copies_done, 0));   // the render reads the streamed records
     fr->mark(LODGS_STAGE_SELECT, 1, st);
     f.use_src = true;
+    fr->cache = c;
+    fr->cache_view = c->view;
     fr->selected = true;
     fr->rendered = false;
     s.cached_spts = (int64_t)c->cached_spts;

@@ -179,6 +179,10 @@ int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, i
 // 0 if `fr` belongs to `sc` and was created for its current layout, else an
 // error code (with the message set, prefixed by `who`)
 int check_frame(const lodgs_scene *sc, const lodgs_frame *fr, const char *who);
+// sparse Adam over `rows` of params/m/v/t (lodgs_adam_step's contract)
+int launch_adam(const lodgs_scene *sc, float *params, float *m, float *v, uint32_t *t, const uint32_t *rows,
+                const float *grads, const uint32_t *d_n, int64_t max_n, const float *lr, float b1, float b2,
+                float eps, cudaStream_t st);
 
 // radix sort and scans (sort.cu).  All take element counts from device memory so
 // that no host synchronisation is needed between stages.
@@ -226,6 +230,8 @@ int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs 
 struct lodgs_frame {
     lodgs_scene *scene = nullptr;
     uint32_t layout_version = 0;        // the scene layout the buffers were sized for
+    const void *cache = nullptr;        // the cache of the last lodgs_stream_nodes, and its view number
+    uint64_t cache_view = 0;
     lodgs::FrameBufs f;
     uint32_t *h_cnt = nullptr;          // pinned mirror of the device counters
     cudaStream_t stream = 0;
