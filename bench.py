@@ -651,6 +651,64 @@ def run_out_of_core(args) -> dict:
         c.close()
         del c
         torch.cuda.empty_cache()
+    # out-of-core training: kNN-scheduled views at 1080p through a 4 GiB training
+    # cache (records, Adam moments and step counts streamed together; trained
+    # prefixes written back on eviction), select + render + mean-L1 + backward +
+    # sparse Adam per iteration, then the write-back of everything still cached
+    pool = [synth.camera_look(c.pos, c.R[2], c.R[0], 1920, 1080, tau=1.0)
+            for c in synth.serving_cameras(512, seed=33)]
+
+    def train_ooc(iters=128) -> dict:
+        tc = api.Cache(scene, capacity_bytes=4 << 30, d_min=0.9, d_max=1.1, train=True)
+        sched_t = schedule.ViewScheduler(np.array([c.pos for c in pool]), k=10, seed=36)
+        order = [sched_t.next() for _ in range(iters + 8)]
+        img = torch.empty((1080, 1920, 3), device="cuda")
+        gen = torch.Generator(device="cuda").manual_seed(37)
+        target = torch.rand((1080, 1920, 3), device="cuda", generator=gen)
+        dL = torch.empty_like(img)
+        g = torch.empty((scene.n_nodes, scene.stride), device="cuda")   # any cut fits
+        lr = np.full(scene.stride, 1.6e-4, np.float32)
+        lr[10], lr[3:6] = 5e-2, 5e-3
+        ft = api.Frame(scene)
+
+        def it(v):
+            _, st = api.stream_nodes(scene, tc, pool[v], ft, copy_stream=copy_stream)
+            api.render(scene, ft, rows=tc.records, image=img, check_capacity=True)
+            api.l1_loss_grad(img, target, dL=dL)
+            api.render_backward(scene, ft, dL, rows=tc.records, grad=g)
+            tc.adam_step(ft, g, lr)
+            return st
+
+        for v in order[:8]:                       # grow the frame's workspace
+            it(v)
+        torch.cuda.synchronize()
+        tot = {"bytes_streamed": 0, "bytes_written_back": 0, "evictions": 0}
+        t0 = time.perf_counter()
+        for v in order[8:]:
+            st = it(v)
+            for k in tot:
+                tot[k] += st[k]
+        max_cut = max(ft.stats()["n_selected"], 0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        tc.writeback()
+        torch.cuda.synchronize()
+        wb = time.perf_counter() - t1
+        tc.close()
+        return {"iterations": iters, "iters_per_s": round(iters / dt, 1), "ms_per_iter": round(1e3 * dt / iters, 3),
+                "bytes_streamed_per_iter": int(tot["bytes_streamed"] / iters),
+                "bytes_written_back_per_iter": int(tot["bytes_written_back"] / iters),
+                "evictions": tot["evictions"], "final_writeback_ms": round(1e3 * wb, 1), "last_cut": max_cut,
+                "cache_gib": 4, "note": "records, m, v and step counts stream together (3x the record bytes + 4 B)"}
+
+    try:
+        training = train_ooc()
+    except Exception as e:  # noqa: BLE001  (pinned host memory for the Adam state may be short)
+        torch.cuda.synchronize()
+        training = {"error": f"{type(e).__name__}: {e}"[:200]}
+    torch.cuda.empty_cache()
+
     cache = api.Cache(scene, capacity_bytes=8 << 30, d_min=0.9, d_max=1.1, release_scene_rows=True)
     torch.cuda.empty_cache()
     main = flythrough(cache)
@@ -659,8 +717,6 @@ def run_out_of_core(args) -> dict:
                   "spt_hit_rate": main["spt_hit_rate"], "evictions": main["evictions"]})
 
     # training view order: uniform against the kNN scheduler (LoD cut and loads only)
-    pool = [synth.camera_look(c.pos, c.R[2], c.R[0], 1920, 1080, tau=1.0)
-            for c in synth.serving_cameras(512, seed=33)]
     iters = 256
 
     def loads(order) -> dict:
@@ -682,7 +738,7 @@ def run_out_of_core(args) -> dict:
     return {"workload": f"{args.ooc_leaves:,}-leaf SH3 city, records in pinned host memory, 8 GiB device "
                         f"cache, {len(cams)}-view flythrough 300 m -> 20 m at 1920x1080, forward only",
             **main, "host_record_gb": round(scene.n_nodes * scene.stride * 4 / 1e9, 2), "reuse_window": [0.9, 1.1],
-            "cache_size_sweep": sweep,
+            "cache_size_sweep": sweep, "training": training,
             "view_selection": {"pool_views": len(pool), "iterations": iters,
                                "note": "nodes loaded from host per training iteration; a cache-less run loads "
                                        "the whole cut (cut_nodes_per_iter)",

@@ -260,7 +260,8 @@ int lodgs_cache_flush(lodgs_cache *cache);
  * and per-column lr[stride]) over the frame's selected rows in the cache's
  * device slabs.  `frame` must hold this cache's latest lodgs_stream_nodes view,
  * rendered with the cache's records and back-propagated (lodgs_render_backward,
- * sparse gradient rows `grads` in selection order).  Marks the view's SPTs
+ * sparse gradient rows `grads` in selection order, grad_capacity rows
+ * allocated; no row at or past it is read).  Marks the view's SPTs
  * and the upper rows as trained.  Asynchronous on `stream`; the next
  * lodgs_stream_nodes orders its write-backs after it.  LODGS_E_STATE for a
  * cache created without `train`.
@@ -274,8 +275,8 @@ int lodgs_cache_flush(lodgs_cache *cache);
  * (n_nodes x stride), m, v (n_nodes x stride; NULL unless training), step
  * counts (n_nodes; NULL unless training).  Library-owned.
  */
-int lodgs_cache_adam_step(lodgs_cache *cache, lodgs_frame *frame, const float *grads, const float *lr, float b1,
-                          float b2, float eps, void *stream);
+int lodgs_cache_adam_step(lodgs_cache *cache, lodgs_frame *frame, const float *grads, int64_t grad_capacity,
+                          const float *lr, float b1, float b2, float eps, void *stream);
 int lodgs_cache_writeback(lodgs_cache *cache, void *stream);
 int lodgs_cache_host_state(lodgs_cache *cache, float **h_rows, float **h_m, float **h_v, uint32_t **h_t);
 /* Device records to pass as `rows` to lodgs_render / lodgs_render_backward for
@@ -326,11 +327,18 @@ int lodgs_render(lodgs_scene *scene, lodgs_frame *frame, const float *rows, cons
  *              for the i-th selected node (lodgs_frame_selection order);
  *              dense != 0: n_nodes x stride by render row, only selected rows
  *              are written (the caller zeroes the rest).
+ *   grad_capacity: rows allocated at grad_rows.  Dense needs n_nodes
+ *              (LODGS_E_INVALID otherwise).  Sparse rows are checked on the
+ *              device against the selection count: if they do not fit, nothing
+ *              is written, the frame records LODGS_E_CAPACITY
+ *              (lodgs_frame_get_stats) and its device row count
+ *              (lodgs_frame_device_count) becomes 0.
  * Gradients are w.r.t. the stored record values (quaternion normalisation
  * included).  Asynchronous.
  */
 int lodgs_render_backward(lodgs_scene *scene, lodgs_frame *frame, const float *rows, const float *bg,
-                          const float *image, const float *dL_dimage, float *grad_rows, int dense, void *stream);
+                          const float *image, const float *dL_dimage, float *grad_rows, int64_t grad_capacity,
+                          int dense, void *stream);
 
 /*
  * Gradient of a multi-view batch loss: sums the per-view sparse gradient rows
@@ -410,11 +418,11 @@ int lodgs_l1_loss_grad(const float *image, const float *target, int64_t n, float
 /* The two halves of lodgs_render_backward, for callers that schedule them
  * separately (e.g. as separate CUDA graphs): the blend backward (per-pixel
  * recomputation, 2D gradients kept in the frame), then the projection backward
- * into gradient rows (same meaning of rows, grad_rows, dense). */
+ * into gradient rows (same meaning of rows, grad_rows, grad_capacity, dense). */
 int lodgs_render_backward_blend(lodgs_scene *scene, lodgs_frame *frame, const float *image, const float *dL_dimage,
                                 void *stream);
 int lodgs_render_backward_project(lodgs_scene *scene, lodgs_frame *frame, const float *rows, float *grad_rows,
-                                  int dense, void *stream);
+                                  int64_t grad_capacity, int dense, void *stream);
 
 /* Counters of the last select/render on this frame (blocks until `stream`,
  * the stream the frame last ran on, is idle). */

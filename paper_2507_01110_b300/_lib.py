@@ -91,14 +91,14 @@ _SIGS = {
     "lodgs_cache_free": (None, [_P]),
     "lodgs_cache_records": (C.c_int, [_P, C.POINTER(_P)]),
     "lodgs_cache_flush": (C.c_int, [_P]),
-    "lodgs_cache_adam_step": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_float, C.c_float, _P]),
+    "lodgs_cache_adam_step": (C.c_int, [_P, _P, _P, C.c_int64, _P, C.c_float, C.c_float, C.c_float, _P]),
     "lodgs_cache_writeback": (C.c_int, [_P, _P]),
     "lodgs_cache_host_state": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P)]),
     "lodgs_stream_nodes": (C.c_int, [_P, _P, C.POINTER(Camera), _P, _P, _P, C.POINTER(StreamStats)]),
     "lodgs_render": (C.c_int, [_P, _P, _P, _P, _P, _P]),
-    "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int, _P]),
+    "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, C.c_int, _P]),
     "lodgs_render_backward_blend": (C.c_int, [_P, _P, _P, _P, _P]),
-    "lodgs_render_backward_project": (C.c_int, [_P, _P, _P, _P, C.c_int, _P]),
+    "lodgs_render_backward_project": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P]),
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
     "lodgs_frame_set_ordering": (C.c_int, [_P, C.c_int]),
     "lodgs_adam_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, C.c_float, C.c_float, C.c_float,

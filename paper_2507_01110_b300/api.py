@@ -263,7 +263,9 @@ class Cache:
         """Sparse Adam on the cached rows of the frame's view (after
         render_backward with rows=cache.records); lr: float or per-column."""
         lrv = np.broadcast_to(np.asarray(lr, dtype=np.float32), (self.scene.stride,)).copy()
-        check(lib().lodgs_cache_adam_step(self._h, frame.handle, _ptr(grads), lrv.ctypes.data_as(C.c_void_p),
+        check(lib().lodgs_cache_adam_step(self._h, frame.handle, _ptr(grads),
+                                          C.c_int64(_grad_rows_capacity(self.scene, grads)),
+                                          lrv.ctypes.data_as(C.c_void_p),
                                           C.c_float(b1), C.c_float(b2), C.c_float(eps), _stream_ptr(stream)))
 
     def writeback(self, stream=None) -> None:
@@ -438,7 +440,8 @@ def render_backward_project(scene: Scene, frame: Frame, grad: torch.Tensor, rows
                             dense: bool = False, stream=None) -> torch.Tensor:
     """Second half of render_backward: the projection backward into `grad`."""
     check(lib().lodgs_render_backward_project(scene.handle, frame.handle, _ptr(rows), _ptr(grad),
-                                              C.c_int(int(dense)), _stream_ptr(stream)))
+                                              C.c_int64(_grad_rows_capacity(scene, grad)), C.c_int(int(dense)),
+                                              _stream_ptr(stream)))
     return grad
 
 
@@ -515,5 +518,13 @@ def render_backward(scene: Scene, frame: Frame, dL_dimage: torch.Tensor, rows: t
     dL = dL_dimage.contiguous()
     img = _rendered_image(frame, image)
     check(lib().lodgs_render_backward(scene.handle, frame.handle, _ptr(rows), bgv, _ptr(img), _ptr(dL), _ptr(grad),
-                                      C.c_int(int(dense)), _stream_ptr(stream)))
+                                      C.c_int64(_grad_rows_capacity(scene, grad)), C.c_int(int(dense)),
+                                      _stream_ptr(stream)))
     return grad
+
+
+def _grad_rows_capacity(scene: Scene, grad: torch.Tensor) -> int:
+    """Whole gradient rows the tensor holds (the library checks the selection
+    against it on the device)."""
+    assert grad.is_cuda and grad.dtype == torch.float32 and grad.is_contiguous()
+    return grad.numel() // scene.stride

@@ -413,7 +413,8 @@ int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *i
     return LODGS_OK;
 }
 
-int lodgs_render_backward_project(lodgs_scene *sc, lodgs_frame *fr, const float *rows, float *grad_rows, int dense,
+int lodgs_render_backward_project(lodgs_scene *sc, lodgs_frame *fr, const float *rows, float *grad_rows,
+                                  int64_t grad_capacity, int dense,
                                   void *stream) {
     if (int rc = check_frame(sc, fr, "render_backward_project")) return rc;
     if (!grad_rows) {
@@ -435,14 +436,15 @@ int lodgs_render_backward_project(lodgs_scene *sc, lodgs_frame *fr, const float 
         fr->stream = st;
     }
     fr->mark(LODGS_STAGE_PROJECT_BWD, 0, st);
-    int rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->f, grad_rows, dense, st);
+    int rc = launch_project_backward(sc, rows ? rows : sc->d_rows, fr->f, grad_rows, grad_capacity, dense, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_PROJECT_BWD, 1, st);
     return LODGS_OK;
 }
 
 int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const float *bg,
-                          const float *image, const float *dL_dimage, float *grad_rows, int dense, void *stream) {
+                          const float *image, const float *dL_dimage, float *grad_rows, int64_t grad_capacity, int dense,
+                          void *stream) {
     if (int rc = check_frame(sc, fr, "render_backward")) return rc;
     if (!image || !dL_dimage || !grad_rows) {
         set_error("render_backward: NULL argument");
@@ -453,14 +455,16 @@ int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, c
         return LODGS_E_STATE;
     }
     int rc = lodgs_render_backward_blend(sc, fr, image, dL_dimage, stream);
-    if (!rc) rc = lodgs_render_backward_project(sc, fr, rows, grad_rows, dense, stream);
+    if (!rc) rc = lodgs_render_backward_project(sc, fr, rows, grad_rows, grad_capacity, dense, stream);
     return rc;
 }
 
 int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {
     if (!fr || !s) { set_error("frame_get_stats: NULL argument"); return LODGS_E_INVALID; }
     LODGS_CUDA(cudaStreamSynchronize(fr->stream));
-    if (!fr->rendered) LODGS_CUDA(cudaMemcpy(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost));
+    // the render leaves a copy of its counters; a backward since may have set a status bit
+    if (!fr->rendered || fr->blend_bwd_done)
+        LODGS_CUDA(cudaMemcpy(fr->h_cnt, fr->f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost));
     const uint32_t *h = fr->h_cnt;
     s->n_selected = h[C_NSEL];
     s->n_upper_selected = h[C_NUP];
@@ -472,6 +476,10 @@ int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {
     s->height = fr->k.H;
     s->status = LODGS_OK;
     if (h[C_STATUS] & ST_TIMEOUT) s->status = LODGS_E_TIMEOUT;
+    if (h[C_STATUS] & ST_GRAD_CAPACITY) {
+        s->status = LODGS_E_CAPACITY;
+        set_error("render_backward: the gradient rows were fewer than the selected nodes; nothing was written");
+    }
     if (h[C_STATUS] & ST_CAPACITY) {
         s->status = LODGS_E_CAPACITY;
         uint64_t ns = h[C_NSEL], np = h[C_NKEPT_WANT];

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(AB) k_adam(float4 *__restrict__ params, float4
                                              const uint32_t *__restrict__ rows, const float4 *__restrict__ grads,
                                              const uint32_t *__restrict__ d_n, uint32_t n_host, int quads, int used,
                                              ColumnRates rates, float b1, float b2, float eps) {
-    const uint32_t n = d_n ? *d_n : n_host;
+    const uint32_t n = d_n ? min(*d_n, n_host) : n_host;    // never past the caller's max_n rows
     const float omb1 = 1.0f - b1, omb2 = 1.0f - b2;
     const int lane = threadIdx.x & 31;
     const int rpw = 32 / quads;                              // rows per warp (quads <= 16)

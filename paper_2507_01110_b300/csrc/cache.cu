@@ -15,7 +15,10 @@
 //   resident  otherwise, if the cached prefix already covers high(x_j): cut at
 //             x_j from device-resident records, no transfer;
 //   load      otherwise copy the prefix [0, high(x_j)) into the slab (evicting
-//             least-recently-used SPTs not used by this view) and cut at x_j.
+//             least-recently-used SPTs not used by this view) and cut at x_j;
+//             a cached SPT whose prefix is too short keeps its records and
+//             streams only the tail: in place when the slab after it is free,
+//             else after a device-to-device move of the cached prefix.
 // The reuse ratio is taken on x = tau d / f, i.e. on the focal-normalised
 // distance, so cameras with different focal lengths share cached cuts.
 //
@@ -119,6 +122,29 @@ cudaError_t copy_rows(lodgs_cache *c, uint64_t dev, uint64_t host, uint64_t n, b
     if ((e = cp(c->d_v, c->h_v)) != cudaSuccess) return e;
     return to_host ? cudaMemcpyAsync(c->h_t + host, c->d_t + dev, n * 4, k, st)
                    : cudaMemcpyAsync(c->d_t + dev, c->h_t + host, n * 4, k, st);
+}
+
+// the records [at, at + len) if a free range starts exactly at `at` and holds them
+bool range_take_at(lodgs_cache *c, uint64_t at, uint64_t len) {
+    auto it = c->free_ranges.find(at);
+    if (it == c->free_ranges.end() || it->second < len) return false;
+    const uint64_t rest = it->second - len;
+    c->free_ranges.erase(it);
+    if (rest) c->free_ranges.emplace(at + len, rest);
+    return true;
+}
+
+// device-to-device move of n slab records (and the Adam state of a training cache)
+cudaError_t move_rows(lodgs_cache *c, uint64_t src, uint64_t dst, uint64_t n, cudaStream_t st) {
+    const size_t w = (size_t)c->scene->stride;
+    auto cp = [&](float *d) {
+        return cudaMemcpyAsync(d + dst * w, d + src * w, n * w * 4, cudaMemcpyDeviceToDevice, st);
+    };
+    cudaError_t e = cp(c->d_records);
+    if (e != cudaSuccess || !c->train) return e;
+    if ((e = cp(c->d_m)) != cudaSuccess) return e;
+    if ((e = cp(c->d_v)) != cudaSuccess) return e;
+    return cudaMemcpyAsync(c->d_t + dst, c->d_t + src, n * 4, cudaMemcpyDeviceToDevice, st);
 }
 
 // drop SPT j from the cache; a dirty prefix is first copied back to host
@@ -272,9 +298,12 @@ int lodgs_cache_host_state(lodgs_cache *c, float **h_rows, float **h_m, float **
     return LODGS_OK;
 }
 
-int lodgs_cache_adam_step(lodgs_cache *c, lodgs_frame *fr, const float *grads, const float *lr, float b1, float b2,
-                          float eps, void *stream) {
-    if (!c || !fr || !grads || !lr) { set_error("cache_adam_step: NULL argument"); return LODGS_E_INVALID; }
+int lodgs_cache_adam_step(lodgs_cache *c, lodgs_frame *fr, const float *grads, int64_t grad_capacity,
+                          const float *lr, float b1, float b2, float eps, void *stream) {
+    if (!c || !fr || !grads || !lr || grad_capacity < 0) {
+        set_error("cache_adam_step: NULL argument or negative capacity");
+        return LODGS_E_INVALID;
+    }
     if (!c->train) { set_error("cache_adam_step: the cache was not created for training"); return LODGS_E_STATE; }
     if (int rc = check_frame(c->scene, fr, "cache_adam_step")) return rc;
     if (fr->cache != c || fr->cache_view != c->view || !fr->blend_bwd_done) {
@@ -283,8 +312,9 @@ int lodgs_cache_adam_step(lodgs_cache *c, lodgs_frame *fr, const float *grads, c
     }
     cudaStream_t st = (cudaStream_t)stream;
     const FrameBufs &f = fr->f;
+    const int64_t max_n = std::min<int64_t>((int64_t)f.cap_sel, grad_capacity);
     if (int rc = launch_adam(c->scene, c->d_records, c->d_m, c->d_v, c->d_t, f.sel_src, grads, f.cnt + C_NSEL_EFF,
-                             (int64_t)f.cap_sel, lr, b1, b2, eps, st))
+                             max_n, lr, b1, b2, eps, st))
         return rc;
     LODGS_CUDA(cudaEventRecord(c->adam_done, st));
     for (Entry &e : c->entry)
@@ -379,18 +409,47 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
                 s.spt_resident += 1;
                 continue;
             }
-            LODGS_CUDA(evict(c, j, cs, &s.bytes_written_back));
+        }
+        const size_t per = c->train ? 3 * rec + 4 : rec;    // bytes a record streams
+        // slab space for `len` records, evicting least recently used SPTs (never this view's)
+        auto alloc = [&](uint64_t len, uint64_t *at) -> int {
+            while (!range_alloc(c, len, at)) {
+                if (c->lru.empty() || c->entry[c->lru.back()].used == c->view) {
+                    set_error("stream_nodes: the view's SPT records exceed the cache capacity");
+                    return LODGS_E_CAPACITY;
+                }
+                LODGS_CUDA(evict(c, c->lru.back(), cs, &s.bytes_written_back));
+                s.evictions += 1;
+            }
+            return LODGS_OK;
+        };
+        if (e.valid) {
+            // a longer prefix of a cached SPT: keep the cached records (trained
+            // or not) and stream only the tail, in place when the slab after the
+            // prefix is free, else after moving the prefix on the device
+            const uint64_t grow = need - e.h;
+            touch(c, j);
+            if (!range_take_at(c, e.off + e.h, grow)) {
+                uint64_t off = 0;
+                if (int rc = alloc(need, &off)) return rc;
+                LODGS_CUDA(move_rows(c, U + e.off, U + off, e.h, cs));
+                range_free(c, e.off, e.h);
+                e.off = off;
+            }
+            LODGS_CUDA(copy_rows(c, U + e.off + e.h, c->spt_base[j] + e.h, grow, false, cs));
+            c->cached_records += grow;
+            e.h = need;
+            e.x = x;
+            s.bytes_streamed += (int64_t)(grow * per);
+            s.spt_loaded += 1;
+            c->h_x_used[q] = x;
+            c->h_src[q] = (uint32_t)(U + e.off);
+            continue;
         }
         uint64_t off = 0;
-        while (!range_alloc(c, need, &off)) {                 // evict least recently used, never this view's
-            if (c->lru.empty() || c->entry[c->lru.back()].used == c->view) {
-                set_error("stream_nodes: the view's SPT records exceed the cache capacity");
-                return LODGS_E_CAPACITY;
-            }
-            LODGS_CUDA(evict(c, c->lru.back(), cs, &s.bytes_written_back));
-            s.evictions += 1;
-        }
+        if (int rc = alloc(need, &off)) return rc;
         e.valid = true;
+        e.dirty = false;
         e.x = x;
         e.h = need;
         e.off = off;
@@ -399,9 +458,8 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
         e.used = c->view;
         c->cached_records += need;
         c->cached_spts += 1;
-        const size_t bytes = (size_t)need * (c->train ? 3 * rec + 4 : rec);
         LODGS_CUDA(copy_rows(c, U + off, c->spt_base[j], need, false, cs));
-        s.bytes_streamed += (int64_t)bytes;
+        s.bytes_streamed += (int64_t)(need * per);
         s.spt_loaded += 1;
         c->h_x_used[q] = x;
         c->h_src[q] = (uint32_t)(U + off);

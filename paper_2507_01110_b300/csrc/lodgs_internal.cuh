@@ -67,7 +67,11 @@ __device__ __forceinline__ bool cam_culled(const CamK &k, const float t[3], floa
 }
 
 // ---- device status words and counters --------------------------------------
-enum : uint32_t { ST_CAPACITY = 1u, ST_TIMEOUT = 2u };
+enum : uint32_t {
+    ST_CAPACITY = 1u,       // a frame workspace buffer was too small
+    ST_TIMEOUT = 2u,        // a bounded device wait ran out
+    ST_GRAD_CAPACITY = 4u,  // the caller's gradient rows were fewer than the selection
+};
 enum {
     C_NSEL = 0,      // selected nodes (a1 + a2)
     C_NUP = 1,       // of which upper-hierarchy nodes
@@ -223,8 +227,8 @@ int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaS
 int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, const StageMarks &sm);
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, const float *dL_dimage,
                            cudaStream_t st);
-int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows, int dense,
-                            cudaStream_t st);
+int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows,
+                            int64_t grad_capacity, int dense, cudaStream_t st);
 }  // namespace lodgs
 
 struct lodgs_frame {

@@ -266,14 +266,23 @@ template <int DEG>
 __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ rows, int stride,
                                                      const uint32_t *__restrict__ sel_src,
                                                      const uint32_t *__restrict__ sel_rows,
-                                                     const View *__restrict__ view, const uint32_t *__restrict__ cnt,
+                                                     const View *__restrict__ view, uint32_t *__restrict__ cnt,
                                                      const uint32_t *__restrict__ ntiles,
                                                      const float *__restrict__ g2d, float *__restrict__ out,
-                                                     int dense) {
+                                                     int dense, uint32_t out_cap) {
     constexpr int RS = rec_stride(DEG), SP = RS + 1;
     __shared__ float s_rows[PB / 32][32 * SP];
     const CamK &k = view->k;
     const uint32_t n = cnt[C_NSEL_EFF];
+    if (!dense && n > out_cap) {
+        // sparse rows do not fit the caller's buffer: record it, write nothing,
+        // and leave no rows for the consumers of the count (Adam, batch sums)
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicOr(&cnt[C_STATUS], ST_GRAD_CAPACITY);
+            cnt[C_NSEL_EFF] = 0u;
+        }
+        return;
+    }
     constexpr int degree = DEG;
     constexpr int K = (DEG + 1) * (DEG + 1) - 1;
     (void)stride;
@@ -447,15 +456,20 @@ int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaS
     return LODGS_OK;
 }
 
-int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows, int dense,
-                            cudaStream_t st) {
+int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows,
+                            int64_t grad_capacity, int dense, cudaStream_t st) {
     if (sc->sh_degree < 0 || sc->sh_degree > 3 || sc->stride != rec_stride(sc->sh_degree)) {
         set_error("render_backward: record stride does not match the SH degree");
         return LODGS_E_INVALID;
     }
+    if (dense && grad_capacity < sc->n_nodes) {
+        set_error("render_backward: dense gradient rows need n_nodes rows");
+        return LODGS_E_INVALID;
+    }
+    const uint32_t cap = (uint32_t)std::min<int64_t>(std::max<int64_t>(grad_capacity, 0), UINT32_MAX);
 #define LAUNCH_PBWD(D)                                                                                     \
     k_project_bwd<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.sel_rows, f.d_view, \
-                                               f.cnt, f.ntiles, f.g2d, grad_rows, dense)
+                                               f.cnt, f.ntiles, f.g2d, grad_rows, dense, cap)
     switch (sc->sh_degree) {
         case 0: LAUNCH_PBWD(0); break;
         case 1: LAUNCH_PBWD(1); break;

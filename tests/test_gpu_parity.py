@@ -247,3 +247,30 @@ def test_select_with_lod_noise_matches_oracle(api, c1):
             api.select_lod(sc_g, cam_s, fr)
             assert np.array_equal(fr.selection().cpu().numpy(), sel_o)
             assert fr.stats()["n_spt_scanned"] == st_o["spt_scanned"]
+
+
+def test_backward_refuses_gradient_rows_smaller_than_the_selection(api, c1):
+    """The caller's sparse gradient buffer is checked on the device against the
+    selection count: nothing is written, the frame reports LODGS_E_CAPACITY and
+    its device row count drops to 0, so a following Adam step does nothing."""
+    cfg, sc_o, sc_g = c1
+    cam = cfg["cameras"][0]
+    fr = api.select_lod(sc_g, cam)
+    img = api.render(sc_g, fr)
+    n = fr.stats()["n_selected"]
+    assert n > 1
+    g = torch.full((n - 1, sc_g.stride), 7.0, device="cuda")
+    api.render_backward(sc_g, fr, torch.ones_like(img), grad=g)
+    st = fr.stats()
+    assert st["status"] == -6
+    assert torch.all(g == 7.0)
+
+    def device_count():
+        return int(api._device_view(api.frame_device_count(fr), (1,), "<u4").item())
+
+    assert device_count() == 0
+    g_ok = torch.empty((n, sc_g.stride), device="cuda")
+    api.select_lod(sc_g, cam, fr)
+    api.render(sc_g, fr)
+    api.render_backward(sc_g, fr, torch.ones_like(img), grad=g_ok)
+    assert fr.stats()["status"] == 0 and device_count() == n
