@@ -55,6 +55,40 @@ struct Entry {
     std::list<uint32_t>::iterator lru;
 };
 
+// One contiguous copy between the device slab and pinned host memory (through
+// its device address) or within the slab, in 16-byte units (4-byte units for
+// step counts).  Spans are cut into pieces of at most 64 KiB, one CTA each.
+struct Piece {
+    const void *src;
+    void *dst;
+    uint32_t n;               // units
+    uint32_t word;            // 1: 4-byte units, 0: 16-byte units
+};
+constexpr uint64_t PIECE_BYTES = 64 << 10;
+constexpr int PIECE_THREADS = 256;
+
+// Every piece of one phase in one launch: the host issues a few launches per
+// view instead of one cudaMemcpyAsync per SPT and array, and reads of host
+// memory keep several 16-byte requests in flight per thread.
+__global__ void __launch_bounds__(PIECE_THREADS) k_copy_pieces(const Piece *__restrict__ pieces) {
+    const Piece p = pieces[blockIdx.x];
+    if (p.word) {
+        const uint32_t *__restrict__ src = static_cast<const uint32_t *>(p.src);
+        uint32_t *__restrict__ dst = static_cast<uint32_t *>(p.dst);
+        for (uint32_t i = threadIdx.x; i < p.n; i += PIECE_THREADS) dst[i] = src[i];
+    } else {
+        const uint4 *__restrict__ src = static_cast<const uint4 *>(p.src);
+        uint4 *__restrict__ dst = static_cast<uint4 *>(p.dst);
+#pragma unroll 4
+        for (uint32_t i = threadIdx.x; i < p.n; i += PIECE_THREADS) dst[i] = src[i];
+    }
+}
+
+// copy phases of one batch, issued in this order: write-backs read slab ranges
+// that moves and loads of the same batch may overwrite, and moves read ranges
+// that are freed only after the batch
+enum : int { PH_TO_HOST = 0, PH_MOVE = 1, PH_LOAD = 2, PH_COUNT = 3 };
+
 }  // namespace
 
 struct lodgs_cache {
@@ -69,6 +103,14 @@ struct lodgs_cache {
     float *h_m = nullptr, *h_v = nullptr, *d_m = nullptr, *d_v = nullptr;
     uint32_t *h_t = nullptr, *d_t = nullptr;
     cudaEvent_t adam_done = nullptr;  // after the last Adam step (its stream is the caller's)
+    // device addresses of the pinned host arrays (read and written by k_copy_pieces)
+    float *hd_rows = nullptr, *hd_m = nullptr, *hd_v = nullptr;
+    uint32_t *hd_t = nullptr;
+    // pending copies of the current batch, and their staging
+    std::vector<Piece> pend[PH_COUNT];
+    Piece *h_pieces = nullptr, *d_pieces = nullptr;
+    size_t pieces_cap = 0;
+    cudaEvent_t pieces_done = nullptr;  // after the last batch's kernels (staging reusable)
     std::vector<uint32_t> spt_base;   // host copy (n_spt + 1)
     std::vector<Entry> entry;
     std::list<uint32_t> lru;          // front = most recently used
@@ -107,21 +149,77 @@ bool range_alloc(lodgs_cache *c, uint64_t len, uint64_t *off) {
     return false;
 }
 
-// copies n records from slab/host slot `dev` to/from host row `host` for the
-// four arrays of a training cache (records only otherwise)
-cudaError_t copy_rows(lodgs_cache *c, uint64_t dev, uint64_t host, uint64_t n, bool to_host, cudaStream_t st) {
-    const size_t w = (size_t)c->scene->stride;
-    const cudaMemcpyKind k = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
-    auto cp = [&](float *d, float *h) {
-        return to_host ? cudaMemcpyAsync(h + host * w, d + dev * w, n * w * 4, k, st)
-                       : cudaMemcpyAsync(d + dev * w, h + host * w, n * w * 4, k, st);
+void add_span(std::vector<Piece> &v, const void *src, void *dst, uint64_t bytes, bool word) {
+    const uint64_t unit = word ? 4 : 16;
+    for (uint64_t o = 0; o < bytes; o += PIECE_BYTES) {
+        const uint64_t b = std::min<uint64_t>(PIECE_BYTES, bytes - o);
+        v.push_back({static_cast<const char *>(src) + o, static_cast<char *>(dst) + o, (uint32_t)(b / unit),
+                     word ? 1u : 0u});
+    }
+}
+
+// n records from slab slot `dev` to/from host row `host`, for the four arrays
+// of a training cache (records only otherwise); rows are multiples of 16 bytes
+void add_rows(lodgs_cache *c, int phase, uint64_t dev, uint64_t host, uint64_t n, bool to_host) {
+    const size_t w = (size_t)c->scene->stride, bytes = n * w * 4;
+    std::vector<Piece> &v = c->pend[phase];
+    auto span = [&](float *d, float *h) {
+        if (to_host) add_span(v, d + dev * w, h + host * w, bytes, false);
+        else add_span(v, h + host * w, d + dev * w, bytes, false);
     };
-    cudaError_t e = cp(c->d_records, c->h_rows);
-    if (e != cudaSuccess || !c->train) return e;
-    if ((e = cp(c->d_m, c->h_m)) != cudaSuccess) return e;
-    if ((e = cp(c->d_v, c->h_v)) != cudaSuccess) return e;
-    return to_host ? cudaMemcpyAsync(c->h_t + host, c->d_t + dev, n * 4, k, st)
-                   : cudaMemcpyAsync(c->d_t + dev, c->h_t + host, n * 4, k, st);
+    span(c->d_records, c->hd_rows);
+    if (!c->train) return;
+    span(c->d_m, c->hd_m);
+    span(c->d_v, c->hd_v);
+    if (to_host) add_span(v, c->d_t + dev, c->hd_t + host, n * 4, true);
+    else add_span(v, c->hd_t + host, c->d_t + dev, n * 4, true);
+}
+
+// n slab records (and their Adam state) from slot src to slot dst
+void add_move(lodgs_cache *c, uint64_t src, uint64_t dst, uint64_t n) {
+    const size_t w = (size_t)c->scene->stride, bytes = n * w * 4;
+    std::vector<Piece> &v = c->pend[PH_MOVE];
+    add_span(v, c->d_records + src * w, c->d_records + dst * w, bytes, false);
+    if (!c->train) return;
+    add_span(v, c->d_m + src * w, c->d_m + dst * w, bytes, false);
+    add_span(v, c->d_v + src * w, c->d_v + dst * w, bytes, false);
+    add_span(v, c->d_t + src, c->d_t + dst, n * 4, true);
+}
+
+// issue the batch on `st`: one descriptor upload, one launch per non-empty phase
+int issue_pieces(lodgs_cache *c, cudaStream_t st) {
+    size_t total = 0;
+    for (auto &v : c->pend) total += v.size();
+    if (!total) return LODGS_OK;
+    LODGS_CUDA(cudaEventSynchronize(c->pieces_done));       // the staging of the last batch is free
+    if (total > c->pieces_cap) {
+        cudaFreeHost(c->h_pieces);
+        cudaFree(c->d_pieces);
+        c->h_pieces = nullptr;
+        c->d_pieces = nullptr;
+        c->pieces_cap = 0;
+        const size_t cap = std::max<size_t>(total + total / 2, 4096);
+        LODGS_CUDA(cudaMallocHost((void **)&c->h_pieces, cap * sizeof(Piece)));
+        LODGS_CUDA(cudaMalloc((void **)&c->d_pieces, cap * sizeof(Piece)));
+        c->pieces_cap = cap;
+    }
+    size_t at = 0, start[PH_COUNT];
+    for (int ph = 0; ph < PH_COUNT; ++ph) {
+        start[ph] = at;
+        if (!c->pend[ph].empty()) memcpy(c->h_pieces + at, c->pend[ph].data(), c->pend[ph].size() * sizeof(Piece));
+        at += c->pend[ph].size();
+    }
+    LODGS_CUDA(cudaMemcpyAsync(c->d_pieces, c->h_pieces, total * sizeof(Piece), cudaMemcpyHostToDevice, st));
+    for (int ph = 0; ph < PH_COUNT; ++ph) {
+        const size_t n = c->pend[ph].size();
+        if (!n) continue;
+        k_copy_pieces<<<(unsigned)n, PIECE_THREADS, 0, st>>>(c->d_pieces + start[ph]);
+        count_launches(1);
+        c->pend[ph].clear();
+    }
+    LODGS_CUDA(cudaGetLastError());
+    LODGS_CUDA(cudaEventRecord(c->pieces_done, st));
+    return LODGS_OK;
 }
 
 // the records [at, at + len) if a free range starts exactly at `at` and holds them
@@ -134,27 +232,13 @@ bool range_take_at(lodgs_cache *c, uint64_t at, uint64_t len) {
     return true;
 }
 
-// device-to-device move of n slab records (and the Adam state of a training cache)
-cudaError_t move_rows(lodgs_cache *c, uint64_t src, uint64_t dst, uint64_t n, cudaStream_t st) {
-    const size_t w = (size_t)c->scene->stride;
-    auto cp = [&](float *d) {
-        return cudaMemcpyAsync(d + dst * w, d + src * w, n * w * 4, cudaMemcpyDeviceToDevice, st);
-    };
-    cudaError_t e = cp(c->d_records);
-    if (e != cudaSuccess || !c->train) return e;
-    if ((e = cp(c->d_m)) != cudaSuccess) return e;
-    if ((e = cp(c->d_v)) != cudaSuccess) return e;
-    return cudaMemcpyAsync(c->d_t + dst, c->d_t + src, n * 4, cudaMemcpyDeviceToDevice, st);
-}
-
-// drop SPT j from the cache; a dirty prefix is first copied back to host
-// memory on `st` (the copy stream), before any later copy into the range
-cudaError_t evict(lodgs_cache *c, uint32_t j, cudaStream_t st, int64_t *written) {
+// drop SPT j from the cache; a dirty prefix is first queued for write-back to
+// host memory (the batch's first phase, ahead of any copy into the range)
+void evict(lodgs_cache *c, uint32_t j, int64_t *written) {
     Entry &e = c->entry[j];
     if (e.dirty) {
         const uint64_t U = (uint64_t)c->scene->n_upper_rows;
-        cudaError_t err = copy_rows(c, U + e.off, c->spt_base[j], e.h, true, st);
-        if (err != cudaSuccess) return err;
+        add_rows(c, PH_TO_HOST, U + e.off, c->spt_base[j], e.h, true);
         if (written) *written += (int64_t)e.h * c->scene->stride * 4 * (c->train ? 3 : 1) + (c->train ? e.h * 4 : 0);
         e.dirty = false;
     }
@@ -163,7 +247,6 @@ cudaError_t evict(lodgs_cache *c, uint32_t j, cudaStream_t st, int64_t *written)
     c->cached_records -= e.h;
     c->cached_spts -= 1;
     e.valid = false;
-    return cudaSuccess;
 }
 
 void touch(lodgs_cache *c, uint32_t j) {
@@ -211,6 +294,9 @@ int lodgs_cache_create(lodgs_scene *sc, const lodgs_cache_params *p, lodgs_cache
     if (e != cudaSuccess) return fail(cuda_fail(e, "cache_create: SPT bases"));
     c->entry.resize(S);
     c->free_ranges.emplace(0, c->slab_records);
+    if ((e = cudaHostGetDevicePointer((void **)&c->hd_rows, c->h_rows, 0)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->pieces_done, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(cuda_fail(e, "cache_create: device address of the host records"));
     const size_t n = (size_t)std::max<int64_t>(S, 1);
     if ((e = cudaMallocHost((void **)&c->h_cnt, C_COUNT * 4)) != cudaSuccess ||
         (e = cudaMallocHost((void **)&c->h_emit_j, n * 4)) != cudaSuccess ||
@@ -230,6 +316,10 @@ int lodgs_cache_create(lodgs_scene *sc, const lodgs_cache_params *p, lodgs_cache
         memset(c->h_m, 0, (size_t)M * rec);
         memset(c->h_v, 0, (size_t)M * rec);
         memset(c->h_t, 0, (size_t)M * 4);
+        if ((e = cudaHostGetDevicePointer((void **)&c->hd_m, c->h_m, 0)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer((void **)&c->hd_v, c->h_v, 0)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer((void **)&c->hd_t, c->h_t, 0)) != cudaSuccess)
+            return fail(cuda_fail(e, "cache_create: device address of the host Adam state"));
         if ((e = cudaMalloc((void **)&c->d_m, slots * rec)) != cudaSuccess ||
             (e = cudaMalloc((void **)&c->d_v, slots * rec)) != cudaSuccess ||
             (e = cudaMalloc((void **)&c->d_t, std::max<size_t>(slots, 1) * 4)) != cudaSuccess)
@@ -259,6 +349,9 @@ void lodgs_cache_free(lodgs_cache *c) {
     cudaFree(c->d_m); cudaFree(c->d_v); cudaFree(c->d_t);
     if (c->copies_done) cudaEventDestroy(c->copies_done);
     if (c->adam_done) cudaEventDestroy(c->adam_done);
+    if (c->pieces_done) cudaEventDestroy(c->pieces_done);
+    cudaFreeHost(c->h_pieces);
+    cudaFree(c->d_pieces);
     delete c;
 }
 
@@ -272,15 +365,15 @@ int writeback_all(lodgs_cache *c, cudaStream_t st) {
     for (uint32_t j = 0; j < (uint32_t)c->entry.size(); ++j) {
         Entry &e = c->entry[j];
         if (!e.valid || !e.dirty) continue;
-        LODGS_CUDA(copy_rows(c, U + e.off, c->spt_base[j], e.h, true, st));
+        add_rows(c, PH_TO_HOST, U + e.off, c->spt_base[j], e.h, true);
         e.dirty = false;
     }
     if (U && c->upper_dirty) {
-        LODGS_CUDA(copy_rows(c, 0, 0, U, true, st));
+        add_rows(c, PH_TO_HOST, 0, 0, U, true);
         c->upper_dirty = false;
     }
     (void)M;
-    return LODGS_OK;
+    return issue_pieces(c, st);
 }
 }  // namespace
 
@@ -387,6 +480,7 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
     const uint32_t n_emit = c->h_cnt[C_NEMIT];
     const size_t rec = (size_t)sc->stride * sizeof(float);
     const uint64_t U = (uint64_t)sc->n_upper_rows;
+    std::vector<std::pair<uint64_t, uint64_t>> moved_from;   // slab ranges vacated by moves
     for (uint32_t q = 0; q < n_emit; ++q) {
         const uint32_t j = c->h_emit_j[q];
         const float x = c->h_emit_x[q];
@@ -418,7 +512,7 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
                     set_error("stream_nodes: the view's SPT records exceed the cache capacity");
                     return LODGS_E_CAPACITY;
                 }
-                LODGS_CUDA(evict(c, c->lru.back(), cs, &s.bytes_written_back));
+                evict(c, c->lru.back(), &s.bytes_written_back);
                 s.evictions += 1;
             }
             return LODGS_OK;
@@ -432,11 +526,11 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
             if (!range_take_at(c, e.off + e.h, grow)) {
                 uint64_t off = 0;
                 if (int rc = alloc(need, &off)) return rc;
-                LODGS_CUDA(move_rows(c, U + e.off, U + off, e.h, cs));
-                range_free(c, e.off, e.h);
+                add_move(c, U + e.off, U + off, e.h);
+                moved_from.emplace_back(e.off, e.h);      // freed once the batch is queued
                 e.off = off;
             }
-            LODGS_CUDA(copy_rows(c, U + e.off + e.h, c->spt_base[j] + e.h, grow, false, cs));
+            add_rows(c, PH_LOAD, U + e.off + e.h, c->spt_base[j] + e.h, grow, false);
             c->cached_records += grow;
             e.h = need;
             e.x = x;
@@ -458,12 +552,15 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
         e.used = c->view;
         c->cached_records += need;
         c->cached_spts += 1;
-        LODGS_CUDA(copy_rows(c, U + off, c->spt_base[j], need, false, cs));
+        add_rows(c, PH_LOAD, U + off, c->spt_base[j], need, false);
         s.bytes_streamed += (int64_t)(need * per);
         s.spt_loaded += 1;
         c->h_x_used[q] = x;
         c->h_src[q] = (uint32_t)(U + off);
     }
+    // the batch: write-backs, then moves, then loads, all on the copy stream
+    if (int rc = issue_pieces(c, cs)) return rc;
+    for (auto &r : moved_from) range_free(c, r.first, r.second);
     LODGS_CUDA(cudaEventRecord(c->copies_done, cs));
     // 3. SPT cut at the chosen distances, with the slab slot of every record
     if (n_emit) {
