@@ -735,13 +735,42 @@ def run_out_of_core(args) -> dict:
                 "cut_nodes_per_iter": int(cut / len(order)),
                 "spt_hit_rate": round(tot["spt_hits"] / max(1, n_spt_views), 4)}
 
+    # the host link: pinned 1 GiB copies each way, the denominator of the streaming stage
+    def link_gbs(to_host: bool) -> float:
+        h = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
+        d = torch.empty(1 << 28, dtype=torch.float32, device="cuda")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 0.0
+        for _ in range(4):
+            ev0.record()
+            if to_host:
+                h.copy_(d, non_blocking=True)
+            else:
+                d.copy_(h, non_blocking=True)
+            ev1.record()
+            ev1.synchronize()
+            best = max(best, (1 << 30) / (ev0.elapsed_time(ev1) * 1e-3) / 1e9)
+        return best
+
+    link = {"h2d_gbs": round(link_gbs(False), 1), "d2h_gbs": round(link_gbs(True), 1),
+            "note": "pinned 1 GiB cudaMemcpyAsync, best of 4"}
+    link["flythrough_h2d_frac"] = round(main["bytes_streamed_per_frame"] * main["frames_per_s"] / 1e9
+                                        / link["h2d_gbs"], 4)
+    for r in training["runs"]:
+        if "ms_per_iter" in r:
+            # the streaming time alone if both directions ran at the link peak, one after the other
+            t_link = r["bytes_streamed_per_iter"] / (link["h2d_gbs"] * 1e9) + \
+                r["bytes_written_back_per_iter"] / (link["d2h_gbs"] * 1e9)
+            r["link_bound_ms"] = round(1e3 * t_link, 2)
+            r["link_frac"] = round(1e3 * t_link / r["ms_per_iter"], 3)
+
     uniform = loads(np.random.default_rng(34).integers(len(pool), size=iters).tolist())
     sched = schedule.ViewScheduler(np.array([c.pos for c in pool]), k=10, seed=35)
     knn = loads([sched.next() for _ in range(iters)])
     return {"workload": f"{args.ooc_leaves:,}-leaf SH3 city, records in pinned host memory, 8 GiB device "
                         f"cache, {len(cams)}-view flythrough 300 m -> 20 m at 1920x1080, forward only",
             **main, "host_record_gb": round(scene.n_nodes * scene.stride * 4 / 1e9, 2), "reuse_window": [0.9, 1.1],
-            "cache_size_sweep": sweep, "training": training,
+            "cache_size_sweep": sweep, "training": training, "host_link": link,
             "view_selection": {"pool_views": len(pool), "iterations": iters,
                                "note": "nodes loaded from host per training iteration; a cache-less run loads "
                                        "the whole cut (cut_nodes_per_iter)",

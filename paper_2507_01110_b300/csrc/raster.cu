@@ -698,10 +698,16 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
                 if (COUNT) n_eval += BP;
                 if (!__any_sync(0xffffffffu, any)) continue;
                 const float cb = s_c[j];
-                const float ax2 = 2.0f * a.z * dx, cy2 = 2.0f * b.x, hdx2 = -0.5f * dx * dx;
                 // predicated: a lane whose pixel misses gets alpha = e = 0, which
-                // leaves T and G.S unchanged and makes every term below zero
-                float gv[9];
+                // leaves T and G.S unchanged and makes every term below zero.
+                // Where alpha is not clamped, dL/dp = alpha dL/dalpha = o de with
+                // de = e dL/dalpha (o the opacity), and de itself is dL/do.  With
+                // p = a.z dx^2 + a.w dx dy + b.x dy^2 the mean and conic gradients
+                // are linear in the moments q0 = sum de, q1 = sum de dy,
+                // q2 = sum de dy^2 over the lane's pixels (which share dx).  The
+                // warp reduces dx q0, q1, dx^2 q0, dx q1, q2 and q0 (= dL/do); the
+                // flush applies o and the coefficients 2 a.z, a.w, 2 b.x.
+                float q0 = 0.f, q1 = 0.f, q2 = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
                 bool died = false;
 #pragma unroll
                 for (int k = 0; k < BP; ++k) {
@@ -714,18 +720,21 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
                     const float gc = G[k][0] * b.z + G[k][1] * b.w + G[k][2] * cb;
                     gS[k] -= w * gc;                                                      // G.S_i
                     const float dA = T[k] * gc - rcp_ftz(1.0f - alpha) * gS[k];
-                    const bool free_ = raw <= ALPHA_MAX;                                  // alpha not clamped
-                    const float dp = free_ ? dA * alpha : 0.f;
-                    const float c[9] = {dp * (ax2 + a.w * dy), dp * (cy2 * dy + bx), dp * hdx2, -(dp * dx) * dy,
-                                        -0.5f * dp * dy * dy, free_ ? dA * e : 0.f, G[k][0] * w, G[k][1] * w,
-                                        G[k][2] * w};
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) gv[q] = k == 0 ? c[q] : gv[q] + c[q];
+                    const float de = raw <= ALPHA_MAX ? dA * e : 0.f;                    // 0 where clamped
+                    const float t = de * dy;
+                    q0 += de;
+                    q1 += t;
+                    q2 = __fmaf_rn(t, dy, q2);
+                    gr += G[k][0] * w;
+                    gg += G[k][1] * w;
+                    gb += G[k][2] * w;
                     T[k] = T[k] * (1.0f - alpha);                                         // as the forward
                     const bool stop = hit[k] && T[k] < T_MIN;
                     live[k] = live[k] && !stop;
                     died |= stop;
                 }
+                const float dq0 = dx * q0;
+                float gv[9] = {dq0, q1, dx * dq0, dx * q1, q2, q0, gr, gg, gb};
                 warp_sum9_to_smem(gv, lane, s_grad[j]);
                 if (__any_sync(0xffffffffu, died)) {
                     done = true;
@@ -738,8 +747,13 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
         __syncthreads();
         for (int q = tid; q < n; q += NT) {
             float *o = g2d + (size_t)s_g[q] * G2D_STRIDE;
-            const float4 x0 = make_float4(s_grad[q][0], s_grad[q][1], s_grad[q][2], s_grad[q][3]);
-            const float4 x1 = make_float4(s_grad[q][4], s_grad[q][5], s_grad[q][6], s_grad[q][7]);
+            // moments -> d(u, v) and d(conic) with this Gaussian's opacity and coefficients
+            const float o_ = s_b[q].y;
+            const float r0 = o_ * s_grad[q][0], r1 = o_ * s_grad[q][1], r2 = o_ * s_grad[q][2];
+            const float r3 = o_ * s_grad[q][3], r4 = o_ * s_grad[q][4];
+            const float az = s_a[q].z, aw = s_a[q].w, bxc = s_b[q].x;
+            const float4 x0 = make_float4(2.0f * az * r0 + aw * r1, aw * r0 + 2.0f * bxc * r1, -0.5f * r2, -r3);
+            const float4 x1 = make_float4(-0.5f * r4, s_grad[q][5], s_grad[q][6], s_grad[q][7]);
             if (x0.x != 0.f || x0.y != 0.f || x0.z != 0.f || x0.w != 0.f)
                 atomicAdd(reinterpret_cast<float4 *>(o), x0);
             if (x1.x != 0.f || x1.y != 0.f || x1.z != 0.f || x1.w != 0.f)
