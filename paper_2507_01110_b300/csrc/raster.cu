@@ -124,15 +124,52 @@ __global__ void k_ranges(const uint32_t *__restrict__ pkey, uint32_t *__restrict
 // rectangle areas, selection order) and is the k-th tile of its rectangle in
 // row-major order.  Returns the tile of the pair, or -1 when the tile support
 // test drops it.
-__device__ __forceinline__ int64_t rect_pair(uint32_t p, uint32_t n, const uint32_t *__restrict__ pair_off,
-                                             const uint2 *__restrict__ rect, const float4 *__restrict__ sp_a,
-                                             const float4 *__restrict__ sp_b, int TX, uint32_t &g) {
-    uint32_t a = 0, b = n;
-    while (b - a > 1) {
-        const uint32_t m = (a + b) >> 1;
-        if (pair_off[m] <= p) a = m; else b = m;
+// Owner of pair p = p0 + lane for a warp's 32 consecutive pair indices: the
+// largest selected index g with pair_off[g] <= p (pair_off is the exclusive
+// scan of the rectangle areas, pair_off[n] = P implied).  One 32-ary search for
+// p0 (each round all lanes probe, about 33x narrower per round), then each lane
+// searches the 32 offsets from that Gaussian on by shuffles; a lane past them
+// (empty rectangles in between) finishes with its own binary search.  Every
+// lane of the warp must call this.
+__device__ __forceinline__ uint32_t warp_pair_owner(uint32_t p0, uint32_t p, uint32_t n,
+                                                    const uint32_t *__restrict__ pair_off, int lane) {
+    uint32_t a = 0, b = n;                       // pair_off[a] <= p0 < pair_off[b]
+    while (b - a > 32) {
+        const uint32_t m = a + (uint32_t)(((uint64_t)(b - a) * (uint32_t)(lane + 1)) / 33u);   // a < m < b
+        const uint32_t c = __popc(__ballot_sync(0xffffffffu, pair_off[m] <= p0));
+        const uint32_t ma = __shfl_sync(0xffffffffu, m, c > 0 ? (int)c - 1 : 0);
+        const uint32_t mb = __shfl_sync(0xffffffffu, m, c < 32 ? (int)c : 31);
+        if (c > 0) a = ma;
+        if (c < 32) b = mb;
     }
-    g = a;
+    {
+        const uint32_t v = a + lane < b ? pair_off[a + lane] : 0xffffffffu;
+        a += __popc(__ballot_sync(0xffffffffu, v <= p0)) - 1;      // pair_off[a] <= p0 holds: >= 1 lane
+    }
+    const uint32_t w = a + lane < n ? pair_off[a + lane] : 0xffffffffu;
+    uint32_t idx = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1) {
+        const uint32_t v = __shfl_sync(0xffffffffu, w, (int)idx + st);
+        if (v <= p) idx += st;
+    }
+    uint32_t g = a + idx;
+    if (idx == 31) {                             // the window may not reach p: finish alone
+        uint32_t lo = g, hi = n;
+        while (hi - lo > 1) {
+            const uint32_t m = (lo + hi) >> 1;
+            if (pair_off[m] <= p) lo = m; else hi = m;
+        }
+        g = lo;
+    }
+    return g;
+}
+
+// Tile of pair p of Gaussian g (row-major in its rectangle), or -1 when the
+// tile support test drops it.
+__device__ __forceinline__ int64_t pair_tile(uint32_t p, uint32_t g, const uint32_t *__restrict__ pair_off,
+                                             const uint2 *__restrict__ rect, const float4 *__restrict__ sp_a,
+                                             const float4 *__restrict__ sp_b, int TX) {
     const uint2 rc = rect[g];
     const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
     const uint32_t w = x1 - x0, k = p - pair_off[g];
@@ -158,8 +195,8 @@ __global__ void __launch_bounds__(RB) k_emit_count(const uint32_t *__restrict__ 
     // whole warps step together so that the match below sees every lane
     for (uint32_t p0 = (blockIdx.x * RB + threadIdx.x) & ~31u; p0 < P; p0 += gridDim.x * RB) {
         const uint32_t p = p0 + lane;
-        uint32_t g;
-        const int64_t t = p < P ? rect_pair(p, n, pair_off, rect, sp_a, sp_b, TX, g) : -1;
+        const uint32_t g = warp_pair_owner(p0, p, n, pair_off, lane);
+        const int64_t t = p < P ? pair_tile(p, g, pair_off, rect, sp_a, sp_b, TX) : -1;
         const uint32_t key = t < 0 ? 0xffffffffu : (uint32_t)t;
         const uint32_t peers = __match_any_sync(0xffffffffu, key);
         if (t >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&tile_cnt[t], (uint32_t)__popc(peers));
@@ -234,8 +271,8 @@ __global__ void __launch_bounds__(RB) k_emit_scatter(const uint32_t *__restrict_
     const int lane = threadIdx.x & 31;
     for (uint32_t p0 = (blockIdx.x * RB + threadIdx.x) & ~31u; p0 < P; p0 += gridDim.x * RB) {
         const uint32_t p = p0 + lane;
-        uint32_t g = 0;
-        const int64_t t = p < P ? rect_pair(p, n, pair_off, rect, sp_a, sp_b, TX, g) : -1;
+        const uint32_t g = warp_pair_owner(p0, p, n, pair_off, lane);
+        const int64_t t = p < P ? pair_tile(p, g, pair_off, rect, sp_a, sp_b, TX) : -1;
         const uint32_t key = t < 0 ? 0xffffffffu : (uint32_t)t;
         const uint32_t peers = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(peers) - 1;
