@@ -424,6 +424,19 @@ int lodgs_render_backward_blend(lodgs_scene *scene, lodgs_frame *frame, const fl
 int lodgs_render_backward_project(lodgs_scene *scene, lodgs_frame *frame, const float *rows, float *grad_rows,
                                   int64_t grad_capacity, int dense, void *stream);
 
+/*
+ * The blend backward of the mean-L1 training step with the loss folded in:
+ * dL/dC = grad_scale * sign(image - target) is formed per pixel inside the
+ * backward (no dL/dC buffer, no separate pass over the image), and
+ * *loss_sum = sum |image - target| over the image (device float, overwritten;
+ * grad_scale = 1/n and loss_sum / n give the mean).  target: device H x W x 3
+ * float32.  The same results as lodgs_l1_loss_grad followed by
+ * lodgs_render_backward_blend, up to the order of float atomic sums.
+ * Not part of the paper's method: its loss is the training objective around it.
+ */
+int lodgs_render_backward_blend_l1(lodgs_scene *scene, lodgs_frame *frame, const float *image, const float *target,
+                                   float grad_scale, float *loss_sum, void *stream);
+
 /* Counters of the last select/render on this frame (blocks until `stream`,
  * the stream the frame last ran on, is idle). */
 int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);

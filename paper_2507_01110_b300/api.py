@@ -436,6 +436,21 @@ def render_backward_blend(scene: Scene, frame: Frame, dL_dimage: torch.Tensor, s
                                             _ptr(dL_dimage.contiguous()), _stream_ptr(stream)))
 
 
+def render_backward_blend_l1(scene: Scene, frame: Frame, target: torch.Tensor, loss_sum: torch.Tensor | None = None,
+                             grad_scale: float | None = None, stream=None, image: torch.Tensor | None = None
+                             ) -> torch.Tensor:
+    """Blend backward of the mean-L1 loss against `target`, the loss folded in:
+    dL/dC = grad_scale * sign(image - target) (default scale 1/numel) is formed
+    in the kernel; returns loss_sum (device, sum |image - target|)."""
+    img = _rendered_image(frame, image)
+    if loss_sum is None:
+        loss_sum = torch.empty(1, dtype=torch.float32, device="cuda")
+    scale = 1.0 / max(img.numel(), 1) if grad_scale is None else grad_scale
+    check(lib().lodgs_render_backward_blend_l1(scene.handle, frame.handle, _ptr(img), _ptr(target.contiguous()),
+                                               C.c_float(scale), _ptr(loss_sum), _stream_ptr(stream)))
+    return loss_sum
+
+
 def render_backward_project(scene: Scene, frame: Frame, grad: torch.Tensor, rows: torch.Tensor | None = None,
                             dense: bool = False, stream=None) -> torch.Tensor:
     """Second half of render_backward: the projection backward into `grad`."""

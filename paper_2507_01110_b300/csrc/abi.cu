@@ -384,11 +384,12 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     return LODGS_OK;
 }
 
-int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const float *dL_dimage,
-                                void *stream) {
-    if (int rc = check_frame(sc, fr, "render_backward_blend")) return rc;
-    if (!image || !dL_dimage) {
-        set_error("render_backward_blend: NULL argument");
+namespace {
+int backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const float *dL_dimage,
+                   const float *target, float l1_scale, float *loss_sum, void *stream, const char *who) {
+    if (int rc = check_frame(sc, fr, who)) return rc;
+    if (!image || (!dL_dimage && !(target && loss_sum))) {
+        set_error(std::string(who) + ": NULL argument");
         return LODGS_E_INVALID;
     }
     if (!fr->rendered) { set_error("render_backward: render was not called on this frame"); return LODGS_E_STATE; }
@@ -406,11 +407,24 @@ int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *i
         fr->stream = st;
     }
     fr->mark(LODGS_STAGE_BLEND_BWD, 0, st);
-    int rc = launch_raster_backward(fr->k, fr->f, image, dL_dimage, st);
+    int rc = launch_raster_backward(fr->k, fr->f, image, dL_dimage, target, l1_scale, loss_sum, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_BLEND_BWD, 1, st);
     fr->blend_bwd_done = true;
     return LODGS_OK;
+}
+}  // namespace
+
+int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const float *dL_dimage,
+                                void *stream) {
+    if (!dL_dimage) { set_error("render_backward_blend: NULL dL_dimage"); return LODGS_E_INVALID; }
+    return backward_blend(sc, fr, image, dL_dimage, nullptr, 0.f, nullptr, stream, "render_backward_blend");
+}
+
+int lodgs_render_backward_blend_l1(lodgs_scene *sc, lodgs_frame *fr, const float *image, const float *target,
+                                   float grad_scale, float *loss_sum, void *stream) {
+    if (!target || !loss_sum) { set_error("render_backward_blend_l1: NULL argument"); return LODGS_E_INVALID; }
+    return backward_blend(sc, fr, image, nullptr, target, grad_scale, loss_sum, stream, "render_backward_blend_l1");
 }
 
 int lodgs_render_backward_project(lodgs_scene *sc, lodgs_frame *fr, const float *rows, float *grad_rows,

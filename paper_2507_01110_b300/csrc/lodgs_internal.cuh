@@ -226,7 +226,7 @@ int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaSt
 int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaStream_t st);
 int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, const StageMarks &sm);
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, const float *dL_dimage,
-                           cudaStream_t st);
+                           const float *target, float l1_scale, float *loss_sum, cudaStream_t st);
 int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows,
                             int64_t grad_capacity, int dense, cudaStream_t st);
 }  // namespace lodgs

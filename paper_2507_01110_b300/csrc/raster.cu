@@ -659,12 +659,17 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
 // with 16-byte atomics.
 // BP pixels per lane: 2 (a warp per 8x8 block, 128 threads per tile) or 4 (a
 // warp per 8x16 column of two blocks, 64 threads per tile).
-template <bool COUNT, int BP>
+// L1: dL/dC is not read but formed from the image and a target as the L1
+// loss's gradient, l1_scale * sign(C - target), and the block adds its
+// sum |C - target| to *loss_sum (the training loss folded into the backward:
+// no separate pass over the image, no dL/dC buffer).
+template <bool COUNT, int BP, bool L1>
 __global__ void __launch_bounds__(TILE_PIX / BP)
     k_blend_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
                 const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c,
                 const uint32_t *__restrict__ cnt, int W, int H, int TX, const float *__restrict__ image,
-                const float *__restrict__ dL_dimg, float *__restrict__ g2d, unsigned long long *__restrict__ work) {
+                const float *__restrict__ dL_dimg, float *__restrict__ g2d, unsigned long long *__restrict__ work,
+                const float *__restrict__ target, float l1_scale, float *__restrict__ loss_sum) {
     constexpr int NT = TILE_PIX / BP, NW = NT / 32;
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
@@ -683,6 +688,7 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
     float yc[BP], T[BP], gS[BP], G[BP][3];
     bool live[BP];
     bool done = true;
+    float l1 = 0.f;
 #pragma unroll
     for (int k = 0; k < BP; ++k) {
         const int py = bp.py0 + 4 * k;
@@ -692,11 +698,34 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
         G[k][0] = G[k][1] = G[k][2] = gS[k] = 0.f;
         if (live[k]) {
             const size_t o = ((size_t)py * W + bp.px) * 3;
+            const float c0 = image[o], c1 = image[o + 1], c2 = image[o + 2];
+            if (L1) {
+                const float d[3] = {c0 - target[o], c1 - target[o + 1], c2 - target[o + 2]};
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) G[k][ch] = dL_dimg[o + ch];
-            gS[k] = G[k][0] * image[o] + G[k][1] * image[o + 1] + G[k][2] * image[o + 2];   // G.C
+                for (int ch = 0; ch < 3; ++ch) {
+                    G[k][ch] = l1_scale * (d[ch] > 0.f ? 1.f : (d[ch] < 0.f ? -1.f : 0.f));
+                    l1 += fabsf(d[ch]);
+                }
+            } else {
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) G[k][ch] = dL_dimg[o + ch];
+            }
+            gS[k] = G[k][0] * c0 + G[k][1] * c1 + G[k][2] * c2;                       // G.C
         }
         done &= !live[k];
+    }
+    if (L1) {                                                                    // the tile's loss sum
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+        __shared__ float s_l1[NW];
+        if (lane == 0) s_l1[bp.w] = l1;
+        __syncthreads();
+        if (tid == 0) {
+            float sum = 0.f;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) sum += s_l1[w];
+            atomicAdd(loss_sum, sum);
+        }
     }
     uint32_t n_eval = 0, n_contrib = 0;
     const uint2 rg = ranges[tile];
@@ -879,12 +908,21 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
 }
 
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, const float *dL_dimage,
-                           cudaStream_t st) {
+                           const float *target, float l1_scale, float *loss_sum, cudaStream_t st) {
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * G2D_STRIDE * sizeof(float), st));
     LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
-    (f.count_work ? k_blend_bwd<true, BWD_PIX> : k_blend_bwd<false, BWD_PIX>)<<<(unsigned)n_tiles, TILE_PIX / BWD_PIX, 0, st>>>(
-        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, dL_dimage, f.g2d, f.work);
+    const unsigned nb = (unsigned)n_tiles, nt = TILE_PIX / BWD_PIX;
+    if (target) {
+        LODGS_CUDA(cudaMemsetAsync(loss_sum, 0, sizeof(float), st));
+        (f.count_work ? k_blend_bwd<true, BWD_PIX, true> : k_blend_bwd<false, BWD_PIX, true>)<<<nb, nt, 0, st>>>(
+            f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, nullptr, f.g2d, f.work,
+            target, l1_scale, loss_sum);
+    } else {
+        (f.count_work ? k_blend_bwd<true, BWD_PIX, false> : k_blend_bwd<false, BWD_PIX, false>)<<<nb, nt, 0, st>>>(
+            f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, dL_dimage, f.g2d, f.work,
+            nullptr, 0.f, nullptr);
+    }
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;

@@ -78,3 +78,32 @@ def test_split_backward_matches_the_combined_call():
     api.render(scene, fr)
     with pytest.raises(Exception):
         api.render_backward_project(scene, fr, g2)
+
+
+def test_fused_l1_backward_matches_loss_then_backward():
+    """lodgs_render_backward_blend_l1 (the mean-L1 gradient formed inside the
+    blend backward) against lodgs_l1_loss_grad followed by the plain blend
+    backward: the same loss sum and the same gradient rows, up to the order of
+    float atomic sums."""
+    from paper_2507_01110_b300 import api, build
+    build.build()
+    cfg = synth.config2_scene(n=200_000)
+    scene = api.build_hierarchy(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
+    cam = synth.camera_look(cfg["cameras"][12].pos, cfg["cameras"][12].R[2], cfg["cameras"][12].R[0], 333, 190)
+    gen = torch.Generator(device="cuda").manual_seed(8)
+    target = torch.rand((cam.height, cam.width, 3), device="cuda", generator=gen)
+    fr = api.select_lod(scene, cam)
+    img = api.render(scene, fr)
+    n = fr.stats()["n_selected"]
+    dL, loss_a = api.l1_loss_grad(img, target)
+    api.render_backward_blend(scene, fr, dL)
+    g_a = torch.empty((n, scene.stride), device="cuda")
+    api.render_backward_project(scene, fr, g_a)
+    loss_b = api.render_backward_blend_l1(scene, fr, target)
+    g_b = torch.empty((n, scene.stride), device="cuda")
+    api.render_backward_project(scene, fr, g_b)
+    torch.cuda.synchronize()
+    assert abs(loss_a.item() - loss_b.item()) <= 1e-5 * abs(loss_a.item())
+    scale = g_a.abs().amax(dim=0) + 1e-30
+    assert torch.all((g_a - g_b).abs() <= 1e-4 * scale)
+    assert g_a.abs().max() > 0
