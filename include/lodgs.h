@@ -149,10 +149,14 @@ int lodgs_scene_export(const lodgs_scene *scene, float *node_rec, int64_t *left,
  * layout before the call and must be leaves of it; a node made by an earlier
  * operation of the same batch cannot be a target or dead, and `dead` != `target`.
  * ops[i].dead is ignored for SPAWN.
- *   old_row_of_new_row  host, capacity >= the new n_nodes: for each render row of
- *                       the new layout, the row the node held before the call,
- *                       or -1 for a node whose record is new (the children).
- *                       Per-row state follows it through lodgs_gather_rows.
+ *   old_row_of_new_row  device int32, capacity >= the new n_nodes: for each render
+ *                       row of the new layout, the row the node held before the
+ *                       call, or -1 for a node whose record is new (the
+ *                       children).  Per-row state follows it through
+ *                       lodgs_gather_rows.
+ * The host edits only the nodes the operations touch (values gathered on the
+ * device, changes scattered back); records, layout and row map are built on the
+ * device.
  * Render rows are renumbered: frames and caches created before the call are
  * rejected afterwards (LODGS_E_STATE) and must be recreated.  Requires the
  * scene's records on the device (LODGS_E_STATE after a cache released them).
@@ -168,6 +172,31 @@ typedef struct {
 } lodgs_densify_op;
 int lodgs_scene_densify(lodgs_scene *scene, const lodgs_densify_op *ops, int64_t n_ops,
                         int32_t *old_row_of_new_row, int64_t capacity);
+
+/*
+ * The operations of one densification step, planned on the device (Sec. 3
+ * "Densification": candidates by maximal screen-space gradient, the
+ * hierarchical 3DGS criterion; dead leaves respawned; appendix edge cases):
+ *   dead:      leaves with a parent whose opacity (record column 10 of `rows`)
+ *              is below min_opacity or whose stale flag is set, except the
+ *              left child of a node whose two children are dead;
+ *   candidate: leaves that are neither transparent nor stale, with
+ *              grad_max >= grad_threshold, largest first, ties by row.
+ * The i-th dead row is respawned under the i-th candidate; the remaining
+ * candidates spawn while n_nodes + 2 * spawns <= max_nodes (max_nodes < 0:
+ * no budget).  ops receives the spawns, then the respawns, in the order
+ * lodgs_scene_densify applies them.
+ *   rows:      device records in render-row order (NULL = the scene's own)
+ *   grad_max:  device float per render row (lodgs_frame_screen_grad_max)
+ *   stale:     device uint8 per render row, nonzero = stale, or NULL
+ *   ops:       host, `capacity` entries; *n_ops = operations planned (also
+ *              when capacity is too small: LODGS_E_INVALID), *n_spawn of them
+ *              spawns.
+ * Synchronises `stream`.
+ */
+int lodgs_densify_plan(lodgs_scene *scene, const float *rows, const float *grad_max, const uint8_t *stale,
+                       float grad_threshold, float min_opacity, int64_t max_nodes, lodgs_densify_op *ops,
+                       int64_t capacity, int64_t *n_ops, int64_t *n_spawn, void *stream);
 
 /* Per-view state: selection, projected splats, sorted pairs and workspace.
  * Buffers grow on demand; a frame may be reused for any camera and resolution

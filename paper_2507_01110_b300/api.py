@@ -52,6 +52,11 @@ def camera_struct(cam) -> _Cam:
     return c
 
 
+# numpy mirror of lodgs_densify_op (int32 kind, int32 padding, int64 target, int64 dead)
+_OP_DTYPE = np.dtype([("kind", np.int32), ("pad_", np.int32), ("target", np.int64), ("dead", np.int64)])
+assert _OP_DTYPE.itemsize == C.sizeof(_lib.DensifyOp)
+
+
 class Scene:
     """A built scene (library-owned device memory)."""
 
@@ -75,16 +80,23 @@ class Scene:
         children.  Both carry the split of the target's record.  Operations run
         spawn first, then respawn, in list order.  Rebuilds the HSPT/SPT layout;
         frames and caches made earlier must be recreated.  Returns, per new
-        render row, the row the node held before (-1 for the new children), to
-        carry per-row state such as Adam moments across."""
-        ops = [(_lib.DENSIFY_SPAWN, int(t), -1) for t in spawn] + \
-              [(_lib.DENSIFY_RESPAWN, int(t), int(d)) for t, d in respawn]
-        arr = (_lib.DensifyOp * max(len(ops), 1))()
-        for i, (k, t, d) in enumerate(ops):
-            arr[i].kind, arr[i].target, arr[i].dead = k, t, d
-        cap = self.n_nodes + 2 * len(spawn)
-        out = np.zeros(cap, np.int32)
-        rc = lib().lodgs_scene_densify(self._h, C.cast(arr, C.c_void_p), len(ops), C.c_void_p(out.ctypes.data), cap)
+        render row, the row the node held before (-1 for the new children), as
+        an int32 CUDA tensor, to carry per-row state such as Adam moments
+        across (gather_rows)."""
+        sp = np.asarray(spawn, dtype=np.int64).reshape(-1)
+        rs = np.asarray(respawn, dtype=np.int64).reshape(-1, 2)
+        n_ops = sp.size + rs.shape[0]
+        arr = np.zeros(max(n_ops, 1), _OP_DTYPE)             # the layout of lodgs_densify_op
+        arr["kind"][:sp.size] = _lib.DENSIFY_SPAWN
+        arr["target"][:sp.size] = sp
+        arr["dead"][:sp.size] = -1
+        arr["kind"][sp.size:n_ops] = _lib.DENSIFY_RESPAWN
+        arr["target"][sp.size:n_ops] = rs[:, 0]
+        arr["dead"][sp.size:n_ops] = rs[:, 1]
+        cap = self.n_nodes + 2 * sp.size
+        out = torch.empty(cap, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        rc = lib().lodgs_scene_densify(self._h, C.c_void_p(arr.ctypes.data), n_ops, C.c_void_p(out.data_ptr()), cap)
         self._refresh()
         check(rc)
         return out[:self.n_nodes]
@@ -97,6 +109,37 @@ class Scene:
         """The scene's node records in render-row order (n_nodes x stride), a
         zero-copy view of library-owned device memory valid while the scene lives."""
         return _device_view(self._rows_ptr, (self.n_nodes, self.stride), "<f4")
+
+    def plan_densify(self, grad_max: torch.Tensor, grad_threshold: float, min_opacity: float = 0.005,
+                     max_nodes: int | None = None, stale: torch.Tensor | None = None,
+                     rows: torch.Tensor | None = None, stream=None) -> tuple[list, list]:
+        """The operations of one densification step, planned on the device
+        (candidates by maximal screen-space gradient, dead leaves by opacity or
+        the stale flag, the appendix's two-dead-siblings rule): (spawn rows,
+        [(target row, dead row)]) for densify()."""
+        assert grad_max.is_cuda and grad_max.dtype == torch.float32 and grad_max.numel() == self.n_nodes
+        if stale is not None:
+            stale = stale.to(device="cuda", dtype=torch.uint8).contiguous()
+        n_ops, n_sp = C.c_int64(), C.c_int64()
+
+        def run(cap):
+            arr = np.zeros(max(cap, 1), _OP_DTYPE)
+            rc = lib().lodgs_densify_plan(self._h, _ptr(rows), _ptr(grad_max.contiguous()),
+                                          C.c_void_p(stale.data_ptr()) if stale is not None else None,
+                                          C.c_float(grad_threshold), C.c_float(min_opacity),
+                                          C.c_int64(-1 if max_nodes is None else int(max_nodes)),
+                                          C.c_void_p(arr.ctypes.data), C.c_int64(cap), C.byref(n_ops),
+                                          C.byref(n_sp), _stream_ptr(stream))
+            return rc, arr
+
+        rc, arr = run(1 << 16)
+        if rc == _lib.LODGS_E_INVALID and n_ops.value > (1 << 16):
+            rc, arr = run(n_ops.value)                 # more operations than the first buffer held
+        check(rc)
+        ns, n = n_sp.value, n_ops.value                # spawns first, then respawns
+        spawn = arr["target"][:ns].tolist()
+        respawn = list(zip(arr["target"][ns:n].tolist(), arr["dead"][ns:n].tolist()))
+        return spawn, respawn
 
     def topology(self) -> dict:
         """Children (canonical ids, -1 for leaves), node_of_row and the root, copied
@@ -334,7 +377,10 @@ def gather_rows(src: torch.Tensor, src_row, stream=None) -> torch.Tensor:
     (a densification's old_row_of_new_row; the gather runs in the library's
     kernel).  src: CUDA tensor of a 4-byte dtype, rows along dim 0."""
     assert src.is_cuda and src.element_size() == 4 and src.is_contiguous()
-    idx = torch.as_tensor(np.ascontiguousarray(src_row, dtype=np.int32)).to("cuda", non_blocking=False)
+    if isinstance(src_row, torch.Tensor):
+        idx = src_row.to(device="cuda", dtype=torch.int32).contiguous()
+    else:
+        idx = torch.as_tensor(np.ascontiguousarray(src_row, dtype=np.int32)).to("cuda", non_blocking=False)
     n = idx.numel()
     words = int(np.prod(src.shape[1:])) if src.dim() > 1 else 1
     out = torch.empty((n,) + tuple(src.shape[1:]), dtype=src.dtype, device="cuda")

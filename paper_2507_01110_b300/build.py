@@ -22,7 +22,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcom
                  "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
 EXACT = {"scene.cu", "select.cu", "project.cu", "abi.cu"}     # no FMA contraction
 SOURCES = ["abi.cu", "scene.cu", "select.cu", "project.cu", "raster.cu", "sort.cu", "noalloc.cu", "cache.cu", "batch.cu",
-           "loss.cu", "adam.cu"]
+           "loss.cu", "adam.cu", "densify.cu"]
 
 
 def _newer(src_paths, out):

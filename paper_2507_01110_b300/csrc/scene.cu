@@ -384,6 +384,46 @@ __global__ void k_upper_rows(const int32_t *__restrict__ up_node, const int32_t 
     hi_row[up_ref[u]] = NAN;
 }
 
+// ---- densification helpers ---------------------------------------------
+__global__ void k_gather_i32(const int32_t *__restrict__ src, const int32_t *__restrict__ idx, int64_t n,
+                             int32_t *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)BT + threadIdx.x;
+    if (i < n) out[i] = idx[i] >= 0 ? src[idx[i]] : -1;
+}
+
+__global__ void k_scatter_i32(int32_t *__restrict__ dst, const int32_t *__restrict__ idx_val, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)BT + threadIdx.x;
+    if (i < n) dst[idx_val[2 * i]] = idx_val[2 * i + 1];
+}
+
+__global__ void k_parent_of(const int32_t *__restrict__ left, const int32_t *__restrict__ right, int64_t M,
+                            int32_t *__restrict__ parent) {
+    const int64_t u = blockIdx.x * (int64_t)BT + threadIdx.x;
+    if (u >= M || left[u] < 0) return;
+    parent[left[u]] = (int32_t)u;
+    parent[right[u]] = (int32_t)u;
+}
+
+__global__ void k_row_of_node(const int32_t *__restrict__ node_of_row, int64_t M, int32_t *__restrict__ row_of) {
+    const int64_t r = blockIdx.x * (int64_t)BT + threadIdx.x;
+    if (r < M) row_of[node_of_row[r]] = (int32_t)r;
+}
+
+__global__ void k_mark(uint8_t *__restrict__ flag, const int32_t *__restrict__ ids, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)BT + threadIdx.x;
+    if (i < n) flag[ids[i]] = 1;
+}
+
+// old render row of each new render row, -1 for a node whose record is new
+__global__ void k_row_map(const int32_t *__restrict__ node_of_row, int64_t M, int64_t M0,
+                          const int32_t *__restrict__ old_row_of, const uint8_t *__restrict__ fresh,
+                          int32_t *__restrict__ out) {
+    const int64_t r = blockIdx.x * (int64_t)BT + threadIdx.x;
+    if (r >= M) return;
+    const int32_t u = node_of_row[r];
+    out[r] = (u < M0 && !fresh[u]) ? old_row_of[u] : -1;
+}
+
 // The two children of a densified leaf (Sec. 3 "Densification": the split of
 // 3DGS-MCMC, whose implementation the paper reuses, with N = 2): both keep the
 // target's mean, rotation and colour.  Their opacity o' = 1 - sqrt(1 - o)
@@ -696,6 +736,98 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
     return build_layout(sc, node_rec.p, left.p, right.p, parent.p, M, (int32_t)(M - 1), p, st);
 }
 
+namespace {
+
+// int32 -> int32 map with open addressing (keys >= 0), for the few nodes a
+// densification touches out of millions
+struct FlatMap {
+    std::vector<int64_t> slot;                  // key << 32 | value, or -1
+    size_t n = 0, mask = 0;
+    FlatMap() { rehash(1024); }
+    void rehash(size_t cap) {
+        std::vector<int64_t> old;
+        old.swap(slot);
+        slot.assign(cap, -1);
+        mask = cap - 1;
+        n = 0;
+        for (int64_t kv : old)
+            if (kv >= 0) put((int32_t)(kv >> 32), (int32_t)(uint32_t)kv);
+    }
+    size_t home(int32_t k) const { return (size_t)(((uint64_t)(uint32_t)k * 0x9E3779B97F4A7C15ull) >> 20) & mask; }
+    int64_t *find(int32_t k) {
+        for (size_t i = home(k);; i = (i + 1) & mask) {
+            if (slot[i] < 0) return nullptr;
+            if ((int32_t)(slot[i] >> 32) == k) return &slot[i];
+        }
+    }
+    void put(int32_t k, int32_t v) {
+        if (2 * (n + 1) > slot.size()) rehash(2 * slot.size());
+        for (size_t i = home(k);; i = (i + 1) & mask) {
+            if (slot[i] < 0) { slot[i] = (int64_t)k << 32 | (uint32_t)v; ++n; return; }
+            if ((int32_t)(slot[i] >> 32) == k) { slot[i] = (int64_t)k << 32 | (uint32_t)v; return; }
+        }
+    }
+    bool get(int32_t k, int32_t *v) {
+        const int64_t *p = find(k);
+        if (!p) return false;
+        *v = (int32_t)(uint32_t)*p;
+        return true;
+    }
+    template <typename F> void each(F f) const {
+        for (int64_t kv : slot)
+            if (kv >= 0) f((int32_t)(kv >> 32), (int32_t)(uint32_t)kv);
+    }
+};
+
+// The tree as the host edits it: values of the device arrays (children, parent,
+// node of row) fetched for the nodes the operations touch, in batched gathers,
+// with the edits kept in an overlay; only the changed entries go back, by
+// scatter.  A value outside the prefetched set (a chain of edits reaching
+// further) is fetched on its own.
+struct TreeView {
+    enum Field { LEFT = 0, RIGHT = 1, PARENT = 2, NOR = 3 };
+    const int32_t *dev[4];
+    FlatMap base[4], edit[3];
+    cudaError_t err = cudaSuccess;
+
+    int32_t get(int f, int32_t i) {
+        int32_t v;
+        if (f < 3 && edit[f].get(i, &v)) return v;
+        if (base[f].get(i, &v)) return v;
+        v = -1;
+        if (i >= 0) {
+            cudaError_t e = cudaMemcpy(&v, dev[f] + i, 4, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) err = e;
+        }
+        base[f].put(i, v);
+        return v;
+    }
+    void set(int f, int32_t i, int32_t v) { edit[f].put(i, v); }
+    // one gather of dev[f] at the given indices (-1 entries skipped) into the base cache
+    int prefetch(int f, const std::vector<int32_t> &idx) {
+        std::vector<int32_t> want;
+        want.reserve(idx.size());
+        int32_t v;
+        for (int32_t i : idx)
+            if (i >= 0 && !base[f].get(i, &v)) want.push_back(i);
+        std::sort(want.begin(), want.end());
+        want.erase(std::unique(want.begin(), want.end()), want.end());
+        if (want.empty()) return LODGS_OK;
+        DevBuf<int32_t> d_idx, d_out;
+        CK(d_idx.alloc(want.size()));
+        CK(d_out.alloc(want.size()));
+        CK(cudaMemcpy(d_idx.p, want.data(), want.size() * 4, cudaMemcpyHostToDevice));
+        k_gather_i32<<<nblk((int64_t)want.size()), BT>>>(dev[f], d_idx.p, (int64_t)want.size(), d_out.p);
+        count_launches(1);
+        std::vector<int32_t> got(want.size());
+        CK(cudaMemcpy(got.data(), d_out.p, want.size() * 4, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < want.size(); ++k) base[f].put(want[k], got[k]);
+        return LODGS_OK;
+    }
+};
+
+}  // namespace
+
 int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, int32_t *old_row_of_new_row,
                   int64_t capacity) {
     if (!sc->d_rows) {
@@ -717,24 +849,47 @@ int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, i
     const int64_t M = M0 + 2 * n_spawn;
     if (M >= (int64_t)1 << 31) { set_error("scene_densify: more than 2^31 nodes"); return LODGS_E_INVALID; }
     if (capacity < M) { set_error("scene_densify: old_row_of_new_row holds fewer than the new node count"); return LODGS_E_INVALID; }
-    // host topology
-    std::vector<int32_t> left(M, -1), right(M, -1), parent(M, -1), node_of_row(M0), row_of_node(M0);
-    CK(cudaMemcpy(left.data(), sc->d_left, M0 * 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(right.data(), sc->d_right, M0 * 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(node_of_row.data(), sc->d_node_of_row, M0 * 4, cudaMemcpyDeviceToHost));
-    for (int64_t r = 0; r < M0; ++r) row_of_node[node_of_row[r]] = (int32_t)r;
-    for (int64_t u = 0; u < M0; ++u) {
-        if (left[u] >= 0) parent[left[u]] = (int32_t)u;
-        if (right[u] >= 0) parent[right[u]] = (int32_t)u;
+    // parents of the current tree, on the device
+    DevBuf<int32_t> d_parent0;
+    CK(d_parent0.alloc(M0));
+    CK(cudaMemset(d_parent0.p, 0xff, M0 * 4));
+    k_parent_of<<<nblk(M0), BT>>>(sc->d_left, sc->d_right, M0, d_parent0.p);
+    count_launches(1);
+    TreeView tv;
+    tv.dev[TreeView::LEFT] = sc->d_left;
+    tv.dev[TreeView::RIGHT] = sc->d_right;
+    tv.dev[TreeView::PARENT] = d_parent0.p;
+    tv.dev[TreeView::NOR] = sc->d_node_of_row;
+    // prefetch what the operations read: targets and dead nodes, their parents,
+    // the parents' children and parents, and those nodes' children
+    {
+        std::vector<int32_t> rows_t, v1, v2, v3;
+        for (int64_t i = 0; i < n_ops; ++i) {
+            rows_t.push_back((int32_t)ops[i].target);
+            if (ops[i].kind == LODGS_DENSIFY_RESPAWN) rows_t.push_back((int32_t)ops[i].dead);
+        }
+        if (int rc = tv.prefetch(TreeView::NOR, rows_t)) return rc;
+        for (int32_t r : rows_t) v1.push_back(tv.get(TreeView::NOR, r));
+        if (int rc = tv.prefetch(TreeView::LEFT, v1)) return rc;
+        if (int rc = tv.prefetch(TreeView::PARENT, v1)) return rc;
+        for (int32_t u : v1) v2.push_back(tv.get(TreeView::PARENT, u));
+        for (int f : {TreeView::LEFT, TreeView::RIGHT, TreeView::PARENT})
+            if (int rc = tv.prefetch(f, v2)) return rc;
+        for (int32_t u : v2) v3.push_back(u >= 0 ? tv.get(TreeView::PARENT, u) : -1);
+        for (int f : {TreeView::LEFT, TreeView::RIGHT})
+            if (int rc = tv.prefetch(f, v3)) return rc;
     }
-    int32_t root = sc->root;
-    std::vector<uint8_t> fresh(M, 0);                // nodes whose record is new
+    FlatMap fresh;                                   // nodes whose record is new (value unused)
+    std::vector<int32_t> fresh_ids;
     std::vector<int32_t> trip;                       // (target, child a, child b) per operation
     trip.reserve(3 * n_ops);
+    int32_t root = sc->root;
     int32_t next = (int32_t)M0;
+    auto L = [&](int32_t u) { return tv.get(TreeView::LEFT, u); };
+    auto is_fresh = [&](int32_t u) { int32_t v; return fresh.get(u, &v); };
     for (int64_t i = 0; i < n_ops; ++i) {
-        const int32_t T = node_of_row[ops[i].target];
-        if (left[T] >= 0 || fresh[T]) {
+        const int32_t T = tv.get(TreeView::NOR, (int32_t)ops[i].target);
+        if (L(T) >= 0 || is_fresh(T)) {
             set_error("scene_densify: operation " + std::to_string(i) + ": the target is not an original leaf");
             return LODGS_E_INVALID;
         }
@@ -743,33 +898,68 @@ int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, i
             a = next++;
             b = next++;
         } else {
-            const int32_t D = node_of_row[ops[i].dead], P = parent[D];
-            if (left[D] >= 0 || fresh[D] || D == T || P < 0) {
+            const int32_t D = tv.get(TreeView::NOR, (int32_t)ops[i].dead);
+            const int32_t P = tv.get(TreeView::PARENT, D);
+            if (L(D) >= 0 || is_fresh(D) || D == T || P < 0) {
                 set_error("scene_densify: operation " + std::to_string(i) +
                           ": the dead node must be an original leaf with a parent, other than the target");
                 return LODGS_E_INVALID;
             }
-            const int32_t S = left[P] == D ? right[P] : left[P], G = parent[P];
+            const int32_t S = tv.get(TreeView::LEFT, P) == D ? tv.get(TreeView::RIGHT, P) : tv.get(TreeView::LEFT, P);
+            const int32_t G = tv.get(TreeView::PARENT, P);
             if (G >= 0) {                            // the sibling takes the parent's place
-                if (left[G] == P) left[G] = S; else right[G] = S;
+                if (tv.get(TreeView::LEFT, G) == P) tv.set(TreeView::LEFT, G, S);
+                else tv.set(TreeView::RIGHT, G, S);
             } else {
                 root = S;
             }
-            parent[S] = G;
+            tv.set(TreeView::PARENT, S, G);
             a = P;
             b = D;
         }
-        left[T] = a; right[T] = b;
-        parent[a] = parent[b] = T;
-        left[a] = right[a] = left[b] = right[b] = -1;
-        fresh[a] = fresh[b] = 1;
+        tv.set(TreeView::LEFT, T, a);
+        tv.set(TreeView::RIGHT, T, b);
+        tv.set(TreeView::PARENT, a, T);
+        tv.set(TreeView::PARENT, b, T);
+        for (int32_t c : {a, b}) {
+            tv.set(TreeView::LEFT, c, -1);
+            tv.set(TreeView::RIGHT, c, -1);
+        }
+        fresh.put(a, 1);
+        fresh.put(b, 1);
+        fresh_ids.push_back(a);
+        fresh_ids.push_back(b);
         trip.push_back(T); trip.push_back(a); trip.push_back(b);
+    }
+    if (tv.err != cudaSuccess) CK(tv.err);
+    // the new topology: the old arrays grown by the spawned nodes, patched with the edits
+    DevBuf<int32_t> d_left, d_right, d_parent, d_patch;
+    CK(d_left.alloc(M)); CK(d_right.alloc(M)); CK(d_parent.alloc(M));
+    CK(cudaMemset(d_left.p, 0xff, M * 4)); CK(cudaMemset(d_right.p, 0xff, M * 4)); CK(cudaMemset(d_parent.p, 0xff, M * 4));
+    CK(cudaMemcpy(d_left.p, sc->d_left, M0 * 4, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(d_right.p, sc->d_right, M0 * 4, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(d_parent.p, d_parent0.p, M0 * 4, cudaMemcpyDeviceToDevice));
+    {
+        size_t most = 0;
+        for (auto &e : tv.edit) most = std::max(most, e.n);
+        CK(d_patch.alloc(2 * std::max<size_t>(most, 1)));
+        int32_t *dst[3] = {d_left.p, d_right.p, d_parent.p};
+        std::vector<int32_t> kv;
+        for (int f = 0; f < 3; ++f) {
+            if (!tv.edit[f].n) continue;
+            kv.clear();
+            tv.edit[f].each([&](int32_t k, int32_t v) { kv.push_back(k); kv.push_back(v); });
+            CK(cudaMemcpy(d_patch.p, kv.data(), kv.size() * 4, cudaMemcpyHostToDevice));
+            k_scatter_i32<<<nblk((int64_t)tv.edit[f].n), BT>>>(dst[f], d_patch.p, (int64_t)tv.edit[f].n);
+            count_launches(1);
+        }
     }
     // the records: canonical order on the device, children written by one kernel
     // (targets are original leaves, never rewritten within a batch, so the
     // operations' splits are independent)
     DevBuf<float> node_rec;
-    DevBuf<int32_t> d_trip;
+    DevBuf<int32_t> d_trip, old_row_of, d_fresh_ids;
+    DevBuf<uint8_t> d_fresh;
     CK(node_rec.alloc((size_t)M * stride));
     CK(d_trip.alloc(trip.size()));
     CK(cudaMemcpy(d_trip.p, trip.data(), trip.size() * 4, cudaMemcpyHostToDevice));
@@ -779,21 +969,25 @@ int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, i
         k_split_children<<<nblk(n_ops * stride), BT>>>(node_rec.p, stride, d_trip.p, n_ops);
         count_launches(1);
     }
+    // what the row map needs from the old layout
+    CK(old_row_of.alloc(M0));
+    k_row_of_node<<<nblk(M0), BT>>>(sc->d_node_of_row, M0, old_row_of.p);
+    CK(d_fresh.alloc(M));
+    CK(cudaMemset(d_fresh.p, 0, M));
+    CK(d_fresh_ids.alloc(fresh_ids.size()));
+    if (!fresh_ids.empty()) {
+        CK(cudaMemcpy(d_fresh_ids.p, fresh_ids.data(), fresh_ids.size() * 4, cudaMemcpyHostToDevice));
+        k_mark<<<nblk((int64_t)fresh_ids.size()), BT>>>(d_fresh.p, d_fresh_ids.p, (int64_t)fresh_ids.size());
+    }
+    count_launches(2);
     CK(cudaGetLastError());
-    DevBuf<int32_t> d_left, d_right, d_parent;
-    CK(d_left.alloc(M)); CK(d_right.alloc(M)); CK(d_parent.alloc(M));
-    CK(cudaMemcpy(d_left.p, left.data(), M * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_right.p, right.data(), M * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_parent.p, parent.data(), M * 4, cudaMemcpyHostToDevice));
     lodgs_build_params p{sc->spt_volume, sc->kappa};
     if (int rc = build_layout(sc, node_rec.p, d_left.p, d_right.p, d_parent.p, M, root, p, 0)) return rc;
     sc->layout_version++;
-    std::vector<int32_t> nor(M);
-    CK(cudaMemcpy(nor.data(), sc->d_node_of_row, M * 4, cudaMemcpyDeviceToHost));
-    for (int64_t r = 0; r < M; ++r) {
-        const int32_t u = nor[r];
-        old_row_of_new_row[r] = (u < M0 && !fresh[u]) ? row_of_node[u] : -1;
-    }
+    k_row_map<<<nblk(M), BT>>>(sc->d_node_of_row, M, M0, old_row_of.p, d_fresh.p, old_row_of_new_row);
+    count_launches(1);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
     return LODGS_OK;
 }
 
