@@ -35,6 +35,7 @@
 
 #include <list>
 #include <map>
+#include <set>
 #include <new>
 #include <string>
 #include <vector>
@@ -115,6 +116,7 @@ struct lodgs_cache {
     std::vector<Entry> entry;
     std::list<uint32_t> lru;          // front = most recently used
     std::map<uint64_t, uint64_t> free_ranges;   // offset -> length
+    std::set<std::pair<uint64_t, uint64_t>> free_by_len;   // (length, offset) of the same ranges
     uint64_t view = 0, cached_records = 0, cached_spts = 0;
     // pinned staging for the per-view decisions
     uint32_t *h_cnt = nullptr, *h_emit_j = nullptr, *h_high = nullptr, *h_src = nullptr;
@@ -124,29 +126,43 @@ struct lodgs_cache {
 
 namespace {
 
+// The slab's free space: ranges by offset (for merging neighbours) and by
+// length (best fit in O(log n) however fragmented the slab is).
+void range_put(lodgs_cache *c, uint64_t off, uint64_t len) {
+    c->free_ranges.emplace(off, len);
+    c->free_by_len.emplace(len, off);
+}
+
+void range_erase(lodgs_cache *c, std::map<uint64_t, uint64_t>::iterator it) {
+    c->free_by_len.erase({it->second, it->first});
+    c->free_ranges.erase(it);
+}
+
 void range_free(lodgs_cache *c, uint64_t off, uint64_t len) {
-    auto it = c->free_ranges.emplace(off, len).first;
-    if (it != c->free_ranges.begin()) {                       // merge with the previous range
-        auto p = std::prev(it);
-        if (p->first + p->second == it->first) { p->second += it->second; c->free_ranges.erase(it); it = p; }
+    auto n = c->free_ranges.lower_bound(off);
+    if (n != c->free_ranges.begin()) {                       // merge with the previous range
+        auto p = std::prev(n);
+        if (p->first + p->second == off) {
+            off = p->first;
+            len += p->second;
+            range_erase(c, p);
+        }
     }
-    auto n = std::next(it);
-    if (n != c->free_ranges.end() && it->first + it->second == n->first) {
-        it->second += n->second;
-        c->free_ranges.erase(n);
+    if (n != c->free_ranges.end() && off + len == n->first) { // and with the next one
+        len += n->second;
+        range_erase(c, n);
     }
+    range_put(c, off, len);
 }
 
 bool range_alloc(lodgs_cache *c, uint64_t len, uint64_t *off) {
-    for (auto it = c->free_ranges.begin(); it != c->free_ranges.end(); ++it)
-        if (it->second >= len) {                              // first fit
-            *off = it->first;
-            uint64_t rest = it->second - len, at = it->first + len;
-            c->free_ranges.erase(it);
-            if (rest) c->free_ranges.emplace(at, rest);
-            return true;
-        }
-    return false;
+    auto b = c->free_by_len.lower_bound({len, 0});           // best fit: the shortest range that holds len
+    if (b == c->free_by_len.end()) return false;
+    const uint64_t l = b->first, o = b->second;
+    range_erase(c, c->free_ranges.find(o));
+    if (l > len) range_put(c, o + len, l - len);
+    *off = o;
+    return true;
 }
 
 void add_span(std::vector<Piece> &v, const void *src, void *dst, uint64_t bytes, bool word) {
@@ -227,8 +243,8 @@ bool range_take_at(lodgs_cache *c, uint64_t at, uint64_t len) {
     auto it = c->free_ranges.find(at);
     if (it == c->free_ranges.end() || it->second < len) return false;
     const uint64_t rest = it->second - len;
-    c->free_ranges.erase(it);
-    if (rest) c->free_ranges.emplace(at + len, rest);
+    range_erase(c, it);
+    if (rest) range_put(c, at + len, rest);
     return true;
 }
 
@@ -293,7 +309,7 @@ int lodgs_cache_create(lodgs_scene *sc, const lodgs_cache_params *p, lodgs_cache
     e = cudaMemcpy(c->spt_base.data(), sc->d_spt_base, (S + 1) * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cache_create: SPT bases"));
     c->entry.resize(S);
-    c->free_ranges.emplace(0, c->slab_records);
+    range_put(c, 0, c->slab_records);
     if ((e = cudaHostGetDevicePointer((void **)&c->hd_rows, c->h_rows, 0)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->pieces_done, cudaEventDisableTiming)) != cudaSuccess)
         return fail(cuda_fail(e, "cache_create: device address of the host records"));
@@ -426,7 +442,8 @@ int lodgs_cache_flush(lodgs_cache *c) {
     for (Entry &e : c->entry) e.valid = false;
     c->lru.clear();
     c->free_ranges.clear();
-    c->free_ranges.emplace(0, c->slab_records);
+    c->free_by_len.clear();
+    range_put(c, 0, c->slab_records);
     c->cached_records = 0;
     c->cached_spts = 0;
     return LODGS_OK;
