@@ -158,6 +158,8 @@ __global__ void __launch_bounds__(ST_THREADS) k_radix_downsweep(
 constexpr int SC_THREADS = 512;
 constexpr int SC_ITEMS = 8;
 constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+// scans of at most this many values run in one block (one launch instead of two)
+constexpr uint32_t SCAN_ONE_BLOCK = 16384;
 
 __device__ __forceinline__ void scan_chunk(uint32_t n, uint32_t &begin, uint32_t &end) {
     uint32_t G = gridDim.x;
@@ -290,7 +292,12 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
 
 int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n, uint32_t *block_sums,
                    uint32_t *d_total, cudaStream_t st, const uint32_t *idx) {
-    (void)max_n;
+    if (max_n <= SCAN_ONE_BLOCK) {                 // short scans: one block, no block sums
+        k_scan_down<<<1, SC_THREADS, 0, st>>>(in, idx, out, d_n, block_sums, d_total);
+        count_launches(1);
+        LODGS_CUDA(cudaGetLastError());
+        return LODGS_OK;
+    }
     k_scan_reduce<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, idx, d_n, block_sums);
     count_launches(1);
     k_scan_down<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, idx, out, d_n, block_sums, d_total);
