@@ -704,12 +704,14 @@ def run_out_of_core(args) -> dict:
             it(v)
         torch.cuda.synchronize()
         tot = {"bytes_streamed": 0, "bytes_written_back": 0, "evictions": 0}
+        wb0 = tc.written_bytes()
         t0 = time.perf_counter()
         for v in order[8:]:
             st = it(v)
             for k in tot:
                 tot[k] += st[k]
         max_cut = max(ft.stats()["n_selected"], 0)
+        wb1 = tc.written_bytes()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         t1 = time.perf_counter()
@@ -719,7 +721,8 @@ def run_out_of_core(args) -> dict:
         tc.close()
         return {"iterations": iters, "iters_per_s": round(iters / dt, 1), "ms_per_iter": round(1e3 * dt / iters, 3),
                 "bytes_streamed_per_iter": int(tot["bytes_streamed"] / iters),
-                "bytes_written_back_per_iter": int(tot["bytes_written_back"] / iters),
+                "bytes_written_back_per_iter": int((wb1 - wb0) / iters),
+                "trained_prefix_bytes_evicted_per_iter": int(tot["bytes_written_back"] / iters),
                 "evictions": tot["evictions"], "final_writeback_ms": round(1e3 * wb, 1), "last_cut": max_cut,
                 "cache_gib": gib}
 

@@ -268,7 +268,9 @@ typedef struct {
     int64_t bytes_streamed;  /* host-to-device bytes issued for this view */
     int64_t evictions;       /* cached SPTs evicted (least recently used) for this view */
     int64_t cached_spts, cached_records;  /* cache contents after this view */
-    int64_t bytes_written_back;  /* device-to-host bytes of evicted trained prefixes (training caches) */
+    int64_t bytes_written_back;  /* training caches: bytes of the trained SPT prefixes this view evicted; an
+                                    upper bound, only rows trained since their load are copied
+                                    (lodgs_cache_written_bytes) */
 } lodgs_stream_stats;
 
 /* Create the cache: copies the scene's records to pinned host memory (the
@@ -294,9 +296,11 @@ int lodgs_cache_flush(lodgs_cache *cache);
  * and the upper rows as trained.  Asynchronous on `stream`; the next
  * lodgs_stream_nodes orders its write-backs after it.  LODGS_E_STATE for a
  * cache created without `train`.
- * A trained SPT prefix is copied back to host memory (records, m, v, step
- * counts) when it is evicted, on the copy stream, ahead of any load into its
- * range.
+ * The rows of a trained SPT prefix that Adam updated since the prefix was loaded
+ * are copied back to host memory (records, m, v, step counts) when it is
+ * evicted, on the copy stream, ahead of any load into its range.
+ * lodgs_cache_written_bytes: the bytes write-backs have copied to host memory
+ * since the cache was created (synchronises the device).
  * lodgs_cache_writeback: copies every trained SPT prefix and the upper rows
  * back to host memory on `stream` (the cache keeps them); the host arrays are
  * current once `stream` has completed.
@@ -308,6 +312,7 @@ int lodgs_cache_adam_step(lodgs_cache *cache, lodgs_frame *frame, const float *g
                           const float *lr, float b1, float b2, float eps, void *stream);
 int lodgs_cache_writeback(lodgs_cache *cache, void *stream);
 int lodgs_cache_host_state(lodgs_cache *cache, float **h_rows, float **h_m, float **h_v, uint32_t **h_t);
+int lodgs_cache_written_bytes(lodgs_cache *cache, int64_t *bytes);
 /* Device records to pass as `rows` to lodgs_render / lodgs_render_backward for
  * frames selected with lodgs_stream_nodes (upper rows, then the slab). */
 int lodgs_cache_records(lodgs_cache *cache, float **d_records);

@@ -95,6 +95,7 @@ _SIGS = {
     "lodgs_cache_flush": (C.c_int, [_P]),
     "lodgs_cache_adam_step": (C.c_int, [_P, _P, _P, C.c_int64, _P, C.c_float, C.c_float, C.c_float, _P]),
     "lodgs_cache_writeback": (C.c_int, [_P, _P]),
+    "lodgs_cache_written_bytes": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "lodgs_cache_host_state": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P)]),
     "lodgs_stream_nodes": (C.c_int, [_P, _P, C.POINTER(Camera), _P, _P, _P, C.POINTER(StreamStats)]),
     "lodgs_render": (C.c_int, [_P, _P, _P, _P, _P, _P]),

@@ -311,6 +311,13 @@ class Cache:
                                           lrv.ctypes.data_as(C.c_void_p),
                                           C.c_float(b1), C.c_float(b2), C.c_float(eps), _stream_ptr(stream)))
 
+    def written_bytes(self) -> int:
+        """Bytes the write-backs have copied to host memory since creation (only
+        rows trained since their load are copied)."""
+        b = C.c_int64()
+        check(lib().lodgs_cache_written_bytes(self._h, C.byref(b)))
+        return b.value
+
     def writeback(self, stream=None) -> None:
         """Copy every trained row (records and Adam state) back to host memory."""
         check(lib().lodgs_cache_writeback(self._h, _stream_ptr(stream)))

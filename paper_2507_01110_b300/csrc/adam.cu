@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(AB) k_adam(float4 *__restrict__ params, float4
                                              float4 *__restrict__ v, uint32_t *__restrict__ t,
                                              const uint32_t *__restrict__ rows, const float4 *__restrict__ grads,
                                              const uint32_t *__restrict__ d_n, uint32_t n_host, int quads, int used,
-                                             ColumnRates rates, float b1, float b2, float eps) {
+                                             ColumnRates rates, float b1, float b2, float eps,
+                                             uint32_t *__restrict__ dirty) {
     const uint32_t n = d_n ? min(*d_n, n_host) : n_host;    // never past the caller's max_n rows
     const float omb1 = 1.0f - b1, omb2 = 1.0f - b2;
     const int lane = threadIdx.x & 31;
@@ -59,7 +60,10 @@ __global__ void __launch_bounds__(AB) k_adam(float4 *__restrict__ params, float4
         }
         __syncwarp();                                        // every quarter has read t[r]
         if (!act) continue;
-        if (q == 0) t[r] = step;
+        if (q == 0) {
+            t[r] = step;
+            if (dirty) dirty[r] = 1u;                // trained since it was loaded (cache slabs)
+        }
         // 1 - b^t as -expm1(t log1p(-(1 - b))): 1 - b is exact in float32 and nothing cancels
         const float bc1 = -expm1f((float)step * log1pf(-omb1)), bc2 = -expm1f((float)step * log1pf(-omb2));
         float *mp = &mm.x, *vp = &vv.x, *pq = &pp.x;
@@ -128,7 +132,7 @@ extern "C" int lodgs_gather_rows(const void *src, int64_t n_src, void *dst, cons
 namespace lodgs {
 int launch_adam(const lodgs_scene *sc, float *params, float *m, float *v, uint32_t *t, const uint32_t *rows,
                 const float *grads, const uint32_t *d_n, int64_t max_n, const float *lr, float b1, float b2,
-                float eps, cudaStream_t st) {
+                float eps, cudaStream_t st, uint32_t *dirty) {
     if (!sc || !params || !m || !v || !t || !rows || !grads || !lr || max_n < 0) {
         set_error("adam_step: NULL argument or negative count");
         return LODGS_E_INVALID;
@@ -151,7 +155,7 @@ int launch_adam(const lodgs_scene *sc, float *params, float *m, float *v, uint32
     const int64_t blocks = std::min<int64_t>((warps + AB / 32 - 1) / (AB / 32), 148 * 64);
     k_adam<<<(unsigned)std::max<int64_t>(blocks, 1), AB, 0, st>>>(
         reinterpret_cast<float4 *>(params), reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), t, rows,
-        reinterpret_cast<const float4 *>(grads), d_n, (uint32_t)max_n, quads, used, rates, b1, b2, eps);
+        reinterpret_cast<const float4 *>(grads), d_n, (uint32_t)max_n, quads, used, rates, b1, b2, eps, dirty);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;

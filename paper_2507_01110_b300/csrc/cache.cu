@@ -27,10 +27,11 @@
 // memory beside the records): a training cache mirrors the record slab with
 // slabs of the Adam moments and step counts.  A load streams the prefix of all
 // four arrays; a sparse Adam step updates the view's cached rows in place and
-// marks the view's SPTs dirty; evicting a dirty SPT copies its prefix of the
-// four arrays back to host memory on the copy stream, ahead of any load that
-// reuses the range (same stream, in order).  Upper rows stay resident and are
-// written back by lodgs_cache_writeback and lodgs_cache_flush.
+// flags each row it trained (and the view's SPTs); evicting a trained SPT
+// copies its flagged rows of the four arrays back to host memory on the copy
+// stream, ahead of any load that reuses the range (same stream, in order).
+// Upper rows stay resident and are written back by lodgs_cache_writeback and
+// lodgs_cache_flush.
 #include <string.h>
 
 #include <list>
@@ -85,10 +86,47 @@ __global__ void __launch_bounds__(PIECE_THREADS) k_copy_pieces(const Piece *__re
     }
 }
 
-// copy phases of one batch, issued in this order: write-backs read slab ranges
-// that moves and loads of the same batch may overwrite, and moves read ranges
-// that are freed only after the batch
-enum : int { PH_TO_HOST = 0, PH_MOVE = 1, PH_LOAD = 2, PH_COUNT = 3 };
+// Write-back of a trained SPT prefix (or of the upper rows): `n` slots from
+// `slot` on, host rows from `host_row` on.  Only slots whose dirty flag the
+// Adam step set are copied (record, m, v, step count) and their flags cleared;
+// one warp per slot.  Bytes copied are added to *written.
+struct RowSpan {
+    uint64_t slot, host_row;
+    uint32_t n, pad;
+};
+constexpr uint32_t SPAN_ROWS = 256;
+
+__global__ void __launch_bounds__(PIECE_THREADS) k_writeback_rows(
+    const RowSpan *__restrict__ spans, int quads, const uint4 *__restrict__ rec, const uint4 *__restrict__ m,
+    const uint4 *__restrict__ v, const uint32_t *__restrict__ t, uint4 *__restrict__ h_rec, uint4 *__restrict__ h_m,
+    uint4 *__restrict__ h_v, uint32_t *__restrict__ h_t, uint32_t *__restrict__ dirty,
+    unsigned long long *__restrict__ written) {
+    const RowSpan sp = spans[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t rows = 0;
+    for (uint32_t r = warp; r < sp.n; r += PIECE_THREADS / 32) {
+        const uint64_t s = sp.slot + r, h = sp.host_row + r;
+        if (!dirty[s]) continue;                                  // warp-uniform
+        for (int k = lane; k < 3 * quads; k += 32) {
+            const int a = k / quads, o = k - a * quads;
+            const uint4 *src = a == 0 ? rec : (a == 1 ? m : v);
+            uint4 *dst = a == 0 ? h_rec : (a == 1 ? h_m : h_v);
+            dst[h * quads + o] = src[s * quads + o];
+        }
+        if (lane == 0) {
+            h_t[h] = t[s];
+            dirty[s] = 0u;
+            ++rows;
+        }
+    }
+    if (lane == 0 && rows)
+        atomicAdd(written, (unsigned long long)rows * (3ull * quads * 16ull + 4ull));
+}
+
+// copy phases of one batch, issued after its masked write-backs (which read
+// slab ranges that moves and loads of the same batch may overwrite): moves,
+// whose source ranges are freed only after the batch, then loads
+enum : int { PH_MOVE = 0, PH_LOAD = 1, PH_COUNT = 2 };
 
 }  // namespace
 
@@ -112,6 +150,12 @@ struct lodgs_cache {
     Piece *h_pieces = nullptr, *d_pieces = nullptr;
     size_t pieces_cap = 0;
     cudaEvent_t pieces_done = nullptr;  // after the last batch's kernels (staging reusable)
+    // training: per-slot trained flags (set by the Adam step), masked write-backs
+    uint32_t *d_dirty = nullptr, *d_zeros = nullptr;
+    unsigned long long *d_written = nullptr;      // bytes the write-backs copied
+    std::vector<RowSpan> wb;
+    RowSpan *h_spans = nullptr, *d_spans = nullptr;
+    size_t spans_cap = 0;
     std::vector<uint32_t> spt_base;   // host copy (n_spt + 1)
     std::vector<Entry> entry;
     std::list<uint32_t> lru;          // front = most recently used
@@ -187,8 +231,20 @@ void add_rows(lodgs_cache *c, int phase, uint64_t dev, uint64_t host, uint64_t n
     if (!c->train) return;
     span(c->d_m, c->hd_m);
     span(c->d_v, c->hd_v);
-    if (to_host) add_span(v, c->d_t + dev, c->hd_t + host, n * 4, true);
-    else add_span(v, c->hd_t + host, c->d_t + dev, n * 4, true);
+    if (to_host) {
+        add_span(v, c->d_t + dev, c->hd_t + host, n * 4, true);
+    } else {
+        add_span(v, c->hd_t + host, c->d_t + dev, n * 4, true);
+        for (uint64_t o = 0; o < n * 4; o += PIECE_BYTES)   // freshly loaded: not trained yet
+            v.push_back({c->d_zeros, reinterpret_cast<char *>(c->d_dirty + dev) + o,
+                         (uint32_t)(std::min<uint64_t>(PIECE_BYTES, n * 4 - o) / 4), 1u});
+    }
+}
+
+// masked write-back of n slots from `slot` on to host rows from `host` on
+void add_wb(lodgs_cache *c, uint64_t slot, uint64_t host, uint64_t n) {
+    for (uint64_t o = 0; o < n; o += SPAN_ROWS)
+        c->wb.push_back({slot + o, host + o, (uint32_t)std::min<uint64_t>(SPAN_ROWS, n - o), 0u});
 }
 
 // n slab records (and their Adam state) from slot src to slot dst
@@ -200,14 +256,44 @@ void add_move(lodgs_cache *c, uint64_t src, uint64_t dst, uint64_t n) {
     add_span(v, c->d_m + src * w, c->d_m + dst * w, bytes, false);
     add_span(v, c->d_v + src * w, c->d_v + dst * w, bytes, false);
     add_span(v, c->d_t + src, c->d_t + dst, n * 4, true);
+    add_span(v, c->d_dirty + src, c->d_dirty + dst, n * 4, true);
 }
 
 // issue the batch on `st`: one descriptor upload, one launch per non-empty phase
 int issue_pieces(lodgs_cache *c, cudaStream_t st) {
     size_t total = 0;
     for (auto &v : c->pend) total += v.size();
-    if (!total) return LODGS_OK;
+    if (!total && c->wb.empty()) return LODGS_OK;
     LODGS_CUDA(cudaEventSynchronize(c->pieces_done));       // the staging of the last batch is free
+    if (!c->wb.empty()) {                                    // masked write-backs go first
+        const size_t n = c->wb.size();
+        if (n > c->spans_cap) {
+            cudaFreeHost(c->h_spans);
+            cudaFree(c->d_spans);
+            c->h_spans = nullptr;
+            c->d_spans = nullptr;
+            c->spans_cap = 0;
+            const size_t cap = std::max<size_t>(n + n / 2, 1024);
+            LODGS_CUDA(cudaMallocHost((void **)&c->h_spans, cap * sizeof(RowSpan)));
+            LODGS_CUDA(cudaMalloc((void **)&c->d_spans, cap * sizeof(RowSpan)));
+            c->spans_cap = cap;
+        }
+        memcpy(c->h_spans, c->wb.data(), n * sizeof(RowSpan));
+        LODGS_CUDA(cudaMemcpyAsync(c->d_spans, c->h_spans, n * sizeof(RowSpan), cudaMemcpyHostToDevice, st));
+        const int quads = c->scene->stride / 4;
+        k_writeback_rows<<<(unsigned)n, PIECE_THREADS, 0, st>>>(
+            c->d_spans, quads, reinterpret_cast<const uint4 *>(c->d_records), reinterpret_cast<const uint4 *>(c->d_m),
+            reinterpret_cast<const uint4 *>(c->d_v), c->d_t, reinterpret_cast<uint4 *>(c->hd_rows),
+            reinterpret_cast<uint4 *>(c->hd_m), reinterpret_cast<uint4 *>(c->hd_v), c->hd_t, c->d_dirty,
+            c->d_written);
+        count_launches(1);
+        c->wb.clear();
+    }
+    if (!total) {
+        LODGS_CUDA(cudaGetLastError());
+        LODGS_CUDA(cudaEventRecord(c->pieces_done, st));
+        return LODGS_OK;
+    }
     if (total > c->pieces_cap) {
         cudaFreeHost(c->h_pieces);
         cudaFree(c->d_pieces);
@@ -254,7 +340,7 @@ void evict(lodgs_cache *c, uint32_t j, int64_t *written) {
     Entry &e = c->entry[j];
     if (e.dirty) {
         const uint64_t U = (uint64_t)c->scene->n_upper_rows;
-        add_rows(c, PH_TO_HOST, U + e.off, c->spt_base[j], e.h, true);
+        add_wb(c, U + e.off, c->spt_base[j], e.h);
         if (written) *written += (int64_t)e.h * c->scene->stride * 4 * (c->train ? 3 : 1) + (c->train ? e.h * 4 : 0);
         e.dirty = false;
     }
@@ -345,6 +431,13 @@ int lodgs_cache_create(lodgs_scene *sc, const lodgs_cache_params *p, lodgs_cache
             (e = cudaMemset(c->d_t, 0, (size_t)U * 4)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&c->adam_done, cudaEventDisableTiming)) != cudaSuccess)
             return fail(cuda_fail(e, "cache_create: upper Adam state"));
+        if ((e = cudaMalloc((void **)&c->d_dirty, std::max<size_t>(slots, 1) * 4)) != cudaSuccess ||
+            (e = cudaMemset(c->d_dirty, 0, std::max<size_t>(slots, 1) * 4)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c->d_zeros, PIECE_BYTES)) != cudaSuccess ||
+            (e = cudaMemset(c->d_zeros, 0, PIECE_BYTES)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c->d_written, 8)) != cudaSuccess ||
+            (e = cudaMemset(c->d_written, 0, 8)) != cudaSuccess)
+            return fail(cuda_fail(e, "cache_create: trained-row flags"));
     }
     if (p->release_scene_rows) {
         cudaFree(sc->d_rows);
@@ -368,6 +461,11 @@ void lodgs_cache_free(lodgs_cache *c) {
     if (c->pieces_done) cudaEventDestroy(c->pieces_done);
     cudaFreeHost(c->h_pieces);
     cudaFree(c->d_pieces);
+    cudaFreeHost(c->h_spans);
+    cudaFree(c->d_spans);
+    cudaFree(c->d_dirty);
+    cudaFree(c->d_zeros);
+    cudaFree(c->d_written);
     delete c;
 }
 
@@ -381,11 +479,11 @@ int writeback_all(lodgs_cache *c, cudaStream_t st) {
     for (uint32_t j = 0; j < (uint32_t)c->entry.size(); ++j) {
         Entry &e = c->entry[j];
         if (!e.valid || !e.dirty) continue;
-        add_rows(c, PH_TO_HOST, U + e.off, c->spt_base[j], e.h, true);
+        add_wb(c, U + e.off, c->spt_base[j], e.h);
         e.dirty = false;
     }
     if (U && c->upper_dirty) {
-        add_rows(c, PH_TO_HOST, 0, 0, U, true);
+        add_wb(c, 0, 0, U);
         c->upper_dirty = false;
     }
     (void)M;
@@ -396,6 +494,17 @@ int writeback_all(lodgs_cache *c, cudaStream_t st) {
 int lodgs_cache_writeback(lodgs_cache *c, void *stream) {
     if (!c) { set_error("cache_writeback: NULL cache"); return LODGS_E_INVALID; }
     return writeback_all(c, (cudaStream_t)stream);
+}
+
+int lodgs_cache_written_bytes(lodgs_cache *c, int64_t *bytes) {
+    if (!c || !bytes) { set_error("cache_written_bytes: NULL argument"); return LODGS_E_INVALID; }
+    *bytes = 0;
+    if (!c->train) return LODGS_OK;
+    LODGS_CUDA(cudaDeviceSynchronize());
+    unsigned long long b = 0;
+    LODGS_CUDA(cudaMemcpy(&b, c->d_written, 8, cudaMemcpyDeviceToHost));
+    *bytes = (int64_t)b;
+    return LODGS_OK;
 }
 
 int lodgs_cache_host_state(lodgs_cache *c, float **h_rows, float **h_m, float **h_v, uint32_t **h_t) {
@@ -423,7 +532,7 @@ int lodgs_cache_adam_step(lodgs_cache *c, lodgs_frame *fr, const float *grads, i
     const FrameBufs &f = fr->f;
     const int64_t max_n = std::min<int64_t>((int64_t)f.cap_sel, grad_capacity);
     if (int rc = launch_adam(c->scene, c->d_records, c->d_m, c->d_v, c->d_t, f.sel_src, grads, f.cnt + C_NSEL_EFF,
-                             max_n, lr, b1, b2, eps, st))
+                             max_n, lr, b1, b2, eps, st, c->d_dirty))
         return rc;
     LODGS_CUDA(cudaEventRecord(c->adam_done, st));
     for (Entry &e : c->entry)

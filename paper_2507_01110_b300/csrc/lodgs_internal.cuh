@@ -183,10 +183,10 @@ int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, i
 // 0 if `fr` belongs to `sc` and was created for its current layout, else an
 // error code (with the message set, prefixed by `who`)
 int check_frame(const lodgs_scene *sc, const lodgs_frame *fr, const char *who);
-// sparse Adam over `rows` of params/m/v/t (lodgs_adam_step's contract)
+// sparse Adam over `rows` of params/m/v/t (lodgs_adam_step's contract); dirty[row] = 1 if given
 int launch_adam(const lodgs_scene *sc, float *params, float *m, float *v, uint32_t *t, const uint32_t *rows,
                 const float *grads, const uint32_t *d_n, int64_t max_n, const float *lr, float b1, float b2,
-                float eps, cudaStream_t st);
+                float eps, cudaStream_t st, uint32_t *dirty = nullptr);
 
 // radix sort and scans (sort.cu).  All take element counts from device memory so
 // that no host synchronisation is needed between stages.
