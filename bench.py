@@ -173,6 +173,25 @@ def stage_bytes(stage: str, st: dict, record_bytes: int, n_upper: int, tile_pass
 # ---------------------------------------------------------------------------
 # CUDA arm
 # ---------------------------------------------------------------------------
+def shard_views(n_views: int, rank: int, world: int) -> list:
+    """The views rank `rank` of `world` renders: every world-th view from its
+    rank on (views are independent units: no exchange between ranks).  With
+    more ranks than views a rank repeats one view."""
+    return [v for v in range(n_views) if v % world == rank] or [rank % n_views]
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The maximum of x over the ranks (the slowest rank's time), through the
+    process group's backend (device tensors for NCCL, host tensors for gloo)."""
+    if world == 1:
+        return x
+    import torch
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_lodgs(args, rank: int, world: int):
     import torch
 
@@ -192,7 +211,7 @@ def run_lodgs(args, rank: int, world: int):
     del leaves_host
     H, W = cams[0].height, cams[0].width
     # views of this rank (independent units: no exchange between ranks)
-    my_views = [v for v in range(nv) if v % world == rank] or [rank % nv]
+    my_views = shard_views(nv, rank, world)
     frames = {v: api.Frame(scene) for v in my_views}     # profiling off: nothing extra in the timed graphs
     gen = torch.Generator().manual_seed(1234)
     targets_h = {v: torch.rand((H, W, 3), generator=gen).pin_memory() for v in my_views}
@@ -398,13 +417,8 @@ def run_lodgs(args, rank: int, world: int):
     if world > 1:
         torch.distributed.barrier()
 
-    # max over ranks
     def maxr(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, world)
 
     ms, fwd_ms, e2e_ms, e2e_wall = maxr(ms), maxr(fwd_ms), maxr(e2e_ms), maxr(max(e2e_wall * 1e3, e2e_ms)) / 1e3
     train_ms = maxr(train_ms)
