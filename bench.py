@@ -577,11 +577,15 @@ def run_serving(args) -> dict:
     torch.cuda.empty_cache()
     t_build = time.perf_counter() - t0
     rate = 200.0
+    # workspaces sized before serving on the most demanding cameras of the pool
+    # (most pixels per squared LoD threshold) plus a sample of the rest
+    worst = sorted(cams, key=lambda c: -(c.width * c.height) / (c.tau * c.tau))[:16]
+    warm_set = worst + cams[:16]
     mix = serving.RenderServer(scene, n_slots=8, mem_budget_bytes=8 << 30)
-    mix.warm(cams[:32])
+    mix.warm(warm_set)
     r_mix = mix.run(serving.poisson_requests(cams, rate, args.serving_requests, seed=4))
     fifo = serving.RenderServer(scene, n_slots=1, mem_budget_bytes=8 << 30)
-    fifo.warm(cams[:32])
+    fifo.warm(warm_set)
     r_fifo = fifo.run(serving.poisson_requests(cams, rate, args.serving_requests, seed=4))
     return {"workload": f"{args.serving_leaves:,}-leaf SH3 city (2 km), Poisson {rate:.0f} req/s, "
                         f"{args.serving_requests} requests, resolution in {{360p,720p,1080p,2160p}}, "
