@@ -197,8 +197,9 @@ struct SortWork {
 #ifndef LODGS_SORT_GRID
 #define LODGS_SORT_GRID 296
 #endif
-constexpr int SORT_GRID = LODGS_SORT_GRID;   // radix sort blocks (2 per SM on 148 SMs)
-constexpr int SORT_HIST = 256 * (SORT_GRID + 1);   // histogram table + digit totals
+constexpr int SORT_GRID = LODGS_SORT_GRID;   // radix sort blocks for short sorts (2 per SM on 148 SMs)
+constexpr int SORT_GRID_MAX = 148 * 8;       // ... growing with the element count up to 8 per SM
+constexpr int SORT_HIST = 256 * (SORT_GRID_MAX + 1);   // histogram table + digit totals
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                      const uint32_t *d_n, uint32_t max_n, int begin_bit, int end_bit, uint32_t *hist,
                      cudaStream_t st, bool *result_in_alt);

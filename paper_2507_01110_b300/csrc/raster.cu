@@ -65,65 +65,6 @@ __device__ __forceinline__ bool tile_keep(float u, float v, float A, float B, fl
     return best >= -4.51f;
 }
 
-// ---- global ordering (large frames): depth sort, emission, tile sort ----
-// One thread per rectangle pair: pair p belongs to the last depth rank r with
-// pair_off[r] <= p (binary search) and is the k-th tile of its rectangle in
-// row-major order.  Pairs whose tile the support ellipse cannot reach get the
-// key n_tiles, which the tile sort moves behind every real tile.
-__global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restrict__ rect,
-                       const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
-                       const uint32_t *__restrict__ pair_off, uint32_t *__restrict__ cnt, uint64_t cap_pairs,
-                       int TX, uint32_t n_tiles, uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
-    // pairs beyond the workspace (or an earlier overflow) are not emitted: capacity error
-    uint32_t P = cnt[C_NPAIR];
-    const bool over = P > cap_pairs || (cnt[C_STATUS] & ST_CAPACITY) ||
-                      *reinterpret_cast<const unsigned long long *>(cnt + C_NPAIR64) > 0xffffffffull;
-    if (over) P = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        cnt[C_NPAIR_EFF] = P;
-        cnt[C_NKEPT_WANT] = cnt[C_NPAIR];           // all rectangle pairs are stored on this path
-        if (over) atomicOr(&cnt[C_STATUS], ST_CAPACITY);
-    }
-    const uint32_t n = cnt[C_NSEL_EFF];
-    for (uint32_t p = blockIdx.x * RB + threadIdx.x; p < P; p += gridDim.x * RB) {
-        uint32_t a = 0, b = n;
-        while (b - a > 1) {
-            uint32_t m = (a + b) >> 1;
-            if (pair_off[m] <= p) a = m; else b = m;
-        }
-        const uint32_t g = order[a];
-        const uint2 rc = rect[g];
-        const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
-        const uint32_t w = x1 - x0, k = p - pair_off[a];
-        const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-        const float4 sa = sp_a[g];
-        const float nhc = sp_b[g].x;
-        const bool keep = tile_keep(sa.x, sa.y, -2.0f * sa.z, -sa.w, -2.0f * nhc, tx, ty);
-        pkey[p] = keep ? ty * (uint32_t)TX + tx : n_tiles;
-        pval[p] = g;
-    }
-}
-
-__global__ void k_ranges(const uint32_t *__restrict__ pkey, uint32_t *__restrict__ cnt, uint32_t n_tiles,
-                         uint2 *__restrict__ ranges) {
-    uint32_t n = cnt[C_NPAIR_EFF];
-    for (uint32_t p = blockIdx.x * RB + threadIdx.x; p < n; p += gridDim.x * RB) {
-        uint32_t t = pkey[p];
-        if (t >= n_tiles) continue;                       // dropped pairs sort behind every tile
-        if (p == 0 || pkey[p - 1] != t) ranges[t].x = p;
-        if (p + 1 == n || pkey[p + 1] != t) {
-            ranges[t].y = p + 1;
-            if (p + 1 == n || pkey[p + 1] >= n_tiles) cnt[C_NKEPT] = p + 1;
-        }
-    }
-}
-
-// ---- per-tile ordering ----
-// Rectangle pairs are enumerated flat: pair p belongs to the last selected
-// Gaussian g with pair_off[g] <= p (binary search over the scan of the
-// rectangle areas, selection order) and is the k-th tile of its rectangle in
-// row-major order.  Returns the tile of the pair, or -1 when the tile support
-// test drops it.
 // Owner of pair p = p0 + lane for a warp's 32 consecutive pair indices: the
 // largest selected index g with pair_off[g] <= p (pair_off is the exclusive
 // scan of the rectangle areas, pair_off[n] = P implied).  One 32-ary search for
@@ -165,6 +106,65 @@ __device__ __forceinline__ uint32_t warp_pair_owner(uint32_t p0, uint32_t p, uin
     return g;
 }
 
+// ---- global ordering (large frames): depth sort, emission, tile sort ----
+// One thread per rectangle pair: pair p belongs to the last depth rank r with
+// pair_off[r] <= p (found per warp, warp_pair_owner) and is the k-th tile of
+// its rectangle in row-major order.  Pairs whose tile the support ellipse cannot reach get the
+// key n_tiles, which the tile sort moves behind every real tile.
+__global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restrict__ rect,
+                       const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
+                       const uint32_t *__restrict__ pair_off, uint32_t *__restrict__ cnt, uint64_t cap_pairs,
+                       int TX, uint32_t n_tiles, uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    // pairs beyond the workspace (or an earlier overflow) are not emitted: capacity error
+    uint32_t P = cnt[C_NPAIR];
+    const bool over = P > cap_pairs || (cnt[C_STATUS] & ST_CAPACITY) ||
+                      *reinterpret_cast<const unsigned long long *>(cnt + C_NPAIR64) > 0xffffffffull;
+    if (over) P = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cnt[C_NPAIR_EFF] = P;
+        cnt[C_NKEPT_WANT] = cnt[C_NPAIR];           // all rectangle pairs are stored on this path
+        if (over) atomicOr(&cnt[C_STATUS], ST_CAPACITY);
+    }
+    const uint32_t n = cnt[C_NSEL_EFF];
+    const int lane = threadIdx.x & 31;
+    // whole warps step together: the owner search is warp-cooperative
+    for (uint32_t p0 = (blockIdx.x * RB + threadIdx.x) & ~31u; p0 < P; p0 += gridDim.x * RB) {
+        const uint32_t p = p0 + lane;
+        const uint32_t a = warp_pair_owner(p0, p, n, pair_off, lane);
+        if (p >= P) continue;
+        const uint32_t g = order[a];
+        const uint2 rc = rect[g];
+        const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+        const uint32_t w = x1 - x0, k = p - pair_off[a];
+        const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+        const float4 sa = sp_a[g];
+        const float nhc = sp_b[g].x;
+        const bool keep = tile_keep(sa.x, sa.y, -2.0f * sa.z, -sa.w, -2.0f * nhc, tx, ty);
+        pkey[p] = keep ? ty * (uint32_t)TX + tx : n_tiles;
+        pval[p] = g;
+    }
+}
+
+__global__ void k_ranges(const uint32_t *__restrict__ pkey, uint32_t *__restrict__ cnt, uint32_t n_tiles,
+                         uint2 *__restrict__ ranges) {
+    uint32_t n = cnt[C_NPAIR_EFF];
+    for (uint32_t p = blockIdx.x * RB + threadIdx.x; p < n; p += gridDim.x * RB) {
+        uint32_t t = pkey[p];
+        if (t >= n_tiles) continue;                       // dropped pairs sort behind every tile
+        if (p == 0 || pkey[p - 1] != t) ranges[t].x = p;
+        if (p + 1 == n || pkey[p + 1] != t) {
+            ranges[t].y = p + 1;
+            if (p + 1 == n || pkey[p + 1] >= n_tiles) cnt[C_NKEPT] = p + 1;
+        }
+    }
+}
+
+// ---- per-tile ordering ----
+// Rectangle pairs are enumerated flat: pair p belongs to the last selected
+// Gaussian g with pair_off[g] <= p (binary search over the scan of the
+// rectangle areas, selection order) and is the k-th tile of its rectangle in
+// row-major order.  Returns the tile of the pair, or -1 when the tile support
+// test drops it.
 // Tile of pair p of Gaussian g (row-major in its rectangle), or -1 when the
 // tile support test drops it.
 __device__ __forceinline__ int64_t pair_tile(uint32_t p, uint32_t g, const uint32_t *__restrict__ pair_off,

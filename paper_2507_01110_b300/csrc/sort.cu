@@ -7,6 +7,8 @@
 // block counts, and a downsweep (which scans the 256 digit totals itself) ranks
 // each tile of its chunk with warp match/ballot ranking and scatters it.  No
 // block waits on another.
+#include <algorithm>
+
 #include "lodgs_internal.cuh"
 
 namespace lodgs {
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_radix_upsweep(const uint32_t *__
 // Per digit d (one warp each): exclusive scan in place of the per-block counts
 // hist[d*G .. d*G+G) and the digit total in totals[d].  All of a digit's counts
 // are loaded before any is written back, so the loads overlap.
-constexpr int DS_CHUNKS = (SORT_GRID + 31) / 32;
+constexpr int DS_CHUNKS = (SORT_GRID_MAX + 31) / 32;
 __global__ void __launch_bounds__(256) k_digit_scan(uint32_t *__restrict__ hist, int G, uint32_t *__restrict__ totals) {
     const int lane = threadIdx.x & 31;
     const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -269,6 +271,10 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
         *result_in_alt = false;
         return LODGS_OK;
     }
+    // blocks: a fixed count for short sorts (the pass is latency-bound there);
+    // long sorts get about 16 tiles per block, up to 8 blocks per SM
+    const int G = (int)std::min<uint64_t>(SORT_GRID_MAX,
+                                          std::max<uint64_t>(SORT_GRID, (uint64_t)max_n / (ST_TILE * 16)));
     for (int shift = begin_bit; shift < end_bit; shift += RADIX_BITS) {
         int bits = end_bit - shift < RADIX_BITS ? end_bit - shift : RADIX_BITS;
         uint32_t mask = (1u << bits) - 1u;
@@ -276,12 +282,12 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
         const uint32_t *vi = alt ? vals_alt : vals;
         uint32_t *ko = alt ? keys : keys_alt;
         uint32_t *vo = alt ? vals : vals_alt;
-        uint32_t *totals = hist + RADIX * SORT_GRID;
-        k_radix_upsweep<<<SORT_GRID, ST_THREADS, 0, st>>>(ki, d_n, shift, mask, hist);
+        uint32_t *totals = hist + RADIX * G;
+        k_radix_upsweep<<<G, ST_THREADS, 0, st>>>(ki, d_n, shift, mask, hist);
         count_launches(1);
-        k_digit_scan<<<RADIX / 8, 256, 0, st>>>(hist, SORT_GRID, totals);
+        k_digit_scan<<<RADIX / 8, 256, 0, st>>>(hist, G, totals);
         count_launches(1);
-        k_radix_downsweep<<<SORT_GRID, ST_THREADS, 0, st>>>(ki, vi, ko, vo, d_n, shift, mask, hist, totals);
+        k_radix_downsweep<<<G, ST_THREADS, 0, st>>>(ki, vi, ko, vo, d_n, shift, mask, hist, totals);
         count_launches(1);
         alt = !alt;
     }
