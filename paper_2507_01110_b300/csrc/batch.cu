@@ -93,12 +93,12 @@ extern "C" int lodgs_accumulate_grads(lodgs_scene *sc, lodgs_frame *const *frame
     if (T == 0) { LODGS_CUDA(cudaMemsetAsync(d_count, 0, 4, st)); return LODGS_OK; }
     // stream-ordered temporaries
     uint32_t *buf = nullptr;
-    const size_t words = 2 * (size_t)n_views + (size_t)T * 7 + SORT_HIST + SCAN_GRID + 8 + (size_t)(n_views + 1) + 64;
+    const size_t words = 2 * (size_t)n_views + (size_t)T * 7 + SORT_HIST + SCAN_GRID_MAX + 8 + (size_t)(n_views + 1) + 64;
     LODGS_CUDA(cudaMallocAsync((void **)&buf, words * 4, st));
     uint64_t *gptr = reinterpret_cast<uint64_t *>(buf);    // first, so it is 8-byte aligned
     uint32_t *key = buf + 2 * n_views, *val = key + T, *key2 = val + T, *val2 = key2 + T, *flag = val2 + T,
              *pos = flag + T, *run_start = pos + T, *hist = run_start + T + 1, *bsum = hist + SORT_HIST,
-             *dn = bsum + SCAN_GRID, *voff = dn + 8;
+             *dn = bsum + SCAN_GRID_MAX, *voff = dn + 8;
     for (int v = 0; v < n_views; ++v) {
         const uint32_t n = off[v + 1] - off[v];
         if (!n) continue;

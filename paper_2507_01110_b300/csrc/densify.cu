@@ -124,7 +124,7 @@ extern "C" int lodgs_densify_plan(lodgs_scene *sc, const float *rows, const floa
     LODGS_CUDA(s.get(&parent, M)); LODGS_CUDA(s.get(&row_of, M)); LODGS_CUDA(s.get(&is_left, M));
     LODGS_CUDA(s.get(&low, M)); LODGS_CUDA(s.get(&dead, M)); LODGS_CUDA(s.get(&cand, M));
     LODGS_CUDA(s.get(&pos_d, M)); LODGS_CUDA(s.get(&pos_c, M)); LODGS_CUDA(s.get(&tot, 2));
-    LODGS_CUDA(s.get(&d_m, 1)); LODGS_CUDA(s.get(&bsum, 2 * SCAN_GRID)); LODGS_CUDA(s.get(&rows_d, M));
+    LODGS_CUDA(s.get(&d_m, 1)); LODGS_CUDA(s.get(&bsum, 2 * SCAN_GRID_MAX)); LODGS_CUDA(s.get(&rows_d, M));
     LODGS_CUDA(s.get(&rows_c, M)); LODGS_CUDA(s.get(&keys, M)); LODGS_CUDA(s.get(&keys_alt, M));
     LODGS_CUDA(s.get(&vals_alt, M)); LODGS_CUDA(s.get(&hist, SORT_HIST));
     LODGS_CUDA(cudaMemsetAsync(parent, 0xff, M * 4, st));
@@ -139,7 +139,7 @@ extern "C" int lodgs_densify_plan(lodgs_scene *sc, const float *rows, const floa
                                     low, grad_threshold, M, dead, cand);
     count_launches(4);
     if (int rc = scan_exclusive(dead, pos_d, d_m, M32, bsum, tot, st)) return rc;
-    if (int rc = scan_exclusive(cand, pos_c, d_m, M32, bsum + SCAN_GRID, tot + 1, st)) return rc;
+    if (int rc = scan_exclusive(cand, pos_c, d_m, M32, bsum + SCAN_GRID_MAX, tot + 1, st)) return rc;
     k_compact<<<nblk(M), DB, 0, st>>>(dead, pos_d, M, grad_max, rows_d, nullptr);
     k_compact<<<nblk(M), DB, 0, st>>>(cand, pos_c, M, grad_max, rows_c, keys);
     count_launches(2);

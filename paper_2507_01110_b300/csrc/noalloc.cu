@@ -30,6 +30,8 @@ constexpr size_t NA_EMIT_X = NA_EMIT_J + NA_MAX_SPT;          // n_spt query val
 constexpr size_t NA_HIGH = NA_EMIT_X + NA_MAX_SPT;            // n_spt + 1 prefix lengths
 constexpr size_t NA_WORK = NA_HIGH + NA_MAX_SPT + 64;         // n_spt + 1 prefix offsets
 constexpr size_t NA_WORDS = NA_WORK + NA_MAX_SPT + 64;        // ~16 MiB in total
+// the scans of this path cover at most NA_MAX_SPT values, which take the
+// short-scan grid (SCAN_GRID blocks)
 static_assert(SCAN_GRID <= 256, "scan block sums must fit their slot");
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];

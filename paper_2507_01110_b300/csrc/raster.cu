@@ -65,6 +65,16 @@ __device__ __forceinline__ bool tile_keep(float u, float v, float A, float B, fl
     return best >= -4.51f;
 }
 
+// The contiguous run [g0, g1) of 32-pair groups of this warp, out of P pairs
+// split evenly over the grid's warps.
+__device__ __forceinline__ void warp_groups(uint32_t P, uint32_t &g0, uint32_t &g1) {
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5), w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t groups = (P + 31u) / 32u, per = (groups + warps - 1u) / warps;
+    const uint64_t b = (uint64_t)w * per, e = b + per;
+    g0 = b < groups ? (uint32_t)b : groups;
+    g1 = e < groups ? (uint32_t)e : groups;
+}
+
 // Owner of pair p = p0 + lane for a warp's 32 consecutive pair indices: the
 // largest selected index g with pair_off[g] <= p (pair_off is the exclusive
 // scan of the rectangle areas, pair_off[n] = P implied).  One 32-ary search for
@@ -73,8 +83,17 @@ __device__ __forceinline__ bool tile_keep(float u, float v, float A, float B, fl
 // (empty rectangles in between) finishes with its own binary search.  Every
 // lane of the warp must call this.
 __device__ __forceinline__ uint32_t warp_pair_owner(uint32_t p0, uint32_t p, uint32_t n,
-                                                    const uint32_t *__restrict__ pair_off, int lane) {
-    uint32_t a = 0, b = n;                       // pair_off[a] <= p0 < pair_off[b]
+                                                    const uint32_t *__restrict__ pair_off, int lane,
+                                                    uint32_t hint = 0) {
+    // hint: the owner of a pair at or before p0 (0 always qualifies).  When the
+    // 32 offsets from it reach past p0, one coalesced load finds p0's owner.
+    uint32_t a = hint, b = n;                    // pair_off[a] <= p0 < pair_off[b]
+    if (hint > 0) {
+        const uint32_t v = hint + lane < n ? pair_off[hint + lane] : 0xffffffffu;
+        const uint32_t bal = __ballot_sync(0xffffffffu, v <= p0);
+        if (!(bal >> 31 & 1u)) b = hint + (uint32_t)__popc(bal);   // p0's owner is within the window
+        else a = hint + 31;
+    }
     while (b - a > 32) {
         const uint32_t m = a + (uint32_t)(((uint64_t)(b - a) * (uint32_t)(lane + 1)) / 33u);   // a < m < b
         const uint32_t c = __popc(__ballot_sync(0xffffffffu, pair_off[m] <= p0));
@@ -127,10 +146,14 @@ __global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restri
     }
     const uint32_t n = cnt[C_NSEL_EFF];
     const int lane = threadIdx.x & 31;
-    // whole warps step together: the owner search is warp-cooperative
-    for (uint32_t p0 = (blockIdx.x * RB + threadIdx.x) & ~31u; p0 < P; p0 += gridDim.x * RB) {
-        const uint32_t p = p0 + lane;
-        const uint32_t a = warp_pair_owner(p0, p, n, pair_off, lane);
+    // each warp takes a contiguous run of 32-pair groups, carrying the owner
+    // of its last pair into the next group's search
+    uint32_t g0, g1, hint = 0;
+    warp_groups(P, g0, g1);
+    for (uint32_t gi = g0; gi < g1; ++gi) {
+        const uint32_t p0 = gi * 32u, p = p0 + lane;
+        const uint32_t a = warp_pair_owner(p0, p, n, pair_off, lane, hint);
+        hint = __shfl_sync(0xffffffffu, a, 31);
         if (p >= P) continue;
         const uint32_t g = order[a];
         const uint2 rc = rect[g];
@@ -192,10 +215,14 @@ __global__ void __launch_bounds__(RB) k_emit_count(const uint32_t *__restrict__ 
     }
     const uint32_t P = cnt[C_NPAIR], n = cnt[C_NSEL_EFF];
     const int lane = threadIdx.x & 31;
-    // whole warps step together so that the match below sees every lane
-    for (uint32_t p0 = (blockIdx.x * RB + threadIdx.x) & ~31u; p0 < P; p0 += gridDim.x * RB) {
-        const uint32_t p = p0 + lane;
-        const uint32_t g = warp_pair_owner(p0, p, n, pair_off, lane);
+    // whole warps step together so that the match below sees every lane; each
+    // warp takes a contiguous run of 32-pair groups (owner search carried over)
+    uint32_t g0, g1, hint = 0;
+    warp_groups(P, g0, g1);
+    for (uint32_t gi = g0; gi < g1; ++gi) {
+        const uint32_t p0 = gi * 32u, p = p0 + lane;
+        const uint32_t g = warp_pair_owner(p0, p, n, pair_off, lane, hint);
+        hint = __shfl_sync(0xffffffffu, g, 31);
         const int64_t t = p < P ? pair_tile(p, g, pair_off, rect, sp_a, sp_b, TX) : -1;
         const uint32_t key = t < 0 ? 0xffffffffu : (uint32_t)t;
         const uint32_t peers = __match_any_sync(0xffffffffu, key);
@@ -269,9 +296,12 @@ __global__ void __launch_bounds__(RB) k_emit_scatter(const uint32_t *__restrict_
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     const uint32_t P = cnt[C_NPAIR], n = cnt[C_NSEL_EFF];
     const int lane = threadIdx.x & 31;
-    for (uint32_t p0 = (blockIdx.x * RB + threadIdx.x) & ~31u; p0 < P; p0 += gridDim.x * RB) {
-        const uint32_t p = p0 + lane;
-        const uint32_t g = warp_pair_owner(p0, p, n, pair_off, lane);
+    uint32_t g0, g1, hint = 0;
+    warp_groups(P, g0, g1);
+    for (uint32_t gi = g0; gi < g1; ++gi) {
+        const uint32_t p0 = gi * 32u, p = p0 + lane;
+        const uint32_t g = warp_pair_owner(p0, p, n, pair_off, lane, hint);
+        hint = __shfl_sync(0xffffffffu, g, 31);
         const int64_t t = p < P ? pair_tile(p, g, pair_off, rect, sp_a, sp_b, TX) : -1;
         const uint32_t key = t < 0 ? 0xffffffffu : (uint32_t)t;
         const uint32_t peers = __match_any_sync(0xffffffffu, key);

@@ -550,7 +550,7 @@ int build_layout(lodgs_scene *sc, const float *node_rec_p, const int32_t *left_p
     DevBuf<uint32_t> flag, pos, bsum, total;
     CK(up_node.alloc(M)); CK(up_kind.alloc(M)); CK(up_parent.alloc(M)); CK(up_ref.alloc(M));
     CK(fr_a.alloc(M)); CK(fr_b.alloc(M)); CK(frp_a.alloc(M)); CK(frp_b.alloc(M));
-    CK(flag.alloc(M)); CK(pos.alloc(M)); CK(bsum.alloc(SCAN_GRID)); CK(total.alloc(1));
+    CK(flag.alloc(M)); CK(pos.alloc(M)); CK(bsum.alloc(SCAN_GRID_MAX)); CK(total.alloc(1));
     int32_t minus1 = -1;
     CK(cudaMemcpy(fr_a.p, &root, 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(frp_a.p, &minus1, 4, cudaMemcpyHostToDevice));

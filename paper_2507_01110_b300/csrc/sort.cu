@@ -304,9 +304,11 @@ int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint3
         LODGS_CUDA(cudaGetLastError());
         return LODGS_OK;
     }
-    k_scan_reduce<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, idx, d_n, block_sums);
+    // long scans: about four tiles per block, up to 8 blocks per SM
+    const int G = (int)std::min<uint64_t>(SCAN_GRID_MAX, std::max<uint64_t>(SCAN_GRID, (uint64_t)max_n / (SC_TILE * 4)));
+    k_scan_reduce<<<G, SC_THREADS, 0, st>>>(in, idx, d_n, block_sums);
     count_launches(1);
-    k_scan_down<<<SCAN_GRID, SC_THREADS, 0, st>>>(in, idx, out, d_n, block_sums, d_total);
+    k_scan_down<<<G, SC_THREADS, 0, st>>>(in, idx, out, d_n, block_sums, d_total);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
