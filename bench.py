@@ -301,9 +301,11 @@ def run_lodgs(args, rank: int, world: int):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
+    h0 = time.perf_counter()
     for i, v in enumerate(order):
         replay(v, i)
     e1.record(stream)
+    host_submit_ms = 1e3 * (time.perf_counter() - h0) / len(order)      # host time to enqueue a step
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     launches_host = _lib.lib().lodgs_kernel_launches() - launches0
@@ -425,7 +427,7 @@ def run_lodgs(args, rank: int, world: int):
     total_views = args.steps * world
     res = {
         "ms": ms, "fwd_ms": fwd_ms, "e2e_ms": max(e2e_ms, e2e_wall * 1e3), "views": total_views,
-        "train_ms": train_ms,
+        "train_ms": train_ms, "host_submit_ms": host_submit_ms,
         "stage_ms": stage_mean_live, "stage_ms_eager": stage_mean, "clocks": clk, "launches": launches,
         "stats_ok": stats_ok, "work": work,
         "fwd_stats": fwd_stats, "scene": {"n_nodes": scene.n_nodes, "n_upper": scene.n_upper, "n_spt": scene.n_spt,
@@ -967,6 +969,7 @@ def main():
                    "l2": "inputs larger than L2 (node records 1.07 GB; per-view reads 100-400 MB)",
                    "parallelism": f"replicas x{world} (views split across ranks)"},
         "fwd_bwd_step_ms": res["ms"] / args.steps,
+        "host_submit_ms_per_step": round(res["host_submit_ms"], 4),
         "train_step": {"value": res["views"] / (res["train_ms"] * 1e-3), "unit": "views/s",
                        "ms_per_step": res["train_ms"] / res["views"] * world,
                        "note": "the fwd+bwd step followed by a sparse Adam step of the view's cut "

@@ -130,6 +130,19 @@ int lodgs_scene_export(const lodgs_scene *scene, float *node_rec, int64_t *left,
                        int64_t *node_of_row, float *lo_row, float *hi_row);
 
 /*
+ * Checkpoint of a scene (training resumes from it): the canonical node records,
+ * the children of every node, the root, the SH degree and the build parameters,
+ * with a checksum.  lodgs_scene_load validates the file (magic, header,
+ * checksum, one full binary tree over all nodes: LODGS_E_INVALID otherwise) and
+ * rebuilds the HSPT and SPT layout, which is deterministic: the loaded scene's
+ * render rows, intervals and upper hierarchy equal the saved scene's, so per-row
+ * state saved beside it (Adam moments) stays valid.  Synchronous.  Save needs
+ * the scene's records on the device (LODGS_E_STATE after a cache released them).
+ */
+int lodgs_scene_save(const lodgs_scene *scene, const char *path);
+int lodgs_scene_load(const char *path, lodgs_scene **out);
+
+/*
  * Densification by moving Gaussians (Sec. 3 "Densification"): a batch of
  * operations on leaves, after which the HSPT and SPT layout are rebuilt
  * (Sec. 4.3, Algorithm 1 split and Sec. 4.1 intervals) with the scene's

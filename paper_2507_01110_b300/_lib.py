@@ -80,6 +80,8 @@ _SIGS = {
     "lodgs_scene_get_info": (C.c_int, [_P, C.POINTER(SceneInfo)]),
     "lodgs_scene_export": (C.c_int, [_P] + [_P] * 13),
     "lodgs_scene_densify": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64]),
+    "lodgs_scene_save": (C.c_int, [_P, C.c_char_p]),
+    "lodgs_scene_load": (C.c_int, [C.c_char_p, C.POINTER(_P)]),
     "lodgs_densify_plan": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_float, C.c_int64, _P, C.c_int64,
                                      C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P]),
     "lodgs_gather_rows": (C.c_int, [_P, C.c_int64, _P, _P, C.c_int64, C.c_int32, _P]),

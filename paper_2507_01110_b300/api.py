@@ -141,6 +141,10 @@ class Scene:
         respawn = list(zip(arr["target"][ns:n].tolist(), arr["dead"][ns:n].tolist()))
         return spawn, respawn
 
+    def save(self, path) -> None:
+        """Checkpoint: records, tree and build parameters (lodgs_scene_save)."""
+        check(lib().lodgs_scene_save(self._h, str(path).encode()))
+
     def topology(self) -> dict:
         """Children (canonical ids, -1 for leaves), node_of_row and the root, copied
         to the host; what densification planning needs without the records."""
@@ -461,6 +465,14 @@ def l1_loss_grad(image: torch.Tensor, target: torch.Tensor, dL: torch.Tensor | N
     check(lib().lodgs_l1_loss_grad(_ptr(image), _ptr(target), C.c_int64(n), C.c_float(1.0 / max(n, 1)),
                                    _ptr(dL), _ptr(loss_sum), _stream_ptr(stream)))
     return dL, loss_sum
+
+
+def load_scene(path) -> Scene:
+    """A scene from a checkpoint written by Scene.save; the layout is rebuilt
+    and equals the saved scene's."""
+    h = C.c_void_p()
+    check(lib().lodgs_scene_load(str(path).encode(), C.byref(h)))
+    return Scene(h)
 
 
 def build_hierarchy(leaves, sh_degree: int, spt_volume: float, kappa: float) -> Scene:

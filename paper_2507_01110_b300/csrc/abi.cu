@@ -197,6 +197,26 @@ int lodgs_scene_get_info(const lodgs_scene *sc, lodgs_scene_info *info) {
     return LODGS_OK;
 }
 
+int lodgs_scene_save(const lodgs_scene *sc, const char *path) {
+    if (!sc || !path) { set_error("scene_save: NULL argument"); return LODGS_E_INVALID; }
+    return save_scene(sc, path);
+}
+
+int lodgs_scene_load(const char *path, lodgs_scene **out) {
+    if (!path || !out) { set_error("scene_load: NULL argument"); return LODGS_E_INVALID; }
+    *out = nullptr;
+    lodgs_scene *sc = new (std::nothrow) lodgs_scene();
+    if (!sc) { set_error("scene_load: host allocation failed"); return LODGS_E_OOM; }
+    int rc = load_scene(path, sc);
+    if (rc) {
+        free_scene(sc);
+        delete sc;
+        return rc;
+    }
+    *out = sc;
+    return LODGS_OK;
+}
+
 int lodgs_scene_densify(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, int32_t *old_row_of_new_row,
                         int64_t capacity) {
     if (!sc || (n_ops > 0 && !ops) || n_ops < 0 || !old_row_of_new_row) {

@@ -180,6 +180,8 @@ int build_scene(const float *leaves, int64_t n, int degree, int on_device, const
 void free_scene(lodgs_scene *sc);
 int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, int32_t *old_row_of_new_row,
                   int64_t capacity);
+int save_scene(const lodgs_scene *sc, const char *path);
+int load_scene(const char *path, lodgs_scene *sc);
 // 0 if `fr` belongs to `sc` and was created for its current layout, else an
 // error code (with the message set, prefixed by `who`)
 int check_frame(const lodgs_scene *sc, const lodgs_frame *fr, const char *who);

@@ -10,6 +10,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "lodgs_internal.cuh"
@@ -989,6 +991,140 @@ int densify_scene(lodgs_scene *sc, const lodgs_densify_op *ops, int64_t n_ops, i
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
     return LODGS_OK;
+}
+
+// ---- checkpoint ------------------------------------------------------------
+// File: "LODGSCN1", u32 version 1, u32 SH degree, u32 stride, u32 0, i64 node
+// count, i64 root, f32 spt_volume, f32 kappa, the canonical node records
+// (n x stride f32), left and right children (n i32 each), then the FNV-1a
+// hash (u64) of everything before it.  The HSPT and SPT layout is not stored:
+// the load rebuilds it, and the rebuild is deterministic.
+namespace {
+constexpr char CKPT_MAGIC[8] = {'L', 'O', 'D', 'G', 'S', 'C', 'N', '1'};
+
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+};
+
+struct File {
+    FILE *f = nullptr;
+    ~File() { if (f) fclose(f); }
+};
+}  // namespace
+
+int save_scene(const lodgs_scene *sc, const char *path) {
+    if (!sc->d_rows) {
+        set_error("scene_save: the scene's records are not on the device (released to a cache)");
+        return LODGS_E_STATE;
+    }
+    const int64_t M = sc->n_nodes;
+    const int stride = sc->stride;
+    DevBuf<float> node_rec;
+    CK(node_rec.alloc((size_t)M * stride));
+    k_unpermute_rows<<<nblk(M * (stride / 4)), BT>>>(sc->d_rows, sc->d_node_of_row, M, stride, node_rec.p);
+    count_launches(1);
+    std::vector<float> rec((size_t)M * stride);
+    std::vector<int32_t> left(M), right(M);
+    CK(cudaMemcpy(rec.data(), node_rec.p, rec.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(left.data(), sc->d_left, M * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(right.data(), sc->d_right, M * 4, cudaMemcpyDeviceToHost));
+    File fh;
+    fh.f = fopen(path, "wb");
+    if (!fh.f) { set_error(std::string("scene_save: cannot open ") + path); return LODGS_E_INVALID; }
+    Fnv h;
+    const uint32_t head[4] = {1u, (uint32_t)sc->sh_degree, (uint32_t)stride, 0u};
+    const int64_t nr[2] = {M, (int64_t)sc->root};
+    const float pr[2] = {sc->spt_volume, sc->kappa};
+    auto put = [&](const void *p, size_t n) {
+        h.add(p, n);
+        return fwrite(p, 1, n, fh.f) == n;
+    };
+    bool ok = put(CKPT_MAGIC, 8) && put(head, sizeof(head)) && put(nr, sizeof(nr)) && put(pr, sizeof(pr)) &&
+              put(rec.data(), rec.size() * 4) && put(left.data(), M * 4) && put(right.data(), M * 4);
+    ok = ok && fwrite(&h.h, 1, 8, fh.f) == 8;
+    if (!ok) { set_error(std::string("scene_save: write failed: ") + path); return LODGS_E_INVALID; }
+    return LODGS_OK;
+}
+
+int load_scene(const char *path, lodgs_scene *sc) {
+    File fh;
+    fh.f = fopen(path, "rb");
+    if (!fh.f) { set_error(std::string("scene_load: cannot open ") + path); return LODGS_E_INVALID; }
+    Fnv h;
+    auto get = [&](void *p, size_t n) {
+        if (fread(p, 1, n, fh.f) != n) return false;
+        h.add(p, n);
+        return true;
+    };
+    char magic[8];
+    uint32_t head[4];
+    int64_t nr[2];
+    float pr[2];
+    if (!get(magic, 8) || memcmp(magic, CKPT_MAGIC, 8) != 0 || !get(head, sizeof(head)) || head[0] != 1u ||
+        !get(nr, sizeof(nr)) || !get(pr, sizeof(pr))) {
+        set_error("scene_load: not a scene checkpoint (magic or version)");
+        return LODGS_E_INVALID;
+    }
+    const int degree = (int)head[1], stride = (int)head[2];
+    const int64_t M = nr[0];
+    const int64_t root = nr[1];
+    if (degree < 0 || degree > 3 || stride != record_stride(degree) || M < 1 || M >= ((int64_t)1 << 31) ||
+        (M & 1) == 0 || root < 0 || root >= M) {
+        set_error("scene_load: inconsistent header");
+        return LODGS_E_INVALID;
+    }
+    std::vector<float> rec((size_t)M * stride);
+    std::vector<int32_t> left(M), right(M);
+    uint64_t want = 0;
+    if (!get(rec.data(), rec.size() * 4) || !get(left.data(), M * 4) || !get(right.data(), M * 4) ||
+        fread(&want, 1, 8, fh.f) != 8) {
+        set_error("scene_load: truncated file");
+        return LODGS_E_INVALID;
+    }
+    if (want != h.h) { set_error("scene_load: checksum mismatch (corrupted file)"); return LODGS_E_INVALID; }
+    // the hierarchy must be a full binary tree over all nodes, rooted at `root`
+    std::vector<int32_t> parent(M, -1);
+    int64_t leaves = 0;
+    for (int64_t u = 0; u < M; ++u) {
+        const int32_t l = left[u], r = right[u];
+        if ((l < 0) != (r < 0) || l >= M || r >= M || l == u || r == u) {
+            set_error("scene_load: invalid children");
+            return LODGS_E_INVALID;
+        }
+        if (l < 0) { ++leaves; continue; }
+        if (parent[l] >= 0 || parent[r] >= 0 || l == r) { set_error("scene_load: a node with two parents"); return LODGS_E_INVALID; }
+        parent[l] = (int32_t)u;
+        parent[r] = (int32_t)u;
+    }
+    int64_t seen = 0;
+    {
+        std::vector<int32_t> stack{(int32_t)root};
+        while (!stack.empty() && seen <= M) {
+            const int32_t u = stack.back();
+            stack.pop_back();
+            ++seen;
+            if (left[u] >= 0) { stack.push_back(left[u]); stack.push_back(right[u]); }
+        }
+    }
+    if (parent[root] >= 0 || seen != M || 2 * leaves - 1 != M) {
+        set_error("scene_load: the hierarchy is not one tree over all nodes");
+        return LODGS_E_INVALID;
+    }
+    sc->sh_degree = degree;
+    sc->stride = stride;
+    DevBuf<float> d_rec;
+    DevBuf<int32_t> d_left, d_right, d_parent;
+    CK(d_rec.alloc(rec.size())); CK(d_left.alloc(M)); CK(d_right.alloc(M)); CK(d_parent.alloc(M));
+    CK(cudaMemcpy(d_rec.p, rec.data(), rec.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_left.p, left.data(), M * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_right.p, right.data(), M * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_parent.p, parent.data(), M * 4, cudaMemcpyHostToDevice));
+    lodgs_build_params p{pr[0], pr[1]};
+    return build_layout(sc, d_rec.p, d_left.p, d_right.p, d_parent.p, M, (int32_t)root, p, 0);
 }
 
 }  // namespace lodgs
