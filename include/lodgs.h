@@ -91,6 +91,25 @@ uint64_t lodgs_kernel_launches(void);
 
 /* Thread-local message for the last failing call of this thread. */
 const char *lodgs_last_error(void);
+
+/*
+ * Host-side fault injection, for tests of the error paths (nothing faults,
+ * traps or hangs on the device): the call at `site` after `after` more
+ * successful ones fails as documented, once; after < 0 disarms.  Sites:
+ *   LODGS_FAULT_STREAM  lodgs_stream_nodes returns LODGS_E_CUDA before it
+ *                       changes any cache or frame state (a failed copy);
+ *   LODGS_FAULT_ALLOC   a frame workspace allocation (lodgs_frame_create or a
+ *                       growth) returns LODGS_E_OOM before releasing the old
+ *                       buffer (device memory exhausted);
+ *   LODGS_FAULT_RENDER  lodgs_render returns LODGS_E_OOM before enqueuing
+ *                       anything (a render whose workspace cannot grow).
+ * Process-wide; LODGS_E_INVALID for an unknown site.
+ */
+#define LODGS_FAULT_STREAM 1
+#define LODGS_FAULT_ALLOC 2
+#define LODGS_FAULT_RENDER 3
+#define LODGS_FAULT_SITES 3
+int lodgs_debug_inject_fault(int site, int64_t after);
 /* Library version string. */
 const char *lodgs_version(void);
 

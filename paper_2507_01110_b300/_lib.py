@@ -49,6 +49,7 @@ class DensifyOp(C.Structure):
 
 
 DENSIFY_SPAWN, DENSIFY_RESPAWN = 0, 1
+FAULT_STREAM, FAULT_ALLOC, FAULT_RENDER = 1, 2, 3
 
 
 class CacheParams(C.Structure):
@@ -81,6 +82,7 @@ _SIGS = {
     "lodgs_scene_export": (C.c_int, [_P] + [_P] * 13),
     "lodgs_scene_densify": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64]),
     "lodgs_scene_save": (C.c_int, [_P, C.c_char_p]),
+    "lodgs_debug_inject_fault": (C.c_int, [C.c_int, C.c_int64]),
     "lodgs_scene_load": (C.c_int, [C.c_char_p, C.POINTER(_P)]),
     "lodgs_densify_plan": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_float, C.c_int64, _P, C.c_int64,
                                      C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P]),

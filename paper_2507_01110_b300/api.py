@@ -467,6 +467,12 @@ def l1_loss_grad(image: torch.Tensor, target: torch.Tensor, dL: torch.Tensor | N
     return dL, loss_sum
 
 
+def inject_fault(site: int, after: int = 0) -> None:
+    """Test hook: the call at `site` (_lib.FAULT_STREAM, _lib.FAULT_ALLOC) after
+    `after` more successful ones fails once, on the host (after < 0 disarms)."""
+    check(lib().lodgs_debug_inject_fault(int(site), int(after)))
+
+
 def load_scene(path) -> Scene:
     """A scene from a checkpoint written by Scene.save; the layout is rebuilt
     and equals the saved scene's."""

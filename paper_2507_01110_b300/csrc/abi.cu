@@ -18,6 +18,21 @@ static std::atomic<uint64_t> g_launches{0};
 
 void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
+// host-side fault injection (tests of the error paths; nothing faults on the device)
+static std::atomic<int64_t> g_fault[LODGS_FAULT_SITES + 1];
+static struct FaultInit {
+    FaultInit() { for (auto &f : g_fault) f.store(-1); }
+} g_fault_init;
+
+bool fault_hit(int site) {
+    int64_t c = g_fault[site].load();
+    while (c >= 0) {
+        const int64_t next = c == 0 ? -1 : c - 1;
+        if (g_fault[site].compare_exchange_weak(c, next)) return c == 0;
+    }
+    return false;
+}
+
 void set_error(const std::string &msg) { g_err = msg; }
 
 int cuda_fail(cudaError_t e, const char *what) {
@@ -71,6 +86,10 @@ bool camera_ok(const lodgs_camera *c) {
 template <typename T>
 int grow(T *&p, uint64_t &cap, uint64_t want, size_t elem_per = 1) {
     if (want <= cap && p) return LODGS_OK;
+    if (fault_hit(LODGS_FAULT_ALLOC)) {                     // before the old buffer is released
+        set_error("frame workspace: injected allocation failure");
+        return LODGS_E_OOM;
+    }
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
@@ -155,6 +174,12 @@ int check_frame(const lodgs_scene *sc, const lodgs_frame *fr, const char *who) {
 extern "C" {
 
 const char *lodgs_last_error(void) { return g_err.c_str(); }
+
+int lodgs_debug_inject_fault(int site, int64_t after) {
+    if (site < 1 || site > LODGS_FAULT_SITES) { set_error("debug_inject_fault: unknown site"); return LODGS_E_INVALID; }
+    g_fault[site].store(after < 0 ? -1 : after);
+    return LODGS_OK;
+}
 const char *lodgs_version(void) { return "lodgs 0.1 (sm_103a)"; }
 uint64_t lodgs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
@@ -360,6 +385,7 @@ int lodgs_frame_selection(lodgs_frame *fr, const uint32_t **d_rows, int64_t *n_s
 int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const float *bg, float *image, void *stream) {
     if (int rc = check_frame(sc, fr, "render")) return rc;
     if (!image) { set_error("render: NULL image"); return LODGS_E_INVALID; }
+    if (fault_hit(LODGS_FAULT_RENDER)) { set_error("render: injected out of device memory"); return LODGS_E_OOM; }
     if (!fr->selected) { set_error("render: select_lod was not called on this frame"); return LODGS_E_STATE; }
     cudaStream_t st = (cudaStream_t)stream;
     if (st != fr->stream) {       // order after the selection's stream

@@ -571,6 +571,10 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
         return LODGS_E_INVALID;
     }
     if (int rc = check_frame(sc, fr, "stream_nodes")) return rc;
+    if (fault_hit(LODGS_FAULT_STREAM)) {                    // before any cache or frame state changes
+        set_error("stream_nodes: injected copy failure");
+        return LODGS_E_CUDA;
+    }
     if (c->layout_version != sc->layout_version) {
         set_error("stream_nodes: the cache was created before the scene was densified; create a new cache");
         return LODGS_E_STATE;

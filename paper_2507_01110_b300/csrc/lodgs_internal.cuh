@@ -167,6 +167,7 @@ struct FrameBufs {
 
 void set_error(const std::string &msg);
 void count_launches(int n);     // process-wide tally of this library's kernel launches
+bool fault_hit(int site);       // an armed injected fault at `site` fires (host side only)
 int cuda_fail(cudaError_t e, const char *what);
 #define LODGS_CUDA(call)                                       \
     do {                                                       \

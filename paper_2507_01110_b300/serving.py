@@ -30,6 +30,7 @@ class Request:
     t_admit: float = 0.0
     t_done: float = 0.0
     retries: int = 0
+    status: str = "pending"          # "done", "expired" (deadline passed in the queue), "failed: ..."
     checksum: float | None = None
     image: torch.Tensor | None = field(default=None, repr=False)
 
@@ -61,14 +62,22 @@ class RenderServer:
         self.budget = mem_budget_bytes
         self.keep_images = keep_images
 
-    def _launch(self, slot: _Slot, req: Request):
+    def _launch(self, slot: _Slot, req: Request) -> bool:
+        """Enqueue the request on the slot; False (request marked failed, slot
+        left free) if the library refused it, e.g. out of device memory."""
         cam = req.camera
         img = slot.image[: cam.height * cam.width * 3].view(cam.height, cam.width, 3)
-        with torch.cuda.stream(slot.stream):
-            api.select_lod(self.scene, cam, slot.frame, stream=slot.stream)
-            api.render(self.scene, slot.frame, rows=self.rows, image=img, stream=slot.stream, check_capacity=False)
-            slot.done.record(slot.stream)
+        try:
+            with torch.cuda.stream(slot.stream):
+                api.select_lod(self.scene, cam, slot.frame, stream=slot.stream)
+                api.render(self.scene, slot.frame, rows=self.rows, image=img, stream=slot.stream,
+                           check_capacity=False)
+                slot.done.record(slot.stream)
+        except _lib.LodgsError as e:
+            req.status = f"failed: {e}"
+            return False
         slot.req = req
+        return True
 
     def _finish(self, slot: _Slot, now: float) -> bool:
         """True if the request completed; False if its frame had to grow and it
@@ -77,7 +86,9 @@ class RenderServer:
         st = slot.frame.stats()                      # the stream is idle: no wait
         if st["status"] == _lib.LODGS_E_CAPACITY:
             req.retries += 1
-            self._launch(slot, req)
+            if not self._launch(slot, req):          # growing the workspace failed: give up on it
+                slot.req = None
+                return True
             return False
         _lib.check(st["status"])
         cam = req.camera
@@ -85,6 +96,7 @@ class RenderServer:
         if self.keep_images:
             req.image = img.clone()
         req.t_done = now
+        req.status = "done"
         slot.req = None
         return True
 
@@ -97,9 +109,12 @@ class RenderServer:
                 api.render(self.scene, slot.frame, rows=self.rows, image=img, check_capacity=True)
         torch.cuda.synchronize()
 
-    def run(self, requests: list[Request], realtime: bool = True) -> dict:
+    def run(self, requests: list[Request], realtime: bool = True, deadline_ms: float | None = None) -> dict:
         """Serve `requests` (sorted by arrival).  realtime: requests arrive on
-        the wall clock at their arrival times."""
+        the wall clock at their arrival times.  deadline_ms: a request still
+        queued that long after it arrived is dropped ("expired").  A request
+        the library refuses (e.g. out of device memory) is marked failed and the
+        server carries on; latencies are over the completed requests."""
         reqs = sorted(requests, key=lambda r: r.arrival_s)
         pending = collections.deque()
         nxt = 0
@@ -124,24 +139,35 @@ class RenderServer:
             free = [s for s in self.slots if s.req is None]
             while pending and free:
                 req = pending[0]
+                if deadline_ms is not None and (time.perf_counter() - t0 - req.t_enqueue) * 1e3 > deadline_ms:
+                    pending.popleft()                # waited past its deadline: never launched
+                    req.status = "expired"
+                    done += 1
+                    continue
                 need = request_bytes(req.camera.width, req.camera.height)
                 if in_use + need > self.budget and in_use > 0:
                     break
                 pending.popleft()
                 slot = free.pop()
+                req.t_admit = time.perf_counter() - t0
+                if not self._launch(slot, req):
+                    free.append(slot)
+                    done += 1
+                    continue
                 slot.bytes = need
                 in_use += need
-                req.t_admit = time.perf_counter() - t0
-                self._launch(slot, req)
             inflight_max = max(inflight_max, sum(s.req is not None for s in self.slots))
             time.sleep(0)
         wall = time.perf_counter() - t0
         # latency from arrival (realtime) or from being queued (batch mode) to completion
-        lat = np.array([(r.t_done - r.t_enqueue) * 1e3 for r in reqs])
-        return {"requests": len(reqs), "wall_s": wall, "throughput_rps": len(reqs) / wall,
+        ok = [r for r in reqs if r.status == "done"]
+        lat = np.array([(r.t_done - r.t_enqueue) * 1e3 for r in ok]) if ok else np.zeros(1)
+        return {"requests": len(reqs), "wall_s": wall, "throughput_rps": len(ok) / wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "max_inflight": inflight_max,
-                "retries": int(sum(r.retries for r in reqs))}
+                "retries": int(sum(r.retries for r in reqs)),
+                "completed": len(ok), "expired": sum(r.status == "expired" for r in reqs),
+                "failed": sum(r.status.startswith("failed") for r in reqs)}
 
 
 def poisson_requests(cameras, rate_per_s: float, n: int, seed: int) -> list[Request]:

@@ -50,3 +50,11 @@ def test_version_and_errors_without_gpu():
     rc = L.lodgs_build_hierarchy(None, 0, 0, 0, C.byref(p), C.byref(h))
     assert rc == _lib.LODGS_E_INVALID and h.value is None
     assert b"build_hierarchy" in L.lodgs_last_error()
+
+
+def test_fault_injection_hook_validates_its_site():
+    from paper_2507_01110_b300 import _lib
+    lib = _lib.lib()
+    assert lib.lodgs_debug_inject_fault(0, 0) == _lib.LODGS_E_INVALID
+    assert lib.lodgs_debug_inject_fault(_lib.FAULT_ALLOC, -1) == _lib.LODGS_OK
+    assert lib.lodgs_debug_inject_fault(_lib.FAULT_STREAM, -1) == _lib.LODGS_OK
