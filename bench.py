@@ -451,6 +451,7 @@ OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB = 6, 11, 34
 # DRAM bytes (read + write) per k_blend_bwd launch, mean over the 32 views of
 # this workload, from one ncu capture (profiles/launches_fwd_bwd_1080p_2Mleaves.md)
 BLEND_BWD_DRAM_BYTES = 57.9e6
+BLEND_BWD_ISSUE_ACTIVE = 0.774    # smsp__issue_active of the same kernel, one view (ncu --set full)
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 
@@ -999,7 +1000,11 @@ def main():
                                            "in the timed region)",
                             "work": f"algorithmic instructions = {OPS_EVAL + OPS_BWD_CONTRIB} per backward "
                                     f"contribution ({OPS_EVAL + OPS_BLEND} per forward blend)",
-                            "work_per_view": rf["work"]}
+                            "work_per_view": rf["work"],
+                            "ncu_issue_active": BLEND_BWD_ISSUE_ACTIVE if dom == "blend_bwd" else None,
+                            "ncu_note": "issue slots the kernel used, one 1080p view (ncu "
+                                        "smsp__issue_active, profiles/k_blend_bwd_1080p_2Mleaves.md); frac "
+                                        "counts only the method's instructions in those slots"}
     line["roofline_stages"] = {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in rf["stages"].items()}
     def section(name, fn):
         try:
