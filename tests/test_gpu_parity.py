@@ -212,12 +212,7 @@ def test_long_tile_lists_match_oracle(api, n, ordering):
     assert lens.max() >= {200: 150, 1000: 700, 6000: 4000, 20000: 12000}[n], lens.max()
 
 
-def test_orderings_agree_on_a_1080p_view(api):
-    """Per-tile and global ordering give the same pairs, image and gradients on
-    a dense 1080p view of the 2M-leaf scene."""
-    cfg = synth.config2_scene()
-    cam = cfg["cameras"][2]
-    sc = api.build_hierarchy(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
+def _orderings_agree(api, sc, cam, min_pairs):
     res = []
     for ordering in (1, 2):
         fr = api.Frame(sc)
@@ -228,11 +223,31 @@ def test_orderings_agree_on_a_1080p_view(api):
         g = api.render_backward(sc, fr, dL)
         ex = fr.export()
         res.append((ex["pair_i"], ex["ranges"], img.cpu().numpy(), g.cpu().numpy(), fr.stats()))
-    assert res[0][4]["n_pairs"] == res[1][4]["n_pairs"] > 100000
+        del fr, img, g
+    assert res[0][4]["n_pairs"] == res[1][4]["n_pairs"] > min_pairs, res[0][4]["n_pairs"]
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
     assert np.array_equal(res[0][2], res[1][2])
     scale = np.abs(res[1][3]).max(axis=0, keepdims=True) + 1e-12
     assert (np.abs(res[0][3] - res[1][3]) / scale).max() < 1e-4
+
+
+def test_orderings_agree_on_a_1080p_view(api):
+    """Per-tile and global ordering give the same pairs, image and gradients on
+    a dense 1080p view of the 2M-leaf scene."""
+    cfg = synth.config2_scene()
+    sc = api.build_hierarchy(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
+    _orderings_agree(api, sc, cfg["cameras"][2], 100_000)
+
+
+def test_orderings_agree_on_a_4k_view_of_large_splats(api):
+    """The same on a 3840x2160 view at tau 0.5 px of 800k metre-scale
+    Gaussians: over ten million tile-Gaussian pairs, so the global ordering's
+    radix sorts and scans run on their element-count-scaled grids (more than
+    two blocks per SM)."""
+    leaves = synth.leaves_uniform_cube(800_000, seed=77, half_extent=50.0, degree=1, log_scale_mu=-0.8)
+    cam = synth.camera_look([4.0, -3.0, -120.0], [0.0, 0.02, 1.0], [1.0, 0.0, 0.0], 3840, 2160, tau=0.5)
+    sc = api.build_hierarchy(leaves, 1, 1.0, float(cam.fx / cam.tau))
+    _orderings_agree(api, sc, cam, 10_000_000)
 
 
 def test_select_with_lod_noise_matches_oracle(api, c1):
