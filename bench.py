@@ -214,7 +214,9 @@ def run_lodgs(args, rank: int, world: int):
     my_views = shard_views(nv, rank, world)
     frames = {v: api.Frame(scene) for v in my_views}     # profiling off: nothing extra in the timed graphs
     gen = torch.Generator().manual_seed(1234)
-    targets_h = {v: torch.rand((H, W, 3), generator=gen).pin_memory() for v in my_views}
+    # 8-bit RGB targets, the format of training photographs (read as byte / 255 in the backward)
+    targets_h = {v: torch.randint(0, 256, (H, W, 3), generator=gen, dtype=torch.uint8).pin_memory()
+                 for v in my_views}
     targets_d = {v: t.cuda() for v, t in targets_h.items()}
     image = torch.empty((H, W, 3), device="cuda")
     stream = torch.cuda.current_stream()
@@ -432,7 +434,7 @@ def run_lodgs(args, rank: int, world: int):
         "stats_ok": stats_ok, "work": work,
         "fwd_stats": fwd_stats, "scene": {"n_nodes": scene.n_nodes, "n_upper": scene.n_upper, "n_spt": scene.n_spt,
                                           "stride": scene.stride},
-        "h2d_bytes": H * W * 3 * 4 + 64, "d2h_bytes": 4, "order": order,
+        "h2d_bytes": H * W * 3 + 64, "d2h_bytes": 4, "order": order,
     }
     return res, cfg
 
@@ -450,8 +452,8 @@ def run_lodgs(args, rank: int, world: int):
 OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB = 6, 11, 34
 # DRAM bytes (read + write) per k_blend_bwd launch, mean over the 32 views of
 # this workload, from one ncu capture (profiles/launches_fwd_bwd_1080p_2Mleaves.md)
-BLEND_BWD_DRAM_BYTES = 57.9e6
-BLEND_BWD_ISSUE_ACTIVE = 0.774    # smsp__issue_active of the same kernel, one view (ncu --set full)
+BLEND_BWD_DRAM_BYTES = 39.2e6
+BLEND_BWD_ISSUE_ACTIVE = 0.768    # smsp__issue_active of the same kernel, one view (ncu --set full)
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 
@@ -967,6 +969,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "leaves": args.leaves, "nodes": res["scene"]["n_nodes"],
                    "spt": res["scene"]["n_spt"], "views": 32, "resolution": "1920x1080", "tau_px": 1.0,
+                   "loss": "mean L1 against 8-bit RGB targets",
                    "l2": "inputs larger than L2 (node records 1.07 GB; per-view reads 100-400 MB)",
                    "parallelism": f"replicas x{world} (views split across ranks)"},
         "fwd_bwd_step_ms": res["ms"] / args.steps,
@@ -979,8 +982,8 @@ def main():
                      "ms_per_frame": res["fwd_ms"] / args.steps},
         "e2e": {"value": res["views"] / (res["e2e_ms"] * 1e-3), "unit": "frames/s",
                 "h2d_bytes_per_step": res["h2d_bytes"], "d2h_bytes_per_step": res["d2h_bytes"],
-                "note": "each view's target (pinned host) uploaded on a copy stream while the previous view "
-                        "computes; the loss read back every step"},
+                "note": "each view's 8-bit RGB target (pinned host) uploaded on a copy stream while the "
+                        "previous view computes; the loss read back every step"},
         "gpu_launches": int(res["launches"]),
         "stages_ms": {k: round(v, 4) for k, v in res["stage_ms_eager"].items()},
         "stages_note": "stages_ms: the timed steps replayed eagerly with every stage timed; the roofline kernel "

@@ -503,6 +503,16 @@ int lodgs_render_backward_project(lodgs_scene *scene, lodgs_frame *frame, const 
 int lodgs_render_backward_blend_l1(lodgs_scene *scene, lodgs_frame *frame, const float *image, const float *target,
                                    float grad_scale, float *loss_sum, void *stream);
 
+/*
+ * lodgs_render_backward_blend_l1 with an 8-bit target (device H x W x 3
+ * uint8, the format training photographs are stored in): each byte t is read
+ * as t / 255, correctly rounded to float32, so the results equal those of
+ * lodgs_render_backward_blend_l1 on that float32 target, up to the order of
+ * float atomic sums.  A quarter of the float target's bytes to upload.
+ */
+int lodgs_render_backward_blend_l1_u8(lodgs_scene *scene, lodgs_frame *frame, const float *image,
+                                      const uint8_t *target, float grad_scale, float *loss_sum, void *stream);
+
 /* Counters of the last select/render on this frame (blocks until `stream`,
  * the stream the frame last ran on, is idle). */
 int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);

@@ -106,6 +106,7 @@ _SIGS = {
     "lodgs_render_backward": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, C.c_int, _P]),
     "lodgs_render_backward_blend": (C.c_int, [_P, _P, _P, _P, _P]),
     "lodgs_render_backward_blend_l1": (C.c_int, [_P, _P, _P, _P, C.c_float, _P, _P]),
+    "lodgs_render_backward_blend_l1_u8": (C.c_int, [_P, _P, _P, _P, C.c_float, _P, _P]),
     "lodgs_render_backward_project": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P]),
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
     "lodgs_frame_set_ordering": (C.c_int, [_P, C.c_int]),

@@ -512,13 +512,21 @@ def render_backward_blend_l1(scene: Scene, frame: Frame, target: torch.Tensor, l
                              ) -> torch.Tensor:
     """Blend backward of the mean-L1 loss against `target`, the loss folded in:
     dL/dC = grad_scale * sign(image - target) (default scale 1/numel) is formed
-    in the kernel; returns loss_sum (device, sum |image - target|)."""
+    in the kernel; returns loss_sum (device, sum |image - target|).  `target`
+    is float32, or uint8 read as byte / 255 (lodgs_render_backward_blend_l1_u8)."""
     img = _rendered_image(frame, image)
     if loss_sum is None:
         loss_sum = torch.empty(1, dtype=torch.float32, device="cuda")
+    if target.shape != img.shape or not target.is_cuda:
+        raise ValueError(f"target must be a CUDA tensor of the image's shape {tuple(img.shape)}")
+    fn = {torch.float32: lib().lodgs_render_backward_blend_l1,
+          torch.uint8: lib().lodgs_render_backward_blend_l1_u8}.get(target.dtype)
+    if fn is None:
+        raise TypeError(f"target must be float32 or uint8, not {target.dtype}")
     scale = 1.0 / max(img.numel(), 1) if grad_scale is None else grad_scale
-    check(lib().lodgs_render_backward_blend_l1(scene.handle, frame.handle, _ptr(img), _ptr(target.contiguous()),
-                                               C.c_float(scale), _ptr(loss_sum), _stream_ptr(stream)))
+    target = target.contiguous()
+    check(fn(scene.handle, frame.handle, _ptr(img), C.c_void_p(target.data_ptr()), C.c_float(scale), _ptr(loss_sum),
+             _stream_ptr(stream)))
     return loss_sum
 
 

@@ -432,7 +432,8 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
 
 namespace {
 int backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const float *dL_dimage,
-                   const float *target, float l1_scale, float *loss_sum, void *stream, const char *who) {
+                   const void *target, bool target_u8, float l1_scale, float *loss_sum, void *stream,
+                   const char *who) {
     if (int rc = check_frame(sc, fr, who)) return rc;
     if (!image || (!dL_dimage && !(target && loss_sum))) {
         set_error(std::string(who) + ": NULL argument");
@@ -453,7 +454,7 @@ int backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const f
         fr->stream = st;
     }
     fr->mark(LODGS_STAGE_BLEND_BWD, 0, st);
-    int rc = launch_raster_backward(fr->k, fr->f, image, dL_dimage, target, l1_scale, loss_sum, st);
+    int rc = launch_raster_backward(fr->k, fr->f, image, dL_dimage, target, target_u8, l1_scale, loss_sum, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_BLEND_BWD, 1, st);
     fr->blend_bwd_done = true;
@@ -464,13 +465,21 @@ int backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const f
 int lodgs_render_backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const float *dL_dimage,
                                 void *stream) {
     if (!dL_dimage) { set_error("render_backward_blend: NULL dL_dimage"); return LODGS_E_INVALID; }
-    return backward_blend(sc, fr, image, dL_dimage, nullptr, 0.f, nullptr, stream, "render_backward_blend");
+    return backward_blend(sc, fr, image, dL_dimage, nullptr, false, 0.f, nullptr, stream, "render_backward_blend");
 }
 
 int lodgs_render_backward_blend_l1(lodgs_scene *sc, lodgs_frame *fr, const float *image, const float *target,
                                    float grad_scale, float *loss_sum, void *stream) {
     if (!target || !loss_sum) { set_error("render_backward_blend_l1: NULL argument"); return LODGS_E_INVALID; }
-    return backward_blend(sc, fr, image, nullptr, target, grad_scale, loss_sum, stream, "render_backward_blend_l1");
+    return backward_blend(sc, fr, image, nullptr, target, false, grad_scale, loss_sum, stream,
+                          "render_backward_blend_l1");
+}
+
+int lodgs_render_backward_blend_l1_u8(lodgs_scene *sc, lodgs_frame *fr, const float *image, const uint8_t *target,
+                                      float grad_scale, float *loss_sum, void *stream) {
+    if (!target || !loss_sum) { set_error("render_backward_blend_l1_u8: NULL argument"); return LODGS_E_INVALID; }
+    return backward_blend(sc, fr, image, nullptr, target, true, grad_scale, loss_sum, stream,
+                          "render_backward_blend_l1_u8");
 }
 
 int lodgs_render_backward_project(lodgs_scene *sc, lodgs_frame *fr, const float *rows, float *grad_rows,

@@ -230,8 +230,10 @@ int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaSt
 // `k` is the host copy of the view (resolution, grid sizes); kernels read f.d_view
 int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaStream_t st);
 int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, const StageMarks &sm);
+// target (with loss_sum): the L1 loss's gradient formed in the kernel from a
+// float32 or (target_u8) 8-bit H x W x 3 target; else dL/dC read from dL_dimage
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, const float *dL_dimage,
-                           const float *target, float l1_scale, float *loss_sum, cudaStream_t st);
+                           const void *target, bool target_u8, float l1_scale, float *loss_sum, cudaStream_t st);
 int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows,
                             int64_t grad_capacity, int dense, cudaStream_t st);
 }  // namespace lodgs

@@ -450,11 +450,6 @@ constexpr float ALPHA_MAX = 0.99f;
 constexpr float T_MIN = 1e-4f;
 constexpr int BATCH = 256;            // Gaussians staged in shared memory per round
 
-// Sum 9 per-lane values over the warp and add the totals to dst[0..8] in shared
-// memory.  Values 0..7 use a transposed butterfly: at each exchange a lane keeps
-// half of its values and receives its partner's share of that half, so the
-// eight sums take 4+2+1+1+1 = 9 shuffles instead of 8 x 5; afterwards lane
-// 4*i holds the total of value i.  Value 8 uses a plain butterfly.
 // per-warp sums of two per-thread counters, one 64-bit atomic each per warp
 __device__ __forceinline__ void add_work(unsigned long long *work, uint32_t a, uint32_t b) {
 #pragma unroll
@@ -468,8 +463,16 @@ __device__ __forceinline__ void add_work(unsigned long long *work, uint32_t a, u
     }
 }
 
+// Sum 9 per-lane values over the warp and add the totals to dst[0..8] in shared
+// memory.  Values 0..7 use a transposed butterfly: at each exchange a lane keeps
+// half of its values and receives its partner's share of that half (4, 2, 1
+// shuffles over lane bits 4, 3, 2), while value 8 is summed plainly beside
+// them.  The exchange over bit 1 is transposed too, between the lane's one
+// remaining value and value 8, and bit 0 is a plain exchange: 12 shuffles in
+// all instead of 9 x 5.  Afterwards lane 4i holds the total of value i and
+// lane 2 that of value 8; one shared-memory atomic adds all nine.
 __device__ __forceinline__ void warp_sum9_to_smem(float v[9], int lane, float *dst) {
-    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
     float w4[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -477,6 +480,7 @@ __device__ __forceinline__ void warp_sum9_to_smem(float v[9], int lane, float *d
         float keep = h16 ? v[i + 4] : v[i];
         w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
+    float s8 = v[8] + __shfl_xor_sync(0xffffffffu, v[8], 16);
     float w2[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -484,22 +488,24 @@ __device__ __forceinline__ void warp_sum9_to_smem(float v[9], int lane, float *d
         float keep = h8 ? w4[i + 2] : w4[i];
         w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
+    s8 += __shfl_xor_sync(0xffffffffu, s8, 8);
     float w1;
     {
         float send = h4 ? w2[0] : w2[1];
         float keep = h4 ? w2[1] : w2[0];
         w1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
     }
-    w1 += __shfl_xor_sync(0xffffffffu, w1, 2);
+    s8 += __shfl_xor_sync(0xffffffffu, s8, 4);
+    {                                   // bit 1: value (lanes with bit 1 clear) against value 8 (set)
+        float send = h2 ? w1 : s8;
+        float keep = h2 ? s8 : w1;
+        w1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
     w1 += __shfl_xor_sync(0xffffffffu, w1, 1);
-    float s8 = v[8];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
-    if ((lane & 3) == 0) {
-        const int idx = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
+    if ((lane & 3) == 0 || lane == 2) {
+        const int idx = h2 ? 8 : (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
         atomicAdd(dst + idx, w1);
     }
-    if (lane == 1) atomicAdd(dst + 8, s8);
 }
 
 // Warp-block layout of a 16x16 tile (128 threads, 2 pixels each): warp w owns
@@ -689,17 +695,18 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
 // with 16-byte atomics.
 // BP pixels per lane: 2 (a warp per 8x8 block, 128 threads per tile) or 4 (a
 // warp per 8x16 column of two blocks, 64 threads per tile).
-// L1: dL/dC is not read but formed from the image and a target as the L1
-// loss's gradient, l1_scale * sign(C - target), and the block adds its
+// L1 (1: float32 target, 2: 8-bit target read as byte / 255, correctly
+// rounded): dL/dC is not read but formed from the image and the target as the
+// L1 loss's gradient, l1_scale * sign(C - target), and the block adds its
 // sum |C - target| to *loss_sum (the training loss folded into the backward:
-// no separate pass over the image, no dL/dC buffer).
-template <bool COUNT, int BP, bool L1>
+// no separate pass over the image, no dL/dC buffer).  0: dL/dC from dL_dimg.
+template <bool COUNT, int BP, int L1>
 __global__ void __launch_bounds__(TILE_PIX / BP)
     k_blend_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
                 const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c,
                 const uint32_t *__restrict__ cnt, int W, int H, int TX, const float *__restrict__ image,
                 const float *__restrict__ dL_dimg, float *__restrict__ g2d, unsigned long long *__restrict__ work,
-                const float *__restrict__ target, float l1_scale, float *__restrict__ loss_sum) {
+                const void *__restrict__ target, float l1_scale, float *__restrict__ loss_sum) {
     constexpr int NT = TILE_PIX / BP, NW = NT / 32;
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
@@ -730,7 +737,12 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
             const size_t o = ((size_t)py * W + bp.px) * 3;
             const float c0 = image[o], c1 = image[o + 1], c2 = image[o + 2];
             if (L1) {
-                const float d[3] = {c0 - target[o], c1 - target[o + 1], c2 - target[o + 2]};
+                float tg[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+                    tg[ch] = L1 == 2 ? __fdiv_rn((float)static_cast<const uint8_t *>(target)[o + ch], 255.0f)
+                                     : static_cast<const float *>(target)[o + ch];
+                const float d[3] = {c0 - tg[0], c1 - tg[1], c2 - tg[2]};
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
                     G[k][ch] = l1_scale * (d[ch] > 0.f ? 1.f : (d[ch] < 0.f ? -1.f : 0.f));
@@ -938,18 +950,19 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
 }
 
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, const float *dL_dimage,
-                           const float *target, float l1_scale, float *loss_sum, cudaStream_t st) {
+                           const void *target, bool target_u8, float l1_scale, float *loss_sum, cudaStream_t st) {
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * G2D_STRIDE * sizeof(float), st));
     LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
     const unsigned nb = (unsigned)n_tiles, nt = TILE_PIX / BWD_PIX;
     if (target) {
         LODGS_CUDA(cudaMemsetAsync(loss_sum, 0, sizeof(float), st));
-        (f.count_work ? k_blend_bwd<true, BWD_PIX, true> : k_blend_bwd<false, BWD_PIX, true>)<<<nb, nt, 0, st>>>(
-            f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, nullptr, f.g2d, f.work,
-            target, l1_scale, loss_sum);
+        auto kern = target_u8 ? (f.count_work ? k_blend_bwd<true, BWD_PIX, 2> : k_blend_bwd<false, BWD_PIX, 2>)
+                              : (f.count_work ? k_blend_bwd<true, BWD_PIX, 1> : k_blend_bwd<false, BWD_PIX, 1>);
+        kern<<<nb, nt, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image,
+                                nullptr, f.g2d, f.work, target, l1_scale, loss_sum);
     } else {
-        (f.count_work ? k_blend_bwd<true, BWD_PIX, false> : k_blend_bwd<false, BWD_PIX, false>)<<<nb, nt, 0, st>>>(
+        (f.count_work ? k_blend_bwd<true, BWD_PIX, 0> : k_blend_bwd<false, BWD_PIX, 0>)<<<nb, nt, 0, st>>>(
             f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, dL_dimage, f.g2d, f.work,
             nullptr, 0.f, nullptr);
     }

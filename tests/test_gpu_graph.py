@@ -107,3 +107,35 @@ def test_fused_l1_backward_matches_loss_then_backward():
     scale = g_a.abs().amax(dim=0) + 1e-30
     assert torch.all((g_a - g_b).abs() <= 1e-4 * scale)
     assert g_a.abs().max() > 0
+
+
+def test_fused_l1_backward_with_an_8bit_target():
+    """An 8-bit target (byte / 255 in the kernel) gives the loss and gradients
+    of the float32 target holding the same quotients, up to the order of float
+    atomic sums; wrong dtypes and shapes are refused before any launch."""
+    from paper_2507_01110_b300 import api, build
+    build.build()
+    cfg = synth.config2_scene(n=200_000)
+    scene = api.build_hierarchy(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
+    c = cfg["cameras"][9]
+    cam = synth.camera_look(c.pos, c.R[2], c.R[0], 301, 177)
+    gen = torch.Generator().manual_seed(21)
+    t8 = torch.randint(0, 256, (cam.height, cam.width, 3), generator=gen, dtype=torch.uint8)
+    t32 = t8.float() / 255.0                      # correctly rounded on the CPU
+    fr = api.select_lod(scene, cam)
+    api.render(scene, fr)
+    n = fr.stats()["n_selected"]
+    out = []
+    for t in (t32.cuda(), t8.cuda()):
+        loss = api.render_backward_blend_l1(scene, fr, t)
+        g = torch.empty((n, scene.stride), device="cuda")
+        api.render_backward_project(scene, fr, g)
+        out.append((loss.item(), g))
+    (la, ga), (lb, gb) = out
+    assert la > 0 and abs(la - lb) <= 1e-5 * la
+    scale = ga.abs().amax(dim=0) + 1e-30
+    assert torch.all((ga - gb).abs() <= 1e-4 * scale) and ga.abs().max() > 0
+    with pytest.raises(TypeError):
+        api.render_backward_blend_l1(scene, fr, t8.cuda().to(torch.int32))
+    with pytest.raises(ValueError):
+        api.render_backward_blend_l1(scene, fr, t8.cuda()[:-1])
