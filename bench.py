@@ -231,7 +231,9 @@ def run_lodgs(args, rank: int, world: int):
         fwd_stats[v] = st
         max_sel = max(max_sel, st["n_selected"])
     grad = torch.empty((max_sel, scene.stride), device="cuda")
-    loss_sum = torch.empty(1, device="cuda")
+    # one loss slot per view: a view's loss can be read back on the copy stream
+    # while the next views compute (no slot is rewritten before its read)
+    loss_slots = torch.zeros(nv, device="cuda")
 
     def step_fwd(v, target, camera):
         fr = api.select_lod(scene, camera, frames[v])                  # camera=None: the frame's view
@@ -239,7 +241,7 @@ def run_lodgs(args, rank: int, world: int):
 
     def step_bwd_blend(v):
         # mean-L1 loss against the view's target folded into the blend backward
-        api.render_backward_blend_l1(scene, frames[v], targets_d[v], loss_sum=loss_sum)
+        api.render_backward_blend_l1(scene, frames[v], targets_d[v], loss_sum=loss_slots[v:v + 1])
 
     def step_bwd_project(v):
         api.render_backward_project(scene, frames[v], grad)
@@ -248,7 +250,7 @@ def run_lodgs(args, rank: int, world: int):
         step_fwd(v, target, camera)
         step_bwd_blend(v)
         step_bwd_project(v)
-        return loss_sum
+        return loss_slots[v:v + 1]
 
     order = [my_views[i % len(my_views)] for i in range(args.steps)]
     for i in range(args.warmup):
@@ -386,7 +388,9 @@ def run_lodgs(args, rank: int, world: int):
     # ---- end to end: targets from pinned host, loss read back every step ----
     # Each step's target goes up on a copy stream while the previous view
     # computes (the compute stream waits for it; a target buffer is rewritten
-    # only after its last reader, that view's backward, has run).
+    # only after its last reader, that view's backward, has run), and each
+    # step's loss comes back on the same copy stream once the step is done, so
+    # the compute stream never waits for a copy engine.
     loss_h = torch.empty(len(order), dtype=torch.float32).pin_memory()
     copy_stream = torch.cuda.Stream()
     used = {v: torch.cuda.Event() for v in set(order)}
@@ -398,6 +402,12 @@ def run_lodgs(args, rank: int, world: int):
             copy_stream.wait_event(used[v])
             targets_d[v].copy_(targets_h[v], non_blocking=True)
             ready[i].record(copy_stream)
+
+    def read_loss(i):
+        v = order[i]
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(used[v])
+            loss_h[i:i + 1].copy_(loss_slots[v:v + 1], non_blocking=True)
 
     torch.cuda.synchronize()
     if world > 1:
@@ -413,7 +423,8 @@ def run_lodgs(args, rank: int, world: int):
         stream.wait_event(ready[i])
         replay(v)
         used[v].record(stream)
-        loss_h[i:i + 1].copy_(loss_sum, non_blocking=True)
+        read_loss(i)
+    stream.wait_stream(copy_stream)
     g1.record(stream)
     torch.cuda.synchronize()
     e2e_wall = time.perf_counter() - t0
