@@ -312,7 +312,7 @@ int lodgs_frame_create(lodgs_scene *sc, lodgs_frame **out) {
 #define AL(p, n)                                                                  \
     if (e == cudaSuccess) e = cudaMalloc((void **)&p, std::max<size_t>((size_t)(n), 1) * sizeof(*p));
     AL(f.cnt, C_COUNT) AL(f.d_view, 1) AL(f.sel_rows, M) AL(f.emit_j, S) AL(f.emit_x, S) AL(f.high, S + 1) AL(f.work_off, S + 1)
-    AL(f.block_counts, 1024) AL(f.scan_bsum, SCAN_GRID_MAX) AL(f.sort_hist, SORT_HIST) AL(f.work, 4)
+    AL(f.block_counts, SEL_BLOCK_COUNTS) AL(f.scan_bsum, SCAN_GRID_MAX) AL(f.sort_hist, SORT_HIST) AL(f.work, 4)
     AL(f.up_out, sc->n_upper) AL(f.up_x, sc->n_upper)
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void **)&fr->h_cnt, C_COUNT * sizeof(uint32_t));

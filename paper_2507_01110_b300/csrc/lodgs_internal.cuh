@@ -208,6 +208,7 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
                      cudaStream_t st, bool *result_in_alt);
 // exclusive scan of n (device count) uint32 values in[idx[i]] (idx null: in[i]);
 // total written to *d_total
+constexpr int SEL_BLOCK_COUNTS = 1024;        // per-block counts of the selection passes (buffer entries)
 constexpr int SCAN_GRID = 148;                // scan blocks for short scans
 constexpr int SCAN_GRID_MAX = 148 * 8;        // ... growing with the element count (block-sum buffers)
 int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n,

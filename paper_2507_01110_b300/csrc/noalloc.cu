@@ -24,7 +24,7 @@ constexpr size_t NA_CNT = 0;                                  // C_COUNT counter
 constexpr size_t NA_VIEW = 64;                                // the view (camera constants)
 constexpr size_t NA_BLOCK = 256;                              // 1024 block counts
 static_assert(sizeof(View) <= (NA_BLOCK - NA_VIEW) * 4, "the view must fit its slot");
-constexpr size_t NA_BSUM = NA_BLOCK + 1024;                   // scan block sums
+constexpr size_t NA_BSUM = NA_BLOCK + SEL_BLOCK_COUNTS;       // scan block sums
 constexpr size_t NA_EMIT_J = NA_BSUM + 256;                   // n_spt SPT indices
 constexpr size_t NA_EMIT_X = NA_EMIT_J + NA_MAX_SPT;          // n_spt query values
 constexpr size_t NA_HIGH = NA_EMIT_X + NA_MAX_SPT;            // n_spt + 1 prefix lengths

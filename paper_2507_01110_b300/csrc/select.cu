@@ -20,6 +20,10 @@ namespace {
 
 constexpr int SB = 256;
 constexpr int SEL_GRID = 296;
+// blocks of the SPT passes: one wave of 6 blocks per SM, so that each block
+// walks few tiles (every tile is a few dependent global-load rounds)
+constexpr int SPT_GRID = 148 * 6;
+static_assert(SPT_GRID <= SEL_BLOCK_COUNTS && SEL_GRID <= SEL_BLOCK_COUNTS, "per-block counts buffer");
 
 enum { OUT_NONE = 0, OUT_SELECT = 1, OUT_SPT = 2 };
 
@@ -166,21 +170,44 @@ __global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict
 }
 
 // ---- a2 --------------------------------------------------------------------
+
+// Number of leading entries of arr[0, n) that satisfy `pred`, which must hold
+// on a prefix (a monotone predicate over sorted data), found by one warp: each
+// round tests 32 evenly spaced pivots of the unresolved range and keeps the
+// gap between the last pivot that holds and the first that does not, so a
+// range of n entries takes about log_33(n) dependent load rounds instead of
+// log_2(n).  All lanes of the warp must call it with the same arguments.
+template <typename T, typename Pred>
+__device__ __forceinline__ uint32_t warp_prefix_count(const T *__restrict__ arr, uint32_t n, Pred pred) {
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t a = 0, b = n;                                  // [0, a) hold, [b, n) do not
+    while (b - a > 32) {
+        const uint64_t span = b - a;
+        const uint32_t m = a + (uint32_t)(span * (lane + 1) / 33);         // a < m < b
+        const uint32_t c = __popc(__ballot_sync(0xffffffffu, pred(arr[m])));
+        const uint32_t m_last = a + (uint32_t)(span * c / 33);             // pivot c - 1 (c > 0)
+        const uint32_t m_first = a + (uint32_t)(span * (c + 1) / 33);      // pivot c (c < 32)
+        if (c > 0) a = m_last + 1;
+        if (c < 32) b = m_first;
+    }
+    const bool in = lane < b - a;
+    return a + __popc(__ballot_sync(0xffffffffu, in && pred(arr[a + lane])));
+}
+
+// One warp per emitted SPT: high = the first entry with hi <= x (entries are
+// sorted by descending hi).
 __global__ void __launch_bounds__(SB) k_spt_high(const uint32_t *__restrict__ cnt_in, const uint32_t *__restrict__ emit_j,
                                                  const float *__restrict__ emit_x,
                                                  const uint32_t *__restrict__ spt_base, const float *__restrict__ hi_row,
                                                  uint32_t *__restrict__ high) {
-    uint32_t n = cnt_in[C_NEMIT];
-    for (uint32_t q = blockIdx.x * SB + threadIdx.x; q < n; q += gridDim.x * SB) {
-        uint32_t j = emit_j[q];
-        float x = emit_x[q];
-        uint32_t base = spt_base[j];
-        uint32_t a = 0, b = spt_base[j + 1] - base;
-        while (a < b) {                                     // first entry with hi <= x
-            uint32_t m = a + (b - a) / 2;
-            if (hi_row[base + m] > x) a = m + 1; else b = m;
-        }
-        high[q] = a;
+    const uint32_t n = cnt_in[C_NEMIT];
+    const uint32_t warps = gridDim.x * (SB / 32);
+    for (uint32_t q = blockIdx.x * (SB / 32) + (threadIdx.x >> 5); q < n; q += warps) {
+        const uint32_t j = emit_j[q];
+        const float x = emit_x[q];
+        const uint32_t base = spt_base[j];
+        const uint32_t h = warp_prefix_count(hi_row + base, spt_base[j + 1] - base, [x](float hi) { return hi > x; });
+        if ((threadIdx.x & 31) == 0) high[q] = h;
     }
 }
 
@@ -196,14 +223,9 @@ struct SptTile {
     uint32_t count;
 };
 
-// last emitted SPT whose first item is <= w (global binary search)
+// last emitted SPT whose first item is <= w (work_off ascends from 0); one warp
 __device__ __forceinline__ uint32_t spt_of_item(uint32_t w, uint32_t n_emit, const uint32_t *__restrict__ work_off) {
-    uint32_t a = 0, b = n_emit;
-    while (b - a > 1) {
-        uint32_t m = a + (b - a) / 2;
-        if (work_off[m] <= w) a = m; else b = m;
-    }
-    return a;
+    return warp_prefix_count(work_off, n_emit, [w](uint32_t o) { return o <= w; }) - 1;
 }
 
 __device__ __forceinline__ void stage_tile(SptTile &T, uint32_t q0, uint32_t t_last, uint32_t n_emit,
@@ -248,7 +270,10 @@ __global__ void __launch_bounds__(SB) k_spt_count(const uint32_t *__restrict__ c
     const uint32_t W = cnt_in[C_WORK], n_emit = cnt_in[C_NEMIT];
     uint32_t begin, end;
     grid_chunk(W, begin, end);
-    if (threadIdx.x == 0 && begin < end) s_q = spt_of_item(begin, n_emit, work_off);
+    if (threadIdx.x < 32 && begin < end) {
+        const uint32_t q = spt_of_item(begin, n_emit, work_off);
+        if (threadIdx.x == 0) s_q = q;
+    }
     __syncthreads();
     uint32_t c = 0;
     for (uint32_t t0 = begin; t0 < end; t0 += SB) {
@@ -280,9 +305,9 @@ __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, co
     uint32_t before = block_prefix(bc, s_warp);
     uint32_t begin, end;
     grid_chunk(W, begin, end);
-    if (threadIdx.x == 0) {
-        s_off = n_up + before;
-        if (begin < end) s_q = spt_of_item(begin, n_emit, work_off);
+    if (threadIdx.x < 32) {
+        const uint32_t q = begin < end ? spt_of_item(begin, n_emit, work_off) : 0u;
+        if (threadIdx.x == 0) { s_off = n_up + before; s_q = q; }
     }
     __syncthreads();
     for (uint32_t t0 = begin; t0 < end; t0 += SB) {
@@ -338,7 +363,8 @@ int launch_select_upper(const lodgs_scene *sc, FrameBufs &f, bool with_src, cuda
 }
 
 int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st) {
-    k_spt_high<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_hi, f.high);
+    const unsigned hb = (unsigned)std::min<int64_t>(SPT_GRID, std::max<int64_t>(1, (sc->n_spt + SB / 32 - 1) / (SB / 32)));
+    k_spt_high<<<hb, SB, 0, st>>>(f.cnt, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_hi, f.high);
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
@@ -347,10 +373,10 @@ int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st) {
 int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st) {
     int rc = scan_exclusive(f.high, f.work_off, f.cnt + C_NEMIT, (uint32_t)sc->n_spt, f.scan_bsum, f.cnt + C_WORK, st);
     if (rc) return rc;
-    k_spt_count<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
+    k_spt_count<<<SPT_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
                                          f.block_counts);
     count_launches(1);
-    k_spt_write<<<SEL_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
+    k_spt_write<<<SPT_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
                                          f.block_counts, f.sel_rows, with_src ? f.sel_src : nullptr,
                                          with_src ? f.emit_src : nullptr);
     count_launches(1);
