@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "../../include/lodgs.h"
 
@@ -167,6 +168,31 @@ struct FrameBufs {
 
 void set_error(const std::string &msg);
 void count_launches(int n);     // process-wide tally of this library's kernel launches
+
+// Programmatic dependent launch.  A kernel launched through pdl_launch may be
+// scheduled while the kernel before it on the stream is still draining its
+// last blocks; it calls pdl_wait() as its first statement, which returns once
+// that kernel has completed and its memory operations are visible.  So only
+// the launch latency overlaps the predecessor's tail: every global read and
+// write still follows it.  (After a copy, a memset or an event wait the launch
+// is ordered as usual; without a programmatic predecessor pdl_wait returns at
+// once.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 bool fault_hit(int site);       // an armed injected fault at `site` fires (host side only)
 int cuda_fail(cudaError_t e, const char *what);
 #define LODGS_CUDA(call)                                       \

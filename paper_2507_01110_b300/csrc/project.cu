@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
                                                  float4 *__restrict__ sp_b, float4 *__restrict__ sp_c,
                                                  uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
                                                  uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles) {
+    pdl_wait();
     const CamK &k = view->k;
     // selections beyond the workspace are not rendered: the frame reports a capacity error
     uint32_t n = cnt[C_NSEL];
@@ -270,6 +271,7 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
                                                      const uint32_t *__restrict__ ntiles,
                                                      const float *__restrict__ g2d, float *__restrict__ out,
                                                      int dense, uint32_t out_cap) {
+    pdl_wait();
     constexpr int RS = rec_stride(DEG), SP = RS + 1;
     __shared__ float s_rows[PB / 32][32 * SP];
     const CamK &k = view->k;
@@ -442,8 +444,8 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
 
 int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaStream_t st) {
 #define LAUNCH_PROJ(D)                                                                                     \
-    k_project<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.d_view, f.cnt, f.cap_sel, f.sp_a, \
-                                           f.sp_b, f.sp_c, f.dkey, f.dval, f.rect, f.ntiles)
+    LODGS_CUDA(pdl_launch(k_project<D>, PROJ_GRID, PB, st, rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.d_view, f.cnt, f.cap_sel, f.sp_a, \
+                                           f.sp_b, f.sp_c, f.dkey, f.dval, f.rect, f.ntiles))
     switch (sc->sh_degree) {
         case 0: LAUNCH_PROJ(0); break;
         case 1: LAUNCH_PROJ(1); break;
@@ -468,8 +470,8 @@ int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs 
     }
     const uint32_t cap = (uint32_t)std::min<int64_t>(std::max<int64_t>(grad_capacity, 0), UINT32_MAX);
 #define LAUNCH_PBWD(D)                                                                                     \
-    k_project_bwd<D><<<PROJ_GRID, PB, 0, st>>>(rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.sel_rows, f.d_view, \
-                                               f.cnt, f.ntiles, f.g2d, grad_rows, dense, cap)
+    LODGS_CUDA(pdl_launch(k_project_bwd<D>, PROJ_GRID, PB, st, rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.sel_rows, f.d_view, \
+                                               f.cnt, f.ntiles, f.g2d, grad_rows, dense, cap))
     switch (sc->sh_degree) {
         case 0: LAUNCH_PBWD(0); break;
         case 1: LAUNCH_PBWD(1); break;

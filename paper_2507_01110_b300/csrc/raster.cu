@@ -134,6 +134,7 @@ __global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restri
                        const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b,
                        const uint32_t *__restrict__ pair_off, uint32_t *__restrict__ cnt, uint64_t cap_pairs,
                        int TX, uint32_t n_tiles, uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    pdl_wait();
     // pairs beyond the workspace (or an earlier overflow) are not emitted: capacity error
     uint32_t P = cnt[C_NPAIR];
     const bool over = P > cap_pairs || (cnt[C_STATUS] & ST_CAPACITY) ||
@@ -170,6 +171,7 @@ __global__ void k_emit(const uint32_t *__restrict__ order, const uint2 *__restri
 
 __global__ void k_ranges(const uint32_t *__restrict__ pkey, uint32_t *__restrict__ cnt, uint32_t n_tiles,
                          uint2 *__restrict__ ranges) {
+    pdl_wait();
     uint32_t n = cnt[C_NPAIR_EFF];
     for (uint32_t p = blockIdx.x * RB + threadIdx.x; p < n; p += gridDim.x * RB) {
         uint32_t t = pkey[p];
@@ -208,6 +210,7 @@ __global__ void __launch_bounds__(RB) k_emit_count(const uint32_t *__restrict__ 
                                                    const uint2 *__restrict__ rect, const float4 *__restrict__ sp_a,
                                                    const float4 *__restrict__ sp_b, uint32_t *__restrict__ cnt,
                                                    int TX, uint32_t *__restrict__ tile_cnt) {
+    pdl_wait();
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     if (*reinterpret_cast<const unsigned long long *>(cnt + C_NPAIR64) > 0xffffffffull) {   // 32-bit pair indices
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr((uint32_t *)&cnt[C_STATUS], ST_CAPACITY);
@@ -237,6 +240,7 @@ constexpr int TO_THREADS = 1024;
 __global__ void __launch_bounds__(TO_THREADS) k_tile_offsets(uint32_t *__restrict__ tile_cnt, uint32_t n_tiles,
                                                              uint64_t cap_pairs, uint32_t *__restrict__ cnt,
                                                              uint2 *__restrict__ ranges) {
+    pdl_wait();
     __shared__ uint32_t s_warp[32];
     __shared__ unsigned long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(RB) k_emit_scatter(const uint32_t *__restrict_
                                                      const uint32_t *__restrict__ dkey, const uint32_t *__restrict__ cnt,
                                                      int TX, uint32_t *__restrict__ cursor, uint32_t *__restrict__ pkey,
                                                      uint32_t *__restrict__ pval) {
+    pdl_wait();
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     const uint32_t P = cnt[C_NPAIR], n = cnt[C_NSEL_EFF];
     const int lane = threadIdx.x & 31;
@@ -392,6 +397,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint2 *__restric
                                                           uint32_t *__restrict__ tile_cnt,
                                                           const uint32_t *__restrict__ cnt, uint32_t *pkey,
                                                           uint32_t *pval, unsigned long long *scratch) {
+    pdl_wait();
     __shared__ unsigned long long s_k[TS_SMEM];
     const uint32_t t = blockIdx.x;
     if (threadIdx.x == 0) tile_cnt[t] = 0;               // counters start at zero for the next render
@@ -595,6 +601,7 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
             const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c, const uint32_t *__restrict__ cnt, int W,
             int H, int TX, const View *__restrict__ view, float *__restrict__ image,
             unsigned long long *__restrict__ work) {
+    pdl_wait();
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
     __shared__ uint8_t s_m[BATCH];
@@ -707,6 +714,7 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
                 const uint32_t *__restrict__ cnt, int W, int H, int TX, const float *__restrict__ image,
                 const float *__restrict__ dL_dimg, float *__restrict__ g2d, unsigned long long *__restrict__ work,
                 const void *__restrict__ target, float l1_scale, float *__restrict__ loss_sum) {
+    pdl_wait();
     constexpr int NT = TILE_PIX / BP, NW = NT / 32;
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
@@ -895,18 +903,18 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         int rc = scan_exclusive(f.ntiles, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
                                 f.cnt + C_NPAIR, st);     // rectangle pairs per selected Gaussian
         if (rc) return rc;
-        k_emit_count<<<EGRID, RB, 0, st>>>(f.pair_off, f.rect, f.sp_a, f.sp_b, f.cnt, k.TX, f.tile_cnt);
-        k_tile_offsets<<<1, TO_THREADS, 0, st>>>(f.tile_cnt, (uint32_t)n_tiles, f.cap_pairs, f.cnt, f.ranges);
+        LODGS_CUDA(pdl_launch(k_emit_count, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.cnt, k.TX, f.tile_cnt));
+        LODGS_CUDA(pdl_launch(k_tile_offsets, 1, TO_THREADS, st, f.tile_cnt, (uint32_t)n_tiles, f.cap_pairs, f.cnt, f.ranges));
         count_launches(2);
         sm.mark(LODGS_STAGE_COUNT, 1, st);
         sm.mark(LODGS_STAGE_EMIT, 0, st);
-        k_emit_scatter<<<EGRID, RB, 0, st>>>(f.pair_off, f.rect, f.sp_a, f.sp_b, f.dkey, f.cnt, k.TX, f.tile_cnt,
-                                             f.pkey, f.pval);
+        LODGS_CUDA(pdl_launch(k_emit_scatter, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.dkey, f.cnt, k.TX, f.tile_cnt,
+                                             f.pkey, f.pval));
         count_launches(1);
         sm.mark(LODGS_STAGE_EMIT, 1, st);
         sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
-        k_tile_sort<<<(unsigned)n_tiles, TS_THREADS, 0, st>>>(f.ranges, f.tile_cnt, f.cnt, f.pkey, f.pval,
-                                                              f.pscratch);
+        LODGS_CUDA(pdl_launch(k_tile_sort, (unsigned)n_tiles, TS_THREADS, st, f.ranges, f.tile_cnt, f.cnt, f.pkey, f.pval,
+                                                              f.pscratch));
         count_launches(1);
         sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
         f.sorted_pval = f.pval;
@@ -924,8 +932,8 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         rc = scan_exclusive(f.ntiles, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
                             f.cnt + C_NPAIR, st, order);  // tile counts in depth order
         if (rc) return rc;
-        k_emit<<<RGRID, RB, 0, st>>>(order, f.rect, f.sp_a, f.sp_b, f.pair_off, f.cnt, f.cap_pairs, k.TX,
-                                     (uint32_t)n_tiles, f.pkey, f.pval);
+        LODGS_CUDA(pdl_launch(k_emit, RGRID, RB, st, order, f.rect, f.sp_a, f.sp_b, f.pair_off, f.cnt, f.cap_pairs, k.TX,
+                                     (uint32_t)n_tiles, f.pkey, f.pval));
         count_launches(1);
         sm.mark(LODGS_STAGE_EMIT, 1, st);
         sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
@@ -935,14 +943,14 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         const uint32_t *skey = alt ? f.pkey_alt : f.pkey;
         f.sorted_pval = alt ? f.pval_alt : f.pval;
         LODGS_CUDA(cudaMemsetAsync(f.ranges, 0, n_tiles * sizeof(uint2), st));
-        k_ranges<<<RGRID, RB, 0, st>>>(skey, f.cnt, (uint32_t)n_tiles, f.ranges);
+        LODGS_CUDA(pdl_launch(k_ranges, RGRID, RB, st, skey, f.cnt, (uint32_t)n_tiles, f.ranges));
         count_launches(1);
         sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
         sm.mark(LODGS_STAGE_BLEND, 0, st);
     }
     LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));
-    (f.count_work ? k_blend<true> : k_blend<false>)<<<(unsigned)n_tiles, BNT, 0, st>>>(
-        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work);
+    LODGS_CUDA(pdl_launch((f.count_work ? k_blend<true> : k_blend<false>), (unsigned)n_tiles, BNT, st,
+        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work));
     count_launches(1);
     sm.mark(LODGS_STAGE_BLEND, 1, st);
     LODGS_CUDA(cudaGetLastError());
@@ -959,12 +967,12 @@ int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, cons
         LODGS_CUDA(cudaMemsetAsync(loss_sum, 0, sizeof(float), st));
         auto kern = target_u8 ? (f.count_work ? k_blend_bwd<true, BWD_PIX, 2> : k_blend_bwd<false, BWD_PIX, 2>)
                               : (f.count_work ? k_blend_bwd<true, BWD_PIX, 1> : k_blend_bwd<false, BWD_PIX, 1>);
-        kern<<<nb, nt, 0, st>>>(f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image,
-                                nullptr, f.g2d, f.work, target, l1_scale, loss_sum);
+        LODGS_CUDA(pdl_launch(kern, nb, nt, st, f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image,
+                                nullptr, f.g2d, f.work, target, l1_scale, loss_sum));
     } else {
-        (f.count_work ? k_blend_bwd<true, BWD_PIX, 0> : k_blend_bwd<false, BWD_PIX, 0>)<<<nb, nt, 0, st>>>(
+        LODGS_CUDA(pdl_launch((f.count_work ? k_blend_bwd<true, BWD_PIX, 0> : k_blend_bwd<false, BWD_PIX, 0>), nb, nt, st,
             f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, dL_dimage, f.g2d, f.work,
-            nullptr, 0.f, nullptr);
+            nullptr, 0.f, nullptr));
     }
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());

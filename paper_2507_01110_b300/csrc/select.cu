@@ -101,6 +101,7 @@ __device__ __forceinline__ uint32_t block_prefix(const uint32_t *__restrict__ co
 __global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict__ up, uint32_t U,
                                                     const View *__restrict__ view, uint32_t *__restrict__ bc,
                                                     uint8_t *__restrict__ up_out, float *__restrict__ up_x) {
+    pdl_wait();
     const CamK &k = view->k;
     __shared__ uint32_t s_warp[32];
     uint32_t begin, end;
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict
                                                     const float *__restrict__ up_x, uint32_t *__restrict__ sel_rows,
                                                     uint32_t *__restrict__ sel_src, uint32_t *__restrict__ emit_j,
                                                     float *__restrict__ emit_x, uint32_t *__restrict__ cnt) {
+    pdl_wait();
     const CamK &k = view->k;
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_off_sel, s_off_emit;
@@ -200,6 +202,7 @@ __global__ void __launch_bounds__(SB) k_spt_high(const uint32_t *__restrict__ cn
                                                  const float *__restrict__ emit_x,
                                                  const uint32_t *__restrict__ spt_base, const float *__restrict__ hi_row,
                                                  uint32_t *__restrict__ high) {
+    pdl_wait();
     const uint32_t n = cnt_in[C_NEMIT];
     const uint32_t warps = gridDim.x * (SB / 32);
     for (uint32_t q = blockIdx.x * (SB / 32) + (threadIdx.x >> 5); q < n; q += warps) {
@@ -264,6 +267,7 @@ __global__ void __launch_bounds__(SB) k_spt_count(const uint32_t *__restrict__ c
                                                   const uint32_t *__restrict__ emit_j, const float *__restrict__ emit_x,
                                                   const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
                                                   uint32_t *__restrict__ bc) {
+    pdl_wait();
     __shared__ uint32_t s_warp[32];
     __shared__ SptTile T;
     __shared__ uint32_t s_q;
@@ -298,6 +302,7 @@ __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, co
                                                   const uint32_t *__restrict__ bc, uint32_t *__restrict__ sel_rows,
                                                   uint32_t *__restrict__ sel_src,
                                                   const uint32_t *__restrict__ emit_src) {
+    pdl_wait();
     __shared__ uint32_t s_warp[32];
     __shared__ SptTile T;
     __shared__ uint32_t s_off, s_q;
@@ -335,6 +340,7 @@ __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, co
 }
 
 __global__ void k_set_view(View v, View *__restrict__ dst) {
+    pdl_wait();
     const uint32_t *s = reinterpret_cast<const uint32_t *>(&v);
     uint32_t *d = reinterpret_cast<uint32_t *>(dst);
     for (uint32_t i = threadIdx.x; i < sizeof(View) / 4; i += blockDim.x) d[i] = s[i];
@@ -345,7 +351,7 @@ __global__ void k_set_view(View v, View *__restrict__ dst) {
 // The view goes to the device as a kernel argument: the copy is asynchronous,
 // needs no host staging buffer, and is ordered on the stream like the kernels.
 int launch_set_view(const View &v, View *dst, cudaStream_t st) {
-    k_set_view<<<1, 32, 0, st>>>(v, dst);
+    LODGS_CUDA(pdl_launch(k_set_view, 1, 32, st, v, dst));
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
@@ -353,10 +359,10 @@ int launch_set_view(const View &v, View *dst, cudaStream_t st) {
 
 int launch_select_upper(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st) {
     uint32_t U = (uint32_t)sc->n_upper;
-    k_upper_count<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, f.d_view, f.block_counts, f.up_out, f.up_x);
+    LODGS_CUDA(pdl_launch(k_upper_count, SEL_GRID, SB, st, sc->d_upper, U, f.d_view, f.block_counts, f.up_out, f.up_x));
     count_launches(1);
-    k_upper_write<<<SEL_GRID, SB, 0, st>>>(sc->d_upper, U, f.d_view, f.block_counts, f.up_out, f.up_x, f.sel_rows,
-                                           with_src ? f.sel_src : nullptr, f.emit_j, f.emit_x, f.cnt);
+    LODGS_CUDA(pdl_launch(k_upper_write, SEL_GRID, SB, st, sc->d_upper, U, f.d_view, f.block_counts, f.up_out, f.up_x, f.sel_rows,
+                                           with_src ? f.sel_src : nullptr, f.emit_j, f.emit_x, f.cnt));
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
@@ -364,7 +370,7 @@ int launch_select_upper(const lodgs_scene *sc, FrameBufs &f, bool with_src, cuda
 
 int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st) {
     const unsigned hb = (unsigned)std::min<int64_t>(SPT_GRID, std::max<int64_t>(1, (sc->n_spt + SB / 32 - 1) / (SB / 32)));
-    k_spt_high<<<hb, SB, 0, st>>>(f.cnt, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_hi, f.high);
+    LODGS_CUDA(pdl_launch(k_spt_high, hb, SB, st, f.cnt, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_hi, f.high));
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
@@ -373,12 +379,12 @@ int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st) {
 int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st) {
     int rc = scan_exclusive(f.high, f.work_off, f.cnt + C_NEMIT, (uint32_t)sc->n_spt, f.scan_bsum, f.cnt + C_WORK, st);
     if (rc) return rc;
-    k_spt_count<<<SPT_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
-                                         f.block_counts);
+    LODGS_CUDA(pdl_launch(k_spt_count, SPT_GRID, SB, st, f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
+                                         f.block_counts));
     count_launches(1);
-    k_spt_write<<<SPT_GRID, SB, 0, st>>>(f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
+    LODGS_CUDA(pdl_launch(k_spt_write, SPT_GRID, SB, st, f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
                                          f.block_counts, f.sel_rows, with_src ? f.sel_src : nullptr,
-                                         with_src ? f.emit_src : nullptr);
+                                         with_src ? f.emit_src : nullptr));
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;

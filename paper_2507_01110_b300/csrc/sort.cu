@@ -34,6 +34,7 @@ __device__ __forceinline__ void chunk_range(uint32_t n, uint32_t &begin, uint32_
 __global__ void __launch_bounds__(ST_THREADS) k_radix_upsweep(const uint32_t *__restrict__ keys,
                                                               const uint32_t *__restrict__ d_n, int shift,
                                                               uint32_t mask, uint32_t *__restrict__ hist) {
+    pdl_wait();
     __shared__ uint32_t s_cnt[ST_WARPS][RADIX];
     const int tid = threadIdx.x, warp = tid >> 5;
     for (int i = tid; i < ST_WARPS * RADIX; i += ST_THREADS) (&s_cnt[0][0])[i] = 0;
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_radix_upsweep(const uint32_t *__
 // are loaded before any is written back, so the loads overlap.
 constexpr int DS_CHUNKS = (SORT_GRID_MAX + 31) / 32;
 __global__ void __launch_bounds__(256) k_digit_scan(uint32_t *__restrict__ hist, int G, uint32_t *__restrict__ totals) {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
     uint32_t *h = hist + (size_t)d * G;
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_radix_downsweep(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ d_n, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals) {
+    pdl_wait();
     __shared__ uint32_t s_off[RADIX];
     __shared__ uint32_t s_tot[RADIX];
     __shared__ uint32_t s_w[ST_WARPS][RADIX];
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__re
                                                             const uint32_t *__restrict__ idx,
                                                             const uint32_t *__restrict__ d_n,
                                                             uint32_t *__restrict__ block_sums) {
+    pdl_wait();
     __shared__ uint32_t s_warp[32];
     uint32_t begin, end;
     scan_chunk(*d_n, begin, end);
@@ -206,6 +210,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *in, co
                                                           uint32_t *out, const uint32_t *__restrict__ d_n,
                                                           const uint32_t *__restrict__ block_sums,
                                                           uint32_t *d_total) {
+    pdl_wait();
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -283,11 +288,11 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
         uint32_t *ko = alt ? keys : keys_alt;
         uint32_t *vo = alt ? vals : vals_alt;
         uint32_t *totals = hist + RADIX * G;
-        k_radix_upsweep<<<G, ST_THREADS, 0, st>>>(ki, d_n, shift, mask, hist);
+        LODGS_CUDA(pdl_launch(k_radix_upsweep, G, ST_THREADS, st, ki, d_n, shift, mask, hist));
         count_launches(1);
-        k_digit_scan<<<RADIX / 8, 256, 0, st>>>(hist, G, totals);
+        LODGS_CUDA(pdl_launch(k_digit_scan, RADIX / 8, 256, st, hist, G, totals));
         count_launches(1);
-        k_radix_downsweep<<<G, ST_THREADS, 0, st>>>(ki, vi, ko, vo, d_n, shift, mask, hist, totals);
+        LODGS_CUDA(pdl_launch(k_radix_downsweep, G, ST_THREADS, st, ki, vi, ko, vo, d_n, shift, mask, hist, totals));
         count_launches(1);
         alt = !alt;
     }
@@ -299,16 +304,16 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
 int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n, uint32_t *block_sums,
                    uint32_t *d_total, cudaStream_t st, const uint32_t *idx) {
     if (max_n <= SCAN_ONE_BLOCK) {                 // short scans: one block, no block sums
-        k_scan_down<<<1, SC_THREADS, 0, st>>>(in, idx, out, d_n, block_sums, d_total);
+        LODGS_CUDA(pdl_launch(k_scan_down, 1, SC_THREADS, st, in, idx, out, d_n, block_sums, d_total));
         count_launches(1);
         LODGS_CUDA(cudaGetLastError());
         return LODGS_OK;
     }
     // long scans: about four tiles per block, up to 8 blocks per SM
     const int G = (int)std::min<uint64_t>(SCAN_GRID_MAX, std::max<uint64_t>(SCAN_GRID, (uint64_t)max_n / (SC_TILE * 4)));
-    k_scan_reduce<<<G, SC_THREADS, 0, st>>>(in, idx, d_n, block_sums);
+    LODGS_CUDA(pdl_launch(k_scan_reduce, G, SC_THREADS, st, in, idx, d_n, block_sums));
     count_launches(1);
-    k_scan_down<<<G, SC_THREADS, 0, st>>>(in, idx, out, d_n, block_sums, d_total);
+    LODGS_CUDA(pdl_launch(k_scan_down, G, SC_THREADS, st, in, idx, out, d_n, block_sums, d_total));
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
