@@ -236,45 +236,64 @@ __global__ void __launch_bounds__(RB) k_emit_count(const uint32_t *__restrict__ 
 // One block: exclusive scan of the tile counts.  Writes the tile ranges, turns
 // the counts into scatter cursors (the tile's first slot) and records the kept
 // pair total, flagging a capacity error when it exceeds the pair buffers.
+// Each pass loads TO_K chunks of TO_THREADS consecutive counts at once (one
+// load latency per pass instead of one per chunk), scans each chunk within
+// its warps, scans the warp totals of every chunk in one warp per chunk, and
+// adds the chunks' totals in order.
 constexpr int TO_THREADS = 1024;
+constexpr int TO_K = 8;
 __global__ void __launch_bounds__(TO_THREADS) k_tile_offsets(uint32_t *__restrict__ tile_cnt, uint32_t n_tiles,
                                                              uint64_t cap_pairs, uint32_t *__restrict__ cnt,
                                                              uint2 *__restrict__ ranges) {
     pdl_wait();
-    __shared__ uint32_t s_warp[32];
+    constexpr int NWT = TO_THREADS / 32;
+    static_assert(TO_K <= NWT, "one warp scans each chunk's warp totals");
+    __shared__ uint32_t s_warp[TO_K][NWT];
     __shared__ unsigned long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_carry = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < n_tiles; base += TO_THREADS) {
-        const uint32_t t = base + tid;
-        const uint32_t v = t < n_tiles ? tile_cnt[t] : 0u;
-        uint32_t x = v;
+    for (uint32_t base = 0; base < n_tiles; base += TO_K * TO_THREADS) {
+        uint32_t v[TO_K], x[TO_K];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+        for (int i = 0; i < TO_K; ++i) {
+            const uint32_t t = base + i * TO_THREADS + tid;
+            v[i] = t < n_tiles ? tile_cnt[t] : 0u;
         }
-        if (lane == 31) s_warp[warp] = x;
+#pragma unroll
+        for (int i = 0; i < TO_K; ++i) {
+            x[i] = v[i];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x[i], o);
+                if (lane >= o) x[i] += y;
+            }
+            if (lane == 31) s_warp[i][warp] = x[i];
+        }
         __syncthreads();
-        if (warp == 0) {
-            uint32_t w = s_warp[lane];
+        if (warp < TO_K) {
+            uint32_t w = s_warp[warp][lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
                 if (lane >= o) w += y;
             }
-            s_warp[lane] = w;
+            s_warp[warp][lane] = w;
         }
         __syncthreads();
-        const unsigned long long off = s_carry + (warp ? s_warp[warp - 1] : 0u) + x - v;
-        if (t < n_tiles) {
-            const uint32_t o32 = off > 0xffffffffull ? 0xffffffffu : (uint32_t)off;
-            ranges[t] = make_uint2(o32, o32 + v);
-            tile_cnt[t] = o32;
+        unsigned long long chunk = s_carry;
+#pragma unroll
+        for (int i = 0; i < TO_K; ++i) {
+            const uint32_t t = base + i * TO_THREADS + tid;
+            const unsigned long long off = chunk + (warp ? s_warp[i][warp - 1] : 0u) + x[i] - v[i];
+            if (t < n_tiles) {
+                const uint32_t o32 = off > 0xffffffffull ? 0xffffffffu : (uint32_t)off;
+                ranges[t] = make_uint2(o32, o32 + v[i]);
+                tile_cnt[t] = o32;
+            }
+            chunk += s_warp[i][NWT - 1];
         }
         __syncthreads();
-        if (tid == 0) s_carry += s_warp[31];
+        if (tid == 0) s_carry = chunk;
         __syncthreads();
     }
     if (tid == 0) {
