@@ -132,7 +132,7 @@ void free_frame_bufs(FrameBufs &f) {
     void *ps[] = {f.cnt, f.d_view, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
                   f.sort_hist, f.sp_a, f.sp_b, f.sp_c, f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.rect, f.ntiles,
                   f.pair_off, f.g2d, f.pkey, f.pval, f.pscratch, f.pkey_alt, f.pval_alt, f.ranges, f.tile_cnt,
-                  f.work,
+                  f.tile_order, f.work,
                   f.sel_src, f.emit_src, f.up_out, f.up_x};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -400,9 +400,10 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     if (int r = ensure_pairs(fr, fr->want_pairs)) return r;
     uint64_t n_tiles = (uint64_t)fr->k.TX * fr->k.TY;
     if (n_tiles > fr->f.cap_tiles || !fr->f.ranges) {
-        uint64_t c = fr->f.cap_tiles, c2 = fr->f.cap_tiles;
+        uint64_t c = fr->f.cap_tiles, c2 = fr->f.cap_tiles, c3 = fr->f.cap_tiles;
         if (int r = grow(fr->f.ranges, c, n_tiles)) return r;
         if (int r = grow(fr->f.tile_cnt, c2, n_tiles)) return r;
+        if (int r = grow(fr->f.tile_order, c3, n_tiles)) return r;
         LODGS_CUDA(cudaMemsetAsync(fr->f.tile_cnt, 0, n_tiles * sizeof(uint32_t), st));   // zero between renders
         fr->f.cap_tiles = c;
     }

@@ -158,6 +158,7 @@ struct FrameBufs {
     // tiles (capacity cap_tiles)
     uint2 *ranges = nullptr;
     uint32_t *tile_cnt = nullptr;     // kept pairs per tile, then scatter cursors; zero between renders
+    uint32_t *tile_order = nullptr;   // tiles by pair count, largest first: the blends' block -> tile map
     unsigned long long *work = nullptr;   // 4 counters, see lodgs_frame_work
     bool count_work = false;              // blends tally the work counters (profiling frames)
     int ordering = 0;                     // ORDER_*: how pairs are put in (tile, depth, index) order

@@ -308,6 +308,70 @@ __global__ void __launch_bounds__(TO_THREADS) k_tile_offsets(uint32_t *__restric
     }
 }
 
+// Longest-first tile order for the blends.  Blocks are handed to SMs in index
+// order as slots free up (greedy list scheduling); in raster order a few long
+// tiles that start late keep some SMs busy while the rest idle.  Tiles are
+// bucketed by pair count on a log scale (two buckets per power of two) and
+// listed largest bucket first; the order within a bucket is arbitrary, as a
+// tile's result does not depend on which block computes it.  One block; each
+// pass loads TOR_K chunks of counts at once.
+constexpr int TOR_THREADS = 1024, TOR_K = 8, TOR_BUCKETS = 64;
+__device__ __forceinline__ uint32_t order_bucket(uint32_t n) {
+    uint32_t key = n;                                          // 0, 1
+    if (n >= 2) {
+        const uint32_t l = 31 - __clz(n);                      // 1..31
+        key = 2 * l + ((n >> (l - 1)) & 1u);                   // 2..63
+    }
+    return (TOR_BUCKETS - 1) - key;                            // largest counts first
+}
+
+__global__ void __launch_bounds__(TOR_THREADS) k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                                            uint32_t *__restrict__ order) {
+    pdl_wait();
+    __shared__ uint32_t s_h[TOR_BUCKETS];
+    const int tid = threadIdx.x;
+    if (tid < TOR_BUCKETS) s_h[tid] = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < n_tiles; base += TOR_K * TOR_THREADS) {
+        uint2 r[TOR_K];
+#pragma unroll
+        for (int i = 0; i < TOR_K; ++i) {
+            const uint32_t t = base + i * TOR_THREADS + tid;
+            r[i] = t < n_tiles ? ranges[t] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < TOR_K; ++i)
+            if (base + i * TOR_THREADS + tid < n_tiles) atomicAdd(&s_h[order_bucket(r[i].y - r[i].x)], 1u);
+    }
+    __syncthreads();
+    if (tid < 32) {                                            // exclusive scan of the 64 buckets
+        const uint32_t a = s_h[2 * tid], b = s_h[2 * tid + 1];
+        uint32_t x = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (tid >= o) x += y;
+        }
+        const uint32_t ex = x - (a + b);
+        s_h[2 * tid] = ex;
+        s_h[2 * tid + 1] = ex + a;
+    }
+    __syncthreads();
+    for (uint32_t base = 0; base < n_tiles; base += TOR_K * TOR_THREADS) {
+        uint2 r[TOR_K];
+#pragma unroll
+        for (int i = 0; i < TOR_K; ++i) {
+            const uint32_t t = base + i * TOR_THREADS + tid;
+            r[i] = t < n_tiles ? ranges[t] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < TOR_K; ++i) {
+            const uint32_t t = base + i * TOR_THREADS + tid;
+            if (t < n_tiles) order[atomicAdd(&s_h[order_bucket(r[i].y - r[i].x)], 1u)] = t;
+        }
+    }
+}
+
 // Scatter the kept pairs into their tiles' slots (in any order within a tile:
 // the per-tile sort fixes it): depth key and selected index.
 __global__ void __launch_bounds__(RB) k_emit_scatter(const uint32_t *__restrict__ pair_off,
@@ -619,7 +683,7 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
     k_blend(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval, const float4 *__restrict__ sp_a,
             const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c, const uint32_t *__restrict__ cnt, int W,
             int H, int TX, const View *__restrict__ view, float *__restrict__ image,
-            unsigned long long *__restrict__ work) {
+            unsigned long long *__restrict__ work, const uint32_t *__restrict__ tile_order) {
     pdl_wait();
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
@@ -627,7 +691,7 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
     __shared__ uint8_t s_list[NWARP][BATCH];
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     const float bg0 = view->bg[0], bg1 = view->bg[1], bg2 = view->bg[2];
-    const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int tile = (int)tile_order[blockIdx.x], tid = threadIdx.x, lane = tid & 31;
     const int tx0 = (tile % TX) * TILE, ty0 = (tile / TX) * TILE;
     const BlockPix bp = block_pix(tile, TX, tid);
     float yc[PIX], T[PIX], c0[PIX], c1[PIX], c2[PIX];
@@ -732,7 +796,8 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
                 const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c,
                 const uint32_t *__restrict__ cnt, int W, int H, int TX, const float *__restrict__ image,
                 const float *__restrict__ dL_dimg, float *__restrict__ g2d, unsigned long long *__restrict__ work,
-                const void *__restrict__ target, float l1_scale, float *__restrict__ loss_sum) {
+                const void *__restrict__ target, float l1_scale, float *__restrict__ loss_sum,
+                const uint32_t *__restrict__ tile_order) {
     pdl_wait();
     constexpr int NT = TILE_PIX / BP, NW = NT / 32;
     __shared__ float4 s_a[BATCH], s_b[BATCH];
@@ -742,7 +807,7 @@ __global__ void __launch_bounds__(TILE_PIX / BP)
     __shared__ uint8_t s_m[BATCH];
     __shared__ uint8_t s_list[NW][BATCH];
     if (cnt[C_STATUS] & ST_CAPACITY) return;
-    const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int tile = (int)tile_order[blockIdx.x], tid = threadIdx.x, lane = tid & 31;
     const int tx0 = (tile % TX) * TILE, ty0 = (tile / TX) * TILE;
     const BlockPix bp = block_pix(tile, TX, tid);
     // blocks this warp covers: (w & 1, (w >> 1) + k / 2) for its pixel rows k
@@ -968,9 +1033,11 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         sm.mark(LODGS_STAGE_BLEND, 0, st);
     }
     LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));
+    LODGS_CUDA(pdl_launch(k_tile_order, 1, TOR_THREADS, st, f.ranges, (uint32_t)n_tiles, f.tile_order));
     LODGS_CUDA(pdl_launch((f.count_work ? k_blend<true> : k_blend<false>), (unsigned)n_tiles, BNT, st,
-        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work));
-    count_launches(1);
+        f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work,
+        f.tile_order));
+    count_launches(2);
     sm.mark(LODGS_STAGE_BLEND, 1, st);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
@@ -987,11 +1054,11 @@ int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, cons
         auto kern = target_u8 ? (f.count_work ? k_blend_bwd<true, BWD_PIX, 2> : k_blend_bwd<false, BWD_PIX, 2>)
                               : (f.count_work ? k_blend_bwd<true, BWD_PIX, 1> : k_blend_bwd<false, BWD_PIX, 1>);
         LODGS_CUDA(pdl_launch(kern, nb, nt, st, f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image,
-                                nullptr, f.g2d, f.work, target, l1_scale, loss_sum));
+                                nullptr, f.g2d, f.work, target, l1_scale, loss_sum, f.tile_order));
     } else {
         LODGS_CUDA(pdl_launch((f.count_work ? k_blend_bwd<true, BWD_PIX, 0> : k_blend_bwd<false, BWD_PIX, 0>), nb, nt, st,
             f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, dL_dimage, f.g2d, f.work,
-            nullptr, 0.f, nullptr));
+            nullptr, 0.f, nullptr, f.tile_order));
     }
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
