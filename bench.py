@@ -463,8 +463,8 @@ def run_lodgs(args, rank: int, world: int):
 OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB = 6, 11, 34
 # DRAM bytes (read + write) per k_blend_bwd launch, mean over the 32 views of
 # this workload, from one ncu capture (profiles/launches_fwd_bwd_1080p_2Mleaves.md)
-BLEND_BWD_DRAM_BYTES = 39.2e6
-BLEND_BWD_ISSUE_ACTIVE = 0.768    # smsp__issue_active of the same kernel, one view (ncu --set full)
+BLEND_BWD_DRAM_BYTES = 39.3e6
+BLEND_BWD_ISSUE_ACTIVE = 0.809    # smsp__issue_active of the same kernel, one view (ncu --set full)
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 
