@@ -479,10 +479,11 @@ __device__ void merge_runs(const TileKeys &src, const TileKeys &dst, uint32_t a0
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint2 *__restrict__ ranges,
                                                           uint32_t *__restrict__ tile_cnt,
                                                           const uint32_t *__restrict__ cnt, uint32_t *pkey,
-                                                          uint32_t *pval, unsigned long long *scratch) {
+                                                          uint32_t *pval, unsigned long long *scratch,
+                                                          const uint32_t *__restrict__ tile_order) {
     pdl_wait();
     __shared__ unsigned long long s_k[TS_SMEM];
-    const uint32_t t = blockIdx.x;
+    const uint32_t t = tile_order[blockIdx.x];
     if (threadIdx.x == 0) tile_cnt[t] = 0;               // counters start at zero for the next render
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     const uint2 rg = ranges[t];
@@ -989,7 +990,8 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         if (rc) return rc;
         LODGS_CUDA(pdl_launch(k_emit_count, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.cnt, k.TX, f.tile_cnt));
         LODGS_CUDA(pdl_launch(k_tile_offsets, 1, TO_THREADS, st, f.tile_cnt, (uint32_t)n_tiles, f.cap_pairs, f.cnt, f.ranges));
-        count_launches(2);
+        LODGS_CUDA(pdl_launch(k_tile_order, 1, TOR_THREADS, st, f.ranges, (uint32_t)n_tiles, f.tile_order));
+        count_launches(3);
         sm.mark(LODGS_STAGE_COUNT, 1, st);
         sm.mark(LODGS_STAGE_EMIT, 0, st);
         LODGS_CUDA(pdl_launch(k_emit_scatter, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.dkey, f.cnt, k.TX, f.tile_cnt,
@@ -998,7 +1000,7 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         sm.mark(LODGS_STAGE_EMIT, 1, st);
         sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
         LODGS_CUDA(pdl_launch(k_tile_sort, (unsigned)n_tiles, TS_THREADS, st, f.ranges, f.tile_cnt, f.cnt, f.pkey, f.pval,
-                                                              f.pscratch));
+                              f.pscratch, f.tile_order));
         count_launches(1);
         sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
         f.sorted_pval = f.pval;
@@ -1028,16 +1030,16 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         f.sorted_pval = alt ? f.pval_alt : f.pval;
         LODGS_CUDA(cudaMemsetAsync(f.ranges, 0, n_tiles * sizeof(uint2), st));
         LODGS_CUDA(pdl_launch(k_ranges, RGRID, RB, st, skey, f.cnt, (uint32_t)n_tiles, f.ranges));
-        count_launches(1);
+        LODGS_CUDA(pdl_launch(k_tile_order, 1, TOR_THREADS, st, f.ranges, (uint32_t)n_tiles, f.tile_order));
+        count_launches(2);
         sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
         sm.mark(LODGS_STAGE_BLEND, 0, st);
     }
     LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));
-    LODGS_CUDA(pdl_launch(k_tile_order, 1, TOR_THREADS, st, f.ranges, (uint32_t)n_tiles, f.tile_order));
     LODGS_CUDA(pdl_launch((f.count_work ? k_blend<true> : k_blend<false>), (unsigned)n_tiles, BNT, st,
         f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work,
         f.tile_order));
-    count_launches(2);
+    count_launches(1);
     sm.mark(LODGS_STAGE_BLEND, 1, st);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
