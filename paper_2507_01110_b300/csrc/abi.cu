@@ -124,6 +124,8 @@ int ensure_pairs(lodgs_frame *fr, uint64_t want) {
     c = f.cap_pairs; if (int r = grow(f.pscratch, c, want)) return r;
     c = f.cap_pairs; if (int r = grow(f.pkey_alt, c, want)) return r;
     c = f.cap_pairs; if (int r = grow(f.pval_alt, c, want)) return r;
+    c = f.cap_keep; if (int r = grow(f.keep, c, want / 16 + 1)) return r;   // rectangle pairs up to 2x kept
+    f.cap_keep = c;
     f.cap_pairs = want;
     return LODGS_OK;
 }
@@ -132,7 +134,7 @@ void free_frame_bufs(FrameBufs &f) {
     void *ps[] = {f.cnt, f.d_view, f.sel_rows, f.emit_j, f.high, f.work_off, f.emit_x, f.block_counts, f.scan_bsum,
                   f.sort_hist, f.sp_a, f.sp_b, f.sp_c, f.dkey, f.dval, f.dkey_alt, f.dval_alt, f.rect, f.ntiles,
                   f.pair_off, f.g2d, f.pkey, f.pval, f.pscratch, f.pkey_alt, f.pval_alt, f.ranges, f.tile_cnt,
-                  f.tile_order, f.work,
+                  f.tile_order, f.keep, f.work,
                   f.sel_src, f.emit_src, f.up_out, f.up_x};
     for (void *p : ps)
         if (p) cudaFree(p);

@@ -155,6 +155,8 @@ struct FrameBufs {
     uint32_t *pkey = nullptr, *pval = nullptr;   // pairs: depth key / tile key, selected index
     uint32_t *pkey_alt = nullptr, *pval_alt = nullptr;   // global ordering: tile sort
     unsigned long long *pscratch = nullptr;      // merge scratch of the per-tile sort (long lists)
+    uint32_t *keep = nullptr;        // per 32 rectangle pairs: kept lanes (per-tile ordering), cap_keep words
+    uint64_t cap_keep = 0;
     // tiles (capacity cap_tiles)
     uint2 *ranges = nullptr;
     uint32_t *tile_cnt = nullptr;     // kept pairs per tile, then scatter cursors; zero between renders

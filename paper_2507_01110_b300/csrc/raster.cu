@@ -190,6 +190,16 @@ __global__ void k_ranges(const uint32_t *__restrict__ pkey, uint32_t *__restrict
 // rectangle areas, selection order) and is the k-th tile of its rectangle in
 // row-major order.  Returns the tile of the pair, or -1 when the tile support
 // test drops it.
+// Tile of pair p of Gaussian g (row-major in its rectangle), whatever the
+// support test says.
+__device__ __forceinline__ int64_t pair_tile_any(uint32_t p, uint32_t g, const uint32_t *__restrict__ pair_off,
+                                                 const uint2 *__restrict__ rect, int TX) {
+    const uint2 rc = rect[g];
+    const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+    const uint32_t w = x1 - x0, k = p - pair_off[g];
+    return (int64_t)(y0 + k / w) * TX + (x0 + k % w);
+}
+
 // Tile of pair p of Gaussian g (row-major in its rectangle), or -1 when the
 // tile support test drops it.
 __device__ __forceinline__ int64_t pair_tile(uint32_t p, uint32_t g, const uint32_t *__restrict__ pair_off,
@@ -205,11 +215,15 @@ __device__ __forceinline__ int64_t pair_tile(uint32_t p, uint32_t g, const uint3
     return (int64_t)ty * TX + tx;
 }
 
-// Count the kept pairs of every tile (one atomic per group of equal tiles in a warp).
+// Count the kept pairs of every tile (one atomic per group of equal tiles in a
+// warp) and record each 32-pair group's kept lanes as a bit mask (keep[gi],
+// for the groups below keep_cap), so that the scatter neither repeats the
+// support test nor visits groups with nothing kept.
 __global__ void __launch_bounds__(RB) k_emit_count(const uint32_t *__restrict__ pair_off,
                                                    const uint2 *__restrict__ rect, const float4 *__restrict__ sp_a,
                                                    const float4 *__restrict__ sp_b, uint32_t *__restrict__ cnt,
-                                                   int TX, uint32_t *__restrict__ tile_cnt) {
+                                                   int TX, uint32_t *__restrict__ tile_cnt, uint32_t *__restrict__ keep,
+                                                   uint32_t keep_cap) {
     pdl_wait();
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     if (*reinterpret_cast<const unsigned long long *>(cnt + C_NPAIR64) > 0xffffffffull) {   // 32-bit pair indices
@@ -227,6 +241,8 @@ __global__ void __launch_bounds__(RB) k_emit_count(const uint32_t *__restrict__ 
         const uint32_t g = warp_pair_owner(p0, p, n, pair_off, lane, hint);
         hint = __shfl_sync(0xffffffffu, g, 31);
         const int64_t t = p < P ? pair_tile(p, g, pair_off, rect, sp_a, sp_b, TX) : -1;
+        const uint32_t kept = __ballot_sync(0xffffffffu, t >= 0);
+        if (lane == 0 && gi < keep_cap) keep[gi] = kept;
         const uint32_t key = t < 0 ? 0xffffffffu : (uint32_t)t;
         const uint32_t peers = __match_any_sync(0xffffffffu, key);
         if (t >= 0 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&tile_cnt[t], (uint32_t)__popc(peers));
@@ -379,7 +395,8 @@ __global__ void __launch_bounds__(RB) k_emit_scatter(const uint32_t *__restrict_
                                                      const float4 *__restrict__ sp_b,
                                                      const uint32_t *__restrict__ dkey, const uint32_t *__restrict__ cnt,
                                                      int TX, uint32_t *__restrict__ cursor, uint32_t *__restrict__ pkey,
-                                                     uint32_t *__restrict__ pval) {
+                                                     uint32_t *__restrict__ pval, const uint32_t *__restrict__ keep,
+                                                     uint32_t keep_cap) {
     pdl_wait();
     if (cnt[C_STATUS] & ST_CAPACITY) return;
     const uint32_t P = cnt[C_NPAIR], n = cnt[C_NSEL_EFF];
@@ -387,10 +404,15 @@ __global__ void __launch_bounds__(RB) k_emit_scatter(const uint32_t *__restrict_
     uint32_t g0, g1, hint = 0;
     warp_groups(P, g0, g1);
     for (uint32_t gi = g0; gi < g1; ++gi) {
+        const bool known = gi < keep_cap;               // the count pass recorded this group's kept lanes
+        const uint32_t kept = known ? keep[gi] : 0xffffffffu;
+        if (kept == 0u) continue;                       // warp-uniform; the carried hint stays a lower bound
         const uint32_t p0 = gi * 32u, p = p0 + lane;
         const uint32_t g = warp_pair_owner(p0, p, n, pair_off, lane, hint);
         hint = __shfl_sync(0xffffffffu, g, 31);
-        const int64_t t = p < P ? pair_tile(p, g, pair_off, rect, sp_a, sp_b, TX) : -1;
+        int64_t t = -1;
+        if (p < P && (kept >> lane & 1u))
+            t = known ? pair_tile_any(p, g, pair_off, rect, TX) : pair_tile(p, g, pair_off, rect, sp_a, sp_b, TX);
         const uint32_t key = t < 0 ? 0xffffffffu : (uint32_t)t;
         const uint32_t peers = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(peers) - 1;
@@ -988,14 +1010,16 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         int rc = scan_exclusive(f.ntiles, f.pair_off, f.cnt + C_NSEL_EFF, (uint32_t)f.cap_sel, f.scan_bsum,
                                 f.cnt + C_NPAIR, st);     // rectangle pairs per selected Gaussian
         if (rc) return rc;
-        LODGS_CUDA(pdl_launch(k_emit_count, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.cnt, k.TX, f.tile_cnt));
+        const uint32_t keep_cap = (uint32_t)std::min<uint64_t>(f.cap_keep, UINT32_MAX);
+        LODGS_CUDA(pdl_launch(k_emit_count, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.cnt, k.TX, f.tile_cnt,
+                              f.keep, keep_cap));
         LODGS_CUDA(pdl_launch(k_tile_offsets, 1, TO_THREADS, st, f.tile_cnt, (uint32_t)n_tiles, f.cap_pairs, f.cnt, f.ranges));
         LODGS_CUDA(pdl_launch(k_tile_order, 1, TOR_THREADS, st, f.ranges, (uint32_t)n_tiles, f.tile_order));
         count_launches(3);
         sm.mark(LODGS_STAGE_COUNT, 1, st);
         sm.mark(LODGS_STAGE_EMIT, 0, st);
-        LODGS_CUDA(pdl_launch(k_emit_scatter, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.dkey, f.cnt, k.TX, f.tile_cnt,
-                                             f.pkey, f.pval));
+        LODGS_CUDA(pdl_launch(k_emit_scatter, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.dkey, f.cnt, k.TX,
+                              f.tile_cnt, f.pkey, f.pval, f.keep, keep_cap));
         count_launches(1);
         sm.mark(LODGS_STAGE_EMIT, 1, st);
         sm.mark(LODGS_STAGE_TILE_SORT, 0, st);
