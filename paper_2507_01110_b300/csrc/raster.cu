@@ -249,6 +249,77 @@ __global__ void __launch_bounds__(RB) k_emit_count(const uint32_t *__restrict__ 
     }
 }
 
+// Longest-first tile order for the blends.  Blocks are handed to SMs in index
+// order as slots free up (greedy list scheduling); in raster order a few long
+// tiles that start late keep some SMs busy while the rest idle.  Tiles are
+// bucketed by pair count on a log scale (two buckets per power of two) and
+// listed largest bucket first; the order within a bucket is arbitrary, as a
+// tile's result does not depend on which block computes it.  One block; each
+// pass loads TOR_K chunks of counts at once.
+constexpr int TOR_THREADS = 1024, TOR_K = 8, TOR_BUCKETS = 64;
+__device__ __forceinline__ uint32_t order_bucket(uint32_t n) {
+    uint32_t key = n;                                          // 0, 1
+    if (n >= 2) {
+        const uint32_t l = 31 - __clz(n);                      // 1..31
+        key = 2 * l + ((n >> (l - 1)) & 1u);                   // 2..63
+    }
+    return (TOR_BUCKETS - 1) - key;                            // largest counts first
+}
+
+// The order itself, computed by the calling block (TOR_THREADS threads, which
+// must see the ranges: written before a barrier, or by an earlier kernel).
+__device__ __forceinline__ void block_tile_order(const uint2 *ranges, uint32_t n_tiles,   // no __restrict__:
+                                                 uint32_t *__restrict__ order, uint32_t *s_h) {  // written in-kernel
+    const int tid = threadIdx.x;
+    if (tid < TOR_BUCKETS) s_h[tid] = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < n_tiles; base += TOR_K * TOR_THREADS) {
+        uint2 r[TOR_K];
+#pragma unroll
+        for (int i = 0; i < TOR_K; ++i) {
+            const uint32_t t = base + i * TOR_THREADS + tid;
+            r[i] = t < n_tiles ? ranges[t] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < TOR_K; ++i)
+            if (base + i * TOR_THREADS + tid < n_tiles) atomicAdd(&s_h[order_bucket(r[i].y - r[i].x)], 1u);
+    }
+    __syncthreads();
+    if (tid < 32) {                                            // exclusive scan of the 64 buckets
+        const uint32_t a = s_h[2 * tid], b = s_h[2 * tid + 1];
+        uint32_t x = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (tid >= o) x += y;
+        }
+        const uint32_t ex = x - (a + b);
+        s_h[2 * tid] = ex;
+        s_h[2 * tid + 1] = ex + a;
+    }
+    __syncthreads();
+    for (uint32_t base = 0; base < n_tiles; base += TOR_K * TOR_THREADS) {
+        uint2 r[TOR_K];
+#pragma unroll
+        for (int i = 0; i < TOR_K; ++i) {
+            const uint32_t t = base + i * TOR_THREADS + tid;
+            r[i] = t < n_tiles ? ranges[t] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < TOR_K; ++i) {
+            const uint32_t t = base + i * TOR_THREADS + tid;
+            if (t < n_tiles) order[atomicAdd(&s_h[order_bucket(r[i].y - r[i].x)], 1u)] = t;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TOR_THREADS) k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                                            uint32_t *__restrict__ order) {
+    pdl_wait();
+    __shared__ uint32_t s_h[TOR_BUCKETS];
+    block_tile_order(ranges, n_tiles, order, s_h);
+}
+
 // One block: exclusive scan of the tile counts.  Writes the tile ranges, turns
 // the counts into scatter cursors (the tile's first slot) and records the kept
 // pair total, flagging a capacity error when it exceeds the pair buffers.
@@ -257,10 +328,12 @@ __global__ void __launch_bounds__(RB) k_emit_count(const uint32_t *__restrict__ 
 // its warps, scans the warp totals of every chunk in one warp per chunk, and
 // adds the chunks' totals in order.
 constexpr int TO_THREADS = 1024;
+static_assert(TO_THREADS == TOR_THREADS, "the offsets block also computes the tile order");
 constexpr int TO_K = 8;
 __global__ void __launch_bounds__(TO_THREADS) k_tile_offsets(uint32_t *__restrict__ tile_cnt, uint32_t n_tiles,
                                                              uint64_t cap_pairs, uint32_t *__restrict__ cnt,
-                                                             uint2 *__restrict__ ranges) {
+                                                             uint2 *__restrict__ ranges,
+                                                             uint32_t *__restrict__ tile_order) {
     pdl_wait();
     constexpr int NWT = TO_THREADS / 32;
     static_assert(TO_K <= NWT, "one warp scans each chunk's warp totals");
@@ -322,70 +395,8 @@ __global__ void __launch_bounds__(TO_THREADS) k_tile_offsets(uint32_t *__restric
             cnt[C_NKEPT] = (uint32_t)total;
         }
     }
-}
-
-// Longest-first tile order for the blends.  Blocks are handed to SMs in index
-// order as slots free up (greedy list scheduling); in raster order a few long
-// tiles that start late keep some SMs busy while the rest idle.  Tiles are
-// bucketed by pair count on a log scale (two buckets per power of two) and
-// listed largest bucket first; the order within a bucket is arbitrary, as a
-// tile's result does not depend on which block computes it.  One block; each
-// pass loads TOR_K chunks of counts at once.
-constexpr int TOR_THREADS = 1024, TOR_K = 8, TOR_BUCKETS = 64;
-__device__ __forceinline__ uint32_t order_bucket(uint32_t n) {
-    uint32_t key = n;                                          // 0, 1
-    if (n >= 2) {
-        const uint32_t l = 31 - __clz(n);                      // 1..31
-        key = 2 * l + ((n >> (l - 1)) & 1u);                   // 2..63
-    }
-    return (TOR_BUCKETS - 1) - key;                            // largest counts first
-}
-
-__global__ void __launch_bounds__(TOR_THREADS) k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles,
-                                                            uint32_t *__restrict__ order) {
-    pdl_wait();
     __shared__ uint32_t s_h[TOR_BUCKETS];
-    const int tid = threadIdx.x;
-    if (tid < TOR_BUCKETS) s_h[tid] = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < n_tiles; base += TOR_K * TOR_THREADS) {
-        uint2 r[TOR_K];
-#pragma unroll
-        for (int i = 0; i < TOR_K; ++i) {
-            const uint32_t t = base + i * TOR_THREADS + tid;
-            r[i] = t < n_tiles ? ranges[t] : make_uint2(0u, 0u);
-        }
-#pragma unroll
-        for (int i = 0; i < TOR_K; ++i)
-            if (base + i * TOR_THREADS + tid < n_tiles) atomicAdd(&s_h[order_bucket(r[i].y - r[i].x)], 1u);
-    }
-    __syncthreads();
-    if (tid < 32) {                                            // exclusive scan of the 64 buckets
-        const uint32_t a = s_h[2 * tid], b = s_h[2 * tid + 1];
-        uint32_t x = a + b;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (tid >= o) x += y;
-        }
-        const uint32_t ex = x - (a + b);
-        s_h[2 * tid] = ex;
-        s_h[2 * tid + 1] = ex + a;
-    }
-    __syncthreads();
-    for (uint32_t base = 0; base < n_tiles; base += TOR_K * TOR_THREADS) {
-        uint2 r[TOR_K];
-#pragma unroll
-        for (int i = 0; i < TOR_K; ++i) {
-            const uint32_t t = base + i * TOR_THREADS + tid;
-            r[i] = t < n_tiles ? ranges[t] : make_uint2(0u, 0u);
-        }
-#pragma unroll
-        for (int i = 0; i < TOR_K; ++i) {
-            const uint32_t t = base + i * TOR_THREADS + tid;
-            if (t < n_tiles) order[atomicAdd(&s_h[order_bucket(r[i].y - r[i].x)], 1u)] = t;
-        }
-    }
+    block_tile_order(ranges, n_tiles, tile_order, s_h);      // this block's range writes precede its barriers
 }
 
 // Scatter the kept pairs into their tiles' slots (in any order within a tile:
@@ -1013,9 +1024,9 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         const uint32_t keep_cap = (uint32_t)std::min<uint64_t>(f.cap_keep, UINT32_MAX);
         LODGS_CUDA(pdl_launch(k_emit_count, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.cnt, k.TX, f.tile_cnt,
                               f.keep, keep_cap));
-        LODGS_CUDA(pdl_launch(k_tile_offsets, 1, TO_THREADS, st, f.tile_cnt, (uint32_t)n_tiles, f.cap_pairs, f.cnt, f.ranges));
-        LODGS_CUDA(pdl_launch(k_tile_order, 1, TOR_THREADS, st, f.ranges, (uint32_t)n_tiles, f.tile_order));
-        count_launches(3);
+        LODGS_CUDA(pdl_launch(k_tile_offsets, 1, TO_THREADS, st, f.tile_cnt, (uint32_t)n_tiles, f.cap_pairs, f.cnt,
+                              f.ranges, f.tile_order));
+        count_launches(2);
         sm.mark(LODGS_STAGE_COUNT, 1, st);
         sm.mark(LODGS_STAGE_EMIT, 0, st);
         LODGS_CUDA(pdl_launch(k_emit_scatter, EGRID, RB, st, f.pair_off, f.rect, f.sp_a, f.sp_b, f.dkey, f.cnt, k.TX,
