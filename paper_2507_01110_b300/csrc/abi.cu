@@ -457,7 +457,8 @@ int backward_blend(lodgs_scene *sc, lodgs_frame *fr, const float *image, const f
         fr->stream = st;
     }
     fr->mark(LODGS_STAGE_BLEND_BWD, 0, st);
-    int rc = launch_raster_backward(fr->k, fr->f, image, dL_dimage, target, target_u8, l1_scale, loss_sum, st);
+    int rc = launch_raster_backward(fr->k, fr->f, image, dL_dimage, target, target_u8, l1_scale, loss_sum,
+                                    fr->blend_bwd_done, st);
     if (rc) return rc;
     fr->mark(LODGS_STAGE_BLEND_BWD, 1, st);
     fr->blend_bwd_done = true;

@@ -262,8 +262,11 @@ int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaS
 int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, const StageMarks &sm);
 // target (with loss_sum): the L1 loss's gradient formed in the kernel from a
 // float32 or (target_u8) 8-bit H x W x 3 target; else dL/dC read from dL_dimage
+// zero_g2d: clear the 2D gradient rows first (the projection of the render
+// cleared those of its selection; set it for a second backward of one render)
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, const float *dL_dimage,
-                           const void *target, bool target_u8, float l1_scale, float *loss_sum, cudaStream_t st);
+                           const void *target, bool target_u8, float l1_scale, float *loss_sum, bool zero_g2d,
+                           cudaStream_t st);
 int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs &f, float *grad_rows,
                             int64_t grad_capacity, int dense, cudaStream_t st);
 }  // namespace lodgs

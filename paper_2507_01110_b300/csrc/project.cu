@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
                                                  uint32_t *__restrict__ cnt, uint64_t cap_sel, float4 *__restrict__ sp_a,
                                                  float4 *__restrict__ sp_b, float4 *__restrict__ sp_c,
                                                  uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
-                                                 uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles) {
+                                                 uint2 *__restrict__ rect, uint32_t *__restrict__ ntiles,
+                                                 float4 *__restrict__ g2d) {
     pdl_wait();
     const CamK &k = view->k;
     // selections beyond the workspace are not rendered: the frame reports a capacity error
@@ -234,6 +235,9 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
             }
         }
         sp_a[i] = a; sp_b[i] = b; sp_c[i] = c4;
+        static_assert(G2D_STRIDE == 12, "three float4 per row");
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);       // the blend backward accumulates here
+        g2d[3 * (size_t)i] = z; g2d[3 * (size_t)i + 1] = z; g2d[3 * (size_t)i + 2] = z;
         dkey[i] = key; dval[i] = i;
         rect[i] = rc; ntiles[i] = nt;
         nvis += vis ? 1u : 0u;
@@ -445,7 +449,8 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
 int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaStream_t st) {
 #define LAUNCH_PROJ(D)                                                                                     \
     LODGS_CUDA(pdl_launch(k_project<D>, PROJ_GRID, PB, st, rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.d_view, f.cnt, f.cap_sel, f.sp_a, \
-                                           f.sp_b, f.sp_c, f.dkey, f.dval, f.rect, f.ntiles))
+                                           f.sp_b, f.sp_c, f.dkey, f.dval, f.rect, f.ntiles, \
+                                           reinterpret_cast<float4 *>(f.g2d)))
     switch (sc->sh_degree) {
         case 0: LAUNCH_PROJ(0); break;
         case 1: LAUNCH_PROJ(1); break;

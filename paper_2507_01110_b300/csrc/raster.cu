@@ -1081,9 +1081,11 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
 }
 
 int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, const float *dL_dimage,
-                           const void *target, bool target_u8, float l1_scale, float *loss_sum, cudaStream_t st) {
+                           const void *target, bool target_u8, float l1_scale, float *loss_sum, bool zero_g2d,
+                           cudaStream_t st) {
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
-    LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * G2D_STRIDE * sizeof(float), st));
+    if (zero_g2d)          // the projection zeroes the rows of its selection; a repeated backward re-zeroes
+        LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * G2D_STRIDE * sizeof(float), st));
     LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
     const unsigned nb = (unsigned)n_tiles, nt = TILE_PIX / BWD_PIX;
     if (target) {
