@@ -594,8 +594,9 @@ int lodgs_frame_stage_ms(lodgs_frame *fr, float *ms) {
 int lodgs_frame_work(lodgs_frame *fr, uint64_t *work) {
     if (!fr || !work) { set_error("frame_work: NULL argument"); return LODGS_E_INVALID; }
     LODGS_CUDA(cudaStreamSynchronize(fr->stream));
-    unsigned long long w[4];
-    LODGS_CUDA(cudaMemcpy(w, fr->f.work, sizeof(w), cudaMemcpyDeviceToHost));
+    unsigned long long w[4] = {0, 0, 0, 0};
+    if (fr->f.count_work)           // the last render was a profiling one (the only kind that tallies)
+        LODGS_CUDA(cudaMemcpy(w, fr->f.work, sizeof(w), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 4; ++i) work[i] = w[i];
     return LODGS_OK;
 }

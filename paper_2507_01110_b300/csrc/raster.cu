@@ -1070,7 +1070,7 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         sm.mark(LODGS_STAGE_TILE_SORT, 1, st);
         sm.mark(LODGS_STAGE_BLEND, 0, st);
     }
-    LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));
+    if (f.count_work) LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));   // profiling only
     LODGS_CUDA(pdl_launch((f.count_work ? k_blend<true> : k_blend<false>), (unsigned)n_tiles, BNT, st,
         f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work,
         f.tile_order));
@@ -1086,7 +1086,7 @@ int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, cons
     const uint64_t n_tiles = (uint64_t)k.TX * k.TY;
     if (zero_g2d)          // the projection zeroes the rows of its selection; a repeated backward re-zeroes
         LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * G2D_STRIDE * sizeof(float), st));
-    LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
+    if (f.count_work) LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
     const unsigned nb = (unsigned)n_tiles, nt = TILE_PIX / BWD_PIX;
     if (target) {
         LODGS_CUDA(cudaMemsetAsync(loss_sum, 0, sizeof(float), st));

@@ -139,3 +139,29 @@ def test_fused_l1_backward_with_an_8bit_target():
         api.render_backward_blend_l1(scene, fr, t8.cuda().to(torch.int32))
     with pytest.raises(ValueError):
         api.render_backward_blend_l1(scene, fr, t8.cuda()[:-1])
+
+
+def test_work_counters_follow_profiling():
+    """The work counters are tallied by profiling renders only: the backward
+    visits exactly the forward's blended contributions; without profiling
+    they read 0."""
+    from paper_2507_01110_b300 import api, build
+    build.build()
+    cfg = synth.config2_scene(n=200_000)
+    scene = api.build_hierarchy(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
+    c = cfg["cameras"][10]
+    cam = synth.camera_look(c.pos, c.R[2], c.R[0], 320, 200)
+    fr = api.Frame(scene)
+    fr.set_profiling(True)
+    api.select_lod(scene, cam, fr)
+    img = api.render(scene, fr)
+    w = fr.work()
+    assert w["fwd_eval"] >= w["fwd_blend"] > 0 and w["bwd_eval"] == w["bwd_contrib"] == 0
+    api.render_backward(scene, fr, torch.full_like(img, 1e-3))
+    w = fr.work()
+    assert w["bwd_contrib"] == w["fwd_blend"] and w["bwd_eval"] >= w["bwd_contrib"]
+    fr.set_profiling(False)
+    api.select_lod(scene, cam, fr)
+    img = api.render(scene, fr)
+    api.render_backward(scene, fr, torch.full_like(img, 1e-3))
+    assert all(v == 0 for v in fr.work().values())
