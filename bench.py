@@ -258,10 +258,11 @@ def run_lodgs(args, rank: int, world: int):
         step(v, targets_d[v], cams[v])
     torch.cuda.synchronize()
 
-    # CUDA graphs per frame: [select, render], [loss + blend backward],
-    # [projection backward]; the camera is uploaded before each replay, outside
-    # the graphs, and events between the graph launches time the blend backward
-    # (the dominant kernel) inside the timed region.
+    # CUDA graphs per frame: [camera upload, select, render], [loss + blend
+    # backward], [projection backward]; each training view has a fixed camera,
+    # so its upload kernel is captured with the view's graph and runs at every
+    # replay.  Events between the graph launches time the blend backward (the
+    # dominant kernel) inside the timed region.
     for v in my_views:
         api.set_view(frames[v], cams[v])
     torch.cuda.synchronize()
@@ -271,7 +272,7 @@ def run_lodgs(args, rank: int, world: int):
         for v in my_views:
             gs = [torch.cuda.CUDAGraph() for _ in range(3)]
             with torch.cuda.graph(gs[0], stream=cap):
-                step_fwd(v, targets_d[v], None)
+                step_fwd(v, targets_d[v], cams[v])
             with torch.cuda.graph(gs[1], stream=cap):
                 step_bwd_blend(v)
             with torch.cuda.graph(gs[2], stream=cap):
@@ -282,7 +283,6 @@ def run_lodgs(args, rank: int, world: int):
     ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
     def replay(v, i=None):
-        api.set_view(frames[v], cams[v])
         graphs[v][0].replay()
         if i is not None:
             ev_a[i].record(stream)
@@ -319,12 +319,11 @@ def run_lodgs(args, rank: int, world: int):
     clk = clocks.stop()
     bwd_ms = [a.elapsed_time(b2) for a, b2 in zip(ev_a, ev_b)]
     stats_ok = all(frames[v].stats()["status"] == 0 for v in set(order))
-    # kernels per step: counted on an eager step without the camera upload (graph
-    # replays launch the same kernels; the upload is counted in launches_host)
-    api.set_view(frames[order[0]], cams[order[0]])
+    # kernels per step: counted on an eager step with the camera upload (graph
+    # replays launch the same kernels; launches_host counts any made outside them)
     torch.cuda.synchronize()
     l0 = _lib.lib().lodgs_kernel_launches()
-    step(order[0], targets_d[order[0]], None)
+    step(order[0], targets_d[order[0]], cams[order[0]])
     torch.cuda.synchronize()
     per_step = _lib.lib().lodgs_kernel_launches() - l0
     launches = launches_host + per_step * len(order)
