@@ -86,41 +86,73 @@ __global__ void __launch_bounds__(PIECE_THREADS) k_copy_pieces(const Piece *__re
     }
 }
 
-// Write-back of a trained SPT prefix (or of the upper rows): `n` slots from
-// `slot` on, host rows from `host_row` on.  Only slots whose dirty flag the
-// Adam step set are copied (record, m, v, step count) and their flags cleared;
-// one warp per slot.  Bytes copied are added to *written.
+// Write-back of trained SPT prefixes (and of the upper rows) in two steps, so
+// that the link carries write-backs and loads at the same time:
+//  k_stage_rows  (copy stream) copies the slots of each span whose dirty flag
+//                the Adam step set (record, m, v, step count) into a compact
+//                device staging area with their host rows, and clears the
+//                flags; the batch's moves and loads may then reuse the slots;
+//  k_unstage_rows (the cache's write-back stream) copies the staged rows to
+//                the pinned host arrays, while the loads run.
+// One warp per row.  Bytes written back are added to *written.
 struct RowSpan {
     uint64_t slot, host_row;
     uint32_t n, pad;
 };
 constexpr uint32_t SPAN_ROWS = 256;
+constexpr int UNSTAGE_BLOCKS = 148 * 4;
 
-__global__ void __launch_bounds__(PIECE_THREADS) k_writeback_rows(
+struct Staging {
+    uint4 *rec, *m, *v;       // capacity rows x quads each
+    uint32_t *t, *host_row, *n;
+};
+
+__global__ void __launch_bounds__(PIECE_THREADS) k_stage_rows(
     const RowSpan *__restrict__ spans, int quads, const uint4 *__restrict__ rec, const uint4 *__restrict__ m,
-    const uint4 *__restrict__ v, const uint32_t *__restrict__ t, uint4 *__restrict__ h_rec, uint4 *__restrict__ h_m,
-    uint4 *__restrict__ h_v, uint32_t *__restrict__ h_t, uint32_t *__restrict__ dirty,
+    const uint4 *__restrict__ v, const uint32_t *__restrict__ t, uint32_t *__restrict__ dirty, Staging sg,
     unsigned long long *__restrict__ written) {
     const RowSpan sp = spans[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t rows = 0;
     for (uint32_t r = warp; r < sp.n; r += PIECE_THREADS / 32) {
-        const uint64_t s = sp.slot + r, h = sp.host_row + r;
+        const uint64_t s = sp.slot + r;
         if (!dirty[s]) continue;                                  // warp-uniform
+        uint32_t i = 0;
+        if (lane == 0) i = atomicAdd(sg.n, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
         for (int k = lane; k < 3 * quads; k += 32) {
             const int a = k / quads, o = k - a * quads;
             const uint4 *src = a == 0 ? rec : (a == 1 ? m : v);
-            uint4 *dst = a == 0 ? h_rec : (a == 1 ? h_m : h_v);
-            dst[h * quads + o] = src[s * quads + o];
+            uint4 *dst = a == 0 ? sg.rec : (a == 1 ? sg.m : sg.v);
+            dst[(size_t)i * quads + o] = src[s * quads + o];
         }
         if (lane == 0) {
-            h_t[h] = t[s];
+            sg.t[i] = t[s];
+            sg.host_row[i] = (uint32_t)(sp.host_row + r);
             dirty[s] = 0u;
             ++rows;
         }
     }
     if (lane == 0 && rows)
         atomicAdd(written, (unsigned long long)rows * (3ull * quads * 16ull + 4ull));
+}
+
+__global__ void __launch_bounds__(PIECE_THREADS) k_unstage_rows(Staging sg, int quads, uint4 *__restrict__ h_rec,
+                                                                uint4 *__restrict__ h_m, uint4 *__restrict__ h_v,
+                                                                uint32_t *__restrict__ h_t) {
+    const uint32_t n = *sg.n;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (PIECE_THREADS / 32);
+    for (uint32_t i = blockIdx.x * (PIECE_THREADS / 32) + (threadIdx.x >> 5); i < n; i += warps) {
+        const size_t h = sg.host_row[i];
+        for (int k = lane; k < 3 * quads; k += 32) {
+            const int a = k / quads, o = k - a * quads;
+            const uint4 *src = a == 0 ? sg.rec : (a == 1 ? sg.m : sg.v);
+            uint4 *dst = a == 0 ? h_rec : (a == 1 ? h_m : h_v);
+            dst[h * quads + o] = src[(size_t)i * quads + o];
+        }
+        if (lane == 0) h_t[h] = sg.t[i];
+    }
 }
 
 // copy phases of one batch, issued after its masked write-backs (which read
@@ -156,6 +188,13 @@ struct lodgs_cache {
     std::vector<RowSpan> wb;
     RowSpan *h_spans = nullptr, *d_spans = nullptr;
     size_t spans_cap = 0;
+    // staged write-backs: device staging area (stage_cap rows), the stream that
+    // copies it to host memory, and events ordering the two
+    Staging stage{};
+    uint64_t stage_cap = 0;
+    cudaStream_t wb_stream = nullptr;
+    cudaEvent_t staged = nullptr, unstage_done = nullptr;
+    bool unstage_pending = false;
     std::vector<uint32_t> spt_base;   // host copy (n_spt + 1)
     std::vector<Entry> entry;
     std::list<uint32_t> lru;          // front = most recently used
@@ -265,6 +304,9 @@ int issue_pieces(lodgs_cache *c, cudaStream_t st) {
     for (auto &v : c->pend) total += v.size();
     if (!total && c->wb.empty()) return LODGS_OK;
     LODGS_CUDA(cudaEventSynchronize(c->pieces_done));       // the staging of the last batch is free
+    // the last batch's write-back to host memory ends before this batch's
+    // copies: loads may read host rows it writes, and staging is reused
+    if (c->unstage_pending) LODGS_CUDA(cudaStreamWaitEvent(st, c->unstage_done, 0));
     if (!c->wb.empty()) {                                    // masked write-backs go first
         const size_t n = c->wb.size();
         if (n > c->spans_cap) {
@@ -279,14 +321,38 @@ int issue_pieces(lodgs_cache *c, cudaStream_t st) {
             c->spans_cap = cap;
         }
         memcpy(c->h_spans, c->wb.data(), n * sizeof(RowSpan));
-        LODGS_CUDA(cudaMemcpyAsync(c->d_spans, c->h_spans, n * sizeof(RowSpan), cudaMemcpyHostToDevice, st));
+        uint64_t rows = 0;                                   // at most the spans' slots are flagged
+        for (const RowSpan &r : c->wb) rows += r.n;
         const int quads = c->scene->stride / 4;
-        k_writeback_rows<<<(unsigned)n, PIECE_THREADS, 0, st>>>(
+        if (rows > c->stage_cap) {                           // the old area is idle: waited for above
+            LODGS_CUDA(cudaStreamSynchronize(st));
+            cudaFree(c->stage.rec); cudaFree(c->stage.m); cudaFree(c->stage.v);
+            cudaFree(c->stage.t); cudaFree(c->stage.host_row); cudaFree(c->stage.n);
+            c->stage = Staging{};
+            c->stage_cap = 0;
+            const uint64_t cap = std::max<uint64_t>(rows + rows / 2, 4096);
+            const size_t rb = (size_t)cap * quads * sizeof(uint4);
+            LODGS_CUDA(cudaMalloc((void **)&c->stage.rec, rb));
+            LODGS_CUDA(cudaMalloc((void **)&c->stage.m, rb));
+            LODGS_CUDA(cudaMalloc((void **)&c->stage.v, rb));
+            LODGS_CUDA(cudaMalloc((void **)&c->stage.t, cap * 4));
+            LODGS_CUDA(cudaMalloc((void **)&c->stage.host_row, cap * 4));
+            LODGS_CUDA(cudaMalloc((void **)&c->stage.n, 4));
+            c->stage_cap = cap;
+        }
+        LODGS_CUDA(cudaMemcpyAsync(c->d_spans, c->h_spans, n * sizeof(RowSpan), cudaMemcpyHostToDevice, st));
+        LODGS_CUDA(cudaMemsetAsync(c->stage.n, 0, 4, st));
+        k_stage_rows<<<(unsigned)n, PIECE_THREADS, 0, st>>>(
             c->d_spans, quads, reinterpret_cast<const uint4 *>(c->d_records), reinterpret_cast<const uint4 *>(c->d_m),
-            reinterpret_cast<const uint4 *>(c->d_v), c->d_t, reinterpret_cast<uint4 *>(c->hd_rows),
-            reinterpret_cast<uint4 *>(c->hd_m), reinterpret_cast<uint4 *>(c->hd_v), c->hd_t, c->d_dirty,
-            c->d_written);
-        count_launches(1);
+            reinterpret_cast<const uint4 *>(c->d_v), c->d_t, c->d_dirty, c->stage, c->d_written);
+        LODGS_CUDA(cudaEventRecord(c->staged, st));
+        LODGS_CUDA(cudaStreamWaitEvent(c->wb_stream, c->staged, 0));
+        k_unstage_rows<<<UNSTAGE_BLOCKS, PIECE_THREADS, 0, c->wb_stream>>>(
+            c->stage, quads, reinterpret_cast<uint4 *>(c->hd_rows), reinterpret_cast<uint4 *>(c->hd_m),
+            reinterpret_cast<uint4 *>(c->hd_v), c->hd_t);
+        LODGS_CUDA(cudaEventRecord(c->unstage_done, c->wb_stream));
+        c->unstage_pending = true;
+        count_launches(2);
         c->wb.clear();
     }
     if (!total) {
@@ -438,6 +504,10 @@ int lodgs_cache_create(lodgs_scene *sc, const lodgs_cache_params *p, lodgs_cache
             (e = cudaMalloc((void **)&c->d_written, 8)) != cudaSuccess ||
             (e = cudaMemset(c->d_written, 0, 8)) != cudaSuccess)
             return fail(cuda_fail(e, "cache_create: trained-row flags"));
+        if ((e = cudaStreamCreateWithFlags(&c->wb_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c->unstage_done, cudaEventDisableTiming)) != cudaSuccess)
+            return fail(cuda_fail(e, "cache_create: write-back stream"));
     }
     if (p->release_scene_rows) {
         cudaFree(sc->d_rows);
@@ -466,6 +536,11 @@ void lodgs_cache_free(lodgs_cache *c) {
     cudaFree(c->d_dirty);
     cudaFree(c->d_zeros);
     cudaFree(c->d_written);
+    cudaFree(c->stage.rec); cudaFree(c->stage.m); cudaFree(c->stage.v);
+    cudaFree(c->stage.t); cudaFree(c->stage.host_row); cudaFree(c->stage.n);
+    if (c->staged) cudaEventDestroy(c->staged);
+    if (c->unstage_done) cudaEventDestroy(c->unstage_done);
+    if (c->wb_stream) cudaStreamDestroy(c->wb_stream);
     delete c;
 }
 
@@ -487,7 +562,9 @@ int writeback_all(lodgs_cache *c, cudaStream_t st) {
         c->upper_dirty = false;
     }
     (void)M;
-    return issue_pieces(c, st);
+    if (int rc = issue_pieces(c, st)) return rc;
+    if (c->unstage_pending) LODGS_CUDA(cudaStreamWaitEvent(st, c->unstage_done, 0));   // host rows written
+    return LODGS_OK;
 }
 }  // namespace
 
