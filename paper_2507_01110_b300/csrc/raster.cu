@@ -644,7 +644,7 @@ constexpr int BNT = TILE_PIX / PIX;
 constexpr int NWARP = BNT / 32;
 // resident CTAs per SM the register allocation is held to (occupancy)
 #ifndef LODGS_FWD_MINB
-#define LODGS_FWD_MINB 8
+#define LODGS_FWD_MINB 7
 #endif
 #ifndef LODGS_BWD_PIX
 #define LODGS_BWD_PIX 2      // pixels per lane of the backward blend (2 or 4)
