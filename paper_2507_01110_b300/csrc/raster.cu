@@ -650,6 +650,13 @@ constexpr int NWARP = BNT / 32;
 #define LODGS_BWD_PIX 2      // pixels per lane of the backward blend (2 or 4)
 #endif
 constexpr int BWD_PIX = LODGS_BWD_PIX;
+// LODGS_BWD_MINB (if defined): resident CTAs per SM the backward's registers
+// are held to; by default the compiler chooses (56 registers, 9 CTAs)
+#ifdef LODGS_BWD_MINB
+#define BWD_BOUNDS(nt) __launch_bounds__(nt, LODGS_BWD_MINB)
+#else
+#define BWD_BOUNDS(nt) __launch_bounds__(nt)
+#endif
 constexpr float BLOCK_HALF = 3.5f;     // half span of an 8x8 block's pixel centres
 constexpr float LOG2E = 1.44269504088896341f;
 
@@ -825,7 +832,7 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
 // sum |C - target| to *loss_sum (the training loss folded into the backward:
 // no separate pass over the image, no dL/dC buffer).  0: dL/dC from dL_dimg.
 template <bool COUNT, int BP, int L1>
-__global__ void __launch_bounds__(TILE_PIX / BP)
+__global__ void BWD_BOUNDS(TILE_PIX / BP)
     k_blend_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
                 const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c,
                 const uint32_t *__restrict__ cnt, int W, int H, int TX, const float *__restrict__ image,
