@@ -146,13 +146,13 @@ void free_frame_bufs(FrameBufs &f) {
 namespace {
 
 // Upload the frame's view (camera constants and background) on `st`.
-int set_view(lodgs_frame *fr, const lodgs_camera *cam, const float *bg, cudaStream_t st) {
+int set_view(lodgs_frame *fr, const lodgs_camera *cam, const float *bg, cudaStream_t st, bool zero_counters = false) {
     if (cam) fr->k = make_camk(*cam);
     if (bg) { fr->bg[0] = bg[0]; fr->bg[1] = bg[1]; fr->bg[2] = bg[2]; }
     View v;
     v.k = fr->k;
     v.bg[0] = fr->bg[0]; v.bg[1] = fr->bg[1]; v.bg[2] = fr->bg[2]; v.bg[3] = 0.f;
-    int rc = launch_set_view(v, fr->f.d_view, st);
+    int rc = launch_set_view(v, fr->f.d_view, st, zero_counters ? fr->f.cnt : nullptr);
     if (!rc) fr->have_view = true;
     return rc;
 }
@@ -361,11 +361,14 @@ int lodgs_select_lod(lodgs_scene *sc, const lodgs_camera *cam, lodgs_frame *fr, 
     fr->cache = nullptr;                 // no longer a cache view
     for (bool &r : fr->ran) r = false;
     fr->mark(LODGS_STAGE_SELECT, 0, st);
-    if (cam)
-        if (int rc = set_view(fr, cam, nullptr, st)) return rc;
-    LODGS_CUDA(cudaMemsetAsync(fr->f.cnt, 0, C_COUNT * sizeof(uint32_t), st));
+    if (cam) {
+        if (int rc = set_view(fr, cam, nullptr, st, true)) return rc;    // uploads the view, clears the counters
+    } else {
+        LODGS_CUDA(cudaMemsetAsync(fr->f.cnt, 0, C_COUNT * sizeof(uint32_t), st));
+    }
     int rc = launch_select(sc, fr->f, st);
     if (rc) return rc;
+    fr->counters_fresh = true;
     fr->mark(LODGS_STAGE_SELECT, 1, st);
     fr->selected = true;
     fr->rendered = false;
@@ -412,8 +415,11 @@ int lodgs_render(lodgs_scene *sc, lodgs_frame *fr, const float *rows, const floa
     if (bg && (bg[0] != fr->bg[0] || bg[1] != fr->bg[1] || bg[2] != fr->bg[2]))
         if (int r = set_view(fr, nullptr, bg, st)) return r;
     fr->f.count_work = fr->prof_mask != 0;
-    // reset the render's counters and status (the selection's counters stay)
-    LODGS_CUDA(cudaMemsetAsync(fr->f.cnt + C_NSEL_EFF, 0, (C_COUNT - C_NSEL_EFF) * sizeof(uint32_t), st));
+    // reset the render's counters and status (the selection's counters stay);
+    // right after a selection they are still zero
+    if (!fr->counters_fresh)
+        LODGS_CUDA(cudaMemsetAsync(fr->f.cnt + C_NSEL_EFF, 0, (C_COUNT - C_NSEL_EFF) * sizeof(uint32_t), st));
+    fr->counters_fresh = false;
     fr->mark(LODGS_STAGE_PROJECT, 0, st);
     if (!rows && !sc->d_rows) {
         set_error("render: the scene's records live in host memory; pass the cache's device records");

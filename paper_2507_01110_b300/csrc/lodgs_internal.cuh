@@ -252,7 +252,8 @@ struct StageMarks {
 };
 
 // per-view stages (select.cu, project.cu, raster.cu)
-int launch_set_view(const View &v, View *dst, cudaStream_t st);
+// zero_cnt: also clear C_COUNT counters there (the start of a selection)
+int launch_set_view(const View &v, View *dst, cudaStream_t st, uint32_t *zero_cnt = nullptr);
 int launch_select(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st);
 int launch_select_upper(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st);
 int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st);
@@ -281,6 +282,7 @@ struct lodgs_frame {
     cudaStream_t stream = 0;
     lodgs::CamK k{};
     bool selected = false, rendered = false, have_view = false, blend_bwd_done = false;
+    bool counters_fresh = false;      // every counter is zero since the last selection: no render reset
     float bg[3] = {0.f, 0.f, 0.f};
     uint64_t want_sel = 0, want_pairs = 0;
     // stage timing: ev[2s] / ev[2s+1] bracket stage s, for the stages in prof_mask

@@ -339,19 +339,21 @@ __global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, co
     }
 }
 
-__global__ void k_set_view(View v, View *__restrict__ dst) {
+__global__ void k_set_view(View v, View *__restrict__ dst, uint32_t *__restrict__ cnt) {
     pdl_wait();
     const uint32_t *s = reinterpret_cast<const uint32_t *>(&v);
     uint32_t *d = reinterpret_cast<uint32_t *>(dst);
     for (uint32_t i = threadIdx.x; i < sizeof(View) / 4; i += blockDim.x) d[i] = s[i];
+    if (cnt)                                      // and clear the frame's counters (a new selection)
+        for (uint32_t i = threadIdx.x; i < C_COUNT; i += blockDim.x) cnt[i] = 0u;
 }
 
 }  // namespace
 
 // The view goes to the device as a kernel argument: the copy is asynchronous,
 // needs no host staging buffer, and is ordered on the stream like the kernels.
-int launch_set_view(const View &v, View *dst, cudaStream_t st) {
-    LODGS_CUDA(pdl_launch(k_set_view, 1, 32, st, v, dst));
+int launch_set_view(const View &v, View *dst, cudaStream_t st, uint32_t *zero_cnt) {
+    LODGS_CUDA(pdl_launch(k_set_view, 1, 32, st, v, dst, zero_cnt));
     count_launches(1);
     LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
