@@ -257,20 +257,23 @@ int lodgs_select_lod(lodgs_scene *scene, const lodgs_camera *cam, lodgs_frame *f
 
 /*
  * The same LoD cut as lodgs_select_lod, written to caller-owned device buffers,
- * for callers that cannot allocate device memory (code running under CUDA
- * graph capture, code tied to its own memory pool, loops that cannot afford
- * cudaMalloc's device synchronisation).  The paper has no counterpart; this is
+ * for callers that cannot allocate device memory: an application whose device
+ * memory all belongs to its own arena or pool, or a loop that cannot afford
+ * cudaMalloc's device synchronisation.  The paper has no counterpart; this is
  * an interface variant only.  It allocates nothing: its scratch is a static
  * device array of about 16 MiB that every GPU loading the library keeps until
  * the process exits.
  *   d_rows:   device uint32 buffer, capacity >= the scene's n_nodes; receives
  *             the selected render rows, ascending
  *   d_count:  device uint32; receives the number of selected rows
- * Scenes with more than LODGS_NOALLOC_MAX_SPT SPTs, or a smaller capacity, are
- * rejected with LODGS_E_INVALID.  All calls on a GPU share the scratch and each
- * call clears it first: calls that overlap on the device race, so serialise
- * them.  The first call on a device looks up the scratch address
- * (cudaGetSymbolAddress); make it before any stream capture.  Asynchronous.
+ * Scenes with more than LODGS_NOALLOC_MAX_SPT SPTs, a smaller capacity, or a
+ * camera lodgs_select_lod would refuse, are rejected with LODGS_E_INVALID.
+ * All calls on a GPU share the scratch and each call clears it first: calls
+ * that overlap on the device race, so serialise them.  The first call on a
+ * device looks up the scratch address (cudaGetSymbolAddress) and keeps it for
+ * the life of the process; make that first call before any stream capture,
+ * and do not call this entry point again on a device after cudaDeviceReset.
+ * Asynchronous.
  */
 #define LODGS_NOALLOC_MAX_SPT (1 << 20)
 int lodgs_select_lod_noalloc(lodgs_scene *scene, const lodgs_camera *cam, uint32_t *d_rows, int64_t capacity,

@@ -10,6 +10,10 @@ Functions and the paper passage they follow:
                    construction (Sec. 4.3) and SPT layout (Sec. 4.1, Eq. 4, Eq. 6)
   select           Algorithm 1 (upper BFS with frustum culling) + Algorithm 2
   select_bruteforce  top-down descent inside each SPT (independent check)
+  select_upper     Algorithm 1 alone (selected upper rows, SPT roots with x_j)
+  cache.NodeCache  the out-of-core cache's decisions per view (Sec. 4.4 Eq. 7,
+                   Algorithm 3): hit, re-cut or load per SPT root, LRU
+                   eviction, and the cut that results
   project          EWA projection and SH colour (Sec. 3, Eq. 2)
   sort_pairs       tile x depth ordering (3DGS sort reused by the paper)
   blend            Eq. 1 front-to-back compositing
@@ -285,6 +289,30 @@ def select(scene: dict, cam, cull: bool = True):
                                      "selected": int(stats[4])}
 
 
+def select_upper(scene: dict, cam, cull: bool = True):
+    """Algorithm 1 alone: the upper rows it selects (ascending) and the SPT roots
+    it reaches in BFS order, as (spt ids, float32 query distances x_j)."""
+    n_up = scene["n_upper"]
+    sel = np.zeros(max(n_up, 1), dtype=np.int64)
+    sj = np.zeros(max(n_up, 1), dtype=np.int64)
+    sx = np.zeros(max(n_up, 1), dtype=np.float32)
+    n, m = np.zeros(1, dtype=np.int64), np.zeros(1, dtype=np.int64)
+    up_child = np.ascontiguousarray(scene["up_child"].reshape(-1))
+    camv = pack_camera(cam)
+    rc = lib().or_select_upper(C.c_int64(n_up), _p(scene["up_node"]), _p(scene["up_kind"]), _p(up_child),
+                               _p(scene["up_ref"]), C.c_int(scene["stride"]), _p(scene["node_rec"]), _p(camv),
+                               C.c_int(int(cull)), _p(sel), _p(n), _p(sj), _p(sx), _p(m))
+    assert rc == 0
+    return np.sort(sel[: int(n[0])]), sj[: int(m[0])].copy(), sx[: int(m[0])].copy()
+
+
+def cull_sphere(cam, mu, max_scale: float) -> bool:
+    """Frustum culling (Sec. 4.3) of one sphere: centre mu, radius 3 * max_scale."""
+    camv = pack_camera(cam)
+    m = np.ascontiguousarray(mu, dtype=np.float32)
+    return bool(lib().or_cull_sphere(_p(camv), _p(m), C.c_float(max_scale)))
+
+
 def select_bruteforce(scene: dict, cam, cull: bool = True) -> np.ndarray:
     M = scene["node_rec"].shape[0]
     sel = np.zeros(M, dtype=np.int64)
@@ -346,7 +374,9 @@ def tile_keep(u, v, ca, cb, cc, tx, ty) -> bool:
 
 
 def block_keep(g, px: int, py: int) -> bool:
-    """Block support test D10 for one (Gaussian, pixel); g = (u, v, A, B, C, rx, ry)."""
+    """Block support test D10 for one (Gaussian, pixel); g = (u, v, A, B, C, rx, ry).
+    The predicate the CUDA blend skips whole 8x8 blocks by; blend() and
+    blend_backward() here do not use it (they test D8 on every listed pair)."""
     gv = np.ascontiguousarray(g, dtype=np.float32)
     return bool(lib().or_block_keep(_p(gv), C.c_int(int(px)), C.c_int(int(py))))
 
@@ -356,11 +386,6 @@ def support_extents(a: float, c: float, det: float) -> tuple:
     rx, ry = C.c_float(), C.c_float()
     lib().or_support_extents(C.c_float(a), C.c_float(c), C.c_float(det), C.byref(rx), C.byref(ry))
     return rx.value, ry.value
-
-
-def set_block_cull(on: bool) -> None:
-    """Switch the block test D10 of blend / blend_backward on (default) or off."""
-    lib().or_set_block_cull(C.c_int(int(bool(on))))
 
 
 def blend(proj: dict, pairs: dict, width: int, height: int, bg=(0.0, 0.0, 0.0), window=None) -> dict:

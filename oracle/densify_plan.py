@@ -1,8 +1,9 @@
 """Densification planning (Sec. 3 "Densification"; appendix "Respawning,
-Densifying, and Pruning Gaussians").
+Densifying, and Pruning Gaussians"), restated on the host as the checker of
+the library's device planner (lodgs_densify_plan).  Test infrastructure, like
+the rest of this package: only tests/ use it.
 
-Host logic that turns per-row statistics into the operations of
-`Scene.densify`:
+It turns per-row statistics into the operations of `Scene.densify`:
 
 * dead leaves: opacity below `min_opacity`, or flagged stale (the pruning
   rule zeroes the opacity of Gaussians that have not contributed for a number

@@ -35,9 +35,12 @@
  *               nha = -0.5f*A, nhc = -0.5f*C, nb = -B ; support iff p >= -4.5f
  *   D9 tile     a (tile, Gaussian) pair is kept iff the support ellipse can
  *               reach a pixel centre of the tile: see tile_keep() below
- *   D10 block   a pixel tests a Gaussian only if the Gaussian's support box
- *               (half extents rx, ry from the 2D covariance, D7) reaches the
- *               8x8 pixel block holding the pixel: see block_keep() below
+ *   D10 block   the CUDA blend's 8x8-block skip test (support half extents
+ *               rx, ry from the 2D covariance, then a box test): written here
+ *               only as a standalone predicate, or_block_keep(), so that tests
+ *               can check by brute force that it never skips a pixel passing
+ *               D8.  The oracle's own blend and backward do not use it: they
+ *               evaluate D8 on every (pixel, listed Gaussian).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC
  */
@@ -468,6 +471,16 @@ static int cam_culled(const cam_t *k, const float t[3], float maxs) {
     return 0;
 }
 
+/* Frustum test of one sphere (centre mu, radius 3 * maxs) for camera cam[]:
+ * 1 iff Sec. 4.3 "Frustum Culling" drops it (D5, D6). */
+int or_cull_sphere(const float *cam, const float *mu, float maxs) {
+    cam_t k;
+    cam_setup(cam, &k);
+    float t[3], dist;
+    cam_view(&k, mu, t, &dist);
+    return cam_culled(&k, t, maxs);
+}
+
 /* ------------------------------------------------------------------------- */
 /* LoD cut: Algorithm 1 on the upper hierarchy (with frustum culling, Sec.     */
 /* 4.3 "Frustum Culling") then Algorithm 2 per selected SPT at the shared root */
@@ -536,6 +549,26 @@ int or_select(int64_t n_upper, const int64_t *up_node, const int32_t *up_kind, c
     qsort(sel, (size_t)ns, sizeof(int64_t), cmp_i64);
     *n_sel = ns;
     stats[4] = ns;
+    free(sq);
+    return 0;
+}
+
+/* Algorithm 1 alone (upper BFS with culling): the upper entries it selects and
+ * the SPT roots it reaches, in the order it reaches them, each with its query
+ * x_j (LoD noise factor applied).  The out-of-core cache model decides per SPT
+ * root from these (Sec. 4.4, Eq. 7). */
+int or_select_upper(int64_t n_upper, const int64_t *up_node, const int32_t *up_kind, const int64_t *up_child,
+                    const int64_t *up_ref, int stride, const float *node_rec, const float *cam, int cull,
+                    int64_t *sel, int64_t *n_sel, int64_t *spt_j, float *spt_x, int64_t *n_spt) {
+    cam_t k;
+    cam_setup(cam, &k);
+    int64_t stats[5] = {0};
+    sptq_t *sq = malloc(sizeof(sptq_t) * (size_t)(n_upper + 1));
+    int64_t ns = 0, nq = 0;
+    upper_bfs(n_upper, up_node, up_kind, up_child, up_ref, stride, node_rec, &k, cull, sel, &ns, sq, &nq, stats);
+    for (int64_t q = 0; q < nq; ++q) { spt_j[q] = sq[q].j; spt_x[q] = sq[q].x; }
+    *n_sel = ns;
+    *n_spt = nq;
     free(sq);
     return 0;
 }
@@ -882,17 +915,15 @@ int or_sort_pairs(int64_t n, const int32_t *vis, const int32_t *rect, const uint
 /* that takes T below the bound is still blended and the pixel stops after    */
 /* it, so the neglected tail is at most 1e-4 times the largest colour.        */
 /* ------------------------------------------------------------------------- */
-/* Block support test D10 (float32, evaluated as written).  The image is cut
- * into 8x8 pixel blocks (four per tile); block (bx0, by0) has pixel centres
- * bx0 + 0.5 .. bx0 + 7.5 (same in y), centre bx0 + 4 and half span 3.5.  A
- * pixel tests Gaussian g (u, v, rx, ry = g[0], g[1], g[5], g[6]) only if the
- * support box |u - x| <= rx, |v - y| <= ry can reach a centre of its block. */
-static int g_block_cull = 1;
-
-void or_set_block_cull(int on) { g_block_cull = on; }
-
+/* Block support test D10 (float32, evaluated as written): the predicate the
+ * CUDA blend uses to skip a Gaussian for a whole 8x8 pixel block, kept here
+ * for the brute-force check that it is conservative; or_blend and
+ * or_blend_backward below do not call it.  The image is cut into 8x8 pixel
+ * blocks (four per tile); block (bx0, by0) has pixel centres bx0 + 0.5 ..
+ * bx0 + 7.5 (same in y), centre bx0 + 4 and half span 3.5.  Gaussian g (u, v,
+ * rx, ry = g[0], g[1], g[5], g[6]) is kept for the block iff its support box
+ * |u - x| <= rx, |v - y| <= ry can reach a centre of the block. */
 int or_block_keep(const float *g, int px, int py) {
-    if (!g_block_cull) return 1;
     float wcx = (float)(px & ~7) + 4.0f, wcy = (float)(py & ~7) + 4.0f;
     return !(fabsf(g[0] - wcx) > g[5] + 3.5f || fabsf(g[1] - wcy) > g[6] + 3.5f);
 }
@@ -917,7 +948,6 @@ int or_blend(int W, int H, const double *bg, const int64_t *tile_start, const in
             for (int64_t e = tile_start[t]; e < tile_start[t + 1]; ++e) {
                 int64_t i = pair_i[e];
                 const float *g = f32 + F32_N * i;
-                if (!or_block_keep(g, px, py)) continue;
                 if (support_p(g[0], g[1], g[2], g[3], g[4], px, py) < SUPPORT_P) continue;
                 const double *q = f64 + 12 * i;
                 double dx = q[0] - (px + 0.5), dy = q[1] - (py + 0.5);
@@ -963,7 +993,6 @@ int or_blend_backward(int W, int H, const double *bg, const int64_t *tile_start,
             for (int64_t e = tile_start[t]; e < tile_start[t + 1]; ++e) {
                 int64_t i = pair_i[e];
                 const float *g = f32 + F32_N * i;
-                if (!or_block_keep(g, px, py)) continue;
                 if (support_p(g[0], g[1], g[2], g[3], g[4], px, py) < SUPPORT_P) continue;
                 const double *q = f64 + 12 * i;
                 double dx = q[0] - (px + 0.5), dy = q[1] - (py + 0.5);

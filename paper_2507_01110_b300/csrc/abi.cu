@@ -75,13 +75,15 @@ CamK make_camk(const lodgs_camera &c) {
 using namespace lodgs;
 
 
-namespace {
-
+namespace lodgs {
 bool camera_ok(const lodgs_camera *c) {
     return c && c->width > 0 && c->height > 0 && c->width <= 65535 * TILE && c->height <= 65535 * TILE &&
            c->fx > 0 && c->fy > 0 && c->tau > 0 && c->znear > 0 && isfinite(c->fx) && isfinite(c->fy) &&
            isfinite(c->cx) && isfinite(c->cy) && isfinite(c->tau) && isfinite(c->spt_scale) && c->spt_scale >= 0;
 }
+}  // namespace lodgs
+
+namespace {
 
 template <typename T>
 int grow(T *&p, uint64_t &cap, uint64_t want, size_t elem_per = 1) {

@@ -656,7 +656,7 @@ int lodgs_stream_nodes(lodgs_scene *sc, lodgs_cache *c, const lodgs_camera *cam,
         set_error("stream_nodes: the cache was created before the scene was densified; create a new cache");
         return LODGS_E_STATE;
     }
-    if (!(cam->width > 0 && cam->height > 0 && cam->fx > 0 && cam->fy > 0 && cam->tau > 0 && cam->znear > 0)) {
+    if (!camera_ok(cam)) {
         set_error("stream_nodes: invalid camera");
         return LODGS_E_INVALID;
     }

@@ -215,6 +215,7 @@ int load_scene(const char *path, lodgs_scene *sc);
 // 0 if `fr` belongs to `sc` and was created for its current layout, else an
 // error code (with the message set, prefixed by `who`)
 int check_frame(const lodgs_scene *sc, const lodgs_frame *fr, const char *who);
+bool camera_ok(const lodgs_camera *c);   // the camera checks every entry point applies
 // sparse Adam over `rows` of params/m/v/t (lodgs_adam_step's contract); dirty[row] = 1 if given
 int launch_adam(const lodgs_scene *sc, float *params, float *m, float *v, uint32_t *t, const uint32_t *rows,
                 const float *grads, const uint32_t *d_n, int64_t max_n, const float *lr, float b1, float b2,

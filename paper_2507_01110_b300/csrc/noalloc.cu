@@ -1,16 +1,20 @@
 // LoD cut into caller-owned buffers with no device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (allocation calls are not allowed there), code bound to its
-// own memory arena or pool, and latency-critical loops where cudaMalloc's
-// implicit device synchronisation is unacceptable.  This variant of
+// Some callers cannot call cudaMalloc: an application whose device memory is
+// all handed to its own arena or pool (a renderer or game engine that budgets
+// every byte itself), and latency-critical loops where cudaMalloc's implicit
+// device synchronisation would stall other work on the GPU.  This variant of
 // lodgs_select_lod keeps its scratch (counters, per-SPT lists, block counts) in
 // one file-scope __device__ array instead of a frame's workspace.
 //
 // The array lives in every GPU that loads the library until the process exits
 // and is shared by all calls on that GPU: calls that overlap on the device
 // (concurrent streams, threads) race on it and must be serialised by the
-// caller.  Its counters are cleared at the start of every call.
+// caller.  Its counters are cleared at the start of every call.  The array's
+// device address is looked up once per device, on the first call there, and
+// kept for the life of the process: after cudaDeviceReset the kept address is
+// stale, so a process that resets a device must not call this entry point on
+// it again.
 #include <mutex>
 
 #include "lodgs_internal.cuh"
@@ -77,7 +81,7 @@ extern "C" int lodgs_select_lod_noalloc(lodgs_scene *scene, const lodgs_camera *
                   " SPTs, more than the static scratch holds (" + std::to_string(NA_MAX_SPT) + ")");
         return LODGS_E_INVALID;
     }
-    if (!(cam->width > 0 && cam->height > 0 && cam->fx > 0 && cam->fy > 0 && cam->tau > 0 && cam->znear > 0)) {
+    if (!camera_ok(cam)) {
         set_error("select_lod_noalloc: invalid camera");
         return LODGS_E_INVALID;
     }

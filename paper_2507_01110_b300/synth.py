@@ -206,6 +206,12 @@ def target_image(seed: int, height: int, width: int) -> np.ndarray:
     return uniform(seed, 7, idx).astype(np.float32).reshape(height, width, 3)
 
 
+def target_bytes(seed: int, height: int, width: int) -> np.ndarray:
+    """Seeded 8-bit RGB target image (bytes uniform on 0..255), HWC uint8."""
+    idx = np.arange(height * width * 3, dtype=np.uint64)
+    return np.minimum(np.floor(uniform(seed, 8, idx) * 256.0), 255.0).astype(np.uint8).reshape(height, width, 3)
+
+
 # ---------------------------------------------------------------------------
 # named workloads
 # ---------------------------------------------------------------------------
@@ -323,6 +329,18 @@ def city_leaves_t(n: int, seed: int, degree: int = 3, extent: float = 2000.0, bl
         for k in range(3 * K):
             rec[:, REC_F + k] = (sh_sigma * normal_t(seed, 40 + k, i)).float()
     return out
+
+
+def flyover_path(n: int = 40, width: int = 320, height: int = 180) -> list[Camera]:
+    """A slow pass over the 300 m ground-and-boxes scene at altitude 35 -> 25 m,
+    looking forward and down; the view distance changes by under a percent a
+    view."""
+    cams = []
+    for i in range(n):
+        s = i / (n - 1)
+        pos = [-100.0 + 200.0 * s, -60.0, 35.0 - 10.0 * s]
+        cams.append(camera_look(pos, [0.3, 1.0, -0.7], [1.0, -0.3, 0.0], width, height, tau=1.0))
+    return cams
 
 
 def flythrough_path(n_views: int = 200, width: int = 1920, height: int = 1080, alt_hi: float = 300.0,

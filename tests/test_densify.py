@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2507_01110_b300 import synth
-from paper_2507_01110_b300 import densify as dplan
+from oracle import densify_plan as dplan
 
 REC_S, REC_OP = 3, 10
 

@@ -83,6 +83,43 @@ def test_reuse_window_gives_hits_and_proper_cuts(world):
     assert hits > 0 and loaded_bytes > 0
 
 
+def test_stream_nodes_matches_the_oracle_cache_model():
+    """lodgs_stream_nodes against the oracle's cache model (Eq. 7 window
+    [0.9, 1.1], LRU eviction, Algorithm 3) on an 80-view out-and-back flyover
+    of a 20K-leaf scene through a slab of 1.3 times the largest view's prefix
+    records: per view the cut (render rows) bit for bit and every counter
+    (hits, re-cuts, loads, streamed bytes, evictions, cached SPTs and
+    records); every tenth view's image against the oracle's render of the
+    model's cut."""
+    import oracle
+    from oracle import cache as oc
+    from paper_2507_01110_b300 import api
+    leaves = synth.leaves_ground_and_boxes(20000, seed=43, degree=0, extent=300.0, n_boxes=40)
+    path = synth.flyover_path()
+    sc_o = oracle.build_scene(leaves, 0, 50.0, float(path[0].fx))
+    sc_g = api.build_hierarchy(leaves, 0, 50.0, float(path[0].fx))
+    cap = int(1.3 * max(oracle.select(sc_o, c)[1]["spt_scanned"] for c in path))
+    rec_bytes = sc_g.stride * 4
+    model = oc.NodeCache(sc_o, cap, 0.9, 1.1)
+    cache = api.Cache(sc_g, capacity_bytes=cap * rec_bytes, d_min=0.9, d_max=1.1)
+    fr = api.Frame(sc_g)
+    tot = dict.fromkeys(("spt_hits", "spt_resident", "spt_loaded", "evictions"), 0)
+    for i, cam in enumerate(path + path[::-1]):
+        _, st = api.stream_nodes(sc_g, cache, cam, fr)
+        rows_o, st_o = model.view(cam)
+        assert np.array_equal(fr.selection().cpu().numpy(), rows_o), i
+        for k in ("spt_hits", "spt_resident", "spt_loaded", "evictions", "cached_spts", "cached_records"):
+            assert st[k] == st_o[k], (i, k, st[k], st_o[k])
+        assert st["bytes_streamed"] == st_o["records_streamed"] * rec_bytes
+        for k in tot:
+            tot[k] += st[k]
+        if i % 10 == 0:
+            img = api.render(sc_g, fr, rows=cache.records).cpu().numpy()
+            ref = oracle.render(sc_o, cam, sel=rows_o)["image"]
+            assert np.abs(img - ref).max() <= 2e-4
+    assert all(v > 0 for v in tot.values()), tot
+
+
 def test_released_scene_rows_need_cache_records(world):
     from paper_2507_01110_b300 import _lib
     api, _, cams = world

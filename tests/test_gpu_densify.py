@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from paper_2507_01110_b300 import synth
-from paper_2507_01110_b300 import densify as dplan
+from oracle import densify_plan as dplan
 from test_gpu_parity import _assert_scene_equal, _compare_render
 
 pytestmark = pytest.mark.gpu

@@ -318,6 +318,96 @@ def test_select_is_proper_cut_and_matches_bruteforce(oracle_lib, scene1):
         assert np.all(cov_c <= cov_n)                     # culling only removes coverage
 
 
+def _corner_ray_planes(cam):
+    """The view frustum's four side planes rebuilt in float64 from the pinhole
+    model alone: each plane holds the camera centre and two adjacent image
+    corner rays ((x - cx)/fx, (y - cy)/fy, 1); its unit normal points to the
+    side of the image centre's ray."""
+    W, H = float(cam.width), float(cam.height)
+    fx, fy, cx, cy = (float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy))
+    ray = lambda x, y: np.array([(x - cx) / fx, (y - cy) / fy, 1.0])
+    corners = [ray(0, 0), ray(W, 0), ray(W, H), ray(0, H)]
+    inside = ray(0.5 * W, 0.5 * H)
+    planes = []
+    for a, b in zip(corners, corners[1:] + corners[:1]):
+        n = np.cross(a, b)
+        n /= np.linalg.norm(n)
+        planes.append(n if n @ inside > 0 else -n)
+    return planes
+
+
+def test_frustum_culling_matches_corner_ray_planes(oracle_lib):
+    """Sec. 4.3 "Frustum Culling": a sphere is dropped iff it lies wholly behind
+    the near plane or wholly outside one side plane.  Against side planes built
+    independently from the image corner rays (float64), on cameras with an
+    off-centre principal point, fx != fy and W != H, the oracle culls exactly
+    the spheres the rebuilt planes cull, wherever the float64 margin exceeds
+    float32 rounding.  A plane tilted inwards, or cx and W - cx swapped, fails."""
+    import dataclasses
+    rng = np.random.default_rng(51)
+    n_cull = n_keep = n_side = 0
+    for it in range(24):
+        W, H = int(rng.integers(64, 400)), int(rng.integers(48, 300))
+        cam = synth.camera_look(rng.normal(0, 20, 3), rng.normal(size=3), rng.normal(size=3), W, H,
+                                fovx_deg=float(rng.uniform(30, 100)), znear=float(rng.uniform(0.05, 2.0)))
+        cam = dataclasses.replace(cam, fy=np.float32(cam.fx * rng.uniform(0.7, 1.4)),
+                                  cx=np.float32(W * rng.uniform(0.2, 0.8)), cy=np.float32(H * rng.uniform(0.2, 0.8)))
+        planes = _corner_ray_planes(cam)
+        R, pos = cam.R.astype(np.float64), cam.pos.astype(np.float64)
+        for _ in range(400):
+            # points around the frustum's boundary: a direction through the image
+            # (or just beyond it) at a random depth, pushed sideways
+            x, y = rng.uniform(-0.4 * W, 1.4 * W), rng.uniform(-0.4 * H, 1.4 * H)
+            z = rng.uniform(-5.0, 60.0)
+            t = np.array([(x - float(cam.cx)) / float(cam.fx) * z, (y - float(cam.cy)) / float(cam.fy) * z, z])
+            rad = float(np.float32(rng.choice([0.01, 0.3, 2.0, 8.0])))
+            mu = (R.T @ t + pos).astype(np.float32)
+            t64 = R @ (mu.astype(np.float64) - pos)          # the float32 centre, exactly
+            ms = np.float32(rad / 3.0)
+            r64 = 3.0 * float(ms)
+            margins = [n @ t64 + r64 for n in planes] + [t64[2] + r64 - float(cam.znear)]
+            tol = 1e-4 * (np.linalg.norm(t64) + r64 + 1.0)
+            if min(abs(m) for m in margins) < tol:
+                continue                                      # within float32 rounding of a plane
+            expect = min(margins) < 0
+            got = oracle_lib.cull_sphere(cam, mu, float(ms))
+            assert got == expect, (it, margins)
+            n_cull += expect
+            n_keep += not expect
+            n_side += expect and min(margins[:4]) < 0 and margins[4] > 0
+    assert n_cull > 2000 and n_keep > 2000 and n_side > 1000
+
+
+def test_culling_drops_only_what_cannot_be_seen_up_to_the_subtree_proxy(oracle_lib, scene1):
+    """Culling on against culling off, image by image.  Sec. 4.3 culls a whole
+    subtree by its root's sphere (radius 3 max s) and says that this proxy for
+    the subtree's extent is not exact.  So, of the nodes a cull-off cut adds
+    (E), those whose own sphere is outside the frustum must change no pixel,
+    bit for bit, and every pixel that does change must come from the rest:
+    descendants of a culled node whose own sphere reaches the frustum, a small
+    fraction of E."""
+    cfg, sc = scene1
+    bg = (0.2, 0.1, 0.3)
+    cams = [synth.camera_look([5.0, -3.0, -20.0], [0.2, 0.1, 1.0], [1.0, 0.0, 0.0], 160, 120, tau=1.0),
+            synth.camera_look([30.0, 20.0, -90.0], [-0.2, -0.1, 1.0], [1.0, 0.0, 0.0], 256, 200, tau=1.0),
+            synth.camera_look([0.0, 0.0, 0.0], [0.3, 0.2, 1.0], [1.0, 0.0, 0.0], 160, 160, tau=0.5)]
+    n_e = n_leak = 0
+    for cam in cams:
+        on = oracle_lib.render(sc, cam, bg=bg, cull=True)
+        off = oracle_lib.render(sc, cam, bg=bg, cull=False)
+        E = np.setdiff1d(off["sel"], on["sel"])
+        assert len(np.setdiff1d(on["sel"], off["sel"])) == 0
+        rec = sc["row_rec"][E]
+        own = np.array([oracle_lib.cull_sphere(cam, r[:3], float(r[3:6].max())) for r in rec], dtype=bool)
+        with_out = oracle_lib.render(sc, cam, bg=bg, sel=np.union1d(on["sel"], E[own]))
+        with_leak = oracle_lib.render(sc, cam, bg=bg, sel=np.union1d(on["sel"], E[~own]))
+        assert np.array_equal(with_out["image"], on["image"])
+        assert np.array_equal(with_leak["image"], off["image"])
+        n_e += len(E)
+        n_leak += int((~own).sum())
+    assert n_e > 10_000 and n_leak <= n_e // 1000
+
+
 def test_upper_bfs_matches_recursive_dfs(scene1):
     """Algorithm 1 (queue) against a textbook recursion with the same predicates."""
     import oracle
@@ -618,38 +708,36 @@ def test_block_support_test_is_conservative(oracle_lib):
     assert max(kaps) > 1e5 and sum(1e3 < k < 1e5 for k in kaps) > 20
 
 
-def test_block_culling_leaves_image_and_gradients_unchanged(oracle_lib, scene1):
-    """Blend and its backward with and without D10 give the same image and
-    2D gradients, bit for bit, on a real view."""
+def test_block_test_skips_no_supported_pixel_on_a_real_view(oracle_lib, scene1):
+    """On a config-1 view, for every listed (tile, Gaussian) pair of the first
+    three tile rows and every 8x8 block of the tile that D10 skips, no pixel
+    centre of the block passes the float32 support test D8 (brute force); and
+    the test does skip blocks there, so it is not vacuous.  The oracle's own
+    blend and backward never call D10."""
     cfg, sc = scene1
     cam = cfg["cameras"][0]
     sel, _ = oracle_lib.select(sc, cam)
     pr = oracle_lib.project(sc, sel, cam)
     pairs = oracle_lib.sort_pairs(pr, cam.width, cam.height)
-    rng = np.random.default_rng(5)
-    dL = rng.standard_normal((cam.height, cam.width, 3))
-    win = (0, 0, cam.width, min(cam.height, 48))
-    try:
-        oracle_lib.set_block_cull(False)
-        a = oracle_lib.blend(pr, pairs, cam.width, cam.height, bg=(0.2, 0.1, 0.3), window=win)
-        ga = oracle_lib.blend_backward(pr, pairs, cam.width, cam.height, dL, bg=(0.2, 0.1, 0.3), window=win)
-    finally:
-        oracle_lib.set_block_cull(True)
-    b = oracle_lib.blend(pr, pairs, cam.width, cam.height, bg=(0.2, 0.1, 0.3), window=win)
-    gb = oracle_lib.blend_backward(pr, pairs, cam.width, cam.height, dL, bg=(0.2, 0.1, 0.3), window=win)
-    assert np.array_equal(a["image"], b["image"]) and np.array_equal(a["n_contrib"], b["n_contrib"])
-    assert np.array_equal(ga, gb) and np.abs(ga).max() > 0
-    # the test is not vacuous: some (pixel, Gaussian) evaluations of the view are skipped
     f = pr["f32"]
     ts = pairs["tile_start"]
     TX = pairs["TX"]
-    skips = 0
+    skips = checked = 0
     for t in range(0, min(len(ts) - 1, 3 * TX)):
+        x0, y0 = (t % TX) * 16, (t // TX) * 16
         for e in range(ts[t], ts[t + 1]):
             gi = f[pairs["pair_i"][e]]
-            x0, y0 = (t % TX) * 16, (t // TX) * 16
-            skips += sum(not oracle_lib.block_keep(gi, x0 + 8 * i, y0 + 8 * j) for i in range(2) for j in range(2))
-    assert skips > 0
+            for j in range(2):
+                for i in range(2):
+                    bx, by = x0 + 8 * i, y0 + 8 * j
+                    if oracle_lib.block_keep(gi, bx, by):
+                        continue
+                    skips += 1
+                    ys, xs = np.mgrid[by:by + 8, bx:bx + 8]
+                    p = _support_f32_grid(gi[0], gi[1], gi[2], gi[3], gi[4], xs, ys)
+                    assert not (p >= np.float32(-4.5)).any(), (t, e, i, j)
+                    checked += 64
+    assert skips > 0 and checked > 0
 
 
 def test_tile_culling_leaves_the_image_unchanged(oracle_lib, scene1):
@@ -721,47 +809,154 @@ def test_blend_transmittance_and_transparent_scene(oracle_lib, scene1):
     assert np.allclose(o2["image"], np.array([0.2, 0.4, 0.6]), atol=0)
 
 
+def _untruncated_eq1(proj, pairs, W, H, bg):
+    """Eq. 1 without truncation, per tile in numpy: every listed Gaussian that
+    passes the float32 support test D8 at a pixel is composited, however small
+    the transmittance in front of it."""
+    img = np.zeros((H, W, 3))
+    f32, f64 = proj["f32"], proj["f64"]
+    ts, TX = pairs["tile_start"], pairs["TX"]
+    for t in range(len(ts) - 1):
+        x0, y0 = (t % TX) * 16, (t // TX) * 16
+        ys, xs = np.mgrid[y0:min(y0 + 16, H), x0:min(x0 + 16, W)]
+        ids = pairs["pair_i"][ts[t]:ts[t + 1]]
+        if len(ids) == 0:
+            img[ys, xs] = bg
+            continue
+        g, q = f32[ids], f64[ids]
+        sup = _support_f32_grid(g[:, 0, None, None], g[:, 1, None, None], g[:, 2, None, None],
+                                g[:, 3, None, None], g[:, 4, None, None], xs[None], ys[None]) >= np.float32(-4.5)
+        dx, dy = q[:, 0, None, None] - (xs[None] + 0.5), q[:, 1, None, None] - (ys[None] + 0.5)
+        p = -0.5 * (q[:, 2, None, None] * dx * dx + q[:, 4, None, None] * dy * dy) - q[:, 3, None, None] * dx * dy
+        alpha = np.where(sup, np.minimum(0.99, q[:, 5, None, None] * np.exp(p)), 0.0)
+        T = np.cumprod(np.concatenate([np.ones((1,) + alpha.shape[1:]), 1.0 - alpha]), axis=0)
+        img[ys, xs] = np.einsum("kyx,kc->yxc", alpha * T[:-1], q[:, 6:9]) + T[-1][..., None] * np.asarray(bg)
+    return img
+
+
+def test_transmittance_truncation_bound_against_untruncated_eq1(oracle_lib, scene1):
+    """Eq. 1 truncated at T < 1e-4 (the Gaussian that takes T below the bound
+    is still composited, then the pixel stops) differs from the untruncated sum
+    by at most 1e-4 times the largest colour or background value: what is
+    dropped is composited behind a transmittance already below 1e-4.  The 3DGS
+    rule, which skips that Gaussian, drops alpha T c with T up to 1e-2 and
+    fails.  On a config-1 view with over a thousand truncated pixels."""
+    cfg, sc = scene1
+    cam = cfg["cameras"][0]
+    bg = (0.3, 0.6, 0.9)
+    out = oracle_lib.render(sc, cam, bg=bg)
+    stopped = out["T_final"] < 1e-4
+    assert stopped.sum() > 1000
+    full = _untruncated_eq1(out["proj"], out["pairs"], cam.width, cam.height, bg)
+    cmax = max(out["proj"]["f64"][:, 6:9].max(), max(bg))
+    d = np.abs(out["image"] - full).max(axis=2)
+    assert d.max() <= 1e-4 * cmax, d.max() / cmax
+    assert d[~stopped].max() <= 1e-12 and d[stopped].max() > 0
+
+
+def test_the_gaussian_crossing_the_transmittance_bound_is_composited(oracle_lib):
+    """A stack of equal on-axis Gaussians in front of the pixel (16, 12):
+    with alpha ~ 0.6 each, T falls below 1e-4 at the eleventh.  The eleventh
+    (red) must appear in the pixel with weight alpha T_10, the twelfth (blue)
+    must not, and the first ten (green) are composited in full."""
+    st = synth.record_stride(0)
+    cam = synth.camera_look([0, 0, -10.0], [0, 0, 1], [1, 0, 0], 32, 24)
+    recs = []
+    for k in range(14):
+        col = (1, 0, 0) if k == 10 else ((0, 0, 1) if k == 11 else (0, 1, 0))
+        recs.append(_rec(st, (0, 0, 0.5 * k), (2.0, 2.0, 2.0), op=0.6, b=col))
+    scene, sel = _one_gaussian_scene(np.stack(recs))
+    out = oracle_lib.render(scene, cam, sel=sel)
+    f = out["proj"]["f64"]
+    order = np.argsort(f[:, 9], kind="stable")
+    assert np.array_equal(order, np.arange(14))                  # depth order = index order
+    dx, dy = f[:, 0] - 16.5, f[:, 1] - 12.5
+    alpha = np.minimum(0.99, f[:, 5] * np.exp(-0.5 * (f[:, 2] * dx * dx + f[:, 4] * dy * dy) - f[:, 3] * dx * dy))
+    T = np.cumprod(np.concatenate([[1.0], 1.0 - alpha]))
+    assert T[10] >= 1e-4 > T[11]                                  # the eleventh crosses the bound
+    px = out["image"][12, 16]
+    assert px[0] == pytest.approx(alpha[10] * T[10], rel=1e-12) and px[0] > 0
+    assert px[2] == 0.0
+    assert px[1] == pytest.approx(float(np.sum(alpha[:10] * T[:10])), rel=1e-12)
+    assert out["T_final"][12, 16] == pytest.approx(T[11], rel=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # backward: finite differences on the oracle's own forward
 # ---------------------------------------------------------------------------
 
-def _fd_scene(degree, rng, n=6, clamp_case=False):
+def _fd_scene(degree, rng, n=6, case=None):
+    """Six overlapping Gaussians in front of a 32x24 camera.  case:
+    "jacobian": Gaussian 0 centred off-screen (clamped Jacobian);
+    "alpha":    Gaussian 0 narrow, opacity 0.999, centred on pixel (16, 12), so
+                alpha = min(0.99, sigma exp(p)) is clamped at that pixel;
+    "negative": Gaussian 1's raw red channel b + sum Y f is -0.3 (clamped at 0)."""
     st = synth.record_stride(degree)
+    cam = synth.camera_look([0.1, -0.05, -6.0], [0.02, 0.01, 1.0], [1, 0, 0], 32, 24)
     recs = []
     for i in range(n):
         q = rng.normal(size=4); q /= np.linalg.norm(q)
         mu = (rng.uniform(-0.6, 0.6), rng.uniform(-0.6, 0.6), rng.uniform(-0.5, 2.0))
         scales = rng.uniform(3.0, 4.5, 3)
-        if clamp_case and i == 0:
+        op = rng.uniform(0.1, 0.45)
+        if case == "jacobian" and i == 0:
             mu = (9.0, 0.2, 1.0)                                  # centre off-screen: clamped Jacobian
             scales = np.array([8.0, 7.0, 9.0])
-        r = _rec(st, mu, scales, q, op=rng.uniform(0.1, 0.45), b=rng.uniform(0.3, 0.7, 3))
+        if case == "alpha" and i == 0:
+            z = 7.0                                               # depth of the pixel-centre ray point
+            t = np.array([(16.5 - float(cam.cx)) / float(cam.fx) * z, (12.5 - float(cam.cy)) / float(cam.fy) * z, z])
+            mu = cam.R.astype(np.float64).T @ t + cam.pos.astype(np.float64)
+            scales, op = np.array([0.5, 0.7, 0.6]), 0.999
+        r = _rec(st, mu, scales, q, op=op, b=rng.uniform(0.3, 0.7, 3))
         if degree:
             r[14:14 + 3 * ((degree + 1) ** 2 - 1)] = rng.normal(0, 0.05, 3 * ((degree + 1) ** 2 - 1))
+        if case == "negative" and i == 1:
+            import oracle
+            d = r[0:3].astype(np.float64) - cam.pos.astype(np.float64)
+            Y, _ = oracle.sh_eval(degree, d / np.linalg.norm(d))
+            r[REC_B] = 0.1
+            r[14 + 0:14 + 3 * len(Y):3] = ((-0.3 - 0.1) * Y / (Y @ Y)).astype(np.float32)
         recs.append(r)
-    cam = synth.camera_look([0.1, -0.05, -6.0], [0.02, 0.01, 1.0], [1, 0, 0], 32, 24)
     return np.stack(recs), cam
 
 
-@pytest.mark.parametrize("degree,clamp_case", [(0, False), (3, False), (1, True)])
-def test_backward_matches_finite_differences(oracle_lib, degree, clamp_case):
+@pytest.mark.parametrize("degree,case", [(0, None), (3, None), (1, "jacobian"), (0, "alpha"), (3, "negative")])
+def test_backward_matches_finite_differences(oracle_lib, degree, case):
+    """The oracle's hand-derived gradients against central differences of its own
+    forward, including the three clamped branches: the Jacobian clamp, the
+    alpha clamp at 0.99 (zero gradient through alpha where it binds) and the
+    colour clamp at 0 (zero gradient through a negative raw channel)."""
     rng = np.random.default_rng(10 + degree)
-    recs, cam = _fd_scene(degree, rng, clamp_case=clamp_case)
+    recs, cam = _fd_scene(degree, rng, case=case)
     scene, sel = _one_gaussian_scene(recs, degree)
     bg = (0.05, 0.1, 0.15)
     fwd = oracle_lib.render(scene, cam, bg=bg, sel=sel)
     assert fwd["proj"]["vis"].all()
     assert np.all(fwd["proj"]["rect"] == [0, 0, 2, 2])
-    f = fwd["proj"]["f64"]                                        # support edge outside the image:
-    py, px = np.mgrid[0:cam.height, 0:cam.width]                  # the float32 test never flips
-    for i in range(recs.shape[0]):
-        dx, dy = f[i, 0] - (px + 0.5), f[i, 1] - (py + 0.5)
-        p = -0.5 * (f[i, 2] * dx * dx + f[i, 4] * dy * dy) - f[i, 3] * dx * dy
-        assert p.min() > -4.3
-    if clamp_case:
+    py, px = np.mgrid[0:cam.height, 0:cam.width]
+
+    def masks(proj, i):
+        """Gaussian i's pixel decisions: the float32 support test D8 and the alpha clamp."""
+        f32, f64 = proj["f32"][i], proj["f64"][i]
+        sup = _support_f32_grid(f32[0], f32[1], f32[2], f32[3], f32[4], px, py) >= np.float32(-4.5)
+        dx, dy = f64[0] - (px + 0.5), f64[1] - (py + 0.5)
+        p = -0.5 * (f64[2] * dx * dx + f64[4] * dy * dy) - f64[3] * dx * dy
+        return sup, f64[5] * np.exp(p) > 0.99
+
+    base_masks = [masks(fwd["proj"], i) for i in range(recs.shape[0])]
+    f = fwd["proj"]["f64"]
+    if case == "alpha":
+        assert base_masks[0][1].sum() == 1 and base_masks[0][0].sum() < 0.8 * px.size
+        assert sum(m[1].sum() for m in base_masks[1:]) == 0    # clamped at one pixel, by Gaussian 0
+    if case == "jacobian":
         assert f[0, 0] > cam.width                                # centre off-screen
+    if case == "negative":
+        assert f[1, 6] == 0.0 and f[1, 7] > 0 and f[1, 8] > 0    # red clamped at 0
     wimg = np.random.default_rng(99).uniform(-1, 1, fwd["image"].shape)
     g = oracle_lib.render_backward(scene, cam, fwd, wimg, bg=bg)["g_rec"]
+    if case == "negative":
+        K = (degree + 1) ** 2 - 1
+        assert g[1, REC_B] == 0.0 and not np.any(g[1, 14:14 + 3 * K:3])
     K = (degree + 1) ** 2 - 1
     cols = list(range(0, 14 + 3 * K))
     for i in range(recs.shape[0]):
@@ -773,7 +968,10 @@ def test_backward_matches_finite_differences(oracle_lib, degree, clamp_case):
                 rr = recs.copy()
                 rr[i, c] = np.float32(base + sgn * h)
                 sc2, _ = _one_gaussian_scene(rr, degree)
-                vals.append((oracle_lib.render(sc2, cam, bg=bg, sel=sel)["image"] * wimg).sum())
+                out2 = oracle_lib.render(sc2, cam, bg=bg, sel=sel)
+                m2 = masks(out2["proj"], i)                   # the step flips no decision
+                assert np.array_equal(m2[0], base_masks[i][0]) and np.array_equal(m2[1], base_masks[i][1]), (i, c)
+                vals.append((out2["image"] * wimg).sum())
             hp = float(np.float32(base + h)) - float(np.float32(base - h))
             num = (vals[0] - vals[1]) / hp
             assert g[i, c] == pytest.approx(num, rel=2e-3, abs=2e-4 * (1 + abs(num))), (i, c)
