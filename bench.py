@@ -173,6 +173,19 @@ def stage_bytes(stage: str, st: dict, record_bytes: int, n_upper: int, tile_pass
 # ---------------------------------------------------------------------------
 # CUDA arm
 # ---------------------------------------------------------------------------
+def spread_views(views: list, steps: int) -> list:
+    """The views `steps` timed steps take, spread evenly over the path: with
+    fewer steps than views, views evenly spaced from the first to the last, so
+    a short run still averages aerial and street views alike; with more, the
+    path repeated."""
+    n = len(views)
+    if steps >= n:
+        return [views[i % n] for i in range(steps)]
+    if steps == 1:
+        return [views[0]]
+    return [views[(2 * i * (n - 1) + steps - 1) // (2 * (steps - 1))] for i in range(steps)]
+
+
 def shard_views(n_views: int, rank: int, world: int) -> list:
     """The views rank `rank` of `world` renders: every world-th view from its
     rank on (views are independent units: no exchange between ranks).  With
@@ -207,8 +220,6 @@ def run_lodgs(args, rank: int, world: int):
     cams = cfg["cameras"]
     nv = len(cams)
     scene = api.build_hierarchy(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
-    leaves_host = cfg.pop("leaves")
-    del leaves_host
     H, W = cams[0].height, cams[0].width
     # views of this rank (independent units: no exchange between ranks)
     my_views = shard_views(nv, rank, world)
@@ -252,7 +263,7 @@ def run_lodgs(args, rank: int, world: int):
         step_bwd_project(v)
         return loss_slots[v:v + 1]
 
-    order = [my_views[i % len(my_views)] for i in range(args.steps)]
+    order = spread_views(my_views, args.steps)
     for i in range(args.warmup):
         v = my_views[i % len(my_views)]
         step(v, targets_d[v], cams[v])
@@ -461,7 +472,9 @@ def run_lodgs(args, rank: int, world: int):
 # clock is the issue peak for any instruction type.
 OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB = 6, 11, 34
 # DRAM bytes (read + write) per k_blend_bwd launch, mean over the 32 views of
-# this workload, from one ncu capture (profiles/launches_fwd_bwd_1080p_2Mleaves.md)
+# this workload, from one ncu capture of the launch list with
+# dram__bytes_read.sum and dram__bytes_write.sum; a constant of the kernel's
+# code at that capture, to be taken again whenever the kernel changes
 BLEND_BWD_DRAM_BYTES = 39.3e6
 BLEND_BWD_ISSUE_ACTIVE = 0.809    # smsp__issue_active of the same kernel, one view (ncu --set full)
 FP32_LANES_PER_SM, N_SM = 128, 148
@@ -506,48 +519,64 @@ def roofline(res: dict, peaks: dict) -> dict:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_view_seconds(sc_o, cam, window_rows: int, target_seed: int) -> tuple[float, str]:
-    """Time select + project + sort on the full view and the blend + backward on
-    a band of `window_rows` pixel rows; scale the band to the full image."""
+def oracle_frame_seconds(sc_o, cam, target_seed: int) -> float:
+    """One whole view through the oracle, as the CUDA step does it: LoD select,
+    projection with SH colour, tile x depth sort, blend, the mean-L1 loss's
+    gradient against an 8-bit target, blend backward, projection backward."""
     import oracle
     from paper_2507_01110_b300 import synth
+    tb = synth.target_bytes(target_seed, cam.height, cam.width).astype(np.float64) / 255.0
     t0 = time.perf_counter()
-    sel, _ = oracle.select(sc_o, cam)
-    proj = oracle.project(sc_o, sel, cam)
-    pairs = oracle.sort_pairs(proj, cam.width, cam.height)
-    t_common = time.perf_counter() - t0
-    y0 = (cam.height - window_rows) // 2
-    win = (0, y0, cam.width, y0 + window_rows)
-    t1 = time.perf_counter()
-    out = oracle.blend(proj, pairs, cam.width, cam.height, window=win)
-    tgt = synth.target_image(target_seed, cam.height, cam.width)
-    dL = np.sign(out["image"] - tgt) / out["image"].size
-    g2d = oracle.blend_backward(proj, pairs, cam.width, cam.height, dL, window=win)
-    oracle.project_backward(sc_o, sel, cam, proj, g2d)
-    t_band = time.perf_counter() - t1
-    scale = cam.height / window_rows
-    return t_common + t_band * scale, f"rows {win[1]}-{win[3]} of {cam.height}"
+    out = oracle.render(sc_o, cam)
+    dL = np.sign(out["image"] - tb) / out["image"].size
+    oracle.render_backward(sc_o, cam, out, dL)
+    return time.perf_counter() - t0
 
 
-def cpu_baseline(cfg_leaves_fn, budget_s: float = 20.0) -> dict:
+def oracle_forward_seconds(sc_o, cam) -> float:
     import oracle
-    from paper_2507_01110_b300 import synth
-    cfg = cfg_leaves_fn()
+    t0 = time.perf_counter()
+    oracle.render(sc_o, cam)
+    return time.perf_counter() - t0
+
+
+def timed_legs(fn, views) -> dict:
+    """The oracle on one thread and on every host core (its OpenMP build):
+    seconds per view of fn(view), with the thread counts actually used."""
+    import oracle
+    out = {}
+    for leg, n in (("one_thread", 1), ("all_cores", None)):
+        threads = oracle.use_threads(n)
+        secs = [fn(v) for v in views]
+        out[leg] = {"threads": threads, "s_per_view": [round(x, 3) for x in secs],
+                    "frames_per_s": len(secs) / sum(secs)}
+    oracle.use_threads(1)
+    return out
+
+
+def cpu_baseline(cfg: dict) -> dict:
+    """The oracle timed on whole 1080p frames of the path's two ends, views 0
+    (aerial, the largest cut) and 31 (street), forward plus backward: once on
+    one thread (the reported value) and once on every host core."""
+    import oracle
     sc_o = oracle.build_scene(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
     cams = cfg["cameras"]
-    secs, views, desc = [], [0, 31], []
-    for v in views:
-        s, d = oracle_view_seconds(sc_o, cams[v], 68, 1000 + v)
-        secs.append(s)
-        desc.append(f"view {v}: {d}")
-    per_view = float(np.mean(secs))
-    return {"value": 1.0 / per_view, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": "float64 C oracle, one thread: select+project+sort on the full view, blend+backward on a "
-                      "68-row band scaled to 1080 rows; " + "; ".join(desc)}
+    legs = timed_legs(lambda v: oracle_frame_seconds(sc_o, cams[v], 300 + v), [0, 31])
+    one, allc = legs["one_thread"], legs["all_cores"]
+    return {"value": one["frames_per_s"], "unit": "frames/s", "cores": one["threads"], "kind": "oracle",
+            "sample": "float64 C oracle, whole 1920x1080 frames of views 0 and 31 (select + project + sort + "
+                      "blend + mean-L1 gradient + blend backward + projection backward), one thread; "
+                      f"seconds per view {one['s_per_view']}",
+            "host_cores": os.cpu_count(),
+            "all_cores": {"value": allc["frames_per_s"], "unit": "frames/s", "cores": allc["threads"],
+                          "s_per_view": allc["s_per_view"],
+                          "note": "the same oracle built with OpenMP: pixel rows and Gaussians in parallel"}}
 
 
 def run_reference(args, rank: int, world: int):
-    """The oracle as the reference arm: each step one view, bounded sample."""
+    """The oracle as the reference arm, on one host thread: each timed step one
+    whole view of the CUDA arm's view order (forward and backward, as the step
+    of that arm); each warm-up step a 16-row band of the street view."""
     import oracle
     from paper_2507_01110_b300 import synth
     if rank != 0:
@@ -555,21 +584,25 @@ def run_reference(args, rank: int, world: int):
     cfg = synth.config2_scene(n=args.leaves)
     sc_o = oracle.build_scene(cfg["leaves"], 3, cfg["spt_volume"], cfg["kappa"])
     cams = cfg["cameras"]
-    for i in range(args.warmup):
-        oracle_view_seconds(sc_o, cams[(i * 7) % len(cams)], 16, 1000 + i)
-    total = 0.0
-    for i in range(args.steps):
-        v = (i * 7) % len(cams)
-        s, _ = oracle_view_seconds(sc_o, cams[v], 16, 1000 + v)
-        total += s
-    value = args.steps / total
+    threads = oracle.use_threads(1)
+    for _ in range(args.warmup):
+        out = oracle.render(sc_o, cams[31], window=(0, 532, cams[31].width, 548))
+        oracle.render_backward(sc_o, cams[31], out, np.zeros_like(out["image"]),
+                               window=(0, 532, cams[31].width, 548))
+    order = spread_views(list(range(len(cams))), args.steps)
+    t0 = time.perf_counter()
+    per = [oracle_frame_seconds(sc_o, cams[v], 300 + v) for v in order]
+    total = time.perf_counter() - t0
+    value = len(order) / total
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step one view (views 0,7,14,..): select+project+sort full, "
-                                       "blend+backward on a 16-row band scaled to 1080 rows"},
+            "config": {"workload": WORKLOAD, "views_timed": order, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads, "kind": "oracle",
+                             "sample": "each timed step one whole 1920x1080 view of the CUDA arm's view order "
+                                       "(select + project + sort + blend + mean-L1 gradient + backward), "
+                                       "one thread, measured wall time",
+                             "host_cores": os.cpu_count(), "s_per_view": [round(x, 3) for x in per]},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -609,6 +642,67 @@ def run_serving(args) -> dict:
             "continuous_batching": {k: round(v, 3) if isinstance(v, float) else v for k, v in r_mix.items()},
             "one_at_a_time": {k: round(v, 3) if isinstance(v, float) else v for k, v in r_fifo.items()},
             "unit": "ms"}
+
+
+def run_config1(args) -> dict:
+    """The plain forward render: 65,536-leaf SH0 scene in a 100 m cube, one
+    256x256 camera at 60 deg, tau 1 px.  GPU frames/s of select + render as one
+    graph replay per frame, back to back (the 4 MB of records stay in L2) and
+    with L2 flushed before each frame (a 256 MB write, outside the per-frame
+    events); the oracle on whole frames, one thread and every host core."""
+    import torch
+
+    import oracle
+    from paper_2507_01110_b300 import api, synth
+    cfg = synth.config1_scene()
+    cam = cfg["cameras"][0]
+    scene = api.build_hierarchy(cfg["leaves"], 0, cfg["spt_volume"], cfg["kappa"])
+    fr = api.Frame(scene)
+    image = torch.empty((cam.height, cam.width, 3), device="cuda")
+    api.select_lod(scene, cam, fr)
+    api.render(scene, fr, image=image, check_capacity=True)
+    n_sel = fr.stats()["n_selected"]
+    api.set_view(fr, cam)
+    torch.cuda.synchronize()
+    cap = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(g, stream=cap):
+            api.select_lod(scene, None, fr)
+            api.render(scene, fr, image=image, bg=None, check_capacity=False)
+    for _ in range(20):
+        g.replay()
+    torch.cuda.synchronize()
+    reps = 2000
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    warm_ms = e0.elapsed_time(e1) / reps
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    cold = []
+    for _ in range(200):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        cold.append((a, b))
+    torch.cuda.synchronize()
+    cold_ms = float(np.mean([a.elapsed_time(b) for a, b in cold]))
+    sc_o = oracle.build_scene(cfg["leaves"], 0, cfg["spt_volume"], cfg["kappa"])
+    legs = timed_legs(lambda _: oracle_forward_seconds(sc_o, cam), [0, 1, 2])
+    return {"workload": "65,536-leaf SH0 scene (100 m cube), one 256x256 camera at 60 deg, tau 1 px, forward "
+                        "(select + render)", "selected": n_sel,
+            "frames_per_s_l2_warm": round(1e3 / warm_ms, 1), "ms_per_frame_l2_warm": round(warm_ms, 4),
+            "frames_per_s_l2_flushed": round(1e3 / cold_ms, 1), "ms_per_frame_l2_flushed": round(cold_ms, 4),
+            "cpu_oracle": {"one_thread": {"frames_per_s": round(legs["one_thread"]["frames_per_s"], 2),
+                                          "cores": legs["one_thread"]["threads"]},
+                           "all_cores": {"frames_per_s": round(legs["all_cores"]["frames_per_s"], 2),
+                                         "cores": legs["all_cores"]["threads"]},
+                           "sample": "three whole frames each"}}
 
 
 def run_lod_sweep(args) -> dict:
@@ -978,7 +1072,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "leaves": args.leaves, "nodes": res["scene"]["n_nodes"],
-                   "spt": res["scene"]["n_spt"], "views": 32, "resolution": "1920x1080", "tau_px": 1.0,
+                   "spt": res["scene"]["n_spt"], "views": 32, "views_timed": res["order"],
+                   "resolution": "1920x1080", "tau_px": 1.0,
                    "loss": "mean L1 against 8-bit RGB targets",
                    "l2": "inputs larger than L2 (node records 1.07 GB; per-view reads 100-400 MB)",
                    "parallelism": f"replicas x{world} (views split across ranks)"},
@@ -1014,10 +1109,13 @@ def main():
                             "work": f"algorithmic instructions = {OPS_EVAL + OPS_BWD_CONTRIB} per backward "
                                     f"contribution ({OPS_EVAL + OPS_BLEND} per forward blend)",
                             "work_per_view": rf["work"],
+                            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
+                                              "kernel, mean per launch over the 32 views (one capture of "
+                                              "the launch list on the current kernel code)",
                             "ncu_issue_active": BLEND_BWD_ISSUE_ACTIVE if dom == "blend_bwd" else None,
                             "ncu_note": "issue slots the kernel used, one 1080p view (ncu "
-                                        "smsp__issue_active, profiles/k_blend_bwd_1080p_2Mleaves.md); frac "
-                                        "counts only the method's instructions in those slots"}
+                                        "smsp__issue_active, --set full capture); frac counts only the "
+                                        "method's instructions in those slots"}
     line["roofline_stages"] = {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in rf["stages"].items()}
     def section(name, fn):
         try:
@@ -1027,6 +1125,8 @@ def main():
         import torch
         torch.cuda.empty_cache()
 
+    if world == 1:
+        section("config1", run_config1)
     if world == 1 and not args.no_out_of_core:
         section("out_of_core", run_out_of_core)
     if world == 1 and not args.no_lod_sweep:
@@ -1038,8 +1138,7 @@ def main():
     if world == 1 and not args.no_densify:
         section("densify", run_densify)
     if not args.no_cpu_baseline and world == 1:
-        from paper_2507_01110_b300 import synth
-        line["cpu_baseline"] = cpu_baseline(lambda: synth.config2_scene(n=args.leaves))
+        line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line))
 
 

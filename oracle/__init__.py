@@ -33,29 +33,45 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lodgs_oracle.c")
 _LIB = os.path.join(_HERE, "liblodgs_oracle.so")
-_lib = None
+_LIB_OMP = os.path.join(_HERE, "liblodgs_oracle_omp.so")
+_libs = {}
+_use_omp = False
 
 KIND_INTERNAL, KIND_LEAF, KIND_SPT = 0, 1, 2
 TILE = 16
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library with gcc (no fused multiply-add)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle shared library with gcc (no fused multiply-add).
+    omp=True builds the OpenMP variant the benchmark times on all host cores."""
+    out = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
-               "-shared", "-fPIC", "-o", _LIB + ".tmp", _SRC, "-lm"]
+               "-shared", "-fPIC"] + (["-fopenmp"] if omp else []) + ["-o", out + ".tmp", _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+        os.replace(out + ".tmp", out)
+    return out
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        build()
-        _lib = C.CDLL(_LIB)
-        _lib.or_morton_code.restype = C.c_uint64
-    return _lib
+    key = "omp" if _use_omp else "serial"
+    if key not in _libs:
+        path = build(omp=_use_omp)
+        lb = C.CDLL(path)
+        lb.or_morton_code.restype = C.c_uint64
+        _libs[key] = lb
+    return _libs[key]
+
+
+def use_threads(n: int | None) -> int:
+    """Route the oracle's calls to its OpenMP build with n threads (None or 0:
+    the OpenMP default, every host core), or back to the single-threaded build
+    (n = 1).  Returns the thread count the calls will use."""
+    global _use_omp
+    _use_omp = n != 1
+    if _use_omp:
+        lib().or_set_threads(C.c_int(int(n or 0)))
+    return int(lib().or_threads())
 
 
 def _p(a: np.ndarray):

@@ -43,11 +43,37 @@
  *               evaluate D8 on every (pixel, listed Gaussian).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC
+ *
+ * The OpenMP pragmas below take effect only in the separate -fopenmp build that
+ * the benchmark times as its all-cores CPU baseline (pixel rows and Gaussians
+ * in parallel, the backward's per-Gaussian sums by atomic adds).  The default
+ * build, which every test uses, ignores them and runs one thread in the order
+ * written.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* threads of the OpenMP build (1 without OpenMP) */
+int or_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
 
 enum { REC_MU = 0, REC_S = 3, REC_Q = 6, REC_OP = 10, REC_B = 11, REC_F = 14 };
 enum { KIND_INTERNAL = 0, KIND_LEAF = 1, KIND_SPT = 2 };
@@ -819,6 +845,7 @@ int or_project(int64_t n, const int64_t *sel, int stride, int degree, const floa
                int32_t *vis, int32_t *rect, uint32_t *key, float *f32, double *f64) {
     cam_t k;
     cam_setup(cam, &k);
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t i = 0; i < n; ++i) {
         const float *r = row_rec + sel[i] * stride;
         proj32_t p;
@@ -940,6 +967,7 @@ int or_blend(int W, int H, const double *bg, const int64_t *tile_start, const in
              const int32_t *win) {
     int TX = (W + TILE - 1) / TILE;
     int wx0 = win ? win[0] : 0, wy0 = win ? win[1] : 0, wx1 = win ? win[2] : W, wy1 = win ? win[3] : H;
+#pragma omp parallel for schedule(dynamic, 1)
     for (int py = wy0; py < wy1; ++py)
         for (int px = wx0; px < wx1; ++px) {
             int64_t t = (int64_t)(py / TILE) * TX + px / TILE;
@@ -967,6 +995,12 @@ int or_blend(int W, int H, const double *bg, const int64_t *tile_start, const in
     return 0;
 }
 
+/* g += v (an atomic add in the OpenMP build, where pixel rows run in parallel) */
+static inline void accum(double *g, double v) {
+#pragma omp atomic
+    *g += v;
+}
+
 /* Backward of the blend: exact derivative of or_blend with the decisions held
  * fixed.  For each pixel, with T_i the transmittance in front of Gaussian i and
  * R_i the colour composited behind it (background included):
@@ -981,10 +1015,13 @@ int or_blend_backward(int W, int H, const double *bg, const int64_t *tile_start,
     int64_t maxlen = 0;
     for (int64_t t = 0; t < (int64_t)TX * ((H + TILE - 1) / TILE); ++t)
         if (tile_start[t + 1] - tile_start[t] > maxlen) maxlen = tile_start[t + 1] - tile_start[t];
+#pragma omp parallel
+    {
     int64_t *li = malloc(sizeof(int64_t) * (size_t)(maxlen + 1));
     double *la = malloc(sizeof(double) * (size_t)(maxlen + 1)), *lT = malloc(sizeof(double) * (size_t)(maxlen + 1));
     double *lp = malloc(sizeof(double) * (size_t)(maxlen + 1)), *lg = malloc(sizeof(double) * (size_t)(maxlen + 1));
     int *lclamp = malloc(sizeof(int) * (size_t)(maxlen + 1));
+#pragma omp for schedule(dynamic, 1)
     for (int py = wy0; py < wy1; ++py)
         for (int px = wx0; px < wx1; ++px) {
             int64_t t = (int64_t)(py / TILE) * TX + px / TILE;
@@ -1012,22 +1049,23 @@ int or_blend_backward(int W, int H, const double *bg, const int64_t *tile_start,
                 double alpha = la[m], Ti = lT[m];
                 double dL_dalpha = 0.0;
                 for (int ch = 0; ch < 3; ++ch) {
-                    g2d[9 * i + 6 + ch] += dC[ch] * alpha * Ti;
+                    accum(&g2d[9 * i + 6 + ch], dC[ch] * alpha * Ti);
                     dL_dalpha += dC[ch] * (q[6 + ch] * Ti - Rb[ch] / (1.0 - alpha));
                 }
                 for (int ch = 0; ch < 3; ++ch) Rb[ch] += q[6 + ch] * alpha * Ti;
                 if (lclamp[m]) continue;
                 double dx = q[0] - (px + 0.5), dy = q[1] - (py + 0.5);
                 double dL_dp = dL_dalpha * alpha;
-                g2d[9 * i + 5] += dL_dalpha * lg[m];
-                g2d[9 * i + 0] += dL_dp * (-(q[2] * dx + q[3] * dy));
-                g2d[9 * i + 1] += dL_dp * (-(q[4] * dy + q[3] * dx));
-                g2d[9 * i + 2] += dL_dp * (-0.5 * dx * dx);
-                g2d[9 * i + 3] += dL_dp * (-dx * dy);
-                g2d[9 * i + 4] += dL_dp * (-0.5 * dy * dy);
+                accum(&g2d[9 * i + 5], dL_dalpha * lg[m]);
+                accum(&g2d[9 * i + 0], dL_dp * (-(q[2] * dx + q[3] * dy)));
+                accum(&g2d[9 * i + 1], dL_dp * (-(q[4] * dy + q[3] * dx)));
+                accum(&g2d[9 * i + 2], dL_dp * (-0.5 * dx * dx));
+                accum(&g2d[9 * i + 3], dL_dp * (-dx * dy));
+                accum(&g2d[9 * i + 4], dL_dp * (-0.5 * dy * dy));
             }
         }
     free(li); free(la); free(lT); free(lp); free(lg); free(lclamp);
+    }
     return 0;
 }
 
@@ -1039,6 +1077,7 @@ int or_project_backward(int64_t n, const int64_t *sel, int stride, int degree, c
     cam_setup(cam, &k);
     memset(g_rec, 0, sizeof(double) * (size_t)(n * stride));
     int K = sh_count(degree);
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t i = 0; i < n; ++i) {
         if (!vis[i]) continue;
         const float *r = row_rec + sel[i] * stride;

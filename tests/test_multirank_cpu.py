@@ -54,3 +54,19 @@ def test_shard_views_covers_views_for_any_rank_count():
             assert sorted(v for s in shards for v in s) == list(range(32))
         else:
             assert all(len(s) == 1 for s in shards)       # more ranks than views: one view each
+
+
+def test_timed_views_spread_over_the_whole_path():
+    """A run shorter than the path times evenly spaced views from the first
+    (aerial) to the last (street); a longer one repeats the path."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for steps in (2, 5, 20, 31):
+        v = bench.spread_views(list(range(32)), steps)
+        assert len(v) == steps and v[0] == 0 and v[-1] == 31
+        assert all(b > a for a, b in zip(v, v[1:]))
+        gaps = [b - a for a, b in zip(v, v[1:])]
+        assert max(gaps) - min(gaps) <= 1
+    assert bench.spread_views(list(range(32)), 32) == list(range(32))
+    assert bench.spread_views(list(range(32)), 40) == list(range(32)) + list(range(8))
+    assert bench.spread_views(list(range(32)), 1) == [0]
