@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--train-leaves", type=int, default=150_000_000)
     p.add_argument("--no-train-batch", action="store_true")
     p.add_argument("--no-densify", action="store_true")
+    p.add_argument("--streams", type=int, default=3,
+                   help="views in flight at once in the timed steps (independent views, one stream each)")
     return p.parse_args()
 
 
@@ -229,7 +231,8 @@ def run_lodgs(args, rank: int, world: int):
     targets_h = {v: torch.randint(0, 256, (H, W, 3), generator=gen, dtype=torch.uint8).pin_memory()
                  for v in my_views}
     targets_d = {v: t.cuda() for v, t in targets_h.items()}
-    image = torch.empty((H, W, 3), device="cuda")
+    # one image and one gradient buffer per view: views in flight at once share nothing
+    images = {v: torch.empty((H, W, 3), device="cuda") for v in my_views}
     stream = torch.cuda.current_stream()
 
     # grow every frame's workspace once (capacity-checked renders), size gradient rows
@@ -237,25 +240,25 @@ def run_lodgs(args, rank: int, world: int):
     fwd_stats = {}
     for v in my_views:
         fr = api.select_lod(scene, cams[v], frames[v])
-        api.render(scene, fr, image=image, check_capacity=True)
+        api.render(scene, fr, image=images[v], check_capacity=True)
         st = fr.stats()
         fwd_stats[v] = st
         max_sel = max(max_sel, st["n_selected"])
-    grad = torch.empty((max_sel, scene.stride), device="cuda")
+    grads = {v: torch.empty((max(fwd_stats[v]["n_selected"], 1), scene.stride), device="cuda") for v in my_views}
     # one loss slot per view: a view's loss can be read back on the copy stream
     # while the next views compute (no slot is rewritten before its read)
     loss_slots = torch.zeros(nv, device="cuda")
 
     def step_fwd(v, target, camera):
         fr = api.select_lod(scene, camera, frames[v])                  # camera=None: the frame's view
-        api.render(scene, fr, image=image, bg=None, check_capacity=False)
+        api.render(scene, fr, image=images[v], bg=None, check_capacity=False)
 
     def step_bwd_blend(v):
         # mean-L1 loss against the view's target folded into the blend backward
         api.render_backward_blend_l1(scene, frames[v], targets_d[v], loss_sum=loss_slots[v:v + 1])
 
     def step_bwd_project(v):
-        api.render_backward_project(scene, frames[v], grad)
+        api.render_backward_project(scene, frames[v], grads[v])
 
     def step(v, target, camera):
         step_fwd(v, target, camera)
@@ -296,11 +299,29 @@ def run_lodgs(args, rank: int, world: int):
     def replay(v, i=None):
         graphs[v][0].replay()
         if i is not None:
-            ev_a[i].record(stream)
+            ev_a[i].record(torch.cuda.current_stream())
         graphs[v][1].replay()
         if i is not None:
-            ev_b[i].record(stream)
+            ev_b[i].record(torch.cuda.current_stream())
         graphs[v][2].replay()
+
+    # views in flight: step i runs on streams[i % S]; the views are independent
+    # (each has its own frame, image, target, gradient rows and loss slot), so a
+    # view's latency-bound selection and pair ordering overlap another view's blends
+    n_streams = max(1, args.streams)
+    streams = [stream] + [torch.cuda.Stream() for _ in range(n_streams - 1)]
+
+    def run_steps(fn):
+        """fn(i, v) for every step, step i on streams[i % S], all joined on `stream`."""
+        start = torch.cuda.Event()
+        start.record(stream)
+        for s_ in streams[1:]:
+            s_.wait_event(start)
+        for i, v in enumerate(order):
+            with torch.cuda.stream(streams[i % n_streams]):
+                fn(i, v)
+        for s_ in streams[1:]:
+            stream.wait_stream(s_)
 
     for v in my_views:                               # one untimed replay each
         replay(v)
@@ -317,8 +338,7 @@ def run_lodgs(args, rank: int, world: int):
     torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     h0 = time.perf_counter()
-    for i, v in enumerate(order):
-        replay(v, i)
+    run_steps(lambda i, v: replay(v))
     e1.record(stream)
     host_submit_ms = 1e3 * (time.perf_counter() - h0) / len(order)      # host time to enqueue a step
     torch.cuda.nvtx.range_pop()
@@ -327,6 +347,15 @@ def run_lodgs(args, rank: int, world: int):
     if world > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
+    # the same steps one view at a time, with events around each blend backward:
+    # the dominant kernel's own launch duration (nothing overlaps it here)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for i, v in enumerate(order):
+        replay(v, i)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    serial_ms = s0.elapsed_time(s1)
     clk = clocks.stop()
     bwd_ms = [a.elapsed_time(b2) for a, b2 in zip(ev_a, ev_b)]
     stats_ok = all(frames[v].stats()["status"] == 0 for v in set(order))
@@ -362,7 +391,7 @@ def run_lodgs(args, rank: int, world: int):
     f0.record(stream)
     for v in order:
         fr = api.select_lod(scene, cams[v], frames[v])
-        api.render(scene, fr, image=image, check_capacity=False)
+        api.render(scene, fr, image=images[v], check_capacity=False)
     f1.record(stream)
     torch.cuda.synchronize()
     fwd_ms = f0.elapsed_time(f1)
@@ -379,7 +408,7 @@ def run_lodgs(args, rank: int, world: int):
             rows_p, dn_p = frames[v].selection_device()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=cap):
-                api.adam_step(scene, params, adam, (rows_p, max_sel), grad, lr, d_n=dn_p)
+                api.adam_step(scene, params, adam, (rows_p, grads[v].shape[0]), grads[v], lr, d_n=dn_p)
             adam_graphs[v] = g
     torch.cuda.synchronize()
     for v in my_views:
@@ -396,14 +425,17 @@ def run_lodgs(args, rank: int, world: int):
     train_ms = a0.elapsed_time(a1)
 
     # ---- end to end: targets from pinned host, loss read back every step ----
-    # Each step's target goes up on a copy stream while the previous view
-    # computes (the compute stream waits for it; a target buffer is rewritten
-    # only after its last reader, that view's backward, has run), and each
-    # step's loss comes back on the same copy stream once the step is done, so
-    # the compute stream never waits for a copy engine.
+    # Each step's target goes up on an upload stream ahead of the step (the
+    # step's stream waits for it; a target buffer is rewritten only after its
+    # last reader, that view's backward, has run), and each step's loss comes
+    # back on a read-back stream once the step is done: uploads never queue
+    # behind a read-back that waits for a step, and no compute stream waits
+    # for a copy engine except for its own input.
     loss_h = torch.empty(len(order), dtype=torch.float32).pin_memory()
     copy_stream = torch.cuda.Stream()
+    back_stream = torch.cuda.Stream()
     used = {v: torch.cuda.Event() for v in set(order)}
+    done_ev = [torch.cuda.Event() for _ in order]
     ready = [torch.cuda.Event() for _ in order]
 
     def upload(i):
@@ -415,8 +447,8 @@ def run_lodgs(args, rank: int, world: int):
 
     def read_loss(i):
         v = order[i]
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(used[v])
+        with torch.cuda.stream(back_stream):
+            back_stream.wait_event(done_ev[i])
             loss_h[i:i + 1].copy_(loss_slots[v:v + 1], non_blocking=True)
 
     torch.cuda.synchronize()
@@ -427,14 +459,24 @@ def run_lodgs(args, rank: int, world: int):
     g0.record(stream)
     copy_stream.wait_event(g0)
     upload(0)
-    for i, v in enumerate(order):
-        if i + 1 < len(order):
-            upload(i + 1)
-        stream.wait_event(ready[i])
+
+    def e2e_step(i, v):
+        for k in range(i + 1, min(i + 1 + n_streams, len(order))):    # keep the next uploads queued
+            if not up_issued[k]:
+                upload(k)
+                up_issued[k] = True
+        cs = torch.cuda.current_stream()
+        cs.wait_event(ready[i])
         replay(v)
-        used[v].record(stream)
+        used[v].record(cs)
+        done_ev[i].record(cs)
         read_loss(i)
+
+    up_issued = [False] * len(order)
+    up_issued[0] = True
+    run_steps(e2e_step)
     stream.wait_stream(copy_stream)
+    stream.wait_stream(back_stream)
     g1.record(stream)
     torch.cuda.synchronize()
     e2e_wall = time.perf_counter() - t0
@@ -446,11 +488,12 @@ def run_lodgs(args, rank: int, world: int):
         return max_over_ranks(x, world)
 
     ms, fwd_ms, e2e_ms, e2e_wall = maxr(ms), maxr(fwd_ms), maxr(e2e_ms), maxr(max(e2e_wall * 1e3, e2e_ms)) / 1e3
+    serial_ms = maxr(serial_ms)
     train_ms = maxr(train_ms)
     total_views = args.steps * world
     res = {
         "ms": ms, "fwd_ms": fwd_ms, "e2e_ms": max(e2e_ms, e2e_wall * 1e3), "views": total_views,
-        "train_ms": train_ms, "host_submit_ms": host_submit_ms,
+        "train_ms": train_ms, "host_submit_ms": host_submit_ms, "serial_ms": serial_ms, "streams": n_streams,
         "stage_ms": stage_mean_live, "stage_ms_eager": stage_mean, "clocks": clk, "launches": launches,
         "stats_ok": stats_ok, "work": work,
         "fwd_stats": fwd_stats, "scene": {"n_nodes": scene.n_nodes, "n_upper": scene.n_upper, "n_spt": scene.n_spt,
@@ -475,8 +518,8 @@ OPS_EVAL, OPS_BLEND, OPS_BWD_CONTRIB = 6, 11, 34
 # this workload, from one ncu capture of the launch list with
 # dram__bytes_read.sum and dram__bytes_write.sum; a constant of the kernel's
 # code at that capture, to be taken again whenever the kernel changes
-BLEND_BWD_DRAM_BYTES = 39.3e6
-BLEND_BWD_ISSUE_ACTIVE = 0.809    # smsp__issue_active of the same kernel, one view (ncu --set full)
+BLEND_BWD_DRAM_BYTES = 39.26e6
+BLEND_BWD_ISSUE_ACTIVE = 0.788    # smsp__issue_active of the same kernel, one view (ncu --set full)
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 
@@ -1076,8 +1119,13 @@ def main():
                    "resolution": "1920x1080", "tau_px": 1.0,
                    "loss": "mean L1 against 8-bit RGB targets",
                    "l2": "inputs larger than L2 (node records 1.07 GB; per-view reads 100-400 MB)",
-                   "parallelism": f"replicas x{world} (views split across ranks)"},
+                   "parallelism": f"replicas x{world} (views split across ranks); {res['streams']} views in "
+                                  "flight per GPU (independent views, one CUDA stream each)"},
         "fwd_bwd_step_ms": res["ms"] / args.steps,
+        "views_in_flight": res["streams"],
+        "serial": {"ms_per_step": res["serial_ms"] / args.steps,
+                   "value": res["views"] / (res["serial_ms"] * 1e-3), "unit": "frames/s",
+                   "note": "the same graph-replayed steps one view at a time on one stream"},
         "host_submit_ms_per_step": round(res["host_submit_ms"], 4),
         "train_step": {"value": res["views"] / (res["train_ms"] * 1e-3), "unit": "views/s",
                        "ms_per_step": res["train_ms"] / res["views"] * world,

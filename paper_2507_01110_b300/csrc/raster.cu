@@ -649,6 +649,17 @@ constexpr int NWARP = BNT / 32;
 #ifndef LODGS_BWD_PIX
 #define LODGS_BWD_PIX 2      // pixels per lane of the backward blend (2 or 4)
 #endif
+// Both blends take a lane's two pixels through packed .f32x2 add/mul/fma
+// (Blackwell): each half is rounded exactly as the scalar operation, so the
+// result is the scalar path's, and the FP32 pipe issues about half the
+// instructions.  0 selects the scalar loops (the backward's four-pixel form
+// always uses them).
+#ifndef LODGS_FWD_F32X2
+#define LODGS_FWD_F32X2 1
+#endif
+#ifndef LODGS_BWD_F32X2
+#define LODGS_BWD_F32X2 1
+#endif
 constexpr int BWD_PIX = LODGS_BWD_PIX;
 // LODGS_BWD_MINB (if defined): resident CTAs per SM the backward's registers
 // are held to; by default the compiler chooses (56 registers, 9 CTAs)
@@ -768,6 +779,40 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
             const float4 b = s_b[j];
             const float dx = __fsub_rn(a.x, bp.xc);
             const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
+#if LODGS_FWD_F32X2
+            {
+                // the same float32 operations as below, two pixels per packed instruction
+                const float2 dy = __fadd2_rn(make_float2(a.y, a.y), make_float2(-yc[0], -yc[1]));
+                const float2 p2 = __ffma2_rn(make_float2(bx, bx), dy,
+                                             __ffma2_rn(__fmul2_rn(make_float2(b.x, b.x), dy), dy,
+                                                        make_float2(hxx, hxx)));
+                const bool h0 = live[0] && p2.x >= SUPPORT_P, h1 = live[1] && p2.y >= SUPPORT_P;
+                if (COUNT) n_eval += PIX;
+                if (!__any_sync(0xffffffffu, h0 || h1)) continue;
+                const float cb = s_c[j];
+                const float2 pl = __fmul2_rn(p2, make_float2(LOG2E, LOG2E));
+                const float2 raw = __fmul2_rn(make_float2(b.y, b.y),
+                                              make_float2(h0 ? ex2_ftz(pl.x) : 0.f, h1 ? ex2_ftz(pl.y) : 0.f));
+                const float2 alpha = make_float2(fminf(ALPHA_MAX, raw.x), fminf(ALPHA_MAX, raw.y));
+                const float2 T2 = make_float2(T[0], T[1]);
+                const float2 w = __fmul2_rn(alpha, T2);
+                const float2 c02 = __ffma2_rn(make_float2(b.z, b.z), w, make_float2(c0[0], c0[1]));
+                const float2 c12 = __ffma2_rn(make_float2(b.w, b.w), w, make_float2(c1[0], c1[1]));
+                const float2 c22 = __ffma2_rn(make_float2(cb, cb), w, make_float2(c2[0], c2[1]));
+                const float2 Tn = __fmul2_rn(T2, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-alpha.x, -alpha.y)));
+                c0[0] = c02.x; c0[1] = c02.y; c1[0] = c12.x; c1[1] = c12.y; c2[0] = c22.x; c2[1] = c22.y;
+                T[0] = Tn.x; T[1] = Tn.y;
+                if (COUNT) n_blend += (uint32_t)h0 + (uint32_t)h1;
+                const bool s0 = h0 && Tn.x < T_MIN, s1 = h1 && Tn.y < T_MIN;
+                live[0] = live[0] && !s0;
+                live[1] = live[1] && !s1;
+                if (__any_sync(0xffffffffu, s0 || s1)) {
+                    done = !live[0] && !live[1];
+                    if (__all_sync(0xffffffffu, done)) break;
+                }
+                continue;
+            }
+#endif
             float p[PIX];
             bool hit[PIX], any = false;
 #pragma unroll
@@ -903,6 +948,12 @@ __global__ void BWD_BOUNDS(TILE_PIX / BP)
         }
     }
     uint32_t n_eval = 0, n_contrib = 0;
+    // packed form of the two pixels' state (LODGS_BWD_F32X2, BP == 2): .x the
+    // upper pixel, .y the lower one; ngs = -G.S
+    float2 T2 = make_float2(T[0], T[BP > 1 ? 1 : 0]), ngs2 = make_float2(-gS[0], -gS[BP > 1 ? 1 : 0]);
+    const float2 nyc2 = make_float2(-yc[0], -yc[BP > 1 ? 1 : 0]);
+    const float2 G02 = make_float2(G[0][0], G[BP > 1 ? 1 : 0][0]), G12 = make_float2(G[0][1], G[BP > 1 ? 1 : 0][1]);
+    const float2 G22 = make_float2(G[0][2], G[BP > 1 ? 1 : 0][2]);
     const uint2 rg = ranges[tile];
     for (uint32_t base = rg.x; base < rg.y; base += BATCH) {
         if (__syncthreads_count(done) == NT) break;
@@ -927,6 +978,53 @@ __global__ void BWD_BOUNDS(TILE_PIX / BP)
                 const float4 b = s_b[j];
                 const float dx = __fsub_rn(a.x, bp.xc);
                 const float hxx = __fmul_rn(__fmul_rn(a.z, dx), dx), bx = __fmul_rn(a.w, dx);
+#if LODGS_BWD_F32X2
+                if constexpr (BP == 2) {
+                    // the same float32 operations as below, two pixels per packed
+                    // instruction (add/mul/fma .f32x2 round each half as the scalar op)
+                    const float2 dy = __fadd2_rn(make_float2(a.y, a.y), nyc2);
+                    const float2 p = __ffma2_rn(make_float2(bx, bx), dy,
+                                                __ffma2_rn(__fmul2_rn(make_float2(b.x, b.x), dy), dy,
+                                                           make_float2(hxx, hxx)));
+                    const bool h0 = live[0] && p.x >= SUPPORT_P, h1 = live[1] && p.y >= SUPPORT_P;
+                    if (COUNT) n_eval += 2;
+                    if (!__any_sync(0xffffffffu, h0 || h1)) continue;
+                    const float cb = s_c[j];
+                    const float2 pl = __fmul2_rn(p, make_float2(LOG2E, LOG2E));
+                    const float2 e = make_float2(h0 ? ex2_ftz(pl.x) : 0.f, h1 ? ex2_ftz(pl.y) : 0.f);
+                    const float2 raw = __fmul2_rn(make_float2(b.y, b.y), e);
+                    const float2 alpha = make_float2(fminf(ALPHA_MAX, raw.x), fminf(ALPHA_MAX, raw.y));
+                    const float2 w = __fmul2_rn(alpha, T2);
+                    const float2 gc = __ffma2_rn(G22, make_float2(cb, cb),
+                                                 __ffma2_rn(G12, make_float2(b.w, b.w),
+                                                            __fmul2_rn(G02, make_float2(b.z, b.z))));
+                    ngs2 = __ffma2_rn(w, gc, ngs2);                                      // -G.S_i
+                    const float2 om = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-alpha.x, -alpha.y));
+                    const float2 dA = __ffma2_rn(make_float2(rcp_ftz(om.x), rcp_ftz(om.y)), ngs2,
+                                                 __fmul2_rn(T2, gc));
+                    float2 de = __fmul2_rn(dA, e);
+                    de.x = raw.x <= ALPHA_MAX ? de.x : 0.f;                              // 0 where clamped
+                    de.y = raw.y <= ALPHA_MAX ? de.y : 0.f;
+                    const float2 t = __fmul2_rn(de, dy);
+                    const float2 t2 = __fmul2_rn(t, dy);
+                    const float2 gw0 = __fmul2_rn(G02, w), gw1 = __fmul2_rn(G12, w), gw2 = __fmul2_rn(G22, w);
+                    T2 = __fmul2_rn(T2, om);                                            // as the forward
+                    if (COUNT) n_contrib += (uint32_t)h0 + (uint32_t)h1;
+                    const bool s0 = h0 && T2.x < T_MIN, s1 = h1 && T2.y < T_MIN;
+                    live[0] = live[0] && !s0;
+                    live[1] = live[1] && !s1;
+                    const float q0 = de.x + de.y, q1 = t.x + t.y;
+                    const float dq0 = dx * q0;
+                    float gv[9] = {dq0, q1, dx * dq0, dx * q1, t2.x + t2.y, q0, gw0.x + gw0.y, gw1.x + gw1.y,
+                                   gw2.x + gw2.y};
+                    warp_sum9_to_smem(gv, lane, s_grad[j]);
+                    if (__any_sync(0xffffffffu, s0 || s1)) {
+                        done = !live[0] && !live[1];
+                        if (__all_sync(0xffffffffu, done)) break;
+                    }
+                    continue;
+                }
+#endif
                 float p[BP], dyk[BP];
                 bool hit[BP], any = false;
 #pragma unroll
