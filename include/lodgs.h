@@ -520,6 +520,32 @@ int lodgs_render_backward_blend_l1_u8(lodgs_scene *scene, lodgs_frame *frame, co
  * the stream the frame last ran on, is idle). */
 int lodgs_frame_get_stats(lodgs_frame *frame, lodgs_frame_stats *stats);
 
+/*
+ * Device memory of a frame, for callers that budget it (a render server that
+ * admits requests by memory).  The paper has no counterpart; this is an
+ * interface addition only.
+ *   held_bytes:   what the frame's workspace holds now: the buffers sized by
+ *                 the scene at creation plus the per-selected-node, per-pair
+ *                 and per-tile buffers as grown so far (they never shrink)
+ *   needed_bytes: what the same buffers take when sized exactly for the
+ *                 frame's last view (its selection, and its kept pairs and
+ *                 tiles if it was rendered)
+ * Either pointer may be NULL.  Synchronises the frame's stream.
+ */
+int lodgs_frame_memory(lodgs_frame *frame, int64_t *held_bytes, int64_t *needed_bytes);
+
+/*
+ * Sizes a frame's per-view buffers for a view of n_selected selected nodes and
+ * n_pairs kept (Gaussian, tile) pairs: grows them now where they are smaller
+ * (they never shrink), and makes this the size the next render grows to,
+ * replacing any growth that a capacity overflow (LODGS_E_CAPACITY) queued.
+ * (0, 0) keeps the current size and cancels queued growth: a caller that
+ * budgets device memory can then move the overflowing view to a larger frame
+ * instead of letting this one grow.  Interface addition; the paper has no
+ * counterpart.  LODGS_E_OOM if an allocation fails.
+ */
+int lodgs_frame_reserve(lodgs_frame *frame, int64_t n_selected, int64_t n_pairs);
+
 /* Stages timed by lodgs_frame_stage_ms, in order. */
 #define LODGS_STAGE_SELECT 0      /* upper-hierarchy BFS cut + SPT interval test and compaction */
 #define LODGS_STAGE_PROJECT 1     /* gather + EWA projection + SH colour */

@@ -246,6 +246,18 @@ class Frame:
         check(lib().lodgs_frame_stage_ms(self._h, ms))
         return dict(zip(_lib.STAGES, [float(v) for v in ms]))
 
+    def memory(self) -> tuple[int, int]:
+        """(held, needed) device bytes: what the frame's workspace holds now, and
+        what it takes sized exactly for the frame's last view (lodgs_frame_memory)."""
+        held, needed = C.c_int64(), C.c_int64()
+        check(lib().lodgs_frame_memory(self._h, C.byref(held), C.byref(needed)))
+        return held.value, needed.value
+
+    def reserve(self, n_selected: int = 0, n_pairs: int = 0) -> None:
+        """Size the per-view buffers for n_selected nodes and n_pairs pairs (grow
+        now, never shrink) and cancel growth a capacity overflow queued."""
+        check(lib().lodgs_frame_reserve(self._h, C.c_int64(int(n_selected)), C.c_int64(int(n_pairs))))
+
     def work(self) -> dict:
         """Pixel-Gaussian work counters of the last render/backward."""
         w = (C.c_uint64 * 4)()

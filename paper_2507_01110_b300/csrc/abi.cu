@@ -327,8 +327,10 @@ int lodgs_frame_create(lodgs_scene *sc, lodgs_frame **out) {
         return cuda_fail(e, "frame_create");
     }
     memset(fr->h_cnt, 0, C_COUNT * sizeof(uint32_t));
-    int rc = ensure_sel(fr, std::min<int64_t>(M, 1 << 20));
-    if (!rc) rc = ensure_pairs(fr, 1 << 22);
+    // small initial per-view buffers: they grow to what the views need (a
+    // render that overflows reports LODGS_E_CAPACITY and the next one is sized)
+    int rc = ensure_sel(fr, std::min<int64_t>(M, 1 << 12));
+    if (!rc) rc = ensure_pairs(fr, 1 << 16);
     if (rc) { lodgs_frame_free(fr); return rc; }
     *out = fr;
     return LODGS_OK;
@@ -567,6 +569,46 @@ int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {
         if (ns > fr->f.cap_sel) fr->want_sel = std::max<uint64_t>(fr->want_sel, ns + ns / 4);
         else if (np > fr->f.cap_pairs) fr->want_pairs = std::max<uint64_t>(fr->want_pairs, np + np / 4);
     }
+    return LODGS_OK;
+}
+
+int lodgs_frame_memory(lodgs_frame *fr, int64_t *held, int64_t *needed) {
+    if (!fr) { set_error("frame_memory: NULL frame"); return LODGS_E_INVALID; }
+    const FrameBufs &f = fr->f;
+    const lodgs_scene *sc = fr->scene;
+    const uint64_t M = (uint64_t)sc->n_nodes, S = (uint64_t)sc->n_spt, U = (uint64_t)sc->n_upper;
+    // bytes per selected node, per pair and per tile of the grown buffers
+    constexpr uint64_t per_sel = 3 * sizeof(float4) + 4 * sizeof(uint32_t) + sizeof(uint2) + 2 * sizeof(uint32_t) +
+                                 G2D_STRIDE * sizeof(float);
+    constexpr uint64_t per_pair = 4 * sizeof(uint32_t) + sizeof(unsigned long long);
+    constexpr uint64_t per_tile = sizeof(uint2) + 2 * sizeof(uint32_t);
+    const uint64_t fixed = C_COUNT * 4 + sizeof(View) + M * 4 + S * 8 + (S + 1) * 8 + SEL_BLOCK_COUNTS * 4 +
+                           SCAN_GRID_MAX * 4 + SORT_HIST * 4 + 4 * sizeof(unsigned long long) + U * 5 +
+                           (f.sel_src ? M * 4 : 0) + (f.emit_src ? std::max<uint64_t>(S, 1) * 4 : 0);
+    if (held)
+        *held = (int64_t)(fixed + f.cap_sel * per_sel + f.cap_pairs * per_pair + f.cap_keep * 4 +
+                          f.cap_tiles * per_tile);
+    if (needed) {
+        LODGS_CUDA(cudaStreamSynchronize(fr->stream));
+        LODGS_CUDA(cudaMemcpy(fr->h_cnt, f.cnt, C_COUNT * 4, cudaMemcpyDeviceToHost));
+        const uint64_t ns = fr->selected ? fr->h_cnt[C_NSEL] : 0;
+        const uint64_t np = fr->rendered ? std::max(fr->h_cnt[C_NKEPT], fr->h_cnt[C_NKEPT_WANT]) : 0;
+        const uint64_t nt = fr->rendered ? (uint64_t)fr->k.TX * fr->k.TY : 0;
+        *needed = (int64_t)(fixed + std::max<uint64_t>(ns, 1) * per_sel + np * per_pair +
+                            (np ? np / 16 + 1 : 0) * 4 + nt * per_tile);
+    }
+    return LODGS_OK;
+}
+
+int lodgs_frame_reserve(lodgs_frame *fr, int64_t n_sel, int64_t n_pairs) {
+    if (!fr || n_sel < 0 || n_pairs < 0) { set_error("frame_reserve: NULL frame or negative count"); return LODGS_E_INVALID; }
+    LODGS_CUDA(cudaStreamSynchronize(fr->stream));        // no render of this frame is reading the buffers
+    fr->want_sel = std::max<uint64_t>((uint64_t)n_sel, fr->f.cap_sel);
+    fr->want_pairs = std::max<uint64_t>((uint64_t)n_pairs, fr->f.cap_pairs);
+    if (int r = ensure_sel(fr, fr->want_sel)) return r;
+    if (int r = ensure_pairs(fr, fr->want_pairs)) return r;
+    fr->want_sel = fr->f.cap_sel;
+    fr->want_pairs = fr->f.cap_pairs;
     return LODGS_OK;
 }
 

@@ -8,6 +8,27 @@ concurrently and overlap on the device.  Completion is polled with CUDA
 events; latency is arrival to completion.  The scene (and the cache, in
 out-of-core mode) is shared and read only, so a request's image does not depend
 on what else is in flight: every kernel of a view reads only that view's frame.
+
+Admission by memory: the budget bounds the device workspace the slots hold
+together (what lodgs_frame_memory reports as held; a frame's workspace only
+grows).  warm() learns, per request class (resolution and LoD threshold), the
+largest workspace a request of the class needed, then sizes the slots within
+the budget: the first slot for the largest class, each next one for the
+largest class that still leaves the remaining slots their base size.  A
+request is admitted to a free slot whose workspace already holds its class's
+need (the one with the least to spare); if every slot that could hold it is
+busy it waits, and up to `lookahead` later requests that fit a free slot may
+start before it.  A request whose view overflows its slot (another camera of
+its class can need more than the warm-up saw, or one buffer of a slot can be
+short while its total is not) raises its class's need; it is rendered again on
+the same slot, which grows, if the budget still holds the grown slot or no slot
+it has not yet overflowed could hold it; otherwise the queued growth is
+cancelled (lodgs_frame_reserve) and the request goes back to the head of the
+queue to wait for one of those slots.  A request therefore goes back to the
+queue at most once per slot before it grows one.  A class not seen in the
+warm-up is
+admitted alone to the largest slot (which grows if it must).  The server keeps
+only as many slots as the budget holds at their base size (at least one).
 """
 from __future__ import annotations
 
@@ -20,6 +41,8 @@ import torch
 
 from . import _lib, api
 
+GROWTH = 1.25      # a frame buffer that overflows grows to 1.25 x the count that overflowed it
+
 
 @dataclass
 class Request:
@@ -29,18 +52,53 @@ class Request:
     t_enqueue: float = 0.0
     t_admit: float = 0.0
     t_done: float = 0.0
-    retries: int = 0
+    retries: int = 0                 # renders again on the same slot after an overflow
+    requeues: int = 0                # returns to the queue after an overflow (no growth within the budget)
     status: str = "pending"          # "done", "expired" (deadline passed in the queue), "failed: ..."
-    checksum: float | None = None
+    dev_ms: tuple | None = None      # (start, end) on the device, ms from the run's start
+    tried: set = field(default_factory=set)   # slots this request overflowed
+    ev_start: object = field(default=None, repr=False)
     image: torch.Tensor | None = field(default=None, repr=False)
 
 
-def request_bytes(width: int, height: int) -> int:
-    """Device memory a request is charged at admission: its image plus the
-    per-view workspace that grows with the pixel count ((Gaussian, tile) pairs,
-    tile ranges); 64 bytes per pixel covers the workspaces measured on the
-    1080p trajectory with margin."""
-    return width * height * (12 + 64)
+def request_class(camera) -> tuple:
+    """The admission class of a request: its resolution and LoD threshold."""
+    return (int(camera.width), int(camera.height), round(float(camera.tau), 6))
+
+
+def pick_slot(need, tried, free, slots, can_wait: bool):
+    """The free slot a queued request takes, or None (it waits).  need: its
+    class's workspace bytes (None: class not seen yet); tried: the slots it has
+    overflowed; free: the free slots; slots: all of them; can_wait: whether it
+    may wait for a busy slot (the head of the queue may not wait when nothing is
+    in flight).  Slots are anything with a `held` byte count."""
+    if need is None:                                 # a class not seen yet: alone, on the largest slot
+        if can_wait:
+            return None
+        return max(free, key=lambda s: s.held)
+    usable = [s for s in free if id(s) not in tried]
+    fits = [s for s in usable if s.held >= GROWTH * need] or [s for s in usable if s.held >= need]
+    if fits:
+        return min(fits, key=lambda s: s.held)
+    if can_wait and any(s.held >= need and id(s) not in tried for s in slots):
+        return None                                  # a slot that holds it is busy: wait for it
+    if can_wait:
+        return None
+    return max(free, key=lambda s: s.held)           # none can: the largest grows
+
+
+def overflow_action(needed: int, need: int, slot, slots, tried, budget: int) -> str:
+    """After a request's view overflowed `slot` (needed: the bytes the view
+    needs; need: its class's need, at least `needed`, the threshold pick_slot
+    applies), 'retry' on this slot, which grows, or 'requeue' (growth
+    cancelled) to wait for another slot.  It requeues only while the grown slot
+    would break the budget and some slot it has not overflowed holds `need`;
+    pick_slot then gives it such a slot, so every requeue is followed by a
+    launch on a slot it has not tried, or by growth: a request requeues at most
+    once per slot."""
+    grown = sum(s.held for s in slots) - slot.held + int(GROWTH * needed)
+    others = [s for s in slots if s is not slot and id(s) not in tried and s.held >= need]
+    return "requeue" if grown > budget and others else "retry"
 
 
 class _Slot:
@@ -48,20 +106,51 @@ class _Slot:
         self.frame = api.Frame(scene)
         self.stream = torch.cuda.Stream()
         self.image = torch.empty(max_pixels * 3, dtype=torch.float32, device="cuda")
-        self.done = torch.cuda.Event()
+        self.done = torch.cuda.Event(enable_timing=True)
         self.req: Request | None = None
-        self.bytes = 0
+        self.held = self.frame.memory()[0]
 
 
 class RenderServer:
     def __init__(self, scene: api.Scene, n_slots: int = 8, mem_budget_bytes: int = 4 << 30,
-                 max_pixels: int = 3840 * 2160, rows: torch.Tensor | None = None, keep_images: bool = False):
+                 max_pixels: int = 3840 * 2160, rows: torch.Tensor | None = None, keep_images: bool = False,
+                 lookahead: int = 8):
         self.scene = scene
         self.rows = rows
         self.slots = [_Slot(scene, max_pixels) for _ in range(n_slots)]
         self.budget = mem_budget_bytes
         self.keep_images = keep_images
+        self.lookahead = lookahead
+        self.need: dict = {}              # request class -> largest workspace bytes it needed
+        self.rep: dict = {}               # request class -> the camera of that largest need
+        self._ref = None                  # event at the start of run(): device times are taken from it
+        while len(self.slots) > 1 and self.held_bytes() > self.budget:
+            self.slots.pop()              # the budget holds fewer slots at their base size (at least one)
 
+    # ---- memory bookkeeping ----
+    def charge(self, camera):
+        """The workspace bytes a request's class needs (None: a class not seen yet)."""
+        return self.need.get(request_class(camera))
+
+    def held_bytes(self) -> int:
+        """Device workspace the slots hold together."""
+        return int(sum(s.held for s in self.slots))
+
+    def _learn(self, slot: _Slot, camera) -> int:
+        held, needed = slot.frame.memory()
+        slot.held = held
+        k = request_class(camera)
+        if needed > self.need.get(k, -1):
+            self.need[k] = needed
+            self.rep[k] = camera
+        return needed
+
+    def _render(self, slot: _Slot, cam) -> None:
+        img = slot.image[: cam.height * cam.width * 3].view(cam.height, cam.width, 3)
+        api.select_lod(self.scene, cam, slot.frame)
+        api.render(self.scene, slot.frame, rows=self.rows, image=img, check_capacity=True)
+
+    # ---- one request on one slot ----
     def _launch(self, slot: _Slot, req: Request) -> bool:
         """Enqueue the request on the slot; False (request marked failed, slot
         left free) if the library refused it, e.g. out of device memory."""
@@ -69,6 +158,9 @@ class RenderServer:
         img = slot.image[: cam.height * cam.width * 3].view(cam.height, cam.width, 3)
         try:
             with torch.cuda.stream(slot.stream):
+                if req.ev_start is None:             # the device start of the request's first launch
+                    req.ev_start = torch.cuda.Event(enable_timing=True)
+                    req.ev_start.record(slot.stream)
                 api.select_lod(self.scene, cam, slot.frame, stream=slot.stream)
                 api.render(self.scene, slot.frame, rows=self.rows, image=img, stream=slot.stream,
                            check_capacity=False)
@@ -79,17 +171,25 @@ class RenderServer:
         slot.req = req
         return True
 
-    def _finish(self, slot: _Slot, now: float) -> bool:
-        """True if the request completed; False if its frame had to grow and it
-        was launched again."""
+    def _finish(self, slot: _Slot, now: float) -> str:
+        """'done', 'retry' (rendered again on this slot, which grows) or
+        'requeue' (the slot overflowed and may not grow within the budget)."""
         req = slot.req
         st = slot.frame.stats()                      # the stream is idle: no wait
         if st["status"] == _lib.LODGS_E_CAPACITY:
-            req.retries += 1
-            if not self._launch(slot, req):          # growing the workspace failed: give up on it
-                slot.req = None
-                return True
-            return False
+            needed = self._learn(slot, req.camera)
+            req.tried.add(id(slot))
+            need = self.charge(req.camera)
+            if overflow_action(needed, need, slot, self.slots, req.tried, self.budget) == "retry":
+                req.retries += 1
+                if not self._launch(slot, req):      # growing the workspace failed: give up on it
+                    slot.req = None
+                    return "done"
+                return "retry"
+            slot.frame.reserve(0, 0)                 # no growth: wait for a slot that holds it
+            req.requeues += 1
+            slot.req = None
+            return "requeue"
         _lib.check(st["status"])
         cam = req.camera
         img = slot.image[: cam.height * cam.width * 3].view(cam.height, cam.width, 3)
@@ -97,16 +197,38 @@ class RenderServer:
             req.image = img.clone()
         req.t_done = now
         req.status = "done"
+        if self._ref is not None:                    # the request's interval on the device
+            req.dev_ms = (self._ref.elapsed_time(req.ev_start), self._ref.elapsed_time(slot.done))
+        self._learn(slot, cam)
         slot.req = None
-        return True
+        return "done"
 
     def warm(self, cameras) -> None:
-        """Grow every slot's workspace on representative cameras (not timed)."""
-        for slot in self.slots:
-            for cam in cameras:
-                img = slot.image[: cam.height * cam.width * 3].view(cam.height, cam.width, 3)
-                api.select_lod(self.scene, cam, slot.frame)
-                api.render(self.scene, slot.frame, rows=self.rows, image=img, check_capacity=True)
+        """Learn the classes' workspace needs on representative cameras, then
+        size the slots within the budget (see the module notes; not timed).
+        Slots the budget cannot give their base size are dropped."""
+        probe = self.slots[0]
+        for cam in cameras:
+            self._render(probe, cam)
+            self._learn(probe, cam)
+        remaining = self.budget - probe.held
+        base = min(s.held for s in self.slots[1:]) if len(self.slots) > 1 else 0
+        kept = [probe]
+        for i, slot in enumerate(self.slots[1:], start=1):
+            after = len(self.slots) - i - 1
+            room = remaining - after * base
+            if slot.held > remaining:
+                break
+            # a frame grows a quarter beyond what overflowed it: size by 1.25 x the need
+            fits = [(n, k) for k, n in self.need.items() if GROWTH * n <= room]
+            if fits:
+                n, k = max(fits)
+                if n > slot.held:
+                    self._render(slot, self.rep[k])
+                    self._learn(slot, self.rep[k])
+            kept.append(slot)
+            remaining -= slot.held
+        self.slots = kept
         torch.cuda.synchronize()
 
     def run(self, requests: list[Request], realtime: bool = True, deadline_ms: float | None = None) -> dict:
@@ -118,9 +240,12 @@ class RenderServer:
         reqs = sorted(requests, key=lambda r: r.arrival_s)
         pending = collections.deque()
         nxt = 0
-        in_use = 0
         done = 0
         inflight_max = 0
+        held_max = self.held_bytes()
+        torch.cuda.synchronize()
+        self._ref = torch.cuda.Event(enable_timing=True)
+        self._ref.record()
         t0 = time.perf_counter()
         while done < len(reqs):
             now = time.perf_counter() - t0
@@ -128,35 +253,45 @@ class RenderServer:
                 reqs[nxt].t_enqueue = reqs[nxt].arrival_s if realtime else now
                 pending.append(reqs[nxt])
                 nxt += 1
-            # completions first: they free slots and memory
+            # completions first: they free slots
             for slot in self.slots:
                 if slot.req is not None and slot.done.query():
-                    if self._finish(slot, time.perf_counter() - t0):
-                        in_use -= slot.bytes
-                        slot.bytes = 0
+                    req = slot.req
+                    out = self._finish(slot, time.perf_counter() - t0)
+                    if out == "done":
                         done += 1
-            # admission: any pending request that fits a free slot and the memory budget
+                    elif out == "requeue":
+                        pending.appendleft(req)
+            held_max = max(held_max, self.held_bytes())
+            # admission: the head of the queue, then up to `lookahead` later
+            # requests, each to a free slot whose workspace holds its class's need
             free = [s for s in self.slots if s.req is None]
-            while pending and free:
-                req = pending[0]
-                if deadline_ms is not None and (time.perf_counter() - t0 - req.t_enqueue) * 1e3 > deadline_ms:
-                    pending.popleft()                # waited past its deadline: never launched
-                    req.status = "expired"
-                    done += 1
+            while deadline_ms is not None and pending and \
+                    (time.perf_counter() - t0 - pending[0].t_enqueue) * 1e3 > deadline_ms:
+                pending.popleft().status = "expired"     # waited past its deadline: never launched
+                done += 1
+            q = 0
+            while q < min(len(pending), 1 + self.lookahead) and free:
+                req = pending[q]
+                busy = len(free) < len(self.slots)
+                slot = pick_slot(self.charge(req.camera), req.tried, free, self.slots, can_wait=busy or q > 0)
+                if slot is None:
+                    q += 1
                     continue
-                need = request_bytes(req.camera.width, req.camera.height)
-                if in_use + need > self.budget and in_use > 0:
-                    break
-                pending.popleft()
-                slot = free.pop()
+                del pending[q]
+                free.remove(slot)
                 req.t_admit = time.perf_counter() - t0
                 if not self._launch(slot, req):
                     free.append(slot)
                     done += 1
                     continue
-                slot.bytes = need
-                in_use += need
-            inflight_max = max(inflight_max, sum(s.req is not None for s in self.slots))
+            inflight = sum(s.req is not None for s in self.slots)
+            # with nothing in flight every slot is free and pick_slot admits the
+            # head (it may not wait): a queue left waiting here would spin forever
+            if not inflight and pending and pick_slot(self.charge(pending[0].camera), pending[0].tried,
+                                                      self.slots, self.slots, can_wait=False) is None:
+                raise RuntimeError("render server: the head of the queue cannot be admitted")
+            inflight_max = max(inflight_max, inflight)
             time.sleep(0)
         wall = time.perf_counter() - t0
         # latency from arrival (realtime) or from being queued (batch mode) to completion
@@ -165,9 +300,25 @@ class RenderServer:
         return {"requests": len(reqs), "wall_s": wall, "throughput_rps": len(ok) / wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "max_inflight": inflight_max,
-                "retries": int(sum(r.retries for r in reqs)),
+                "gpu_busy": gpu_busy_fraction([r.dev_ms for r in ok if r.dev_ms is not None], wall * 1e3),
+                "slots": len(self.slots), "slot_workspace_bytes": self.held_bytes(),
+                "peak_slot_workspace_bytes": int(held_max), "budget_bytes": int(self.budget),
+                "retries": int(sum(r.retries for r in reqs)), "requeues": int(sum(r.requeues for r in reqs)),
                 "completed": len(ok), "expired": sum(r.status == "expired" for r in reqs),
                 "failed": sum(r.status.startswith("failed") for r in reqs)}
+
+
+def gpu_busy_fraction(intervals, wall_ms: float) -> float:
+    """Fraction of the run's wall time during which at least one request was
+    executing on the device: the union of the requests' [start, end] device
+    intervals (ms from the run's start) over the wall time."""
+    busy, end = 0.0, -np.inf
+    for a, b in sorted(intervals):
+        if b <= end:
+            continue
+        busy += b - max(a, end)
+        end = b
+    return float(busy / wall_ms) if wall_ms > 0 else 0.0
 
 
 def poisson_requests(cameras, rate_per_s: float, n: int, seed: int) -> list[Request]:
