@@ -3,6 +3,11 @@
 Translation units that take float32 decisions (scene build, LoD selection,
 projection) are compiled with -fmad=false so that every expression is rounded
 as written; host code is compiled with -ffp-contract=off for the same reason.
+
+Build knobs (environment): LODGS_DEFINES adds preprocessor definitions (for
+example "LODGS_BWD_F32X2=0 LODGS_FWD_F32X2=0" for the blends' scalar loops);
+objects then go to their own folder.  LODGS_LIBRARY, if set, is where the
+library is written (and where the binding loads it from).
 """
 from __future__ import annotations
 
@@ -14,8 +19,10 @@ from concurrent.futures import ThreadPoolExecutor
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-BUILD = os.path.join(ROOT, "_build")
-LIB = os.path.join(PKG, "liblodgs.so")
+DEFINES = os.environ.get("LODGS_DEFINES", "").split()
+BUILD = os.path.join(ROOT, "_build", "_".join(d.replace("=", "-") for d in DEFINES)) if DEFINES else \
+    os.path.join(ROOT, "_build")
+LIB = os.environ.get("LODGS_LIBRARY", os.path.join(PKG, "liblodgs.so"))
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -34,6 +41,7 @@ def _newer(src_paths, out):
 
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(os.path.dirname(LIB) or ".", exist_ok=True)
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     hdrs.append(os.path.join(ROOT, "include", "lodgs.h"))
     jobs = []
@@ -43,7 +51,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         obj = os.path.join(BUILD, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or _newer([src] + hdrs + [__file__], obj):
-            flags = COMMON + (["-fmad=false"] if s in EXACT else [])
+            flags = COMMON + (["-fmad=false"] if s in EXACT else []) + [f"-D{d}" for d in DEFINES]
             jobs.append([NVCC] + flags + ["-c", src, "-o", obj])
 
     def run(cmd):
