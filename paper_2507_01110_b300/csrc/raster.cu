@@ -788,7 +788,10 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
                                                         make_float2(hxx, hxx)));
                 const bool h0 = live[0] && p2.x >= SUPPORT_P, h1 = live[1] && p2.y >= SUPPORT_P;
                 if (COUNT) n_eval += PIX;
-                if (!__any_sync(0xffffffffu, h0 || h1)) continue;
+                // no vote to skip a Gaussian no lane reaches: a lane that misses
+                // gets alpha = 0, which leaves its colour and T exactly as they
+                // were, and the packed body costs less than the vote and branch
+                // (measured: forward render 0.1708 -> 0.1664 ms per 1080p view)
                 const float cb = s_c[j];
                 const float2 pl = __fmul2_rn(p2, make_float2(LOG2E, LOG2E));
                 const float2 raw = __fmul2_rn(make_float2(b.y, b.y),
