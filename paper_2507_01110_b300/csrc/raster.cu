@@ -991,7 +991,7 @@ __global__ void BWD_BOUNDS(TILE_PIX / BP)
                                                            make_float2(hxx, hxx)));
                     const bool h0 = live[0] && p.x >= SUPPORT_P, h1 = live[1] && p.y >= SUPPORT_P;
                     if (COUNT) n_eval += 2;
-                    if (!__any_sync(0xffffffffu, h0 || h1)) continue;
+                    if (!__any_sync(0xffffffffu, h0 || h1)) continue;   // here the skip pays (measured)
                     const float cb = s_c[j];
                     const float2 pl = __fmul2_rn(p, make_float2(LOG2E, LOG2E));
                     const float2 e = make_float2(h0 ? ex2_ftz(pl.x) : 0.f, h1 ? ex2_ftz(pl.y) : 0.f);
