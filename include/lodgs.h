@@ -256,6 +256,24 @@ int lodgs_frame_set_view(lodgs_frame *frame, const lodgs_camera *cam, const floa
 int lodgs_select_lod(lodgs_scene *scene, const lodgs_camera *cam, lodgs_frame *frame, void *stream);
 
 /*
+ * The LoD cuts of n views at once (Algorithms 1-2, as lodgs_select_lod for
+ * each): cams[i] is cut into frames[i], with one launch of each selection pass
+ * serving all n views (a view index in the grid), so n short, latency-bound
+ * selections cost about as many launches as one.  Afterwards each frame is
+ * exactly as lodgs_select_lod(scene, &cams[i], frames[i], stream) leaves it;
+ * its render may run on another stream (it is ordered after the selection).
+ *   cams:   host array of n cameras
+ *   frames: host array of n distinct frames of this scene
+ *   n:      1 <= n <= LODGS_SELECT_BATCH_MAX
+ * LODGS_E_INVALID for a bad n, camera or repeated frame, with nothing
+ * enqueued.  Asynchronous on `stream`.  Interface addition for serving and
+ * multi-view batches; the paper selects one camera at a time.
+ */
+#define LODGS_SELECT_BATCH_MAX 8
+int lodgs_select_lod_batch(lodgs_scene *scene, const lodgs_camera *cams, lodgs_frame *const *frames, int n,
+                           void *stream);
+
+/*
  * The same LoD cut as lodgs_select_lod, written to caller-owned device buffers,
  * for callers that cannot allocate device memory: an application whose device
  * memory all belongs to its own arena or pool, or a loop that cannot afford

@@ -111,6 +111,7 @@ _SIGS = {
     "lodgs_frame_get_stats": (C.c_int, [_P, C.POINTER(FrameStats)]),
     "lodgs_frame_set_ordering": (C.c_int, [_P, C.c_int]),
     "lodgs_frame_memory": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "lodgs_select_lod_batch": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "lodgs_frame_reserve": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "lodgs_adam_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, C.c_float, C.c_float, C.c_float,
                                   _P]),

@@ -574,6 +574,22 @@ def select_lod(scene: Scene, camera, frame: Frame | None = None, stream=None) ->
     return fr
 
 
+def select_lod_batch(scene: Scene, cameras, frames: list, stream=None) -> list:
+    """LoD cuts of up to LODGS_SELECT_BATCH_MAX views in one launch of each
+    selection pass; frames[i] ends as select_lod(scene, cameras[i], frames[i])
+    leaves it (its render may run on another stream)."""
+    n = len(cameras)
+    if n != len(frames):
+        raise ValueError("one frame per camera")
+    cs = (_lib.Camera * n)(*[camera_struct(c) for c in cameras])
+    hs = (C.c_void_p * n)(*[f.handle.value for f in frames])
+    check(lib().lodgs_select_lod_batch(scene.handle, C.cast(cs, C.c_void_p), C.cast(hs, C.c_void_p), C.c_int(n),
+                                       _stream_ptr(stream)))
+    for f, c in zip(frames, cameras):
+        f.camera = c
+    return frames
+
+
 def render(scene: Scene, frame: Frame, rows: torch.Tensor | None = None, bg=(0.0, 0.0, 0.0),
            image: torch.Tensor | None = None, stream=None, check_capacity: bool = True) -> torch.Tensor:
     """Render the frame's selection into an H x W x 3 float32 CUDA tensor.

@@ -542,6 +542,47 @@ int lodgs_render_backward(lodgs_scene *sc, lodgs_frame *fr, const float *rows, c
     return rc;
 }
 
+int lodgs_select_lod_batch(lodgs_scene *sc, const lodgs_camera *cams, lodgs_frame *const *frames, int n,
+                           void *stream) {
+    static_assert(LODGS_SELECT_BATCH_MAX <= SCAN_BATCH_MAX, "batch bound");
+    if (!sc || !cams || !frames || n < 1 || n > LODGS_SELECT_BATCH_MAX) {
+        set_error("select_lod_batch: NULL argument or n not in 1..LODGS_SELECT_BATCH_MAX");
+        return LODGS_E_INVALID;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (int rc = check_frame(sc, frames[i], "select_lod_batch")) return rc;
+        if (!camera_ok(&cams[i])) { set_error("select_lod_batch: invalid camera"); return LODGS_E_INVALID; }
+        for (int j = 0; j < i; ++j)
+            if (frames[j] == frames[i]) { set_error("select_lod_batch: a frame appears twice"); return LODGS_E_INVALID; }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    View views[LODGS_SELECT_BATCH_MAX];
+    FrameBufs *fs[LODGS_SELECT_BATCH_MAX];
+    for (int i = 0; i < n; ++i) {
+        lodgs_frame *fr = frames[i];
+        fr->stream = st;
+        fr->f.use_src = false;
+        fr->cache = nullptr;
+        for (bool &r : fr->ran) r = false;
+        fr->mark(LODGS_STAGE_SELECT, 0, st);
+        fr->k = make_camk(cams[i]);
+        views[i].k = fr->k;
+        views[i].bg[0] = fr->bg[0]; views[i].bg[1] = fr->bg[1]; views[i].bg[2] = fr->bg[2]; views[i].bg[3] = 0.f;
+        fs[i] = &fr->f;
+    }
+    if (int rc = launch_select_batch(sc, fs, views, n, st)) return rc;
+    for (int i = 0; i < n; ++i) {
+        lodgs_frame *fr = frames[i];
+        fr->have_view = true;
+        fr->counters_fresh = true;
+        fr->mark(LODGS_STAGE_SELECT, 1, st);
+        fr->selected = true;
+        fr->rendered = false;
+        fr->blend_bwd_done = false;
+    }
+    return LODGS_OK;
+}
+
 int lodgs_frame_get_stats(lodgs_frame *fr, lodgs_frame_stats *s) {
     if (!fr || !s) { set_error("frame_get_stats: NULL argument"); return LODGS_E_INVALID; }
     LODGS_CUDA(cudaStreamSynchronize(fr->stream));

@@ -241,6 +241,17 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
 constexpr int SEL_BLOCK_COUNTS = 1024;        // per-block counts of the selection passes (buffer entries)
 constexpr int SCAN_GRID = 148;                // scan blocks for short scans
 constexpr int SCAN_GRID_MAX = 148 * 8;        // ... growing with the element count (block-sum buffers)
+// Exclusive scans of k arrays at once (one grid row each), each as
+// scan_exclusive with no index array; the same max_n bounds every array.
+constexpr int SCAN_BATCH_MAX = 8;
+struct ScanBatch {
+    const uint32_t *in[SCAN_BATCH_MAX];
+    uint32_t *out[SCAN_BATCH_MAX];
+    const uint32_t *d_n[SCAN_BATCH_MAX];
+    uint32_t *block_sums[SCAN_BATCH_MAX];
+    uint32_t *d_total[SCAN_BATCH_MAX];
+};
+int scan_exclusive_batch(const ScanBatch &b, int k, uint32_t max_n, cudaStream_t st);
 int scan_exclusive(const uint32_t *in, uint32_t *out, const uint32_t *d_n, uint32_t max_n,
                    uint32_t *block_sums, uint32_t *d_total, cudaStream_t st, const uint32_t *idx = nullptr);
 // optional CUDA events bracketing stages (ev[2s], ev[2s+1]) of the stages in `mask`
@@ -256,6 +267,9 @@ struct StageMarks {
 // zero_cnt: also clear C_COUNT counters there (the start of a selection)
 int launch_set_view(const View &v, View *dst, cudaStream_t st, uint32_t *zero_cnt = nullptr);
 int launch_select(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st);
+// the selection of k <= SCAN_BATCH_MAX views in one launch of each pass (views
+// given: uploaded to each frame, its counters cleared)
+int launch_select_batch(const lodgs_scene *sc, FrameBufs *const *fs, const View *views, int k, cudaStream_t st);
 int launch_select_upper(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st);
 int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st);
 int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st);

@@ -27,6 +27,21 @@ static_assert(SPT_GRID <= SEL_BLOCK_COUNTS && SEL_GRID <= SEL_BLOCK_COUNTS, "per
 
 enum { OUT_NONE = 0, OUT_SELECT = 1, OUT_SPT = 2 };
 
+// One view's selection buffers.  Every selection kernel takes the views of a
+// batch by value and serves view blockIdx.y of them: lodgs_select_lod is a
+// batch of one, lodgs_select_lod_batch a batch of up to SEL_BATCH_MAX.
+struct SelPtrs {
+    const View *view;
+    uint32_t *cnt, *bc, *sel_rows, *sel_src, *emit_j, *high, *work_off, *scan_bsum;
+    float *emit_x, *up_x;
+    uint8_t *up_out;
+    const uint32_t *emit_src;
+};
+constexpr int SEL_BATCH_MAX = SCAN_BATCH_MAX;
+struct SelBatch {
+    SelPtrs v[SEL_BATCH_MAX];
+};
+
 // Algorithm 1 outcome for upper entry u; *x_out = tau * d / f of the entry.
 __device__ int upper_outcome(const UpperEntry *__restrict__ up, int u, const CamK &k, float *x_out) {
     UpperEntry e = up[u];
@@ -98,11 +113,13 @@ __device__ __forceinline__ uint32_t block_prefix(const uint32_t *__restrict__ co
 // ---- a1 --------------------------------------------------------------------
 // Counts per block; with a cache (up_out, up_x) the outcomes are kept for the
 // write pass, which then skips the ancestor walks.
-__global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict__ up, uint32_t U,
-                                                    const View *__restrict__ view, uint32_t *__restrict__ bc,
-                                                    uint8_t *__restrict__ up_out, float *__restrict__ up_x) {
+__global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict__ up, uint32_t U, SelBatch B) {
     pdl_wait();
-    const CamK &k = view->k;
+    const SelPtrs &P = B.v[blockIdx.y];
+    const CamK &k = P.view->k;
+    uint32_t *__restrict__ bc = P.bc;
+    uint8_t *__restrict__ up_out = P.up_out;
+    float *__restrict__ up_x = P.up_x;
     __shared__ uint32_t s_warp[32];
     uint32_t begin, end;
     grid_chunk(U, begin, end);
@@ -118,14 +135,16 @@ __global__ void __launch_bounds__(SB) k_upper_count(const UpperEntry *__restrict
     if (threadIdx.x == 0) bc[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict__ up, uint32_t U,
-                                                    const View *__restrict__ view,
-                                                    const uint32_t *__restrict__ bc, const uint8_t *__restrict__ up_out,
-                                                    const float *__restrict__ up_x, uint32_t *__restrict__ sel_rows,
-                                                    uint32_t *__restrict__ sel_src, uint32_t *__restrict__ emit_j,
-                                                    float *__restrict__ emit_x, uint32_t *__restrict__ cnt) {
+__global__ void __launch_bounds__(SB) k_upper_write(const UpperEntry *__restrict__ up, uint32_t U, SelBatch B) {
     pdl_wait();
-    const CamK &k = view->k;
+    const SelPtrs &P = B.v[blockIdx.y];
+    const CamK &k = P.view->k;
+    const uint32_t *__restrict__ bc = P.bc;
+    const uint8_t *__restrict__ up_out = P.up_out;
+    const float *__restrict__ up_x = P.up_x;
+    uint32_t *__restrict__ sel_rows = P.sel_rows, *__restrict__ sel_src = P.sel_src, *__restrict__ emit_j = P.emit_j;
+    float *__restrict__ emit_x = P.emit_x;
+    uint32_t *__restrict__ cnt = P.cnt;
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_off_sel, s_off_emit;
     uint32_t sel_before = 0, emit_before = 0;
@@ -198,11 +217,13 @@ __device__ __forceinline__ uint32_t warp_prefix_count(const T *__restrict__ arr,
 
 // One warp per emitted SPT: high = the first entry with hi <= x (entries are
 // sorted by descending hi).
-__global__ void __launch_bounds__(SB) k_spt_high(const uint32_t *__restrict__ cnt_in, const uint32_t *__restrict__ emit_j,
-                                                 const float *__restrict__ emit_x,
-                                                 const uint32_t *__restrict__ spt_base, const float *__restrict__ hi_row,
-                                                 uint32_t *__restrict__ high) {
+__global__ void __launch_bounds__(SB) k_spt_high(const uint32_t *__restrict__ spt_base, const float *__restrict__ hi_row,
+                                                 SelBatch B) {
     pdl_wait();
+    const SelPtrs &P = B.v[blockIdx.y];
+    const uint32_t *__restrict__ cnt_in = P.cnt, *__restrict__ emit_j = P.emit_j;
+    const float *__restrict__ emit_x = P.emit_x;
+    uint32_t *__restrict__ high = P.high;
     const uint32_t n = cnt_in[C_NEMIT];
     const uint32_t warps = gridDim.x * (SB / 32);
     for (uint32_t q = blockIdx.x * (SB / 32) + (threadIdx.x >> 5); q < n; q += warps) {
@@ -263,11 +284,13 @@ __device__ __forceinline__ bool tile_item(const SptTile &T, uint32_t w, const fl
     return lo_row[*row] <= T.x[a];
 }
 
-__global__ void __launch_bounds__(SB) k_spt_count(const uint32_t *__restrict__ cnt_in, const uint32_t *__restrict__ work_off,
-                                                  const uint32_t *__restrict__ emit_j, const float *__restrict__ emit_x,
-                                                  const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
-                                                  uint32_t *__restrict__ bc) {
+__global__ void __launch_bounds__(SB) k_spt_count(const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
+                                                  SelBatch B) {
     pdl_wait();
+    const SelPtrs &P = B.v[blockIdx.y];
+    const uint32_t *__restrict__ cnt_in = P.cnt, *__restrict__ work_off = P.work_off, *__restrict__ emit_j = P.emit_j;
+    const float *__restrict__ emit_x = P.emit_x;
+    uint32_t *__restrict__ bc = P.bc;
     __shared__ uint32_t s_warp[32];
     __shared__ SptTile T;
     __shared__ uint32_t s_q;
@@ -296,13 +319,15 @@ __global__ void __launch_bounds__(SB) k_spt_count(const uint32_t *__restrict__ c
     if (threadIdx.x == 0) bc[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(SB) k_spt_write(uint32_t *__restrict__ cnt, const uint32_t *__restrict__ work_off,
-                                                  const uint32_t *__restrict__ emit_j, const float *__restrict__ emit_x,
-                                                  const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
-                                                  const uint32_t *__restrict__ bc, uint32_t *__restrict__ sel_rows,
-                                                  uint32_t *__restrict__ sel_src,
-                                                  const uint32_t *__restrict__ emit_src) {
+__global__ void __launch_bounds__(SB) k_spt_write(const uint32_t *__restrict__ spt_base, const float *__restrict__ lo_row,
+                                                  SelBatch B) {
     pdl_wait();
+    const SelPtrs &P = B.v[blockIdx.y];
+    uint32_t *__restrict__ cnt = P.cnt;
+    const uint32_t *__restrict__ work_off = P.work_off, *__restrict__ emit_j = P.emit_j, *__restrict__ bc = P.bc;
+    const float *__restrict__ emit_x = P.emit_x;
+    uint32_t *__restrict__ sel_rows = P.sel_rows, *__restrict__ sel_src = P.sel_src;
+    const uint32_t *__restrict__ emit_src = P.emit_src;
     __shared__ uint32_t s_warp[32];
     __shared__ SptTile T;
     __shared__ uint32_t s_off, s_q;
@@ -348,6 +373,76 @@ __global__ void k_set_view(View v, View *__restrict__ dst, uint32_t *__restrict_
         for (uint32_t i = threadIdx.x; i < C_COUNT; i += blockDim.x) cnt[i] = 0u;
 }
 
+// k views at once: block b uploads view b and clears its frame's counters
+struct ViewBatch {
+    View v[SEL_BATCH_MAX];
+    View *dst[SEL_BATCH_MAX];
+    uint32_t *cnt[SEL_BATCH_MAX];
+};
+__global__ void k_set_views(ViewBatch b) {
+    pdl_wait();
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(&b.v[blockIdx.x]);
+    uint32_t *d = reinterpret_cast<uint32_t *>(b.dst[blockIdx.x]);
+    for (uint32_t i = threadIdx.x; i < sizeof(View) / 4; i += blockDim.x) d[i] = s[i];
+    for (uint32_t i = threadIdx.x; i < C_COUNT; i += blockDim.x) b.cnt[blockIdx.x][i] = 0u;
+}
+
+SelPtrs sel_ptrs(FrameBufs &f, bool with_src) {
+    SelPtrs p{};
+    p.view = f.d_view;
+    p.cnt = f.cnt;
+    p.bc = f.block_counts;
+    p.sel_rows = f.sel_rows;
+    p.sel_src = with_src ? f.sel_src : nullptr;
+    p.emit_j = f.emit_j;
+    p.high = f.high;
+    p.work_off = f.work_off;
+    p.scan_bsum = f.scan_bsum;
+    p.emit_x = f.emit_x;
+    p.up_x = f.up_x;
+    p.up_out = f.up_out;
+    p.emit_src = with_src ? f.emit_src : nullptr;
+    return p;
+}
+
+// the passes of Algorithms 1-2 for views[0, k) of a batch (the count pass
+// keeps each upper entry's outcome for the write pass)
+int launch_upper(const lodgs_scene *sc, const SelBatch &b, int k, cudaStream_t st) {
+    const uint32_t U = (uint32_t)sc->n_upper;
+    LODGS_CUDA(pdl_launch(k_upper_count, dim3(SEL_GRID, k), SB, st, sc->d_upper, U, b));
+    count_launches(1);
+    LODGS_CUDA(pdl_launch(k_upper_write, dim3(SEL_GRID, k), SB, st, sc->d_upper, U, b));
+    count_launches(1);
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
+
+int launch_high(const lodgs_scene *sc, const SelBatch &b, int k, cudaStream_t st) {
+    const unsigned hb = (unsigned)std::min<int64_t>(SPT_GRID, std::max<int64_t>(1, (sc->n_spt + SB / 32 - 1) / (SB / 32)));
+    LODGS_CUDA(pdl_launch(k_spt_high, dim3(hb, k), SB, st, sc->d_spt_base, sc->d_hi, b));
+    count_launches(1);
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
+
+int launch_spt(const lodgs_scene *sc, const SelBatch &b, int k, cudaStream_t st) {
+    ScanBatch s{};
+    for (int v = 0; v < k; ++v) {
+        s.in[v] = b.v[v].high;
+        s.out[v] = b.v[v].work_off;
+        s.d_n[v] = b.v[v].cnt + C_NEMIT;
+        s.block_sums[v] = b.v[v].scan_bsum;
+        s.d_total[v] = b.v[v].cnt + C_WORK;
+    }
+    if (int rc = scan_exclusive_batch(s, k, (uint32_t)sc->n_spt, st)) return rc;
+    LODGS_CUDA(pdl_launch(k_spt_count, dim3(SPT_GRID, k), SB, st, sc->d_spt_base, sc->d_lo, b));
+    count_launches(1);
+    LODGS_CUDA(pdl_launch(k_spt_write, dim3(SPT_GRID, k), SB, st, sc->d_spt_base, sc->d_lo, b));
+    count_launches(1);
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
+
 }  // namespace
 
 // The view goes to the device as a kernel argument: the copy is asynchronous,
@@ -360,42 +455,42 @@ int launch_set_view(const View &v, View *dst, cudaStream_t st, uint32_t *zero_cn
 }
 
 int launch_select_upper(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st) {
-    uint32_t U = (uint32_t)sc->n_upper;
-    LODGS_CUDA(pdl_launch(k_upper_count, SEL_GRID, SB, st, sc->d_upper, U, f.d_view, f.block_counts, f.up_out, f.up_x));
-    count_launches(1);
-    LODGS_CUDA(pdl_launch(k_upper_write, SEL_GRID, SB, st, sc->d_upper, U, f.d_view, f.block_counts, f.up_out, f.up_x, f.sel_rows,
-                                           with_src ? f.sel_src : nullptr, f.emit_j, f.emit_x, f.cnt));
-    count_launches(1);
-    LODGS_CUDA(cudaGetLastError());
-    return LODGS_OK;
+    SelBatch b{};
+    b.v[0] = sel_ptrs(f, with_src);
+    return launch_upper(sc, b, 1, st);
 }
 
 int launch_spt_high(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st) {
-    const unsigned hb = (unsigned)std::min<int64_t>(SPT_GRID, std::max<int64_t>(1, (sc->n_spt + SB / 32 - 1) / (SB / 32)));
-    LODGS_CUDA(pdl_launch(k_spt_high, hb, SB, st, f.cnt, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_hi, f.high));
-    count_launches(1);
-    LODGS_CUDA(cudaGetLastError());
-    return LODGS_OK;
+    SelBatch b{};
+    b.v[0] = sel_ptrs(f, false);
+    return launch_high(sc, b, 1, st);
 }
 
 int launch_select_spt(const lodgs_scene *sc, FrameBufs &f, bool with_src, cudaStream_t st) {
-    int rc = scan_exclusive(f.high, f.work_off, f.cnt + C_NEMIT, (uint32_t)sc->n_spt, f.scan_bsum, f.cnt + C_WORK, st);
-    if (rc) return rc;
-    LODGS_CUDA(pdl_launch(k_spt_count, SPT_GRID, SB, st, f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
-                                         f.block_counts));
-    count_launches(1);
-    LODGS_CUDA(pdl_launch(k_spt_write, SPT_GRID, SB, st, f.cnt, f.work_off, f.emit_j, f.emit_x, sc->d_spt_base, sc->d_lo,
-                                         f.block_counts, f.sel_rows, with_src ? f.sel_src : nullptr,
-                                         with_src ? f.emit_src : nullptr));
-    count_launches(1);
-    LODGS_CUDA(cudaGetLastError());
-    return LODGS_OK;
+    SelBatch b{};
+    b.v[0] = sel_ptrs(f, with_src);
+    return launch_spt(sc, b, 1, st);
 }
 
 int launch_select(const lodgs_scene *sc, FrameBufs &f, cudaStream_t st) {
-    int rc = launch_select_upper(sc, f, false, st);
-    if (!rc) rc = launch_spt_high(sc, f, st);
-    if (!rc) rc = launch_select_spt(sc, f, false, st);
+    FrameBufs *fs[1] = {&f};
+    return launch_select_batch(sc, fs, nullptr, 1, st);
+}
+
+// views[v] (if given) is uploaded to frame v and its counters cleared first
+int launch_select_batch(const lodgs_scene *sc, FrameBufs *const *fs, const View *views, int k, cudaStream_t st) {
+    if (k < 1 || k > SEL_BATCH_MAX) { set_error("select: batch size out of range"); return LODGS_E_INVALID; }
+    if (views) {
+        ViewBatch vb{};
+        for (int v = 0; v < k; ++v) { vb.v[v] = views[v]; vb.dst[v] = fs[v]->d_view; vb.cnt[v] = fs[v]->cnt; }
+        LODGS_CUDA(pdl_launch(k_set_views, k, 32, st, vb));
+        count_launches(1);
+    }
+    SelBatch b{};
+    for (int v = 0; v < k; ++v) b.v[v] = sel_ptrs(*fs[v], false);
+    int rc = launch_upper(sc, b, k, st);
+    if (!rc) rc = launch_high(sc, b, k, st);
+    if (!rc) rc = launch_spt(sc, b, k, st);
     return rc;
 }
 

@@ -192,11 +192,11 @@ __device__ __forceinline__ uint32_t block_reduce_add(uint32_t v, uint32_t *s_war
     return t;   // valid in warp 0
 }
 
-__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ in,
-                                                            const uint32_t *__restrict__ idx,
-                                                            const uint32_t *__restrict__ d_n,
-                                                            uint32_t *__restrict__ block_sums) {
-    pdl_wait();
+// The scan's two passes as device functions, launched for one array
+// (k_scan_reduce, k_scan_down) or for several at once (the _batch kernels: one
+// array per grid row blockIdx.y).
+__device__ __forceinline__ void scan_reduce_body(const uint32_t *__restrict__ in, const uint32_t *__restrict__ idx,
+                                                 const uint32_t *__restrict__ d_n, uint32_t *__restrict__ block_sums) {
     __shared__ uint32_t s_warp[32];
     uint32_t begin, end;
     scan_chunk(*d_n, begin, end);
@@ -206,11 +206,9 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__re
     if (threadIdx.x == 0) block_sums[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *in, const uint32_t *__restrict__ idx,
-                                                          uint32_t *out, const uint32_t *__restrict__ d_n,
-                                                          const uint32_t *__restrict__ block_sums,
-                                                          uint32_t *d_total) {
-    pdl_wait();
+__device__ __forceinline__ void scan_down_body(const uint32_t *in, const uint32_t *__restrict__ idx, uint32_t *out,
+                                               const uint32_t *__restrict__ d_n,
+                                               const uint32_t *__restrict__ block_sums, uint32_t *d_total) {
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -266,6 +264,34 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *in, co
     }
     if (blockIdx.x == gridDim.x - 1 && tid == 0 && d_total) *d_total = s_carry;
 }
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ in,
+                                                            const uint32_t *__restrict__ idx,
+                                                            const uint32_t *__restrict__ d_n,
+                                                            uint32_t *__restrict__ block_sums) {
+    pdl_wait();
+    scan_reduce_body(in, idx, d_n, block_sums);
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down(const uint32_t *in, const uint32_t *__restrict__ idx,
+                                                          uint32_t *out, const uint32_t *__restrict__ d_n,
+                                                          const uint32_t *__restrict__ block_sums,
+                                                          uint32_t *d_total) {
+    pdl_wait();
+    scan_down_body(in, idx, out, d_n, block_sums, d_total);
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce_batch(ScanBatch b) {
+    pdl_wait();
+    const int v = blockIdx.y;
+    scan_reduce_body(b.in[v], nullptr, b.d_n[v], b.block_sums[v]);
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down_batch(ScanBatch b) {
+    pdl_wait();
+    const int v = blockIdx.y;
+    scan_down_body(b.in[v], nullptr, b.out[v], b.d_n[v], b.block_sums[v], b.d_total[v]);
+}
 }  // namespace
 
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_n,
@@ -298,6 +324,23 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_
     }
     LODGS_CUDA(cudaGetLastError());
     *result_in_alt = alt;
+    return LODGS_OK;
+}
+
+int scan_exclusive_batch(const ScanBatch &b, int k, uint32_t max_n, cudaStream_t st) {
+    if (k < 1 || k > SCAN_BATCH_MAX) { set_error("scan: batch size out of range"); return LODGS_E_INVALID; }
+    if (max_n <= SCAN_ONE_BLOCK) {
+        LODGS_CUDA(pdl_launch(k_scan_down_batch, dim3(1, k), SC_THREADS, st, b));
+        count_launches(1);
+        LODGS_CUDA(cudaGetLastError());
+        return LODGS_OK;
+    }
+    const int G = (int)std::min<uint64_t>(SCAN_GRID_MAX, std::max<uint64_t>(SCAN_GRID, (uint64_t)max_n / (SC_TILE * 4)));
+    LODGS_CUDA(pdl_launch(k_scan_reduce_batch, dim3(G, k), SC_THREADS, st, b));
+    count_launches(1);
+    LODGS_CUDA(pdl_launch(k_scan_down_batch, dim3(G, k), SC_THREADS, st, b));
+    count_launches(1);
+    LODGS_CUDA(cudaGetLastError());
     return LODGS_OK;
 }
 
