@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--train-leaves", type=int, default=150_000_000)
     p.add_argument("--no-train-batch", action="store_true")
     p.add_argument("--no-densify", action="store_true")
+    p.add_argument("--no-config1", action="store_true")
     p.add_argument("--streams", type=int, default=3,
                    help="views in flight at once in the timed steps (independent views, one stream each)")
     return p.parse_args()
@@ -381,6 +382,8 @@ def run_lodgs(args, rank: int, world: int):
         for s in _lib.STAGES:
             stage_ms[s].append(t[s])
         work[v] = frames[v].work()          # pixel-Gaussian work, tallied by the profiling launches
+    for fr in frames.values():              # no stage events in what follows
+        fr.set_profiling(False)
     stage_mean = {s: float(np.mean(x)) for s, x in stage_ms.items()}
     stage_mean_live = dict(stage_mean)
     stage_mean_live["blend_bwd"] = float(np.mean(bwd_ms))
@@ -416,6 +419,43 @@ def run_lodgs(args, rank: int, world: int):
             q1.record(stream)
             torch.cuda.synchronize()
         fwd_inflight[k] = q0.elapsed_time(q1) / len(order)
+
+    # ---- LoD selection of K views (K = 1, 2, 4, 8): K single-view selections
+    # one after another against one lodgs_select_lod_batch, each graph-replayed
+    # on one stream over the distinct views of this rank, ms per view ----
+    select_k = {}
+    distinct = list(dict.fromkeys(order)) if len(set(order)) >= 8 else list(my_views)
+    with torch.cuda.stream(cap):
+        for k in (1, 2, 4, 8):
+            groups = [distinct[i:i + k] for i in range(0, len(distinct) - k + 1, k)]
+            pair = []
+            for g in groups:
+                one, many = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+                with torch.cuda.graph(one, stream=cap):
+                    for v in g:
+                        api.select_lod(scene, cams[v], frames[v])
+                with torch.cuda.graph(many, stream=cap):
+                    api.select_lod_batch(scene, [cams[v] for v in g], [frames[v] for v in g])
+                pair.append((one, many))
+            select_k[k] = (pair, sum(len(g) for g in groups))
+    torch.cuda.synchronize()
+    select_batch_ms = {}
+    for k, (pair, nvk) in select_k.items():
+        t = {}
+        for which in (0, 1):
+            for rep in range(3):                 # the last of three passes (the first warms)
+                q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                q0.record(stream)
+                for p in pair:
+                    p[which].replay()
+                q1.record(stream)
+                torch.cuda.synchronize()
+            t[which] = q0.elapsed_time(q1) / nvk
+        select_batch_ms[k] = {"one_at_a_time": round(t[0], 4), "batched": round(t[1], 4)}
+    del select_k
+    for v in my_views:                           # the frames back on their own views (same cuts)
+        graphs[v][0].replay()
+    torch.cuda.synchronize()
 
     # ---- training step: the same step followed by a sparse Adam step of the view's
     # cut (device-resident state, 3DGS-style per-column rates on the stored values) ----
@@ -515,7 +555,7 @@ def run_lodgs(args, rank: int, world: int):
     res = {
         "ms": ms, "fwd_ms": fwd_ms, "e2e_ms": max(e2e_ms, e2e_wall * 1e3), "views": total_views,
         "train_ms": train_ms, "host_submit_ms": host_submit_ms, "serial_ms": serial_ms, "streams": n_streams,
-        "fwd_inflight_ms": fwd_inflight,
+        "fwd_inflight_ms": fwd_inflight, "select_batch_ms": select_batch_ms,
         "stage_ms": stage_mean_live, "stage_ms_eager": stage_mean, "clocks": clk, "launches": launches,
         "stats_ok": stats_ok, "work": work,
         "fwd_stats": fwd_stats, "scene": {"n_nodes": scene.n_nodes, "n_upper": scene.n_upper, "n_spt": scene.n_spt,
@@ -702,6 +742,8 @@ def run_serving(args) -> dict:
     mix.warm(warm_set)
     fifo = serving.RenderServer(scene, n_slots=1, mem_budget_bytes=16 << 30)
     fifo.warm(warm_set)
+    mix_pv = serving.RenderServer(scene, n_slots=8, mem_budget_bytes=16 << 30, batch_select=False)
+    mix_pv.warm(warm_set)
 
     def fmt(r):
         return {k: round(v, 4) if isinstance(v, float) else v for k, v in r.items()}
@@ -712,13 +754,17 @@ def run_serving(args) -> dict:
         r_mix = mix.run(serving.poisson_requests(cams, rate, n, seed=4))
         r_fifo = fifo.run(serving.poisson_requests(cams, rate, n, seed=4))
         loads[f"{int(rate)}_per_s"] = {"requests": n, "continuous_batching": fmt(r_mix), "one_at_a_time": fmt(r_fifo)}
+        if rate >= 800.0:
+            r_pv = mix_pv.run(serving.poisson_requests(cams, rate, n, seed=4))
+            loads[f"{int(rate)}_per_s"]["continuous_batching_per_view_selection"] = fmt(r_pv)
     return {"workload": f"{args.serving_leaves:,}-leaf SH3 city (2 km), Poisson arrivals, resolution in "
                         "{360p,720p,1080p,2160p}, tau in {0.5,1,2,4} px, half aerial half street; 8 slots, "
-                        "8 GiB workspace budget",
+                        "16 GiB workspace budget; requests admitted together share one batched LoD selection",
             "nodes": scene.n_nodes, "spt": scene.n_spt, "build_s": round(t_build, 2),
             "request_classes_learned": len(mix.need), **loads["200_per_s"],
             "load_600_per_s": loads["600_per_s"], "load_800_per_s": loads["800_per_s"], "unit": "ms",
             "slot_workspace_gb": [round(sl.held / 1e9, 2) for sl in mix.slots],
+            "slot_workspace_after_warm_gb": round(mix.warm_bytes / 1e9, 3),
             "admission": "a request runs on a free slot whose workspace holds the largest bytes its class "
                          "(resolution, tau) needed (lodgs_frame_memory); slots sized within the budget in the "
                          "warm-up"}
@@ -1071,30 +1117,53 @@ def run_train_batch(args) -> dict:
     sizes = [fr.stats()["n_selected"] for fr in frames]
     grads = [torch.empty((max(n, 1), scene.stride), device="cuda") for n in sizes]
 
-    def step():
+    main = torch.cuda.current_stream()
+
+    def step(batched: bool):
+        """batched: the 8 cuts in one lodgs_select_lod_batch on the main
+        stream, then each view's render and backward on its own stream;
+        otherwise each view selects on its own stream."""
+        if batched:
+            api.select_lod_batch(scene, views, frames, stream=main)
+            sel = torch.cuda.Event()
+            sel.record(main)
         for v, cam in enumerate(views):
             with torch.cuda.stream(streams[v]):
-                fr = api.select_lod(scene, cam, frames[v], stream=streams[v])
+                if batched:
+                    streams[v].wait_event(sel)
+                    fr = frames[v]
+                else:
+                    streams[v].wait_stream(main)
+                    fr = api.select_lod(scene, cam, frames[v], stream=streams[v])
                 api.render(scene, fr, image=imgs[v], stream=streams[v], check_capacity=False)
                 api.render_backward_blend_l1(scene, fr, targets[v], stream=streams[v])
                 api.render_backward_project(scene, fr, grads[v], stream=streams[v])
+        for s_ in streams:
+            main.wait_stream(s_)
         return api.accumulate_grads(scene, frames, grads)
 
-    for _ in range(2):
-        step()
-    torch.cuda.synchronize()
-    reps = 5
-    t1 = time.perf_counter()
-    for _ in range(reps):
-        rows, _g = step()
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t1) / reps
+    out = {}
+    for batched in (True, False):
+        for _ in range(2):
+            step(batched)
+        torch.cuda.synchronize()
+        reps = 5
+        t1 = time.perf_counter()
+        for _ in range(reps):
+            rows, _g = step(batched)
+        torch.cuda.synchronize()
+        out[batched] = (time.perf_counter() - t1) / reps
+    dt = out[True]
     return {"workload": f"{args.train_leaves:,}-leaf SH3 city (2 km), batch of 8 views (4 aerial, 4 street) at "
-                        "1600x1200: select + render + mean-L1 + backward, batch gradient on the union of the cuts",
+                        "1600x1200: one batched LoD selection of the 8 views, then render + mean-L1 + backward "
+                        "per view on its own stream, batch gradient on the union of the cuts",
             "nodes": scene.n_nodes, "spt": scene.n_spt, "build_s": round(t_build, 2),
             "step_ms": round(dt * 1e3, 3), "views_per_s": round(8 / dt, 1),
+            "step_ms_per_view_selection": round(out[False] * 1e3, 3),
             "selected_per_view": sizes, "union_rows": int(rows.numel()),
-            "device_gb_peak": round(torch.cuda.max_memory_allocated() / 1e9, 1)}
+            "device_gb_peak": round(torch.cuda.max_memory_allocated() / 1e9, 1),
+            "note": "wall time per batch step (host enqueue included); step_ms_per_view_selection: the same "
+                    "step with each view's selection launched on its own stream"}
 
 
 def run_densify(args) -> dict:
@@ -1206,6 +1275,10 @@ def main():
                      "views_in_flight_ms_per_frame": {str(k): round(v, 4) for k, v in res["fwd_inflight_ms"].items()},
                      "views_in_flight_note": "graph-replayed forward (camera upload, select, render) round-robin "
                                              "on K streams, ms per view"},
+        "select_batch": {"ms_per_view": {str(k): v for k, v in res["select_batch_ms"].items()},
+                         "note": "LoD selection alone for groups of K distinct views, graph-replayed on one "
+                                 "stream: K lodgs_select_lod calls one after another against one "
+                                 "lodgs_select_lod_batch (each selection pass launched once for the K views)"},
         "e2e": {"value": res["views"] / (res["e2e_ms"] * 1e-3), "unit": "frames/s",
                 "h2d_bytes_per_step": res["h2d_bytes"], "d2h_bytes_per_step": res["d2h_bytes"],
                 "note": "each view's 8-bit RGB target (pinned host) uploaded on a copy stream while the "
@@ -1246,7 +1319,7 @@ def main():
         import torch
         torch.cuda.empty_cache()
 
-    if world == 1:
+    if world == 1 and not args.no_config1:
         section("config1", run_config1)
     if world == 1 and not args.no_out_of_core:
         section("out_of_core", run_out_of_core)

@@ -18,6 +18,7 @@ LODGS_E_CUDA = -3
 LODGS_E_TIMEOUT = -4
 LODGS_E_STATE = -5
 LODGS_E_CAPACITY = -6
+LODGS_SELECT_BATCH_MAX = 8       # views per lodgs_select_lod_batch call
 STAGES = ("select", "project", "count", "emit", "tile_sort", "blend", "blend_bwd", "project_bwd")
 _NAMES = {-1: "INVALID", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", -6: "CAPACITY"}
 

@@ -26,9 +26,15 @@ it has not yet overflowed could hold it; otherwise the queued growth is
 cancelled (lodgs_frame_reserve) and the request goes back to the head of the
 queue to wait for one of those slots.  A request therefore goes back to the
 queue at most once per slot before it grows one.  A class not seen in the
-warm-up is
-admitted alone to the largest slot (which grows if it must).  The server keeps
-only as many slots as the budget holds at their base size (at least one).
+warm-up is admitted alone to the largest slot (which grows if it must).  The
+server keeps only as many slots as the budget holds at their base size (at
+least one).
+
+Requests admitted in the same pass of the loop share one batched LoD
+selection (lodgs_select_lod_batch: each selection pass launched once for up
+to eight views) on the server's front stream; each one's render then runs on
+its own slot's stream after it.  The selection of a view in a batch is the
+one it has alone, so a request's image still does not depend on the others.
 """
 from __future__ import annotations
 
@@ -114,18 +120,23 @@ class _Slot:
 class RenderServer:
     def __init__(self, scene: api.Scene, n_slots: int = 8, mem_budget_bytes: int = 4 << 30,
                  max_pixels: int = 3840 * 2160, rows: torch.Tensor | None = None, keep_images: bool = False,
-                 lookahead: int = 8):
+                 lookahead: int = 8, batch_select: bool = True):
         self.scene = scene
         self.rows = rows
+        self.max_pixels = max_pixels
         self.slots = [_Slot(scene, max_pixels) for _ in range(n_slots)]
         self.budget = mem_budget_bytes
         self.keep_images = keep_images
         self.lookahead = lookahead
+        self.batch_select = batch_select  # one batched selection for the requests admitted together
+        self.front = torch.cuda.Stream()  # where the batched selections run
+        self.batches = self.batched_views = 0
         self.need: dict = {}              # request class -> largest workspace bytes it needed
         self.rep: dict = {}               # request class -> the camera of that largest need
         self._ref = None                  # event at the start of run(): device times are taken from it
         while len(self.slots) > 1 and self.held_bytes() > self.budget:
             self.slots.pop()              # the budget holds fewer slots at their base size (at least one)
+        self.warm_bytes = self.held_bytes()   # what the slots hold after warm()
 
     # ---- memory bookkeeping ----
     def charge(self, camera):
@@ -170,6 +181,52 @@ class RenderServer:
             return False
         slot.req = req
         return True
+
+    def _launch_together(self, admitted: list) -> list:
+        """Enqueue requests admitted in the same pass: one batched LoD
+        selection per LODGS_SELECT_BATCH_MAX of them on the front stream, after
+        which each render runs on its slot's stream.  A batch the library
+        refuses (e.g. one invalid camera) is launched view by view, so only the
+        offending request fails.  Returns the pairs that failed (slot left
+        free)."""
+        failed = []
+        nb = _lib.LODGS_SELECT_BATCH_MAX
+        for i in range(0, len(admitted), nb):
+            chunk = admitted[i:i + nb]
+            if len(chunk) == 1 or not self.batch_select:
+                failed += [(s, r) for s, r in chunk if not self._launch(s, r)]
+                continue
+            fs = self.front
+            for s, _ in chunk:               # a free slot's stream is idle; the wait keeps the order explicit
+                fs.wait_stream(s.stream)
+            start = torch.cuda.Event(enable_timing=True)
+            start.record(fs)
+            try:
+                api.select_lod_batch(self.scene, [r.camera for _, r in chunk], [s.frame for s, _ in chunk],
+                                     stream=fs)
+            except _lib.LodgsError:
+                failed += [(s, r) for s, r in chunk if not self._launch(s, r)]
+                continue
+            selected = torch.cuda.Event()
+            selected.record(fs)
+            self.batches += 1
+            self.batched_views += len(chunk)
+            for s, r in chunk:
+                cam = r.camera
+                img = s.image[: cam.height * cam.width * 3].view(cam.height, cam.width, 3)
+                if r.ev_start is None:
+                    r.ev_start = start
+                s.stream.wait_event(selected)
+                try:
+                    api.render(self.scene, s.frame, rows=self.rows, image=img, stream=s.stream,
+                               check_capacity=False)
+                except _lib.LodgsError as e:
+                    r.status = f"failed: {e}"
+                    failed.append((s, r))
+                    continue
+                s.done.record(s.stream)
+                s.req = r
+        return failed
 
     def _finish(self, slot: _Slot, now: float) -> str:
         """'done', 'retry' (rendered again on this slot, which grows) or
@@ -226,10 +283,14 @@ class RenderServer:
                 if n > slot.held:
                     self._render(slot, self.rep[k])
                     self._learn(slot, self.rep[k])
+                    if slot.held > room:         # grew past its share: a fresh base-size slot instead
+                        slot.frame.close()
+                        slot = _Slot(self.scene, self.max_pixels)
             kept.append(slot)
             remaining -= slot.held
         self.slots = kept
         torch.cuda.synchronize()
+        self.warm_bytes = self.held_bytes()
 
     def run(self, requests: list[Request], realtime: bool = True, deadline_ms: float | None = None) -> dict:
         """Serve `requests` (sorted by arrival).  realtime: requests arrive on
@@ -243,6 +304,8 @@ class RenderServer:
         done = 0
         inflight_max = 0
         held_max = self.held_bytes()
+        self.batches = self.batched_views = 0
+        grown_past = 0                    # retries that grew the slots past the budget (no slot could hold the view)
         torch.cuda.synchronize()
         self._ref = torch.cuda.Event(enable_timing=True)
         self._ref.record()
@@ -262,7 +325,10 @@ class RenderServer:
                         done += 1
                     elif out == "requeue":
                         pending.appendleft(req)
-            held_max = max(held_max, self.held_bytes())
+            held = self.held_bytes()
+            if held > self.budget and held > held_max:
+                grown_past += 1
+            held_max = max(held_max, held)
             # admission: the head of the queue, then up to `lookahead` later
             # requests, each to a free slot whose workspace holds its class's need
             free = [s for s in self.slots if s.req is None]
@@ -271,6 +337,7 @@ class RenderServer:
                 pending.popleft().status = "expired"     # waited past its deadline: never launched
                 done += 1
             q = 0
+            admitted = []
             while q < min(len(pending), 1 + self.lookahead) and free:
                 req = pending[q]
                 busy = len(free) < len(self.slots)
@@ -281,10 +348,8 @@ class RenderServer:
                 del pending[q]
                 free.remove(slot)
                 req.t_admit = time.perf_counter() - t0
-                if not self._launch(slot, req):
-                    free.append(slot)
-                    done += 1
-                    continue
+                admitted.append((slot, req))
+            done += len(self._launch_together(admitted))
             inflight = sum(s.req is not None for s in self.slots)
             # with nothing in flight every slot is free and pick_slot admits the
             # head (it may not wait): a queue left waiting here would spin forever
@@ -303,7 +368,9 @@ class RenderServer:
                 "gpu_busy": gpu_busy_fraction([r.dev_ms for r in ok if r.dev_ms is not None], wall * 1e3),
                 "slots": len(self.slots), "slot_workspace_bytes": self.held_bytes(),
                 "peak_slot_workspace_bytes": int(held_max), "budget_bytes": int(self.budget),
+                "growths_past_budget": grown_past,
                 "retries": int(sum(r.retries for r in reqs)), "requeues": int(sum(r.requeues for r in reqs)),
+                "batched_selections": self.batches, "views_in_batched_selections": self.batched_views,
                 "completed": len(ok), "expired": sum(r.status == "expired" for r in reqs),
                 "failed": sum(r.status.startswith("failed") for r in reqs)}
 

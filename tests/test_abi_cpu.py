@@ -58,3 +58,19 @@ def test_fault_injection_hook_validates_its_site():
     assert lib.lodgs_debug_inject_fault(0, 0) == _lib.LODGS_E_INVALID
     assert lib.lodgs_debug_inject_fault(_lib.FAULT_ALLOC, -1) == _lib.LODGS_OK
     assert lib.lodgs_debug_inject_fault(_lib.FAULT_STREAM, -1) == _lib.LODGS_OK
+
+
+def test_binding_constants_match_the_header():
+    """Every #define of include/lodgs.h that the binding mirrors has the
+    header's value (status codes, batch bound, fault sites, densify ops)."""
+    from paper_2507_01110_b300 import _lib
+    src = open(os.path.join(ROOT, "include", "lodgs.h")).read()
+    defs = {m.group(1): int(m.group(2).replace(" ", ""))
+            for m in re.finditer(r"#define\s+(LODGS_[A-Z0-9_]+)\s+\(?\s*(-?\s*\d+)\s*\)?\s*(?:/\*|$)", src, flags=re.M)}
+    mirrored = {"LODGS_OK", "LODGS_E_INVALID", "LODGS_E_OOM", "LODGS_E_CUDA", "LODGS_E_TIMEOUT", "LODGS_E_STATE",
+                "LODGS_E_CAPACITY", "LODGS_SELECT_BATCH_MAX"}
+    assert mirrored <= set(defs), mirrored - set(defs)
+    for name in mirrored:
+        assert getattr(_lib, name) == defs[name], name
+    for name in ("FAULT_STREAM", "FAULT_ALLOC", "FAULT_RENDER"):
+        assert getattr(_lib, name) == defs["LODGS_" + name], name

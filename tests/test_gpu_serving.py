@@ -1,5 +1,6 @@
 """Continuous-batching server: overlapping requests of mixed resolution and
-LoD threshold give exactly the images they give alone."""
+LoD threshold, admitted together and sharing batched LoD selections, give
+exactly the images they give alone."""
 import pytest
 import torch
 
@@ -36,6 +37,7 @@ def test_results_identical_alone_and_in_the_mix(scene):
     r_mix = _requests(52)
     st_mix = mix.run(r_mix, realtime=False)
     assert st_alone["max_inflight"] == 1 and st_mix["max_inflight"] > 1
+    assert st_alone["batched_selections"] == 0 and st_mix["batched_selections"] > 0   # shared selections
     by_id = {r.rid: r for r in r_alone}
     for r in r_mix:
         assert torch.equal(r.image, by_id[r.rid].image), r.rid
