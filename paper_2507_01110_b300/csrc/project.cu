@@ -148,6 +148,10 @@ __device__ __forceinline__ void support_extents(float a, float c, float det, flo
     }
 }
 
+// Floats per record of SH degree DEG (14 base values + 3 per SH coefficient,
+// padded to a multiple of 8).
+__host__ __device__ constexpr int rec_stride(int deg) { return (14 + 3 * ((deg + 1) * (deg + 1) - 1) + 7) / 8 * 8; }
+
 template <int DEG>
 __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, int stride,
                                                  const uint32_t *__restrict__ sel_rows, const View *__restrict__ view,
@@ -217,7 +221,18 @@ __global__ void __launch_bounds__(PB) k_project(const float *__restrict__ rows, 
                         if (K > 0) {
                             float Y[15];
                             sh_basis(degree, dx, dy, dz, Y);
-                            const float *f = r + REC_F;
+                            // the coefficients (row floats 14 .. 14 + 3K) as float4 loads from
+                            // float 12: rows are 16-byte aligned and padded to 8 floats, so the
+                            // last chunk ends inside the row
+                            constexpr int NCH = (2 + 3 * K + 3) / 4;
+                            static_assert(12 + 4 * NCH <= rec_stride(DEG), "chunks inside the row");
+                            float fl[4 * NCH];
+#pragma unroll
+                            for (int m = 0; m < NCH; ++m) {
+                                const float4 v = *reinterpret_cast<const float4 *>(r + 12 + 4 * m);
+                                fl[4 * m] = v.x; fl[4 * m + 1] = v.y; fl[4 * m + 2] = v.z; fl[4 * m + 3] = v.w;
+                            }
+                            const float *f = fl + (REC_F - 12);
 #pragma unroll
                             for (int kk = 0; kk < K; ++kk) {
                                 col[0] += Y[kk] * f[3 * kk];
@@ -257,9 +272,6 @@ __device__ __forceinline__ void cp_async4(float *dst_smem, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 
-// Floats per record of SH degree DEG (14 base values + 3 per SH coefficient,
-// padded to a multiple of 8).
-__host__ __device__ constexpr int rec_stride(int deg) { return (14 + 3 * ((deg + 1) * (deg + 1) - 1) + 7) / 8 * 8; }
 
 // Each warp handles 32 selected Gaussians at a time: the records of the
 // visible ones are staged in shared memory row by row (whole-warp, coalesced

@@ -25,7 +25,10 @@ the same slot, which grows, if the budget still holds the grown slot or no slot
 it has not yet overflowed could hold it; otherwise the queued growth is
 cancelled (lodgs_frame_reserve) and the request goes back to the head of the
 queue to wait for one of those slots.  A request therefore goes back to the
-queue at most once per slot before it grows one.  A class not seen in the
+queue at most once per slot before it grows one.  A growth that would break
+the budget first returns idle slots to a fresh workspace, largest first, if
+that makes room; only when the idle slots cannot make room does a growth take
+the slots past the budget.  A class not seen in the
 warm-up is admitted alone to the largest slot (which grows if it must).  The
 server keeps only as many slots as the budget holds at their base size (at
 least one).
@@ -107,6 +110,23 @@ def overflow_action(needed: int, need: int, slot, slots, tried, budget: int) -> 
     return "requeue" if grown > budget and others else "retry"
 
 
+def shrink_plan(grown_total: int, slot, slots, budget: int, base: int) -> list:
+    """The idle slots to return to their base workspace (largest first) so
+    that `slot`, growing the slots' total to `grown_total`, stays within the
+    budget; [] if it already does or if even all of them would not make room
+    (the growth then goes past the budget: no slot could hold the view)."""
+    if grown_total <= budget:
+        return []
+    idle = sorted((s for s in slots if s is not slot and s.req is None and s.held > base), key=lambda s: -s.held)
+    plan, total = [], grown_total
+    for s in idle:
+        if total <= budget:
+            break
+        plan.append(s)
+        total -= s.held - base
+    return plan if total <= budget else []
+
+
 class _Slot:
     def __init__(self, scene: api.Scene, max_pixels: int):
         self.frame = api.Frame(scene)
@@ -130,13 +150,14 @@ class RenderServer:
         self.lookahead = lookahead
         self.batch_select = batch_select  # one batched selection for the requests admitted together
         self.front = torch.cuda.Stream()  # where the batched selections run
-        self.batches = self.batched_views = 0
+        self.batches = self.batched_views = self.shrinks = 0
         self.need: dict = {}              # request class -> largest workspace bytes it needed
         self.rep: dict = {}               # request class -> the camera of that largest need
         self._ref = None                  # event at the start of run(): device times are taken from it
         while len(self.slots) > 1 and self.held_bytes() > self.budget:
             self.slots.pop()              # the budget holds fewer slots at their base size (at least one)
         self.warm_bytes = self.held_bytes()   # what the slots hold after warm()
+        self.base = min(sl.held for sl in self.slots)   # a fresh frame's workspace
 
     # ---- memory bookkeeping ----
     def charge(self, camera):
@@ -238,6 +259,12 @@ class RenderServer:
             req.tried.add(id(slot))
             need = self.charge(req.camera)
             if overflow_action(needed, need, slot, self.slots, req.tried, self.budget) == "retry":
+                grown = self.held_bytes() - slot.held + int(GROWTH * needed)
+                for idle in shrink_plan(grown, slot, self.slots, self.budget, self.base):
+                    idle.frame.close()               # back to a fresh frame: room for this growth
+                    idle.frame = api.Frame(self.scene)
+                    idle.held = idle.frame.memory()[0]
+                    self.shrinks += 1
                 req.retries += 1
                 if not self._launch(slot, req):      # growing the workspace failed: give up on it
                     slot.req = None
@@ -304,7 +331,7 @@ class RenderServer:
         done = 0
         inflight_max = 0
         held_max = self.held_bytes()
-        self.batches = self.batched_views = 0
+        self.batches = self.batched_views = self.shrinks = 0
         grown_past = 0                    # retries that grew the slots past the budget (no slot could hold the view)
         torch.cuda.synchronize()
         self._ref = torch.cuda.Event(enable_timing=True)
@@ -368,7 +395,7 @@ class RenderServer:
                 "gpu_busy": gpu_busy_fraction([r.dev_ms for r in ok if r.dev_ms is not None], wall * 1e3),
                 "slots": len(self.slots), "slot_workspace_bytes": self.held_bytes(),
                 "peak_slot_workspace_bytes": int(held_max), "budget_bytes": int(self.budget),
-                "growths_past_budget": grown_past,
+                "growths_past_budget": grown_past, "slots_shrunk": self.shrinks,
                 "retries": int(sum(r.retries for r in reqs)), "requeues": int(sum(r.requeues for r in reqs)),
                 "batched_selections": self.batches, "views_in_batched_selections": self.batched_views,
                 "completed": len(ok), "expired": sum(r.status == "expired" for r in reqs),

@@ -3,7 +3,8 @@ overflow_action) on the CPU: a simulation with the server loop's structure
 over fake slots whose selection and pair buffers overflow separately, as the
 library's do.  Every request completes (no request goes back to the queue
 forever), each one returns to the queue at most once per slot, and the slots
-grow past the budget only when no slot could hold a view."""
+grow past the budget only when no slot could hold a view and the idle slots,
+returned to their base size, could not make room (shrink_plan)."""
 import collections
 import random
 from types import SimpleNamespace
@@ -25,11 +26,12 @@ def _slot(cap_sel, cap_pairs):
     return s
 
 
-def _simulate(rng, n_slots, budget, views, lookahead):
+def _simulate(rng, n_slots, budget, views, lookahead, sizes=None):
     """The server loop: completions (overflow -> retry or requeue), then
-    admission of the head and up to `lookahead` later requests."""
+    admission of the head and up to `lookahead` later requests.  sizes: the
+    slots' (selection, pair) capacities after a warm-up (default: base)."""
     base = _bytes(64, 256)
-    slots = [_slot(64, 256) for _ in range(n_slots)]
+    slots = [_slot(*(sizes[i] if sizes else (64, 256))) for i in range(n_slots)]
     while len(slots) > 1 and sum(s.held for s in slots) > budget:
         slots.pop()
     need = {}
@@ -37,6 +39,7 @@ def _simulate(rng, n_slots, budget, views, lookahead):
             for i, (c, ns, npairs) in enumerate(views)]
     pending = collections.deque(reqs)
     forced = 0
+    shrinks = [0]
     done = 0
     for tick in range(20_000):
         if done == len(reqs):
@@ -52,6 +55,10 @@ def _simulate(rng, n_slots, budget, views, lookahead):
                 r.tried.add(id(s))
                 act = serving.overflow_action(vb, need[r.cls], s, slots, r.tried, budget)
                 if act == "retry":                       # grows the short buffer, launches again
+                    grown = sum(x.held for x in slots) - s.held + int(serving.GROWTH * vb)
+                    for idle in serving.shrink_plan(grown, s, slots, budget, base):
+                        idle.cap_sel, idle.cap_pairs, idle.held = 64, 256, base
+                        shrinks[0] += 1
                     before = sum(x.held for x in slots)
                     if r.ns > s.cap_sel:
                         s.cap_sel = int(serving.GROWTH * r.ns)
@@ -80,6 +87,7 @@ def _simulate(rng, n_slots, budget, views, lookahead):
             del pending[q]
             free.remove(s)
             s.req = r
+    _simulate.shrinks = shrinks[0]
     return reqs, slots, forced, tick, base
 
 
@@ -128,3 +136,33 @@ def test_the_budget_holds_when_a_large_enough_slot_exists():
     assert all(r.done for r in reqs) and forced == 0
     assert sum(s.held for s in slots) <= budget
     assert any(r.requeues for r in reqs)
+
+
+def test_shrink_plan_returns_the_largest_idle_slots_until_the_growth_fits():
+    base = 100
+    mk = lambda held, busy=False: SimpleNamespace(held=held, req=object() if busy else None)
+    grower, a, b, c, busy = mk(300), mk(900), mk(400), mk(100), mk(2000, busy=True)
+    slots = [grower, a, b, c, busy]
+    total = sum(x.held for x in slots)                               # 3700
+    assert serving.shrink_plan(total, grower, slots, 4000, base) == []          # fits already
+    assert serving.shrink_plan(total + 500, grower, slots, 4000, base) == [a]   # 4200 - 800 <= 4000
+    assert serving.shrink_plan(total + 1200, grower, slots, 4000, base) == [a, b]   # 4900 - 800 - 300
+    assert serving.shrink_plan(total + 3000, grower, slots, 4000, base) == []   # idle slots cannot make room
+
+
+def test_a_view_larger_than_every_slot_grows_within_the_budget_by_shrinking_idle_slots():
+    """Light requests spread over all slots, then heavy ones of the same class
+    that no slot holds: the slot that grows takes its room from idle slots
+    returned to their base size, and the slots stay within the budget."""
+    rng = random.Random(11)
+    light, heavy = (0, 200, 800), (0, 3000, 12000)
+    views = [light] * 12 + [heavy] * 3 + [light] * 6
+    g = serving.GROWTH
+    lcap = (int(g * 200), int(g * 800))
+    light_slot = _bytes(*lcap)
+    heavy_slot = _bytes(int(g * 3000), int(g * 12000))
+    budget = 4 * light_slot + heavy_slot          # six light slots fit; a heavy one needs two of them back
+    reqs, slots, forced, _, _ = _simulate(rng, 6, budget, views, lookahead=8, sizes=[lcap] * 6)
+    assert all(r.done for r in reqs)
+    assert forced == 0 and _simulate.shrinks > 0
+    assert sum(s.held for s in slots) <= budget
