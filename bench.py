@@ -495,55 +495,66 @@ def run_lodgs(args, rank: int, world: int):
     loss_h = torch.empty(len(order), dtype=torch.float32).pin_memory()
     copy_stream = torch.cuda.Stream()
     back_stream = torch.cuda.Stream()
-    used = {v: torch.cuda.Event() for v in set(order)}
-    done_ev = [torch.cuda.Event() for _ in order]
-    ready = [torch.cuda.Event() for _ in order]
 
-    def upload(i):
-        v = order[i]
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(used[v])
-            targets_d[v].copy_(targets_h[v], non_blocking=True)
-            ready[i].record(copy_stream)
+    def e2e_pass():
+        """One pass of the K steps end to end: (device ms, wall ms)."""
+        used = {v: torch.cuda.Event() for v in set(order)}
+        done_ev = [torch.cuda.Event() for _ in order]
+        ready = [torch.cuda.Event() for _ in order]
 
-    def read_loss(i):
-        v = order[i]
-        with torch.cuda.stream(back_stream):
-            back_stream.wait_event(done_ev[i])
-            loss_h[i:i + 1].copy_(loss_slots[v:v + 1], non_blocking=True)
+        def upload(i):
+            v = order[i]
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(used[v])
+                targets_d[v].copy_(targets_h[v], non_blocking=True)
+                ready[i].record(copy_stream)
 
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    copy_stream.wait_event(g0)
-    upload(0)
+        def read_loss(i):
+            v = order[i]
+            with torch.cuda.stream(back_stream):
+                back_stream.wait_event(done_ev[i])
+                loss_h[i:i + 1].copy_(loss_slots[v:v + 1], non_blocking=True)
 
-    def e2e_step(i, v):
-        for k in range(i + 1, min(i + 1 + n_streams, len(order))):    # keep the next uploads queued
-            if not up_issued[k]:
-                upload(k)
-                up_issued[k] = True
-        cs = torch.cuda.current_stream()
-        cs.wait_event(ready[i])
-        replay(v)
-        used[v].record(cs)
-        done_ev[i].record(cs)
-        read_loss(i)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        copy_stream.wait_event(g0)
+        upload(0)
+        up_issued = [False] * len(order)
+        up_issued[0] = True
 
-    up_issued = [False] * len(order)
-    up_issued[0] = True
-    run_steps(e2e_step)
-    stream.wait_stream(copy_stream)
-    stream.wait_stream(back_stream)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    e2e_wall = time.perf_counter() - t0
-    e2e_ms = g0.elapsed_time(g1)
-    if world > 1:
-        torch.distributed.barrier()
+        def e2e_step(i, v):
+            for k in range(i + 1, min(i + 1 + n_streams, len(order))):    # keep the next uploads queued
+                if not up_issued[k]:
+                    upload(k)
+                    up_issued[k] = True
+            cs = torch.cuda.current_stream()
+            cs.wait_event(ready[i])
+            replay(v)
+            used[v].record(cs)
+            done_ev[i].record(cs)
+            read_loss(i)
+
+        run_steps(e2e_step)
+        stream.wait_stream(copy_stream)
+        stream.wait_stream(back_stream)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if world > 1:
+            torch.distributed.barrier()
+        return g0.elapsed_time(g1), wall * 1e3
+
+    # three passes; the pass with the median end-to-end time (the larger of its
+    # device and wall times) is reported: one host stall in a ~10 ms pass
+    # would otherwise decide the number
+    passes = sorted((max(d, w), d, w) for d, w in (e2e_pass() for _ in range(3)))
+    _, e2e_ms, e2e_wall_ms = passes[1]
+    e2e_wall = e2e_wall_ms / 1e3
+    e2e_passes_ms = [round(x[0], 3) for x in passes]
 
     def maxr(x):
         return max_over_ranks(x, world)
@@ -555,7 +566,7 @@ def run_lodgs(args, rank: int, world: int):
     res = {
         "ms": ms, "fwd_ms": fwd_ms, "e2e_ms": max(e2e_ms, e2e_wall * 1e3), "views": total_views,
         "train_ms": train_ms, "host_submit_ms": host_submit_ms, "serial_ms": serial_ms, "streams": n_streams,
-        "fwd_inflight_ms": fwd_inflight, "select_batch_ms": select_batch_ms,
+        "fwd_inflight_ms": fwd_inflight, "select_batch_ms": select_batch_ms, "e2e_passes_ms": e2e_passes_ms,
         "stage_ms": stage_mean_live, "stage_ms_eager": stage_mean, "clocks": clk, "launches": launches,
         "stats_ok": stats_ok, "work": work,
         "fwd_stats": fwd_stats, "scene": {"n_nodes": scene.n_nodes, "n_upper": scene.n_upper, "n_spt": scene.n_spt,
@@ -1282,7 +1293,9 @@ def main():
         "e2e": {"value": res["views"] / (res["e2e_ms"] * 1e-3), "unit": "frames/s",
                 "h2d_bytes_per_step": res["h2d_bytes"], "d2h_bytes_per_step": res["d2h_bytes"],
                 "note": "each view's 8-bit RGB target (pinned host) uploaded on a copy stream while the "
-                        "previous view computes; the loss read back every step"},
+                        "previous view computes; the loss read back every step; the median of three passes "
+                        "over the K steps (each pass's time the larger of its device and wall times)",
+                "passes_ms": res["e2e_passes_ms"]},
         "gpu_launches": int(res["launches"]),
         "stages_ms": {k: round(v, 4) for k, v in res["stage_ms_eager"].items()},
         "stages_note": "stages_ms: the timed steps replayed eagerly with every stage timed; the roofline kernel "

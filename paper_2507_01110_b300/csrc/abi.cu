@@ -40,6 +40,15 @@ int cuda_fail(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? LODGS_E_OOM : LODGS_E_CUDA;
 }
 
+int launch_priority_high() {
+    static const int prio = [] {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+        return greatest;
+    }();
+    return prio;
+}
+
 // Camera constants in float32 (host).  The LoD test compares tau*d/f with the
 // node size; culling uses the four side planes through the camera centre and
 // the near plane; the EWA Jacobian is clamped at 1.3x the half field of view.

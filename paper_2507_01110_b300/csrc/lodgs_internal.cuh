@@ -182,19 +182,42 @@ void count_launches(int n);     // process-wide tally of this library's kernel l
 // once.)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+//
+// Launch priority (LODGS_PRIO_SPLIT): every kernel but the two blends is
+// launched at the device's greatest priority, so that when several views are
+// in flight the short memory- and latency-bound kernels of one view take SMs
+// as the issue-bound blend CTAs of another retire, instead of waiting behind
+// the blend's remaining waves.  The blends use pdl_launch_p with priority 0
+// (the default, lowest).  Measured with three views in flight: fwd+bwd step
+// 0.2836 -> 0.2790 ms, forward with two views in flight 0.140 -> 0.132 ms per
+// view; 0 launches everything at the default priority.
+#ifndef LODGS_PRIO_SPLIT
+#define LODGS_PRIO_SPLIT 1
+#endif
+int launch_priority_high();     // the device's greatest stream priority (cached)
+
 template <typename... KArgs, typename... Args>
-inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args) {
-    cudaLaunchAttribute attr[1];
+inline cudaError_t pdl_launch_p(int prio, void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                                Args &&...args) {
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributePriority;
+    attr[1].val.priority = prio;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = prio != 0 ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args) {
+    return pdl_launch_p(LODGS_PRIO_SPLIT ? launch_priority_high() : 0, kern, grid, block, st,
+                        std::forward<Args>(args)...);
 }
 bool fault_hit(int site);       // an armed injected fault at `site` fires (host side only)
 int cuda_fail(cudaError_t e, const char *what);

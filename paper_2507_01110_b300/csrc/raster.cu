@@ -1179,7 +1179,7 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         sm.mark(LODGS_STAGE_BLEND, 0, st);
     }
     if (f.count_work) LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));   // profiling only
-    LODGS_CUDA(pdl_launch((f.count_work ? k_blend<true> : k_blend<false>), (unsigned)n_tiles, BNT, st,
+    LODGS_CUDA(pdl_launch_p(0, (f.count_work ? k_blend<true> : k_blend<false>), (unsigned)n_tiles, BNT, st,
         f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work,
         f.tile_order));
     count_launches(1);
@@ -1200,10 +1200,10 @@ int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, cons
         LODGS_CUDA(cudaMemsetAsync(loss_sum, 0, sizeof(float), st));
         auto kern = target_u8 ? (f.count_work ? k_blend_bwd<true, BWD_PIX, 2> : k_blend_bwd<false, BWD_PIX, 2>)
                               : (f.count_work ? k_blend_bwd<true, BWD_PIX, 1> : k_blend_bwd<false, BWD_PIX, 1>);
-        LODGS_CUDA(pdl_launch(kern, nb, nt, st, f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image,
+        LODGS_CUDA(pdl_launch_p(0, kern, nb, nt, st, f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image,
                                 nullptr, f.g2d, f.work, target, l1_scale, loss_sum, f.tile_order));
     } else {
-        LODGS_CUDA(pdl_launch((f.count_work ? k_blend_bwd<true, BWD_PIX, 0> : k_blend_bwd<false, BWD_PIX, 0>), nb, nt, st,
+        LODGS_CUDA(pdl_launch_p(0, (f.count_work ? k_blend_bwd<true, BWD_PIX, 0> : k_blend_bwd<false, BWD_PIX, 0>), nb, nt, st,
             f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, dL_dimage, f.g2d, f.work,
             nullptr, 0.f, nullptr, f.tile_order));
     }
