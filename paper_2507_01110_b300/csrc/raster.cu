@@ -729,8 +729,61 @@ __device__ __forceinline__ int warp_list(const uint8_t *s_m, int n, uint32_t wma
     return len;
 }
 
-// COUNT: tally the work counters (profiling launches only).
-template <bool COUNT>
+// Live-pixel box: once some of a warp's pixels have stopped, the warp builds
+// its next lists against the box of the pixel centres still live (centre cx,
+// cy; half spans hx, hy) instead of its whole block.  A Gaussian whose support
+// box misses it reaches no live pixel (the argument of the block test), so the
+// pixels meet exactly the Gaussians they met before: only list entries that
+// would have been walked without a hit go.  A long tile list whose block keeps
+// one unsaturated pixel then no longer costs a walk of the whole list.  The
+// blends take this form (BOX) for frames on the global ordering, the ones with
+// long tile lists; elsewhere the lists end before the box would pay for the
+// registers it takes.
+__device__ __forceinline__ void live_box(float xc, const float *yc, const bool *live, int np, int lane,
+                                         float4 *box) {
+    float x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (int k = 0; k < np; ++k) {
+        if (live[k]) {
+            x0 = fminf(x0, xc); x1 = fmaxf(x1, xc);
+            y0 = fminf(y0, yc[k]); y1 = fmaxf(y1, yc[k]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    // pixel centres are k + 0.5: the centre and half spans are exact
+    if (x0 <= x1 && lane == 0) *box = make_float4(0.5f * (x0 + x1), 0.5f * (y0 + y1), 0.5f * (x1 - x0), 0.5f * (y1 - y0));
+    __syncwarp();
+}
+
+// warp_list restricted to the entries whose support box (half extents r) also
+// reaches the live box (centre box.x, box.y; half spans box.z, box.w).
+__device__ __forceinline__ int warp_list_box(const uint8_t *s_m, const float4 *s_a, const float2 *s_r, int n,
+                                             uint32_t wmask, const float4 &box, int lane, uint8_t *list) {
+    const float cx = box.x, cy = box.y, hx = box.z, hy = box.w;
+    int len = 0;
+    for (int q0 = 0; q0 < n; q0 += 32) {
+        const int q = q0 + lane;
+        bool mine = false;
+        if (q < n && (s_m[q] & wmask)) {
+            const float4 a = s_a[q];
+            const float2 r = s_r[q];
+            mine = !(fabsf(__fsub_rn(a.x, cx)) > __fadd_rn(r.x, hx)) && !(fabsf(__fsub_rn(a.y, cy)) > __fadd_rn(r.y, hy));
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, mine);
+        if (mine) list[len + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)q;
+        len += __popc(bal);
+    }
+    __syncwarp();
+    return len;
+}
+
+// COUNT: tally the work counters (profiling launches only).  BOX: live-box lists.
+template <bool COUNT, bool BOX>
 __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
     k_blend(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval, const float4 *__restrict__ sp_a,
             const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c, const uint32_t *__restrict__ cnt, int W,
@@ -739,6 +792,8 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
     pdl_wait();
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
+    __shared__ float2 s_r[BOX ? BATCH : 1];
+    __shared__ float4 s_box[BOX ? NWARP : 1];
     __shared__ uint8_t s_m[BATCH];
     __shared__ uint8_t s_list[NWARP][BATCH];
     if (cnt[C_STATUS] & ST_CAPACITY) return;
@@ -758,6 +813,7 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
         done &= !live[k];
     }
     uint32_t n_eval = 0, n_blend = 0;
+    bool whole = true, shrunk = false;      // BOX: lists against the block until a pixel stops
     const uint2 rg = ranges[tile];
     for (uint32_t base = rg.x; base < rg.y; base += BATCH) {
         if (__syncthreads_count(done) == BNT) break;
@@ -768,11 +824,23 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
             s_a[q] = a;
             s_b[q] = sp_b[g];
             s_c[q] = c.x;
+            if constexpr (BOX) s_r[q] = make_float2(c.y, c.z);
             s_m[q] = (uint8_t)block_mask(a, c, tx0, ty0);
         }
         __syncthreads();
         if (__all_sync(0xffffffffu, done)) continue;
-        const int len = warp_list(s_m, n, 1u << bp.w, lane, s_list[bp.w]);
+        int len;
+        if constexpr (BOX) {
+            if (shrunk) {
+                live_box(bp.xc, yc, live, PIX, lane, &s_box[bp.w]);
+                whole = false;
+                shrunk = false;
+            }
+            len = whole ? warp_list(s_m, n, 1u << bp.w, lane, s_list[bp.w])
+                        : warp_list_box(s_m, s_a, s_r, n, 1u << bp.w, s_box[bp.w], lane, s_list[bp.w]);
+        } else {
+            len = warp_list(s_m, n, 1u << bp.w, lane, s_list[bp.w]);
+        }
         for (int i = 0; i < len; ++i) {
             const int j = s_list[bp.w][i];
             const float4 a = s_a[j];
@@ -810,6 +878,7 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
                 live[0] = live[0] && !s0;
                 live[1] = live[1] && !s1;
                 if (__any_sync(0xffffffffu, s0 || s1)) {
+                    if (BOX) shrunk = true;
                     done = !live[0] && !live[1];
                     if (__all_sync(0xffffffffu, done)) break;
                 }
@@ -841,6 +910,7 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
                 died |= stop;
             }
             if (__any_sync(0xffffffffu, died)) {
+                if (BOX) shrunk = true;
                 done = true;
 #pragma unroll
                 for (int k = 0; k < PIX; ++k) done &= !live[k];
@@ -879,7 +949,7 @@ __global__ void __launch_bounds__(BNT, LODGS_FWD_MINB)
 // L1 loss's gradient, l1_scale * sign(C - target), and the block adds its
 // sum |C - target| to *loss_sum (the training loss folded into the backward:
 // no separate pass over the image, no dL/dC buffer).  0: dL/dC from dL_dimg.
-template <bool COUNT, int BP, int L1>
+template <bool COUNT, int BP, int L1, bool BOX>
 __global__ void BWD_BOUNDS(TILE_PIX / BP)
     k_blend_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
                 const float4 *__restrict__ sp_a, const float4 *__restrict__ sp_b, const float4 *__restrict__ sp_c,
@@ -891,6 +961,8 @@ __global__ void BWD_BOUNDS(TILE_PIX / BP)
     constexpr int NT = TILE_PIX / BP, NW = NT / 32;
     __shared__ float4 s_a[BATCH], s_b[BATCH];
     __shared__ float s_c[BATCH];
+    __shared__ float2 s_r[BOX ? BATCH : 1];
+    __shared__ float4 s_box[BOX ? NW : 1];
     __shared__ uint32_t s_g[BATCH];
     __shared__ float s_grad[BATCH][9];
     __shared__ uint8_t s_m[BATCH];
@@ -957,6 +1029,7 @@ __global__ void BWD_BOUNDS(TILE_PIX / BP)
     const float2 nyc2 = make_float2(-yc[0], -yc[BP > 1 ? 1 : 0]);
     const float2 G02 = make_float2(G[0][0], G[BP > 1 ? 1 : 0][0]), G12 = make_float2(G[0][1], G[BP > 1 ? 1 : 0][1]);
     const float2 G22 = make_float2(G[0][2], G[BP > 1 ? 1 : 0][2]);
+    bool whole = true, shrunk = false;      // BOX: lists against the blocks until a pixel stops
     const uint2 rg = ranges[tile];
     for (uint32_t base = rg.x; base < rg.y; base += BATCH) {
         if (__syncthreads_count(done) == NT) break;
@@ -968,13 +1041,25 @@ __global__ void BWD_BOUNDS(TILE_PIX / BP)
             s_a[q] = a;
             s_b[q] = sp_b[g];
             s_c[q] = c.x;
+            if constexpr (BOX) s_r[q] = make_float2(c.y, c.z);
             s_m[q] = (uint8_t)block_mask(a, c, tx0, ty0);
 #pragma unroll
             for (int v = 0; v < 9; ++v) s_grad[q][v] = 0.f;
         }
         __syncthreads();
         if (!__all_sync(0xffffffffu, done)) {
-            const int len = warp_list(s_m, n, wmask, lane, s_list[bp.w]);
+            int len;
+            if constexpr (BOX) {
+                if (shrunk) {
+                    live_box(bp.xc, yc, live, BP, lane, &s_box[bp.w]);
+                    whole = false;
+                    shrunk = false;
+                }
+                len = whole ? warp_list(s_m, n, wmask, lane, s_list[bp.w])
+                            : warp_list_box(s_m, s_a, s_r, n, wmask, s_box[bp.w], lane, s_list[bp.w]);
+            } else {
+                len = warp_list(s_m, n, wmask, lane, s_list[bp.w]);
+            }
             for (int i = 0; i < len; ++i) {
                 const int j = s_list[bp.w][i];
                 const float4 a = s_a[j];
@@ -1022,6 +1107,7 @@ __global__ void BWD_BOUNDS(TILE_PIX / BP)
                                    gw2.x + gw2.y};
                     warp_sum9_to_smem(gv, lane, s_grad[j]);
                     if (__any_sync(0xffffffffu, s0 || s1)) {
+                        if (BOX) shrunk = true;
                         done = !live[0] && !live[1];
                         if (__all_sync(0xffffffffu, done)) break;
                     }
@@ -1079,6 +1165,7 @@ __global__ void BWD_BOUNDS(TILE_PIX / BP)
                 float gv[9] = {dq0, q1, dx * dq0, dx * q1, q2, q0, gr, gg, gb};
                 warp_sum9_to_smem(gv, lane, s_grad[j]);
                 if (__any_sync(0xffffffffu, died)) {
+                    if (BOX) shrunk = true;
                     done = true;
 #pragma unroll
                     for (int k = 0; k < BP; ++k) done &= !live[k];
@@ -1179,7 +1266,9 @@ int launch_raster(const CamK &k, FrameBufs &f, float *image, cudaStream_t st, co
         sm.mark(LODGS_STAGE_BLEND, 0, st);
     }
     if (f.count_work) LODGS_CUDA(cudaMemsetAsync(f.work, 0, 4 * sizeof(unsigned long long), st));   // profiling only
-    LODGS_CUDA(pdl_launch_p(0, (f.count_work ? k_blend<true> : k_blend<false>), (unsigned)n_tiles, BNT, st,
+    const bool box = f.order != nullptr;     // global ordering: a frame with long tile lists
+    LODGS_CUDA(pdl_launch_p(0, (f.count_work ? (box ? k_blend<true, true> : k_blend<true, false>)
+                                             : (box ? k_blend<false, true> : k_blend<false, false>)), (unsigned)n_tiles, BNT, st,
         f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, f.d_view, image, f.work,
         f.tile_order));
     count_launches(1);
@@ -1196,14 +1285,18 @@ int launch_raster_backward(const CamK &k, FrameBufs &f, const float *image, cons
         LODGS_CUDA(cudaMemsetAsync(f.g2d, 0, f.cap_sel * G2D_STRIDE * sizeof(float), st));
     if (f.count_work) LODGS_CUDA(cudaMemsetAsync(f.work + 2, 0, 2 * sizeof(unsigned long long), st));
     const unsigned nb = (unsigned)n_tiles, nt = TILE_PIX / BWD_PIX;
+    const bool box = f.order != nullptr;     // the render's global ordering: long tile lists
     if (target) {
         LODGS_CUDA(cudaMemsetAsync(loss_sum, 0, sizeof(float), st));
-        auto kern = target_u8 ? (f.count_work ? k_blend_bwd<true, BWD_PIX, 2> : k_blend_bwd<false, BWD_PIX, 2>)
-                              : (f.count_work ? k_blend_bwd<true, BWD_PIX, 1> : k_blend_bwd<false, BWD_PIX, 1>);
+        auto kern = box ? (target_u8 ? (f.count_work ? k_blend_bwd<true, BWD_PIX, 2, true> : k_blend_bwd<false, BWD_PIX, 2, true>)
+                                     : (f.count_work ? k_blend_bwd<true, BWD_PIX, 1, true> : k_blend_bwd<false, BWD_PIX, 1, true>))
+                        : (target_u8 ? (f.count_work ? k_blend_bwd<true, BWD_PIX, 2, false> : k_blend_bwd<false, BWD_PIX, 2, false>)
+                                     : (f.count_work ? k_blend_bwd<true, BWD_PIX, 1, false> : k_blend_bwd<false, BWD_PIX, 1, false>));
         LODGS_CUDA(pdl_launch_p(0, kern, nb, nt, st, f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image,
                                 nullptr, f.g2d, f.work, target, l1_scale, loss_sum, f.tile_order));
     } else {
-        LODGS_CUDA(pdl_launch_p(0, (f.count_work ? k_blend_bwd<true, BWD_PIX, 0> : k_blend_bwd<false, BWD_PIX, 0>), nb, nt, st,
+        LODGS_CUDA(pdl_launch_p(0, (box ? (f.count_work ? k_blend_bwd<true, BWD_PIX, 0, true> : k_blend_bwd<false, BWD_PIX, 0, true>)
+                                        : (f.count_work ? k_blend_bwd<true, BWD_PIX, 0, false> : k_blend_bwd<false, BWD_PIX, 0, false>)), nb, nt, st,
             f.ranges, f.sorted_pval, f.sp_a, f.sp_b, f.sp_c, f.cnt, k.W, k.H, k.TX, image, dL_dimage, f.g2d, f.work,
             nullptr, 0.f, nullptr, f.tile_order));
     }

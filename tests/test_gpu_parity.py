@@ -261,6 +261,30 @@ def test_long_tile_lists_match_oracle(api, n, ordering):
     assert lens.max() >= {200: 150, 1000: 700, 6000: 4000, 20000: 12000}[n], lens.max()
 
 
+@pytest.mark.parametrize("ordering", [1, 2])
+@pytest.mark.parametrize("n", [6000, 20000])
+def test_long_tile_backward_matches_oracle(api, n, ordering):
+    """Tiles of thousands of pairs whose pixels stop at different depths.  On
+    the global ordering (2) the blends build their later lists against the box
+    of the pixels still live, which must leave the image and every gradient as
+    the oracle computes them, as the block lists of the per-tile ordering (1)
+    do."""
+    leaves = synth.leaves_uniform_cube(n, seed=900 + n, half_extent=0.05, degree=0, log_scale_mu=-6.0)
+    cam = synth.camera_look([0.013, -0.021, -10.0], [0, 0, 1], [1, 0, 0], 64, 48, tau=0.01)
+    kappa = float(cam.fx / cam.tau)
+    sc_o = oracle.build_scene(leaves, 0, 1e-9, kappa)
+    sc_g = api.build_hierarchy(leaves, 0, 1e-9, kappa)
+    bg = (0.2, 0.3, 0.1)
+    fr = api.Frame(sc_g)
+    fr.set_ordering(ordering)
+    fr, out, img = _compare_render(api, sc_o, sc_g, cam, bg=bg, fr=fr)
+    assert np.diff(out["pairs"]["tile_start"]).max() > 1024
+    w = np.random.default_rng(n).uniform(-1, 1, img.shape).astype(np.float32)
+    grad = api.render_backward(sc_g, fr, torch.from_numpy(w).cuda()).cpu().numpy()
+    ref = oracle.render_backward(sc_o, cam, out, w.astype(np.float64), bg=bg)["g_rec"]
+    _check_grads(grad[: len(out["sel"])], ref, 0)
+
+
 def _orderings_agree(api, sc, cam, min_pairs):
     res = []
     for ordering in (1, 2):
