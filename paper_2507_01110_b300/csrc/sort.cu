@@ -20,6 +20,7 @@ constexpr int ST_THREADS = 256;                 // 8 warps
 constexpr int ST_WARPS = ST_THREADS / 32;
 constexpr int ST_ITEMS = 8;
 constexpr int ST_TILE = ST_THREADS * ST_ITEMS;  // 2048 keys per tile
+static_assert(RADIX == ST_THREADS, "one thread per digit in the digit scans");
 
 __device__ __forceinline__ void chunk_range(uint32_t n, uint32_t &begin, uint32_t &end) {
     uint32_t G = gridDim.x;
@@ -92,7 +93,10 @@ __global__ void __launch_bounds__(ST_THREADS) k_radix_downsweep(
     pdl_wait();
     __shared__ uint32_t s_off[RADIX];
     __shared__ uint32_t s_tot[RADIX];
+    __shared__ uint32_t s_start[RADIX];           // the tile's digit runs: exclusive scan of s_tot
+    __shared__ uint32_t s_sum[ST_WARPS];
     __shared__ uint32_t s_w[ST_WARPS][RADIX];
+    __shared__ uint32_t s_k[ST_TILE], s_v[ST_TILE];   // the tile, stably ordered by digit
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {   // digit bases: exclusive scan of the digit totals (RADIX == ST_THREADS)
         uint32_t t = totals[tid];
@@ -143,15 +147,42 @@ __global__ void __launch_bounds__(ST_THREADS) k_radix_downsweep(
             s_tot[d] = run;
         }
         __syncthreads();
+        {   // where each digit's run starts in the tile (RADIX == ST_THREADS)
+            const uint32_t c = s_tot[tid];
+            uint32_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_sum[warp] = x;
+            __syncthreads();
+            uint32_t wb = 0;
+            for (int w = 0; w < warp; ++w) wb += s_sum[w];
+            s_start[tid] = wb + x - c;
+        }
+        __syncthreads();
+        // stage the tile in shared memory in (digit, input order) order, then
+        // write each digit's run out contiguously: consecutive threads write
+        // consecutive addresses instead of one scattered word per key
 #pragma unroll
         for (int k = 0; k < ST_ITEMS; ++k) {
             uint32_t idx = t0 + warp * (32 * ST_ITEMS) + k * 32 + lane;
             if (idx < end) {
                 uint32_t d = (key[k] >> shift) & mask;
-                uint32_t pos = s_off[d] + s_w[warp][d] + rank[k];
-                keys_out[pos] = key[k];
-                vals_out[pos] = val[k];
+                uint32_t lp = s_start[d] + s_w[warp][d] + rank[k];
+                s_k[lp] = key[k];
+                s_v[lp] = val[k];
             }
+        }
+        __syncthreads();
+        const uint32_t nt = end - t0 < (uint32_t)ST_TILE ? end - t0 : (uint32_t)ST_TILE;
+        for (uint32_t i = tid; i < nt; i += ST_THREADS) {
+            const uint32_t kk = s_k[i];
+            const uint32_t d = (kk >> shift) & mask;
+            const uint32_t pos = s_off[d] + (i - s_start[d]);
+            keys_out[pos] = kk;
+            vals_out[pos] = s_v[i];
         }
         __syncthreads();
         for (int d = tid; d < RADIX; d += ST_THREADS) s_off[d] += s_tot[d];
