@@ -1164,6 +1164,10 @@ def run_train_batch(args) -> dict:
             rows, _g = step(batched)
         torch.cuda.synchronize()
         out[batched] = (time.perf_counter() - t1) / reps
+    torch.cuda.nvtx.range_push("train_batch_step")       # one more step, for profilers
+    step(True)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     dt = out[True]
     return {"workload": f"{args.train_leaves:,}-leaf SH3 city (2 km), batch of 8 views (4 aerial, 4 street) at "
                         "1600x1200: one batched LoD selection of the 8 views, then render + mean-L1 + backward "
