@@ -51,6 +51,7 @@ import torch
 from . import _lib, api
 
 GROWTH = 1.25      # a frame buffer that overflows grows to 1.25 x the count that overflowed it
+GROWTH_MARGIN = 1.1   # a growth can take more than GROWTH x the needed bytes (buffers grow separately)
 
 
 @dataclass
@@ -151,6 +152,7 @@ class RenderServer:
         self.batch_select = batch_select  # one batched selection for the requests admitted together
         self.front = torch.cuda.Stream()  # where the batched selections run
         self.batches = self.batched_views = self.shrinks = 0
+        self.peak = 0                     # the largest workspace the slots held in run(), growths included
         self.need: dict = {}              # request class -> largest workspace bytes it needed
         self.rep: dict = {}               # request class -> the camera of that largest need
         self._ref = None                  # event at the start of run(): device times are taken from it
@@ -259,12 +261,8 @@ class RenderServer:
             req.tried.add(id(slot))
             need = self.charge(req.camera)
             if overflow_action(needed, need, slot, self.slots, req.tried, self.budget) == "retry":
-                grown = self.held_bytes() - slot.held + int(GROWTH * needed)
-                for idle in shrink_plan(grown, slot, self.slots, self.budget, self.base):
-                    idle.frame.close()               # back to a fresh frame: room for this growth
-                    idle.frame = api.Frame(self.scene)
-                    idle.held = idle.frame.memory()[0]
-                    self.shrinks += 1
+                grown = self.held_bytes() - slot.held + int(GROWTH * GROWTH_MARGIN * needed)
+                self._shrink(shrink_plan(grown, slot, self.slots, self.budget, self.base))
                 req.retries += 1
                 if not self._launch(slot, req):      # growing the workspace failed: give up on it
                     slot.req = None
@@ -284,8 +282,19 @@ class RenderServer:
         if self._ref is not None:                    # the request's interval on the device
             req.dev_ms = (self._ref.elapsed_time(req.ev_start), self._ref.elapsed_time(slot.done))
         self._learn(slot, cam)
+        self.peak = max(self.peak, self.held_bytes())
+        # a growth that took more than its estimate: idle slots make the room back
+        self._shrink(shrink_plan(self.held_bytes(), slot, self.slots, self.budget, self.base))
         slot.req = None
         return "done"
+
+    def _shrink(self, idle_slots) -> None:
+        """Return slots (idle) to a fresh frame's workspace."""
+        for idle in idle_slots:
+            idle.frame.close()
+            idle.frame = api.Frame(self.scene)
+            idle.held = idle.frame.memory()[0]
+            self.shrinks += 1
 
     def warm(self, cameras) -> None:
         """Learn the classes' workspace needs on representative cameras, then
@@ -331,6 +340,7 @@ class RenderServer:
         done = 0
         inflight_max = 0
         held_max = self.held_bytes()
+        self.peak = held_max
         self.batches = self.batched_views = self.shrinks = 0
         grown_past = 0                    # retries that grew the slots past the budget (no slot could hold the view)
         torch.cuda.synchronize()
@@ -352,7 +362,7 @@ class RenderServer:
                         done += 1
                     elif out == "requeue":
                         pending.appendleft(req)
-            held = self.held_bytes()
+            held = max(self.held_bytes(), self.peak)   # peak: before any shrink that followed a growth
             if held > self.budget and held > held_max:
                 grown_past += 1
             held_max = max(held_max, held)

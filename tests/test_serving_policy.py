@@ -75,6 +75,9 @@ def _simulate(rng, n_slots, budget, views, lookahead, sizes=None):
             need[r.cls] = max(need.get(r.cls, 0), vb)
             r.done = True
             done += 1
+            for idle in serving.shrink_plan(sum(x.held for x in slots), s, slots, budget, base):
+                idle.cap_sel, idle.cap_pairs, idle.held = 64, 256, base    # a growth past its estimate
+                shrinks[0] += 1
         free = [s for s in slots if s.req is None]
         q = 0
         while q < min(len(pending), 1 + lookahead) and free:
