@@ -434,6 +434,9 @@ int lodgs_render_backward(lodgs_scene *scene, lodgs_frame *frame, const float *r
  * Implementation Details).  Deterministic: rows of a node are summed in view
  * order, without atomics.
  *   frames[v], grads[v]  the n_views rendered frames and their device gradient rows
+ *              (NULL allowed for a view that selected nothing); rows of at
+ *              most 64 floats (SH degree <= 3), read as float2 when every
+ *              array is 8-byte aligned
  *   out_rows   device uint32, capacity >= sum of the views' selections: union rows, ascending
  *   out_grads  device float32, capacity x stride: the summed rows, in out_rows order
  *   d_count    device uint32: the union size
