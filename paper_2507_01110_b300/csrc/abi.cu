@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -47,6 +49,49 @@ int launch_priority_high() {
         return greatest;
     }();
     return prio;
+}
+
+static int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    return dev;
+}
+
+int device_sms() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 148;
+    }
+    cache.emplace(dev, sms);
+    return sms;
+}
+
+int resident_blocks(const void *kern, int threads) {
+    static std::mutex mu;
+    static std::map<std::pair<int, std::pair<const void *, int>>, int> cache;
+    const int dev = current_device();
+    const int sms = device_sms();
+    const auto key = std::make_pair(dev, std::make_pair(kern, threads));
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess || per_sm <= 0) {
+        cudaGetLastError();   // a grid of one block per SM is still correct
+        per_sm = 1;
+    }
+    cache.emplace(key, sms * per_sm);
+    return sms * per_sm;
 }
 
 // Camera constants in float32 (host).  The LoD test compares tau*d/f with the

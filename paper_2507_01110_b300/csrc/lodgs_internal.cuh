@@ -196,6 +196,19 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 #endif
 int launch_priority_high();     // the device's greatest stream priority (cached)
 
+// Blocks of `kern` (with `threads` threads and its static shared memory) that
+// are resident on the current device at once: the SM count times the
+// occupancy calculator's blocks per SM, cached per kernel and device.  Kernels
+// whose blocks split the work evenly (grid-stride loops, even chunks) are
+// launched with a whole number of such waves: a partial last wave would run a
+// few blocks per SM while the rest of the device idles.
+int resident_blocks(const void *kern, int threads);
+int device_sms();   // SM count of the current device (cached per device)
+template <typename... KArgs>
+inline int resident_grid(void (*kern)(KArgs...), int threads, int waves = 1) {
+    return waves * resident_blocks(reinterpret_cast<const void *>(kern), threads);
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t pdl_launch_p(int prio, void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
                                 Args &&...args) {

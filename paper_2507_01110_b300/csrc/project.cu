@@ -13,7 +13,11 @@ namespace lodgs {
 namespace {
 
 constexpr int PB = 128;
-constexpr int PROJ_GRID = 148 * 8;
+// Grids: the projection runs one wave of resident blocks (resident_grid).  A
+// fixed 8 blocks per SM was 1.14 waves at its 7 resident blocks per SM (70
+// registers), the last 148 blocks almost alone on their SMs.  The backward (4
+// resident blocks per SM at 128 registers) keeps 8 per SM: two full waves.
+constexpr int PROJ_BWD_GRID = 148 * 8;
 
 // Real spherical harmonics of degrees 1..3 (orthonormal, no Condon-Shortley
 // phase), as polynomials of the unit direction (x, y, z); index l^2-1+(m+l).
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(PB) k_project_bwd(const float *__restrict__ ro
 
 int launch_project(const lodgs_scene *sc, const float *rows, FrameBufs &f, cudaStream_t st) {
 #define LAUNCH_PROJ(D)                                                                                     \
-    LODGS_CUDA(pdl_launch(k_project<D>, PROJ_GRID, PB, st, rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.d_view, f.cnt, f.cap_sel, f.sp_a, \
+    LODGS_CUDA(pdl_launch(k_project<D>, resident_grid(k_project<D>, PB), PB, st, rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.d_view, f.cnt, f.cap_sel, f.sp_a, \
                                            f.sp_b, f.sp_c, f.dkey, f.dval, f.rect, f.ntiles, \
                                            reinterpret_cast<float4 *>(f.g2d)))
     switch (sc->sh_degree) {
@@ -487,7 +491,7 @@ int launch_project_backward(const lodgs_scene *sc, const float *rows, FrameBufs 
     }
     const uint32_t cap = (uint32_t)std::min<int64_t>(std::max<int64_t>(grad_capacity, 0), UINT32_MAX);
 #define LAUNCH_PBWD(D)                                                                                     \
-    LODGS_CUDA(pdl_launch(k_project_bwd<D>, PROJ_GRID, PB, st, rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.sel_rows, f.d_view, \
+    LODGS_CUDA(pdl_launch(k_project_bwd<D>, PROJ_BWD_GRID, PB, st, rows, sc->stride, f.use_src ? f.sel_src : f.sel_rows, f.sel_rows, f.d_view, \
                                                f.cnt, f.ntiles, f.g2d, grad_rows, dense, cap))
     switch (sc->sh_degree) {
         case 0: LAUNCH_PBWD(0); break;
