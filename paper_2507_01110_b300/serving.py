@@ -16,12 +16,15 @@ largest workspace a request of the class needed, then sizes the slots within
 the budget: the first slot for the largest class, each next one for the
 largest class that still leaves the remaining slots their base size.  A
 request is admitted to a free slot whose workspace already holds its class's
-need (the one with the least to spare); if every slot that could hold it is
-busy it waits, and up to `lookahead` later requests that fit a free slot may
-start before it.  A request whose view overflows its slot (another camera of
-its class can need more than the warm-up saw, or one buffer of a slot can be
-short while its total is not) raises its class's need; it is rendered again on
-the same slot, which grows, if the budget still holds the grown slot or no slot
+need (the one with the least to spare); if none does but the budget has room
+to grow a free slot to that need, the largest such slot grows (before the
+launch, to the class's largest rendered counts) and takes it; otherwise, if
+every slot that could hold it is busy it waits, and up to `lookahead` later
+requests that fit a free slot may start before it.  A request whose view
+overflows its slot (another camera of its class can need more than the
+warm-up saw, or one buffer of a slot can be short while its total is not)
+raises its class's need; it is rendered again on the same slot, which grows,
+if the budget still holds the grown slot or no slot
 it has not yet overflowed could hold it; otherwise the queued growth is
 cancelled (lodgs_frame_reserve) and the request goes back to the head of the
 queue to wait for one of those slots.  A request therefore goes back to the
@@ -76,12 +79,16 @@ def request_class(camera) -> tuple:
     return (int(camera.width), int(camera.height), round(float(camera.tau), 6))
 
 
-def pick_slot(need, tried, free, slots, can_wait: bool):
+def pick_slot(need, tried, free, slots, can_wait: bool, room=None):
     """The free slot a queued request takes, or None (it waits).  need: its
     class's workspace bytes (None: class not seen yet); tried: the slots it has
     overflowed; free: the free slots; slots: all of them; can_wait: whether it
     may wait for a busy slot (the head of the queue may not wait when nothing is
-    in flight).  Slots are anything with a `held` byte count."""
+    in flight); room: the bytes the budget has left (None: no slot is grown at
+    admission).  When no free slot holds the class but one can grow to it
+    within `room`, the request takes the largest such slot (the caller grows
+    it) instead of queueing behind a busy slot that holds it.  Slots are
+    anything with a `held` byte count."""
     if need is None:                                 # a class not seen yet: alone, on the largest slot
         if can_wait:
             return None
@@ -90,6 +97,10 @@ def pick_slot(need, tried, free, slots, can_wait: bool):
     fits = [s for s in usable if s.held >= GROWTH * need] or [s for s in usable if s.held >= need]
     if fits:
         return min(fits, key=lambda s: s.held)
+    if room is not None:
+        growable = [s for s in usable if GROWTH * GROWTH_MARGIN * need - s.held <= room]
+        if growable:
+            return max(growable, key=lambda s: s.held)
     if can_wait and any(s.held >= need and id(s) not in tried for s in slots):
         return None                                  # a slot that holds it is busy: wait for it
     if can_wait:
@@ -155,6 +166,8 @@ class RenderServer:
         self.peak = 0                     # the largest workspace the slots held in run(), growths included
         self.need: dict = {}              # request class -> largest workspace bytes it needed
         self.rep: dict = {}               # request class -> the camera of that largest need
+        self.counts: dict = {}            # request class -> largest (selected, rectangle pairs) rendered
+        self.grown = 0                    # slots grown at admission (pick_slot with room)
         self._ref = None                  # event at the start of run(): device times are taken from it
         while len(self.slots) > 1 and self.held_bytes() > self.budget:
             self.slots.pop()              # the budget holds fewer slots at their base size (at least one)
@@ -170,14 +183,34 @@ class RenderServer:
         """Device workspace the slots hold together."""
         return int(sum(s.held for s in self.slots))
 
-    def _learn(self, slot: _Slot, camera) -> int:
+    def _learn(self, slot: _Slot, camera, rendered: bool = False) -> int:
         held, needed = slot.frame.memory()
         slot.held = held
         k = request_class(camera)
         if needed > self.need.get(k, -1):
             self.need[k] = needed
             self.rep[k] = camera
+        if rendered:                      # a completed view: its counts bound the class's buffers
+            st = slot.frame.stats()
+            ns, npairs = self.counts.get(k, (0, 0))
+            self.counts[k] = (max(ns, int(st["n_selected"])), max(npairs, int(st["n_pairs"])))
         return needed
+
+    def _grow(self, slot: _Slot, camera) -> None:
+        """Grow a free slot's workspace for a request's class before its
+        launch (admission within the budget's room): GROWTH x the largest
+        selection and rectangle pair counts the class rendered (the rectangle
+        pairs bound the stored ones).  A class known only from an overflow is
+        left to the overflow path; a failed growth leaves the slot as it was."""
+        counts = self.counts.get(request_class(camera))
+        if counts is None:
+            return
+        try:
+            slot.frame.reserve(int(GROWTH * counts[0]), int(GROWTH * counts[1]))
+            self.grown += 1
+        except _lib.LodgsError:
+            pass
+        slot.held = slot.frame.memory()[0]
 
     def _render(self, slot: _Slot, cam) -> None:
         img = slot.image[: cam.height * cam.width * 3].view(cam.height, cam.width, 3)
@@ -281,7 +314,7 @@ class RenderServer:
         req.status = "done"
         if self._ref is not None:                    # the request's interval on the device
             req.dev_ms = (self._ref.elapsed_time(req.ev_start), self._ref.elapsed_time(slot.done))
-        self._learn(slot, cam)
+        self._learn(slot, cam, rendered=True)
         self.peak = max(self.peak, self.held_bytes())
         # a growth that took more than its estimate: idle slots make the room back
         self._shrink(shrink_plan(self.held_bytes(), slot, self.slots, self.budget, self.base))
@@ -303,7 +336,7 @@ class RenderServer:
         probe = self.slots[0]
         for cam in cameras:
             self._render(probe, cam)
-            self._learn(probe, cam)
+            self._learn(probe, cam, rendered=True)
         remaining = self.budget - probe.held
         base = min(s.held for s in self.slots[1:]) if len(self.slots) > 1 else 0
         kept = [probe]
@@ -341,7 +374,7 @@ class RenderServer:
         inflight_max = 0
         held_max = self.held_bytes()
         self.peak = held_max
-        self.batches = self.batched_views = self.shrinks = 0
+        self.batches = self.batched_views = self.shrinks = self.grown = 0
         grown_past = 0                    # retries that grew the slots past the budget (no slot could hold the view)
         torch.cuda.synchronize()
         self._ref = torch.cuda.Event(enable_timing=True)
@@ -378,10 +411,14 @@ class RenderServer:
             while q < min(len(pending), 1 + self.lookahead) and free:
                 req = pending[q]
                 busy = len(free) < len(self.slots)
-                slot = pick_slot(self.charge(req.camera), req.tried, free, self.slots, can_wait=busy or q > 0)
+                need = self.charge(req.camera)
+                slot = pick_slot(need, req.tried, free, self.slots, can_wait=busy or q > 0,
+                                 room=self.budget - self.held_bytes())
                 if slot is None:
                     q += 1
                     continue
+                if need is not None and slot.held < need:
+                    self._grow(slot, req.camera)        # a free slot grown within the budget's room
                 del pending[q]
                 free.remove(slot)
                 req.t_admit = time.perf_counter() - t0
@@ -399,15 +436,24 @@ class RenderServer:
         # latency from arrival (realtime) or from being queued (batch mode) to completion
         ok = [r for r in reqs if r.status == "done"]
         lat = np.array([(r.t_done - r.t_enqueue) * 1e3 for r in ok]) if ok else np.zeros(1)
+        # where the latency goes: the wait before admission (host clock) and the
+        # request's interval on the device, first launch to completion (its
+        # kernels and whatever ran beside them)
+        wait = np.array([(r.t_admit - r.t_enqueue) * 1e3 for r in ok]) if ok else np.zeros(1)
+        dev = np.array([r.dev_ms[1] - r.dev_ms[0] for r in ok if r.dev_ms is not None])
+        dev = dev if dev.size else np.zeros(1)
         return {"requests": len(reqs), "wall_s": wall, "throughput_rps": len(ok) / wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "max_inflight": inflight_max,
+                "admit_wait_p50_ms": float(np.percentile(wait, 50)), "admit_wait_p99_ms": float(np.percentile(wait, 99)),
+                "device_p50_ms": float(np.percentile(dev, 50)), "device_p99_ms": float(np.percentile(dev, 99)),
                 "gpu_busy": gpu_busy_fraction([r.dev_ms for r in ok if r.dev_ms is not None], wall * 1e3),
                 "slots": len(self.slots), "slot_workspace_bytes": self.held_bytes(),
                 "peak_slot_workspace_bytes": int(held_max), "budget_bytes": int(self.budget),
                 "growths_past_budget": grown_past, "slots_shrunk": self.shrinks,
                 "retries": int(sum(r.retries for r in reqs)), "requeues": int(sum(r.requeues for r in reqs)),
                 "batched_selections": self.batches, "views_in_batched_selections": self.batched_views,
+                "slots_grown_at_admission": self.grown,
                 "completed": len(ok), "expired": sum(r.status == "expired" for r in reqs),
                 "failed": sum(r.status.startswith("failed") for r in reqs)}
 

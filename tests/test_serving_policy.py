@@ -1,5 +1,6 @@
-"""The render server's admission and overflow decisions (pick_slot,
-overflow_action) on the CPU: a simulation with the server loop's structure
+"""The render server's admission and overflow decisions (pick_slot, with and
+without growth of a free slot at admission, and overflow_action) on the CPU:
+a simulation with the server loop's structure
 over fake slots whose selection and pair buffers overflow separately, as the
 library's do.  Every request completes (no request goes back to the queue
 forever), each one returns to the queue at most once per slot, and the slots
@@ -26,15 +27,19 @@ def _slot(cap_sel, cap_pairs):
     return s
 
 
-def _simulate(rng, n_slots, budget, views, lookahead, sizes=None):
+def _simulate(rng, n_slots, budget, views, lookahead, sizes=None, grow=False):
     """The server loop: completions (overflow -> retry or requeue), then
     admission of the head and up to `lookahead` later requests.  sizes: the
-    slots' (selection, pair) capacities after a warm-up (default: base)."""
+    slots' (selection, pair) capacities after a warm-up (default: base).
+    grow: admission may grow a free slot within the budget's room to GROWTH x
+    the largest counts its class completed with (the server's reserve)."""
     base = _bytes(64, 256)
     slots = [_slot(*(sizes[i] if sizes else (64, 256))) for i in range(n_slots)]
     while len(slots) > 1 and sum(s.held for s in slots) > budget:
         slots.pop()
     need = {}
+    counts = {}                                          # class -> largest completed (selection, pairs)
+    _simulate.max_inflight = 0
     reqs = [SimpleNamespace(rid=i, cls=c, ns=ns, np=npairs, tried=set(), requeues=0, done=False)
             for i, (c, ns, npairs) in enumerate(views)]
     pending = collections.deque(reqs)
@@ -73,6 +78,8 @@ def _simulate(rng, n_slots, budget, views, lookahead, sizes=None):
                     pending.appendleft(r)
                 continue
             need[r.cls] = max(need.get(r.cls, 0), vb)
+            c = counts.get(r.cls, (0, 0))
+            counts[r.cls] = (max(c[0], r.ns), max(c[1], r.np))
             r.done = True
             done += 1
             for idle in serving.shrink_plan(sum(x.held for x in slots), s, slots, budget, base):
@@ -83,13 +90,20 @@ def _simulate(rng, n_slots, budget, views, lookahead, sizes=None):
         while q < min(len(pending), 1 + lookahead) and free:
             r = pending[q]
             busy = len(free) < len(slots)
-            s = serving.pick_slot(need.get(r.cls), r.tried, free, slots, can_wait=busy or q > 0)
+            room = budget - sum(x.held for x in slots) if grow else None
+            s = serving.pick_slot(need.get(r.cls), r.tried, free, slots, can_wait=busy or q > 0, room=room)
             if s is None:
                 q += 1
                 continue
+            if grow and need.get(r.cls) is not None and s.held < need[r.cls] and r.cls in counts:
+                ns, npairs = counts[r.cls]                # the server's reserve: grow, never shrink
+                s.cap_sel = max(s.cap_sel, int(serving.GROWTH * ns))
+                s.cap_pairs = max(s.cap_pairs, int(serving.GROWTH * npairs))
+                s.held = _bytes(s.cap_sel, s.cap_pairs)
             del pending[q]
             free.remove(s)
             s.req = r
+        _simulate.max_inflight = max(_simulate.max_inflight, sum(x.req is not None for x in slots))
     _simulate.shrinks = shrinks[0]
     return reqs, slots, forced, tick, base
 
@@ -97,6 +111,7 @@ def _simulate(rng, n_slots, budget, views, lookahead, sizes=None):
 @pytest.mark.parametrize("seed", range(200))
 def test_every_request_completes_and_requeues_at_most_once_per_slot(seed):
     rng = random.Random(seed)
+    grow = seed % 2 == 1                                  # half the cases grow free slots at admission
     n_slots = rng.randint(1, 6)
     budget = rng.choice([1, 50_000, 200_000, 2_000_000])
     classes = [(rng.randint(10, 3000), rng.randint(10, 20000)) for _ in range(rng.randint(1, 5))]
@@ -105,7 +120,8 @@ def test_every_request_completes_and_requeues_at_most_once_per_slot(seed):
         c = rng.randrange(len(classes))
         ns, npairs = classes[c]
         views.append((c, max(1, int(ns * rng.uniform(0.3, 1.6))), max(1, int(npairs * rng.uniform(0.3, 1.6)))))
-    reqs, slots, forced, ticks, _ = _simulate(rng, n_slots, budget, views, lookahead=rng.choice([0, 1, 8]))
+    reqs, slots, forced, ticks, _ = _simulate(rng, n_slots, budget, views, lookahead=rng.choice([0, 1, 8]),
+                                              grow=grow)
     assert all(r.done for r in reqs), (seed, ticks)
     assert all(r.requeues <= len(slots) for r in reqs)
 
@@ -169,3 +185,27 @@ def test_a_view_larger_than_every_slot_grows_within_the_budget_by_shrinking_idle
     assert all(r.done for r in reqs)
     assert forced == 0 and _simulate.shrinks > 0
     assert sum(s.held for s in slots) <= budget
+
+
+def test_admission_grows_free_base_slots_instead_of_queueing_behind_the_one_large_slot():
+    """Slots returned to their base size (after shrinks) hold no mid-size
+    class; one large slot does.  Without growth at admission every request of
+    the class waits for the large slot (one in flight); with it, free base
+    slots grow within the budget's room and the requests overlap, and the
+    growth at admission never takes the slots past the budget."""
+    g = serving.GROWTH
+    mid = (0, 1000, 4000)
+    views = [mid] * 30
+    mid_slot = _bytes(int(g * 1000), int(g * 4000))
+    big = (4 * int(g * 1000), 4 * int(g * 4000))
+    budget = _bytes(*big) + 3 * mid_slot + 2 * _bytes(64, 256)
+    sizes = [big] + [(64, 256)] * 5
+    inflight = {}
+    for grow in (False, True):
+        reqs, slots, forced, _, _ = _simulate(random.Random(5), 6, budget, views, lookahead=8, sizes=sizes,
+                                              grow=grow)
+        assert all(r.done for r in reqs)
+        assert forced == 0 and sum(x.held for x in slots) <= budget
+        inflight[grow] = _simulate.max_inflight
+    # the room's check charges GROWTH x the 10% margin: two of the three mid-size slots it could hold
+    assert inflight[False] == 1 and inflight[True] == 3, inflight
