@@ -31,10 +31,9 @@ namespace {
 
 constexpr int RB = 256;
 constexpr int RGRID = 148 * 8;
-// Blocks of the pair enumeration kernels: more than are resident at once (six
-// per SM), so that blocks whose warps finish early are replaced while others
-// still run; one resident wave measured slower (pair counting 0.0376 -> 0.0408
-// ms on a 1080p view).
+// Blocks of the pair enumeration kernels: 16 per SM, more than are resident at
+// once (six); one resident wave measured slower (pair counting 0.0376 ->
+// 0.0408 ms on a 1080p view).
 #ifndef LODGS_EMIT_GRID
 #define LODGS_EMIT_GRID (148 * 16)
 #endif
