@@ -3,10 +3,12 @@
 // Each view's backward writes one gradient row per node of its own LoD cut;
 // only cut-set nodes receive gradients (appendix "Implementation Details").  For
 // a batch of views the rows of a node selected by several views must be summed.
-// The selected rows of all views are concatenated, stably radix-sorted by node
-// row, split into runs of equal rows (scan of run starts), and each run is
-// summed by one warp in view order, so the result is deterministic and no
-// atomics are needed.
+// The entries (a view's selected rows) are grouped by node row in view order:
+// for up to 8 views from one byte of view bits per node row (no sort, see
+// k_mark_views); for more views by a stable radix sort of the concatenated
+// rows, split into runs of equal rows (scan of run starts).  Each run is
+// summed in view order, so the result is deterministic and no float atomics
+// are needed.
 #include <algorithm>
 #include <vector>
 
@@ -38,6 +40,123 @@ __global__ void k_runs(const uint32_t *__restrict__ key, const uint32_t *__restr
         run_start[pos[p]] = p;
     }
     if (p == n - 1) run_start[pos[p] + flag[p]] = n;      // sentinel: one past the last run
+}
+
+// ---- grouping without a sort (up to 8 views) ----
+// Every view's selection is ascending and holds a row once, so the (row, view)
+// order of the entries that the stable sort gives can be built from one byte
+// per node row: bit v set when view v selected the row.  The union rows are
+// the rows with a nonzero byte (ascending), a row's run starts after the
+// entries of the union rows before it (the popcounts), and view v's entry of
+// row r sits at the run's start plus the number of earlier views that selected
+// r.  Bytes are packed four to a word.
+constexpr int CH_WORDS = 1024;                 // mask words per chunk (one block of BB threads, 4 words each)
+constexpr int CH_PER_THREAD = CH_WORDS / BB;
+
+__global__ void k_mark_views(const uint32_t *__restrict__ sel, uint32_t n, int v, uint32_t *__restrict__ mask) {
+    const uint32_t i = blockIdx.x * BB + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t r = sel[i];
+    atomicOr(&mask[r >> 2], (1u << v) << (8 * (r & 3u)));
+}
+
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t w) {
+    return (uint32_t)((w & 0xffu) != 0) + (uint32_t)((w & 0xff00u) != 0) + (uint32_t)((w & 0xff0000u) != 0) +
+           (uint32_t)((w & 0xff000000u) != 0);
+}
+
+// union rows (cu) and entries (ce) of each chunk
+__global__ void __launch_bounds__(BB) k_chunk_counts(const uint32_t *__restrict__ mask, uint64_t n_words,
+                                                     uint32_t *__restrict__ cu, uint32_t *__restrict__ ce) {
+    __shared__ uint32_t s_u[BB / 32], s_e[BB / 32];
+    const uint64_t w0 = (uint64_t)blockIdx.x * CH_WORDS + (uint64_t)threadIdx.x * CH_PER_THREAD;
+    uint32_t nu = 0, ne = 0;
+#pragma unroll
+    for (int k = 0; k < CH_PER_THREAD; ++k) {
+        const uint32_t w = w0 + k < n_words ? mask[w0 + k] : 0u;
+        nu += nonzero_bytes(w);
+        ne += __popc(w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nu += __shfl_xor_sync(0xffffffffu, nu, o);
+        ne += __shfl_xor_sync(0xffffffffu, ne, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s_u[warp] = nu; s_e[warp] = ne; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = 0, b = 0;
+#pragma unroll
+        for (int w = 0; w < BB / 32; ++w) { a += s_u[w]; b += s_e[w]; }
+        cu[blockIdx.x] = a;
+        ce[blockIdx.x] = b;
+    }
+}
+
+// The union rows of each chunk in ascending order: out_rows[u], the start of
+// their run of entries (run_start[u], and the end of the last run at
+// run_start[U]) and slot[r] = u for the entry pass.  cu_off / ce_off: the
+// exclusive scans of the chunks' counts; *d_nruns: the union row count U.
+__global__ void __launch_bounds__(BB) k_chunk_write(const uint32_t *__restrict__ mask, uint64_t n_words,
+                                                    const uint32_t *__restrict__ cu_off,
+                                                    const uint32_t *__restrict__ ce_off,
+                                                    const uint32_t *__restrict__ d_nruns,
+                                                    uint32_t *__restrict__ out_rows, uint32_t *__restrict__ run_start,
+                                                    uint32_t *__restrict__ slot) {
+    __shared__ uint32_t s_u[BB / 32], s_e[BB / 32];
+    const uint64_t w0 = (uint64_t)blockIdx.x * CH_WORDS + (uint64_t)threadIdx.x * CH_PER_THREAD;
+    uint32_t w[CH_PER_THREAD];
+    uint32_t nu = 0, ne = 0;
+#pragma unroll
+    for (int k = 0; k < CH_PER_THREAD; ++k) {
+        w[k] = w0 + k < n_words ? mask[w0 + k] : 0u;
+        nu += nonzero_bytes(w[k]);
+        ne += __popc(w[k]);
+    }
+    // block-wide exclusive scans of (nu, ne), in thread order = row order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t xu = nu, xe = ne;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yu = __shfl_up_sync(0xffffffffu, xu, o), ye = __shfl_up_sync(0xffffffffu, xe, o);
+        if (lane >= o) { xu += yu; xe += ye; }
+    }
+    if (lane == 31) { s_u[warp] = xu; s_e[warp] = xe; }
+    __syncthreads();
+    uint32_t u = cu_off[blockIdx.x] + xu - nu, e = ce_off[blockIdx.x] + xe - ne;
+    for (int k = 0; k < warp; ++k) { u += s_u[k]; e += s_e[k]; }
+    const uint32_t U = *d_nruns;
+#pragma unroll
+    for (int k = 0; k < CH_PER_THREAD; ++k) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t m = (w[k] >> (8 * b)) & 0xffu;
+            if (!m) continue;
+            const uint32_t r = (uint32_t)((w0 + k) * 4u + b);
+            out_rows[u] = r;
+            run_start[u] = e;
+            slot[r] = u;
+            e += __popc(m);
+            if (u + 1 == U) run_start[U] = e;            // one past the last run
+            ++u;
+        }
+    }
+}
+
+// Place view v's entries (index i in the view, row sel[i]) in (row, view)
+// order: the entry id (vals) and, if addr is given, its gradient row's address.
+__global__ void k_place_entries(const uint32_t *__restrict__ sel, uint32_t n, int v, uint32_t first,
+                                uint64_t grad_base, int stride, const uint32_t *__restrict__ mask,
+                                const uint32_t *__restrict__ slot, const uint32_t *__restrict__ run_start,
+                                uint32_t *__restrict__ vals, uint64_t *__restrict__ addr) {
+    const uint32_t i = blockIdx.x * BB + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t r = sel[i];
+    const uint32_t m = (mask[r >> 2] >> (8 * (r & 3u))) & 0xffu;
+    const uint32_t p = run_start[slot[r]] + (uint32_t)__popc(m & ((1u << v) - 1u));
+    vals[p] = first + i;
+    if (addr) addr[p] = grad_base + (uint64_t)i * (uint64_t)stride * 4u;
 }
 
 // One warp per run (a node row selected by several views).  The lanes find
@@ -185,6 +304,79 @@ __global__ void __launch_bounds__(BB) k_sum_runs4(const uint32_t *__restrict__ r
 
 int nb(uint64_t n) { return (int)std::max<uint64_t>(1, (n + BB - 1) / BB); }
 
+// The runs summed into out_grads: the lane-group kernel over the entries' row
+// addresses (addr) when rows are float4-aligned and their width is one it is
+// instantiated for, else one warp per run over the entry ids (sv).
+int launch_sums(const lodgs_scene *sc, bool vec4, bool vec2, const uint32_t *run_start, const uint32_t *d_count,
+                const uint32_t *sv, const uint64_t *addr, const uint64_t *gptr, const uint32_t *voff, int n_views,
+                float *out_grads, cudaStream_t st) {
+    const int lpr = sc->stride / 4;
+    if (vec4 && addr && (lpr == 4 || lpr == 6 || lpr == 10 || lpr == 16)) {
+        float4 *o4 = reinterpret_cast<float4 *>(out_grads);
+        if (lpr == 16) k_sum_runs4<16><<<1184, BB, 0, st>>>(run_start, d_count, addr, o4);
+        else if (lpr == 10) k_sum_runs4<10><<<1184, BB, 0, st>>>(run_start, d_count, addr, o4);
+        else if (lpr == 6) k_sum_runs4<6><<<1184, BB, 0, st>>>(run_start, d_count, addr, o4);
+        else k_sum_runs4<4><<<1184, BB, 0, st>>>(run_start, d_count, addr, o4);
+    } else if (vec2) {
+        k_sum_runs<2><<<1184, BB, 0, st>>>(run_start, d_count, sv, gptr, voff, n_views, sc->stride, out_grads);
+    } else {
+        k_sum_runs<1><<<1184, BB, 0, st>>>(run_start, d_count, sv, gptr, voff, n_views, sc->stride, out_grads);
+    }
+    count_launches(1);
+    LODGS_CUDA(cudaGetLastError());
+    return LODGS_OK;
+}
+
+// Grouping by view masks (up to 8 views; see k_mark_views), then the sums.
+int accumulate_by_mask(const lodgs_scene *sc, lodgs_frame *const *frames, const std::vector<uint32_t> &off,
+                       const std::vector<uint64_t> &gp, int n_views, uint32_t *out_rows, float *out_grads,
+                       uint32_t *d_count, bool vec4, bool vec2, cudaStream_t st) {
+    const uint32_t T = off[n_views];
+    const uint64_t M = (uint64_t)sc->n_nodes;
+    const uint64_t n_chunks = ((M + 3) / 4 + CH_WORDS - 1) / CH_WORDS;
+    const uint64_t W = n_chunks * CH_WORDS;                 // mask words, whole chunks
+    const size_t words = 2 * (size_t)n_views + 2 * (size_t)T + 2 +          // gptr, addr (8-byte words first)
+                         W + M + 4 * n_chunks + SCAN_GRID_MAX + 8 + (size_t)(n_views + 1) + (size_t)T + 1 + T;
+    uint32_t *buf = nullptr;
+    LODGS_CUDA(cudaMallocAsync((void **)&buf, words * 4, st));
+    uint64_t *gptr = reinterpret_cast<uint64_t *>(buf);
+    uint64_t *addr = gptr + n_views;
+    uint32_t *mask = reinterpret_cast<uint32_t *>(addr + T + 1), *slot = mask + W, *cu = slot + M,
+             *ce = cu + n_chunks, *cu_off = ce + n_chunks, *ce_off = cu_off + n_chunks,
+             *bsum = ce_off + n_chunks, *dn = bsum + SCAN_GRID_MAX, *voff = dn + 8, *run_start = voff + n_views + 1,
+             *sv = run_start + T + 1;
+    int rc = LODGS_OK;
+    const uint32_t nc = (uint32_t)n_chunks;
+    LODGS_CUDA(cudaMemsetAsync(mask, 0, W * 4, st));
+    LODGS_CUDA(cudaMemcpyAsync(dn, &nc, 4, cudaMemcpyHostToDevice, st));
+    LODGS_CUDA(cudaMemcpyAsync(voff, off.data(), (n_views + 1) * 4, cudaMemcpyHostToDevice, st));
+    LODGS_CUDA(cudaMemcpyAsync(gptr, gp.data(), n_views * 8, cudaMemcpyHostToDevice, st));
+    for (int v = 0; v < n_views; ++v) {
+        const uint32_t n = off[v + 1] - off[v];
+        if (!n) continue;
+        k_mark_views<<<nb(n), BB, 0, st>>>(frames[v]->f.sel_rows, n, v, mask);
+        count_launches(1);
+    }
+    k_chunk_counts<<<nc, BB, 0, st>>>(mask, W, cu, ce);
+    count_launches(1);
+    rc = scan_exclusive(cu, cu_off, dn, nc, bsum, d_count, st);
+    if (!rc) rc = scan_exclusive(ce, ce_off, dn, nc, bsum, dn + 1, st);
+    if (rc) { cudaFreeAsync(buf, st); return rc; }
+    k_chunk_write<<<nc, BB, 0, st>>>(mask, W, cu_off, ce_off, d_count, out_rows, run_start, slot);
+    count_launches(1);
+    for (int v = 0; v < n_views; ++v) {
+        const uint32_t n = off[v + 1] - off[v];
+        if (!n) continue;
+        k_place_entries<<<nb(n), BB, 0, st>>>(frames[v]->f.sel_rows, n, v, off[v], gp[v], sc->stride, mask, slot,
+                                              run_start, sv, vec4 ? addr : nullptr);
+        count_launches(1);
+    }
+    LODGS_CUDA(cudaGetLastError());
+    rc = launch_sums(sc, vec4, vec2, run_start, d_count, sv, addr, gptr, voff, n_views, out_grads, st);
+    cudaFreeAsync(buf, st);
+    return rc;
+}
+
 }  // namespace
 
 extern "C" int lodgs_accumulate_grads(lodgs_scene *sc, lodgs_frame *const *frames, const float *const *grads,
@@ -215,11 +407,16 @@ extern "C" int lodgs_accumulate_grads(lodgs_scene *sc, lodgs_frame *const *frame
     const uint32_t T = off[n_views];
     if ((int64_t)T > capacity) { set_error("accumulate_grads: capacity below the total selection"); return LODGS_E_INVALID; }
     if (T == 0) { LODGS_CUDA(cudaMemsetAsync(d_count, 0, 4, st)); return LODGS_OK; }
-    // stream-ordered temporaries
-    uint32_t *buf = nullptr;
-    // float4 rows when every row array is 16-byte aligned (row strides are multiples of 16 bytes)
+    // float4 rows when every row array is 16-byte aligned (row strides are multiples of 16 bytes),
+    // float2 rows when every row array is 8-byte aligned (strides are even)
     bool vec4 = ((uintptr_t)out_grads & 15u) == 0 && sc->stride % 4 == 0;
     for (int v = 0; v < n_views; ++v) vec4 = vec4 && (gp[v] & 15u) == 0;
+    bool vec2 = ((uintptr_t)out_grads & 7u) == 0;
+    for (int v = 0; v < n_views; ++v) vec2 = vec2 && (gp[v] & 7u) == 0;
+    if (n_views <= 8)
+        return accumulate_by_mask(sc, frames, off, gp, n_views, out_rows, out_grads, d_count, vec4, vec2, st);
+    // more views: the entries sorted by node row (stream-ordered temporaries)
+    uint32_t *buf = nullptr;
     const size_t words = 2 * (size_t)n_views + (size_t)T * (vec4 ? 9 : 7) + SORT_HIST + SCAN_GRID_MAX + 8 +
                          (size_t)(n_views + 1) + 64;
     LODGS_CUDA(cudaMallocAsync((void **)&buf, words * 4, st));
@@ -250,25 +447,14 @@ extern "C" int lodgs_accumulate_grads(lodgs_scene *sc, lodgs_frame *const *frame
     k_runs<<<nb(T), BB, 0, st>>>(sk, flag, pos, T, out_rows, run_start);
     count_launches(1);
     const int lpr = sc->stride / 4;
+    uint64_t *addr = nullptr;
     if (vec4 && (lpr == 4 || lpr == 6 || lpr == 10 || lpr == 16)) {
-        uint64_t *addr = reinterpret_cast<uint64_t *>(((uintptr_t)(voff + n_views + 1) + 7u) & ~(uintptr_t)7u);
+        addr = reinterpret_cast<uint64_t *>(((uintptr_t)(voff + n_views + 1) + 7u) & ~(uintptr_t)7u);
         k_entry_addr<<<nb(T), BB, 0, st>>>(sv, T, gptr, voff, n_views, sc->stride, addr);
-        float4 *o4 = reinterpret_cast<float4 *>(out_grads);
-        if (lpr == 16) k_sum_runs4<16><<<1184, BB, 0, st>>>(run_start, d_count, addr, o4);
-        else if (lpr == 10) k_sum_runs4<10><<<1184, BB, 0, st>>>(run_start, d_count, addr, o4);
-        else if (lpr == 6) k_sum_runs4<6><<<1184, BB, 0, st>>>(run_start, d_count, addr, o4);
-        else k_sum_runs4<4><<<1184, BB, 0, st>>>(run_start, d_count, addr, o4);
-        count_launches(2);
-    } else {
-        // float2 rows when every row array is 8-byte aligned (strides are even)
-        bool vec2 = ((uintptr_t)out_grads & 7u) == 0;
-        for (int v = 0; v < n_views; ++v) vec2 = vec2 && (gp[v] & 7u) == 0;
-        if (vec2)
-            k_sum_runs<2><<<1184, BB, 0, st>>>(run_start, d_count, sv, gptr, voff, n_views, sc->stride, out_grads);
-        else
-            k_sum_runs<1><<<1184, BB, 0, st>>>(run_start, d_count, sv, gptr, voff, n_views, sc->stride, out_grads);
         count_launches(1);
     }
+    rc = launch_sums(sc, vec4, vec2, run_start, d_count, sv, addr, gptr, voff, n_views, out_grads, st);
+    if (rc) { cudaFreeAsync(buf, st); return rc; }
     LODGS_CUDA(cudaGetLastError());
     LODGS_CUDA(cudaFreeAsync(buf, st));
     return LODGS_OK;
