@@ -440,7 +440,7 @@ int lodgs_render_backward(lodgs_scene *scene, lodgs_frame *frame, const float *r
  *   out_rows   device uint32, capacity >= sum of the views' selections: union rows, ascending
  *   out_grads  device float32, capacity x stride: the summed rows, in out_rows order
  *   d_count    device uint32: the union size
- * Temporary device memory (stream-ordered, freed on return): for up to 8 views
+ * Temporary device memory (allocated and released in stream order): up to 8 views,
  * about 5 bytes per scene node plus 16 per entry (entries grouped by a byte of
  * view bits per node); for more views about 36 bytes per entry (a radix sort).
  * Synchronises the frames' streams, then runs asynchronously on `stream`.
