@@ -105,35 +105,37 @@ __global__ void __launch_bounds__(BB) k_chunk_write(const uint32_t *__restrict__
                                                     uint32_t *__restrict__ out_rows, uint32_t *__restrict__ run_start,
                                                     uint32_t *__restrict__ slot) {
     __shared__ uint32_t s_u[BB / 32], s_e[BB / 32];
-    const uint64_t w0 = (uint64_t)blockIdx.x * CH_WORDS + (uint64_t)threadIdx.x * CH_PER_THREAD;
-    uint32_t w[CH_PER_THREAD];
-    uint32_t nu = 0, ne = 0;
-#pragma unroll
-    for (int k = 0; k < CH_PER_THREAD; ++k) {
-        w[k] = w0 + k < n_words ? mask[w0 + k] : 0u;
-        nu += nonzero_bytes(w[k]);
-        ne += __popc(w[k]);
-    }
-    // block-wide exclusive scans of (nu, ne), in thread order = row order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t xu = nu, xe = ne;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t yu = __shfl_up_sync(0xffffffffu, xu, o), ye = __shfl_up_sync(0xffffffffu, xe, o);
-        if (lane >= o) { xu += yu; xe += ye; }
-    }
-    if (lane == 31) { s_u[warp] = xu; s_e[warp] = xe; }
-    __syncthreads();
-    uint32_t u = cu_off[blockIdx.x] + xu - nu, e = ce_off[blockIdx.x] + xe - ne;
-    for (int k = 0; k < warp; ++k) { u += s_u[k]; e += s_e[k]; }
+    uint32_t ubase = cu_off[blockIdx.x], ebase = ce_off[blockIdx.x];
     const uint32_t U = *d_nruns;
-#pragma unroll
+    // CH_PER_THREAD rounds of BB consecutive words (one per thread, so that
+    // neighbouring threads write neighbouring rows), each with block-wide
+    // exclusive scans of the union rows and entries, in row order
     for (int k = 0; k < CH_PER_THREAD; ++k) {
+        const uint64_t wi = (uint64_t)blockIdx.x * CH_WORDS + (uint64_t)k * BB + threadIdx.x;
+        const uint32_t w = wi < n_words ? mask[wi] : 0u;
+        const uint32_t nu = nonzero_bytes(w), ne = __popc(w);
+        uint32_t xu = nu, xe = ne;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t yu = __shfl_up_sync(0xffffffffu, xu, o), ye = __shfl_up_sync(0xffffffffu, xe, o);
+            if (lane >= o) { xu += yu; xe += ye; }
+        }
+        if (lane == 31) { s_u[warp] = xu; s_e[warp] = xe; }
+        __syncthreads();
+        uint32_t u = ubase + xu - nu, e = ebase + xe - ne, tu = 0, te = 0;
+#pragma unroll
+        for (int j = 0; j < BB / 32; ++j) {
+            const uint32_t a = s_u[j], b = s_e[j];
+            if (j < warp) { u += a; e += b; }
+            tu += a;
+            te += b;
+        }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const uint32_t m = (w[k] >> (8 * b)) & 0xffu;
+            const uint32_t m = (w >> (8 * b)) & 0xffu;
             if (!m) continue;
-            const uint32_t r = (uint32_t)((w0 + k) * 4u + b);
+            const uint32_t r = (uint32_t)(wi * 4u + b);
             out_rows[u] = r;
             run_start[u] = e;
             slot[r] = u;
@@ -141,6 +143,9 @@ __global__ void __launch_bounds__(BB) k_chunk_write(const uint32_t *__restrict__
             if (u + 1 == U) run_start[U] = e;            // one past the last run
             ++u;
         }
+        ubase += tu;
+        ebase += te;
+        __syncthreads();                                 // s_u and s_e are rewritten next round
     }
 }
 
