@@ -166,7 +166,7 @@ class RenderServer:
         self.peak = 0                     # the largest workspace the slots held in run(), growths included
         self.need: dict = {}              # request class -> largest workspace bytes it needed
         self.rep: dict = {}               # request class -> the camera of that largest need
-        self.counts: dict = {}            # request class -> largest (selected, rectangle pairs) rendered
+        self.counts: dict = {}            # request class -> largest (selected, kept pairs) rendered
         self.grown = 0                    # slots grown at admission (pick_slot with room)
         self._ref = None                  # event at the start of run(): device times are taken from it
         while len(self.slots) > 1 and self.held_bytes() > self.budget:
@@ -199,9 +199,10 @@ class RenderServer:
     def _grow(self, slot: _Slot, camera) -> None:
         """Grow a free slot's workspace for a request's class before its
         launch (admission within the budget's room): GROWTH x the largest
-        selection and rectangle pair counts the class rendered (the rectangle
-        pairs bound the stored ones).  A class known only from an overflow is
-        left to the overflow path; a failed growth leaves the slot as it was."""
+        selection and kept-pair counts the class rendered.  A view that needs
+        more (a frame on the global ordering stores every rectangle pair)
+        overflows once and grows on the overflow path, as does a class known
+        only from an overflow; a failed growth leaves the slot as it was."""
         counts = self.counts.get(request_class(camera))
         if counts is None:
             return
